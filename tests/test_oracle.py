@@ -1,0 +1,363 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a transposed operand) fails one of them:
+  * brute force: multigrid converges to the direct sparse solution of the
+    assembled system (checks the cycle's transfer operators and smoother);
+  * polynomial exactness of every equation row (quadratic for the full
+    3^d stencils, linear for the reduced ones), in 2D and 3D, Dirichlet and
+    Neumann: pins interior stencil, closest point B, stencil orientation,
+    Lagrange weights and the discrete normal;
+  * a whole-system quadratic patch test (discrete solution == exact u);
+  * second-order convergence to manufactured solutions (Sec. 2.3 accuracy);
+  * h-independent V-cycle factor on Dirichlet domains (the central claim);
+  * the paper's printed convergence factors (Tables rhoC, badrho);
+  * invariants of restriction (printed stencils, partition of unity),
+    extension (constants, fields constant along normals), interpolation
+    (linear exactness), mirror symmetry and the CFL bounds of Sec. 2.3.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1111_0983_gb300 import inputs
+from helpers import direct_solve, oracle_for, problem_rhs, rel_maxdiff, rho_homogeneous
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return json.load(fh)
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("P,n,nc", [(inputs.disk(), 33, 9), (inputs.flower(), 65, 17),
+                                    (inputs.star(4), 65, 33), (inputs.torus(), 17, 9)])
+def test_multigrid_matches_direct_solve(P, n, nc):
+    O = oracle_for(P, n, nc)
+    f, g = problem_rhs(O, P, n)
+    ud = direct_solve(O, f, g)
+    u, norms, ok = O.solve(rtol=1e-13, max_cycles=200)
+    assert ok
+    T = O.types(0)
+    assert rel_maxdiff(u, ud, T > 0) < 1e-11
+
+
+# ------------------------------------------------------ polynomial exactness
+def _row_residuals(O, P, n, l=0):
+    """Residual of the exact u in every equation row of level l."""
+    G = O.ghosts(l)
+    types = P.bc_types(G["B"])
+    O.set_bc(l, types)
+    f = P.f_grid(n)
+    g = P.g_values(G["B"], G["nu"], types)
+    if l == 0:
+        O.set_rhs(f, g)
+    r, _ = O.defect(P.u_grid(n), l)
+    return r, G
+
+
+@pytest.mark.parametrize("dim,n,neumann", [(2, 33, "none"), (2, 33, "all"), (2, 65, "half"),
+                                           (3, 17, "none"), (3, 17, "all"), (3, 33, "half")])
+def test_quadratic_rows_exact(dim, n, neumann):
+    P = inputs.quadratic_patch(dim, neumann=neumann)
+    O = oracle.Oracle(P.phi_grid(n), 9)
+    r, G = _row_residuals(O, P, n)
+    T = O.types(0)
+    scale = np.abs(P.u_grid(n)).max()
+    assert np.abs(r[T == 1]).max() < 1e-9 * scale * (n * n)        # 5/7-point Laplacian
+    quad = G["case"] == oracle.ST_QUAD
+    assert quad.sum() > 0.8 * len(quad)
+    rg = r.ravel()[G["node"]]
+    assert np.abs(rg[quad]).max() < 1e-11 * scale * n
+
+
+@pytest.mark.parametrize("P,n", [(inputs.star(4), 33), (inputs.star(27), 33), (inputs.star(21), 33),
+                                 (inputs.quadratic_patch(3), 17)])
+def test_linear_rows_exact_all_stencils(P, n):
+    rng = np.random.default_rng(3)
+    c = rng.uniform(-1, 1, size=P.dim + 1)
+    lin = inputs.quadratic_patch(P.dim, coef=np.concatenate([c, np.zeros(P.dim * (P.dim + 1) // 2)]))
+    lin.phi = P.phi
+    lin.is_neumann = lambda B: B[:, 0] > 0.05
+    O = oracle.Oracle(lin.phi_grid(n), 17)
+    r, G = _row_residuals(O, lin, n)
+    cases = np.bincount(G["case"], minlength=4)
+    assert cases[1:].sum() > 0          # reduced stencils present
+    T = O.types(0)
+    assert np.abs(r[T == 1]).max() < 1e-11 * n * n
+    # every ghost row is exact for linear u, except the two-point axis
+    # stencil with Dirichlet data: it interpolates at the projection of B on
+    # its axis line (first order, the "less accurate" stencil of Remark 3)
+    types = lin.bc_types(G["B"])
+    exact = ~((G["case"] == oracle.ST_AXIS) & (types == 0))
+    rg = r.ravel()[G["node"]]
+    assert np.abs(rg[exact]).max() < 1e-11 * n * n
+    assert (~exact).sum() <= 0.05 * len(exact)
+
+
+def test_ghost_weight_identities():
+    """Dirichlet weights interpolate constants (sum 1); Neumann weights
+    differentiate constants (sum 0) and give nu . grad for linear fields."""
+    P = inputs.star(4)
+    n = 65
+    O = oracle.Oracle(P.phi_grid(n), 17)
+    G = O.ghosts(0)
+    h = 2.0 / (n - 1)
+    X = inputs.coords(2, n)
+    for q in range(len(G["node"])):
+        k = G["nk"][q]
+        st = G["stn"][q, :k]
+        assert abs(G["wD"][q, :k].sum() - 1.0) < 1e-13
+        assert abs(G["wN"][q, :k].sum()) < 1e-10 / h
+        for a in range(2):
+            if G["case"][q] == oracle.ST_AXIS and G["s"][q, a] == 0:
+                continue        # the two-point stencil sees only its own axis
+            xa = X[a].ravel()[st]
+            assert abs(G["wD"][q, :k] @ xa - G["B"][q, a]) < 1e-13
+            assert abs(G["wN"][q, :k] @ xa - G["nu"][q, a]) < 1e-10
+        assert abs(np.linalg.norm(G["nu"][q]) - 1) < 1e-14
+
+
+def test_closest_point_lies_on_sdf_boundary():
+    """For a signed distance function, B = G - phi grad phi/|grad phi|^2 lies on
+    the circle up to the O(h^2) central-difference error (Eq. clpt)."""
+    P = inputs.circle_paper()
+    for n in (65, 129):
+        O = oracle.Oracle(P.phi_grid(n), 9)
+        B = O.ghosts(0)["B"]
+        c = (math.sqrt(2) / 20, math.sqrt(3) / 30)
+        d = np.hypot(B[:, 0] - c[0], B[:, 1] - c[1]) - 0.563
+        h = 2.0 / (n - 1)
+        assert np.abs(d).max() < 0.5 * h * h
+
+
+# --------------------------------------------------------- whole-system patch
+@pytest.mark.parametrize("neumann", ["none", "half"])
+def test_quadratic_patch_solution_exact(neumann):
+    P = inputs.quadratic_patch(2, neumann=neumann)
+    n = 65
+    O = oracle_for(P, n, 9)
+    assert np.all(O.ghosts(0)["case"] == oracle.ST_QUAD)
+    f, g = problem_rhs(O, P, n)
+    u = direct_solve(O, f, g)
+    T = O.types(0)
+    assert np.abs(u - P.u_grid(n))[T > 0].max() < 1e-10
+
+
+# ------------------------------------------------------------- second order
+@pytest.mark.parametrize("P,ns", [(inputs.flower(), (257, 513, 1025)), (inputs.disk(), (65, 129, 257)),
+                                  (inputs.torus(), (65, 129))])
+def test_second_order_convergence(P, ns):
+    errs = []
+    for n in ns:
+        O = oracle_for(P, n, 17 if P.dim == 3 else P.n_coarse)
+        f, g = problem_rhs(O, P, n)
+        u = direct_solve(O, f, g) if P.dim == 2 else O.solve(rtol=1e-10, max_cycles=40)[0]
+        T = O.types(0)
+        errs.append(np.abs(u - P.u_grid(n))[T == 1].max())
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert min(ratios) > 3.0, (errs, ratios)
+
+
+# ----------------------------------------------------- convergence factors
+def test_vcycle_rho_h_independent_dirichlet():
+    """Sec. 3 central claim on a Dirichlet domain: V(2,1) factor bounded as h -> 0."""
+    P = inputs.flower()
+    P.is_neumann = lambda B: np.zeros(B.shape[0], bool)
+    rhos = [rho_homogeneous(oracle_for(P, n, 33, rhs=False)) for n in (129, 257, 513)]
+    assert max(rhos) < 0.12, rhos
+    assert rhos[-1] <= 1.1 * rhos[0] + 0.01, rhos
+
+
+def test_paper_table_rhoC_W_cycle_nu3():
+    """Circle, W-cycle, lambda = 5, nu = 3, Nc = 8 (Table rhoC, right)."""
+    gold = _gold("paper_rho.json")["rhoC_W_lambda5_nu3_Nc8"]
+    P = inputs.circle_paper()
+    for N, rho_p in zip(gold["N"][:4], gold["rho"][:4]):
+        rho = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, gamma=2, nu1=2, nu2=1))
+        assert abs(rho - rho_p) < 0.045, (N, rho, rho_p)
+
+
+def test_paper_table_rhoC_W_cycle_nu2():
+    """Circle, W-cycle, lambda = 5, nu = 2 (Table rhoC, left): same size as printed."""
+    gold = _gold("paper_rho.json")["rhoC_W_lambda5_nu2_Nc8"]
+    P = inputs.circle_paper()
+    for N, rho_p in zip(gold["N"][:4], gold["rho"][:4]):
+        rho = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, gamma=2, nu1=1, nu2=1))
+        assert abs(rho - rho_p) < 0.08, (N, rho, rho_p)
+
+
+def test_paper_table_badrho_degradation():
+    """Without extra sweeps the factor is far from LFA (Table badrho); the
+    extra sweeps (lambda = 5) restore it (Sec. 3.2)."""
+    gold = _gold("paper_rho.json")["badrho_nu21_no_extra"]
+    P = inputs.circle_paper()
+    for N, tg_p, w_p in zip(gold["N"][:2], gold["TGCS"][:2], gold["W"][:2]):
+        tg = rho_homogeneous(oracle_for(P, N + 1, N // 2 + 1, rhs=False, lam=0, nu1=2, nu2=1))
+        w = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, lam=0, gamma=2, nu1=2, nu2=1))
+        assert abs(tg - tg_p) < 0.08 and abs(w - w_p) < 0.08, (N, tg, w)
+        good = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, lam=5, gamma=2, nu1=2, nu2=1))
+        assert good < 0.25 * tg
+
+
+# -------------------------------------------------------------- restriction
+def test_restriction_printed_stencils():
+    """Sec. 2.5: the partial transfer over Omega_h of an axis-aligned square
+    gives full weighting inside, the 3x2 stencil (Fstencil23) on an edge and
+    the 2x2 stencil (Fstencil22) at a corner."""
+    gold = _gold("restriction_stencils.json")
+    n = 33
+    h = 2.0 / (n - 1)
+    X = inputs.coords(2, n)
+    # interior nodes: |x|, |y| <= 0.5; coarse nodes at x = 0.5 have their +x fine
+    # neighbour outside
+    phi = np.maximum(np.abs(X[0]), np.abs(X[1])) - (0.5 + 0.5 * h)
+    O = oracle.Oracle(phi, 17)
+    nc = 17
+    hc = 2 * h
+    J = lambda x: int(round((x + 1) / hc))
+    cases = {"full_3x3": (J(0.0), J(0.0)),
+             "rect_3x2_x_in_-1_0": (J(0.5), J(0.0)),     # x in {-1,0}, y in {-1,1}
+             "rect_2x2": (J(0.5), J(-0.5))}             # x in {-1,0}, y in {0,1}
+    for key, (jx, jy) in cases.items():
+        wt = O.restrict_weights(0, np.ravel_multi_index((jx, jy), (nc, nc)), 1)
+        want = np.array(gold[key]["w16"], float) / 16.0
+        # printed stencils: rows = y offset, columns = x offset; ours [x][y]
+        assert wt is not None and np.allclose(wt.T, want), (key, wt.T * 16)
+
+
+def test_restriction_partition_of_unity():
+    P = inputs.star(4)
+    n = 65
+    O = oracle_for(P, n, 17, rhs=False)
+    Tc = O.types(1)
+    cnt = 0
+    for X in np.flatnonzero(Tc.ravel() > 0):
+        wt = O.restrict_weights(0, X, 1 if Tc.ravel()[X] == 1 else 0)
+        assert wt is not None and abs(wt.sum() - 1) < 1e-14
+        cnt += 1
+    assert cnt > 100
+    # a constant defect restricts to the same constant everywhere
+    r = np.full(O.shape(0), 2.5)
+    fc, gc = O.restrict(r)
+    assert np.allclose(fc[Tc == 1], 2.5) and np.allclose(gc, 2.5)
+
+
+# ---------------------------------------------------------------- extension
+def test_extension_constants_and_normal_invariance():
+    P = inputs.disk()
+    n = 129
+    O = oracle_for(P, n, 17, rhs=False)
+    E = O.extension(0)
+    assert len(E["node"]) > 0
+    r = np.zeros(O.shape(0))
+    T = O.types(0)
+    r[T == 2] = 1.75
+    re = O.extend(r)
+    assert np.allclose(re.ravel()[E["node"]], 1.75, rtol=0, atol=1e-14)
+    # a field constant along the normals of the (SDF) disk is kept to O(h)
+    X = inputs.coords(2, n)
+    ang = np.arctan2(X[1] - 0.01, X[0] - 0.02)
+    field = np.cos(3 * ang)
+    r = np.where(T == 2, field, 0.0)
+    re = O.extend(r)
+    h = 2.0 / (n - 1)
+    err = np.abs(re.ravel()[E["node"]] - field.ravel()[E["node"]]).max()
+    assert err < 12 * h, err
+
+
+def test_extension_is_upwind_ordered():
+    O = oracle_for(inputs.flower(), 129, 33, rhs=False)
+    E = O.extension(0)
+    phi = inputs.flower().phi_grid(129).ravel()
+    pos = {int(v): i for i, v in enumerate(E["node"])}
+    for i, P in enumerate(E["node"]):
+        for s in E["src"][i, :E["nsrc"][i]]:
+            assert phi[s] < phi[P]
+            if int(s) in pos:
+                assert pos[int(s)] < i
+
+
+# --------------------------------------------------------------- prolongation
+def test_prolongation_linear_exact_where_parents_exist():
+    P = inputs.flower()
+    n = 129
+    O = oracle_for(P, n, 33, rhs=False)
+    Xc = inputs.coords(2, 65)
+    e = 0.3 + 1.7 * Xc[0] - 0.9 * Xc[1]
+    Tc = O.types(1)
+    ec = np.where(Tc > 0, e, 0.0)
+    out = O.prolong(ec)
+    X = inputs.coords(2, n)
+    want = 0.3 + 1.7 * X[0] - 0.9 * X[1]
+    T = O.types(0)
+    # fine nodes whose coarse parents all lie in Omega_2h u Gamma_2h
+    ok = np.zeros(T.shape, bool)
+    for i, j in zip(*np.nonzero(T > 0)):
+        par = [(a, b) for a in {i // 2, (i + 1) // 2} for b in {j // 2, (j + 1) // 2}]
+        ok[i, j] = all(Tc[a, b] > 0 for a, b in par)
+    assert ok.sum() > 0.9 * (T > 0).sum()
+    assert np.abs(out - want)[ok].max() < 1e-13
+    # a constant is reproduced at every unknown (renormalised weights)
+    out = O.prolong(np.where(Tc > 0, 4.0, 0.0))
+    assert np.allclose(out[T > 0], 4.0)
+
+
+# ------------------------------------------------------ symmetry and CFL
+def test_mirror_symmetry_sgn_zero_rule():
+    """A domain and data symmetric under y -> -y give a symmetric solution to
+    rounding; ghosts on y = 0 exercise the sgn(0) reading."""
+    P = inputs.Problem("mirror", 2,
+                       phi=lambda x, y: np.sqrt((x - 0.031) ** 2 + y * y) - 0.57,
+                       u=lambda x, y: np.cos(2 * x) * np.cosh(y),
+                       grad_u=lambda x, y: [-2 * np.sin(2 * x) * np.cosh(y), np.cos(2 * x) * np.sinh(y)],
+                       f=lambda x, y: 3 * np.cos(2 * x) * np.cosh(y),
+                       is_neumann=lambda B: B[:, 0] > 0.1)
+    n = 129
+    O = oracle_for(P, n, 17)
+    G = O.ghosts(0)
+    assert (G["s"] == 0).any()
+    T = O.types(0)
+    assert np.array_equal(T, T[:, ::-1])
+    f, g = problem_rhs(O, P, n)
+    ud = direct_solve(O, f, g)
+    # an asymmetric discretisation would show at the O(h^2) ~ 1e-4 level; the
+    # sparse LU's rounding stays near cond * eps
+    assert np.abs(ud - ud[:, ::-1])[T > 0].max() < 1e-9 * np.abs(ud).max()
+    # red-black + Jacobi ghost sweeps commute with the mirror (n - 1 even)
+    u, norms, ok = O.solve(rtol=1e-10, max_cycles=100)
+    assert ok
+    assert np.abs(u - u[:, ::-1])[T > 0].max() < 1e-9 * np.abs(u).max()
+
+
+@pytest.mark.parametrize("P,n", [(inputs.flower(), 257), (inputs.star(4), 129), (inputs.torus(), 33)])
+def test_cfl_bounds(P, n):
+    """Sec. 2.3: mu_D dt = 0.9 and mu_N dt = 0.9 * 2h / (3 sqrt d) keep every
+    ghost's self coefficient times its step in (0, 0.9]."""
+    O = oracle_for(P, n, 17, rhs=False)
+    G = O.ghosts(0)
+    h = 2.0 / (n - 1)
+    types = P.bc_types(G["B"])
+    cN = 0.9 * 2 * h / (3 * math.sqrt(P.dim))
+    for q in range(len(G["node"])):
+        k = G["nk"][q]
+        self_k = np.flatnonzero(G["stn"][q, :k] == G["node"][q])
+        assert len(self_k) == 1
+        wself = (G["wN"] if types[q] else G["wD"])[q, self_k[0]]
+        c = cN if types[q] else 0.9
+        assert 0 < c * wself <= 0.9 + 1e-12, (q, c * wself)
+
+
+def test_geometry_errors_reported():
+    n = 33
+    X = inputs.coords(2, n)
+    with pytest.raises(oracle.OracleError):
+        oracle.Oracle(np.hypot(X[0], X[1]) - 0.99, 9)       # touches the box edge
+    with pytest.raises(oracle.OracleError):
+        oracle.Oracle(np.zeros((n, n)) - 1.0, 9)            # everything inside
