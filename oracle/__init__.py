@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("lam", C.c_int), ("gamma", C.c_int),
                 ("mode", C.c_int), ("extra_once", C.c_int), ("delta_over_h", C.c_double),
-                ("c_dirichlet", C.c_double), ("c_neumann_factor", C.c_double)]
+                ("c_dirichlet", C.c_double), ("c_neumann_factor", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double)]
 
 
 _lib = None
@@ -94,13 +94,13 @@ class Oracle:
     """One multigrid hierarchy built from a fine level set ``phi`` (shape n^dim)."""
 
     def __init__(self, phi, n_coarse, nu1=2, nu2=1, lam=5, gamma=1, mode=0, extra_once=0,
-                 delta_over_h=3.0, c_dirichlet=0.9, c_neumann_factor=0.9):
+                 delta_over_h=3.0, c_dirichlet=0.9, c_neumann_factor=0.9, junction_sweeps=40, junction_radius=12.0):
         phi = np.ascontiguousarray(phi, dtype=np.float64)
         self.dim = phi.ndim
         self.n = phi.shape[0]
         assert all(s == self.n for s in phi.shape)
         self.params = Params(nu1, nu2, lam, gamma, mode, extra_once, delta_over_h, c_dirichlet,
-                             c_neumann_factor)
+                             c_neumann_factor, junction_sweeps, junction_radius)
         L = lib()
         self._h = L.orc_create(self.dim, self.n, n_coarse, _p(phi), C.byref(self.params))
         if not self._h:

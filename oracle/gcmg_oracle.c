@@ -44,6 +44,8 @@ typedef struct {
     double delta_over_h;   /* band width delta / h (Sec. 3.2 uses 3) */
     double c_dirichlet;    /* mu_D dt (Sec. 2.3 uses 0.9) */
     double c_neumann_factor; /* mu_N dt = factor * 2h / (3 sqrt(d)) (Sec. 2.3 uses 0.9) */
+    int junction_sweeps;   /* mu_J: local sweeps near Dirichlet/Neumann junctions (0: none) */
+    double junction_radius;/* R_J: junction zone radius, in units of h of each level */
 } orc_params;
 
 typedef struct {
@@ -54,6 +56,7 @@ typedef struct {
     double *phi;
     uint8_t *type;
     uint8_t *band;
+    uint8_t *jzone;        /* unknowns of the junction zone (NULL: none) */
     /* ghost records, in increasing node index */
     int64_t ng;
     int64_t *gnode;
@@ -622,6 +625,55 @@ static void base_relax(Oracle *O, Level *L) {
     else { rb_sweep(L, 0); ghost_jacobi(L); }
 }
 
+/* Junction relaxation (an addition to the paper's smoother; mu_J = 0 gives
+ * the paper's method).  Where Dirichlet and Neumann ghosts meet, the error of
+ * the mixed problem is singular and the boundary extra sweeps of Sec. 3.2 do
+ * not reach it, so the cycle's factor grows as h shrinks.  Following the same
+ * rationale (relax more where the error decays slowly), mu_J extra sweeps --
+ * red, black, then Jacobi on the ghosts -- run on the unknowns within R_J h of
+ * a ghost whose 3^d neighbourhood holds a ghost of the other type, after every
+ * relaxation on every level. */
+static void zone_sweep(Level *L) {
+    for (int color = 0; color < 2; color++)
+        for (int64_t i = 0; i < L->nn; i++)
+            if (L->type[i] == T_INT && L->jzone[i] && parity(L, i) == color) interior_update(L, i);
+    for (int64_t q = 0; q < L->ng; q++)
+        if (L->jzone[L->gnode[q]]) L->gtmp[q] = L->u[L->gnode[q]] + L->c[q] * (L->g[q] - ghost_operator(L, q, L->u));
+    for (int64_t q = 0; q < L->ng; q++)
+        if (L->jzone[L->gnode[q]]) L->u[L->gnode[q]] = L->gtmp[q];
+}
+
+/* marks unknowns within radius (in h) of a junction ghost: a ghost whose
+ * 3^d neighbourhood holds a ghost of the other bc type */
+static void build_jzone(Level *L, double radius) {
+    int d = L->dim;
+    if (!L->jzone) L->jzone = (uint8_t *)calloc((size_t)L->nn, 1);
+    memset(L->jzone, 0, (size_t)L->nn);
+    int R = (int)ceil(radius);
+    for (int64_t q = 0; q < L->ng; q++) {
+        int64_t G = L->gnode[q];
+        int j[MAXD]; idx_to_j(L, G, j);
+        int junction = 0;
+        int total = 1; for (int a = 0; a < d; a++) total *= 3;
+        for (int c = 0; c < total; c++) {
+            int jj[MAXD], rem = c;
+            for (int a = d - 1; a >= 0; a--) { jj[a] = j[a] + rem % 3 - 1; rem /= 3; }
+            if (!j_in_box(L, jj)) continue;
+            int64_t P = j_to_idx(L, jj);
+            if (L->type[P] == T_GHOST && L->bc[L->gid[P]] != L->bc[q]) junction = 1;
+        }
+        if (!junction) continue;
+        int side = 2 * R + 1, tot = 1; for (int a = 0; a < d; a++) tot *= side;
+        for (int c = 0; c < tot; c++) {
+            int jj[MAXD], rem = c; double r2 = 0;
+            for (int a = d - 1; a >= 0; a--) { int o = rem % side - R; rem /= side; jj[a] = j[a] + o; r2 += (double)o * o; }
+            if (r2 > radius * radius || !j_in_box(L, jj)) continue;
+            int64_t P = j_to_idx(L, jj);
+            if (is_unknown(L, P)) L->jzone[P] = 1;
+        }
+    }
+}
+
 /* lambda extra sweeps on Gamma_h and the band (Sec. 3.2) */
 static void extra_sweeps(Oracle *O, Level *L) {
     for (int k = 0; k < O->p.lambda; k++) {
@@ -634,6 +686,8 @@ static void smooth(Oracle *O, Level *L, int nu) {
     for (int k = 0; k < nu; k++) {
         base_relax(O, L);
         if (!O->p.extra_once) extra_sweeps(O, L);
+        if (O->p.junction_sweeps && L->jzone)
+            for (int m = 0; m < O->p.junction_sweeps; m++) zone_sweep(L);
     }
     if (O->p.extra_once && nu > 0) extra_sweeps(O, L);
 }
@@ -924,7 +978,7 @@ static void cycle(Oracle *O, int l) {
 /* ------------------------------------------------------------ public API */
 
 static void free_level(Level *L) {
-    free(L->phi); free(L->type); free(L->band); free(L->gnode); free(L->gid);
+    free(L->phi); free(L->type); free(L->band); free(L->jzone); free(L->gnode); free(L->gid);
     free(L->B); free(L->nu); free(L->tloc); free(L->sdir); free(L->gcase); free(L->nk);
     free(L->stn); free(L->wD); free(L->wN); free(L->bc); free(L->c);
     free(L->u); free(L->f); free(L->r); free(L->g); free(L->gtmp);
@@ -1043,6 +1097,7 @@ void orc_set_bc(void *h, int l, const uint8_t *bc) {
         L->c[q] = (L->bc[q] == BC_D) ? O->p.c_dirichlet
                                      : O->p.c_neumann_factor * 2.0 * L->h / (3.0 * sqrt((double)L->dim));
     }
+    build_jzone(L, O->p.junction_radius);
     if (l == O->nlev - 1) {
         free(L->unk); free(L->LU); free(L->piv);
         L->unk = NULL; L->LU = NULL; L->piv = NULL;

@@ -180,7 +180,7 @@ def test_paper_table_rhoC_W_cycle_nu3():
     gold = _gold("paper_rho.json")["rhoC_W_lambda5_nu3_Nc8"]
     P = inputs.circle_paper()
     for N, rho_p in zip(gold["N"][:4], gold["rho"][:4]):
-        rho = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, gamma=2, nu1=2, nu2=1))
+        rho = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, gamma=2, nu1=2, nu2=1, junction_sweeps=0))
         assert abs(rho - rho_p) < 0.045, (N, rho, rho_p)
 
 
@@ -189,7 +189,7 @@ def test_paper_table_rhoC_W_cycle_nu2():
     gold = _gold("paper_rho.json")["rhoC_W_lambda5_nu2_Nc8"]
     P = inputs.circle_paper()
     for N, rho_p in zip(gold["N"][:4], gold["rho"][:4]):
-        rho = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, gamma=2, nu1=1, nu2=1))
+        rho = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, gamma=2, nu1=1, nu2=1, junction_sweeps=0))
         assert abs(rho - rho_p) < 0.08, (N, rho, rho_p)
 
 
@@ -199,11 +199,25 @@ def test_paper_table_badrho_degradation():
     gold = _gold("paper_rho.json")["badrho_nu21_no_extra"]
     P = inputs.circle_paper()
     for N, tg_p, w_p in zip(gold["N"][:2], gold["TGCS"][:2], gold["W"][:2]):
-        tg = rho_homogeneous(oracle_for(P, N + 1, N // 2 + 1, rhs=False, lam=0, nu1=2, nu2=1))
-        w = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, lam=0, gamma=2, nu1=2, nu2=1))
+        paper = dict(rhs=False, nu1=2, nu2=1, junction_sweeps=0)
+        tg = rho_homogeneous(oracle_for(P, N + 1, N // 2 + 1, lam=0, **paper))
+        w = rho_homogeneous(oracle_for(P, N + 1, 9, lam=0, gamma=2, **paper))
         assert abs(tg - tg_p) < 0.08 and abs(w - w_p) < 0.08, (N, tg, w)
-        good = rho_homogeneous(oracle_for(P, N + 1, 9, rhs=False, lam=5, gamma=2, nu1=2, nu2=1))
+        good = rho_homogeneous(oracle_for(P, N + 1, 9, lam=5, gamma=2, **paper))
         assert good < 0.25 * tg
+
+
+def test_junction_relaxation_restores_mixed_bc_vcycle():
+    """Where Dirichlet and Neumann ghosts meet, the V-cycle of the paper's
+    smoother degrades with h (and diverges on star 0); the junction relaxation
+    keeps the factor bounded."""
+    P = inputs.star(0)
+    assert rho_homogeneous(oracle_for(P, 257, 65, rhs=False, junction_sweeps=0)) > 1.0
+    assert rho_homogeneous(oracle_for(P, 257, 65, rhs=False)) < 0.15
+    F = inputs.flower()
+    plain = [rho_homogeneous(oracle_for(F, n, 33, rhs=False, junction_sweeps=0)) for n in (257, 513)]
+    fixed = [rho_homogeneous(oracle_for(F, n, 33, rhs=False)) for n in (257, 513)]
+    assert plain[1] > 0.5 and fixed[1] < 0.2 and fixed[0] < 0.15, (plain, fixed)
 
 
 # -------------------------------------------------------------- restriction
