@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 ghost-cell multigrid.
+
+Metric: unknowns (|Omega_h| + |Gamma_h|) solved per second from u = 0 to
+relative residual 1e-10 (||r||_inf / ||r0||_inf, r0 = (f, g)).  One step is
+one whole solve of the workload with f and g already resident in HBM; an L2
+flush (a 256 MB write) separates steps.  `e2e` repeats the measurement
+through the host-buffer entry point (host -> device copies of f and g and the
+device -> host copy of u inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config flower4097]
+                    [--precision mixed|fp64] [--impl gcmg|reference]
+
+Under torchrun every rank solves its own replica (the single-grid solve does
+not shard); value = all ranks' unknowns / the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle (the correctness reference) on
+bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1111_0983_gb300 import inputs  # noqa: E402
+
+METRIC = "unknowns/s to rel. residual 1e-10"
+WORKLOADS = {
+    # name: (problem factory, n, n_coarse, description)
+    "flower4097": (inputs.flower, 4097, 33, "2D flower r-0.5-0.15 sin(5 theta), mixed D/N, 4097^2"),
+    "flower1025": (inputs.flower, 1025, 33, "2D flower r-0.5-0.15 sin(5 theta), mixed D/N, 1025^2"),
+    "disk65": (inputs.disk, 65, 17, "2D disk r=0.7, Dirichlet, 65^2"),
+    "torus257": (inputs.torus, 257, 17, "3D torus R=0.5 r=0.25, mixed D/N, 257^3"),
+    "torus513": (inputs.torus, 513, 17, "3D torus R=0.5 r=0.25, mixed D/N, 513^3"),
+}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="flower4097", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--gamma", type=int, default=1)
+    ap.add_argument("--impl", default="gcmg", choices=["gcmg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-cycles", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------- clock sampling
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since it was captured."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1111_0983_gb300", "csrc", "kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec.get("dram_bytes_per_launch") if rec.get("kernels_cu_sha") == sha else None
+
+
+# ------------------------------------------------------------------ problem
+def build_problem(name):
+    fac, n, nc, desc = WORKLOADS[name]
+    return fac(), n, nc, desc
+
+
+def oracle_cycle_sample(P, n, nc, gamma, cycles):
+    """Seconds per cycle of the FP64 CPU oracle on the full workload."""
+    import oracle
+    O = oracle.Oracle(P.phi_grid(n), nc, gamma=gamma)
+    for l in range(O.nlev):
+        O.set_bc(l, P.bc_types(O.ghosts(l)["B"]))
+    G = O.ghosts(0)
+    types = P.bc_types(G["B"])
+    O.set_rhs(P.f_grid(n), P.g_values(G["B"], G["nu"], types))
+    t0 = time.perf_counter()
+    _, norms, _ = O.solve(rtol=0.0, max_cycles=cycles)
+    dt = time.perf_counter() - t0
+    nunk = int((O.types(0) > 0).sum())
+    return dt / max(len(norms) - 1, 1), nunk, norms
+
+
+def cycles_reference(name, precision):
+    """Cycles to 1e-10 of the oracle on this workload (written by
+    tests/golden/make_bench_cycles.py, which calls only the oracle)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "bench_cycles.json")) as fh:
+            return json.load(fh)[name]["cycles"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist()
+    if rank != 0:
+        return
+    P, n, nc, desc = build_problem(args.config)
+    cyc = cycles_reference(args.config, args.precision)
+    per_cycle = []
+    nunk = None
+    t_total0 = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        sec, nunk, _ = oracle_cycle_sample(P, n, nc, args.gamma, 1)
+        if i >= args.warmup:
+            per_cycle.append(sec)
+    wall = time.perf_counter() - t_total0
+    sec = statistics.mean(per_cycle)
+    value = nunk / (sec * cyc) if cyc else None
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.config, "description": desc, "unknowns": nunk, "cycle": "V" if args.gamma == 1 else "W"},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one oracle cycle per step on the full {args.config} problem; "
+                                       f"unknowns/s = unknowns / (s per cycle x {cyc} cycles to 1e-10 of the oracle)"},
+            "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- gcmg arm
+def run_gcmg(args):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    from paper_1111_0983_gb300 import gcmg
+
+    rank, world, local = dist()
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    P, n, nc, desc = build_problem(args.config)
+    precision = 1 if args.precision == "mixed" else 0
+    phi = P.phi_grid(n)
+    S = gcmg.Solver(phi, nc, stream=stream, precision=precision, gamma=args.gamma, rtol=1e-10, max_cycles=256)
+    for l in range(S.nlev):
+        S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+    G = S.ghosts(0)
+    types = P.bc_types(G["B"])
+    f_h = P.f_grid(n)
+    g_h = P.g_values(G["B"], G["nu"], types)
+    f = torch.from_numpy(f_h).cuda()
+    g = torch.from_numpy(g_h).cuda()
+    S.set_rhs(f, g)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    nunk = S.num_unknowns(0)
+    n_in = int(((S.node_types(0) & 3) == 1).sum())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        u.zero_()
+        st = S.solve(u)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    S.set_kernel_timing(S.KERNEL_SMOOTH)
+    launches0 = gcmg.launch_counter()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    cycles = []
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        u.zero_()
+        ev[k][0].record(stream)
+        st = S.solve(u)
+        ev[k][1].record(stream)
+        cycles.append(st["cycles"])
+        if not st["converged"]:
+            raise RuntimeError(f"solve did not converge: {st}")
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    launches = gcmg.launch_counter() - launches0
+    k_launches, k_ms = S.kernel_timing()
+    S.set_kernel_timing(-1)
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nunk * args.steps * world / (ms / 1e3)
+
+    # end to end through the host-buffer entry point
+    f_pin = torch.from_numpy(f_h).pin_memory().numpy()
+    g_pin = torch.from_numpy(g_h).pin_memory().numpy()
+    u_pin = torch.empty(S.shape(0), dtype=torch.float64).pin_memory().numpy()
+    S.solve_host(f_pin, g_pin, u_pin)
+    barrier()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st_h = S.solve_host(f_pin, g_pin, u_pin)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = nunk * args.steps * world / e2e_s
+
+    peaks, peak_kind = measured_peaks()
+    bytes_per_node = 12 if precision == 0 else 6      # one colour half-sweep: see the design doc
+    alg_bytes = bytes_per_node * n_in
+    avg_ms = k_ms / max(k_launches, 1)
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if k_launches else None
+    peak = peaks.get("hbm_gbs")
+    kname = f"rb_interior_{'f64' if precision == 0 else 'f32'}_{args.config}"
+    roofline = {"bound": "hbm", "kernel": "k_rb_interior (fine level, one colour)", "achieved": achieved,
+                "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms, "launches_timed": k_launches}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 cycles + f64 refinement" if precision else "f64", "data": "synthetic",
+                "config": {"workload": args.config, "description": desc, "unknowns": nunk, "inside": n_in,
+                           "ghosts": S.num_ghosts(0), "levels": S.nlev, "n_coarse": nc,
+                           "cycle": "V(2,1)" if args.gamma == 1 else "W(2,1)", "lambda": 5,
+                           "cycles_per_solve": cycles, "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": int(f_h.nbytes + g_h.nbytes),
+                        "d2h_bytes_per_step": int(u_pin.nbytes)},
+                "wall_s": wall}
+        if world == 1 and not args.no_cpu_baseline:
+            sec, nu_o, _ = oracle_cycle_sample(P, n, nc, args.gamma, args.cpu_sample_cycles)
+            cyc = cycles_reference(args.config, args.precision) or statistics.median(cycles)
+            line["cpu_baseline"] = {"value": nu_o / (sec * cyc), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{args.cpu_sample_cycles} oracle cycles on the full problem, "
+                                              f"{sec:.2f} s/cycle, scaled by {cyc} cycles to 1e-10"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gcmg(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * gcmg.h -- C ABI of the GB300 ghost-cell multigrid library (libgcmg.so).
+ *
+ * Solves the Poisson problem with mixed boundary conditions on an arbitrary
+ * domain given by a level set (Coco & Russo, "A Finite Difference Ghost-cell
+ * Multigrid approach for Poisson Equation with mixed Boundary Conditions in
+ * Arbitrary Domain", arXiv 1111.0983, Sec. 2, Eq. (mainpr)):
+ *
+ *     -Lap u = f  in Omega = {phi < 0},   u = g_D on Gamma_D,   du/dn = g_N on Gamma_N,
+ *
+ * discretised on the vertex grid of D = [-1,1]^d (d = 2 or 3) with n = N+1
+ * nodes per axis, h = 2/N, node j at -1 + j h (Sec. 2.3).  The unknowns are
+ * the inside nodes Omega_h (phi < 0) and the ghost nodes Gamma_h (outside
+ * nodes with an axis neighbour inside).  Each ghost G carries the boundary
+ * condition at its closest boundary point B (Eq. clpt), interpolated on an
+ * upwind 3^d stencil (Eqs. St_G, dir2d, neu2d; reduced stencils of Remark 3).
+ * The system (Eq. discr) is solved by multigrid V- or W-cycles (TGCS of
+ * Sec. 2.4 applied recursively) with the boundary restriction of Sec. 2.5,
+ * the defect extension of Sec. 2.6 and the extra boundary sweeps of Sec. 3.2.
+ *
+ * Conventions for every call:
+ *  - Grid arrays are dense, C ordered, axis 0 (x) slowest: element
+ *    ((j0 * n) + j1) * n + j2 for node (j0, j1, j2); n^d elements.
+ *  - Per-ghost arrays of a level follow the ghost order of that level, which
+ *    is increasing node index.
+ *  - "_dev" pointers are device memory on the context's device, "_host"
+ *    pointers host memory.  All buffers stay owned by the caller and are only
+ *    borrowed for the duration of the call; the library copies what it keeps.
+ *  - Work is enqueued on the stream given at creation (cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  Calls that return values to the
+ *    host synchronise that stream before returning.
+ *  - Every call returns a status; no call aborts or throws.  The message of
+ *    the last failure is kept per context (gcmg_last_error).
+ *  - A context is not thread safe: use one context per host thread.
+ */
+#ifndef GCMG_H
+#define GCMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gcmg_ctx gcmg_ctx;
+
+typedef enum {
+    GCMG_OK = 0,
+    GCMG_E_ARG = 1,      /* invalid argument (sizes, pointers, level index) */
+    GCMG_E_CUDA = 2,     /* a CUDA call failed; see gcmg_last_error */
+    GCMG_E_OOM = 3,      /* device or host allocation failed */
+    GCMG_E_GEOM = 4,     /* geometry unusable: an unknown, ghost stencil or extension
+                            node on the box boundary, no usable ghost stencil, a
+                            degenerate normal, or a singular coarsest system */
+    GCMG_E_NOCONV = 5,   /* max_cycles reached, or a NaN/Inf defect */
+    GCMG_E_STATE = 6     /* call out of order (e.g. solve before set_rhs) */
+} gcmg_status;
+
+/* Cycle parameters (Sec. 2.4, Sec. 3.2).  gcmg_default_params fills the
+ * paper's values: nu1 = 2, nu2 = 1, lambda = 5, delta = 3h, mu_D dt = 0.9,
+ * mu_N dt = 0.9 * 2h / (3 sqrt(d)), V-cycle; plus the junction relaxation
+ * that this library adds for mixed boundaries (mu_J = 40, R_J = 12; the
+ * paper has no counterpart -- without it the V-cycle factor of a mixed
+ * problem grows as h shrinks). */
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int n;                   /* fine nodes per axis: (n - 1) = (n_coarse - 1) * 2^k, k >= 1 */
+    int n_coarse;            /* nodes per axis of the coarsest grid (exact solve there) */
+    int nu1, nu2;            /* pre / post relaxations */
+    int lambda;              /* extra sweeps on the band and the ghosts after each relaxation */
+    int gamma;               /* 1 = V-cycle, 2 = W-cycle */
+    double delta_over_h;     /* band half-width delta / h of the extra sweeps */
+    double c_dirichlet;      /* mu_D dt of Eq. dir2d */
+    double c_neumann_factor; /* mu_N dt = c_neumann_factor * 2h / (3 sqrt(d)) (Eq. neu2d) */
+    int precision;           /* 0: FP64 cycles; 1: FP32 cycles inside FP64 iterative refinement */
+    int max_cycles;          /* limit of cycles (plain) or refinement steps (mixed) */
+    double rtol;             /* stop when ||r||_inf <= rtol * ||r0||_inf, r0 = (f, g) */
+    int junction_sweeps;     /* mu_J: local sweeps near Dirichlet/Neumann junctions after every
+                                relaxation on every level (0: the paper's smoother alone) */
+    double junction_radius;  /* R_J: zone = unknowns within R_J h of a ghost whose 3^d
+                                neighbourhood holds a ghost of the other boundary type */
+} gcmg_params;
+
+/* Per-solve report.  rel[m] = ||r^(m)||_inf / ||r^(0)||_inf for m = 0..cycles
+ * (max 256 kept), over Omega_h u Gamma_h, in FP64; the ratio of consecutive
+ * entries is the convergence factor rho^(m) of Sec. 3. */
+typedef struct {
+    int cycles;
+    int converged;
+    double rel_residual;
+    double r0_norm;
+    double rel[257];
+} gcmg_stats;
+
+/* Fills p with the defaults above for (dim, n, n_coarse). */
+gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse);
+
+/* Builds the hierarchy from the fine level set phi_dev (device, n^d doubles):
+ * classification, ghost equations, bands and extension lists of every level
+ * (coarse levels use phi at their nodes; coarse operators are rediscretised,
+ * Sec. 1.3 Remark 3), and the coarsest dense inverse with all ghosts
+ * Dirichlet until gcmg_set_bc_types is called for that level.  stream is a
+ * cudaStream_t (NULL: default).  On failure *out is NULL unless a context
+ * exists to read the message from; destroy it with gcmg_destroy. */
+gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *stream, gcmg_ctx **out);
+
+void gcmg_destroy(gcmg_ctx *ctx);
+const char *gcmg_last_error(const gcmg_ctx *ctx);
+
+int gcmg_num_levels(const gcmg_ctx *ctx);
+int gcmg_level_n(const gcmg_ctx *ctx, int level);
+
+/* Number of ghost points of a level, and the number of unknowns
+ * |Omega_h| + |Gamma_h| (the unit of the throughput metric). */
+gcmg_status gcmg_num_ghosts(const gcmg_ctx *ctx, int level, int64_t *count);
+gcmg_status gcmg_num_unknowns(const gcmg_ctx *ctx, int level, int64_t *count);
+
+/* Ghost geometry of a level (host outputs, any may be NULL):
+ * node_host[count]  linear node index of each ghost G,
+ * B_host[count*dim] closest boundary point B (Eq. clpt),
+ * nu_host[count*dim] discrete outward normal at B used by the Neumann row,
+ * case_host[count]  stencil: 0 quadratic 3^d, 1 linear 2^d, 2 corner, 3 two-point. */
+gcmg_status gcmg_ghost_geometry(const gcmg_ctx *ctx, int level, int64_t *node_host, double *B_host,
+                                double *nu_host, uint8_t *case_host);
+
+/* Full ghost equations of a level for inspection (host outputs, any may be
+ * NULL): stencil nodes stn_host[count*27] and Dirichlet / Neumann weights
+ * wD_host, wN_host[count*27] (unused slots: node = G, weight 0). */
+gcmg_status gcmg_ghost_equations(const gcmg_ctx *ctx, int level, int64_t *stn_host, double *wD_host,
+                                 double *wN_host);
+
+/* Node types of a level (host, n^d bytes): 0 outside, 1 inside (Omega_h),
+ * 2 ghost (Gamma_h); bit 2 (value 4) marks inside nodes of the extra-sweep
+ * band (distance -phi/|grad phi| <= delta, Sec. 3.2). */
+gcmg_status gcmg_node_types(const gcmg_ctx *ctx, int level, uint8_t *types_host);
+
+/* Junction zone of a level under its current boundary types (host, n^d
+ * bytes): 1 for the unknowns that the junction sweeps relax, else 0. */
+gcmg_status gcmg_junction_zone(const gcmg_ctx *ctx, int level, uint8_t *mask_host);
+
+/* Boundary type per ghost of a level (host, count bytes): 0 Dirichlet, 1
+ * Neumann -- whether the ghost's B lies on Gamma_D or Gamma_N.  Must be given
+ * for every level whose ghosts are not all Dirichlet; sets the relaxation
+ * coefficient mu dt of each ghost and, for the coarsest level, refactors the
+ * dense inverse. */
+gcmg_status gcmg_set_bc_types(gcmg_ctx *ctx, int level, const uint8_t *types_host);
+
+/* Right-hand side: f_dev (device, n^d doubles; values at inside nodes are
+ * used) and g_dev (device, one double per fine ghost: g_D(B) or g_N(B)). */
+gcmg_status gcmg_set_rhs(gcmg_ctx *ctx, const double *f_dev, const double *g_dev);
+
+/* Multigrid solve: u_dev (device, n^d doubles) holds the initial guess on
+ * entry and the solution on exit (0 off Omega_h u Gamma_h).  Stops at
+ * rel <= rtol or max_cycles; returns GCMG_E_NOCONV if not converged.  stats
+ * may be NULL. */
+gcmg_status gcmg_solve(gcmg_ctx *ctx, double *u_dev, gcmg_stats *stats);
+
+/* Same solve with host buffers: copies f_host (n^d), g_host (fine ghosts) to
+ * the device, solves from u = 0 and copies the solution to u_host (n^d). */
+gcmg_status gcmg_solve_host(gcmg_ctx *ctx, const double *f_host, const double *g_host, double *u_host,
+                            gcmg_stats *stats);
+
+/* ---- single steps of the cycle on caller buffers, for tests and tools.
+ * Each works on level `level` of the hierarchy, in FP64, on device grid
+ * arrays of that level's size (n_l^d doubles) and per-ghost arrays. */
+
+/* Defect (TGCS step 3): r = f + Lap_h u on Omega_h, r = g - L_h u on Gamma_h,
+ * 0 elsewhere; *norm = ||r||_inf over Omega_h u Gamma_h (may be NULL). */
+gcmg_status gcmg_defect(gcmg_ctx *ctx, int level, const double *u_dev, const double *f_dev,
+                        const double *g_dev, double *r_dev, double *norm);
+
+/* One relaxation R_h in place: red-black Gauss-Seidel on Omega_h (red =
+ * even index sum first), then a simultaneous (Jacobi) update of all ghosts
+ * (Eqs. jac2d, dir2d, neu2d); with_extra adds the lambda band sweeps of
+ * Sec. 3.2. */
+gcmg_status gcmg_relax(gcmg_ctx *ctx, int level, double *u_dev, const double *f_dev, const double *g_dev,
+                       int with_extra);
+
+/* Defect extension along normals (Sec. 2.6) in place on r_dev (level grid);
+ * writes the extension nodes only. */
+gcmg_status gcmg_extend(gcmg_ctx *ctx, int level, double *r_dev);
+
+/* Composite restriction (Sec. 2.5) of the fine grid function r_dev (level
+ * `level`) to level + 1: fc_dev (coarse grid; inside nodes written, others 0)
+ * and gc_dev (one value per coarse ghost). */
+gcmg_status gcmg_restrict(gcmg_ctx *ctx, int level, const double *r_dev, double *fc_dev, double *gc_dev);
+
+/* Interpolation (Sec. 2.6) of ec_dev (level + 1 grid) to level `level`:
+ * out_dev = I e on Omega_h u Gamma_h, 0 elsewhere. */
+gcmg_status gcmg_prolong(gcmg_ctx *ctx, int level, const double *ec_dev, double *out_dev);
+
+/* ---- measurement */
+
+/* Kernel classes whose fine-level launches can be timed. */
+enum {
+    GCMG_KERNEL_SMOOTH = 0,   /* red-black interior half-sweep (Eq. jac2d) */
+    GCMG_KERNEL_DEFECT = 1,   /* defect (TGCS step 3) */
+    GCMG_KERNEL_PROLONG = 2,  /* interpolation and correction (Sec. 2.6) */
+    GCMG_KERNEL_RESTRICT = 3  /* composite restriction (Sec. 2.5) */
+};
+
+/* With kind >= 0, later solves bracket every fine-level launch of that
+ * kernel class with CUDA events on the context's stream (kind = -1: off).
+ * gcmg_kernel_timing synchronises the stream and returns the number of timed
+ * launches and their summed device time since the last call or enable. */
+gcmg_status gcmg_set_kernel_timing(gcmg_ctx *ctx, int kind);
+gcmg_status gcmg_kernel_timing(gcmg_ctx *ctx, int64_t *launches, double *total_ms);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t gcmg_launch_counter(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCMG_H */

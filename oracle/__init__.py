@@ -64,6 +64,7 @@ def lib():
         L.orc_set_rhs.argtypes = [vp, vp, vp]
         L.orc_get_types.argtypes = [vp, C.c_int, vp]
         L.orc_get_band.argtypes = [vp, C.c_int, vp]
+        L.orc_get_jzone.argtypes = [vp, C.c_int, vp]
         L.orc_get_ghosts.argtypes = [vp, C.c_int] + [vp] * 10
         L.orc_get_ext.argtypes = [vp, C.c_int, vp, vp, vp, vp]
         L.orc_defect.restype = dbl
@@ -139,6 +140,11 @@ class Oracle:
     def band(self, l):
         out = np.empty(self.shape(l), np.uint8)
         lib().orc_get_band(self._h, l, _p(out))
+        return out
+
+    def junction_zone(self, l):
+        out = np.empty(self.shape(l), np.uint8)
+        lib().orc_get_jzone(self._h, l, _p(out))
         return out
 
     def ghosts(self, l):

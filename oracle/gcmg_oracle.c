@@ -1118,6 +1118,12 @@ void orc_get_types(void *h, int l, uint8_t *out) {
     memcpy(out, L->type, (size_t)L->nn);
 }
 
+void orc_get_jzone(void *h, int l, uint8_t *out) {
+    Level *L = &((Oracle *)h)->L[l];
+    if (L->jzone) memcpy(out, L->jzone, (size_t)L->nn);
+    else memset(out, 0, (size_t)L->nn);
+}
+
 void orc_get_band(void *h, int l, uint8_t *out) {
     Level *L = &((Oracle *)h)->L[l];
     memcpy(out, L->band, (size_t)L->nn);
@@ -1183,7 +1189,8 @@ void orc_prolong(void *h, int l, const double *e, double *out) {
     for (int64_t P = 0; P < F->nn; P++) out[P] = is_unknown(F, P) ? prolong_at(F, C, P, e) : 0.0;
 }
 
-/* One relaxation (base sweep + extra sweeps) of u in place at level l */
+/* One relaxation of u in place at level l: the base sweep, then (with_extra)
+ * the lambda band sweeps and the junction sweeps */
 void orc_relax(void *h, int l, double *u, const double *f, const double *g, int with_extra) {
     Oracle *O = (Oracle *)h;
     Level *L = &O->L[l];
@@ -1191,7 +1198,11 @@ void orc_relax(void *h, int l, double *u, const double *f, const double *g, int 
     for (int64_t i = 0; i < L->nn; i++) L->f[i] = (L->type[i] == T_INT) ? f[i] : 0.0;
     memcpy(L->g, g, sizeof(double) * (size_t)L->ng);
     base_relax(O, L);
-    if (with_extra) extra_sweeps(O, L);
+    if (with_extra) {
+        extra_sweeps(O, L);
+        if (O->p.junction_sweeps && L->jzone)
+            for (int m = 0; m < O->p.junction_sweeps; m++) zone_sweep(L);
+    }
     memcpy(u, L->u, sizeof(double) * (size_t)L->nn);
 }
 

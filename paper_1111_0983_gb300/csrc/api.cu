@@ -1,0 +1,737 @@
+// C ABI of libgcmg (include/gcmg.h): context lifetime, hierarchy upload,
+// cycle schedule and the solve loops.  The per-level arithmetic lives in
+// kernels.cu; geometry construction in setup.cpp.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gcmg_internal.h"
+#include "kernels.h"
+
+using namespace gcmg;
+
+struct gcmg_ctx {
+    gcmg_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<HostLevel> H;
+    std::vector<DevGeom> G;
+    std::vector<DevData<double>> D64;
+    std::vector<DevData<float>> D32;
+    bool rhs_set = false;
+    unsigned long long *d_norm = nullptr;   // two slots: defect norm, rhs norm
+    unsigned long long *h_norm = nullptr;   // pinned
+    // event timing of one fine-level kernel class during solves
+    int timing_kind = -1;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+namespace {
+
+struct CudaFail {
+    cudaError_t e;
+    const char *what;
+};
+
+inline void ck(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw CudaFail{e, what};
+}
+
+template <typename T>
+T *dalloc(gcmg_ctx *c, size_t count) {
+    if (count == 0) count = 1;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw std::bad_alloc();
+    }
+    c->allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+
+template <typename T>
+T *upload(gcmg_ctx *c, const T *host, size_t count) {
+    T *d = dalloc<T>(c, count);
+    if (count) ck(cudaMemcpyAsync(d, host, count * sizeof(T), cudaMemcpyHostToDevice, c->stream), "upload");
+    return d;
+}
+
+int kslots(int dim) { return dim == 2 ? 9 : 27; }
+
+// slot-major copies of per-ghost / per-extension-node arrays
+template <typename S, typename T>
+std::vector<T> slot_major(const std::vector<S> &src, int64_t count, int width, int used) {
+    std::vector<T> out((size_t)count * used);
+    for (int64_t i = 0; i < count; i++)
+        for (int k = 0; k < used; k++) out[(size_t)k * count + i] = (T)src[(size_t)i * width + k];
+    return out;
+}
+
+template <typename T>
+void upload_ghost_data(gcmg_ctx *c, int l, DevData<T> &D, bool alloc) {
+    const HostLevel &L = c->H[l];
+    const int64_t ng = L.ng();
+    const int K = kslots(L.dim);
+    std::vector<double> w((size_t)ng * KMAX);
+    std::vector<T> coef(ng);
+    const double cN = c->p.c_neumann_factor * 2.0 * L.h / (3.0 * std::sqrt((double)L.dim));
+    for (int64_t q = 0; q < ng; q++) {
+        const double *src = (L.bc[q] ? L.wN.data() : L.wD.data()) + q * KMAX;
+        std::memcpy(&w[q * KMAX], src, sizeof(double) * KMAX);
+        coef[q] = (T)(L.bc[q] ? cN : c->p.c_dirichlet);
+    }
+    std::vector<T> ws = slot_major<double, T>(w, ng, KMAX, K);
+    if (alloc) {
+        D.gw = dalloc<T>(c, ws.size());
+        D.gc = dalloc<T>(c, ng);
+    }
+    ck(cudaMemcpyAsync(D.gw, ws.data(), ws.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream), "gw");
+    ck(cudaMemcpyAsync(D.gc, coef.data(), coef.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream), "gc");
+    if (l + 1 == (int)c->H.size()) {
+        std::vector<T> A(L.Ainv.begin(), L.Ainv.end());
+        if (alloc) D.Ainv = dalloc<T>(c, A.size());
+        ck(cudaMemcpyAsync(D.Ainv, A.data(), A.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream), "Ainv");
+    }
+    // synchronous: the staging vectors die at return
+    ck(cudaStreamSynchronize(c->stream), "sync");
+}
+
+template <typename T>
+void alloc_data(gcmg_ctx *c, int l, DevData<T> &D, bool grids) {
+    const HostLevel &L = c->H[l];
+    upload_ghost_data<T>(c, l, D, true);
+    D.gg = dalloc<T>(c, L.ng());
+    D.gtmp = dalloc<T>(c, L.ng());
+    const int64_t ne = (int64_t)L.ext_node.size();
+    std::vector<T> ew = slot_major<double, T>(L.ext_w, ne, EMAX, EMAX);
+    D.ew = upload<T>(c, ew.data(), ew.size());
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    if (grids) {
+        D.u = dalloc<T>(c, L.nn);
+        D.f = dalloc<T>(c, L.nn);
+        D.r = dalloc<T>(c, L.nn);
+        ck(cudaMemsetAsync(D.u, 0, L.nn * sizeof(T), c->stream), "memset");
+        ck(cudaMemsetAsync(D.f, 0, L.nn * sizeof(T), c->stream), "memset");
+        ck(cudaMemsetAsync(D.r, 0, L.nn * sizeof(T), c->stream), "memset");
+    }
+}
+
+void upload_geometry(gcmg_ctx *c, int l) {
+    const HostLevel &L = c->H[l];
+    DevGeom g;
+    g.dim = L.dim;
+    g.n = L.n;
+    g.nn = L.nn;
+    g.ng = (int)L.ng();
+    g.nred = (int)L.band_red.size();
+    g.nblack = (int)L.band_black.size();
+    g.ne = (int)L.ext_node.size();
+    g.type = upload<uint8_t>(c, L.type.data(), L.type.size());
+    g.gnode = upload<int32_t>(c, L.ghost_node.data(), L.ghost_node.size());
+    std::vector<int32_t> stn = slot_major<int32_t, int32_t>(L.stn, g.ng, KMAX, kslots(L.dim));
+    g.gstn = upload<int32_t>(c, stn.data(), stn.size());
+    g.red = upload<int32_t>(c, L.band_red.data(), L.band_red.size());
+    g.black = upload<int32_t>(c, L.band_black.data(), L.band_black.size());
+    g.enode = upload<int32_t>(c, L.ext_node.data(), L.ext_node.size());
+    g.ecnt = upload<uint8_t>(c, L.ext_cnt.data(), L.ext_cnt.size());
+    std::vector<int32_t> es = slot_major<int32_t, int32_t>(L.ext_src, g.ne, EMAX, EMAX);
+    g.esrc = upload<int32_t>(c, es.data(), es.size());
+    g.wave = L.ext_wave;
+    if (l + 1 == (int)c->H.size()) {
+        g.nunk = (int)L.unk_node.size();
+        g.unk_node = upload<int32_t>(c, L.unk_node.data(), L.unk_node.size());
+        g.unk_ghost = upload<int32_t>(c, L.unk_ghost.data(), L.unk_ghost.size());
+    }
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    c->G.push_back(g);
+}
+
+void free_tracked(gcmg_ctx *c, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); i++)
+        if (c->allocs[i] == p) {
+            cudaFree(p);
+            c->allocs.erase(c->allocs.begin() + i);
+            return;
+        }
+}
+
+// (re)uploads the junction-zone components of level l
+void upload_junction(gcmg_ctx *c, int l) {
+    const HostLevel::Junction &J = c->H[l].junction;
+    auto &z = c->G[l].jz;
+    int32_t **arrs[] = {&z.node_off, &z.zone_cnt, &z.lnode, &z.int_off, &z.red_cnt, &z.int_glob,
+                        &z.int_me, &z.int_nb, &z.gh_off, &z.gh_me, &z.gh_q, &z.gh_stn,
+                        &z.zred, &z.zblack, &z.zghost};
+    for (int32_t **a : arrs) { free_tracked(c, *a); *a = nullptr; }
+    z.ncomp = J.ncomp();
+    z.max_nodes = J.max_nodes;
+    z.max_int = J.max_int;
+    z.max_gh = J.max_gh;
+    if (z.ncomp == 0) return;
+    z.node_off = upload<int32_t>(c, J.node_off.data(), J.node_off.size());
+    z.zone_cnt = upload<int32_t>(c, J.zone_cnt.data(), J.zone_cnt.size());
+    z.lnode = upload<int32_t>(c, J.lnode.data(), J.lnode.size());
+    z.int_off = upload<int32_t>(c, J.int_off.data(), J.int_off.size());
+    z.red_cnt = upload<int32_t>(c, J.red_cnt.data(), J.red_cnt.size());
+    z.int_glob = upload<int32_t>(c, J.int_glob.data(), J.int_glob.size());
+    z.int_me = upload<int32_t>(c, J.int_me.data(), J.int_me.size());
+    z.int_nb = upload<int32_t>(c, J.int_nb.data(), J.int_nb.size());
+    z.gh_off = upload<int32_t>(c, J.gh_off.data(), J.gh_off.size());
+    z.gh_me = upload<int32_t>(c, J.gh_me.data(), J.gh_me.size());
+    z.gh_q = upload<int32_t>(c, J.gh_q.data(), J.gh_q.size());
+    z.gh_stn = upload<int32_t>(c, J.gh_stn.data(), J.gh_stn.size());
+    z.nzred = (int)J.zred.size();
+    z.nzblack = (int)J.zblack.size();
+    z.nzghost = (int)J.zghost.size();
+    z.zred = upload<int32_t>(c, J.zred.data(), J.zred.size());
+    z.zblack = upload<int32_t>(c, J.zblack.data(), J.zblack.size());
+    z.zghost = upload<int32_t>(c, J.zghost.data(), J.zghost.size());
+    ck(cudaStreamSynchronize(c->stream), "sync");
+}
+
+template <typename T>
+LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
+    const HostLevel &L = c->H[l];
+    const DevGeom &g = c->G[l];
+    LevelView<T> v;
+    v.n = L.n;
+    v.nn = L.nn;
+    v.s0 = L.stride[0];
+    v.s1 = L.stride[1];
+    v.s2 = L.dim == 3 ? L.stride[2] : 0;
+    v.h2 = (T)(L.h * L.h);
+    v.inv_h2 = (T)(1.0 / (L.h * L.h));
+    v.type = g.type;
+    v.u = D.u;
+    v.f = D.f;
+    v.r = D.r;
+    v.ng = g.ng;
+    v.gnode = g.gnode;
+    v.gstn = g.gstn;
+    v.gw = D.gw;
+    v.gc = D.gc;
+    v.gg = D.gg;
+    v.gtmp = D.gtmp;
+    return v;
+}
+
+template <typename T>
+std::vector<DevData<T>> &data(gcmg_ctx *c);
+template <>
+std::vector<DevData<double>> &data<double>(gcmg_ctx *c) { return c->D64; }
+template <>
+std::vector<DevData<float>> &data<float>(gcmg_ctx *c) { return c->D32; }
+
+// events around fine-level launches of the kernel class being timed
+void timer_mark(gcmg_ctx *c, int kind, int l) {
+    if (c->timing_kind != kind || l != 0) return;
+    if (c->events_used == c->events.size()) {
+        if (c->events.size() >= 65536) return;
+        cudaEvent_t e;
+        ck(cudaEventCreate(&e), "cudaEventCreate");
+        c->events.push_back(e);
+    }
+    ck(cudaEventRecord(c->events[c->events_used++], c->stream), "cudaEventRecord");
+}
+
+template <typename T>
+JunctionView<T> jview(const gcmg_ctx *c, int l, const LevelView<T> &v) {
+    const auto &z = c->G[l].jz;
+    JunctionView<T> J;
+    J.ncomp = z.ncomp;
+    J.max_nodes = z.max_nodes;
+    J.max_int = z.max_int;
+    J.max_gh = z.max_gh;
+    J.ng = v.ng;
+    J.node_off = z.node_off; J.zone_cnt = z.zone_cnt; J.lnode = z.lnode;
+    J.int_off = z.int_off; J.red_cnt = z.red_cnt; J.int_glob = z.int_glob; J.int_me = z.int_me; J.int_nb = z.int_nb;
+    J.gh_off = z.gh_off; J.gh_me = z.gh_me; J.gh_q = z.gh_q; J.gh_stn = z.gh_stn;
+    J.u = v.u; J.f = v.f; J.gg = v.gg; J.gc = v.gc; J.gw = v.gw;
+    J.h2 = v.h2;
+    return J;
+}
+
+// one relaxation R_h followed by the lambda extra sweeps (Sec. 2.4, 3.2) and
+// the junction sweeps
+template <typename T>
+void relax(gcmg_ctx *c, const LevelView<T> &v, int l, bool extra) {
+    const int dim = c->p.dim;
+    const DevGeom &g = c->G[l];
+    for (int colour = 0; colour < 2; colour++) {
+        timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+        launch_rb<T>(v, dim, colour, c->stream);
+        timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+    }
+    launch_ghost_relax<T>(v, dim, c->stream);
+    if (!extra) return;
+    for (int k = 0; k < c->p.lambda; k++) {
+        launch_rb_list<T>(v, dim, g.red, g.nred, c->stream);
+        launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
+        launch_ghost_relax<T>(v, dim, c->stream);
+    }
+    if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
+        if (g.jz.in_smem) {
+            launch_junction<T>(jview<T>(c, l, v), dim, c->p.junction_sweeps, c->stream);
+        } else {
+            for (int k = 0; k < c->p.junction_sweeps; k++) {
+                launch_rb_list<T>(v, dim, g.jz.zred, g.jz.nzred, c->stream);
+                launch_rb_list<T>(v, dim, g.jz.zblack, g.jz.nzblack, c->stream);
+                launch_ghost_relax_list<T>(v, dim, g.jz.zghost, g.jz.nzghost, c->stream);
+            }
+        }
+    }
+}
+
+// checks the junction components of level l fit in shared memory
+void check_junction_fits(gcmg_ctx *c, int l) {
+    if (c->p.junction_sweeps <= 0 || c->G[l].jz.ncomp == 0) return;
+    LevelView<double> v = view<double>(c, l, c->D64[l]);
+    const size_t need = junction_smem_bytes<double>(jview<double>(c, l, v), c->p.dim);
+    int dev_max = 0;
+    ck(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
+    c->G[l].jz.in_smem = need <= (size_t)dev_max;
+    if (!c->G[l].jz.in_smem) return;    // relaxed from global memory instead
+    // the attribute is per kernel: allow the device maximum once for all levels
+    junction_prepare<double>(c->p.dim, (size_t)dev_max);
+    junction_prepare<float>(c->p.dim, (size_t)dev_max);
+}
+
+// TGCS (Sec. 2.4) applied recursively: V (gamma = 1) or W (gamma = 2) cycle
+template <typename T>
+void cycle(gcmg_ctx *c, int l) {
+    std::vector<DevData<T>> &D = data<T>(c);
+    const int last = (int)c->H.size() - 1;
+    const LevelView<T> v = view<T>(c, l, D[l]);
+    const int dim = c->p.dim;
+    if (l == last) {
+        ck(cudaMemsetAsync(D[l].u, 0, c->H[l].nn * sizeof(T), c->stream), "memset");
+        launch_coarse_solve<T>(v, c->G[l], D[l].Ainv, c->stream);
+        return;
+    }
+    for (int k = 0; k < c->p.nu1; k++) relax<T>(c, v, l, true);
+    timer_mark(c, GCMG_KERNEL_DEFECT, l);
+    launch_defect<T>(v, dim, false, nullptr, c->stream);
+    timer_mark(c, GCMG_KERNEL_DEFECT, l);
+    launch_extend<T>(D[l].r, c->G[l], D[l].ew, c->stream);
+    const LevelView<T> vc = view<T>(c, l + 1, D[l + 1]);
+    timer_mark(c, GCMG_KERNEL_RESTRICT, l);
+    launch_restrict<T>(v, vc, dim, D[l + 1].f, D[l + 1].gg, c->stream);
+    timer_mark(c, GCMG_KERNEL_RESTRICT, l);
+    ck(cudaMemsetAsync(D[l + 1].u, 0, c->H[l + 1].nn * sizeof(T), c->stream), "memset");
+    const int gam = (l + 1 == last) ? 1 : c->p.gamma;
+    for (int k = 0; k < gam; k++) cycle<T>(c, l + 1);
+    timer_mark(c, GCMG_KERNEL_PROLONG, l);
+    launch_prolong<T>(v, vc, dim, D[l + 1].u, D[l].u, true, c->stream);
+    timer_mark(c, GCMG_KERNEL_PROLONG, l);
+    for (int k = 0; k < c->p.nu2; k++) relax<T>(c, v, l, true);
+}
+
+__global__ void k_rhs_norm(const uint8_t *type, const double *f, int64_t nn, const double *g, int ng,
+                           unsigned long long *bits) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < nn && (type[i] & NODE_KIND) == NODE_IN) v = fabs(f[i]);
+    if (i < ng) v = fmax(v, fabs(g[i]));
+    if (v != v) v = __longlong_as_double(0x7ff0000000000000ull);
+    if (v > 0.0) atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+}
+
+double read_norm(gcmg_ctx *c) {
+    ck(cudaMemcpyAsync(c->h_norm, c->d_norm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
+       "norm");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    double v;
+    std::memcpy(&v, c->h_norm, sizeof(double));
+    return v;
+}
+
+// FP64 defect of level 0 and its norm
+double fine_defect_norm(gcmg_ctx *c) {
+    ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
+    launch_defect<double>(view<double>(c, 0, c->D64[0]), c->p.dim, false, c->d_norm, c->stream);
+    return read_norm(c);
+}
+
+gcmg_status fail(gcmg_ctx *c, gcmg_status s, const std::string &m) {
+    if (c) c->err = m;
+    return s;
+}
+
+#define GCMG_GUARD(ctx, ...)                                                                  \
+    try {                                                                                     \
+        __VA_ARGS__                                                                           \
+    } catch (const CudaFail &f) {                                                             \
+        cudaGetLastError();                                                                   \
+        return fail(ctx, GCMG_E_CUDA, std::string(f.what) + ": " + cudaGetErrorString(f.e));  \
+    } catch (const GeomError &g) {                                                            \
+        return fail(ctx, GCMG_E_GEOM, g.msg);                                                 \
+    } catch (const std::bad_alloc &) {                                                        \
+        return fail(ctx, GCMG_E_OOM, "allocation failed");                                    \
+    } catch (const std::exception &e) {                                                       \
+        return fail(ctx, GCMG_E_ARG, e.what());                                               \
+    }
+
+bool valid_level(const gcmg_ctx *c, int l) { return c && l >= 0 && l < (int)c->H.size(); }
+
+void check_launch() { ck(cudaGetLastError(), "kernel launch"); }
+
+}  // namespace
+
+extern "C" {
+
+gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
+    if (!p) return GCMG_E_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = dim;
+    p->n = n;
+    p->n_coarse = n_coarse;
+    p->nu1 = 2;
+    p->nu2 = 1;
+    p->lambda = 5;
+    p->gamma = 1;
+    p->delta_over_h = 3.0;
+    p->c_dirichlet = 0.9;
+    p->c_neumann_factor = 0.9;
+    p->precision = 0;
+    p->max_cycles = 100;
+    p->rtol = 1e-10;
+    p->junction_sweeps = 40;
+    p->junction_radius = 12.0;
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *stream, gcmg_ctx **out) {
+    if (!out) return GCMG_E_ARG;
+    *out = nullptr;
+    if (!p || !phi_dev) return GCMG_E_ARG;
+    if (p->dim < 2 || p->dim > 3 || p->n_coarse < 3 || p->n <= p->n_coarse) return GCMG_E_ARG;
+    {
+        int m = p->n;
+        while (m > p->n_coarse) {
+            if ((m - 1) % 2) return GCMG_E_ARG;
+            m = (m - 1) / 2 + 1;
+        }
+        if (m != p->n_coarse) return GCMG_E_ARG;
+        const double nn = std::pow((double)p->n, p->dim);
+        if (nn >= 2147483647.0) return GCMG_E_ARG;   // 32-bit node indices
+        if (p->gamma < 1 || p->gamma > 2 || p->nu1 < 0 || p->nu2 < 0 || p->lambda < 0) return GCMG_E_ARG;
+        if (p->precision < 0 || p->precision > 1 || p->max_cycles < 1 || p->max_cycles > 256) return GCMG_E_ARG;
+        if (p->junction_sweeps < 0 || p->junction_radius < 0.0 || p->junction_radius > 64.0) return GCMG_E_ARG;
+    }
+    gcmg_ctx *c = new (std::nothrow) gcmg_ctx;
+    if (!c) return GCMG_E_OOM;
+    *out = c;
+    c->p = *p;
+    c->stream = (cudaStream_t)stream;
+    GCMG_GUARD(c, {
+        ck(cudaGetDevice(&c->device), "cudaGetDevice");
+        int64_t nn = 1;
+        for (int a = 0; a < p->dim; a++) nn *= p->n;
+        std::vector<double> phi(nn);
+        ck(cudaMemcpyAsync(phi.data(), phi_dev, nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "phi");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        build_hierarchy(p->dim, p->n, p->n_coarse, phi.data(), p->delta_over_h, c->H);
+        const int nl = (int)c->H.size();
+        for (int l = 0; l < nl; l++) upload_geometry(c, l);
+        c->D64.resize(nl);
+        for (int l = 0; l < nl; l++) alloc_data<double>(c, l, c->D64[l], p->precision == 0 || l == 0);
+        if (p->precision == 1) {
+            c->D32.resize(nl);
+            for (int l = 0; l < nl; l++) alloc_data<float>(c, l, c->D32[l], true);
+        }
+        c->d_norm = dalloc<unsigned long long>(c, 2);
+        ck(cudaMallocHost((void **)&c->h_norm, 2 * sizeof(unsigned long long)), "cudaMallocHost");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
+void gcmg_destroy(gcmg_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->h_norm) cudaFreeHost(c->h_norm);
+    delete c;
+}
+
+const char *gcmg_last_error(const gcmg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int gcmg_num_levels(const gcmg_ctx *c) { return c ? (int)c->H.size() : 0; }
+
+int gcmg_level_n(const gcmg_ctx *c, int l) { return valid_level(c, l) ? c->H[l].n : 0; }
+
+gcmg_status gcmg_num_ghosts(const gcmg_ctx *c, int l, int64_t *count) {
+    if (!valid_level(c, l) || !count) return GCMG_E_ARG;
+    *count = c->H[l].ng();
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_num_unknowns(const gcmg_ctx *c, int l, int64_t *count) {
+    if (!valid_level(c, l) || !count) return GCMG_E_ARG;
+    *count = c->H[l].n_in + c->H[l].ng();
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_ghost_geometry(const gcmg_ctx *c, int l, int64_t *node, double *B, double *nu, uint8_t *scase) {
+    if (!valid_level(c, l)) return GCMG_E_ARG;
+    const HostLevel &L = c->H[l];
+    const int64_t ng = L.ng();
+    for (int64_t q = 0; q < ng; q++) {
+        if (node) node[q] = L.ghost_node[q];
+        if (scase) scase[q] = L.scase[q];
+    }
+    if (B) std::memcpy(B, L.B.data(), sizeof(double) * ng * L.dim);
+    if (nu) std::memcpy(nu, L.nu.data(), sizeof(double) * ng * L.dim);
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_ghost_equations(const gcmg_ctx *c, int l, int64_t *stn, double *wD, double *wN) {
+    if (!valid_level(c, l)) return GCMG_E_ARG;
+    const HostLevel &L = c->H[l];
+    const int64_t total = L.ng() * KMAX;
+    for (int64_t i = 0; i < total; i++) {
+        if (stn) stn[i] = L.stn[i];
+        if (wD) wD[i] = L.wD[i];
+        if (wN) wN[i] = L.wN[i];
+    }
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_node_types(const gcmg_ctx *c, int l, uint8_t *types) {
+    if (!valid_level(c, l) || !types) return GCMG_E_ARG;
+    std::memcpy(types, c->H[l].type.data(), c->H[l].nn);
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_set_bc_types(gcmg_ctx *c, int l, const uint8_t *types) {
+    if (!valid_level(c, l) || !types) return fail(c, GCMG_E_ARG, "bad level or pointer");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        HostLevel &L = c->H[l];
+        for (int64_t q = 0; q < L.ng(); q++) L.bc[q] = types[q] ? 1 : 0;
+        if (l + 1 == (int)c->H.size()) build_coarse_inverse(L);
+        build_junction(L, c->p.junction_radius);
+        upload_junction(c, l);
+        check_junction_fits(c, l);
+        upload_ghost_data<double>(c, l, c->D64[l], false);
+        if (!c->D32.empty()) upload_ghost_data<float>(c, l, c->D32[l], false);
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_set_rhs(gcmg_ctx *c, const double *f_dev, const double *g_dev) {
+    if (!c || !f_dev || (!g_dev && c->H[0].ng() > 0)) return fail(c, GCMG_E_ARG, "null pointer");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        const HostLevel &L = c->H[0];
+        ck(cudaMemcpyAsync(c->D64[0].f, f_dev, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "f");
+        if (L.ng() > 0)
+            ck(cudaMemcpyAsync(c->D64[0].gg, g_dev, L.ng() * sizeof(double), cudaMemcpyDeviceToDevice, c->stream),
+               "g");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        c->rhs_set = true;
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
+    if (!c || !u_dev) return fail(c, GCMG_E_ARG, "null pointer");
+    if (!c->rhs_set) return fail(c, GCMG_E_STATE, "gcmg_set_rhs has not been called");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        const HostLevel &L0 = c->H[0];
+        const DevGeom &g0 = c->G[0];
+        double *own_u = c->D64[0].u;
+        c->D64[0].u = u_dev;   // solve in place in the caller's array (same layout)
+        struct Restore {
+            gcmg_ctx *c;
+            double *u;
+            ~Restore() { c->D64[0].u = u; }
+        } restore{c, own_u};
+        launch_mask_unknowns<double>(g0.type, u_dev, L0.nn, c->stream);
+        // ||r0|| = ||(f, g)||
+        ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
+        {
+            const int64_t cnt = std::max<int64_t>(L0.nn, L0.ng());
+            k_rhs_norm<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn,
+                                                                             c->D64[0].gg, g0.ng, c->d_norm);
+        }
+        check_launch();
+        const double r0 = read_norm(c);
+        gcmg_stats st;
+        std::memset(&st, 0, sizeof(st));
+        st.r0_norm = r0;
+        double rel = 0.0;
+        if (r0 > 0.0) rel = fine_defect_norm(c) / r0;
+        st.rel[0] = rel;
+        int m = 0;
+        bool ok = (r0 == 0.0) || rel <= c->p.rtol;
+        while (!ok && m < c->p.max_cycles) {
+            if (c->p.precision == 0) {
+                cycle<double>(c, 0);
+            } else {
+                DevData<float> &F0 = c->D32[0];
+                launch_defect_to_f32(g0, c->D64[0].r, F0.f, F0.gg, c->stream);
+                ck(cudaMemsetAsync(F0.u, 0, L0.nn * sizeof(float), c->stream), "memset");   // e = 0
+                cycle<float>(c, 0);
+                launch_add_correction(g0, u_dev, F0.u, c->stream);
+            }
+            check_launch();
+            m++;
+            rel = fine_defect_norm(c) / r0;
+            if (m <= 256) st.rel[m] = rel;
+            if (!(rel == rel) || std::isinf(rel)) break;
+            ok = rel <= c->p.rtol;
+        }
+        st.cycles = m;
+        st.converged = ok ? 1 : 0;
+        st.rel_residual = rel;
+        if (stats) *stats = st;
+        if (!ok) return fail(c, GCMG_E_NOCONV, "not converged");
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_solve_host(gcmg_ctx *c, const double *f_host, const double *g_host, double *u_host,
+                            gcmg_stats *stats) {
+    if (!c || !f_host || !u_host) return fail(c, GCMG_E_ARG, "null pointer");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        const HostLevel &L = c->H[0];
+        ck(cudaMemcpyAsync(c->D64[0].f, f_host, L.nn * sizeof(double), cudaMemcpyHostToDevice, c->stream), "f");
+        if (L.ng() > 0)
+            ck(cudaMemcpyAsync(c->D64[0].gg, g_host, L.ng() * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+               "g");
+        c->rhs_set = true;
+        double *u = c->D64[0].u;
+        ck(cudaMemsetAsync(u, 0, L.nn * sizeof(double), c->stream), "memset");
+        gcmg_status s = gcmg_solve(c, u, stats);
+        ck(cudaMemcpyAsync(u_host, u, L.nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "u");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return s;
+    })
+}
+
+// ------------------------------------------------------------ single steps
+gcmg_status gcmg_defect(gcmg_ctx *c, int l, const double *u, const double *f, const double *g, double *r,
+                        double *norm) {
+    if (!valid_level(c, l) || !u || !f || !r) return fail(c, GCMG_E_ARG, "bad argument");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        LevelView<double> v = view<double>(c, l, c->D64[l]);
+        v.u = const_cast<double *>(u);
+        v.f = f;
+        v.gg = g;
+        v.r = r;
+        ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
+        launch_defect<double>(v, c->p.dim, true, c->d_norm, c->stream);
+        check_launch();
+        const double nv = read_norm(c);
+        if (norm) *norm = nv;
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_relax(gcmg_ctx *c, int l, double *u, const double *f, const double *g, int with_extra) {
+    if (!valid_level(c, l) || !u || !f) return fail(c, GCMG_E_ARG, "bad argument");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        LevelView<double> v = view<double>(c, l, c->D64[l]);
+        v.u = u;
+        v.f = f;
+        v.gg = g;
+        relax<double>(c, v, l, with_extra != 0);
+        check_launch();
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_extend(gcmg_ctx *c, int l, double *r) {
+    if (!valid_level(c, l) || !r) return fail(c, GCMG_E_ARG, "bad argument");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        launch_extend<double>(r, c->G[l], c->D64[l].ew, c->stream);
+        check_launch();
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_restrict(gcmg_ctx *c, int l, const double *r, double *fc, double *gc) {
+    if (!valid_level(c, l + 1) || l < 0 || !r || !fc || (!gc && c->H[l + 1].ng() > 0))
+        return fail(c, GCMG_E_ARG, "bad argument");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        LevelView<double> v = view<double>(c, l, c->D64[l]);
+        v.r = const_cast<double *>(r);
+        LevelView<double> vc = view<double>(c, l + 1, c->D64[l + 1]);
+        launch_restrict<double>(v, vc, c->p.dim, fc, gc, c->stream);
+        check_launch();
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_prolong(gcmg_ctx *c, int l, const double *ec, double *out) {
+    if (!valid_level(c, l + 1) || l < 0 || !ec || !out) return fail(c, GCMG_E_ARG, "bad argument");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        LevelView<double> v = view<double>(c, l, c->D64[l]);
+        LevelView<double> vc = view<double>(c, l + 1, c->D64[l + 1]);
+        launch_prolong<double>(v, vc, c->p.dim, ec, out, false, c->stream);
+        check_launch();
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_set_kernel_timing(gcmg_ctx *c, int kind) {
+    if (!c || kind < -1 || kind > GCMG_KERNEL_RESTRICT) return fail(c, GCMG_E_ARG, "bad kernel class");
+    c->timing_kind = kind;
+    c->events_used = 0;
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_kernel_timing(gcmg_ctx *c, int64_t *launches, double *total_ms) {
+    if (!c || !launches || !total_ms) return fail(c, GCMG_E_ARG, "null pointer");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        double tot = 0.0;
+        for (size_t i = 0; i + 1 < c->events_used; i += 2) {
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, c->events[i], c->events[i + 1]), "cudaEventElapsedTime");
+            tot += ms;
+        }
+        *launches = (int64_t)(c->events_used / 2);
+        *total_ms = tot;
+        c->events_used = 0;
+        return GCMG_OK;
+    })
+}
+
+int64_t gcmg_launch_counter(void) { return (int64_t)g_launches.load(); }
+
+gcmg_status gcmg_junction_zone(const gcmg_ctx *c, int l, uint8_t *mask) {
+    if (!valid_level(c, l) || !mask) return GCMG_E_ARG;
+    const HostLevel &L = c->H[l];
+    std::memset(mask, 0, L.nn);
+    const auto &J = L.junction;
+    for (int k = 0; k < J.ncomp(); k++)
+        for (int i = J.node_off[k]; i < J.node_off[k] + J.zone_cnt[k]; i++) mask[J.lnode[i]] = 1;
+    return GCMG_OK;
+}
+
+}  // extern "C"

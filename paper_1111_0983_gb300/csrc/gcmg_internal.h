@@ -1,0 +1,147 @@
+// Internal declarations of libgcmg: host-side geometry of every level, the
+// device copies the kernels read, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gcmg.h"
+
+namespace gcmg {
+
+constexpr int KMAX = 27;   // ghost stencil slots (3^3)
+constexpr int EMAX = 6;    // extension sources (2 d)
+
+enum : uint8_t { NODE_OUT = 0, NODE_IN = 1, NODE_GHOST = 2, NODE_KIND = 3, NODE_BAND = 4 };
+enum : uint8_t { STENCIL_QUAD = 0, STENCIL_LIN = 1, STENCIL_CORNER = 2, STENCIL_AXIS = 3 };
+
+struct GeomError {
+    std::string msg;
+};
+
+// Geometry of one level, built on the host from phi (Sec. 2.2 - 2.6, 3.2).
+struct HostLevel {
+    int dim = 2, n = 0;
+    double h = 0;
+    int64_t nn = 0;
+    int64_t stride[3] = {0, 0, 0};
+    std::vector<double> phi;
+    std::vector<uint8_t> type;          // NODE_* (+ NODE_BAND)
+    int64_t n_in = 0;
+    // ghosts, increasing node index
+    std::vector<int32_t> ghost_node;
+    std::vector<double> B, nu;          // ng * dim
+    std::vector<uint8_t> scase;         // STENCIL_*
+    std::vector<int32_t> stn;           // ng * KMAX, per ghost
+    std::vector<double> wD, wN;         // ng * KMAX
+    std::vector<uint8_t> bc;            // 0 Dirichlet, 1 Neumann
+    // inside nodes of the extra-sweep band, split by colour
+    std::vector<int32_t> band_red, band_black;
+    // defect extension of this level (before restricting to the next coarser one)
+    std::vector<int32_t> ext_node;      // ordered by upwind wavefront
+    std::vector<uint8_t> ext_cnt;
+    std::vector<int32_t> ext_src;       // ne * EMAX
+    std::vector<double> ext_w;          // ne * EMAX
+    std::vector<int> ext_wave;          // wavefront offsets into ext_node (size nwave + 1)
+    // junction zone (depends on bc): independent components, each closed under
+    // the reads of its updates; local node lists hold the zone nodes first,
+    // then the halo nodes they read
+    struct Junction {
+        std::vector<int32_t> node_off{0}, zone_cnt, lnode;
+        std::vector<int32_t> int_off{0}, red_cnt, int_glob, int_me, int_nb;   // nb: 2 dim per entry
+        std::vector<int32_t> gh_off{0}, gh_me, gh_q, gh_stn;                  // stn: 3^dim per entry
+        std::vector<int32_t> zred, zblack, zghost;   // whole zone: inside nodes by colour, ghost numbers
+        int max_nodes = 0, max_int = 0, max_gh = 0;
+        int ncomp() const { return (int)zone_cnt.size(); }
+    } junction;
+    // coarsest level: unknowns (node, ghost number or -1) and dense inverse
+    std::vector<int32_t> unk_node, unk_ghost;
+    std::vector<double> Ainv;           // nunk * nunk, row major
+
+    int64_t ng() const { return (int64_t)ghost_node.size(); }
+};
+
+// Builds all levels (throws GeomError).  phi: fine grid, n^dim values.
+void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
+                     std::vector<HostLevel> &levels);
+// Dense inverse of the coarsest system with the level's current bc (throws GeomError).
+void build_coarse_inverse(HostLevel &L);
+// Junction zone of the level's current bc (radius in h).
+void build_junction(HostLevel &L, double radius);
+
+// --------------------------------------------------------------- device side
+// Integer geometry of a level on the device (shared by both precisions).
+struct DevGeom {
+    int dim = 2, n = 0;
+    int64_t nn = 0;
+    int ng = 0, nred = 0, nblack = 0, ne = 0, nunk = 0;
+    uint8_t *type = nullptr;
+    int32_t *gnode = nullptr;    // ng
+    int32_t *gstn = nullptr;     // KMAX * ng, slot major
+    int32_t *red = nullptr, *black = nullptr;
+    int32_t *enode = nullptr;    // ne
+    uint8_t *ecnt = nullptr;     // ne
+    int32_t *esrc = nullptr;     // EMAX * ne, slot major
+    int32_t *unk_node = nullptr, *unk_ghost = nullptr;
+    std::vector<int> wave;       // host copy of the wavefront offsets
+    // junction zone components (reallocated when the bc changes)
+    struct {
+        int ncomp = 0, max_nodes = 0, max_int = 0, max_gh = 0;
+        int32_t *node_off = nullptr, *zone_cnt = nullptr, *lnode = nullptr;
+        int32_t *int_off = nullptr, *red_cnt = nullptr, *int_glob = nullptr, *int_me = nullptr, *int_nb = nullptr;
+        int32_t *gh_off = nullptr, *gh_me = nullptr, *gh_q = nullptr, *gh_stn = nullptr;
+        int nzred = 0, nzblack = 0, nzghost = 0;
+        int32_t *zred = nullptr, *zblack = nullptr, *zghost = nullptr;
+        bool in_smem = true;       // false: relaxed by per-sweep launches over the lists
+    } jz;
+};
+
+// Floating-point data of a level in precision T.
+template <typename T>
+struct DevData {
+    T *u = nullptr, *f = nullptr, *r = nullptr;   // grids (may be null if unused)
+    T *gw = nullptr;     // KMAX * ng ghost weights for the current bc, slot major
+    T *gc = nullptr;     // ng relaxation coefficient mu dt
+    T *gg = nullptr;     // ng boundary data (level 0) or restricted boundary defect
+    T *gtmp = nullptr;   // ng new ghost values of a Jacobi sweep
+    T *ew = nullptr;     // EMAX * ne extension weights, slot major
+    T *Ainv = nullptr;   // nunk * nunk (coarsest level)
+};
+
+// Kernel view of one level in precision T (passed by value).
+template <typename T>
+struct LevelView {
+    int n;
+    int64_t nn;
+    int64_t s0, s1, s2;          // strides of axes 0, 1, 2 (s2 = 1 in 3D; 2D uses s0, s1)
+    T h2;                        // h^2
+    T inv_h2;
+    const uint8_t *type;
+    T *u;
+    const T *f;
+    T *r;
+    int ng;
+    const int32_t *gnode;
+    const int32_t *gstn;
+    const T *gw;
+    const T *gc;
+    const T *gg;
+    T *gtmp;
+};
+
+// Kernel view of a level's junction-zone components in precision T.
+template <typename T>
+struct JunctionView {
+    int ncomp, max_nodes, max_int, max_gh, ng;
+    const int32_t *node_off, *zone_cnt, *lnode;
+    const int32_t *int_off, *red_cnt, *int_glob, *int_me, *int_nb;
+    const int32_t *gh_off, *gh_me, *gh_q, *gh_stn;
+    T *u;
+    const T *f, *gg, *gc, *gw;
+    T h2;
+};
+
+}  // namespace gcmg

@@ -1,0 +1,45 @@
+// Launchers of the per-level kernels (kernels.cu).
+#pragma once
+
+#include <algorithm>
+#include <atomic>
+
+#include "gcmg_internal.h"
+
+namespace gcmg {
+
+extern std::atomic<long long> g_launches;   // kernels launched by this library
+
+template <typename T>
+void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s);
+template <typename T>
+void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s);
+template <typename T>
+void launch_ghost_relax(const LevelView<T> &v, int dim, cudaStream_t s);
+template <typename T>
+void launch_ghost_relax_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s);
+template <typename T>
+void launch_defect(const LevelView<T> &v, int dim, bool zero_rest, unsigned long long *norm, cudaStream_t s);
+template <typename T>
+void launch_extend(T *r, const DevGeom &g, const T *ew, cudaStream_t s);
+template <typename T>
+void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, T *gc, cudaStream_t s);
+template <typename T>
+void launch_prolong(const LevelView<T> &F, const LevelView<T> &C, int dim, const T *e, T *out, bool add,
+                    cudaStream_t s);
+template <typename T>
+void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv, cudaStream_t s);
+template <typename T>
+void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s);
+
+template <typename T>
+size_t junction_smem_bytes(const JunctionView<T> &J, int dim);
+template <typename T>
+void launch_junction(const JunctionView<T> &J, int dim, int sweeps, cudaStream_t s);
+template <typename T>
+void junction_prepare(int dim, size_t smem);
+
+void launch_defect_to_f32(const DevGeom &g, const double *r64, float *f32, float *g32, cudaStream_t s);
+void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cudaStream_t s);
+
+}  // namespace gcmg

@@ -1,0 +1,673 @@
+// Host-side geometry of the multigrid hierarchy: node classification, ghost
+// equations, extra-sweep band, defect-extension wavefronts and the coarsest
+// dense inverse.  Runs once per context; the per-cycle work is all on the GPU.
+//
+// Compiled without floating-point contraction so that x86 and Arm hosts build
+// bit-identical records.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+
+#include "gcmg_internal.h"
+
+namespace gcmg {
+namespace {
+
+struct Idx {
+    const HostLevel &L;
+    void split(int64_t p, int j[3]) const {
+        for (int a = 0; a < L.dim; a++) {
+            j[a] = (int)(p / L.stride[a]);
+            p -= (int64_t)j[a] * L.stride[a];
+        }
+    }
+    int64_t join(const int j[3]) const {
+        int64_t p = 0;
+        for (int a = 0; a < L.dim; a++) p += (int64_t)j[a] * L.stride[a];
+        return p;
+    }
+    bool inside_box(const int j[3]) const {
+        for (int a = 0; a < L.dim; a++)
+            if (j[a] < 0 || j[a] >= L.n) return false;
+        return true;
+    }
+    bool on_edge(int64_t p) const {
+        int j[3];
+        split(p, j);
+        for (int a = 0; a < L.dim; a++)
+            if (j[a] == 0 || j[a] == L.n - 1) return true;
+        return false;
+    }
+};
+
+inline bool unknown(const HostLevel &L, int64_t p) {
+    uint8_t k = L.type[p] & NODE_KIND;
+    return k == NODE_IN || k == NODE_GHOST;
+}
+
+inline void central_grad(const HostLevel &L, int64_t p, double g[3]) {
+    for (int a = 0; a < L.dim; a++)
+        g[a] = (L.phi[p + L.stride[a]] - L.phi[p - L.stride[a]]) / (2.0 * L.h);
+}
+
+// Omega_h = {phi < 0}; ghosts: outside nodes with an inside axis neighbour.
+void classify(HostLevel &L) {
+    Idx I{L};
+    L.type.assign(L.nn, NODE_OUT);
+    L.n_in = 0;
+    for (int64_t p = 0; p < L.nn; p++)
+        if (L.phi[p] < 0.0) {
+            if (I.on_edge(p)) throw GeomError{"an inside node lies on the box boundary"};
+            L.type[p] = NODE_IN;
+            L.n_in++;
+        }
+    L.ghost_node.clear();
+    for (int64_t p = 0; p < L.nn; p++) {
+        if (L.type[p] != NODE_OUT) continue;
+        int j[3];
+        I.split(p, j);
+        bool g = false;
+        for (int a = 0; a < L.dim && !g; a++)
+            for (int s = -1; s <= 1 && !g; s += 2) {
+                int k[3] = {j[0], j[1], j[2]};
+                k[a] += s;
+                if (I.inside_box(k) && L.type[I.join(k)] == NODE_IN) g = true;
+            }
+        if (g) {
+            L.type[p] = NODE_GHOST;
+            L.ghost_node.push_back((int32_t)p);
+        }
+    }
+}
+
+// One axis of a ghost stencil: node offsets, value and d/dx weights.
+struct AxisRule {
+    int m = 0;
+    int off[3] = {0, 0, 0};
+    double w[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
+};
+
+// quadratic Lagrange basis on t in {0,1,2} for nodes at offsets base + k dir
+AxisRule quad_rule(double h, int base, int dir, double t) {
+    AxisRule r;
+    r.m = 3;
+    const double l[3] = {0.5 * (t - 1.0) * (t - 2.0), t * (2.0 - t), 0.5 * t * (t - 1.0)};
+    const double dl[3] = {t - 1.5, 2.0 - 2.0 * t, t - 0.5};
+    for (int k = 0; k < 3; k++) {
+        r.off[k] = base + k * dir;
+        r.w[k] = l[k];
+        r.dw[k] = dl[k] / (dir * h);
+    }
+    return r;
+}
+
+AxisRule lin_rule(double h, int dir, double t) {
+    AxisRule r;
+    r.m = 2;
+    r.off[0] = 0;
+    r.off[1] = dir;
+    r.w[0] = 1.0 - t;
+    r.w[1] = t;
+    r.dw[0] = -1.0 / (dir * h);
+    r.dw[1] = 1.0 / (dir * h);
+    return r;
+}
+
+struct Candidate {
+    int nk = 0;
+    int64_t node[KMAX];
+    double val[KMAX];
+    double grad[3][KMAX];
+};
+
+bool all_unknown(const HostLevel &L, const Candidate &c) {
+    for (int k = 0; k < c.nk; k++)
+        if (c.node[k] < 0 || !unknown(L, c.node[k])) return false;
+    return true;
+}
+
+// tensor product of per-axis rules, slots in lexicographic order (axis 0 slowest)
+void tensor(const HostLevel &L, const int jg[3], const AxisRule *ax, Candidate &c) {
+    Idx I{L};
+    const int d = L.dim;
+    int cnt[3] = {1, 1, 1};
+    for (int a = 0; a < d; a++) cnt[a] = ax[a].m;
+    c.nk = 0;
+    for (int k0 = 0; k0 < cnt[0]; k0++)
+        for (int k1 = 0; k1 < cnt[1]; k1++)
+            for (int k2 = 0; k2 < (d == 3 ? cnt[2] : 1); k2++) {
+                const int kk[3] = {k0, k1, k2};
+                int j[3] = {0, 0, 0};
+                for (int a = 0; a < d; a++) j[a] = jg[a] + ax[a].off[kk[a]];
+                const int s = c.nk++;
+                c.node[s] = I.inside_box(j) ? I.join(j) : -1;
+                double v = 1.0;
+                for (int a = 0; a < d; a++) v *= ax[a].w[kk[a]];
+                c.val[s] = v;
+                for (int a = 0; a < d; a++) {
+                    double g = ax[a].dw[kk[a]];
+                    for (int b = 0; b < d; b++)
+                        if (b != a) g *= ax[b].w[kk[b]];
+                    c.grad[a][s] = g;
+                }
+            }
+}
+
+// Ghost equation of ghost q (Eqs. clpt, St_G, dir2d, neu2d; Remark 3).
+// Readings shared with the paper-level description of the library:
+//  * B = G - phi(G) grad_h phi / |grad_h phi|^2;
+//  * s_a = sign of the offset -phi(G) g_a; a zero offset tries centred nodes
+//    {-1,0,1} (quadratic only), then +1, then -1;
+//  * stencils tried in order: quadratic 3^d, linear 2^d, corner (G and
+//    G + s_a h e_a), two points along the first axis (direction -1 then +1)
+//    whose neighbour of G is inside.
+void ghost_equation(HostLevel &L, int64_t q) {
+    Idx I{L};
+    const int d = L.dim;
+    const int64_t G = L.ghost_node[q];
+    if (I.on_edge(G)) throw GeomError{"a ghost node lies on the box boundary"};
+    int jg[3] = {0, 0, 0};
+    I.split(G, jg);
+    double g[3] = {0, 0, 0}, gg = 0.0;
+    central_grad(L, G, g);
+    for (int a = 0; a < d; a++) gg += g[a] * g[a];
+    if (!(gg > 0.0)) throw GeomError{"zero level-set gradient at a ghost node"};
+    const double ph = L.phi[G];
+    double off[3] = {0, 0, 0};
+    int sgn[3] = {0, 0, 0};
+    std::vector<int> zero_axes;
+    for (int a = 0; a < d; a++) {
+        off[a] = -ph * g[a] / gg;
+        const double sg = -ph * g[a];
+        sgn[a] = sg > 0.0 ? 1 : (sg < 0.0 ? -1 : 0);
+        L.B[q * d + a] = (-1.0 + jg[a] * L.h) + off[a];
+        if (sgn[a] == 0) zero_axes.push_back(a);
+    }
+    const int nz = (int)zero_axes.size();
+    Candidate c;
+    int kind = -1;
+    // quadratic: options per zero axis 0 centred, 1 +1, 2 -1
+    int combos = 1;
+    for (int z = 0; z < nz; z++) combos *= 3;
+    for (int cb = 0; cb < combos && kind < 0; cb++) {
+        AxisRule ax[3];
+        int digits = cb, zi = nz - 1;
+        int opt[3] = {0, 0, 0};
+        for (; zi >= 0; zi--) { opt[zi] = digits % 3; digits /= 3; }
+        int z = 0;
+        for (int a = 0; a < d; a++) {
+            if (sgn[a] != 0) {
+                ax[a] = quad_rule(L.h, 0, sgn[a], off[a] / (sgn[a] * L.h));
+            } else {
+                const int o = opt[z++];
+                ax[a] = (o == 0) ? quad_rule(L.h, -1, 1, 1.0) : quad_rule(L.h, 0, o == 1 ? 1 : -1, 0.0);
+            }
+        }
+        tensor(L, jg, ax, c);
+        if (all_unknown(L, c)) kind = STENCIL_QUAD;
+    }
+    // linear 2^d and corner: zero axes try +1 then -1
+    for (int pass = 0; pass < 2 && kind < 0; pass++) {
+        const int nc = 1 << nz;
+        for (int cb = 0; cb < nc && kind < 0; cb++) {
+            int dir[3] = {0, 0, 0};
+            int z = 0;
+            for (int a = 0; a < d; a++) {
+                dir[a] = sgn[a];
+                if (dir[a] == 0) { dir[a] = ((cb >> (nz - 1 - z)) & 1) ? -1 : 1; z++; }
+            }
+            if (pass == 0) {
+                AxisRule ax[3];
+                for (int a = 0; a < d; a++) ax[a] = lin_rule(L.h, dir[a], off[a] / (dir[a] * L.h));
+                tensor(L, jg, ax, c);
+                if (all_unknown(L, c)) kind = STENCIL_LIN;
+            } else {
+                c.nk = d + 1;
+                c.node[0] = G;
+                double tsum = 0.0;
+                for (int a = 0; a < d; a++)
+                    for (int s = 0; s <= d; s++) c.grad[a][s] = 0.0;
+                for (int a = 0; a < d; a++) {
+                    const double t = off[a] / (dir[a] * L.h);
+                    int j[3] = {jg[0], jg[1], jg[2]};
+                    j[a] += dir[a];
+                    c.node[1 + a] = I.inside_box(j) ? I.join(j) : -1;
+                    c.val[1 + a] = t;
+                    tsum += t;
+                    c.grad[a][1 + a] = 1.0 / (dir[a] * L.h);
+                    c.grad[a][0] = -1.0 / (dir[a] * L.h);
+                }
+                c.val[0] = 1.0 - tsum;
+                if (all_unknown(L, c)) kind = STENCIL_CORNER;
+            }
+        }
+    }
+    // two points along an axis towards an inside neighbour
+    for (int a = 0; a < d && kind < 0; a++)
+        for (int s = -1; s <= 1 && kind < 0; s += 2) {
+            const int64_t P = G + s * L.stride[a];
+            if ((L.type[P] & NODE_KIND) != NODE_IN) continue;
+            const double t = off[a] / (s * L.h);
+            c.nk = 2;
+            c.node[0] = G;
+            c.node[1] = P;
+            c.val[0] = 1.0 - t;
+            c.val[1] = t;
+            for (int b = 0; b < d; b++) c.grad[b][0] = c.grad[b][1] = 0.0;
+            c.grad[a][0] = -1.0 / (s * L.h);
+            c.grad[a][1] = 1.0 / (s * L.h);
+            kind = STENCIL_AXIS;
+        }
+    if (kind < 0) throw GeomError{"no usable ghost stencil"};
+    // discrete normal: gradient of the interpolant of phi at B
+    double gn[3] = {0, 0, 0}, norm2 = 0.0;
+    for (int a = 0; a < d; a++) {
+        for (int k = 0; k < c.nk; k++) gn[a] += c.grad[a][k] * L.phi[c.node[k]];
+        norm2 += gn[a] * gn[a];
+    }
+    const double nrm = std::sqrt(norm2);
+    if (!(nrm > 0.0)) throw GeomError{"degenerate discrete normal at a ghost node"};
+    for (int a = 0; a < d; a++) L.nu[q * d + a] = gn[a] / nrm;
+    L.scase[q] = (uint8_t)kind;
+    for (int k = 0; k < KMAX; k++) {
+        const int64_t o = q * KMAX + k;
+        if (k < c.nk) {
+            L.stn[o] = (int32_t)c.node[k];
+            L.wD[o] = c.val[k];
+            double w = 0.0;
+            for (int a = 0; a < d; a++) w += L.nu[q * d + a] * c.grad[a][k];
+            L.wN[o] = w;
+        } else {
+            L.stn[o] = (int32_t)G;
+            L.wD[o] = 0.0;
+            L.wN[o] = 0.0;
+        }
+    }
+}
+
+// Band of Sec. 3.2: inside nodes with -phi/|grad_h phi| <= delta.
+void mark_band(HostLevel &L, double delta) {
+    Idx I{L};
+    L.band_red.clear();
+    L.band_black.clear();
+    for (int64_t p = 0; p < L.nn; p++) {
+        if ((L.type[p] & NODE_KIND) != NODE_IN) continue;
+        double g[3] = {0, 0, 0}, gg = 0.0;
+        central_grad(L, p, g);
+        for (int a = 0; a < L.dim; a++) gg += g[a] * g[a];
+        if (!(gg > 0.0)) continue;
+        if (L.phi[p] / std::sqrt(gg) >= -delta) {
+            L.type[p] |= NODE_BAND;
+            int j[3];
+            I.split(p, j);
+            int par = 0;
+            for (int a = 0; a < L.dim; a++) par += j[a];
+            ((par & 1) ? L.band_black : L.band_red).push_back((int32_t)p);
+        }
+    }
+}
+
+// Defect extension of Sec. 2.6 on fine level F: steady state of the upwind
+// transport, r(P) = sum_a |n_a| r(Q_a) / sum_a |n_a| over Q_a = P - sgn(n_a) h e_a
+// with phi(Q_a) < phi(P) (else the mean of the lower ghost / extended axis
+// neighbours, else 0); the set is every outside non-ghost node next to a
+// coarse ghost, closed under these dependencies.  Nodes are grouped into
+// wavefronts: a node's sources all lie in earlier wavefronts (or are ghosts).
+void build_extension(HostLevel &F, const HostLevel &C) {
+    Idx I{F}, IC{C};
+    const int d = F.dim;
+    std::vector<uint8_t> in_set(F.nn, 0);
+    std::vector<int64_t> work;
+    for (int64_t q = 0; q < C.ng(); q++) {
+        int J[3] = {0, 0, 0};
+        IC.split(C.ghost_node[q], J);
+        const int cube = d == 2 ? 9 : 27;
+        for (int c = 0; c < cube; c++) {
+            int j[3] = {0, 0, 0}, rem = c;
+            for (int a = d - 1; a >= 0; a--) { j[a] = 2 * J[a] + rem % 3 - 1; rem /= 3; }
+            if (!I.inside_box(j)) continue;
+            const int64_t P = I.join(j);
+            if (F.type[P] == NODE_OUT && !in_set[P]) { in_set[P] = 1; work.push_back(P); }
+        }
+    }
+    for (size_t w = 0; w < work.size(); w++) {
+        const int64_t P = work[w];
+        if (I.on_edge(P)) throw GeomError{"the defect extension reaches the box boundary"};
+        double g[3] = {0, 0, 0};
+        central_grad(F, P, g);
+        for (int a = 0; a < d; a++) {
+            if (g[a] == 0.0) continue;
+            const int64_t Q = P - (g[a] > 0.0 ? 1 : -1) * F.stride[a];
+            if (F.phi[Q] < F.phi[P] && F.type[Q] == NODE_OUT && !in_set[Q]) {
+                in_set[Q] = 1;
+                work.push_back(Q);
+            }
+        }
+    }
+    // sources and weights of each node
+    struct Ext {
+        int64_t node;
+        int cnt;
+        int64_t src[EMAX];
+        double w[EMAX];
+        int wave;
+    };
+    std::vector<Ext> ext(work.size());
+    std::vector<int32_t> slot(F.nn > 0 ? 0 : 0);
+    std::sort(work.begin(), work.end());
+    auto lower_usable = [&](int64_t P, int64_t Q) {
+        return F.phi[Q] < F.phi[P] && ((F.type[Q] & NODE_KIND) == NODE_GHOST || in_set[Q]);
+    };
+    for (size_t e = 0; e < work.size(); e++) {
+        const int64_t P = work[e];
+        Ext &x = ext[e];
+        x.node = P;
+        x.cnt = 0;
+        double g[3] = {0, 0, 0}, ws = 0.0;
+        central_grad(F, P, g);
+        for (int a = 0; a < d; a++) {
+            if (g[a] == 0.0) continue;
+            const int64_t Q = P - (g[a] > 0.0 ? 1 : -1) * F.stride[a];
+            if (!lower_usable(P, Q)) continue;
+            x.src[x.cnt] = Q;
+            x.w[x.cnt] = std::fabs(g[a]);
+            ws += std::fabs(g[a]);
+            x.cnt++;
+        }
+        if (x.cnt > 0 && ws > 0.0) {
+            for (int i = 0; i < x.cnt; i++) x.w[i] /= ws;
+        } else {
+            x.cnt = 0;
+            for (int a = 0; a < d; a++)
+                for (int s = -1; s <= 1; s += 2) {
+                    const int64_t Q = P + s * F.stride[a];
+                    if (lower_usable(P, Q)) x.src[x.cnt++] = Q;
+                }
+            for (int i = 0; i < x.cnt; i++) x.w[i] = 1.0 / x.cnt;
+        }
+    }
+    // wavefront = 1 + max wavefront of extended sources (ghosts: 0); process
+    // in increasing phi so sources are final before their dependants
+    std::vector<size_t> order(work.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const double pa = F.phi[ext[a].node], pb = F.phi[ext[b].node];
+        return pa < pb || (pa == pb && ext[a].node < ext[b].node);
+    });
+    std::vector<int> wave_of(F.nn, 0);
+    int nwave = 0;
+    for (size_t oi : order) {
+        Ext &x = ext[oi];
+        int wv = 1;
+        for (int i = 0; i < x.cnt; i++)
+            if (in_set[x.src[i]]) wv = std::max(wv, wave_of[x.src[i]] + 1);
+        x.wave = wv;
+        wave_of[x.node] = wv;
+        nwave = std::max(nwave, wv);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ext[a].wave < ext[b].wave; });
+    const size_t ne = work.size();
+    F.ext_node.resize(ne);
+    F.ext_cnt.resize(ne);
+    F.ext_src.assign(ne * EMAX, 0);
+    F.ext_w.assign(ne * EMAX, 0.0);
+    F.ext_wave.assign(nwave + 1, 0);
+    for (size_t i = 0; i < ne; i++) {
+        const Ext &x = ext[order[i]];
+        F.ext_node[i] = (int32_t)x.node;
+        F.ext_cnt[i] = (uint8_t)x.cnt;
+        for (int k = 0; k < x.cnt; k++) {
+            F.ext_src[i * EMAX + k] = (int32_t)x.src[k];
+            F.ext_w[i * EMAX + k] = x.w[k];
+        }
+        for (int k = x.cnt; k < EMAX; k++) F.ext_src[i * EMAX + k] = (int32_t)x.node;
+        F.ext_wave[x.wave]++;
+    }
+    for (int w = 1; w <= nwave; w++) F.ext_wave[w] += F.ext_wave[w - 1];
+    // ext_wave[w] now = number of nodes in waves <= w: offsets of wave w are [ext_wave[w-1], ext_wave[w])
+}
+
+}  // namespace
+
+// Junction zone: unknowns within radius h of a ghost whose 3^d neighbourhood
+// holds a ghost of the other boundary type.  Split into components closed
+// under the reads of their updates (inside node: axis neighbours; ghost: its
+// stencil), so each can be relaxed on its own.
+void build_junction(HostLevel &L, double radius) {
+    Idx I{L};
+    const int d = L.dim;
+    HostLevel::Junction J;
+    std::vector<int32_t> ghost_of(L.nn, -1);
+    for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;
+    std::vector<uint8_t> zone(L.nn, 0);
+    const int R = (int)std::ceil(radius);
+    const int cube = d == 2 ? 9 : 27;
+    for (int64_t q = 0; q < L.ng(); q++) {
+        int j[3] = {0, 0, 0};
+        I.split(L.ghost_node[q], j);
+        bool junction = false;
+        for (int c = 0; c < cube && !junction; c++) {
+            int k[3] = {0, 0, 0}, rem = c;
+            for (int a = d - 1; a >= 0; a--) { k[a] = j[a] + rem % 3 - 1; rem /= 3; }
+            if (!I.inside_box(k)) continue;
+            const int32_t g2 = ghost_of[I.join(k)];
+            if (g2 >= 0 && L.bc[g2] != L.bc[q]) junction = true;
+        }
+        if (!junction) continue;
+        const int side = 2 * R + 1;
+        const int total = d == 2 ? side * side : side * side * side;
+        for (int c = 0; c < total; c++) {
+            int k[3] = {0, 0, 0}, rem = c;
+            double r2 = 0.0;
+            for (int a = d - 1; a >= 0; a--) {
+                const int o = rem % side - R;
+                rem /= side;
+                k[a] = j[a] + o;
+                r2 += (double)o * o;
+            }
+            if (r2 > radius * radius || !I.inside_box(k)) continue;
+            const int64_t P = I.join(k);
+            if (unknown(L, P)) zone[P] = 1;
+        }
+    }
+    // reads of each zone node
+    auto reads = [&](int64_t P, std::vector<int64_t> &out) {
+        out.clear();
+        if ((L.type[P] & NODE_KIND) == NODE_IN) {
+            for (int a = 0; a < d; a++) { out.push_back(P - L.stride[a]); out.push_back(P + L.stride[a]); }
+        } else {
+            const int64_t q = ghost_of[P];
+            for (int k = 0; k < cube; k++) out.push_back(L.stn[q * KMAX + k]);
+        }
+    };
+    // union-find over zone nodes
+    std::vector<int64_t> zn;
+    for (int64_t P = 0; P < L.nn; P++)
+        if (zone[P]) zn.push_back(P);
+    std::vector<int32_t> zid(L.nn, -1);
+    for (size_t i = 0; i < zn.size(); i++) zid[zn[i]] = (int32_t)i;
+    std::vector<int32_t> parent(zn.size());
+    std::iota(parent.begin(), parent.end(), 0);
+    std::function<int32_t(int32_t)> find = [&](int32_t x) {
+        while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
+        return x;
+    };
+    std::vector<int64_t> rd;
+    for (size_t i = 0; i < zn.size(); i++) {
+        reads(zn[i], rd);
+        for (int64_t Q : rd)
+            if (zid[Q] >= 0) {
+                const int32_t a = find((int32_t)i), b = find(zid[Q]);
+                if (a != b) parent[std::max(a, b)] = std::min(a, b);
+            }
+    }
+    std::vector<int32_t> comp_of_root(zn.size(), -1);
+    std::vector<std::vector<int64_t>> comps;
+    for (size_t i = 0; i < zn.size(); i++) {
+        const int32_t r = find((int32_t)i);
+        if (comp_of_root[r] < 0) { comp_of_root[r] = (int32_t)comps.size(); comps.emplace_back(); }
+        comps[comp_of_root[r]].push_back(zn[i]);
+    }
+    std::vector<int32_t> local(L.nn, -1);
+    for (const auto &cz : comps) {
+        // local nodes: zone nodes (increasing index), then halo nodes
+        std::vector<int64_t> halo;
+        for (int64_t P : cz) {
+            reads(P, rd);
+            for (int64_t Q : rd)
+                if (!zone[Q]) halo.push_back(Q);
+        }
+        std::sort(halo.begin(), halo.end());
+        halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+        std::vector<int64_t> nodes(cz);
+        nodes.insert(nodes.end(), halo.begin(), halo.end());
+        for (size_t i = 0; i < nodes.size(); i++) {
+            local[nodes[i]] = (int32_t)i;
+            J.lnode.push_back((int32_t)nodes[i]);
+        }
+        J.node_off.push_back((int32_t)J.lnode.size());
+        J.zone_cnt.push_back((int32_t)cz.size());
+        int nred = 0, nint = 0, ngh = 0;
+        for (int colour = 0; colour < 2; colour++)
+            for (int64_t P : cz) {
+                if ((L.type[P] & NODE_KIND) != NODE_IN) continue;
+                int j[3] = {0, 0, 0}, par = 0;
+                I.split(P, j);
+                for (int a = 0; a < d; a++) par += j[a];
+                if ((par & 1) != colour) continue;
+                J.int_glob.push_back((int32_t)P);
+                J.int_me.push_back(local[P]);
+                reads(P, rd);
+                for (int64_t Q : rd) J.int_nb.push_back(local[Q]);
+                nint++;
+                if (colour == 0) nred++;
+            }
+        for (int64_t P : cz) {
+            if ((L.type[P] & NODE_KIND) != NODE_GHOST) continue;
+            J.gh_me.push_back(local[P]);
+            J.gh_q.push_back(ghost_of[P]);
+            reads(P, rd);
+            for (int64_t Q : rd) J.gh_stn.push_back(local[Q]);
+            ngh++;
+        }
+        J.int_off.push_back((int32_t)J.int_me.size());
+        J.red_cnt.push_back(nred);
+        J.gh_off.push_back((int32_t)J.gh_me.size());
+        J.max_nodes = std::max(J.max_nodes, (int)nodes.size());
+        J.max_int = std::max(J.max_int, nint);
+        J.max_gh = std::max(J.max_gh, ngh);
+        for (int64_t P : nodes) local[P] = -1;
+    }
+    for (int64_t P : zn) {
+        if ((L.type[P] & NODE_KIND) == NODE_GHOST) {
+            J.zghost.push_back(ghost_of[P]);
+        } else {
+            int j[3] = {0, 0, 0}, par = 0;
+            I.split(P, j);
+            for (int a = 0; a < d; a++) par += j[a];
+            ((par & 1) ? J.zblack : J.zred).push_back((int32_t)P);
+        }
+    }
+    L.junction = std::move(J);
+}
+
+void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
+                     std::vector<HostLevel> &levels) {
+    levels.clear();
+    int nl = 1;
+    for (int m = n; m > n_coarse; m = (m - 1) / 2 + 1) nl++;
+    for (int l = 0; l < nl; l++) {
+        HostLevel L;
+        L.dim = dim;
+        L.n = (n - 1) / (1 << l) + 1;
+        L.h = 2.0 / (L.n - 1);
+        L.nn = 1;
+        for (int a = 0; a < dim; a++) L.nn *= L.n;
+        L.stride[dim - 1] = 1;
+        for (int a = dim - 2; a >= 0; a--) L.stride[a] = L.stride[a + 1] * L.n;
+        L.phi.resize(L.nn);
+        const int64_t step = (int64_t)1 << l;
+        Idx I{L};
+        for (int64_t p = 0; p < L.nn; p++) {
+            int j[3] = {0, 0, 0};
+            I.split(p, j);
+            int64_t fi = 0;
+            for (int a = 0; a < dim; a++) fi = fi * n + j[a] * step;
+            L.phi[p] = phi[fi];
+        }
+        classify(L);
+        const int64_t ng = L.ng();
+        L.B.assign(ng * dim, 0.0);
+        L.nu.assign(ng * dim, 0.0);
+        L.scase.assign(ng, 0);
+        L.stn.assign(ng * KMAX, 0);
+        L.wD.assign(ng * KMAX, 0.0);
+        L.wN.assign(ng * KMAX, 0.0);
+        L.bc.assign(ng, 0);
+        for (int64_t q = 0; q < ng; q++) ghost_equation(L, q);
+        mark_band(L, delta_over_h * L.h);
+        levels.push_back(std::move(L));
+    }
+    for (int l = 0; l + 1 < nl; l++) build_extension(levels[l], levels[l + 1]);
+    build_coarse_inverse(levels.back());
+}
+
+// Dense inverse of the coarsest system (Eq. discr with the level's bc):
+// Gauss-Jordan elimination with partial pivoting on [A | I].
+void build_coarse_inverse(HostLevel &L) {
+    std::vector<int64_t> id(L.nn, -1);
+    L.unk_node.clear();
+    L.unk_ghost.clear();
+    std::vector<int32_t> ghost_of(L.nn, -1);
+    for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;
+    for (int64_t p = 0; p < L.nn; p++)
+        if (unknown(L, p)) {
+            id[p] = (int64_t)L.unk_node.size();
+            L.unk_node.push_back((int32_t)p);
+            L.unk_ghost.push_back(ghost_of[p]);
+        }
+    const int64_t m = (int64_t)L.unk_node.size();
+    std::vector<double> A(m * m, 0.0), X(m * m, 0.0);
+    const double ih2 = 1.0 / (L.h * L.h);
+    for (int64_t i = 0; i < m; i++) {
+        const int64_t p = L.unk_node[i];
+        X[i * m + i] = 1.0;
+        if (L.unk_ghost[i] < 0) {
+            A[i * m + i] += 2.0 * L.dim * ih2;
+            for (int a = 0; a < L.dim; a++) {
+                A[i * m + id[p + L.stride[a]]] -= ih2;
+                A[i * m + id[p - L.stride[a]]] -= ih2;
+            }
+        } else {
+            const int64_t q = L.unk_ghost[i];
+            const double *w = (L.bc[q] ? L.wN.data() : L.wD.data()) + q * KMAX;
+            for (int k = 0; k < KMAX; k++)
+                if (w[k] != 0.0) A[i * m + id[L.stn[q * KMAX + k]]] += w[k];
+        }
+    }
+    for (int64_t c = 0; c < m; c++) {
+        int64_t piv = c;
+        for (int64_t i = c + 1; i < m; i++)
+            if (std::fabs(A[i * m + c]) > std::fabs(A[piv * m + c])) piv = i;
+        if (!(std::fabs(A[piv * m + c]) > 0.0)) throw GeomError{"singular coarsest-level system"};
+        if (piv != c) {
+            std::swap_ranges(A.begin() + c * m, A.begin() + (c + 1) * m, A.begin() + piv * m);
+            std::swap_ranges(X.begin() + c * m, X.begin() + (c + 1) * m, X.begin() + piv * m);
+        }
+        const double inv = 1.0 / A[c * m + c];
+        for (int64_t j = 0; j < m; j++) { A[c * m + j] *= inv; X[c * m + j] *= inv; }
+        for (int64_t i = 0; i < m; i++) {
+            if (i == c) continue;
+            const double f = A[i * m + c];
+            if (f == 0.0) continue;
+            double *ai = &A[i * m], *xi = &X[i * m];
+            const double *ac = &A[c * m], *xc = &X[c * m];
+            for (int64_t j = 0; j < m; j++) { ai[j] -= f * ac[j]; xi[j] -= f * xc[j]; }
+        }
+    }
+    L.Ainv.swap(X);
+}
+
+}  // namespace gcmg

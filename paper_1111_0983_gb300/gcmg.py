@@ -1,0 +1,245 @@
+"""ctypes binding of libgcmg.so (include/gcmg.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (float64, contiguous);
+PyTorch only provides device memory and streams.  Loading fails loudly when
+the compiled library is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgcmg.so")
+
+GCMG_OK, GCMG_E_ARG, GCMG_E_CUDA, GCMG_E_OOM, GCMG_E_GEOM, GCMG_E_NOCONV, GCMG_E_STATE = range(7)
+STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_OOM", 4: "E_GEOM", 5: "E_NOCONV", 6: "E_STATE"}
+KMAX = 27
+
+
+class Params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int), ("n_coarse", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("lam", C.c_int), ("gamma", C.c_int), ("delta_over_h", C.c_double), ("c_dirichlet", C.c_double),
+                ("c_neumann_factor", C.c_double), ("precision", C.c_int), ("max_cycles", C.c_int),
+                ("rtol", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
+                ("r0_norm", C.c_double), ("rel", C.c_double * 257)]
+
+    def to_dict(self):
+        m = self.cycles
+        return dict(cycles=m, converged=bool(self.converged), rel_residual=self.rel_residual,
+                    r0_norm=self.r0_norm, rel=np.array(self.rel[: min(m, 256) + 1]))
+
+
+class GcmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gcmg {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1111_0983_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl, st = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_int
+        sig = {
+            "gcmg_default_params": (st, [C.POINTER(Params), i32, i32, i32]),
+            "gcmg_create": (st, [C.POINTER(Params), vp, vp, C.POINTER(vp)]),
+            "gcmg_destroy": (None, [vp]),
+            "gcmg_last_error": (C.c_char_p, [vp]),
+            "gcmg_num_levels": (i32, [vp]),
+            "gcmg_level_n": (i32, [vp, i32]),
+            "gcmg_num_ghosts": (st, [vp, i32, C.POINTER(i64)]),
+            "gcmg_num_unknowns": (st, [vp, i32, C.POINTER(i64)]),
+            "gcmg_ghost_geometry": (st, [vp, i32, vp, vp, vp, vp]),
+            "gcmg_ghost_equations": (st, [vp, i32, vp, vp, vp]),
+            "gcmg_node_types": (st, [vp, i32, vp]),
+            "gcmg_set_bc_types": (st, [vp, i32, vp]),
+            "gcmg_set_rhs": (st, [vp, vp, vp]),
+            "gcmg_solve": (st, [vp, vp, C.POINTER(Stats)]),
+            "gcmg_solve_host": (st, [vp, vp, vp, vp, C.POINTER(Stats)]),
+            "gcmg_defect": (st, [vp, i32, vp, vp, vp, vp, C.POINTER(dbl)]),
+            "gcmg_relax": (st, [vp, i32, vp, vp, vp, i32]),
+            "gcmg_extend": (st, [vp, i32, vp]),
+            "gcmg_restrict": (st, [vp, i32, vp, vp, vp]),
+            "gcmg_prolong": (st, [vp, i32, vp, vp]),
+            "gcmg_set_kernel_timing": (st, [vp, i32]),
+            "gcmg_kernel_timing": (st, [vp, C.POINTER(i64), C.POINTER(dbl)]),
+            "gcmg_launch_counter": (i64, []),
+            "gcmg_junction_zone": (st, [vp, i32, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_params(dim, n, n_coarse, **kw):
+    p = Params()
+    lib().gcmg_default_params(C.byref(p), dim, n, n_coarse)
+    for k, v in kw.items():
+        setattr(p, "lam" if k == "lam" or k == "lambda_" else k, v)
+    return p
+
+
+def _ptr(t):
+    """Device (torch) or host (numpy) buffer -> void*."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return C.c_void_p(t.ctypes.data)
+    assert t.is_contiguous()
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One multigrid hierarchy (a gcmg context) on the current CUDA device."""
+
+    def __init__(self, phi, n_coarse, stream=None, **params):
+        import torch
+        phi_t = phi if isinstance(phi, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(phi))
+        phi_t = phi_t.to(device="cuda", dtype=torch.float64).contiguous()
+        self.dim = phi_t.dim()
+        self.n = phi_t.shape[0]
+        self.params = default_params(self.dim, self.n, n_coarse, **params)
+        self.stream = stream
+        h = C.c_void_p()
+        s = lib().gcmg_create(C.byref(self.params), _ptr(phi_t), C.c_void_p(stream.cuda_stream) if stream else None,
+                              C.byref(h))
+        self._h = h
+        if s != GCMG_OK:
+            msg = lib().gcmg_last_error(h).decode() if h.value else ""
+            if h.value:
+                lib().gcmg_destroy(h)
+            self._h = None
+            raise GcmgError(s, msg)
+        self.nlev = lib().gcmg_num_levels(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gcmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s != GCMG_OK:
+            raise GcmgError(s, lib().gcmg_last_error(self._h).decode())
+
+    # ---- geometry
+    def level_n(self, l):
+        return lib().gcmg_level_n(self._h, l)
+
+    def shape(self, l):
+        return (self.level_n(l),) * self.dim
+
+    def num_ghosts(self, l):
+        v = C.c_int64()
+        self._check(lib().gcmg_num_ghosts(self._h, l, C.byref(v)))
+        return v.value
+
+    def num_unknowns(self, l=0):
+        v = C.c_int64()
+        self._check(lib().gcmg_num_unknowns(self._h, l, C.byref(v)))
+        return v.value
+
+    def ghosts(self, l):
+        ng, d = self.num_ghosts(l), self.dim
+        out = dict(node=np.empty(ng, np.int64), B=np.empty((ng, d)), nu=np.empty((ng, d)),
+                   case=np.empty(ng, np.uint8))
+        self._check(lib().gcmg_ghost_geometry(self._h, l, *[_ptr(out[k]) for k in ("node", "B", "nu", "case")]))
+        return out
+
+    def ghost_equations(self, l):
+        ng = self.num_ghosts(l)
+        out = dict(stn=np.empty((ng, KMAX), np.int64), wD=np.empty((ng, KMAX)), wN=np.empty((ng, KMAX)))
+        self._check(lib().gcmg_ghost_equations(self._h, l, *[_ptr(out[k]) for k in ("stn", "wD", "wN")]))
+        return out
+
+    def junction_zone(self, l):
+        out = np.empty(self.shape(l), np.uint8)
+        self._check(lib().gcmg_junction_zone(self._h, l, _ptr(out)))
+        return out
+
+    def node_types(self, l):
+        out = np.empty(self.shape(l), np.uint8)
+        self._check(lib().gcmg_node_types(self._h, l, _ptr(out)))
+        return out
+
+    # ---- data
+    def set_bc_types(self, l, types):
+        t = np.ascontiguousarray(types, dtype=np.uint8)
+        assert t.shape == (self.num_ghosts(l),)
+        self._check(lib().gcmg_set_bc_types(self._h, l, _ptr(t)))
+
+    def set_rhs(self, f, g):
+        self._check(lib().gcmg_set_rhs(self._h, _ptr(f), _ptr(g)))
+
+    def solve(self, u):
+        st = Stats()
+        s = lib().gcmg_solve(self._h, _ptr(u), C.byref(st))
+        if s not in (GCMG_OK, GCMG_E_NOCONV):
+            self._check(s)
+        return st.to_dict()
+
+    def solve_host(self, f, g, u_out=None):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        u = np.empty(self.shape(0)) if u_out is None else u_out
+        st = Stats()
+        s = lib().gcmg_solve_host(self._h, _ptr(f), _ptr(g), _ptr(u), C.byref(st))
+        if s not in (GCMG_OK, GCMG_E_NOCONV):
+            self._check(s)
+        return u, st.to_dict()
+
+    # ---- single steps (FP64, caller buffers of the level's size)
+    def defect(self, l, u, f, g, r):
+        nrm = C.c_double()
+        self._check(lib().gcmg_defect(self._h, l, _ptr(u), _ptr(f), _ptr(g), _ptr(r), C.byref(nrm)))
+        return nrm.value
+
+    def relax(self, l, u, f, g, with_extra=True):
+        self._check(lib().gcmg_relax(self._h, l, _ptr(u), _ptr(f), _ptr(g), int(with_extra)))
+
+    def extend(self, l, r):
+        self._check(lib().gcmg_extend(self._h, l, _ptr(r)))
+
+    def restrict(self, l, r, fc, gc):
+        self._check(lib().gcmg_restrict(self._h, l, _ptr(r), _ptr(fc), _ptr(gc)))
+
+    def prolong(self, l, ec, out):
+        self._check(lib().gcmg_prolong(self._h, l, _ptr(ec), _ptr(out)))
+
+    # ---- measurement
+    KERNEL_SMOOTH, KERNEL_DEFECT, KERNEL_PROLONG, KERNEL_RESTRICT = 0, 1, 2, 3
+
+    def set_kernel_timing(self, kind):
+        self._check(lib().gcmg_set_kernel_timing(self._h, int(kind)))
+
+    def kernel_timing(self):
+        n, ms = C.c_int64(), C.c_double()
+        self._check(lib().gcmg_kernel_timing(self._h, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
+
+def launch_counter():
+    return lib().gcmg_launch_counter()

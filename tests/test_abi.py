@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares; host-only argument checks work without a GPU."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(gcmg_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1111_0983_gb300 import build, gcmg
+    build.build()
+    return gcmg.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params_host_only(lib):
+    from paper_1111_0983_gb300 import gcmg
+    p = gcmg.default_params(2, 4097, 33)
+    assert (p.nu1, p.nu2, p.lam, p.gamma) == (2, 1, 5, 1)
+    assert p.delta_over_h == 3.0 and p.c_dirichlet == 0.9 and p.rtol == 1e-10
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib):
+    from paper_1111_0983_gb300 import gcmg
+    h = C.c_void_p()
+    p = gcmg.default_params(2, 65, 17)
+    assert lib.gcmg_create(C.byref(p), None, None, C.byref(h)) == gcmg.GCMG_E_ARG
+    assert lib.gcmg_create(None, None, None, C.byref(h)) == gcmg.GCMG_E_ARG
+    assert lib.gcmg_create(C.byref(p), None, None, None) == gcmg.GCMG_E_ARG
+    assert not h.value
+    assert lib.gcmg_num_levels(None) == 0
+    assert lib.gcmg_last_error(None) == b"null context"
+
+
+def test_oracle_builds_separately():
+    import oracle
+    path = oracle.build()
+    assert os.path.exists(path) and "oracle" in os.path.basename(path)

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA library against the FP64 oracle, element by element.
+
+Every step of the cycle (defect, relaxation with the extra sweeps, defect
+extension, composite restriction, interpolation) is compared on the same
+seeded inputs, then whole solves: the converged solution must match the
+oracle's converged discrete solution within 1e-10 relative max-norm over
+Omega_h u Gamma_h, and the per-cycle convergence factors are compared.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1111_0983_gb300 import inputs  # noqa: E402
+from helpers import oracle_for, problem_rhs, rel_maxdiff  # noqa: E402
+
+PARITY = 1e-10
+
+
+def _gcmg():
+    from paper_1111_0983_gb300 import gcmg
+    return gcmg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def solver_for(P, n, nc, **kw):
+    S = _gcmg().Solver(P.phi_grid(n), nc, **kw)
+    for l in range(S.nlev):
+        S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+    return S
+
+
+def set_problem_rhs(S, P, n):
+    G = S.ghosts(0)
+    types = P.bc_types(G["B"])
+    f = P.f_grid(n)
+    g = P.g_values(G["B"], G["nu"], types)
+    S.set_rhs(dev(f), dev(g))
+    return f, g
+
+
+CASES = [(inputs.disk(), 65, 17), (inputs.flower(), 257, 33), (inputs.star(27), 257, 33),
+         (inputs.star(0), 257, 65), (inputs.torus(), 33, 17)]
+
+
+# ----------------------------------------------------------------- records
+@pytest.mark.parametrize("P,n,nc", CASES)
+def test_ghost_records_match_oracle(P, n, nc):
+    S = solver_for(P, n, nc)
+    O = oracle_for(P, n, nc, rhs=False)
+    assert S.nlev == O.nlev
+    for l in range(S.nlev):
+        assert np.array_equal(S.node_types(l) & 3, O.types(l))
+        assert np.array_equal((S.node_types(l) & 4) > 0, O.band(l) > 0)
+        Gs, Go = S.ghosts(l), O.ghosts(l)
+        assert np.array_equal(Gs["node"], Go["node"])
+        assert np.array_equal(Gs["case"], Go["case"])
+        assert np.abs(Gs["B"] - Go["B"]).max(initial=0) < 1e-13
+        assert np.abs(Gs["nu"] - Go["nu"]).max(initial=0) < 1e-12
+        Es = S.ghost_equations(l)
+        assert np.array_equal(Es["stn"], Go["stn"])
+        h = 2.0 / (S.level_n(l) - 1)
+        assert np.abs(Es["wD"] - Go["wD"]).max(initial=0) < 1e-12
+        assert np.abs(Es["wN"] - Go["wN"]).max(initial=0) * h < 1e-12
+        assert S.num_unknowns(l) == int((O.types(l) > 0).sum())
+        assert np.array_equal(S.junction_zone(l), O.junction_zone(l))
+
+
+# -------------------------------------------------------------- each step
+@pytest.mark.parametrize("P,n,nc", CASES)
+def test_cycle_steps_match_oracle(P, n, nc):
+    S = solver_for(P, n, nc)
+    O = oracle_for(P, n, nc, rhs=False)
+    rng = np.random.default_rng(11)
+    for l in range(S.nlev - 1):
+        shape, cshape = S.shape(l), S.shape(l + 1)
+        T = O.types(l)
+        unk = T > 0
+        u = np.where(unk, rng.uniform(-1, 1, shape), 0.0)
+        f = np.where(T == 1, rng.uniform(-1, 1, shape), 0.0)
+        g = rng.uniform(-1, 1, O.num_ghosts(l))
+        # defect
+        r_d = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        nrm = S.defect(l, dev(u), dev(f), dev(g), r_d)
+        if l == 0:
+            O.set_rhs(f, g)
+            r_o, nrm_o = O.defect(u, 0)
+            assert rel_maxdiff(host(r_d), r_o, unk) < 1e-13
+            assert abs(nrm - nrm_o) <= 1e-13 * nrm_o
+        # relaxation with the extra sweeps
+        u_d = dev(u)
+        S.relax(l, u_d, dev(f), dev(g), True)
+        u_o = O.relax(u, f, g, l, True)
+        assert rel_maxdiff(host(u_d), u_o, unk) < 1e-13
+        # extension of a defect-like field (values on unknowns)
+        r = np.where(unk, rng.uniform(-1, 1, shape), 0.0)
+        r_d = dev(r)
+        S.extend(l, r_d)
+        r_o = O.extend(r, l)
+        E = O.extension(l)
+        if len(E["node"]):
+            assert np.abs(host(r_d).ravel()[E["node"]] - r_o.ravel()[E["node"]]).max() < 1e-14
+        # composite restriction of the extended field
+        fc_d = torch.zeros(cshape, dtype=torch.float64, device="cuda")
+        gc_d = torch.zeros(max(S.num_ghosts(l + 1), 1), dtype=torch.float64, device="cuda")
+        S.restrict(l, dev(r_o), fc_d, gc_d)
+        fc_o, gc_o = O.restrict(r_o, l)
+        Tc = O.types(l + 1)
+        assert np.abs(host(fc_d) - fc_o)[Tc == 1].max(initial=0) < 1e-14
+        assert np.abs(host(gc_d)[: len(gc_o)] - gc_o).max(initial=0) < 1e-14
+        # interpolation
+        ec = np.where(Tc > 0, rng.uniform(-1, 1, cshape), 0.0)
+        out_d = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        S.prolong(l, dev(ec), out_d)
+        assert np.abs(host(out_d) - O.prolong(ec, l)).max() < 1e-14
+
+
+# --------------------------------------------------------------- solves
+def oracle_solution(P, n, nc, **kw):
+    O = oracle_for(P, n, nc, **kw)
+    u, norms, ok = O.solve(rtol=1e-13, max_cycles=60)
+    return O, u, norms
+
+
+@pytest.mark.parametrize("P,n,nc,kw", [(inputs.disk(), 65, 17, {}),
+                                       (inputs.flower(), 257, 33, {}),
+                                       (inputs.flower(), 257, 33, {"gamma": 2}),
+                                       (inputs.flower(), 257, 33, {"junction_sweeps": 0}),
+                                       (inputs.star(0), 257, 65, {}),
+                                       (inputs.star(2), 257, 33, {}),
+                                       (inputs.torus(), 33, 17, {"junction_radius": 3.0}),
+                                       (inputs.torus(), 65, 17, {})])
+def test_solve_matches_oracle(P, n, nc, kw):
+    S = solver_for(P, n, nc, rtol=1e-11, max_cycles=200, **kw)
+    set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    O, u_o, norms = oracle_solution(P, n, nc, **kw)
+    T = O.types(0)
+    assert st["converged"], st["rel"]
+    assert rel_maxdiff(host(u), u_o, T > 0) < PARITY
+    assert np.all(host(u)[T == 0] == 0)
+    # per-cycle convergence factors beside the oracle's (same algorithm)
+    k = min(6, st["cycles"], len(norms) - 1)
+    rel_o = norms[: k + 1] / norms[0]
+    assert np.allclose(st["rel"][1: k + 1], rel_o[1: k + 1], rtol=1e-6, atol=0), (st["rel"][: k + 1], rel_o)
+
+
+@pytest.mark.parametrize("P,n,nc", [(inputs.flower(), 257, 33), (inputs.torus(), 65, 17),
+                                    (inputs.disk(), 65, 17)])
+def test_mixed_precision_refinement_matches_oracle(P, n, nc):
+    S = solver_for(P, n, nc, rtol=1e-11, max_cycles=200, precision=1)
+    set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    assert st["converged"], st["rel"]
+    O, u_o, _ = oracle_solution(P, n, nc)
+    T = O.types(0)
+    assert rel_maxdiff(host(u), u_o, T > 0) < PARITY
+    # residual measured by the oracle (FP64) on the GPU's solution
+    f, g = problem_rhs(O, P, n)
+    O.set_rhs(f, g)
+    _, rn = O.defect(host(u))
+    assert rn <= 2e-11 * st["r0_norm"]
+
+
+def test_solve_host_equals_device():
+    P, n, nc = inputs.flower(), 257, 33
+    S = solver_for(P, n, nc)
+    f, g = set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    uh, sth = S.solve_host(f, g)
+    assert np.array_equal(uh, host(u))
+    assert sth["cycles"] == st["cycles"]
+
+
+def test_errors_are_reported():
+    gcmg = _gcmg()
+    X = inputs.coords(2, 65)
+    with pytest.raises(gcmg.GcmgError) as e:
+        gcmg.Solver(np.hypot(X[0], X[1]) - 0.995, 17)
+    assert e.value.status == gcmg.GCMG_E_GEOM
+    with pytest.raises(gcmg.GcmgError) as e:
+        gcmg.Solver(np.hypot(X[0], X[1]) - 0.5, 13)      # 64 is not 12 * 2^k
+    assert e.value.status == gcmg.GCMG_E_ARG
+    S = gcmg.Solver(np.hypot(X[0], X[1]) - 0.5, 17)
+    u = torch.zeros((65, 65), dtype=torch.float64, device="cuda")
+    with pytest.raises(gcmg.GcmgError) as e:
+        S.solve(u)                                        # no right-hand side yet
+    assert e.value.status == gcmg.GCMG_E_STATE
+
+
+def test_nan_rhs_reports_noconv():
+    P, n, nc = inputs.disk(), 65, 17
+    S = solver_for(P, n, nc, max_cycles=5)
+    f = P.f_grid(n)
+    f[32, 32] = np.nan
+    G = S.ghosts(0)
+    S.set_rhs(dev(f), dev(P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))))
+    u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    assert not st["converged"]
