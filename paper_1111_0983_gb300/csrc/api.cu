@@ -26,6 +26,16 @@ struct gcmg_ctx {
     bool rhs_set = false;
     unsigned long long *d_norm = nullptr;   // two slots: defect norm, rhs norm
     unsigned long long *h_norm = nullptr;   // pinned
+    // the solve loop as one CUDA graph: a device-side while loop over cycles
+    cudaStream_t gstream = nullptr;         // capture / launch stream (never the legacy one)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    double *d_rel = nullptr;                // rel[0..256]
+    double *d_r0 = nullptr;
+    int *d_m = nullptr;
+    bool use_graph = true;
+    long long graph_kernels = 0;            // kernels in one loop iteration
     // event timing of one fine-level kernel class during solves
     int timing_kind = -1;
     std::vector<cudaEvent_t> events;
@@ -114,6 +124,8 @@ void alloc_data(gcmg_ctx *c, int l, DevData<T> &D, bool grids) {
     const int64_t ne = (int64_t)L.ext_node.size();
     std::vector<T> ew = slot_major<double, T>(L.ext_w, ne, EMAX, EMAX);
     D.ew = upload<T>(c, ew.data(), ew.size());
+    std::vector<T> gtv(L.gt_val.begin(), L.gt_val.end());
+    D.gt_val = upload<T>(c, gtv.data(), gtv.size());
     ck(cudaStreamSynchronize(c->stream), "sync");
     if (grids) {
         D.u = dalloc<T>(c, L.nn);
@@ -140,12 +152,16 @@ void upload_geometry(gcmg_ctx *c, int l) {
     std::vector<int32_t> stn = slot_major<int32_t, int32_t>(L.stn, g.ng, KMAX, kslots(L.dim));
     g.gstn = upload<int32_t>(c, stn.data(), stn.size());
     g.red = upload<int32_t>(c, L.band_red.data(), L.band_red.size());
+    g.ntiles = (int)L.tiles.size();
+    g.tiles = upload<int32_t>(c, L.tiles.data(), L.tiles.size());
     g.black = upload<int32_t>(c, L.band_black.data(), L.band_black.size());
     g.enode = upload<int32_t>(c, L.ext_node.data(), L.ext_node.size());
     g.ecnt = upload<uint8_t>(c, L.ext_cnt.data(), L.ext_cnt.size());
     std::vector<int32_t> es = slot_major<int32_t, int32_t>(L.ext_src, g.ne, EMAX, EMAX);
     g.esrc = upload<int32_t>(c, es.data(), es.size());
     g.wave = L.ext_wave;
+    g.gt_ptr = upload<int32_t>(c, L.gt_ptr.data(), L.gt_ptr.size());
+    g.gt_col = upload<int32_t>(c, L.gt_col.data(), L.gt_col.size());
     if (l + 1 == (int)c->H.size()) {
         g.nunk = (int)L.unk_node.size();
         g.unk_node = upload<int32_t>(c, L.unk_node.data(), L.unk_node.size());
@@ -165,11 +181,9 @@ void free_tracked(gcmg_ctx *c, void *p) {
         }
 }
 
-// (re)uploads the junction-zone components of level l
-void upload_junction(gcmg_ctx *c, int l) {
-    const HostLevel::Junction &J = c->H[l].junction;
-    auto &z = c->G[l].jz;
-    int32_t **arrs[] = {&z.node_off, &z.zone_cnt, &z.lnode, &z.int_off, &z.red_cnt, &z.int_glob,
+// (re)uploads a local program of level l
+void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
+    int32_t **arrs[] = {&z.node_off, &z.wb_cnt, &z.lnode, &z.int_off, &z.red_cnt, &z.int_glob,
                         &z.int_me, &z.int_nb, &z.gh_off, &z.gh_me, &z.gh_q, &z.gh_stn,
                         &z.zred, &z.zblack, &z.zghost};
     for (int32_t **a : arrs) { free_tracked(c, *a); *a = nullptr; }
@@ -177,9 +191,10 @@ void upload_junction(gcmg_ctx *c, int l) {
     z.max_nodes = J.max_nodes;
     z.max_int = J.max_int;
     z.max_gh = J.max_gh;
+    z.nzred = z.nzblack = z.nzghost = 0;
     if (z.ncomp == 0) return;
     z.node_off = upload<int32_t>(c, J.node_off.data(), J.node_off.size());
-    z.zone_cnt = upload<int32_t>(c, J.zone_cnt.data(), J.zone_cnt.size());
+    z.wb_cnt = upload<int32_t>(c, J.wb_cnt.data(), J.wb_cnt.size());
     z.lnode = upload<int32_t>(c, J.lnode.data(), J.lnode.size());
     z.int_off = upload<int32_t>(c, J.int_off.data(), J.int_off.size());
     z.red_cnt = upload<int32_t>(c, J.red_cnt.data(), J.red_cnt.size());
@@ -245,15 +260,14 @@ void timer_mark(gcmg_ctx *c, int kind, int l) {
 }
 
 template <typename T>
-JunctionView<T> jview(const gcmg_ctx *c, int l, const LevelView<T> &v) {
-    const auto &z = c->G[l].jz;
-    JunctionView<T> J;
+LocalView<T> lview(const LocalDev &z, const LevelView<T> &v) {
+    LocalView<T> J;
     J.ncomp = z.ncomp;
     J.max_nodes = z.max_nodes;
     J.max_int = z.max_int;
     J.max_gh = z.max_gh;
     J.ng = v.ng;
-    J.node_off = z.node_off; J.zone_cnt = z.zone_cnt; J.lnode = z.lnode;
+    J.node_off = z.node_off; J.wb_cnt = z.wb_cnt; J.lnode = z.lnode;
     J.int_off = z.int_off; J.red_cnt = z.red_cnt; J.int_glob = z.int_glob; J.int_me = z.int_me; J.int_nb = z.int_nb;
     J.gh_off = z.gh_off; J.gh_me = z.gh_me; J.gh_q = z.gh_q; J.gh_stn = z.gh_stn;
     J.u = v.u; J.f = v.f; J.gg = v.gg; J.gc = v.gc; J.gw = v.gw;
@@ -267,21 +281,32 @@ template <typename T>
 void relax(gcmg_ctx *c, const LevelView<T> &v, int l, bool extra) {
     const int dim = c->p.dim;
     const DevGeom &g = c->G[l];
-    for (int colour = 0; colour < 2; colour++) {
+    if (dim == 2) {
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
-        launch_rb<T>(v, dim, colour, c->stream);
+        launch_rb_fused2d<T>(v, g.tiles, g.ntiles, c->stream);
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+    } else {
+        for (int colour = 0; colour < 2; colour++) {
+            timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+            launch_rb<T>(v, dim, colour, c->stream);
+            timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+        }
     }
-    launch_ghost_relax<T>(v, dim, c->stream);
-    if (!extra) return;
-    for (int k = 0; k < c->p.lambda; k++) {
-        launch_rb_list<T>(v, dim, g.red, g.nred, c->stream);
-        launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
+    if (extra && g.bz.ncomp > 0 && g.bz.in_smem) {
+        // ghost sweep + lambda band sweeps in one shared-memory launch
+        launch_local<T>(lview<T>(g.bz, v), dim, 1, c->p.lambda, c->stream);
+    } else {
         launch_ghost_relax<T>(v, dim, c->stream);
+        if (!extra) return;
+        for (int k = 0; k < c->p.lambda; k++) {
+            launch_rb_list<T>(v, dim, g.red, g.nred, c->stream);
+            launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
+            launch_ghost_relax<T>(v, dim, c->stream);
+        }
     }
     if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
         if (g.jz.in_smem) {
-            launch_junction<T>(jview<T>(c, l, v), dim, c->p.junction_sweeps, c->stream);
+            launch_local<T>(lview<T>(g.jz, v), dim, 0, c->p.junction_sweeps, c->stream);
         } else {
             for (int k = 0; k < c->p.junction_sweeps; k++) {
                 launch_rb_list<T>(v, dim, g.jz.zred, g.jz.nzred, c->stream);
@@ -292,18 +317,18 @@ void relax(gcmg_ctx *c, const LevelView<T> &v, int l, bool extra) {
     }
 }
 
-// checks the junction components of level l fit in shared memory
-void check_junction_fits(gcmg_ctx *c, int l) {
-    if (c->p.junction_sweeps <= 0 || c->G[l].jz.ncomp == 0) return;
-    LevelView<double> v = view<double>(c, l, c->D64[l]);
-    const size_t need = junction_smem_bytes<double>(jview<double>(c, l, v), c->p.dim);
+// decides whether a program's components fit in shared memory
+void check_program_fits(gcmg_ctx *c, LocalDev &z) {
+    if (z.ncomp == 0) return;
+    LevelView<double> dummy{};
+    const size_t need = local_smem_bytes<double>(lview<double>(z, dummy), c->p.dim);
     int dev_max = 0;
     ck(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
-    c->G[l].jz.in_smem = need <= (size_t)dev_max;
-    if (!c->G[l].jz.in_smem) return;    // relaxed from global memory instead
+    z.in_smem = need <= (size_t)dev_max && local_fits_registers(z.max_int);
+    if (!z.in_smem) return;    // relaxed from global memory instead
     // the attribute is per kernel: allow the device maximum once for all levels
-    junction_prepare<double>(c->p.dim, (size_t)dev_max);
-    junction_prepare<float>(c->p.dim, (size_t)dev_max);
+    local_prepare<double>(c->p.dim, (size_t)dev_max);
+    local_prepare<float>(c->p.dim, (size_t)dev_max);
 }
 
 // TGCS (Sec. 2.4) applied recursively: V (gamma = 1) or W (gamma = 2) cycle
@@ -322,10 +347,12 @@ void cycle(gcmg_ctx *c, int l) {
     timer_mark(c, GCMG_KERNEL_DEFECT, l);
     launch_defect<T>(v, dim, false, nullptr, c->stream);
     timer_mark(c, GCMG_KERNEL_DEFECT, l);
-    launch_extend<T>(D[l].r, c->G[l], D[l].ew, c->stream);
     const LevelView<T> vc = view<T>(c, l + 1, D[l + 1]);
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
-    launch_restrict<T>(v, vc, dim, D[l + 1].f, D[l + 1].gg, c->stream);
+    launch_restrict_interior<T>(v, vc, dim, D[l + 1].f, c->stream);
+    // defect extension (Sec. 2.6) and the transfer at the coarse ghosts, composed
+    launch_ghost_transfer<T>(D[l].r, c->G[l].gnode, c->G[l].gt_ptr, c->G[l].gt_col, D[l].gt_val, D[l + 1].gg,
+                             c->G[l + 1].ng, c->stream);
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
     ck(cudaMemsetAsync(D[l + 1].u, 0, c->H[l + 1].nn * sizeof(T), c->stream), "memset");
     const int gam = (l + 1 == last) ? 1 : c->p.gamma;
@@ -338,12 +365,22 @@ void cycle(gcmg_ctx *c, int l) {
 
 __global__ void k_rhs_norm(const uint8_t *type, const double *f, int64_t nn, const double *g, int ng,
                            unsigned long long *bits) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ double wmax[32];
     double v = 0.0;
-    if (i < nn && (type[i] & NODE_KIND) == NODE_IN) v = fabs(f[i]);
-    if (i < ng) v = fmax(v, fabs(g[i]));
-    if (v != v) v = __longlong_as_double(0x7ff0000000000000ull);
-    if (v > 0.0) atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn || i < ng;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < nn && (type[i] & NODE_KIND) == NODE_IN) v = fmax(v, fabs(f[i]));
+        if (i < ng) v = fmax(v, fabs(g[i]));
+        if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0 && v > 0.0) atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+    }
 }
 
 double read_norm(gcmg_ctx *c) {
@@ -360,6 +397,83 @@ double fine_defect_norm(gcmg_ctx *c) {
     ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
     launch_defect<double>(view<double>(c, 0, c->D64[0]), c->p.dim, false, c->d_norm, c->stream);
     return read_norm(c);
+}
+
+// end of one loop iteration: records rel[m] and sets the while condition
+__global__ void k_loop_check(cudaGraphConditionalHandle h, const unsigned long long *bits, const double *r0,
+                             double *rel, int *m, double rtol, int max_cycles) {
+    const double nr = __longlong_as_double((long long)*bits);
+    const int k = *m + 1;
+    *m = k;
+    const double v = nr / *r0;
+    if (k <= 256) rel[k] = v;
+    const bool go = (v == v) && !isinf(v) && v > rtol && k < max_cycles;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// one iteration of the solve loop: a cycle (plain) or a refinement step
+// (mixed), then the FP64 defect and its norm
+void loop_body(gcmg_ctx *c) {
+    const DevGeom &g0 = c->G[0];
+    const HostLevel &L0 = c->H[0];
+    if (c->p.precision == 0) {
+        cycle<double>(c, 0);
+    } else {
+        DevData<float> &F0 = c->D32[0];
+        launch_defect_to_f32(g0, c->D64[0].r, F0.f, F0.gg, c->stream);
+        ck(cudaMemsetAsync(F0.u, 0, L0.nn * sizeof(float), c->stream), "memset");   // e = 0
+        cycle<float>(c, 0);
+        launch_add_correction(g0, c->D64[0].u, F0.u, c->stream);
+    }
+    ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
+    launch_defect<double>(view<double>(c, 0, c->D64[0]), c->p.dim, false, c->d_norm, c->stream);
+}
+
+void destroy_graph(gcmg_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+}
+
+void build_graph(gcmg_ctx *c) {
+    destroy_graph(c);
+    if (!c->gstream) ck(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!c->ev_in) ck(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+    if (!c->ev_out) ck(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+    ck(cudaGraphCreate(&c->graph, 0), "cudaGraphCreate");
+    cudaGraphConditionalHandle h;
+    ck(cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault), "conditional handle");
+    alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_raw);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    ck(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &np), "cudaGraphAddNode");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t saved = c->stream;
+    c->stream = c->gstream;
+    ck(cudaStreamBeginCaptureToGraph(c->gstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+       "begin capture");
+    const long long before = g_launches.load();
+    try {
+        loop_body(c);
+        k_loop_check<<<1, 1, 0, c->gstream>>>(h, c->d_norm, c->d_r0, c->d_rel, c->d_m, c->p.rtol, c->p.max_cycles);
+        g_launches++;
+        c->graph_kernels = g_launches.load() - before;
+        g_launches -= c->graph_kernels;   // counted when executed
+    } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(c->gstream, &dummy);
+        c->stream = saved;
+        throw;
+    }
+    c->stream = saved;
+    cudaGraph_t captured;
+    ck(cudaStreamEndCapture(c->gstream, &captured), "end capture");
+    ck(cudaGraphInstantiate(&c->gexec, c->graph, 0), "cudaGraphInstantiate");
 }
 
 gcmg_status fail(gcmg_ctx *c, gcmg_status s, const std::string &m) {
@@ -443,6 +557,12 @@ gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *strea
         build_hierarchy(p->dim, p->n, p->n_coarse, phi.data(), p->delta_over_h, c->H);
         const int nl = (int)c->H.size();
         for (int l = 0; l < nl; l++) upload_geometry(c, l);
+        if (p->dim == 2)
+            for (int l = 0; l < nl; l++) {
+                build_boundary_blocks(c->H[l], p->lambda, 32);
+                upload_program(c, c->H[l].boundary, c->G[l].bz);
+                check_program_fits(c, c->G[l].bz);
+            }
         c->D64.resize(nl);
         for (int l = 0; l < nl; l++) alloc_data<double>(c, l, c->D64[l], p->precision == 0 || l == 0);
         if (p->precision == 1) {
@@ -450,6 +570,9 @@ gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *strea
             for (int l = 0; l < nl; l++) alloc_data<float>(c, l, c->D32[l], true);
         }
         c->d_norm = dalloc<unsigned long long>(c, 2);
+        c->d_rel = dalloc<double>(c, 257);
+        c->d_r0 = dalloc<double>(c, 1);
+        c->d_m = dalloc<int>(c, 1);
         ck(cudaMallocHost((void **)&c->h_norm, 2 * sizeof(unsigned long long)), "cudaMallocHost");
         ck(cudaStreamSynchronize(c->stream), "sync");
         return GCMG_OK;
@@ -459,6 +582,10 @@ gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *strea
 void gcmg_destroy(gcmg_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    destroy_graph(c);
+    if (c->gstream) { cudaStreamSynchronize(c->gstream); cudaStreamDestroy(c->gstream); }
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
     if (c->h_norm) cudaFreeHost(c->h_norm);
@@ -519,11 +646,12 @@ gcmg_status gcmg_set_bc_types(gcmg_ctx *c, int l, const uint8_t *types) {
     GCMG_GUARD(c, {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         HostLevel &L = c->H[l];
+        destroy_graph(c);   // the junction arrays are reallocated below
         for (int64_t q = 0; q < L.ng(); q++) L.bc[q] = types[q] ? 1 : 0;
         if (l + 1 == (int)c->H.size()) build_coarse_inverse(L);
         build_junction(L, c->p.junction_radius);
-        upload_junction(c, l);
-        check_junction_fits(c, l);
+        upload_program(c, L.junction, c->G[l].jz);
+        check_program_fits(c, c->G[l].jz);
         upload_ghost_data<double>(c, l, c->D64[l], false);
         if (!c->D32.empty()) upload_ghost_data<float>(c, l, c->D32[l], false);
         return GCMG_OK;
@@ -552,20 +680,17 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         const HostLevel &L0 = c->H[0];
         const DevGeom &g0 = c->G[0];
-        double *own_u = c->D64[0].u;
-        c->D64[0].u = u_dev;   // solve in place in the caller's array (same layout)
-        struct Restore {
-            gcmg_ctx *c;
-            double *u;
-            ~Restore() { c->D64[0].u = u; }
-        } restore{c, own_u};
-        launch_mask_unknowns<double>(g0.type, u_dev, L0.nn, c->stream);
+        double *u = c->D64[0].u;   // internal buffer: the captured graph uses fixed pointers
+        if (u_dev != u)
+            ck(cudaMemcpyAsync(u, u_dev, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u in");
+        launch_mask_unknowns<double>(g0.type, u, L0.nn, c->stream);
         // ||r0|| = ||(f, g)||
         ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
         {
             const int64_t cnt = std::max<int64_t>(L0.nn, L0.ng());
-            k_rhs_norm<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn,
-                                                                             c->D64[0].gg, g0.ng, c->d_norm);
+            const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 4096);
+            k_rhs_norm<<<nb, 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn, c->D64[0].gg, g0.ng, c->d_norm);
+            g_launches++;
         }
         check_launch();
         const double r0 = read_norm(c);
@@ -577,23 +702,37 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
         st.rel[0] = rel;
         int m = 0;
         bool ok = (r0 == 0.0) || rel <= c->p.rtol;
-        while (!ok && m < c->p.max_cycles) {
-            if (c->p.precision == 0) {
-                cycle<double>(c, 0);
-            } else {
-                DevData<float> &F0 = c->D32[0];
-                launch_defect_to_f32(g0, c->D64[0].r, F0.f, F0.gg, c->stream);
-                ck(cudaMemsetAsync(F0.u, 0, L0.nn * sizeof(float), c->stream), "memset");   // e = 0
-                cycle<float>(c, 0);
-                launch_add_correction(g0, u_dev, F0.u, c->stream);
-            }
-            check_launch();
-            m++;
-            rel = fine_defect_norm(c) / r0;
-            if (m <= 256) st.rel[m] = rel;
-            if (!(rel == rel) || std::isinf(rel)) break;
+        if (!ok && c->use_graph && c->timing_kind < 0) {
+            if (!c->gexec) build_graph(c);
+            const int zero = 0;
+            ck(cudaMemcpyAsync(c->d_r0, &r0, sizeof(double), cudaMemcpyHostToDevice, c->stream), "r0");
+            ck(cudaMemcpyAsync(c->d_m, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream), "m");
+            ck(cudaEventRecord(c->ev_in, c->stream), "event");
+            ck(cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "wait");
+            ck(cudaGraphLaunch(c->gexec, c->gstream), "cudaGraphLaunch");
+            ck(cudaEventRecord(c->ev_out, c->gstream), "event");
+            ck(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "wait");
+            ck(cudaMemcpyAsync(&m, c->d_m, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "m");
+            ck(cudaStreamSynchronize(c->stream), "sync");
+            g_launches += c->graph_kernels * m;
+            const int kept = std::min(m, 256);
+            ck(cudaMemcpy(&st.rel[1], c->d_rel + 1, kept * sizeof(double), cudaMemcpyDeviceToHost), "rel");
+            rel = st.rel[kept];
             ok = rel <= c->p.rtol;
+        } else {
+            while (!ok && m < c->p.max_cycles) {
+                loop_body(c);
+                check_launch();
+                m++;
+                rel = read_norm(c) / r0;
+                if (m <= 256) st.rel[m] = rel;
+                if (!(rel == rel) || std::isinf(rel)) break;
+                ok = rel <= c->p.rtol;
+            }
         }
+        if (u_dev != u)
+            ck(cudaMemcpyAsync(u_dev, u, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u out");
+        ck(cudaStreamSynchronize(c->stream), "sync");
         st.cycles = m;
         st.converged = ok ? 1 : 0;
         st.rel_residual = rel;
@@ -730,7 +869,7 @@ gcmg_status gcmg_junction_zone(const gcmg_ctx *c, int l, uint8_t *mask) {
     std::memset(mask, 0, L.nn);
     const auto &J = L.junction;
     for (int k = 0; k < J.ncomp(); k++)
-        for (int i = J.node_off[k]; i < J.node_off[k] + J.zone_cnt[k]; i++) mask[J.lnode[i]] = 1;
+        for (int i = J.node_off[k]; i < J.node_off[k] + J.wb_cnt[k]; i++) mask[J.lnode[i]] = 1;
     return GCMG_OK;
 }
 

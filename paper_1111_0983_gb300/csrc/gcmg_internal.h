@@ -13,6 +13,8 @@
 namespace gcmg {
 
 constexpr int KMAX = 27;   // ghost stencil slots (3^3)
+constexpr int TILE_R = 16; // 2D interior tiles: rows (axis 0)
+constexpr int TILE_C = 64; //                    columns (axis 1, contiguous)
 constexpr int EMAX = 6;    // extension sources (2 d)
 
 enum : uint8_t { NODE_OUT = 0, NODE_IN = 1, NODE_GHOST = 2, NODE_KIND = 3, NODE_BAND = 4 };
@@ -20,6 +22,20 @@ enum : uint8_t { STENCIL_QUAD = 0, STENCIL_LIN = 1, STENCIL_CORNER = 2, STENCIL_
 
 struct GeomError {
     std::string msg;
+};
+
+// A set of independent components relaxed in shared memory by one CTA each.
+// Component c stages the nodes lnode[node_off[c] .. node_off[c+1]) -- first
+// the wb_cnt[c] nodes it writes back, then the other nodes it updates, then
+// read-only nodes -- and runs: an optional ghost sweep, then reps x (red
+// inside nodes, black inside nodes, Jacobi ghosts) on its updated nodes.
+struct LocalProgram {
+    std::vector<int32_t> node_off{0}, wb_cnt, lnode;
+    std::vector<int32_t> int_off{0}, red_cnt, int_glob, int_me, int_nb;   // nb: 2 dim per entry
+    std::vector<int32_t> gh_off{0}, gh_me, gh_q, gh_stn;                  // stn: 3^dim per entry
+    std::vector<int32_t> zred, zblack, zghost;   // union over components (global fallback)
+    int max_nodes = 0, max_int = 0, max_gh = 0;
+    int ncomp() const { return (int)wb_cnt.size(); }
 };
 
 // Geometry of one level, built on the host from phi (Sec. 2.2 - 2.6, 3.2).
@@ -40,23 +56,22 @@ struct HostLevel {
     std::vector<uint8_t> bc;            // 0 Dirichlet, 1 Neumann
     // inside nodes of the extra-sweep band, split by colour
     std::vector<int32_t> band_red, band_black;
+    // 2D tiles (TILE_R x TILE_C) holding inside nodes, packed (tile row << 16 | tile column)
+    std::vector<int32_t> tiles;
     // defect extension of this level (before restricting to the next coarser one)
     std::vector<int32_t> ext_node;      // ordered by upwind wavefront
     std::vector<uint8_t> ext_cnt;
     std::vector<int32_t> ext_src;       // ne * EMAX
     std::vector<double> ext_w;          // ne * EMAX
     std::vector<int> ext_wave;          // wavefront offsets into ext_node (size nwave + 1)
-    // junction zone (depends on bc): independent components, each closed under
-    // the reads of its updates; local node lists hold the zone nodes first,
-    // then the halo nodes they read
-    struct Junction {
-        std::vector<int32_t> node_off{0}, zone_cnt, lnode;
-        std::vector<int32_t> int_off{0}, red_cnt, int_glob, int_me, int_nb;   // nb: 2 dim per entry
-        std::vector<int32_t> gh_off{0}, gh_me, gh_q, gh_stn;                  // stn: 3^dim per entry
-        std::vector<int32_t> zred, zblack, zghost;   // whole zone: inside nodes by colour, ghost numbers
-        int max_nodes = 0, max_int = 0, max_gh = 0;
-        int ncomp() const { return (int)zone_cnt.size(); }
-    } junction;
+    // extension followed by the partial transfer at the coarse ghosts, as one
+    // sparse map from this level's ghost defects to the next level's ghost
+    // data (CSR over coarse ghosts; columns are this level's ghost numbers)
+    std::vector<int32_t> gt_ptr, gt_col;
+    std::vector<double> gt_val;
+    // shared-memory relaxation programs: the junction zone (depends on bc)
+    // and, in 2D, the boundary blocks of the lambda extra sweeps
+    LocalProgram junction, boundary;
     // coarsest level: unknowns (node, ghost number or -1) and dense inverse
     std::vector<int32_t> unk_node, unk_ghost;
     std::vector<double> Ainv;           // nunk * nunk, row major
@@ -67,12 +82,29 @@ struct HostLevel {
 // Builds all levels (throws GeomError).  phi: fine grid, n^dim values.
 void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
                      std::vector<HostLevel> &levels);
+// Partial-transfer weights (Sec. 2.5) at the fine image p of a coarse node over
+// the inside set (interior) or its complement; wt[3^dim], axis 0 slowest.
+bool partial_transfer_weights(const HostLevel &F, int64_t p, bool interior, double *wt);
 // Dense inverse of the coarsest system with the level's current bc (throws GeomError).
 void build_coarse_inverse(HostLevel &L);
 // Junction zone of the level's current bc (radius in h).
 void build_junction(HostLevel &L, double radius);
+// 2D boundary blocks of the extra sweeps: block x block tiles with a halo
+// covering the dependency cone of one ghost sweep + lambda (R, B, G) sweeps.
+void build_boundary_blocks(HostLevel &L, int lambda, int block);
 
 // --------------------------------------------------------------- device side
+// A LocalProgram on the device.
+struct LocalDev {
+    int ncomp = 0, max_nodes = 0, max_int = 0, max_gh = 0;
+    int32_t *node_off = nullptr, *wb_cnt = nullptr, *lnode = nullptr;
+    int32_t *int_off = nullptr, *red_cnt = nullptr, *int_glob = nullptr, *int_me = nullptr, *int_nb = nullptr;
+    int32_t *gh_off = nullptr, *gh_me = nullptr, *gh_q = nullptr, *gh_stn = nullptr;
+    int nzred = 0, nzblack = 0, nzghost = 0;
+    int32_t *zred = nullptr, *zblack = nullptr, *zghost = nullptr;
+    bool in_smem = true;       // false: relaxed by per-sweep launches over the union lists
+};
+
 // Integer geometry of a level on the device (shared by both precisions).
 struct DevGeom {
     int dim = 2, n = 0;
@@ -82,21 +114,15 @@ struct DevGeom {
     int32_t *gnode = nullptr;    // ng
     int32_t *gstn = nullptr;     // KMAX * ng, slot major
     int32_t *red = nullptr, *black = nullptr;
+    int ntiles = 0;
+    int32_t *tiles = nullptr;    // active 2D interior tiles
     int32_t *enode = nullptr;    // ne
     uint8_t *ecnt = nullptr;     // ne
     int32_t *esrc = nullptr;     // EMAX * ne, slot major
+    int32_t *gt_ptr = nullptr, *gt_col = nullptr;   // ghost transfer to the next level
     int32_t *unk_node = nullptr, *unk_ghost = nullptr;
     std::vector<int> wave;       // host copy of the wavefront offsets
-    // junction zone components (reallocated when the bc changes)
-    struct {
-        int ncomp = 0, max_nodes = 0, max_int = 0, max_gh = 0;
-        int32_t *node_off = nullptr, *zone_cnt = nullptr, *lnode = nullptr;
-        int32_t *int_off = nullptr, *red_cnt = nullptr, *int_glob = nullptr, *int_me = nullptr, *int_nb = nullptr;
-        int32_t *gh_off = nullptr, *gh_me = nullptr, *gh_q = nullptr, *gh_stn = nullptr;
-        int nzred = 0, nzblack = 0, nzghost = 0;
-        int32_t *zred = nullptr, *zblack = nullptr, *zghost = nullptr;
-        bool in_smem = true;       // false: relaxed by per-sweep launches over the lists
-    } jz;
+    LocalDev jz, bz;             // junction zone / boundary blocks
 };
 
 // Floating-point data of a level in precision T.
@@ -108,6 +134,7 @@ struct DevData {
     T *gg = nullptr;     // ng boundary data (level 0) or restricted boundary defect
     T *gtmp = nullptr;   // ng new ghost values of a Jacobi sweep
     T *ew = nullptr;     // EMAX * ne extension weights, slot major
+    T *gt_val = nullptr; // ghost transfer weights to the next level
     T *Ainv = nullptr;   // nunk * nunk (coarsest level)
 };
 
@@ -132,11 +159,11 @@ struct LevelView {
     T *gtmp;
 };
 
-// Kernel view of a level's junction-zone components in precision T.
+// Kernel view of a LocalDev program in precision T.
 template <typename T>
-struct JunctionView {
+struct LocalView {
     int ncomp, max_nodes, max_int, max_gh, ng;
-    const int32_t *node_off, *zone_cnt, *lnode;
+    const int32_t *node_off, *wb_cnt, *lnode;
     const int32_t *int_off, *red_cnt, *int_glob, *int_me, *int_nb;
     const int32_t *gh_off, *gh_me, *gh_q, *gh_stn;
     T *u;

@@ -35,13 +35,21 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// block-wide max of |v| then one atomic per warp
+// block-wide max of |v| (all threads of the block must call), one atomic per block
 __device__ __forceinline__ void reduce_norm(unsigned long long *bits, double v) {
     if (!bits) return;
+    __shared__ double wmax[32];
     double a = fabs(v);
     if (a != a) a = __longlong_as_double(0x7ff0000000000000ull);
     a = warp_max(a);
-    if ((threadIdx.x & 31) == 0 && a > 0.0) atomic_max_abs(bits, a);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) wmax[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        a = (int)threadIdx.x < nw ? wmax[threadIdx.x] : 0.0;
+        a = warp_max(a);
+        if (threadIdx.x == 0 && a > 0.0) atomic_max_abs(bits, a);
+    }
 }
 
 template <int D>
@@ -82,6 +90,59 @@ __global__ void k_rb_interior(LevelView<T> v, int color) {
     if ((v.type[p] & NODE_KIND) != NODE_IN) return;
     const T s = v.h2 * v.f[p] + neighbour_sum<T, D>(v.u, p, v.s0, v.s1);
     v.u[p] = s * (T)(1.0 / (2 * D));
+}
+
+// Both colours in one pass over the active 2D tiles (TILE_R x TILE_C nodes,
+// axis 1 contiguous): u is staged with a 2-node halo, f and the node types
+// with a 1-node halo; red nodes are updated on the tile and its 1-node halo
+// (the values the neighbouring tiles compute for their own nodes), then black
+// nodes on the tile, and the tile's inside nodes are stored.  Equal to a red
+// half-sweep followed by a black half-sweep over the whole grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rb_fused2d(LevelView<T> v, const int32_t *__restrict__ tiles) {
+    constexpr int UR = TILE_R + 4, UC = TILE_C + 4, FR = TILE_R + 2, FC = TILE_C + 2;
+    __shared__ T su[UR][UC];
+    __shared__ T sf[FR][FC];
+    __shared__ uint8_t sk[FR][FC];
+    const int tile = tiles[blockIdx.x];
+    const int i0 = (tile >> 16) * TILE_R, j0 = (tile & 0xffff) * TILE_C;
+    const int n = v.n;
+    for (int idx = threadIdx.x; idx < UR * UC; idx += blockDim.x) {
+        const int r = idx / UC, cc = idx - r * UC;
+        const int gi = i0 - 2 + r, gj = j0 - 2 + cc;
+        su[r][cc] = (gi >= 0 && gi < n && gj >= 0 && gj < n) ? v.u[(int64_t)gi * v.s0 + gj] : (T)0;
+    }
+    for (int idx = threadIdx.x; idx < FR * FC; idx += blockDim.x) {
+        const int r = idx / FC, cc = idx - r * FC;
+        const int gi = i0 - 1 + r, gj = j0 - 1 + cc;
+        const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+        const int64_t p = (int64_t)gi * v.s0 + gj;
+        const uint8_t k = in ? (uint8_t)(v.type[p] & NODE_KIND) : (uint8_t)NODE_OUT;
+        sk[r][cc] = k;
+        sf[r][cc] = (k == NODE_IN) ? v.h2 * v.f[p] : (T)0;
+    }
+    __syncthreads();
+    // red (even index sum) on the tile and its 1-node halo
+    for (int idx = threadIdx.x; idx < FR * FC; idx += blockDim.x) {
+        const int r = idx / FC, cc = idx - r * FC;
+        if (sk[r][cc] != NODE_IN || (((i0 - 1 + r) + (j0 - 1 + cc)) & 1)) continue;
+        const int ur = r + 1, uc = cc + 1;
+        su[ur][uc] = (sf[r][cc] + su[ur - 1][uc] + su[ur + 1][uc] + su[ur][uc - 1] + su[ur][uc + 1]) * (T)0.25;
+    }
+    __syncthreads();
+    // black on the tile
+    for (int idx = threadIdx.x; idx < TILE_R * TILE_C; idx += blockDim.x) {
+        const int r = idx / TILE_C, cc = idx - r * TILE_C;
+        if (sk[r + 1][cc + 1] != NODE_IN || (((i0 + r) + (j0 + cc)) & 1) == 0) continue;
+        const int ur = r + 2, uc = cc + 2;
+        su[ur][uc] = (sf[r + 1][cc + 1] + su[ur - 1][uc] + su[ur + 1][uc] + su[ur][uc - 1] + su[ur][uc + 1]) * (T)0.25;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TILE_R * TILE_C; idx += blockDim.x) {
+        const int r = idx / TILE_C, cc = idx - r * TILE_C;
+        if (sk[r + 1][cc + 1] != NODE_IN) continue;
+        v.u[(int64_t)(i0 + r) * v.s0 + (j0 + cc)] = su[r + 2][cc + 2];
+    }
 }
 
 // Same update over a compact list of band nodes of one colour (Sec. 3.2).
@@ -132,61 +193,103 @@ __global__ void k_ghost_store(LevelView<T> v) {
     v.u[v.gnode[q]] = v.gtmp[q];
 }
 
-// ------------------------------------------------------- junction relaxation
-// mu_J sweeps (red, black, Jacobi ghosts) on one junction-zone component per
-// CTA, entirely in shared memory: the component's zone and halo values, f at
-// its inside nodes, g, mu dt and the ghost weights are staged once, the sweeps
-// run on the staged copy, and the zone values are written back.  Components
-// are closed under the reads of their updates, so CTAs are independent.
+// ------------------------------------------------- shared-memory programs
+// One CTA per component of a LocalProgram.  The component's node values, the
+// ghost weights, stencil slots, g and mu dt are staged in shared memory; each
+// thread keeps its inside-node entries (slot, neighbour slots, h^2 f) in
+// registers.  Then an optional ghost sweep and reps x (red, black, Jacobi
+// ghosts) run on the staged copy, and the write-back nodes are stored.  Used
+// for the junction zones (components closed under their reads) and the 2D
+// boundary blocks (halo = dependency cone of the sweeps, so the written values
+// equal those of the global sweeps).
+constexpr int LOCAL_THREADS = 512;
+constexpr int LOCAL_EPT = 4;     // inside entries per thread and colour
+
 template <typename T, int D>
-__global__ void k_junction(JunctionView<T> J, int sweeps) {
+__global__ void __launch_bounds__(LOCAL_THREADS) k_local(LocalView<T> J, int lead_ghost, int reps) {
     constexpr int K = D == 2 ? 9 : 27;
     extern __shared__ __align__(16) unsigned char smem_j[];
     const int c = blockIdx.x;
     const int n0 = J.node_off[c], nl = J.node_off[c + 1] - n0;
-    const int i0 = J.int_off[c], ni = J.int_off[c + 1] - i0, nred = J.red_cnt[c];
+    const int i0 = J.int_off[c], ni = J.int_off[c + 1] - i0, nred = J.red_cnt[c], nblk = ni - nred;
     const int g0 = J.gh_off[c], ngh = J.gh_off[c + 1] - g0;
     T *val = reinterpret_cast<T *>(smem_j);
-    T *fi = val + J.max_nodes;
-    T *gw = fi + J.max_int;          // K per ghost
+    T *gw = val + J.max_nodes;       // K per ghost
     T *gv = gw + (size_t)K * J.max_gh;
     T *gcv = gv + J.max_gh;
     T *gt = gcv + J.max_gh;
+    int *gst = reinterpret_cast<int *>(gt + J.max_gh);   // K per ghost
+    int *gme = gst + (size_t)K * J.max_gh;
     for (int i = threadIdx.x; i < nl; i += blockDim.x) val[i] = J.u[J.lnode[n0 + i]];
-    for (int i = threadIdx.x; i < ni; i += blockDim.x) fi[i] = J.h2 * J.f[J.int_glob[i0 + i]];
     for (int e = threadIdx.x; e < ngh; e += blockDim.x) {
         const int q = J.gh_q[g0 + e];
         gv[e] = J.gg[q];
         gcv[e] = J.gc[q];
-        for (int k = 0; k < K; k++) gw[e * K + k] = J.gw[(int64_t)k * J.ng + q];
+        gme[e] = J.gh_me[g0 + e];
+        for (int k = 0; k < K; k++) {
+            gw[e * K + k] = J.gw[(int64_t)k * J.ng + q];
+            gst[e * K + k] = J.gh_stn[(size_t)(g0 + e) * K + k];
+        }
     }
+    // this thread's inside entries: e-th red entry is threadIdx.x + e * blockDim.x
+    int rme[LOCAL_EPT], rnb[LOCAL_EPT][2 * D], bme[LOCAL_EPT], bnb[LOCAL_EPT][2 * D];
+    T rf[LOCAL_EPT], bf[LOCAL_EPT];
+#pragma unroll
+    for (int e = 0; e < LOCAL_EPT; e++) {
+        const int ir = threadIdx.x + e * blockDim.x, ib = nred + threadIdx.x + e * blockDim.x;
+        rme[e] = -1;
+        bme[e] = -1;
+        if (ir < nred) {
+            rme[e] = J.int_me[i0 + ir];
+            rf[e] = J.h2 * J.f[J.int_glob[i0 + ir]];
+#pragma unroll
+            for (int a = 0; a < 2 * D; a++) rnb[e][a] = J.int_nb[(size_t)(i0 + ir) * (2 * D) + a];
+        }
+        if (ib < ni) {
+            bme[e] = J.int_me[i0 + ib];
+            bf[e] = J.h2 * J.f[J.int_glob[i0 + ib]];
+#pragma unroll
+            for (int a = 0; a < 2 * D; a++) bnb[e][a] = J.int_nb[(size_t)(i0 + ib) * (2 * D) + a];
+        }
+    }
+    (void)nblk;
     __syncthreads();
     const T inv = (T)(1.0 / (2 * D));
-    for (int it = 0; it < sweeps; it++) {
-        for (int colour = 0; colour < 2; colour++) {
-            const int b = colour ? nred : 0, e = colour ? ni : nred;
-            for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-                const int *nb = J.int_nb + (size_t)(i0 + i) * (2 * D);
-                T s = fi[i];
-#pragma unroll
-                for (int a = 0; a < 2 * D; a++) s += val[nb[a]];
-                val[J.int_me[i0 + i]] = s * inv;
-            }
-            __syncthreads();
-        }
+    auto ghost_sweep = [&]() {
         for (int e = threadIdx.x; e < ngh; e += blockDim.x) {
-            const int *st = J.gh_stn + (size_t)(g0 + e) * K;
             T s = 0;
 #pragma unroll
-            for (int k = 0; k < K; k++) s += gw[e * K + k] * val[st[k]];
-            gt[e] = val[J.gh_me[g0 + e]] + gcv[e] * (gv[e] - s);
+            for (int k = 0; k < K; k++) s += gw[e * K + k] * val[gst[e * K + k]];
+            gt[e] = val[gme[e]] + gcv[e] * (gv[e] - s);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < ngh; e += blockDim.x) val[J.gh_me[g0 + e]] = gt[e];
+        for (int e = threadIdx.x; e < ngh; e += blockDim.x) val[gme[e]] = gt[e];
         __syncthreads();
+    };
+    if (lead_ghost) ghost_sweep();
+    for (int it = 0; it < reps; it++) {
+#pragma unroll
+        for (int e = 0; e < LOCAL_EPT; e++)
+            if (rme[e] >= 0) {
+                T s = rf[e];
+#pragma unroll
+                for (int a = 0; a < 2 * D; a++) s += val[rnb[e][a]];
+                val[rme[e]] = s * inv;
+            }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < LOCAL_EPT; e++)
+            if (bme[e] >= 0) {
+                T s = bf[e];
+#pragma unroll
+                for (int a = 0; a < 2 * D; a++) s += val[bnb[e][a]];
+                val[bme[e]] = s * inv;
+            }
+        __syncthreads();
+        ghost_sweep();
     }
-    const int nz = J.zone_cnt[c];
-    for (int i = threadIdx.x; i < nz; i += blockDim.x) J.u[J.lnode[n0 + i]] = val[i];
+    const int nw = J.wb_cnt[c];
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) J.u[J.lnode[n0 + i]] = val[i];
 }
 
 // ------------------------------------------------------------------ defect
@@ -372,6 +475,19 @@ __global__ void k_restrict_ghost(LevelView<T> F, LevelView<T> C, T *__restrict__
     gc[q] = partial_transfer<T, D>(F, p, false);
 }
 
+// extension + partial transfer at the coarse ghosts as one sparse map from
+// the fine ghost defects (read from the fine defect grid)
+template <typename T>
+__global__ void k_ghost_transfer(const T *__restrict__ rf, const int32_t *__restrict__ fgnode,
+                                 const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                 const T *__restrict__ val, T *__restrict__ gc, int ngc) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ngc) return;
+    T s = 0;
+    for (int j = ptr[q]; j < ptr[q + 1]; j++) s += val[j] * rf[fgnode[col[j]]];
+    gc[q] = s;
+}
+
 // ------------------------------------------------------------ interpolation
 // Bilinear / trilinear interpolation onto Omega_h u Gamma_h (Sec. 2.6),
 // weights renormalised over the parents in Omega_2h u Gamma_2h.
@@ -481,6 +597,13 @@ void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s) {
 }
 
 template <typename T>
+void launch_rb_fused2d(const LevelView<T> &v, const int32_t *tiles, int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    g_launches++;
+    k_rb_fused2d<T><<<ntiles, 256, 0, s>>>(v, tiles);
+}
+
+template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s) {
     if (cnt <= 0) return;
     g_launches++;
@@ -527,6 +650,13 @@ void launch_extend(T *r, const DevGeom &g, const T *ew, cudaStream_t s) {
 }
 
 template <typename T>
+void launch_restrict_interior(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, cudaStream_t s) {
+    g_launches++;
+    if (dim == 2) k_restrict_interior<T, 2><<<blocks_for(C.nn), kThreads, 0, s>>>(F, C, fc);
+    else k_restrict_interior<T, 3><<<blocks_for(C.nn), kThreads, 0, s>>>(F, C, fc);
+}
+
+template <typename T>
 void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, T *gc, cudaStream_t s) {
     g_launches += C.ng > 0 ? 2 : 1;
     if (dim == 2) {
@@ -536,6 +666,14 @@ void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *f
         k_restrict_interior<T, 3><<<blocks_for(C.nn), kThreads, 0, s>>>(F, C, fc);
         if (C.ng > 0) k_restrict_ghost<T, 3><<<blocks_for(C.ng), kThreads, 0, s>>>(F, C, gc);
     }
+}
+
+template <typename T>
+void launch_ghost_transfer(const T *rf, const int32_t *fgnode, const int32_t *ptr, const int32_t *col, const T *val,
+                           T *gc, int ngc, cudaStream_t s) {
+    if (ngc <= 0) return;
+    g_launches++;
+    k_ghost_transfer<T><<<blocks_for(ngc), kThreads, 0, s>>>(rf, fgnode, ptr, col, val, gc, ngc);
 }
 
 template <typename T>
@@ -557,25 +695,27 @@ void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv,
 }
 
 template <typename T>
-size_t junction_smem_bytes(const JunctionView<T> &J, int dim) {
+size_t local_smem_bytes(const LocalView<T> &J, int dim) {
     const int K = dim == 2 ? 9 : 27;
-    return sizeof(T) * ((size_t)J.max_nodes + J.max_int + (size_t)(K + 3) * J.max_gh);
+    return sizeof(T) * ((size_t)J.max_nodes + (size_t)(K + 3) * J.max_gh) + sizeof(int) * (size_t)(K + 1) * J.max_gh;
 }
 
+bool local_fits_registers(int max_int_per_colour) { return max_int_per_colour <= LOCAL_THREADS * LOCAL_EPT; }
+
 template <typename T>
-void launch_junction(const JunctionView<T> &J, int dim, int sweeps, cudaStream_t s) {
-    if (J.ncomp <= 0 || sweeps <= 0) return;
+void launch_local(const LocalView<T> &J, int dim, int lead_ghost, int reps, cudaStream_t s) {
+    if (J.ncomp <= 0 || (reps <= 0 && !lead_ghost)) return;
     g_launches++;
-    const size_t smem = junction_smem_bytes(J, dim);
-    if (dim == 2) k_junction<T, 2><<<J.ncomp, 512, smem, s>>>(J, sweeps);
-    else k_junction<T, 3><<<J.ncomp, 512, smem, s>>>(J, sweeps);
+    const size_t smem = local_smem_bytes(J, dim);
+    if (dim == 2) k_local<T, 2><<<J.ncomp, LOCAL_THREADS, smem, s>>>(J, lead_ghost, reps);
+    else k_local<T, 3><<<J.ncomp, LOCAL_THREADS, smem, s>>>(J, lead_ghost, reps);
 }
 
 template <typename T>
-void junction_prepare(int dim, size_t smem) {
+void local_prepare(int dim, size_t smem) {
     // opt in to large dynamic shared memory once per precision / dimension
-    if (dim == 2) cudaFuncSetAttribute(k_junction<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else cudaFuncSetAttribute(k_junction<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dim == 2) cudaFuncSetAttribute(k_local<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else cudaFuncSetAttribute(k_local<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T>
@@ -598,18 +738,22 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
 #define GCMG_INSTANTIATE(T)                                                                              \
     template void launch_rb<T>(const LevelView<T> &, int, int, cudaStream_t);                            \
     template void launch_rb_list<T>(const LevelView<T> &, int, const int32_t *, int, cudaStream_t);     \
+    template void launch_rb_fused2d<T>(const LevelView<T> &, const int32_t *, int, cudaStream_t);       \
     template void launch_ghost_relax<T>(const LevelView<T> &, int, cudaStream_t);                         \
     template void launch_ghost_relax_list<T>(const LevelView<T> &, int, const int32_t *, int, cudaStream_t); \
     template void launch_defect<T>(const LevelView<T> &, int, bool, unsigned long long *, cudaStream_t); \
     template void launch_extend<T>(T *, const DevGeom &, const T *, cudaStream_t);                        \
     template void launch_restrict<T>(const LevelView<T> &, const LevelView<T> &, int, T *, T *, cudaStream_t); \
+    template void launch_restrict_interior<T>(const LevelView<T> &, const LevelView<T> &, int, T *, cudaStream_t); \
+    template void launch_ghost_transfer<T>(const T *, const int32_t *, const int32_t *, const int32_t *, const T *, \
+                                           T *, int, cudaStream_t);                                              \
     template void launch_prolong<T>(const LevelView<T> &, const LevelView<T> &, int, const T *, T *, bool,  \
                                     cudaStream_t);                                                       \
     template void launch_coarse_solve<T>(const LevelView<T> &, const DevGeom &, const T *, cudaStream_t); \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
-    template size_t junction_smem_bytes<T>(const JunctionView<T> &, int);                           \
-    template void launch_junction<T>(const JunctionView<T> &, int, int, cudaStream_t);              \
-    template void junction_prepare<T>(int, size_t);
+    template size_t local_smem_bytes<T>(const LocalView<T> &, int);                                 \
+    template void launch_local<T>(const LocalView<T> &, int, int, int, cudaStream_t);               \
+    template void local_prepare<T>(int, size_t);
 
 GCMG_INSTANTIATE(float)
 GCMG_INSTANTIATE(double)

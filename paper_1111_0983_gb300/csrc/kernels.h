@@ -13,6 +13,8 @@ extern std::atomic<long long> g_launches;   // kernels launched by this library
 template <typename T>
 void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s);
 template <typename T>
+void launch_rb_fused2d(const LevelView<T> &v, const int32_t *tiles, int ntiles, cudaStream_t s);
+template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s);
 template <typename T>
 void launch_ghost_relax(const LevelView<T> &v, int dim, cudaStream_t s);
@@ -25,6 +27,11 @@ void launch_extend(T *r, const DevGeom &g, const T *ew, cudaStream_t s);
 template <typename T>
 void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, T *gc, cudaStream_t s);
 template <typename T>
+void launch_restrict_interior(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, cudaStream_t s);
+template <typename T>
+void launch_ghost_transfer(const T *rf, const int32_t *fgnode, const int32_t *ptr, const int32_t *col, const T *val,
+                           T *gc, int ngc, cudaStream_t s);
+template <typename T>
 void launch_prolong(const LevelView<T> &F, const LevelView<T> &C, int dim, const T *e, T *out, bool add,
                     cudaStream_t s);
 template <typename T>
@@ -33,11 +40,13 @@ template <typename T>
 void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s);
 
 template <typename T>
-size_t junction_smem_bytes(const JunctionView<T> &J, int dim);
+size_t local_smem_bytes(const LocalView<T> &J, int dim);
 template <typename T>
-void launch_junction(const JunctionView<T> &J, int dim, int sweeps, cudaStream_t s);
+void launch_local(const LocalView<T> &J, int dim, int lead_ghost, int reps, cudaStream_t s);
 template <typename T>
-void junction_prepare(int dim, size_t smem);
+void local_prepare(int dim, size_t smem);
+// whether a program's largest component keeps its inside entries in registers
+bool local_fits_registers(int max_int_per_colour);
 
 void launch_defect_to_f32(const DevGeom &g, const double *r64, float *f32, float *g32, cudaStream_t s);
 void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cudaStream_t s);

@@ -431,6 +431,101 @@ void build_extension(HostLevel &F, const HostLevel &C) {
 
 }  // namespace
 
+namespace {
+
+// Appends one component to a local program: `upd` (sorted) are the nodes it
+// updates, of which `wb` (sorted, a subset) are written back.
+struct ProgramBuilder {
+    HostLevel &L;
+    LocalProgram &P;
+    std::vector<int32_t> ghost_of;
+    std::vector<int32_t> local;
+    std::vector<int64_t> rd;
+    explicit ProgramBuilder(HostLevel &lv, LocalProgram &pr) : L(lv), P(pr), ghost_of(lv.nn, -1), local(lv.nn, -1) {
+        for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;
+    }
+    // nodes read by the update of P (inside: axis neighbours; ghost: stencil)
+    void reads(int64_t p, std::vector<int64_t> &out) const {
+        out.clear();
+        if ((L.type[p] & NODE_KIND) == NODE_IN) {
+            for (int a = 0; a < L.dim; a++) {
+                out.push_back(p - L.stride[a]);
+                out.push_back(p + L.stride[a]);
+            }
+        } else {
+            const int64_t q = ghost_of[p];
+            const int cube = L.dim == 2 ? 9 : 27;
+            for (int k = 0; k < cube; k++) out.push_back(L.stn[q * KMAX + k]);
+        }
+    }
+    int parity(int64_t p) const {
+        int par = 0;
+        for (int a = 0; a < L.dim; a++) {
+            par += (int)(p / L.stride[a]);
+            p %= L.stride[a];
+        }
+        return par & 1;
+    }
+    void add(const std::vector<int64_t> &upd, const std::vector<int64_t> &wb) {
+        std::vector<int64_t> nodes(wb);
+        std::vector<uint8_t> in_wb_tmp;
+        for (int64_t p : wb) local[p] = 0;
+        for (int64_t p : upd)
+            if (local[p] < 0) nodes.push_back(p);
+        for (int64_t p : upd) local[p] = 0;
+        std::vector<int64_t> halo;
+        for (int64_t p : upd) {
+            reads(p, rd);
+            for (int64_t q : rd)
+                if (local[q] < 0) halo.push_back(q);
+        }
+        std::sort(halo.begin(), halo.end());
+        halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+        nodes.insert(nodes.end(), halo.begin(), halo.end());
+        for (size_t i = 0; i < nodes.size(); i++) {
+            local[nodes[i]] = (int32_t)i;
+            P.lnode.push_back((int32_t)nodes[i]);
+        }
+        P.node_off.push_back((int32_t)P.lnode.size());
+        P.wb_cnt.push_back((int32_t)wb.size());
+        int nred = 0, nint = 0, ngh = 0;
+        for (int colour = 0; colour < 2; colour++)
+            for (int64_t p : upd) {
+                if ((L.type[p] & NODE_KIND) != NODE_IN || parity(p) != colour) continue;
+                P.int_glob.push_back((int32_t)p);
+                P.int_me.push_back(local[p]);
+                reads(p, rd);
+                for (int64_t q : rd) P.int_nb.push_back(local[q]);
+                nint++;
+                if (colour == 0) nred++;
+            }
+        for (int64_t p : upd) {
+            if ((L.type[p] & NODE_KIND) != NODE_GHOST) continue;
+            P.gh_me.push_back(local[p]);
+            P.gh_q.push_back(ghost_of[p]);
+            reads(p, rd);
+            for (int64_t q : rd) P.gh_stn.push_back(local[q]);
+            ngh++;
+        }
+        P.int_off.push_back((int32_t)P.int_me.size());
+        P.red_cnt.push_back(nred);
+        P.gh_off.push_back((int32_t)P.gh_me.size());
+        P.max_nodes = std::max(P.max_nodes, (int)nodes.size());
+        P.max_int = std::max(P.max_int, nint);
+        P.max_gh = std::max(P.max_gh, ngh);
+        for (int64_t p : nodes) local[p] = -1;
+    }
+    // union lists of the updated nodes of all components (global fallback)
+    void finish(const std::vector<int64_t> &all) {
+        for (int64_t p : all) {
+            if ((L.type[p] & NODE_KIND) == NODE_GHOST) P.zghost.push_back(ghost_of[p]);
+            else (parity(p) ? P.zblack : P.zred).push_back((int32_t)p);
+        }
+    }
+};
+
+}  // namespace
+
 // Junction zone: unknowns within radius h of a ghost whose 3^d neighbourhood
 // holds a ghost of the other boundary type.  Split into components closed
 // under the reads of their updates (inside node: axis neighbours; ghost: its
@@ -438,9 +533,8 @@ void build_extension(HostLevel &F, const HostLevel &C) {
 void build_junction(HostLevel &L, double radius) {
     Idx I{L};
     const int d = L.dim;
-    HostLevel::Junction J;
-    std::vector<int32_t> ghost_of(L.nn, -1);
-    for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;
+    LocalProgram prog;
+    ProgramBuilder PB(L, prog);
     std::vector<uint8_t> zone(L.nn, 0);
     const int R = (int)std::ceil(radius);
     const int cube = d == 2 ? 9 : 27;
@@ -452,7 +546,7 @@ void build_junction(HostLevel &L, double radius) {
             int k[3] = {0, 0, 0}, rem = c;
             for (int a = d - 1; a >= 0; a--) { k[a] = j[a] + rem % 3 - 1; rem /= 3; }
             if (!I.inside_box(k)) continue;
-            const int32_t g2 = ghost_of[I.join(k)];
+            const int32_t g2 = PB.ghost_of[I.join(k)];
             if (g2 >= 0 && L.bc[g2] != L.bc[q]) junction = true;
         }
         if (!junction) continue;
@@ -472,31 +566,21 @@ void build_junction(HostLevel &L, double radius) {
             if (unknown(L, P)) zone[P] = 1;
         }
     }
-    // reads of each zone node
-    auto reads = [&](int64_t P, std::vector<int64_t> &out) {
-        out.clear();
-        if ((L.type[P] & NODE_KIND) == NODE_IN) {
-            for (int a = 0; a < d; a++) { out.push_back(P - L.stride[a]); out.push_back(P + L.stride[a]); }
-        } else {
-            const int64_t q = ghost_of[P];
-            for (int k = 0; k < cube; k++) out.push_back(L.stn[q * KMAX + k]);
-        }
-    };
-    // union-find over zone nodes
     std::vector<int64_t> zn;
     for (int64_t P = 0; P < L.nn; P++)
         if (zone[P]) zn.push_back(P);
+    // union-find over zone nodes joined by reads
     std::vector<int32_t> zid(L.nn, -1);
     for (size_t i = 0; i < zn.size(); i++) zid[zn[i]] = (int32_t)i;
     std::vector<int32_t> parent(zn.size());
     std::iota(parent.begin(), parent.end(), 0);
-    std::function<int32_t(int32_t)> find = [&](int32_t x) {
+    auto find = [&](int32_t x) {
         while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
         return x;
     };
     std::vector<int64_t> rd;
     for (size_t i = 0; i < zn.size(); i++) {
-        reads(zn[i], rd);
+        PB.reads(zn[i], rd);
         for (int64_t Q : rd)
             if (zid[Q] >= 0) {
                 const int32_t a = find((int32_t)i), b = find(zid[Q]);
@@ -510,67 +594,155 @@ void build_junction(HostLevel &L, double radius) {
         if (comp_of_root[r] < 0) { comp_of_root[r] = (int32_t)comps.size(); comps.emplace_back(); }
         comps[comp_of_root[r]].push_back(zn[i]);
     }
-    std::vector<int32_t> local(L.nn, -1);
-    for (const auto &cz : comps) {
-        // local nodes: zone nodes (increasing index), then halo nodes
-        std::vector<int64_t> halo;
-        for (int64_t P : cz) {
-            reads(P, rd);
-            for (int64_t Q : rd)
-                if (!zone[Q]) halo.push_back(Q);
+    for (const auto &cz : comps) PB.add(cz, cz);
+    PB.finish(zn);
+    L.junction = std::move(prog);
+}
+
+// Boundary blocks (2D): each block x block tile holding band nodes or ghosts
+// becomes a component that updates every band node and ghost within
+// Chebyshev distance 2 + 4 lambda of the tile (the reach of one ghost sweep
+// plus lambda red / black / ghost sweeps) and writes back only the tile's
+// own, so the result equals the global sweeps.
+void build_boundary_blocks(HostLevel &L, int lambda, int block) {
+    LocalProgram prog;
+    ProgramBuilder PB(L, prog);
+    const int n = L.n;
+    const int H = 2 + 4 * lambda;
+    const int nb = (n + block - 1) / block;
+    auto updated = [&](int64_t p) {
+        const uint8_t t = L.type[p];
+        return (t & NODE_KIND) == NODE_GHOST || ((t & NODE_KIND) == NODE_IN && (t & NODE_BAND));
+    };
+    std::vector<int64_t> all;
+    for (int bi = 0; bi < nb; bi++)
+        for (int bj = 0; bj < nb; bj++) {
+            std::vector<int64_t> wb, upd;
+            const int i0 = bi * block, j0 = bj * block;
+            for (int i = i0; i < std::min(n, i0 + block); i++)
+                for (int j = j0; j < std::min(n, j0 + block); j++) {
+                    const int64_t p = (int64_t)i * n + j;
+                    if (updated(p)) wb.push_back(p);
+                }
+            if (wb.empty()) continue;
+            for (int i = std::max(0, i0 - H); i < std::min(n, i0 + block + H); i++)
+                for (int j = std::max(0, j0 - H); j < std::min(n, j0 + block + H); j++) {
+                    const int64_t p = (int64_t)i * n + j;
+                    if (updated(p)) upd.push_back(p);
+                }
+            PB.add(upd, wb);
+            all.insert(all.end(), wb.begin(), wb.end());
         }
-        std::sort(halo.begin(), halo.end());
-        halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
-        std::vector<int64_t> nodes(cz);
-        nodes.insert(nodes.end(), halo.begin(), halo.end());
-        for (size_t i = 0; i < nodes.size(); i++) {
-            local[nodes[i]] = (int32_t)i;
-            J.lnode.push_back((int32_t)nodes[i]);
-        }
-        J.node_off.push_back((int32_t)J.lnode.size());
-        J.zone_cnt.push_back((int32_t)cz.size());
-        int nred = 0, nint = 0, ngh = 0;
-        for (int colour = 0; colour < 2; colour++)
-            for (int64_t P : cz) {
-                if ((L.type[P] & NODE_KIND) != NODE_IN) continue;
-                int j[3] = {0, 0, 0}, par = 0;
-                I.split(P, j);
-                for (int a = 0; a < d; a++) par += j[a];
-                if ((par & 1) != colour) continue;
-                J.int_glob.push_back((int32_t)P);
-                J.int_me.push_back(local[P]);
-                reads(P, rd);
-                for (int64_t Q : rd) J.int_nb.push_back(local[Q]);
-                nint++;
-                if (colour == 0) nred++;
+    std::sort(all.begin(), all.end());
+    PB.finish(all);
+    L.boundary = std::move(prog);
+}
+
+bool partial_transfer_weights(const HostLevel &F, int64_t p, bool interior, double *wt) {
+    const int d = F.dim;
+    const int cube = d == 2 ? 9 : 27, nbox = d == 2 ? 16 : 64;
+    // interval codes per axis: 0 [-1,1], 1 [-1,0], 2 [0,1], 3 [0,0]
+    static const int LO[4] = {-1, -1, 0, 0}, HI[4] = {1, 0, 1, 0};
+    static const double W[4][3] = {{0.25, 0.5, 0.25}, {0.5, 0.5, 0.0}, {0.0, 0.5, 0.5}, {0.0, 1.0, 0.0}};
+    bool member[27];
+    for (int c = 0; c < cube; c++) {
+        int rem = c;
+        int64_t P = p;
+        for (int a = d - 1; a >= 0; a--) { P += (int64_t)(rem % 3 - 1) * F.stride[a]; rem /= 3; }
+        const uint8_t k = F.type[P] & NODE_KIND;
+        member[c] = interior ? (k == NODE_IN) : (k != NODE_IN);
+        wt[c] = 0.0;
+    }
+    int best = 0, count = 0;
+    for (int pass = 0; pass < 2; pass++)
+        for (int b = 0; b < nbox; b++) {
+            int iv[3] = {0, 0, 0}, size = 1;
+            for (int a = 0; a < d; a++) { iv[a] = (b >> (2 * a)) & 3; size *= HI[iv[a]] - LO[iv[a]] + 1; }
+            bool ok = true;
+            for (int c = 0; c < cube && ok; c++) {
+                int rem = c;
+                bool inside = true;
+                for (int a = d - 1; a >= 0; a--) {
+                    const int o = rem % 3 - 1;
+                    rem /= 3;
+                    if (o < LO[iv[a]] || o > HI[iv[a]]) inside = false;
+                }
+                if (inside && !member[c]) ok = false;
             }
-        for (int64_t P : cz) {
-            if ((L.type[P] & NODE_KIND) != NODE_GHOST) continue;
-            J.gh_me.push_back(local[P]);
-            J.gh_q.push_back(ghost_of[P]);
-            reads(P, rd);
-            for (int64_t Q : rd) J.gh_stn.push_back(local[Q]);
-            ngh++;
+            if (!ok) continue;
+            if (pass == 0) {
+                if (size > best) { best = size; count = 0; }
+                if (size == best) count++;
+            } else if (size == best) {
+                for (int c = 0; c < cube; c++) {
+                    int rem = c;
+                    double w = 1.0;
+                    for (int a = d - 1; a >= 0; a--) { w *= W[iv[a]][rem % 3]; rem /= 3; }
+                    wt[c] += w / count;
+                }
+            }
         }
-        J.int_off.push_back((int32_t)J.int_me.size());
-        J.red_cnt.push_back(nred);
-        J.gh_off.push_back((int32_t)J.gh_me.size());
-        J.max_nodes = std::max(J.max_nodes, (int)nodes.size());
-        J.max_int = std::max(J.max_int, nint);
-        J.max_gh = std::max(J.max_gh, ngh);
-        for (int64_t P : nodes) local[P] = -1;
-    }
-    for (int64_t P : zn) {
-        if ((L.type[P] & NODE_KIND) == NODE_GHOST) {
-            J.zghost.push_back(ghost_of[P]);
-        } else {
-            int j[3] = {0, 0, 0}, par = 0;
-            I.split(P, j);
-            for (int a = 0; a < d; a++) par += j[a];
-            ((par & 1) ? J.zblack : J.zred).push_back((int32_t)P);
+    return count > 0;
+}
+
+// Composes the extension of F (wavefront order: sources first) with the
+// partial transfer over D_h - Omega_h at every ghost of C.
+static void build_ghost_transfer(HostLevel &F, const HostLevel &C) {
+    const int d = F.dim;
+    const int cube = d == 2 ? 9 : 27;
+    std::vector<int32_t> ghost_of(F.nn, -1), ext_of(F.nn, -1);
+    for (int64_t q = 0; q < F.ng(); q++) ghost_of[F.ghost_node[q]] = (int32_t)q;
+    for (size_t e = 0; e < F.ext_node.size(); e++) ext_of[F.ext_node[e]] = (int32_t)e;
+    // each extension node as a combination of ghost defects
+    std::vector<std::vector<std::pair<int32_t, double>>> expand(F.ext_node.size());
+    for (size_t e = 0; e < F.ext_node.size(); e++) {
+        std::vector<std::pair<int32_t, double>> acc;
+        for (int k = 0; k < F.ext_cnt[e]; k++) {
+            const int64_t src = F.ext_src[e * EMAX + k];
+            const double w = F.ext_w[e * EMAX + k];
+            if (ghost_of[src] >= 0) acc.emplace_back(ghost_of[src], w);
+            else
+                for (const auto &t : expand[ext_of[src]]) acc.emplace_back(t.first, w * t.second);
         }
+        std::sort(acc.begin(), acc.end());
+        std::vector<std::pair<int32_t, double>> merged;
+        for (const auto &t : acc) {
+            if (!merged.empty() && merged.back().first == t.first) merged.back().second += t.second;
+            else merged.push_back(t);
+        }
+        expand[e].swap(merged);
     }
-    L.junction = std::move(J);
+    F.gt_ptr.assign(1, 0);
+    F.gt_col.clear();
+    F.gt_val.clear();
+    for (int64_t q = 0; q < C.ng(); q++) {
+        int64_t rem = C.ghost_node[q], p = 0;
+        for (int a = 0; a < d; a++) {
+            const int64_t J = rem / C.stride[a];
+            rem -= J * C.stride[a];
+            p += 2 * J * F.stride[a];
+        }
+        double wt[27];
+        std::vector<std::pair<int32_t, double>> acc;
+        if (partial_transfer_weights(F, p, false, wt)) {
+            for (int c = 0; c < cube; c++) {
+                if (wt[c] == 0.0) continue;
+                int r2 = c;
+                int64_t P = p;
+                for (int a = d - 1; a >= 0; a--) { P += (int64_t)(r2 % 3 - 1) * F.stride[a]; r2 /= 3; }
+                if (ghost_of[P] >= 0) acc.emplace_back(ghost_of[P], wt[c]);
+                else if (ext_of[P] >= 0)
+                    for (const auto &t : expand[ext_of[P]]) acc.emplace_back(t.first, wt[c] * t.second);
+            }
+        }
+        std::sort(acc.begin(), acc.end());
+        for (size_t i = 0; i < acc.size(); i++) {
+            if (i > 0 && acc[i].first == acc[i - 1].first) { F.gt_val.back() += acc[i].second; continue; }
+            F.gt_col.push_back(acc[i].first);
+            F.gt_val.push_back(acc[i].second);
+        }
+        F.gt_ptr.push_back((int32_t)F.gt_col.size());
+    }
 }
 
 void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
@@ -608,9 +780,21 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
         L.bc.assign(ng, 0);
         for (int64_t q = 0; q < ng; q++) ghost_equation(L, q);
         mark_band(L, delta_over_h * L.h);
+        if (dim == 2) {
+            const int tr = (L.n + TILE_R - 1) / TILE_R, tc = (L.n + TILE_C - 1) / TILE_C;
+            std::vector<uint8_t> active((size_t)tr * tc, 0);
+            for (int64_t p = 0; p < L.nn; p++)
+                if ((L.type[p] & NODE_KIND) == NODE_IN) active[(p / L.n) / TILE_R * tc + (p % L.n) / TILE_C] = 1;
+            for (int a = 0; a < tr; a++)
+                for (int b = 0; b < tc; b++)
+                    if (active[(size_t)a * tc + b]) L.tiles.push_back((a << 16) | b);
+        }
         levels.push_back(std::move(L));
     }
-    for (int l = 0; l + 1 < nl; l++) build_extension(levels[l], levels[l + 1]);
+    for (int l = 0; l + 1 < nl; l++) {
+        build_extension(levels[l], levels[l + 1]);
+        build_ghost_transfer(levels[l], levels[l + 1]);
+    }
     build_coarse_inverse(levels.back());
 }
 

@@ -152,7 +152,8 @@ def test_solve_matches_oracle(P, n, nc, kw):
     # per-cycle convergence factors beside the oracle's (same algorithm)
     k = min(6, st["cycles"], len(norms) - 1)
     rel_o = norms[: k + 1] / norms[0]
-    assert np.allclose(st["rel"][1: k + 1], rel_o[1: k + 1], rtol=1e-6, atol=0), (st["rel"][: k + 1], rel_o)
+    # rounding differs by summation order: about 1e-13 of ||r0|| per cycle
+    assert np.allclose(st["rel"][1: k + 1], rel_o[1: k + 1], rtol=1e-6, atol=1e-11), (st["rel"][: k + 1], rel_o)
 
 
 @pytest.mark.parametrize("P,n,nc", [(inputs.flower(), 257, 33), (inputs.torus(), 65, 17),
