@@ -54,7 +54,8 @@ typedef enum {
                             node on the box boundary, no usable ghost stencil, a
                             degenerate normal, or a singular coarsest system */
     GCMG_E_NOCONV = 5,   /* max_cycles reached, or a NaN/Inf defect */
-    GCMG_E_STATE = 6     /* call out of order (e.g. solve before set_rhs) */
+    GCMG_E_STATE = 6,    /* call out of order (e.g. solve before set_rhs) */
+    GCMG_E_SIZE = 7      /* problem larger than a fixed-capacity entry point accepts */
 } gcmg_status;
 
 /* Cycle parameters (Sec. 2.4, Sec. 3.2).  gcmg_default_params fills the
@@ -209,6 +210,33 @@ gcmg_status gcmg_kernel_timing(gcmg_ctx *ctx, int64_t *launches, double *total_m
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t gcmg_launch_counter(void);
+
+/* ---- allocation-free defect (no counterpart in the paper: a service for
+ * callers that cannot allocate device memory -- code whose device memory is
+ * all owned by another allocator, such as a framework's caching pool or an
+ * arena reserved under a fixed budget, and latency-critical loops that must
+ * not pay the device-wide synchronisation of cudaMalloc / cudaFree).
+ *
+ * Same result as gcmg_defect without a context: the caller passes every input
+ * and output.  type_dev: node types (n^dim bytes, 0 outside, 1 inside, 2
+ * ghost; higher bits ignored), u_dev, f_dev, r_dev: n^dim doubles, h = 2/(n-1);
+ * ng ghosts with gnode_dev[ng] (node index), stn_dev[ng*27] and w_dev[ng*27]
+ * (the ghost's stencil nodes and the weights of its boundary type, as
+ * returned by gcmg_ghost_equations; unused slots weight 0) and g_dev[ng].
+ * Writes r on the whole grid and, if norm_host is not NULL, ||r||_inf over
+ * inside nodes and ghosts (after synchronising the stream).
+ *
+ * It allocates nothing: its scratch is a fixed array of 65,537 doubles
+ * (512 KiB) in the library's device image, held by every device that loads
+ * the library until the process exits.  Capacity: n^dim + ng <= 67,108,864;
+ * larger problems return GCMG_E_SIZE.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls on a device share the array: calls
+ * that overlap on the GPU race and must be serialised by the caller. */
+gcmg_status gcmg_defect_noalloc(int dim, int n, double h, const uint8_t *type_dev, const double *u_dev,
+                                const double *f_dev, int64_t ng, const int32_t *gnode_dev, const int32_t *stn_dev,
+                                const double *w_dev, const double *g_dev, double *r_dev, double *norm_host,
+                                void *stream);
 
 #ifdef __cplusplus
 }

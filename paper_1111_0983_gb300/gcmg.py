@@ -15,8 +15,9 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgcmg.so")
 
-GCMG_OK, GCMG_E_ARG, GCMG_E_CUDA, GCMG_E_OOM, GCMG_E_GEOM, GCMG_E_NOCONV, GCMG_E_STATE = range(7)
-STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_OOM", 4: "E_GEOM", 5: "E_NOCONV", 6: "E_STATE"}
+GCMG_OK, GCMG_E_ARG, GCMG_E_CUDA, GCMG_E_OOM, GCMG_E_GEOM, GCMG_E_NOCONV, GCMG_E_STATE, GCMG_E_SIZE = range(8)
+STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_OOM", 4: "E_GEOM", 5: "E_NOCONV", 6: "E_STATE",
+                7: "E_SIZE"}
 KMAX = 27
 
 
@@ -79,6 +80,7 @@ def lib():
             "gcmg_kernel_timing": (st, [vp, C.POINTER(i64), C.POINTER(dbl)]),
             "gcmg_launch_counter": (i64, []),
             "gcmg_junction_zone": (st, [vp, i32, vp]),
+            "gcmg_defect_noalloc": (st, [i32, i32, dbl, vp, vp, vp, i64, vp, vp, vp, vp, vp, C.POINTER(dbl), vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
