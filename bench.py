@@ -44,6 +44,7 @@ WORKLOADS = {
     "disk65": (inputs.disk, 65, 17, "2D disk r=0.7, Dirichlet, 65^2"),
     "torus257": (inputs.torus, 257, 17, "3D torus R=0.5 r=0.25, mixed D/N, 257^3"),
     "torus513": (inputs.torus, 513, 17, "3D torus R=0.5 r=0.25, mixed D/N, 513^3"),
+    "stars256": (None, None, 33, "256 seeded 2D stars, n in {129,257,513,1025}, mixed D/N, one batched solve"),
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -55,12 +56,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="flower1025", choices=sorted(WORKLOADS))
     ap.add_argument("--rtol", type=float, default=1e-10)
-    ap.add_argument("--also", default="flower4097:1e-9",
-                    help="secondary workload:rtol measured after the main one ('' to skip)")
+    ap.add_argument("--also", default="flower4097:1e-9,torus257:1e-10",
+                    help="comma-separated secondary workload:rtol pairs measured after the main one ('' to skip)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--gamma", type=int, default=1)
     ap.add_argument("--impl", default="gcmg", choices=["gcmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=256, help="domains of the batched secondary / stars256 run")
     ap.add_argument("--cpu-sample-cycles", type=int, default=2)
     return ap.parse_args()
 
@@ -208,14 +210,61 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batch
+def build_batch(count, stream):
+    """Seeded stars (inputs.star_params) as one gcmg batch with their data set."""
+    import torch
+    from paper_1111_0983_gb300 import gcmg
+    probs = [inputs.star(i) for i in range(count)]
+    sizes = [P.meta["n"] for P in probs]
+    B = gcmg.Batch([P.phi_grid(n) for P, n in zip(probs, sizes)], 33, stream=stream, rtol=1e-10, max_cycles=100)
+    n_in = 0
+    for S, P, n in zip(B.domains, probs, sizes):
+        for l in range(S.nlev):
+            S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+        G = S.ghosts(0)
+        g = P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))
+        S.set_rhs(torch.from_numpy(P.f_grid(n)).cuda(), torch.from_numpy(g).cuda())
+    unknowns = sum(S.num_unknowns(0) for S in B.domains)
+    # fused-sweep bytes of one cycle: 12 B (FP32) per inside node per sweep,
+    # nu1 + nu2 sweeps on every level of every domain
+    for S in B.domains:
+        for l in range(S.nlev - 1):
+            n_in += int(((S.node_types(l) & 3) == 1).sum())
+    return B, sizes, unknowns, 12 * 3 * n_in
+
+
+def run_batch_measure(B, steps, warmup, stream, flush):
+    import torch
+    best, tune_ms = B.autotune()
+    for _ in range(warmup):
+        stats, m = B.solve()
+    ms, cyc = 0.0, []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        stats, m = B.solve()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        cyc.append(m)
+        if not all(st["converged"] for st in stats):
+            raise RuntimeError("batched solve did not converge")
+    return ms / steps, cyc, best, tune_ms
+
+
 # ----------------------------------------------------------------- gcmg arm
 def secondary(name, rtol, precision, args, stream, flush):
     """Time the same form on another workload (plain FP64 and mixed)."""
     import torch
     from paper_1111_0983_gb300 import gcmg
     P, n, nc, desc = build_problem(name)
-    out = {"workload": name, "description": desc, "rtol": rtol, "note": FP64_FLOOR_NOTE}
+    out = {"workload": name, "description": desc, "rtol": rtol}
+    if name == "flower4097":
+        out["note"] = FP64_FLOOR_NOTE
     for prec in (0, 1):
+        t0 = time.perf_counter()
         S = gcmg.Solver(P.phi_grid(n), nc, stream=stream, precision=prec, gamma=args.gamma, rtol=rtol,
                         max_cycles=256)
         for l in range(S.nlev):
@@ -246,6 +295,7 @@ def secondary(name, rtol, precision, args, stream, flush):
             out["f64" if prec == 0 else "mixed"] = {"value": S.num_unknowns(0) * k / (ms / 1e3),
                                                    "unit": "unknowns/s", "ms_per_solve": ms / k, "cycles": cyc}
         out["unknowns"] = S.num_unknowns(0)
+        out["setup_s_" + ("f64" if prec == 0 else "mixed")] = time.perf_counter() - t0
         S.close()
     return out
 
@@ -378,8 +428,23 @@ def run_gcmg(args):
                         "d2h_bytes_per_step": int(u_pin.nbytes)},
                 "wall_s": wall}
         if args.also and world == 1:
-            name, rt = args.also.split(":")
-            line["also"] = secondary(name, float(rt), precision, args, stream, flush)
+            line["also"] = []
+            for item in args.also.split(","):
+                name, rt = item.split(":")
+                line["also"].append(secondary(name, float(rt), precision, args, stream, flush))
+        if args.batch and world == 1:
+            t0 = time.perf_counter()
+            B, sizes, bun, fused_bytes = build_batch(args.batch, stream)
+            setup_s = time.perf_counter() - t0
+            bms, bcyc, best, tune_ms = run_batch_measure(B, max(1, min(args.steps, 3)), 2, stream, flush)
+            line["batch"] = {"workload": f"stars{args.batch}", "domains": args.batch,
+                             "grid_sizes": {str(n): sizes.count(n) for n in sorted(set(sizes))},
+                             "unknowns": bun, "value": bun / (bms / 1e3), "unit": "unknowns/s",
+                             "ms_per_solve": bms, "refinement_steps": bcyc, "setup_s": setup_s,
+                             "tile_variant": ["16x64", "8x128", "32x32"][best],
+                             "autotune_ms_fused_sweeps_per_cycle": tune_ms,
+                             "fused_sweep_GBs": fused_bytes / (min(tune_ms) / 1e3) / 1e9}
+            B.close()
         if world == 1 and not args.no_cpu_baseline:
             sec, nu_o, _ = oracle_cycle_sample(P, n, nc, args.gamma, args.cpu_sample_cycles)
             cyc = cycles_reference(args.config, args.precision) or statistics.median(cycles)

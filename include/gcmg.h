@@ -61,9 +61,9 @@ typedef enum {
 /* Cycle parameters (Sec. 2.4, Sec. 3.2).  gcmg_default_params fills the
  * paper's values: nu1 = 2, nu2 = 1, lambda = 5, delta = 3h, mu_D dt = 0.9,
  * mu_N dt = 0.9 * 2h / (3 sqrt(d)), V-cycle; plus the junction relaxation
- * that this library adds for mixed boundaries (mu_J = 40, R_J = 12; the
- * paper has no counterpart -- without it the V-cycle factor of a mixed
- * problem grows as h shrinks). */
+ * that this library adds for mixed boundaries (mu_J = 40, R_J = 12 in 2D;
+ * mu_J = 10, R_J = 2 in 3D; the paper has no counterpart -- without it the
+ * V-cycle factor of a mixed problem grows as h shrinks). */
 typedef struct {
     int dim;                 /* 2 or 3 */
     int n;                   /* fine nodes per axis: (n - 1) = (n_coarse - 1) * 2^k, k >= 1 */
@@ -210,6 +210,43 @@ gcmg_status gcmg_kernel_timing(gcmg_ctx *ctx, int64_t *launches, double *total_m
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t gcmg_launch_counter(void);
+
+/* ---- batched solves of many domains (BASELINE batching; not in the paper).
+ * Independent 2D domains of uneven grid sizes are solved together: each step
+ * of the cycle is one kernel launch over all domains and the whole solve --
+ * FP32 V-cycles inside FP64 iterative refinement until every domain reaches
+ * rtol -- is one CUDA-graph launch with a device-side loop. */
+typedef struct gcmg_batch gcmg_batch;
+
+/* Creates `count` domains: params[i] (dim 2, precision 1, gamma 1; nu1, nu2,
+ * lambda and junction_sweeps equal across domains; rtol and max_cycles of
+ * params[0] apply to the batch) and phi_dev[i] (device, n_i^2 doubles).  The
+ * host geometry of the domains is built in parallel threads. */
+gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double *const *phi_dev, void *stream,
+                              gcmg_batch **out);
+void gcmg_batch_destroy(gcmg_batch *batch);
+const char *gcmg_batch_last_error(const gcmg_batch *batch);
+int gcmg_batch_size(const gcmg_batch *batch);
+
+/* The context of domain i, owned by the batch: use it for the ghost
+ * geometry, gcmg_set_bc_types and gcmg_set_rhs of that domain (do not destroy
+ * it, and do not call gcmg_solve on it while the batch is in use). */
+gcmg_ctx *gcmg_batch_domain(gcmg_batch *batch, int i);
+
+/* Solves every domain from u = 0.  stats (may be NULL) receives one entry per
+ * domain; *steps (may be NULL) the number of refinement steps the batch ran
+ * (all domains run the same number).  GCMG_E_NOCONV if a domain missed rtol. */
+gcmg_status gcmg_batch_solve(gcmg_batch *batch, gcmg_stats *stats, int *steps);
+
+/* Copies the solution of domain i to u_dev (device, n_i^2 doubles). */
+gcmg_status gcmg_batch_get_solution(gcmg_batch *batch, int i, double *u_dev);
+
+/* Tile shape of the fused interior sweep: 0 = 16 x 64, 1 = 8 x 128, 2 = 32 x 32. */
+gcmg_status gcmg_batch_set_tiles(gcmg_batch *batch, int variant);
+
+/* Autotuner: times the batched interior sweeps of one cycle with every tile
+ * shape, selects the fastest (*best) and reports each time in ms[0..2]. */
+gcmg_status gcmg_batch_autotune(gcmg_batch *batch, int *best, double *ms);
 
 /* ---- allocation-free defect (no counterpart in the paper: a service for
  * callers that cannot allocate device memory -- code whose device memory is

@@ -95,9 +95,14 @@ class Oracle:
     """One multigrid hierarchy built from a fine level set ``phi`` (shape n^dim)."""
 
     def __init__(self, phi, n_coarse, nu1=2, nu2=1, lam=5, gamma=1, mode=0, extra_once=0,
-                 delta_over_h=3.0, c_dirichlet=0.9, c_neumann_factor=0.9, junction_sweeps=40, junction_radius=12.0):
+                 delta_over_h=3.0, c_dirichlet=0.9, c_neumann_factor=0.9, junction_sweeps=None, junction_radius=None):
         phi = np.ascontiguousarray(phi, dtype=np.float64)
         self.dim = phi.ndim
+        # junction relaxation defaults: 40 sweeps within 12h (2D), 10 within 2h (3D)
+        if junction_sweeps is None:
+            junction_sweeps = 40 if self.dim == 2 else 10
+        if junction_radius is None:
+            junction_radius = 12.0 if self.dim == 2 else 2.0
         self.n = phi.shape[0]
         assert all(s == self.n for s in phi.shape)
         self.params = Params(nu1, nu2, lam, gamma, mode, extra_once, delta_over_h, c_dirichlet,

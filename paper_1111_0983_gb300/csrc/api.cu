@@ -10,39 +10,11 @@
 #include <string>
 #include <vector>
 
+#include "ctx.h"
 #include "gcmg_internal.h"
 #include "kernels.h"
 
 using namespace gcmg;
-
-struct gcmg_ctx {
-    gcmg_params p{};
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    std::vector<HostLevel> H;
-    std::vector<DevGeom> G;
-    std::vector<DevData<double>> D64;
-    std::vector<DevData<float>> D32;
-    bool rhs_set = false;
-    unsigned long long *d_norm = nullptr;   // two slots: defect norm, rhs norm
-    unsigned long long *h_norm = nullptr;   // pinned
-    // the solve loop as one CUDA graph: a device-side while loop over cycles
-    cudaStream_t gstream = nullptr;         // capture / launch stream (never the legacy one)
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    double *d_rel = nullptr;                // rel[0..256]
-    double *d_r0 = nullptr;
-    int *d_m = nullptr;
-    bool use_graph = true;
-    long long graph_kernels = 0;            // kernels in one loop iteration
-    // event timing of one fine-level kernel class during solves
-    int timing_kind = -1;
-    std::vector<cudaEvent_t> events;
-    size_t events_used = 0;
-    std::vector<void *> allocs;
-    std::string err;
-};
 
 namespace {
 
@@ -106,11 +78,7 @@ void upload_ghost_data(gcmg_ctx *c, int l, DevData<T> &D, bool alloc) {
     }
     ck(cudaMemcpyAsync(D.gw, ws.data(), ws.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream), "gw");
     ck(cudaMemcpyAsync(D.gc, coef.data(), coef.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream), "gc");
-    if (l + 1 == (int)c->H.size()) {
-        std::vector<T> A(L.Ainv.begin(), L.Ainv.end());
-        if (alloc) D.Ainv = dalloc<T>(c, A.size());
-        ck(cudaMemcpyAsync(D.Ainv, A.data(), A.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream), "Ainv");
-    }
+    if (l + 1 == (int)c->H.size() && alloc) D.Ainv = dalloc<T>(c, L.unk_node.size() * L.unk_node.size());
     // synchronous: the staging vectors die at return
     ck(cudaStreamSynchronize(c->stream), "sync");
 }
@@ -215,32 +183,6 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
 }
 
 template <typename T>
-LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
-    const HostLevel &L = c->H[l];
-    const DevGeom &g = c->G[l];
-    LevelView<T> v;
-    v.n = L.n;
-    v.nn = L.nn;
-    v.s0 = L.stride[0];
-    v.s1 = L.stride[1];
-    v.s2 = L.dim == 3 ? L.stride[2] : 0;
-    v.h2 = (T)(L.h * L.h);
-    v.inv_h2 = (T)(1.0 / (L.h * L.h));
-    v.type = g.type;
-    v.u = D.u;
-    v.f = D.f;
-    v.r = D.r;
-    v.ng = g.ng;
-    v.gnode = g.gnode;
-    v.gstn = g.gstn;
-    v.gw = D.gw;
-    v.gc = D.gc;
-    v.gg = D.gg;
-    v.gtmp = D.gtmp;
-    return v;
-}
-
-template <typename T>
 std::vector<DevData<T>> &data(gcmg_ctx *c);
 template <>
 std::vector<DevData<double>> &data<double>(gcmg_ctx *c) { return c->D64; }
@@ -257,22 +199,6 @@ void timer_mark(gcmg_ctx *c, int kind, int l) {
         c->events.push_back(e);
     }
     ck(cudaEventRecord(c->events[c->events_used++], c->stream), "cudaEventRecord");
-}
-
-template <typename T>
-LocalView<T> lview(const LocalDev &z, const LevelView<T> &v) {
-    LocalView<T> J;
-    J.ncomp = z.ncomp;
-    J.max_nodes = z.max_nodes;
-    J.max_int = z.max_int;
-    J.max_gh = z.max_gh;
-    J.ng = v.ng;
-    J.node_off = z.node_off; J.wb_cnt = z.wb_cnt; J.lnode = z.lnode;
-    J.int_off = z.int_off; J.red_cnt = z.red_cnt; J.int_glob = z.int_glob; J.int_me = z.int_me; J.int_nb = z.int_nb;
-    J.gh_off = z.gh_off; J.gh_me = z.gh_me; J.gh_q = z.gh_q; J.gh_stn = z.gh_stn;
-    J.u = v.u; J.f = v.f; J.gg = v.gg; J.gc = v.gc; J.gw = v.gw;
-    J.h2 = v.h2;
-    return J;
 }
 
 // one relaxation R_h followed by the lambda extra sweeps (Sec. 2.4, 3.2) and
@@ -501,6 +427,82 @@ void check_launch() { ck(cudaGetLastError(), "kernel launch"); }
 
 }  // namespace
 
+namespace gcmg {
+
+gcmg_status check_params(const gcmg_params &q) {
+    const gcmg_params *p = &q;
+    if (p->dim < 2 || p->dim > 3 || p->n_coarse < 3 || p->n <= p->n_coarse) return GCMG_E_ARG;
+    int m = p->n;
+    while (m > p->n_coarse) {
+        if ((m - 1) % 2) return GCMG_E_ARG;
+        m = (m - 1) / 2 + 1;
+    }
+    if (m != p->n_coarse) return GCMG_E_ARG;
+    const double nn = std::pow((double)p->n, p->dim);
+    if (nn >= 2147483647.0) return GCMG_E_ARG;   // 32-bit node indices
+    if (p->gamma < 1 || p->gamma > 2 || p->nu1 < 0 || p->nu2 < 0 || p->lambda < 0) return GCMG_E_ARG;
+    if (p->precision < 0 || p->precision > 1 || p->max_cycles < 1 || p->max_cycles > 256) return GCMG_E_ARG;
+    if (p->junction_sweeps < 0 || p->junction_radius < 0.0 || p->junction_radius > 64.0) return GCMG_E_ARG;
+    return GCMG_OK;
+}
+
+void prepare_levels(const gcmg_params &p, const double *phi_host, std::vector<HostLevel> &H) {
+    build_hierarchy(p.dim, p.n, p.n_coarse, phi_host, p.delta_over_h, H);
+    if (p.dim == 2)
+        for (auto &L : H) build_boundary_blocks(L, p.lambda, 32);
+}
+
+gcmg_status create_from_levels(const gcmg_params &q, std::vector<HostLevel> &&H, cudaStream_t stream, gcmg_ctx **out) {
+    const gcmg_params *p = &q;
+    gcmg_ctx *c = new (std::nothrow) gcmg_ctx;
+    if (!c) return GCMG_E_OOM;
+    *out = c;
+    c->p = *p;
+    c->stream = stream;
+    c->H = std::move(H);
+    GCMG_GUARD(c, {
+        ck(cudaGetDevice(&c->device), "cudaGetDevice");
+        const int nl = (int)c->H.size();
+        for (int l = 0; l < nl; l++) upload_geometry(c, l);
+        if (p->dim == 2)
+            for (int l = 0; l < nl; l++) {
+                upload_program(c, c->H[l].boundary, c->G[l].bz);
+                check_program_fits(c, c->G[l].bz);
+            }
+        c->D64.resize(nl);
+        for (int l = 0; l < nl; l++) alloc_data<double>(c, l, c->D64[l], p->precision == 0 || l == 0);
+        if (p->precision == 1) {
+            c->D32.resize(nl);
+            for (int l = 0; l < nl; l++) alloc_data<float>(c, l, c->D32[l], true);
+        }
+        c->d_norm = dalloc<unsigned long long>(c, 2);
+        c->d_rel = dalloc<double>(c, 257);
+        c->d_r0 = dalloc<double>(c, 1);
+        c->d_m = dalloc<int>(c, 1);
+        ck(cudaMallocHost((void **)&c->h_norm, 2 * sizeof(unsigned long long)), "cudaMallocHost");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
+void upload_inverse(gcmg_ctx *c) {
+    const HostLevel &L = c->H.back();
+    const size_t m2 = L.unk_node.size() * L.unk_node.size();
+    ck(cudaMemcpy(c->D64.back().Ainv, L.Ainv.data(), m2 * sizeof(double), cudaMemcpyHostToDevice), "Ainv");
+    if (!c->D32.empty()) {
+        std::vector<float> A(L.Ainv.begin(), L.Ainv.end());
+        ck(cudaMemcpy(c->D32.back().Ainv, A.data(), m2 * sizeof(float), cudaMemcpyHostToDevice), "Ainv");
+    }
+}
+
+void ensure_inverse(gcmg_ctx *c) {
+    if (!c->H.back().ainv_dirty) return;
+    build_coarse_inverse(c->H.back());
+    upload_inverse(c);
+}
+
+}  // namespace gcmg
+
 extern "C" {
 
 gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
@@ -519,8 +521,11 @@ gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
     p->precision = 0;
     p->max_cycles = 100;
     p->rtol = 1e-10;
-    p->junction_sweeps = 40;
-    p->junction_radius = 12.0;
+    // 2D: 40 sweeps within 12h; 3D: the zone is a tube around junction curves,
+    // where 10 sweeps within 2h keep the factor bounded (more sweeps on a wider
+    // 3D zone amplify a local ghost mode)
+    p->junction_sweeps = dim == 3 ? 10 : 40;
+    p->junction_radius = dim == 3 ? 2.0 : 12.0;
     return GCMG_OK;
 }
 
@@ -528,55 +533,29 @@ gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *strea
     if (!out) return GCMG_E_ARG;
     *out = nullptr;
     if (!p || !phi_dev) return GCMG_E_ARG;
-    if (p->dim < 2 || p->dim > 3 || p->n_coarse < 3 || p->n <= p->n_coarse) return GCMG_E_ARG;
-    {
-        int m = p->n;
-        while (m > p->n_coarse) {
-            if ((m - 1) % 2) return GCMG_E_ARG;
-            m = (m - 1) / 2 + 1;
-        }
-        if (m != p->n_coarse) return GCMG_E_ARG;
-        const double nn = std::pow((double)p->n, p->dim);
-        if (nn >= 2147483647.0) return GCMG_E_ARG;   // 32-bit node indices
-        if (p->gamma < 1 || p->gamma > 2 || p->nu1 < 0 || p->nu2 < 0 || p->lambda < 0) return GCMG_E_ARG;
-        if (p->precision < 0 || p->precision > 1 || p->max_cycles < 1 || p->max_cycles > 256) return GCMG_E_ARG;
-        if (p->junction_sweeps < 0 || p->junction_radius < 0.0 || p->junction_radius > 64.0) return GCMG_E_ARG;
+    if (check_params(*p) != GCMG_OK) return GCMG_E_ARG;
+    int64_t nn = 1;
+    for (int a = 0; a < p->dim; a++) nn *= p->n;
+    std::vector<double> phi(nn);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(phi.data(), phi_dev, nn * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return GCMG_E_CUDA;
     }
-    gcmg_ctx *c = new (std::nothrow) gcmg_ctx;
-    if (!c) return GCMG_E_OOM;
-    *out = c;
-    c->p = *p;
-    c->stream = (cudaStream_t)stream;
-    GCMG_GUARD(c, {
-        ck(cudaGetDevice(&c->device), "cudaGetDevice");
-        int64_t nn = 1;
-        for (int a = 0; a < p->dim; a++) nn *= p->n;
-        std::vector<double> phi(nn);
-        ck(cudaMemcpyAsync(phi.data(), phi_dev, nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "phi");
-        ck(cudaStreamSynchronize(c->stream), "sync");
-        build_hierarchy(p->dim, p->n, p->n_coarse, phi.data(), p->delta_over_h, c->H);
-        const int nl = (int)c->H.size();
-        for (int l = 0; l < nl; l++) upload_geometry(c, l);
-        if (p->dim == 2)
-            for (int l = 0; l < nl; l++) {
-                build_boundary_blocks(c->H[l], p->lambda, 32);
-                upload_program(c, c->H[l].boundary, c->G[l].bz);
-                check_program_fits(c, c->G[l].bz);
-            }
-        c->D64.resize(nl);
-        for (int l = 0; l < nl; l++) alloc_data<double>(c, l, c->D64[l], p->precision == 0 || l == 0);
-        if (p->precision == 1) {
-            c->D32.resize(nl);
-            for (int l = 0; l < nl; l++) alloc_data<float>(c, l, c->D32[l], true);
-        }
-        c->d_norm = dalloc<unsigned long long>(c, 2);
-        c->d_rel = dalloc<double>(c, 257);
-        c->d_r0 = dalloc<double>(c, 1);
-        c->d_m = dalloc<int>(c, 1);
-        ck(cudaMallocHost((void **)&c->h_norm, 2 * sizeof(unsigned long long)), "cudaMallocHost");
-        ck(cudaStreamSynchronize(c->stream), "sync");
-        return GCMG_OK;
-    })
+    std::vector<HostLevel> H;
+    try {
+        prepare_levels(*p, phi.data(), H);
+    } catch (const GeomError &g) {
+        gcmg_ctx *c = new (std::nothrow) gcmg_ctx;
+        if (!c) return GCMG_E_OOM;
+        c->err = g.msg;
+        *out = c;
+        return GCMG_E_GEOM;
+    } catch (const std::bad_alloc &) {
+        return GCMG_E_OOM;
+    }
+    return create_from_levels(*p, std::move(H), s, out);
 }
 
 void gcmg_destroy(gcmg_ctx *c) {
@@ -647,8 +626,9 @@ gcmg_status gcmg_set_bc_types(gcmg_ctx *c, int l, const uint8_t *types) {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         HostLevel &L = c->H[l];
         destroy_graph(c);   // the junction arrays are reallocated below
+        c->version++;
         for (int64_t q = 0; q < L.ng(); q++) L.bc[q] = types[q] ? 1 : 0;
-        if (l + 1 == (int)c->H.size()) build_coarse_inverse(L);
+        if (l + 1 == (int)c->H.size()) L.ainv_dirty = true;   // rebuilt before the next solve
         build_junction(L, c->p.junction_radius);
         upload_program(c, L.junction, c->G[l].jz);
         check_program_fits(c, c->G[l].jz);
@@ -680,6 +660,7 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         const HostLevel &L0 = c->H[0];
         const DevGeom &g0 = c->G[0];
+        ensure_inverse(c);
         double *u = c->D64[0].u;   // internal buffer: the captured graph uses fixed pointers
         if (u_dev != u)
             ck(cudaMemcpyAsync(u, u_dev, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u in");

@@ -1,0 +1,788 @@
+// Batched multi-domain solves (gcmg_batch_*): many independent 2D domains of
+// uneven grid sizes advance together.  Every step of the cycle is ONE kernel
+// launch over all domains: each CTA reads a (view, start) item naming the
+// domain level and the tile / component / node range it works on, and runs the
+// same device body as the single-domain kernels (kernels_dev.cuh).  Levels are
+// aligned by depth from the coarsest grid, so a 129^2 domain joins the descent
+// later than a 1025^2 one; each domain still follows its own V-cycle.  The
+// whole solve (FP32 cycles inside FP64 iterative refinement, per-domain
+// convergence) is captured once into a CUDA graph with a device-side while
+// loop.  The fused interior sweep comes in several tile shapes; the autotuner
+// times them on the batch and keeps the fastest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ctx.h"
+#include "gcmg_internal.h"
+#include "kernels.h"
+#include "kernels_dev.cuh"
+
+using namespace gcmg;
+using namespace gcmg::dev;
+
+namespace {
+
+struct BItem {
+    int32_t view;    // index into the view table
+    int32_t start;   // tile / component / first node / first ghost / block
+};
+
+// one level of one domain, in FP32 (the cycle precision of the batch)
+struct BView32 {
+    LevelView<float> v;      // this level
+    LevelView<float> c;      // next coarser level (when it exists)
+    float *cf, *cg;          // coarser level's f and ghost data (restriction targets)
+    const int32_t *tiles;    // active tiles of the selected shape
+    LocalView<float> bz, jz; // boundary blocks, junction zone
+    const int32_t *gt_ptr, *gt_col;
+    const float *gt_val;
+    const int32_t *unk_node, *unk_ghost;
+    const float *Ainv;
+    int nunk;
+    int dom;
+};
+
+// level 0 of one domain in FP64 plus its FP32 correction arrays
+struct BView64 {
+    LevelView<double> v;
+    float *f32, *g32, *e32;
+    int dom;
+};
+
+constexpr int kThreads = 256;
+constexpr int kCoarseBlocks = 4;     // CTAs per domain for the coarsest solve
+constexpr int kVariants = 3;         // tile shapes of the fused sweep
+const int kTileR[kVariants] = {16, 8, 32};
+const int kTileC[kVariants] = {64, 128, 32};
+
+// ---------------------------------------------------------------- kernels
+template <int TR, int TC>
+__global__ void __launch_bounds__(256) kb_fused(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    rb_fused2d_body<float, TR, TC>(V[b.view].v, V[b.view].tiles[b.start]);
+}
+
+__global__ void __launch_bounds__(LOCAL_THREADS) kb_local(const BView32 *__restrict__ V, const BItem *__restrict__ it,
+                                                          int junction, int lead_ghost, int reps) {
+    const BItem b = it[blockIdx.x];
+    local_body<float, 2>(junction ? V[b.view].jz : V[b.view].bz, b.start, lead_ghost, reps);
+}
+
+__global__ void kb_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    const LevelView<float> &v = V[b.view].v;
+    const int64_t p = (int64_t)b.start + threadIdx.x;
+    if (p < v.nn) defect_node<float, 2>(v, p, false);
+}
+
+__global__ void kb_defect_ghost(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    const LevelView<float> &v = V[b.view].v;
+    const int q = b.start + threadIdx.x;
+    if (q < v.ng) defect_ghost_item<float, 9>(v, q);
+}
+
+__global__ void kb_restrict(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    const BView32 &w = V[b.view];
+    const int64_t X = (int64_t)b.start + threadIdx.x;
+    if (X < w.c.nn) restrict_node<float, 2>(w.v, w.c, X, w.cf);
+}
+
+__global__ void kb_transfer(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    const BView32 &w = V[b.view];
+    const int q = b.start + threadIdx.x;
+    if (q < w.c.ng) ghost_transfer_row<float>(w.v.r, w.v.gnode, w.gt_ptr, w.gt_col, w.gt_val, w.cg, q);
+}
+
+// zero u of the view's level (coarse = 0) or of its coarser level (coarse = 1)
+__global__ void kb_zero(const BView32 *__restrict__ V, const BItem *__restrict__ it, int coarse) {
+    const BItem b = it[blockIdx.x];
+    const LevelView<float> &v = coarse ? V[b.view].c : V[b.view].v;
+    const int64_t p = (int64_t)b.start + threadIdx.x;
+    if (p < v.nn) v.u[p] = 0.f;
+}
+
+__global__ void kb_prolong(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    const BView32 &w = V[b.view];
+    const int64_t p = (int64_t)b.start + threadIdx.x;
+    if (p < w.v.nn) prolong_node<float, 2>(w.v, w.c, w.c.u, w.v.u, true, p);
+}
+
+__global__ void kb_coarse(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    const BView32 &w = V[b.view];
+    coarse_rows<float>(w.v, w.unk_node, w.unk_ghost, w.Ainv, w.nunk, b.start, kCoarseBlocks);
+}
+
+// FP64 level 0: defect with per-domain norms (nodes, then ghosts)
+__global__ void kb_defect64(const BView64 *__restrict__ V, const BItem *__restrict__ it, unsigned long long *norms,
+                            int ghosts) {
+    const BItem b = it[blockIdx.x];
+    const LevelView<double> &v = V[b.view].v;
+    double val = 0.0;
+    if (!ghosts) {
+        const int64_t p = (int64_t)b.start + threadIdx.x;
+        if (p < v.nn) val = defect_node<double, 2>(v, p, false);
+    } else {
+        const int q = b.start + threadIdx.x;
+        if (q < v.ng) val = defect_ghost_item<double, 9>(v, q);
+    }
+    reduce_norm(norms + V[b.view].dom, val);
+}
+
+// ||(f, g)|| per domain
+__global__ void kb_rhs_norm(const BView64 *__restrict__ V, const BItem *__restrict__ it, unsigned long long *norms,
+                            int ghosts) {
+    const BItem b = it[blockIdx.x];
+    const LevelView<double> &v = V[b.view].v;
+    double val = 0.0;
+    if (!ghosts) {
+        const int64_t p = (int64_t)b.start + threadIdx.x;
+        if (p < v.nn && (v.type[p] & NODE_KIND) == NODE_IN) val = v.f[p];
+    } else {
+        const int q = b.start + threadIdx.x;
+        if (q < v.ng) val = v.gg[q];
+    }
+    reduce_norm(norms + V[b.view].dom, val);
+}
+
+// FP64 defect -> FP32 right-hand side; e32 = 0
+__global__ void kb_to_f32(const BView64 *__restrict__ V, const BItem *__restrict__ it, int ghosts) {
+    const BItem b = it[blockIdx.x];
+    const BView64 &w = V[b.view];
+    if (!ghosts) {
+        const int64_t p = (int64_t)b.start + threadIdx.x;
+        if (p < w.v.nn) {
+            w.f32[p] = ((w.v.type[p] & NODE_KIND) == NODE_IN) ? (float)w.v.r[p] : 0.f;
+            w.e32[p] = 0.f;
+        }
+    } else {
+        const int q = b.start + threadIdx.x;
+        if (q < w.v.ng) w.g32[q] = (float)w.v.r[w.v.gnode[q]];
+    }
+}
+
+// u64 += e32 on Omega_h u Gamma_h
+__global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    const BView64 &w = V[b.view];
+    const int64_t p = (int64_t)b.start + threadIdx.x;
+    if (p >= w.v.nn) return;
+    const uint8_t k = w.v.type[p] & NODE_KIND;
+    if (k == NODE_IN || k == NODE_GHOST) w.v.u[p] += (double)w.e32[p];
+}
+
+// end of one refinement step: per-domain relative residual, loop condition
+__global__ void kb_check(cudaGraphConditionalHandle h, const unsigned long long *norms, const double *r0, double *rel,
+                         int *m, int ndom, double rtol, int max_steps) {
+    __shared__ int pending;
+    if (threadIdx.x == 0) pending = 0;
+    __syncthreads();
+    const int k = *m + 1;
+    for (int d = threadIdx.x; d < ndom; d += blockDim.x) {
+        const double v = __longlong_as_double((long long)norms[d]) / r0[d];
+        if (k <= 256) rel[(size_t)d * 257 + k] = v;
+        if (!(v <= rtol)) atomicAdd(&pending, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *m = k;
+        cudaGraphSetConditional(h, (pending > 0 && k < max_steps) ? 1u : 0u);
+    }
+}
+
+struct CudaFail {
+    cudaError_t e;
+    const char *what;
+};
+inline void ck(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw CudaFail{e, what};
+}
+
+// a captured launch: kernel kind, item range and parameters
+struct Launch {
+    enum Kind { FUSED, BOUNDARY, JUNCTION, DEFECT, DEFECT_GHOST, RESTRICT, TRANSFER, ZERO_COARSE, PROLONG, COARSE,
+                ZERO };
+    Kind kind;
+    size_t off, count;
+    size_t smem;
+};
+
+}  // namespace
+
+struct gcmg_batch {
+    std::vector<gcmg_ctx *> doms;
+    cudaStream_t stream = nullptr, gstream = nullptr;
+    int device = 0;
+    int variant = 0;
+    double rtol = 1e-10;
+    int max_steps = 100;
+    // device tables
+    std::vector<std::vector<int>> view_of;    // [dom][level] -> view index
+    BView32 *d_v32 = nullptr;
+    BView64 *d_v64 = nullptr;
+    BItem *d_items = nullptr;
+    std::vector<int32_t *> tile_bufs;         // tile lists per view for the selected shape
+    std::vector<Launch> cycle;                // FP32 V-cycle over all domains
+    size_t items64_nodes = 0, items64_ghosts = 0, n_items64_nodes = 0, n_items64_ghosts = 0;
+    unsigned long long *d_norms = nullptr;
+    double *d_r0 = nullptr, *d_rel = nullptr;
+    int *d_m = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<int> versions;
+    long long graph_kernels = 0;
+    std::string err;
+};
+
+namespace {
+
+gcmg_status bfail(gcmg_batch *b, gcmg_status s, const std::string &m) {
+    if (b) b->err = m;
+    return s;
+}
+
+#define BATCH_GUARD(b, ...)                                                                     \
+    try {                                                                                        \
+        __VA_ARGS__                                                                              \
+    } catch (const CudaFail &f) {                                                                \
+        cudaGetLastError();                                                                      \
+        return bfail(b, GCMG_E_CUDA, std::string(f.what) + ": " + cudaGetErrorString(f.e));      \
+    } catch (const GeomError &g) {                                                               \
+        return bfail(b, GCMG_E_GEOM, g.msg);                                                     \
+    } catch (const std::bad_alloc &) {                                                           \
+        return bfail(b, GCMG_E_OOM, "allocation failed");                                        \
+    }
+
+void free_tables(gcmg_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    for (void *p : {(void *)b->d_v32, (void *)b->d_v64, (void *)b->d_items}) cudaFree(p);
+    b->d_v32 = nullptr;
+    b->d_v64 = nullptr;
+    b->d_items = nullptr;
+    for (int32_t *t : b->tile_bufs) cudaFree(t);
+    b->tile_bufs.clear();
+    b->cycle.clear();
+}
+
+// tiles of shape tr x tc holding inside nodes (packed row tile << 16 | column tile)
+std::vector<int32_t> tiles_for(const HostLevel &L, int tr, int tc) {
+    const int nr = (L.n + tr - 1) / tr, ncol = (L.n + tc - 1) / tc;
+    std::vector<uint8_t> act((size_t)nr * ncol, 0);
+    for (int64_t p = 0; p < L.nn; p++)
+        if ((L.type[p] & NODE_KIND) == NODE_IN) act[(p / L.n) / tr * ncol + (p % L.n) / tc] = 1;
+    std::vector<int32_t> t;
+    for (int a = 0; a < nr; a++)
+        for (int c = 0; c < ncol; c++)
+            if (act[(size_t)a * ncol + c]) t.push_back((a << 16) | c);
+    return t;
+}
+
+size_t smem_of(const LocalView<float> &J) {
+    LocalView<float> tmp = J;
+    return local_smem_bytes<float>(tmp, 2);
+}
+
+// Builds the view tables and the launch schedule of one FP32 V-cycle.
+void build_tables(gcmg_batch *b) {
+    free_tables(b);
+    const int nd = (int)b->doms.size();
+    std::vector<BView32> v32;
+    std::vector<BView64> v64;
+    std::vector<int> ntile;   // tiles per view
+    b->view_of.assign(nd, {});
+    int kmax = 0;
+    const int tr = kTileR[b->variant], tc = kTileC[b->variant];
+    for (int d = 0; d < nd; d++) {
+        gcmg_ctx *c = b->doms[d];
+        const int nl = (int)c->H.size();
+        kmax = std::max(kmax, nl - 1);
+        for (int l = 0; l < nl; l++) {
+            BView32 w;
+            std::memset(&w, 0, sizeof(w));
+            w.v = view<float>(c, l, c->D32[l]);
+            if (l + 1 < nl) {
+                w.c = view<float>(c, l + 1, c->D32[l + 1]);
+                w.cf = c->D32[l + 1].f;
+                w.cg = c->D32[l + 1].gg;
+            }
+            std::vector<int32_t> t = tiles_for(c->H[l], tr, tc);
+            int32_t *dt = nullptr;
+            ck(cudaMalloc(&dt, std::max<size_t>(t.size(), 1) * sizeof(int32_t)), "cudaMalloc");
+            b->tile_bufs.push_back(dt);
+            if (!t.empty()) ck(cudaMemcpy(dt, t.data(), t.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
+            w.tiles = dt;
+            ntile.push_back((int)t.size());
+            w.bz = lview<float>(c->G[l].bz, w.v);
+            w.jz = lview<float>(c->G[l].jz, w.v);
+            w.gt_ptr = c->G[l].gt_ptr;
+            w.gt_col = c->G[l].gt_col;
+            w.gt_val = c->D32[l].gt_val;
+            w.unk_node = c->G[l].unk_node;
+            w.unk_ghost = c->G[l].unk_ghost;
+            w.Ainv = c->D32[l].Ainv;
+            w.nunk = c->G[l].nunk;
+            w.dom = d;
+            b->view_of[d].push_back((int)v32.size());
+            v32.push_back(w);
+            if (!c->G[l].bz.in_smem || (c->p.junction_sweeps > 0 && c->G[l].jz.ncomp > 0 && !c->G[l].jz.in_smem))
+                throw GeomError{"a batched domain needs shared-memory boundary and junction programs"};
+        }
+        BView64 w64;
+        std::memset(&w64, 0, sizeof(w64));
+        w64.v = view<double>(c, 0, c->D64[0]);
+        w64.f32 = c->D32[0].f;
+        w64.g32 = c->D32[0].gg;
+        w64.e32 = c->D32[0].u;
+        w64.dom = d;
+        v64.push_back(w64);
+    }
+    // items
+    std::vector<BItem> items;
+    auto dense = [&](int view, int64_t count) {
+        for (int64_t s = 0; s < count; s += kThreads) items.push_back({view, (int32_t)s});
+    };
+    auto add_launch = [&](Launch::Kind k, size_t before, size_t smem) {
+        if (items.size() > before) b->cycle.push_back({k, before, items.size() - before, smem});
+    };
+    const gcmg_params &p0 = b->doms[0]->p;
+    auto relax = [&](int k) {
+        size_t s0 = items.size();
+        for (int d = 0; d < nd; d++) {
+            const int l = (int)b->doms[d]->H.size() - 1 - k;
+            if (l < 0) continue;
+            const int vi = b->view_of[d][l];
+            for (int i = 0; i < ntile[vi]; i++) items.push_back({vi, (int32_t)i});
+        }
+        add_launch(Launch::FUSED, s0, 0);
+        for (int which = 0; which < 2; which++) {
+            s0 = items.size();
+            size_t smem = 0;
+            for (int d = 0; d < nd; d++) {
+                const int l = (int)b->doms[d]->H.size() - 1 - k;
+                if (l < 0) continue;
+                const int vi = b->view_of[d][l];
+                const LocalView<float> &J = which ? v32[vi].jz : v32[vi].bz;
+                if (which && b->doms[d]->p.junction_sweeps <= 0) continue;
+                for (int c = 0; c < J.ncomp; c++) items.push_back({vi, c});
+                if (J.ncomp) smem = std::max(smem, smem_of(J));
+            }
+            add_launch(which ? Launch::JUNCTION : Launch::BOUNDARY, s0, smem);
+        }
+    };
+    for (int k = kmax; k >= 1; k--) {
+        for (int r = 0; r < p0.nu1; r++) relax(k);
+        size_t s0 = items.size();
+        for (int d = 0; d < nd; d++) {
+            const int l = (int)b->doms[d]->H.size() - 1 - k;
+            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].nn);
+        }
+        add_launch(Launch::DEFECT, s0, 0);
+        s0 = items.size();
+        for (int d = 0; d < nd; d++) {
+            const int l = (int)b->doms[d]->H.size() - 1 - k;
+            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].ng());
+        }
+        add_launch(Launch::DEFECT_GHOST, s0, 0);
+        s0 = items.size();
+        for (int d = 0; d < nd; d++) {
+            const int l = (int)b->doms[d]->H.size() - 1 - k;
+            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l + 1].nn);
+        }
+        add_launch(Launch::RESTRICT, s0, 0);
+        add_launch(Launch::ZERO_COARSE, s0, 0);   // same items: the coarser grid's nodes
+        s0 = items.size();
+        for (int d = 0; d < nd; d++) {
+            const int l = (int)b->doms[d]->H.size() - 1 - k;
+            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l + 1].ng());
+        }
+        add_launch(Launch::TRANSFER, s0, 0);
+    }
+    {
+        size_t s0 = items.size();
+        for (int d = 0; d < nd; d++) dense(b->view_of[d].back(), b->doms[d]->H.back().nn);
+        add_launch(Launch::ZERO, s0, 0);
+        s0 = items.size();
+        size_t smem = 0;
+        for (int d = 0; d < nd; d++) {
+            for (int blk = 0; blk < kCoarseBlocks; blk++) items.push_back({b->view_of[d].back(), blk});
+            smem = std::max(smem, sizeof(float) * (size_t)v32[b->view_of[d].back()].nunk);
+        }
+        add_launch(Launch::COARSE, s0, smem);
+    }
+    for (int k = 1; k <= kmax; k++) {
+        size_t s0 = items.size();
+        for (int d = 0; d < nd; d++) {
+            const int l = (int)b->doms[d]->H.size() - 1 - k;
+            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].nn);
+        }
+        add_launch(Launch::PROLONG, s0, 0);
+        for (int r = 0; r < p0.nu2; r++) relax(k);
+    }
+    // FP64 level-0 items (view index = domain)
+    b->items64_nodes = items.size();
+    for (int d = 0; d < nd; d++) dense(d, b->doms[d]->H[0].nn);
+    b->n_items64_nodes = items.size() - b->items64_nodes;
+    b->items64_ghosts = items.size();
+    for (int d = 0; d < nd; d++) dense(d, b->doms[d]->H[0].ng());
+    b->n_items64_ghosts = items.size() - b->items64_ghosts;
+    ck(cudaMalloc(&b->d_v32, v32.size() * sizeof(BView32)), "cudaMalloc");
+    ck(cudaMalloc(&b->d_v64, v64.size() * sizeof(BView64)), "cudaMalloc");
+    ck(cudaMalloc(&b->d_items, std::max<size_t>(items.size(), 1) * sizeof(BItem)), "cudaMalloc");
+    ck(cudaMemcpy(b->d_v32, v32.data(), v32.size() * sizeof(BView32), cudaMemcpyHostToDevice), "views");
+    ck(cudaMemcpy(b->d_v64, v64.data(), v64.size() * sizeof(BView64), cudaMemcpyHostToDevice), "views");
+    ck(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice), "items");
+    b->versions.clear();
+    for (gcmg_ctx *c : b->doms) b->versions.push_back(c->version);
+}
+
+template <int TR, int TC>
+void launch_fused(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
+    kb_fused<TR, TC><<<(unsigned)L.count, 256, 0, s>>>(b->d_v32, b->d_items + L.off);
+}
+
+void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
+    const BItem *it = b->d_items + L.off;
+    const unsigned n = (unsigned)L.count;
+    const int junction_sweeps = b->doms[0]->p.junction_sweeps, lambda = b->doms[0]->p.lambda;
+    switch (L.kind) {
+        case Launch::FUSED:
+            if (b->variant == 0) launch_fused<16, 64>(b, L, s);
+            else if (b->variant == 1) launch_fused<8, 128>(b, L, s);
+            else launch_fused<32, 32>(b, L, s);
+            break;
+        case Launch::BOUNDARY: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda); break;
+        case Launch::JUNCTION: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps); break;
+        case Launch::DEFECT: kb_defect<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::DEFECT_GHOST: kb_defect_ghost<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::RESTRICT: kb_restrict<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::ZERO_COARSE: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 1); break;
+        case Launch::TRANSFER: kb_transfer<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::ZERO: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 0); break;
+        case Launch::COARSE: kb_coarse<<<n, 512, L.smem, s>>>(b->d_v32, it); break;
+        case Launch::PROLONG: kb_prolong<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+    }
+}
+
+// one refinement step of every domain, then the FP64 defect norms
+void step_body(gcmg_batch *b, cudaStream_t s) {
+    const BItem *in = b->d_items + b->items64_nodes, *ig = b->d_items + b->items64_ghosts;
+    kb_to_f32<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, 0);
+    if (b->n_items64_ghosts) kb_to_f32<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, 1);
+    for (const Launch &L : b->cycle) launch_one(b, L, s);
+    kb_add<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in);
+    ck(cudaMemsetAsync(b->d_norms, 0, b->doms.size() * sizeof(unsigned long long), s), "memset");
+    kb_defect64<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0);
+    if (b->n_items64_ghosts) kb_defect64<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1);
+}
+
+long long step_kernels(const gcmg_batch *b) {
+    return (long long)b->cycle.size() + 4 + (b->n_items64_ghosts ? 2 : 0) + 1;
+}
+
+void build_graph(gcmg_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    ck(cudaGraphCreate(&b->graph, 0), "cudaGraphCreate");
+    cudaGraphConditionalHandle h;
+    ck(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault), "conditional handle");
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    ck(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np), "cudaGraphAddNode");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ck(cudaStreamBeginCaptureToGraph(b->gstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+       "begin capture");
+    try {
+        step_body(b, b->gstream);
+        kb_check<<<1, 256, 0, b->gstream>>>(h, b->d_norms, b->d_r0, b->d_rel, b->d_m, (int)b->doms.size(), b->rtol,
+                                            b->max_steps);
+    } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(b->gstream, &dummy);
+        throw;
+    }
+    cudaGraph_t captured;
+    ck(cudaStreamEndCapture(b->gstream, &captured), "end capture");
+    ck(cudaGraphInstantiate(&b->gexec, b->graph, 0), "cudaGraphInstantiate");
+    b->graph_kernels = step_kernels(b);
+}
+
+bool stale(const gcmg_batch *b) {
+    if (!b->d_items || b->versions.size() != b->doms.size()) return true;
+    for (size_t d = 0; d < b->doms.size(); d++)
+        if (b->doms[d]->version != b->versions[d]) return true;
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double *const *phi_dev, void *stream,
+                              gcmg_batch **out) {
+    if (!out) return GCMG_E_ARG;
+    *out = nullptr;
+    if (count <= 0 || !params || !phi_dev) return GCMG_E_ARG;
+    for (int i = 0; i < count; i++) {
+        const gcmg_params &p = params[i];
+        if (!phi_dev[i] || check_params(p) != GCMG_OK || p.dim != 2 || p.precision != 1 || p.gamma != 1 ||
+            p.nu1 != params[0].nu1 || p.nu2 != params[0].nu2 || p.lambda != params[0].lambda ||
+            p.junction_sweeps != params[0].junction_sweeps)
+            return GCMG_E_ARG;
+    }
+    gcmg_batch *b = new (std::nothrow) gcmg_batch;
+    if (!b) return GCMG_E_OOM;
+    *out = b;
+    b->stream = (cudaStream_t)stream;
+    b->rtol = params[0].rtol;
+    b->max_steps = params[0].max_cycles;
+    BATCH_GUARD(b, {
+        ck(cudaGetDevice(&b->device), "cudaGetDevice");
+        // level sets to the host, then host geometry of all domains in parallel
+        std::vector<std::vector<double>> phi(count);
+        for (int i = 0; i < count; i++) {
+            int64_t nn = (int64_t)params[i].n * params[i].n;
+            phi[i].resize(nn);
+            ck(cudaMemcpyAsync(phi[i].data(), phi_dev[i], nn * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+               "phi");
+        }
+        ck(cudaStreamSynchronize(b->stream), "sync");
+        std::vector<std::vector<HostLevel>> H(count);
+        std::vector<std::string> errs(count);
+        std::atomic<int> next{0};
+        const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (unsigned t = 0; t < nt; t++)
+            pool.emplace_back([&]() {
+                for (int i = next++; i < count; i = next++) {
+                    try {
+                        prepare_levels(params[i], phi[i].data(), H[i]);
+                    } catch (const GeomError &g) {
+                        errs[i] = g.msg;
+                    } catch (const std::bad_alloc &) {
+                        errs[i] = "allocation failed";
+                    }
+                }
+            });
+        for (auto &t : pool) t.join();
+        for (int i = 0; i < count; i++)
+            if (!errs[i].empty()) return bfail(b, GCMG_E_GEOM, "domain " + std::to_string(i) + ": " + errs[i]);
+        for (int i = 0; i < count; i++) {
+            gcmg_ctx *c = nullptr;
+            const gcmg_status s = create_from_levels(params[i], std::move(H[i]), b->stream, &c);
+            if (s != GCMG_OK) {
+                const std::string m = c ? c->err : std::string("create failed");
+                if (c) gcmg_destroy(c);
+                return bfail(b, s, "domain " + std::to_string(i) + ": " + m);
+            }
+            b->doms.push_back(c);
+        }
+        int smax = 0;
+        ck(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device), "attr");
+        ck(cudaFuncSetAttribute(kb_local, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "attr");
+        ck(cudaFuncSetAttribute(kb_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "attr");
+        ck(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
+        ck(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        ck(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+        ck(cudaMalloc(&b->d_norms, count * sizeof(unsigned long long)), "cudaMalloc");
+        ck(cudaMalloc(&b->d_r0, count * sizeof(double)), "cudaMalloc");
+        ck(cudaMalloc(&b->d_rel, (size_t)count * 257 * sizeof(double)), "cudaMalloc");
+        ck(cudaMalloc(&b->d_m, sizeof(int)), "cudaMalloc");
+        return GCMG_OK;
+    })
+}
+
+void gcmg_batch_destroy(gcmg_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->gstream) cudaStreamSynchronize(b->gstream);
+    free_tables(b);
+    for (gcmg_ctx *c : b->doms) gcmg_destroy(c);
+    for (void *p : {(void *)b->d_norms, (void *)b->d_r0, (void *)b->d_rel, (void *)b->d_m}) cudaFree(p);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    delete b;
+}
+
+const char *gcmg_batch_last_error(const gcmg_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+int gcmg_batch_size(const gcmg_batch *b) { return b ? (int)b->doms.size() : 0; }
+
+gcmg_ctx *gcmg_batch_domain(gcmg_batch *b, int i) {
+    return (b && i >= 0 && i < (int)b->doms.size()) ? b->doms[i] : nullptr;
+}
+
+gcmg_status gcmg_batch_set_tiles(gcmg_batch *b, int variant) {
+    if (!b || variant < 0 || variant >= kVariants) return bfail(b, GCMG_E_ARG, "bad tile variant");
+    if (b->variant != variant) {
+        b->variant = variant;
+        b->versions.clear();   // rebuild tables at the next solve
+    }
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_batch_solve(gcmg_batch *b, gcmg_stats *stats, int *steps) {
+    if (!b) return GCMG_E_ARG;
+    for (gcmg_ctx *c : b->doms)
+        if (!c->rhs_set) return bfail(b, GCMG_E_STATE, "gcmg_set_rhs has not been called for every domain");
+    BATCH_GUARD(b, {
+        ck(cudaSetDevice(b->device), "cudaSetDevice");
+        {   // coarsest inverses out of date: rebuild on host threads, then upload
+            std::vector<int> dirty;
+            for (int d = 0; d < (int)b->doms.size(); d++)
+                if (b->doms[d]->H.back().ainv_dirty) dirty.push_back(d);
+            std::vector<std::string> errs(dirty.size());
+            std::atomic<int> next{0};
+            const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+            std::vector<std::thread> pool;
+            for (unsigned t = 0; t < nt; t++)
+                pool.emplace_back([&]() {
+                    for (int i = next++; i < (int)dirty.size(); i = next++) {
+                        try {
+                            build_coarse_inverse(b->doms[dirty[i]]->H.back());
+                        } catch (const GeomError &g) {
+                            errs[i] = g.msg;
+                        }
+                    }
+                });
+            for (auto &t : pool) t.join();
+            for (size_t i = 0; i < dirty.size(); i++) {
+                if (!errs[i].empty()) return bfail(b, GCMG_E_GEOM, "domain " + std::to_string(dirty[i]) + ": " + errs[i]);
+                upload_inverse(b->doms[dirty[i]]);
+            }
+        }
+        if (stale(b)) {
+            build_tables(b);
+            build_graph(b);
+        }
+        const int nd = (int)b->doms.size();
+        cudaStream_t s = b->stream;
+        const BItem *in = b->d_items + b->items64_nodes, *ig = b->d_items + b->items64_ghosts;
+        for (gcmg_ctx *c : b->doms)
+            ck(cudaMemsetAsync(c->D64[0].u, 0, c->H[0].nn * sizeof(double), s), "memset");
+        // ||r0|| = ||(f, g)|| per domain
+        ck(cudaMemsetAsync(b->d_norms, 0, nd * sizeof(unsigned long long), s), "memset");
+        kb_rhs_norm<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0);
+        if (b->n_items64_ghosts) kb_rhs_norm<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1);
+        std::vector<unsigned long long> bits(nd);
+        ck(cudaMemcpyAsync(bits.data(), b->d_norms, nd * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s), "r0");
+        ck(cudaStreamSynchronize(s), "sync");
+        std::vector<double> r0(nd);
+        for (int d = 0; d < nd; d++) {
+            std::memcpy(&r0[d], &bits[d], sizeof(double));
+            if (!(r0[d] > 0.0)) r0[d] = 1.0;
+        }
+        ck(cudaMemcpyAsync(b->d_r0, r0.data(), nd * sizeof(double), cudaMemcpyHostToDevice, s), "r0");
+        // defect of u = 0 (the FP64 defect every step starts from)
+        ck(cudaMemsetAsync(b->d_norms, 0, nd * sizeof(unsigned long long), s), "memset");
+        kb_defect64<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0);
+        if (b->n_items64_ghosts) kb_defect64<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1);
+        ck(cudaGetLastError(), "kernel launch");
+        const int zero = 0;
+        ck(cudaMemcpyAsync(b->d_m, &zero, sizeof(int), cudaMemcpyHostToDevice, s), "m");
+        ck(cudaEventRecord(b->ev_in, s), "event");
+        ck(cudaStreamWaitEvent(b->gstream, b->ev_in, 0), "wait");
+        ck(cudaGraphLaunch(b->gexec, b->gstream), "cudaGraphLaunch");
+        ck(cudaEventRecord(b->ev_out, b->gstream), "event");
+        ck(cudaStreamWaitEvent(s, b->ev_out, 0), "wait");
+        int m = 0;
+        ck(cudaMemcpyAsync(&m, b->d_m, sizeof(int), cudaMemcpyDeviceToHost, s), "m");
+        ck(cudaStreamSynchronize(s), "sync");
+        g_launches += 4 + b->graph_kernels * m;
+        std::vector<double> rel((size_t)nd * 257, 0.0);
+        ck(cudaMemcpy(rel.data(), b->d_rel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost), "rel");
+        bool all = true;
+        for (int d = 0; d < nd; d++) {
+            const int kept = std::min(m, 256);
+            const double last = kept > 0 ? rel[(size_t)d * 257 + kept] : 1.0;
+            const bool ok = last <= b->rtol;
+            all = all && ok;
+            if (stats) {
+                gcmg_stats &st = stats[d];
+                std::memset(&st, 0, sizeof(st));
+                st.cycles = m;
+                st.converged = ok ? 1 : 0;
+                st.rel_residual = last;
+                st.r0_norm = r0[d];
+                st.rel[0] = 1.0;
+                for (int k = 1; k <= kept; k++) st.rel[k] = rel[(size_t)d * 257 + k];
+            }
+        }
+        if (steps) *steps = m;
+        if (!all) return bfail(b, GCMG_E_NOCONV, "not every domain converged");
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_batch_get_solution(gcmg_batch *b, int i, double *u_dev) {
+    if (!b || i < 0 || i >= (int)b->doms.size() || !u_dev) return bfail(b, GCMG_E_ARG, "bad argument");
+    BATCH_GUARD(b, {
+        const gcmg_ctx *c = b->doms[i];
+        ck(cudaMemcpyAsync(u_dev, c->D64[0].u, c->H[0].nn * sizeof(double), cudaMemcpyDeviceToDevice, b->stream),
+           "copy");
+        ck(cudaStreamSynchronize(b->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
+// Times one batched sweep set (all relaxations of one cycle) for each tile
+// shape and selects the fastest; ms[k] receives the time of shape k.
+gcmg_status gcmg_batch_autotune(gcmg_batch *b, int *best, double *ms) {
+    if (!b) return GCMG_E_ARG;
+    BATCH_GUARD(b, {
+        ck(cudaSetDevice(b->device), "cudaSetDevice");
+        cudaEvent_t e0, e1;
+        ck(cudaEventCreate(&e0), "event");
+        ck(cudaEventCreate(&e1), "event");
+        double bestms = 1e30;
+        int bestv = b->variant;
+        for (int v = 0; v < kVariants; v++) {
+            b->variant = v;
+            build_tables(b);
+            for (int rep = 0; rep < 3; rep++) {   // warm-up, then timed twice
+                ck(cudaEventRecord(e0, b->stream), "event");
+                for (const Launch &L : b->cycle)
+                    if (L.kind == Launch::FUSED) launch_one(b, L, b->stream);
+                ck(cudaEventRecord(e1, b->stream), "event");
+            }
+            ck(cudaEventSynchronize(e1), "sync");
+            float t = 0.f;
+            ck(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+            ck(cudaGetLastError(), "kernel launch");
+            if (ms) ms[v] = t;
+            if (t < bestms) { bestms = t; bestv = v; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->variant = bestv;
+        b->versions.clear();
+        if (best) *best = bestv;
+        return GCMG_OK;
+    })
+}
+
+}  // extern "C"

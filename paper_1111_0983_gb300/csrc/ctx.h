@@ -1,0 +1,104 @@
+// Internal: the context behind the C ABI (shared by api.cu and batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "gcmg_internal.h"
+
+using gcmg::DevData;
+using gcmg::DevGeom;
+using gcmg::HostLevel;
+using gcmg::LevelView;
+using gcmg::LocalDev;
+using gcmg::LocalView;
+
+struct gcmg_ctx {
+    gcmg_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<HostLevel> H;
+    std::vector<DevGeom> G;
+    std::vector<DevData<double>> D64;
+    std::vector<DevData<float>> D32;
+    bool rhs_set = false;
+    unsigned long long *d_norm = nullptr;   // two slots: defect norm, rhs norm
+    unsigned long long *h_norm = nullptr;   // pinned
+    // the solve loop as one CUDA graph: a device-side while loop over cycles
+    cudaStream_t gstream = nullptr;         // capture / launch stream (never the legacy one)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    double *d_rel = nullptr;                // rel[0..256]
+    double *d_r0 = nullptr;
+    int *d_m = nullptr;
+    bool use_graph = true;
+    long long graph_kernels = 0;            // kernels in one loop iteration
+    // event timing of one fine-level kernel class during solves
+    int timing_kind = -1;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    std::vector<void *> allocs;
+    std::string err;
+    int version = 0;                        // bumped when the boundary types change
+};
+
+
+namespace gcmg {
+
+template <typename T>
+LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
+    const HostLevel &L = c->H[l];
+    const DevGeom &g = c->G[l];
+    LevelView<T> v;
+    v.n = L.n;
+    v.nn = L.nn;
+    v.s0 = L.stride[0];
+    v.s1 = L.stride[1];
+    v.s2 = L.dim == 3 ? L.stride[2] : 0;
+    v.h2 = (T)(L.h * L.h);
+    v.inv_h2 = (T)(1.0 / (L.h * L.h));
+    v.type = g.type;
+    v.u = D.u;
+    v.f = D.f;
+    v.r = D.r;
+    v.ng = g.ng;
+    v.gnode = g.gnode;
+    v.gstn = g.gstn;
+    v.gw = D.gw;
+    v.gc = D.gc;
+    v.gg = D.gg;
+    v.gtmp = D.gtmp;
+    return v;
+}
+
+template <typename T>
+LocalView<T> lview(const LocalDev &z, const LevelView<T> &v) {
+    LocalView<T> J;
+    J.ncomp = z.ncomp;
+    J.max_nodes = z.max_nodes;
+    J.max_int = z.max_int;
+    J.max_gh = z.max_gh;
+    J.ng = v.ng;
+    J.node_off = z.node_off; J.wb_cnt = z.wb_cnt; J.lnode = z.lnode;
+    J.int_off = z.int_off; J.red_cnt = z.red_cnt; J.int_glob = z.int_glob; J.int_me = z.int_me; J.int_nb = z.int_nb;
+    J.gh_off = z.gh_off; J.gh_me = z.gh_me; J.gh_q = z.gh_q; J.gh_stn = z.gh_stn;
+    J.u = v.u; J.f = v.f; J.gg = v.gg; J.gc = v.gc; J.gw = v.gw;
+    J.h2 = v.h2;
+    return J;
+}
+
+// Host geometry of a context's levels (no CUDA calls; thread safe): the
+// hierarchy of build_hierarchy plus the 2D boundary-block programs.
+void prepare_levels(const gcmg_params &p, const double *phi_host, std::vector<HostLevel> &H);
+// Validates p; GCMG_OK if usable.
+gcmg_status check_params(const gcmg_params &p);
+// Rebuilds (if out of date) and uploads the coarsest inverse; upload only.
+void ensure_inverse(gcmg_ctx *c);
+void upload_inverse(gcmg_ctx *c);
+// Creates a context from prepared levels (uploads everything to the current device).
+gcmg_status create_from_levels(const gcmg_params &p, std::vector<HostLevel> &&H, cudaStream_t stream, gcmg_ctx **out);
+
+}  // namespace gcmg

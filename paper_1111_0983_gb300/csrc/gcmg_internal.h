@@ -75,6 +75,7 @@ struct HostLevel {
     // coarsest level: unknowns (node, ghost number or -1) and dense inverse
     std::vector<int32_t> unk_node, unk_ghost;
     std::vector<double> Ainv;           // nunk * nunk, row major
+    bool ainv_dirty = true;             // Ainv out of date with bc
 
     int64_t ng() const { return (int64_t)ghost_node.size(); }
 };
@@ -85,6 +86,8 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
 // Partial-transfer weights (Sec. 2.5) at the fine image p of a coarse node over
 // the inside set (interior) or its complement; wt[3^dim], axis 0 slowest.
 bool partial_transfer_weights(const HostLevel &F, int64_t p, bool interior, double *wt);
+// Unknown numbering of the coarsest level (independent of bc).
+void number_coarse_unknowns(HostLevel &L);
 // Dense inverse of the coarsest system with the level's current bc (throws GeomError).
 void build_coarse_inverse(HostLevel &L);
 // Junction zone of the level's current bc (radius in h).

@@ -1,0 +1,426 @@
+// Device-side bodies of the per-level kernels, shared by the single-domain
+// kernels (kernels.cu) and the batched multi-domain kernels (batch.cu).  Each
+// body does the work of one thread (or one CTA) for one item -- a node, a
+// ghost, a tile or a program component -- given that level's view.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gcmg_internal.h"
+
+namespace gcmg {
+namespace dev {
+
+constexpr int LOCAL_THREADS = 512;
+constexpr int LOCAL_EPT = 4;     // inside entries per thread and colour in local programs
+
+// max-norm reduction on the bit pattern of a non-negative double (monotone
+// for non-negative IEEE values); NaN is folded into +Inf so that it is seen.
+__device__ __forceinline__ void atomic_max_abs(unsigned long long *bits, double v) {
+    v = fabs(v);
+    if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);
+    atomicMax(bits, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// block-wide max of |v| (every thread of the block must call), one atomic per block
+__device__ __forceinline__ void reduce_norm(unsigned long long *bits, double v) {
+    if (!bits) return;
+    __shared__ double wmax[32];
+    double a = fabs(v);
+    if (a != a) a = __longlong_as_double(0x7ff0000000000000ll);
+    a = warp_max(a);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) wmax[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        a = (int)threadIdx.x < nw ? wmax[threadIdx.x] : 0.0;
+        a = warp_max(a);
+        if (threadIdx.x == 0 && a > 0.0) atomic_max_abs(bits, a);
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T neighbour_sum(const T *__restrict__ u, int64_t p, int64_t s0, int64_t s1) {
+    T s = u[p - 1] + u[p + 1] + u[p - s0] + u[p + s0];
+    if (D == 3) s += u[p - s1] + u[p + s1];
+    return s;
+}
+
+// ------------------------------------------------------------ fused sweep
+// Both colours of the Gauss-Seidel form of Eq. (jac2d) in one pass over one
+// 2D tile (TR x TC nodes, axis 1 contiguous; tile = row tile << 16 | column
+// tile): u staged with a 2-node halo, f and node types with a 1-node halo;
+// red nodes updated on the tile and its 1-node halo (the values the
+// neighbouring tiles compute for their own nodes), then black nodes on the
+// tile; the tile's inside nodes are stored.  Equal to a red half-sweep
+// followed by a black half-sweep over the whole grid.
+template <typename T, int TR, int TC>
+__device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, int tile) {
+    constexpr int UR = TR + 4, UC = TC + 4, FR = TR + 2, FC = TC + 2;
+    __shared__ T su[UR][UC];
+    __shared__ T sf[FR][FC];
+    __shared__ uint8_t sk[FR][FC];
+    const int i0 = (tile >> 16) * TR, j0 = (tile & 0xffff) * TC;
+    const int n = v.n;
+    for (int idx = threadIdx.x; idx < UR * UC; idx += blockDim.x) {
+        const int r = idx / UC, cc = idx - r * UC;
+        const int gi = i0 - 2 + r, gj = j0 - 2 + cc;
+        su[r][cc] = (gi >= 0 && gi < n && gj >= 0 && gj < n) ? v.u[(int64_t)gi * v.s0 + gj] : (T)0;
+    }
+    for (int idx = threadIdx.x; idx < FR * FC; idx += blockDim.x) {
+        const int r = idx / FC, cc = idx - r * FC;
+        const int gi = i0 - 1 + r, gj = j0 - 1 + cc;
+        const bool in = gi >= 0 && gi < n && gj >= 0 && gj < n;
+        const int64_t p = (int64_t)gi * v.s0 + gj;
+        const uint8_t k = in ? (uint8_t)(v.type[p] & NODE_KIND) : (uint8_t)NODE_OUT;
+        sk[r][cc] = k;
+        sf[r][cc] = (k == NODE_IN) ? v.h2 * v.f[p] : (T)0;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < FR * FC; idx += blockDim.x) {
+        const int r = idx / FC, cc = idx - r * FC;
+        if (sk[r][cc] != NODE_IN || (((i0 - 1 + r) + (j0 - 1 + cc)) & 1)) continue;
+        const int ur = r + 1, uc = cc + 1;
+        su[ur][uc] = (sf[r][cc] + su[ur - 1][uc] + su[ur + 1][uc] + su[ur][uc - 1] + su[ur][uc + 1]) * (T)0.25;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TR * TC; idx += blockDim.x) {
+        const int r = idx / TC, cc = idx - r * TC;
+        if (sk[r + 1][cc + 1] != NODE_IN || (((i0 + r) + (j0 + cc)) & 1) == 0) continue;
+        const int ur = r + 2, uc = cc + 2;
+        su[ur][uc] = (sf[r + 1][cc + 1] + su[ur - 1][uc] + su[ur + 1][uc] + su[ur][uc - 1] + su[ur][uc + 1]) * (T)0.25;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TR * TC; idx += blockDim.x) {
+        const int r = idx / TC, cc = idx - r * TC;
+        if (sk[r + 1][cc + 1] != NODE_IN) continue;
+        v.u[(int64_t)(i0 + r) * v.s0 + (j0 + cc)] = su[r + 2][cc + 2];
+    }
+}
+
+// ------------------------------------------------------- local programs
+// One component of a LocalProgram relaxed in shared memory by one CTA of
+// LOCAL_THREADS threads: node values, ghost weights, stencil slots, g and
+// mu dt staged in shared memory, each thread's inside entries (slot,
+// neighbour slots, h^2 f) in registers; an optional ghost sweep, then reps x
+// (red, black, Jacobi ghosts); the write-back nodes are stored.  Junction
+// zones are components closed under their reads; 2D boundary blocks carry a
+// halo covering the dependency cone of the sweeps, so the written values
+// equal those of the global sweeps.
+template <typename T, int D>
+__device__ __forceinline__ void local_body(const LocalView<T> &J, int c, int lead_ghost, int reps) {
+    constexpr int K = D == 2 ? 9 : 27;
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    const int n0 = J.node_off[c], nl = J.node_off[c + 1] - n0;
+    const int i0 = J.int_off[c], ni = J.int_off[c + 1] - i0, nred = J.red_cnt[c];
+    const int g0 = J.gh_off[c], ngh = J.gh_off[c + 1] - g0;
+    T *val = reinterpret_cast<T *>(smem_dyn);
+    T *gw = val + J.max_nodes;       // K per ghost
+    T *gv = gw + (size_t)K * J.max_gh;
+    T *gcv = gv + J.max_gh;
+    T *gt = gcv + J.max_gh;
+    int *gst = reinterpret_cast<int *>(gt + J.max_gh);   // K per ghost
+    int *gme = gst + (size_t)K * J.max_gh;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) val[i] = J.u[J.lnode[n0 + i]];
+    for (int e = threadIdx.x; e < ngh; e += blockDim.x) {
+        const int q = J.gh_q[g0 + e];
+        gv[e] = J.gg[q];
+        gcv[e] = J.gc[q];
+        gme[e] = J.gh_me[g0 + e];
+        for (int k = 0; k < K; k++) {
+            gw[e * K + k] = J.gw[(int64_t)k * J.ng + q];
+            gst[e * K + k] = J.gh_stn[(size_t)(g0 + e) * K + k];
+        }
+    }
+    int rme[LOCAL_EPT], rnb[LOCAL_EPT][2 * D], bme[LOCAL_EPT], bnb[LOCAL_EPT][2 * D];
+    T rf[LOCAL_EPT], bf[LOCAL_EPT];
+#pragma unroll
+    for (int e = 0; e < LOCAL_EPT; e++) {
+        const int ir = threadIdx.x + e * blockDim.x, ib = nred + threadIdx.x + e * blockDim.x;
+        rme[e] = -1;
+        bme[e] = -1;
+        if (ir < nred) {
+            rme[e] = J.int_me[i0 + ir];
+            rf[e] = J.h2 * J.f[J.int_glob[i0 + ir]];
+#pragma unroll
+            for (int a = 0; a < 2 * D; a++) rnb[e][a] = J.int_nb[(size_t)(i0 + ir) * (2 * D) + a];
+        }
+        if (ib < ni) {
+            bme[e] = J.int_me[i0 + ib];
+            bf[e] = J.h2 * J.f[J.int_glob[i0 + ib]];
+#pragma unroll
+            for (int a = 0; a < 2 * D; a++) bnb[e][a] = J.int_nb[(size_t)(i0 + ib) * (2 * D) + a];
+        }
+    }
+    __syncthreads();
+    const T inv = (T)(1.0 / (2 * D));
+    auto ghost_sweep = [&]() {
+        for (int e = threadIdx.x; e < ngh; e += blockDim.x) {
+            T s = 0;
+#pragma unroll
+            for (int k = 0; k < K; k++) s += gw[e * K + k] * val[gst[e * K + k]];
+            gt[e] = val[gme[e]] + gcv[e] * (gv[e] - s);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < ngh; e += blockDim.x) val[gme[e]] = gt[e];
+        __syncthreads();
+    };
+    if (lead_ghost) ghost_sweep();
+    for (int it = 0; it < reps; it++) {
+#pragma unroll
+        for (int e = 0; e < LOCAL_EPT; e++)
+            if (rme[e] >= 0) {
+                T s = rf[e];
+#pragma unroll
+                for (int a = 0; a < 2 * D; a++) s += val[rnb[e][a]];
+                val[rme[e]] = s * inv;
+            }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < LOCAL_EPT; e++)
+            if (bme[e] >= 0) {
+                T s = bf[e];
+#pragma unroll
+                for (int a = 0; a < 2 * D; a++) s += val[bnb[e][a]];
+                val[bme[e]] = s * inv;
+            }
+        __syncthreads();
+        ghost_sweep();
+    }
+    const int nw = J.wb_cnt[c];
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) J.u[J.lnode[n0 + i]] = val[i];
+}
+
+// ------------------------------------------------------------------ defect
+// r = f + Lap_h u at inside node p (TGCS step 3), as a sum of differences so
+// that the O(u / h^2) terms do not cancel; with zero_rest, 0 at outside nodes.
+// Returns the defect (0 off Omega_h) for the norm.
+template <typename T, int D>
+__device__ __forceinline__ double defect_node(const LevelView<T> &v, int64_t p, bool zero_rest) {
+    const uint8_t k = v.type[p] & NODE_KIND;
+    if (k == NODE_IN) {
+        const T up = v.u[p];
+        T lap = (v.u[p - 1] - up) + (v.u[p + 1] - up) + (v.u[p - v.s0] - up) + (v.u[p + v.s0] - up);
+        if (D == 3) lap += (v.u[p - v.s1] - up) + (v.u[p + v.s1] - up);
+        const T r = v.f[p] + lap * v.inv_h2;
+        v.r[p] = r;
+        return (double)r;
+    }
+    if (zero_rest && k == NODE_OUT) v.r[p] = 0;
+    return 0.0;
+}
+
+// r = g - L_G u at ghost q
+template <typename T, int K>
+__device__ __forceinline__ double defect_ghost_item(const LevelView<T> &v, int q) {
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) s += v.gw[(int64_t)k * v.ng + q] * v.u[v.gstn[(int64_t)k * v.ng + q]];
+    const T r = v.gg[q] - s;
+    v.r[v.gnode[q]] = r;
+    return (double)r;
+}
+
+// ------------------------------------------------------------- restriction
+// Partial transfer (Sec. 2.5) at a coarse node whose fine image is p: boxes
+// prod_a [al_a, be_a] inside the member set, largest ones averaged, weights
+// the tensor products of (1,2,1)/4, (2,2,0)/4, (0,2,2)/4, (0,4,0)/4.
+template <int D>
+__device__ __forceinline__ unsigned box_mask(int b) {
+    // bit c of the 3^D neighbourhood (axis 0 slowest, offsets -1,0,1) inside box b;
+    // interval code per axis: 0 [-1,1], 1 [-1,0], 2 [0,1], 3 [0,0]
+    unsigned m = 0;
+    const int cube = D == 2 ? 9 : 27;
+    for (int c = 0; c < cube; c++) {
+        int rem = c, ok = 1;
+        for (int a = D - 1; a >= 0; a--) {
+            const int o = rem % 3 - 1;
+            rem /= 3;
+            const int iv = (b >> (2 * a)) & 3;
+            const int lo = (iv == 2 || iv == 3) ? 0 : -1;
+            const int hi = (iv == 1 || iv == 3) ? 0 : 1;
+            if (o < lo || o > hi) ok = 0;
+        }
+        if (ok) m |= 1u << c;
+    }
+    return m;
+}
+
+__device__ __forceinline__ double w1d(int iv, int o) {
+    switch (iv) {
+        case 0: return o == 0 ? 0.5 : 0.25;
+        case 1: return o == 1 ? 0.0 : 0.5;
+        case 2: return o == -1 ? 0.0 : 0.5;
+        default: return o == 0 ? 1.0 : 0.0;
+    }
+}
+
+template <typename T, int D>
+__device__ T partial_transfer(const LevelView<T> &F, int64_t p, bool interior) {
+    const int cube = D == 2 ? 9 : 27;
+    const unsigned full = (1u << cube) - 1u;
+    unsigned member = 0;
+    for (int c = 0; c < cube; c++) {
+        int rem = c;
+        int64_t q = p;
+        for (int a = D - 1; a >= 0; a--) {
+            const int o = rem % 3 - 1;
+            rem /= 3;
+            q += o * (a == D - 1 ? (int64_t)1 : (a == 0 ? F.s0 : F.s1));
+        }
+        const uint8_t k = F.type[q] & NODE_KIND;
+        if (interior ? (k == NODE_IN) : (k != NODE_IN)) member |= 1u << c;
+    }
+    const int nbox = D == 2 ? 16 : 64;
+    int best = 0, count = 0;
+    if (member == full) {
+        best = 1;  // full weighting fast path
+    } else {
+        for (int b = 0; b < nbox; b++) {
+            const unsigned m = box_mask<D>(b);
+            if (m & ~member) continue;
+            const int sz = __popc(m);
+            if (sz > best) { best = sz; count = 1; }
+            else if (sz == best) count++;
+        }
+        if (count == 0) return (T)0;
+    }
+    double acc = 0.0;
+    for (int c = 0; c < cube; c++) {
+        if (!((member >> c) & 1u)) continue;
+        int rem = c;
+        int64_t q = p;
+        int o[3] = {0, 0, 0};
+        for (int a = D - 1; a >= 0; a--) {
+            o[a] = rem % 3 - 1;
+            rem /= 3;
+            q += o[a] * (a == D - 1 ? (int64_t)1 : (a == 0 ? F.s0 : F.s1));
+        }
+        double w = 0.0;
+        if (member == full) {
+            w = 1.0;
+            for (int a = 0; a < D; a++) w *= w1d(0, o[a]);
+        } else {
+            for (int b = 0; b < nbox; b++) {
+                const unsigned m = box_mask<D>(b);
+                if ((m & ~member) || __popc(m) != best) continue;
+                double wb = 1.0;
+                for (int a = 0; a < D; a++) wb *= w1d((b >> (2 * a)) & 3, o[a]);
+                w += wb;
+            }
+            w /= count;
+        }
+        if (w != 0.0) acc += w * (double)F.r[q];
+    }
+    return (T)acc;
+}
+
+template <int D>
+__device__ __forceinline__ int64_t fine_image(int64_t X, int64_t cs0, int64_t cs1, int64_t fs0, int64_t fs1) {
+    int64_t rem = X;
+    if (D == 2) {
+        const int64_t j0 = rem / cs0, j1 = rem - j0 * cs0;
+        return 2 * j0 * fs0 + 2 * j1;
+    }
+    const int64_t j0 = rem / cs0;
+    rem -= j0 * cs0;
+    const int64_t j1 = rem / cs1, j2 = rem - j1 * cs1;
+    return 2 * j0 * fs0 + 2 * j1 * fs1 + 2 * j2;
+}
+
+// coarse node X: transfer over Omega_h at coarse inside nodes, 0 elsewhere
+template <typename T, int D>
+__device__ __forceinline__ void restrict_node(const LevelView<T> &F, const LevelView<T> &C, int64_t X, T *fc) {
+    if ((C.type[X] & NODE_KIND) != NODE_IN) { fc[X] = 0; return; }
+    fc[X] = partial_transfer<T, D>(F, fine_image<D>(X, C.s0, C.s1, F.s0, F.s1), true);
+}
+
+// coarse ghost q: transfer over D_h - Omega_h (used by the single-step API)
+template <typename T, int D>
+__device__ __forceinline__ void restrict_ghost_item(const LevelView<T> &F, const LevelView<T> &C, int q, T *gc) {
+    gc[q] = partial_transfer<T, D>(F, fine_image<D>(C.gnode[q], C.s0, C.s1, F.s0, F.s1), false);
+}
+
+// extension + partial transfer at coarse ghost q as one sparse row over the
+// fine ghost defects (read from the fine defect grid)
+template <typename T>
+__device__ __forceinline__ void ghost_transfer_row(const T *__restrict__ rf, const int32_t *__restrict__ fgnode,
+                                                   const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                                   const T *__restrict__ val, T *__restrict__ gc, int q) {
+    T s = 0;
+    for (int j = ptr[q]; j < ptr[q + 1]; j++) s += val[j] * rf[fgnode[col[j]]];
+    gc[q] = s;
+}
+
+// ------------------------------------------------------------ interpolation
+// Bilinear / trilinear interpolation onto Omega_h u Gamma_h at fine node p
+// (Sec. 2.6), weights renormalised over the parents in Omega_2h u Gamma_2h.
+template <typename T, int D>
+__device__ __forceinline__ void prolong_node(const LevelView<T> &F, const LevelView<T> &C, const T *__restrict__ e,
+                                             T *__restrict__ out, bool add, int64_t p) {
+    const uint8_t k = F.type[p] & NODE_KIND;
+    if (k != NODE_IN && k != NODE_GHOST) {
+        if (!add) out[p] = 0;
+        return;
+    }
+    int j[3] = {0, 0, 0};
+    int64_t rem = p;
+    j[0] = (int)(rem / F.s0);
+    rem -= (int64_t)j[0] * F.s0;
+    if (D == 2) {
+        j[1] = (int)rem;
+    } else {
+        j[1] = (int)(rem / F.s1);
+        j[2] = (int)(rem - (int64_t)j[1] * F.s1);
+    }
+    T num = 0, den = 0;
+    const int n1 = (j[0] & 1) ? 2 : 1, n2 = (j[1] & 1) ? 2 : 1, n3 = (D == 3 && (j[2] & 1)) ? 2 : 1;
+    for (int a = 0; a < n1; a++)
+        for (int b = 0; b < n2; b++)
+            for (int c = 0; c < n3; c++) {
+                const int64_t X = (int64_t)(j[0] / 2 + a) * C.s0 +
+                                  (D == 2 ? (int64_t)(j[1] / 2 + b) : (int64_t)(j[1] / 2 + b) * C.s1 + (j[2] / 2 + c));
+                const uint8_t kc = C.type[X] & NODE_KIND;
+                if (kc != NODE_IN && kc != NODE_GHOST) continue;
+                const T w = (T)(1.0 / (n1 * n2 * n3));
+                num += w * e[X];
+                den += w;
+            }
+    const T val = den > (T)0 ? num / den : (T)0;
+    if (add) out[p] += val;
+    else out[p] = val;
+}
+
+// --------------------------------------------------------------- coarsest
+// e = A^-1 b on the coarsest level, rows blk, blk + nblk, ... of one CTA: b
+// gathered into shared memory from f (inside) and the ghost data, each warp
+// computing row dot products of the dense inverse.
+template <typename T>
+__device__ __forceinline__ void coarse_rows(const LevelView<T> &v, const int32_t *__restrict__ unk_node,
+                                            const int32_t *__restrict__ unk_ghost, const T *__restrict__ Ainv,
+                                            int m, int blk, int nblk) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    T *b = reinterpret_cast<T *>(smem_dyn);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int g = unk_ghost[i];
+        b[i] = g < 0 ? v.f[unk_node[i]] : v.gg[g];
+    }
+    __syncthreads();
+    const int warps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int row = blk * warps + (threadIdx.x >> 5); row < m; row += nblk * warps) {
+        const T *a = Ainv + (int64_t)row * m;
+        T s = 0;
+        for (int k = lane; k < m; k += 32) s += a[k] * b[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) v.u[unk_node[row]] = s;
+    }
+}
+
+}  // namespace dev
+}  // namespace gcmg

@@ -795,23 +795,29 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
         build_extension(levels[l], levels[l + 1]);
         build_ghost_transfer(levels[l], levels[l + 1]);
     }
-    build_coarse_inverse(levels.back());
+    number_coarse_unknowns(levels.back());   // the inverse is built before the first solve
 }
 
-// Dense inverse of the coarsest system (Eq. discr with the level's bc):
-// Gauss-Jordan elimination with partial pivoting on [A | I].
-void build_coarse_inverse(HostLevel &L) {
-    std::vector<int64_t> id(L.nn, -1);
+// Unknowns of the coarsest level (inside nodes and ghosts in node order) with
+// their ghost numbers; independent of the boundary types.
+void number_coarse_unknowns(HostLevel &L) {
     L.unk_node.clear();
     L.unk_ghost.clear();
     std::vector<int32_t> ghost_of(L.nn, -1);
     for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;
     for (int64_t p = 0; p < L.nn; p++)
         if (unknown(L, p)) {
-            id[p] = (int64_t)L.unk_node.size();
             L.unk_node.push_back((int32_t)p);
             L.unk_ghost.push_back(ghost_of[p]);
         }
+    L.ainv_dirty = true;
+}
+
+// Dense inverse of the coarsest system (Eq. discr with the level's bc):
+// Gauss-Jordan elimination with partial pivoting on [A | I].
+void build_coarse_inverse(HostLevel &L) {
+    std::vector<int64_t> id(L.nn, -1);
+    for (size_t i = 0; i < L.unk_node.size(); i++) id[L.unk_node[i]] = (int64_t)i;
     const int64_t m = (int64_t)L.unk_node.size();
     std::vector<double> A(m * m, 0.0), X(m * m, 0.0);
     const double ih2 = 1.0 / (L.h * L.h);
@@ -852,6 +858,7 @@ void build_coarse_inverse(HostLevel &L) {
         }
     }
     L.Ainv.swap(X);
+    L.ainv_dirty = false;
 }
 
 }  // namespace gcmg

@@ -81,6 +81,15 @@ def lib():
             "gcmg_launch_counter": (i64, []),
             "gcmg_junction_zone": (st, [vp, i32, vp]),
             "gcmg_defect_noalloc": (st, [i32, i32, dbl, vp, vp, vp, i64, vp, vp, vp, vp, vp, C.POINTER(dbl), vp]),
+            "gcmg_batch_create": (st, [i32, C.POINTER(Params), C.POINTER(vp), vp, C.POINTER(vp)]),
+            "gcmg_batch_destroy": (None, [vp]),
+            "gcmg_batch_last_error": (C.c_char_p, [vp]),
+            "gcmg_batch_size": (i32, [vp]),
+            "gcmg_batch_domain": (vp, [vp, i32]),
+            "gcmg_batch_solve": (st, [vp, C.POINTER(Stats), C.POINTER(i32)]),
+            "gcmg_batch_get_solution": (st, [vp, i32, vp]),
+            "gcmg_batch_set_tiles": (st, [vp, i32]),
+            "gcmg_batch_autotune": (st, [vp, C.POINTER(i32), C.POINTER(dbl)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -112,6 +121,16 @@ def _ptr(t):
 class Solver:
     """One multigrid hierarchy (a gcmg context) on the current CUDA device."""
 
+    @classmethod
+    def _borrow(cls, handle, dim, n, params):
+        """Wraps a context owned by someone else (a batch domain)."""
+        self = cls.__new__(cls)
+        self._h = C.c_void_p(handle)
+        self.dim, self.n, self.params, self.stream = dim, n, params, None
+        self.nlev = lib().gcmg_num_levels(self._h)
+        self._borrowed = True
+        return self
+
     def __init__(self, phi, n_coarse, stream=None, **params):
         import torch
         phi_t = phi if isinstance(phi, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(phi))
@@ -133,9 +152,9 @@ class Solver:
         self.nlev = lib().gcmg_num_levels(self._h)
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and not getattr(self, "_borrowed", False):
             lib().gcmg_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -245,3 +264,65 @@ class Solver:
 
 def launch_counter():
     return lib().gcmg_launch_counter()
+
+
+class Batch:
+    """Many 2D domains solved together (gcmg_batch): one launch per cycle step
+    over all domains, one graph launch per solve."""
+
+    def __init__(self, phis, n_coarse, stream=None, **params):
+        import torch
+        self.count = len(phis)
+        ts = [torch.from_numpy(np.ascontiguousarray(p)).to("cuda", torch.float64) for p in phis]
+        ncs = n_coarse if isinstance(n_coarse, (list, tuple)) else [n_coarse] * self.count
+        P = (Params * self.count)()
+        for i, t in enumerate(ts):
+            P[i] = default_params(2, t.shape[0], ncs[i], precision=1, **params)
+        ptrs = (C.c_void_p * self.count)(*[t.data_ptr() for t in ts])
+        h = C.c_void_p()
+        s = lib().gcmg_batch_create(self.count, P, ptrs, C.c_void_p(stream.cuda_stream) if stream else None,
+                                    C.byref(h))
+        self._h = h
+        if s != GCMG_OK:
+            msg = lib().gcmg_batch_last_error(h).decode() if h.value else ""
+            if h.value:
+                lib().gcmg_batch_destroy(h)
+            self._h = None
+            raise GcmgError(s, msg)
+        self.domains = [Solver._borrow(lib().gcmg_batch_domain(self._h, i), 2, ts[i].shape[0], P[i])
+                        for i in range(self.count)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gcmg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s != GCMG_OK:
+            raise GcmgError(s, lib().gcmg_batch_last_error(self._h).decode())
+
+    def solve(self):
+        st = (Stats * self.count)()
+        steps = C.c_int()
+        s = lib().gcmg_batch_solve(self._h, st, C.byref(steps))
+        if s not in (GCMG_OK, GCMG_E_NOCONV):
+            self._check(s)
+        return [x.to_dict() for x in st], steps.value
+
+    def solution(self, i, out):
+        self._check(lib().gcmg_batch_get_solution(self._h, i, _ptr(out)))
+
+    def set_tiles(self, variant):
+        self._check(lib().gcmg_batch_set_tiles(self._h, int(variant)))
+
+    def autotune(self):
+        best = C.c_int()
+        ms = (C.c_double * 3)()
+        self._check(lib().gcmg_batch_autotune(self._h, C.byref(best), ms))
+        return best.value, list(ms)
