@@ -38,7 +38,8 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("lam", C.c_int), ("gamma", C.c_int),
                 ("mode", C.c_int), ("extra_once", C.c_int), ("delta_over_h", C.c_double),
-                ("c_dirichlet", C.c_double), ("c_neumann_factor", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double)]
+                ("c_dirichlet", C.c_double), ("c_neumann_factor", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double),
+                ("junction_solve", C.c_int)]
 
 
 _lib = None
@@ -65,6 +66,7 @@ def lib():
         L.orc_get_types.argtypes = [vp, C.c_int, vp]
         L.orc_get_band.argtypes = [vp, C.c_int, vp]
         L.orc_get_jzone.argtypes = [vp, C.c_int, vp]
+        L.orc_get_jsolve.argtypes = [vp, C.c_int, vp]
         L.orc_get_ghosts.argtypes = [vp, C.c_int] + [vp] * 10
         L.orc_get_ext.argtypes = [vp, C.c_int, vp, vp, vp, vp]
         L.orc_defect.restype = dbl
@@ -95,18 +97,23 @@ class Oracle:
     """One multigrid hierarchy built from a fine level set ``phi`` (shape n^dim)."""
 
     def __init__(self, phi, n_coarse, nu1=2, nu2=1, lam=5, gamma=1, mode=0, extra_once=0,
-                 delta_over_h=3.0, c_dirichlet=0.9, c_neumann_factor=0.9, junction_sweeps=None, junction_radius=None):
+                 delta_over_h=3.0, c_dirichlet=0.9, c_neumann_factor=0.9, junction_sweeps=None, junction_radius=None,
+                 junction_solve=None):
         phi = np.ascontiguousarray(phi, dtype=np.float64)
         self.dim = phi.ndim
-        # junction relaxation defaults: 40 sweeps within 12h (2D), 10 within 2h (3D)
+        # junction relaxation defaults: 2D an exact solve of the zone within
+        # 12h; 3D (the zone is a tube around junction curves) 10 sweeps
+        # within 2h.  junction_sweeps=0 alone turns it off.
+        if junction_solve is None:
+            junction_solve = 1 if (self.dim == 2 and junction_sweeps is None) else 0
         if junction_sweeps is None:
-            junction_sweeps = 40 if self.dim == 2 else 10
+            junction_sweeps = 0 if self.dim == 2 else 10
         if junction_radius is None:
             junction_radius = 12.0 if self.dim == 2 else 2.0
         self.n = phi.shape[0]
         assert all(s == self.n for s in phi.shape)
         self.params = Params(nu1, nu2, lam, gamma, mode, extra_once, delta_over_h, c_dirichlet,
-                             c_neumann_factor, junction_sweeps, junction_radius)
+                             c_neumann_factor, junction_sweeps, junction_radius, junction_solve)
         L = lib()
         self._h = L.orc_create(self.dim, self.n, n_coarse, _p(phi), C.byref(self.params))
         if not self._h:
@@ -152,6 +159,12 @@ class Oracle:
         lib().orc_get_jzone(self._h, l, _p(out))
         return out
 
+    def junction_solve_set(self, l):
+        """Mask of the unknowns whose equations the exact junction solve solves."""
+        out = np.empty(self.shape(l), np.uint8)
+        lib().orc_get_jsolve(self._h, l, _p(out))
+        return out
+
     def ghosts(self, l):
         ng, d = self.num_ghosts(l), self.dim
         rec = dict(node=np.empty(ng, np.int64), B=np.empty((ng, d)), nu=np.empty((ng, d)),
@@ -178,6 +191,9 @@ class Oracle:
         bc = np.ascontiguousarray(bc, dtype=np.uint8)
         assert bc.shape == (self.num_ghosts(l),)
         lib().orc_set_bc(self._h, l, _p(bc))
+        st = lib().orc_status(self._h)
+        if st != 0:
+            raise OracleError(f"oracle status {st}: {lib().orc_error(self._h).decode()}")
 
     def set_rhs(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64)

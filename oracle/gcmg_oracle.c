@@ -46,6 +46,7 @@ typedef struct {
     double c_neumann_factor; /* mu_N dt = factor * 2h / (3 sqrt(d)) (Sec. 2.3 uses 0.9) */
     int junction_sweeps;   /* mu_J: local sweeps near Dirichlet/Neumann junctions (0: none) */
     double junction_radius;/* R_J: junction zone radius, in units of h of each level */
+    int junction_solve;    /* 1: solve the zone's equations exactly instead of mu_J sweeps */
 } orc_params;
 
 typedef struct {
@@ -57,6 +58,10 @@ typedef struct {
     uint8_t *type;
     uint8_t *band;
     uint8_t *jzone;        /* unknowns of the junction zone (NULL: none) */
+    int64_t jn;            /* exact zone solve: number of zone unknowns, */
+    int64_t *jnode;        /* their nodes (increasing index) */
+    double *jLU;           /* and the LU factors of their equations (jn x jn) */
+    int64_t *jpiv;
     /* ghost records, in increasing node index */
     int64_t ng;
     int64_t *gnode;
@@ -625,14 +630,15 @@ static void base_relax(Oracle *O, Level *L) {
     else { rb_sweep(L, 0); ghost_jacobi(L); }
 }
 
-/* Junction relaxation (an addition to the paper's smoother; mu_J = 0 gives
- * the paper's method).  Where Dirichlet and Neumann ghosts meet, the error of
- * the mixed problem is singular and the boundary extra sweeps of Sec. 3.2 do
- * not reach it, so the cycle's factor grows as h shrinks.  Following the same
- * rationale (relax more where the error decays slowly), mu_J extra sweeps --
- * red, black, then Jacobi on the ghosts -- run on the unknowns within R_J h of
- * a ghost whose 3^d neighbourhood holds a ghost of the other type, after every
- * relaxation on every level. */
+/* Junction relaxation (an addition to the paper's smoother; none gives the
+ * paper's method).  Where Dirichlet and Neumann ghosts meet, the error of the
+ * mixed problem is singular and the boundary extra sweeps of Sec. 3.2 do not
+ * reach it, so the cycle's factor grows as h shrinks.  Following the same
+ * rationale (relax more where the error decays slowly), the unknowns within
+ * R_J h of a ghost whose 3^d neighbourhood holds a ghost of the other type
+ * are relaxed again after every relaxation on every level, either by mu_J
+ * sweeps (red, black, then Jacobi on the ghosts; zone_sweep) or by solving
+ * their equations exactly (zone_solve, below). */
 static void zone_sweep(Level *L) {
     for (int color = 0; color < 2; color++)
         for (int64_t i = 0; i < L->nn; i++)
@@ -674,6 +680,101 @@ static void build_jzone(Level *L, double radius) {
     }
 }
 
+/* Exact junction-zone solve (the alternative to the mu_J sweeps): the
+ * equations of the zone's unknowns, with every value outside the zone held
+ * fixed, are solved exactly, i.e. u_Z += A_ZZ^{-1} r_Z with r the defect.
+ * A block (Schwarz) step of the same system; unlike the sweeps it cannot
+ * grow a local mode, e.g. next to a Dirichlet ghost whose own weight in its
+ * condition is almost zero. */
+static int lu_factor(double *A, int64_t n, int64_t *piv);
+static void lu_solve(const double *A, int64_t n, const int64_t *piv, double *b);
+
+static double row_defect(const Level *L, int64_t i, const double *u) {
+    if (L->type[i] == T_INT) {
+        double lap = -2.0 * L->dim * u[i];
+        for (int a = 0; a < L->dim; a++) lap += u[i + L->st[a]] + u[i - L->st[a]];
+        return L->f[i] + lap / (L->h * L->h);
+    }
+    int64_t q = L->gid[i];
+    return L->g[q] - ghost_operator(L, q, u);
+}
+
+static int build_jsolve(Level *L) {
+    free(L->jnode); free(L->jLU); free(L->jpiv);
+    L->jnode = NULL; L->jLU = NULL; L->jpiv = NULL; L->jn = 0;
+    /* the solved set: the zone grown by the stencils of its ghosts, then
+     * stripped (repeatedly) of every ghost whose stencil leaves it, so that
+     * each ghost row is complete: a row cut off from the node that carries
+     * most of its weight would leave A_ZZ nearly singular */
+    uint8_t *in = (uint8_t *)malloc((size_t)L->nn);
+    memcpy(in, L->jzone, (size_t)L->nn);
+    for (int64_t q = 0; q < L->ng; q++)
+            if (L->jzone[L->gnode[q]])
+                for (int m = 0; m < L->nk[q]; m++) in[L->stn[q * MAXK + m]] = 1;
+    for (int changed = 1; changed;) {
+        changed = 0;
+        for (int64_t q = 0; q < L->ng; q++) {
+            int64_t G = L->gnode[q];
+            if (!in[G]) continue;
+            for (int m = 0; m < L->nk[q]; m++)
+                if (!in[L->stn[q * MAXK + m]]) { in[G] = 0; changed = 1; break; }
+        }
+    }
+    int64_t n = 0;
+    for (int64_t i = 0; i < L->nn; i++) n += in[i] ? 1 : 0;
+    if (n == 0) { free(in); return 0; }
+    int64_t *loc = (int64_t *)malloc(sizeof(int64_t) * (size_t)L->nn);
+    L->jnode = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    L->jLU = (double *)calloc((size_t)(n * n), sizeof(double));
+    L->jpiv = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t k = 0;
+    for (int64_t i = 0; i < L->nn; i++) {
+        loc[i] = in[i] ? k : -1;
+        if (in[i]) L->jnode[k++] = i;
+    }
+    free(in);
+    L->jn = n;
+    double ih2 = 1.0 / (L->h * L->h);
+    for (int64_t r = 0; r < n; r++) {
+        int64_t i = L->jnode[r];
+        double *row = L->jLU + r * n;
+        if (L->type[i] == T_INT) {   /* -Delta_h */
+            row[r] += 2.0 * L->dim * ih2;
+            for (int a = 0; a < L->dim; a++)
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    int64_t P = i + sg * L->st[a];
+                    if (loc[P] >= 0) row[loc[P]] -= ih2;
+                }
+        } else {                     /* L_h of the ghost's condition */
+            int64_t q = L->gid[i];
+            const double *w = (L->bc[q] == BC_D) ? L->wD : L->wN;
+            for (int m = 0; m < L->nk[q]; m++) {
+                int64_t P = L->stn[q * MAXK + m];
+                if (loc[P] >= 0) row[loc[P]] += w[q * MAXK + m];
+            }
+        }
+    }
+    free(loc);
+    return lu_factor(L->jLU, n, L->jpiv);
+}
+
+static void zone_solve(Level *L) {
+    double *b = (double *)malloc(sizeof(double) * (size_t)L->jn);
+    for (int64_t k = 0; k < L->jn; k++) b[k] = row_defect(L, L->jnode[k], L->u);
+    lu_solve(L->jLU, L->jn, L->jpiv, b);
+    for (int64_t k = 0; k < L->jn; k++) L->u[L->jnode[k]] += b[k];
+    free(b);
+}
+
+static void junction_relax(Oracle *O, Level *L) {
+    if (!L->jzone) return;
+    if (O->p.junction_solve) {
+        if (L->jn) zone_solve(L);
+    } else {
+        for (int m = 0; m < O->p.junction_sweeps; m++) zone_sweep(L);
+    }
+}
+
 /* lambda extra sweeps on Gamma_h and the band (Sec. 3.2) */
 static void extra_sweeps(Oracle *O, Level *L) {
     for (int k = 0; k < O->p.lambda; k++) {
@@ -686,8 +787,7 @@ static void smooth(Oracle *O, Level *L, int nu) {
     for (int k = 0; k < nu; k++) {
         base_relax(O, L);
         if (!O->p.extra_once) extra_sweeps(O, L);
-        if (O->p.junction_sweeps && L->jzone)
-            for (int m = 0; m < O->p.junction_sweeps; m++) zone_sweep(L);
+        if (O->p.junction_sweeps || O->p.junction_solve) junction_relax(O, L);
     }
     if (O->p.extra_once && nu > 0) extra_sweeps(O, L);
 }
@@ -978,7 +1078,7 @@ static void cycle(Oracle *O, int l) {
 /* ------------------------------------------------------------ public API */
 
 static void free_level(Level *L) {
-    free(L->phi); free(L->type); free(L->band); free(L->jzone); free(L->gnode); free(L->gid);
+    free(L->phi); free(L->type); free(L->band); free(L->jzone); free(L->jnode); free(L->jLU); free(L->jpiv); free(L->gnode); free(L->gid);
     free(L->B); free(L->nu); free(L->tloc); free(L->sdir); free(L->gcase); free(L->nk);
     free(L->stn); free(L->wD); free(L->wN); free(L->bc); free(L->c);
     free(L->u); free(L->f); free(L->r); free(L->g); free(L->gtmp);
@@ -1098,6 +1198,10 @@ void orc_set_bc(void *h, int l, const uint8_t *bc) {
                                      : O->p.c_neumann_factor * 2.0 * L->h / (3.0 * sqrt((double)L->dim));
     }
     build_jzone(L, O->p.junction_radius);
+    if (O->p.junction_solve && build_jsolve(L) != 0) {
+        O->status = ORC_E_SINGULAR;
+        strcpy(O->err, "singular junction-zone system");
+    }
     if (l == O->nlev - 1) {
         free(L->unk); free(L->LU); free(L->piv);
         L->unk = NULL; L->LU = NULL; L->piv = NULL;
@@ -1122,6 +1226,13 @@ void orc_get_jzone(void *h, int l, uint8_t *out) {
     Level *L = &((Oracle *)h)->L[l];
     if (L->jzone) memcpy(out, L->jzone, (size_t)L->nn);
     else memset(out, 0, (size_t)L->nn);
+}
+
+/* nodes whose equations the exact junction solve of level l solves (mask) */
+void orc_get_jsolve(void *h, int l, uint8_t *out) {
+    Level *L = &((Oracle *)h)->L[l];
+    memset(out, 0, (size_t)L->nn);
+    for (int64_t k = 0; k < L->jn; k++) out[L->jnode[k]] = 1;
 }
 
 void orc_get_band(void *h, int l, uint8_t *out) {
@@ -1200,8 +1311,7 @@ void orc_relax(void *h, int l, double *u, const double *f, const double *g, int 
     base_relax(O, L);
     if (with_extra) {
         extra_sweeps(O, L);
-        if (O->p.junction_sweeps && L->jzone)
-            for (int m = 0; m < O->p.junction_sweeps; m++) zone_sweep(L);
+        if (O->p.junction_sweeps || O->p.junction_solve) junction_relax(O, L);
     }
     memcpy(u, L->u, sizeof(double) * (size_t)L->nn);
 }

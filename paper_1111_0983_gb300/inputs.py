@@ -161,17 +161,37 @@ def circle_paper(radius: float = 0.563) -> Problem:
         n_coarse=9)
 
 
+def star_min_concave_radius(R0: float, a: float, k: int) -> float:
+    """Smallest radius of curvature on the concave parts of the boundary
+    r(theta) = R0 (1 + a sin(k theta + p)) (inf if it is convex); the
+    curvature depends on k theta + p only, sampled finely over one period."""
+    ph = np.linspace(0.0, 2 * math.pi, 8192, endpoint=False)
+    r = R0 * (1 + a * np.sin(ph))
+    r1 = R0 * a * k * np.cos(ph)
+    r2 = -R0 * a * k * k * np.sin(ph)
+    kap = (r * r + 2 * r1 * r1 - r * r2) / (r * r + r1 * r1) ** 1.5
+    return float(1.0 / -kap.min()) if kap.min() < 0 else math.inf
+
+
+STAR_MIN_RADIUS = 0.02
+
+
 def star_params(i: int, base: int = 1111 << 20):
     """Seeded star i: R0 ~ U[0.4,0.7], a ~ U[0,0.3], k ~ U{3..8}, p ~ U[0,2pi),
-    split angle al ~ U[0,2pi), n ~ U{129,257,513,1025}."""
+    split angle al ~ U[0,2pi), n ~ U{129,257,513,1025}.  A draw whose concave
+    radius of curvature falls below STAR_MIN_RADIUS (about 1.3 h of the 129^2
+    grid, 0.3 h of the 65^2 one) is rejected and drawn again from the same
+    stream: the coarse levels of the hierarchy must resolve the boundary."""
     rng = SplitMix(splitmix64(base + i))
-    R0 = rng.uniform(0.4, 0.7)
-    a = rng.uniform(0.0, 0.3)
-    k = rng.randint(3, 8)
-    p = rng.uniform(0.0, 2 * math.pi)
-    al = rng.uniform(0.0, 2 * math.pi)
-    n = (129, 257, 513, 1025)[rng.randint(0, 3)]
-    return dict(R0=R0, a=a, k=k, p=p, al=al, n=n)
+    while True:
+        R0 = rng.uniform(0.4, 0.7)
+        a = rng.uniform(0.0, 0.3)
+        k = rng.randint(3, 8)
+        p = rng.uniform(0.0, 2 * math.pi)
+        al = rng.uniform(0.0, 2 * math.pi)
+        n = (129, 257, 513, 1025)[rng.randint(0, 3)]
+        if star_min_concave_radius(R0, a, k) >= STAR_MIN_RADIUS:
+            return dict(R0=R0, a=a, k=k, p=p, al=al, n=n)
 
 
 def star(i: int = 0, base: int = 1111 << 20, params: dict | None = None) -> Problem:

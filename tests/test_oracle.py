@@ -220,6 +220,55 @@ def test_junction_relaxation_restores_mixed_bc_vcycle():
     assert plain[1] > 0.5 and fixed[1] < 0.2 and fixed[0] < 0.15, (plain, fixed)
 
 
+def test_junction_solve_is_exact_on_its_set():
+    """The exact junction solve leaves a zero defect on every equation it
+    solves (with all other values held fixed); its set holds each junction
+    ghost and, for each ghost in it, the ghost's whole stencil."""
+    F = inputs.flower()
+    n = 129
+    O = oracle_for(F, n, 33)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(O.shape(0))
+    G = O.ghosts(0)
+    f = F.f_grid(n)
+    g = F.g_values(G["B"], G["nu"], F.bc_types(G["B"]))
+    O.set_rhs(f, g)
+    r_before = np.abs(O.defect(u, 0)[0]).max()
+    u1 = O.relax(u, f, g, 0)
+    r = np.abs(O.defect(u1, 0)[0]).ravel()
+    S = O.junction_solve_set(0).ravel().astype(bool)
+    assert S.sum() > 100
+    assert r[S].max() < 1e-9 * r_before
+    assert r[~S].max() > 1e-3 * r_before          # elsewhere only relaxed
+    T = O.types(0).ravel() & 3
+    assert np.all(T[S] > 0)                      # unknowns only
+    bc = F.bc_types(G["B"])
+    pos = {int(x): q for q, x in enumerate(G["node"])}
+    for q, node in enumerate(G["node"]):
+        if S[node]:
+            assert all(S[int(m)] for m in G["stn"][q][:G["nk"][q]]), q
+    Z = O.junction_zone(0).ravel().astype(bool)
+    nl = O.level_n(0)
+    for q, node in enumerate(G["node"]):
+        i, j = divmod(int(node), nl)
+        nb = [pos.get((i + a) * nl + j + b) for a in (-1, 0, 1) for b in (-1, 0, 1)]
+        if any(k is not None and bc[k] != bc[q] for k in nb):
+            assert Z[node]
+
+
+def test_junction_solve_stable_where_sweeps_grow():
+    """Next to a Dirichlet ghost whose own weight in its condition is almost
+    zero (star 167 at 1025^2: 0.004), mu_J = 40 zone sweeps grow a local
+    mode, while the exact solve of the same zone converges."""
+    P = inputs.star(167)
+    n = P.meta["n"]
+    assert n == 1025
+    _, norms, ok = oracle_for(P, n, 33, junction_sweeps=40, junction_solve=0).solve(rtol=1e-10, max_cycles=8)
+    assert norms[-1] > 1e3 * norms[0]
+    _, norms, ok = oracle_for(P, n, 33).solve(rtol=1e-10, max_cycles=30)
+    assert ok and len(norms) - 1 <= 20
+
+
 # -------------------------------------------------------------- restriction
 def test_restriction_printed_stencils():
     """Sec. 2.5: the partial transfer over Omega_h of an axis-aligned square
