@@ -102,14 +102,14 @@ class Oracle:
         phi = np.ascontiguousarray(phi, dtype=np.float64)
         self.dim = phi.ndim
         # junction relaxation defaults: 2D an exact solve of the zone within
-        # 12h; 3D (the zone is a tube around junction curves) 10 sweeps
+        # 20h; 3D (the zone is a tube around junction curves) 10 sweeps
         # within 2h.  junction_sweeps=0 alone turns it off.
         if junction_solve is None:
             junction_solve = 1 if (self.dim == 2 and junction_sweeps is None) else 0
         if junction_sweeps is None:
             junction_sweeps = 0 if self.dim == 2 else 10
         if junction_radius is None:
-            junction_radius = 12.0 if self.dim == 2 else 2.0
+            junction_radius = 20.0 if self.dim == 2 else 2.0
         self.n = phi.shape[0]
         assert all(s == self.n for s in phi.shape)
         self.params = Params(nu1, nu2, lam, gamma, mode, extra_once, delta_over_h, c_dirichlet,

@@ -1,5 +1,5 @@
 """Writes tests/golden/bench_cycles.json: the number of cycles (plain FP64,
-V(2,1), lambda = 5, junction sweeps on) the FP64 oracle needs to bring each
+V(2,1), lambda = 5, junction relaxation at its defaults) the FP64 oracle needs to bring each
 benchmark workload to its relative-residual target.  Calls only the oracle;
 bench.py uses the counts to scale the oracle's seconds per cycle into its
 unknowns/s baseline.

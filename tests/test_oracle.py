@@ -258,12 +258,13 @@ def test_junction_solve_is_exact_on_its_set():
 
 def test_junction_solve_stable_where_sweeps_grow():
     """Next to a Dirichlet ghost whose own weight in its condition is almost
-    zero (star 167 at 1025^2: 0.004), mu_J = 40 zone sweeps grow a local
-    mode, while the exact solve of the same zone converges."""
+    zero (star 167 at 1025^2: 0.004), mu_J = 40 sweeps of the 12h zone grow
+    a local mode, while the exact zone solve (the 2D default) converges."""
     P = inputs.star(167)
     n = P.meta["n"]
     assert n == 1025
-    _, norms, ok = oracle_for(P, n, 33, junction_sweeps=40, junction_solve=0).solve(rtol=1e-10, max_cycles=8)
+    _, norms, ok = oracle_for(P, n, 33, junction_sweeps=40, junction_solve=0,
+                              junction_radius=12.0).solve(rtol=1e-10, max_cycles=8)
     assert norms[-1] > 1e3 * norms[0]
     _, norms, ok = oracle_for(P, n, 33).solve(rtol=1e-10, max_cycles=30)
     assert ok and len(norms) - 1 <= 20
