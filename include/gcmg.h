@@ -61,9 +61,10 @@ typedef enum {
 /* Cycle parameters (Sec. 2.4, Sec. 3.2).  gcmg_default_params fills the
  * paper's values: nu1 = 2, nu2 = 1, lambda = 5, delta = 3h, mu_D dt = 0.9,
  * mu_N dt = 0.9 * 2h / (3 sqrt(d)), V-cycle; plus the junction relaxation
- * that this library adds for mixed boundaries (mu_J = 40, R_J = 12 in 2D;
- * mu_J = 10, R_J = 2 in 3D; the paper has no counterpart -- without it the
- * V-cycle factor of a mixed problem grows as h shrinks). */
+ * that this library adds for mixed boundaries (2D: an exact solve of the
+ * zone within R_J = 12 h; 3D: mu_J = 10 sweeps within R_J = 2 h; the paper
+ * has no counterpart -- without it the V-cycle factor of a mixed problem
+ * grows as h shrinks). */
 typedef struct {
     int dim;                 /* 2 or 3 */
     int n;                   /* fine nodes per axis: (n - 1) = (n_coarse - 1) * 2^k, k >= 1 */
@@ -81,6 +82,11 @@ typedef struct {
                                 relaxation on every level (0: the paper's smoother alone) */
     double junction_radius;  /* R_J: zone = unknowns within R_J h of a ghost whose 3^d
                                 neighbourhood holds a ghost of the other boundary type */
+    int junction_solve;      /* 1: after every relaxation solve the zone's equations exactly
+                                (values outside held fixed) instead of mu_J sweeps; the zone
+                                is first grown by its ghosts' stencils, then stripped of
+                                ghosts whose stencil leaves it; components of at most 4096
+                                unknowns (larger: GCMG_E_GEOM at the solve) */
 } gcmg_params;
 
 /* Per-solve report.  rel[m] = ||r^(m)||_inf / ||r^(0)||_inf for m = 0..cycles
@@ -137,8 +143,14 @@ gcmg_status gcmg_ghost_equations(const gcmg_ctx *ctx, int level, int64_t *stn_ho
 gcmg_status gcmg_node_types(const gcmg_ctx *ctx, int level, uint8_t *types_host);
 
 /* Junction zone of a level under its current boundary types (host, n^d
- * bytes): 1 for the unknowns that the junction sweeps relax, else 0. */
+ * bytes): 1 for the unknowns within R_J h of a junction ghost, else 0. */
 gcmg_status gcmg_junction_zone(const gcmg_ctx *ctx, int level, uint8_t *mask_host);
+
+/* The unknowns whose equations the exact junction solve of a level solves
+ * (host, n^d bytes, 1 / 0) under its current boundary types; all 0 unless
+ * junction_solve is set.  Builds the zone's inverses if they are out of date
+ * (GCMG_E_GEOM: singular or too large a component). */
+gcmg_status gcmg_junction_solve_set(gcmg_ctx *ctx, int level, uint8_t *mask_host);
 
 /* Boundary type per ghost of a level (host, count bytes): 0 Dirichlet, 1
  * Neumann -- whether the ghost's B lies on Gamma_D or Gamma_N.  Must be given
@@ -219,7 +231,7 @@ int64_t gcmg_launch_counter(void);
 typedef struct gcmg_batch gcmg_batch;
 
 /* Creates `count` domains: params[i] (dim 2, precision 1, gamma 1; nu1, nu2,
- * lambda and junction_sweeps equal across domains; rtol and max_cycles of
+ * lambda, junction_sweeps and junction_solve equal across domains; rtol and max_cycles of
  * params[0] apply to the batch) and phi_dev[i] (device, n_i^2 doubles).  The
  * host geometry of the domains is built in parallel threads. */
 gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double *const *phi_dev, void *stream,

@@ -230,7 +230,10 @@ void relax(gcmg_ctx *c, const LevelView<T> &v, int l, bool extra) {
             launch_ghost_relax<T>(v, dim, c->stream);
         }
     }
-    if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
+    if (c->p.junction_solve) {
+        const DevData<T> &D = data<T>(c)[l];
+        launch_junction_solve<T>(v, g, D.js_inv, D.js_r, c->stream);
+    } else if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
         if (g.jz.in_smem) {
             launch_local<T>(lview<T>(g.jz, v), dim, 0, c->p.junction_sweeps, c->stream);
         } else {
@@ -443,6 +446,7 @@ gcmg_status check_params(const gcmg_params &q) {
     if (p->gamma < 1 || p->gamma > 2 || p->nu1 < 0 || p->nu2 < 0 || p->lambda < 0) return GCMG_E_ARG;
     if (p->precision < 0 || p->precision > 1 || p->max_cycles < 1 || p->max_cycles > 256) return GCMG_E_ARG;
     if (p->junction_sweeps < 0 || p->junction_radius < 0.0 || p->junction_radius > 64.0) return GCMG_E_ARG;
+    if (p->junction_solve < 0 || p->junction_solve > 1) return GCMG_E_ARG;
     return GCMG_OK;
 }
 
@@ -495,6 +499,58 @@ void upload_inverse(gcmg_ctx *c) {
     }
 }
 
+// (re)uploads the exact junction solve of level l
+void upload_js(gcmg_ctx *c, int l) {
+    const HostLevel &L = c->H[l];
+    DevGeom &g = c->G[l];
+    for (int32_t **a : {&g.js_node, &g.js_ghost, &g.js_comp, &g.js_off}) { free_tracked(c, *a); *a = nullptr; }
+    free_tracked(c, g.js_aoff);
+    g.js_aoff = nullptr;
+    auto drop = [&](auto &D) {
+        free_tracked(c, D.js_inv);
+        free_tracked(c, D.js_r);
+        D.js_inv = nullptr;
+        D.js_r = nullptr;
+    };
+    drop(c->D64[l]);
+    if (!c->D32.empty()) drop(c->D32[l]);
+    g.js_n = (int)L.js_node.size();
+    g.js_ncomp = L.js_off.empty() ? 0 : (int)L.js_off.size() - 1;
+    if (g.js_n == 0) return;
+    std::vector<int32_t> comp(g.js_n);
+    for (int k = 0; k < g.js_ncomp; k++)
+        for (int i = L.js_off[k]; i < L.js_off[k + 1]; i++) comp[i] = k;
+    g.js_node = upload<int32_t>(c, L.js_node.data(), L.js_node.size());
+    g.js_ghost = upload<int32_t>(c, L.js_ghost.data(), L.js_ghost.size());
+    g.js_comp = upload<int32_t>(c, comp.data(), comp.size());
+    g.js_off = upload<int32_t>(c, L.js_off.data(), L.js_off.size());
+    g.js_aoff = upload<int64_t>(c, L.js_aoff.data(), L.js_aoff.size());
+    // FP64 for FP64 cycles and single relaxations (gcmg_relax), FP32 for FP32 cycles
+    if (c->p.precision == 0 || c->js64) {
+        c->D64[l].js_inv = upload<double>(c, L.js_inv.data(), L.js_inv.size());
+        c->D64[l].js_r = dalloc<double>(c, g.js_n);
+    }
+    if (!c->D32.empty()) {
+        std::vector<float> inv(L.js_inv.begin(), L.js_inv.end());
+        c->D32[l].js_inv = upload<float>(c, inv.data(), inv.size());
+        c->D32[l].js_r = dalloc<float>(c, g.js_n);
+    }
+    ck(cudaStreamSynchronize(c->stream), "sync");   // the staging vectors die at return
+}
+
+// builds and uploads the exact junction solves that are out of date with bc
+void ensure_junction_solve(gcmg_ctx *c) {
+    if (!c->p.junction_solve) return;
+    for (int l = 0; l < (int)c->H.size(); l++) {
+        HostLevel &L = c->H[l];
+        if (!L.js_dirty) continue;
+        destroy_graph(c);   // a captured graph holds the arrays reallocated below
+        build_junction_solve(L, c->p.junction_radius);
+        upload_js(c, l);
+        L.js_dirty = false;
+    }
+}
+
 void ensure_inverse(gcmg_ctx *c) {
     if (!c->H.back().ainv_dirty) return;
     build_coarse_inverse(c->H.back());
@@ -521,11 +577,13 @@ gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
     p->precision = 0;
     p->max_cycles = 100;
     p->rtol = 1e-10;
-    // 2D: 40 sweeps within 12h; 3D: the zone is a tube around junction curves,
-    // where 10 sweeps within 2h keep the factor bounded (more sweeps on a wider
-    // 3D zone amplify a local ghost mode)
-    p->junction_sweeps = dim == 3 ? 10 : 40;
-    p->junction_radius = dim == 3 ? 2.0 : 12.0;
+    // 2D: an exact solve of the zone within 20h; 3D: the zone is a tube around
+    // junction curves, too large for dense inverses, where 10 sweeps within 2h
+    // keep the factor bounded (more sweeps on a wider 3D zone amplify a local
+    // ghost mode)
+    p->junction_solve = dim == 2 ? 1 : 0;
+    p->junction_sweeps = dim == 3 ? 10 : 0;
+    p->junction_radius = dim == 3 ? 2.0 : 20.0;
     return GCMG_OK;
 }
 
@@ -629,9 +687,13 @@ gcmg_status gcmg_set_bc_types(gcmg_ctx *c, int l, const uint8_t *types) {
         c->version++;
         for (int64_t q = 0; q < L.ng(); q++) L.bc[q] = types[q] ? 1 : 0;
         if (l + 1 == (int)c->H.size()) L.ainv_dirty = true;   // rebuilt before the next solve
-        build_junction(L, c->p.junction_radius);
-        upload_program(c, L.junction, c->G[l].jz);
-        check_program_fits(c, c->G[l].jz);
+        if (c->p.junction_solve) {
+            L.js_dirty = true;                                  // rebuilt before the next solve
+        } else {
+            build_junction(L, c->p.junction_radius);
+            upload_program(c, L.junction, c->G[l].jz);
+            check_program_fits(c, c->G[l].jz);
+        }
         upload_ghost_data<double>(c, l, c->D64[l], false);
         if (!c->D32.empty()) upload_ghost_data<float>(c, l, c->D32[l], false);
         return GCMG_OK;
@@ -661,6 +723,7 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
         const HostLevel &L0 = c->H[0];
         const DevGeom &g0 = c->G[0];
         ensure_inverse(c);
+        ensure_junction_solve(c);
         double *u = c->D64[0].u;   // internal buffer: the captured graph uses fixed pointers
         if (u_dev != u)
             ck(cudaMemcpyAsync(u, u_dev, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u in");
@@ -767,6 +830,17 @@ gcmg_status gcmg_relax(gcmg_ctx *c, int l, double *u, const double *f, const dou
     if (!valid_level(c, l) || !u || !f) return fail(c, GCMG_E_ARG, "bad argument");
     GCMG_GUARD(c, {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
+        ensure_junction_solve(c);
+        if (c->p.junction_solve && !c->js64) {   // FP64 inverses for FP64 relaxations
+            c->js64 = true;
+            for (int k = 0; k < (int)c->H.size(); k++) {
+                const HostLevel &L = c->H[k];
+                if (L.js_node.empty() || c->D64[k].js_inv) continue;
+                c->D64[k].js_inv = upload<double>(c, L.js_inv.data(), L.js_inv.size());
+                c->D64[k].js_r = dalloc<double>(c, L.js_node.size());
+            }
+            ck(cudaStreamSynchronize(c->stream), "sync");
+        }
         LevelView<double> v = view<double>(c, l, c->D64[l]);
         v.u = u;
         v.f = f;
@@ -846,12 +920,21 @@ int64_t gcmg_launch_counter(void) { return (int64_t)g_launches.load(); }
 
 gcmg_status gcmg_junction_zone(const gcmg_ctx *c, int l, uint8_t *mask) {
     if (!valid_level(c, l) || !mask) return GCMG_E_ARG;
-    const HostLevel &L = c->H[l];
-    std::memset(mask, 0, L.nn);
-    const auto &J = L.junction;
-    for (int k = 0; k < J.ncomp(); k++)
-        for (int i = J.node_off[k]; i < J.node_off[k] + J.wb_cnt[k]; i++) mask[J.lnode[i]] = 1;
+    const std::vector<uint8_t> z = junction_zone_mask(c->H[l], c->p.junction_radius);
+    std::memcpy(mask, z.data(), z.size());
     return GCMG_OK;
+}
+
+gcmg_status gcmg_junction_solve_set(gcmg_ctx *c, int l, uint8_t *mask) {
+    if (!valid_level(c, l) || !mask) return fail(c, GCMG_E_ARG, "bad level or pointer");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        ensure_junction_solve(c);
+        const HostLevel &L = c->H[l];
+        std::memset(mask, 0, L.nn);
+        for (int32_t p : L.js_node) mask[p] = 1;
+        return GCMG_OK;
+    })
 }
 
 }  // extern "C"

@@ -49,6 +49,13 @@ struct BView32 {
     const float *Ainv;
     int nunk;
     int dom;
+    const int *active;       // per-domain flag: still iterating
+    // exact junction solve of this level
+    const int32_t *js_node, *js_ghost, *js_comp, *js_off;
+    const int64_t *js_aoff;
+    const float *js_inv;
+    float *js_r;
+    int js_n;
 };
 
 // level 0 of one domain in FP64 plus its FP32 correction arrays
@@ -56,6 +63,7 @@ struct BView64 {
     LevelView<double> v;
     float *f32, *g32, *e32;
     int dom;
+    const int *active;
 };
 
 constexpr int kThreads = 256;
@@ -68,17 +76,42 @@ const int kTileC[kVariants] = {64, 128, 32};
 template <int TR, int TC>
 __global__ void __launch_bounds__(256) kb_fused(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     rb_fused2d_body<float, TR, TC>(V[b.view].v, V[b.view].tiles[b.start]);
 }
 
 __global__ void __launch_bounds__(LOCAL_THREADS) kb_local(const BView32 *__restrict__ V, const BItem *__restrict__ it,
                                                           int junction, int lead_ghost, int reps) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     local_body<float, 2>(junction ? V[b.view].jz : V[b.view].bz, b.start, lead_ghost, reps);
+}
+
+// exact junction solve: defects of the solved equations (256 rows per item),
+// then u += A_ZZ^-1 r (one warp per row, kJsRows rows per item)
+constexpr int kJsRows = 8;
+
+__global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
+    const BView32 &w = V[b.view];
+    const int k = b.start + threadIdx.x;
+    if (k < w.js_n) w.js_r[k] = js_defect<float, 2>(w.v, w.js_node[k], w.js_ghost[k]);
+}
+
+__global__ void __launch_bounds__(kJsRows * 32) kb_js_apply(const BView32 *__restrict__ V,
+                                                            const BItem *__restrict__ it) {
+    const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
+    const BView32 &w = V[b.view];
+    const int k = b.start + (threadIdx.x >> 5);
+    if (k < w.js_n)
+        js_apply_row<float>(w.v.u, w.js_node, w.js_comp, w.js_off, w.js_aoff, w.js_inv, w.js_r, k, threadIdx.x & 31);
 }
 
 __global__ void kb_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const LevelView<float> &v = V[b.view].v;
     const int64_t p = (int64_t)b.start + threadIdx.x;
     if (p < v.nn) defect_node<float, 2>(v, p, false);
@@ -86,6 +119,7 @@ __global__ void kb_defect(const BView32 *__restrict__ V, const BItem *__restrict
 
 __global__ void kb_defect_ghost(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const LevelView<float> &v = V[b.view].v;
     const int q = b.start + threadIdx.x;
     if (q < v.ng) defect_ghost_item<float, 9>(v, q);
@@ -93,6 +127,7 @@ __global__ void kb_defect_ghost(const BView32 *__restrict__ V, const BItem *__re
 
 __global__ void kb_restrict(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     const int64_t X = (int64_t)b.start + threadIdx.x;
     if (X < w.c.nn) restrict_node<float, 2>(w.v, w.c, X, w.cf);
@@ -100,6 +135,7 @@ __global__ void kb_restrict(const BView32 *__restrict__ V, const BItem *__restri
 
 __global__ void kb_transfer(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     const int q = b.start + threadIdx.x;
     if (q < w.c.ng) ghost_transfer_row<float>(w.v.r, w.v.gnode, w.gt_ptr, w.gt_col, w.gt_val, w.cg, q);
@@ -108,6 +144,7 @@ __global__ void kb_transfer(const BView32 *__restrict__ V, const BItem *__restri
 // zero u of the view's level (coarse = 0) or of its coarser level (coarse = 1)
 __global__ void kb_zero(const BView32 *__restrict__ V, const BItem *__restrict__ it, int coarse) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const LevelView<float> &v = coarse ? V[b.view].c : V[b.view].v;
     const int64_t p = (int64_t)b.start + threadIdx.x;
     if (p < v.nn) v.u[p] = 0.f;
@@ -115,6 +152,7 @@ __global__ void kb_zero(const BView32 *__restrict__ V, const BItem *__restrict__
 
 __global__ void kb_prolong(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     const int64_t p = (int64_t)b.start + threadIdx.x;
     if (p < w.v.nn) prolong_node<float, 2>(w.v, w.c, w.c.u, w.v.u, true, p);
@@ -122,6 +160,7 @@ __global__ void kb_prolong(const BView32 *__restrict__ V, const BItem *__restric
 
 __global__ void kb_coarse(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     coarse_rows<float>(w.v, w.unk_node, w.unk_ghost, w.Ainv, w.nunk, b.start, kCoarseBlocks);
 }
@@ -130,6 +169,7 @@ __global__ void kb_coarse(const BView32 *__restrict__ V, const BItem *__restrict
 __global__ void kb_defect64(const BView64 *__restrict__ V, const BItem *__restrict__ it, unsigned long long *norms,
                             int ghosts) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;   // uniform per block
     const LevelView<double> &v = V[b.view].v;
     double val = 0.0;
     if (!ghosts) {
@@ -161,6 +201,7 @@ __global__ void kb_rhs_norm(const BView64 *__restrict__ V, const BItem *__restri
 // FP64 defect -> FP32 right-hand side; e32 = 0
 __global__ void kb_to_f32(const BView64 *__restrict__ V, const BItem *__restrict__ it, int ghosts) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const BView64 &w = V[b.view];
     if (!ghosts) {
         const int64_t p = (int64_t)b.start + threadIdx.x;
@@ -177,6 +218,7 @@ __global__ void kb_to_f32(const BView64 *__restrict__ V, const BItem *__restrict
 // u64 += e32 on Omega_h u Gamma_h
 __global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
     const BView64 &w = V[b.view];
     const int64_t p = (int64_t)b.start + threadIdx.x;
     if (p >= w.v.nn) return;
@@ -186,15 +228,18 @@ __global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ 
 
 // end of one refinement step: per-domain relative residual, loop condition
 __global__ void kb_check(cudaGraphConditionalHandle h, const unsigned long long *norms, const double *r0, double *rel,
-                         int *m, int ndom, double rtol, int max_steps) {
+                         int *m, int *active, int *steps_of, int ndom, double rtol, int max_steps) {
     __shared__ int pending;
     if (threadIdx.x == 0) pending = 0;
     __syncthreads();
     const int k = *m + 1;
     for (int d = threadIdx.x; d < ndom; d += blockDim.x) {
+        if (!active[d]) continue;    // converged earlier: its work is skipped
         const double v = __longlong_as_double((long long)norms[d]) / r0[d];
         if (k <= 256) rel[(size_t)d * 257 + k] = v;
-        if (!(v <= rtol)) atomicAdd(&pending, 1);
+        steps_of[d] = k;
+        if (!(v <= rtol) && v == v && !isinf(v)) atomicAdd(&pending, 1);
+        else active[d] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -213,8 +258,8 @@ inline void ck(cudaError_t e, const char *what) {
 
 // a captured launch: kernel kind, item range and parameters
 struct Launch {
-    enum Kind { FUSED, BOUNDARY, JUNCTION, DEFECT, DEFECT_GHOST, RESTRICT, TRANSFER, ZERO_COARSE, PROLONG, COARSE,
-                ZERO };
+    enum Kind { FUSED, BOUNDARY, JUNCTION, JS_DEFECT, JS_APPLY, DEFECT, DEFECT_GHOST, RESTRICT, TRANSFER,
+                ZERO_COARSE, PROLONG, COARSE, ZERO };
     Kind kind;
     size_t off, count;
     size_t smem;
@@ -240,6 +285,7 @@ struct gcmg_batch {
     unsigned long long *d_norms = nullptr;
     double *d_r0 = nullptr, *d_rel = nullptr;
     int *d_m = nullptr;
+    int *d_active = nullptr, *d_steps = nullptr;   // per domain
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -339,6 +385,15 @@ void build_tables(gcmg_batch *b) {
             w.Ainv = c->D32[l].Ainv;
             w.nunk = c->G[l].nunk;
             w.dom = d;
+            w.active = b->d_active;
+            w.js_n = c->G[l].js_n;
+            w.js_node = c->G[l].js_node;
+            w.js_ghost = c->G[l].js_ghost;
+            w.js_comp = c->G[l].js_comp;
+            w.js_off = c->G[l].js_off;
+            w.js_aoff = c->G[l].js_aoff;
+            w.js_inv = c->D32[l].js_inv;
+            w.js_r = c->D32[l].js_r;
             b->view_of[d].push_back((int)v32.size());
             v32.push_back(w);
             if (!c->G[l].bz.in_smem || (c->p.junction_sweeps > 0 && c->G[l].jz.ncomp > 0 && !c->G[l].jz.in_smem))
@@ -351,6 +406,7 @@ void build_tables(gcmg_batch *b) {
         w64.g32 = c->D32[0].gg;
         w64.e32 = c->D32[0].u;
         w64.dom = d;
+        w64.active = b->d_active;
         v64.push_back(w64);
     }
     // items
@@ -384,6 +440,22 @@ void build_tables(gcmg_batch *b) {
                 if (J.ncomp) smem = std::max(smem, smem_of(J));
             }
             add_launch(which ? Launch::JUNCTION : Launch::BOUNDARY, s0, smem);
+        }
+        if (p0.junction_solve) {
+            s0 = items.size();
+            for (int d = 0; d < nd; d++) {
+                const int l = (int)b->doms[d]->H.size() - 1 - k;
+                if (l >= 0) dense(b->view_of[d][l], v32[b->view_of[d][l]].js_n);
+            }
+            add_launch(Launch::JS_DEFECT, s0, 0);
+            s0 = items.size();
+            for (int d = 0; d < nd; d++) {
+                const int l = (int)b->doms[d]->H.size() - 1 - k;
+                if (l < 0) continue;
+                const int vi = b->view_of[d][l];
+                for (int r = 0; r < v32[vi].js_n; r += kJsRows) items.push_back({vi, (int32_t)r});
+            }
+            add_launch(Launch::JS_APPLY, s0, 0);
         }
     };
     for (int k = kmax; k >= 1; k--) {
@@ -469,6 +541,8 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
             break;
         case Launch::BOUNDARY: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda); break;
         case Launch::JUNCTION: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps); break;
+        case Launch::JS_DEFECT: kb_js_defect<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::JS_APPLY: kb_js_apply<<<n, kJsRows * 32, 0, s>>>(b->d_v32, it); break;
         case Launch::DEFECT: kb_defect<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
         case Launch::DEFECT_GHOST: kb_defect_ghost<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
         case Launch::RESTRICT: kb_restrict<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
@@ -517,8 +591,8 @@ void build_graph(gcmg_batch *b) {
        "begin capture");
     try {
         step_body(b, b->gstream);
-        kb_check<<<1, 256, 0, b->gstream>>>(h, b->d_norms, b->d_r0, b->d_rel, b->d_m, (int)b->doms.size(), b->rtol,
-                                            b->max_steps);
+        kb_check<<<1, 256, 0, b->gstream>>>(h, b->d_norms, b->d_r0, b->d_rel, b->d_m, b->d_active, b->d_steps,
+                                            (int)b->doms.size(), b->rtol, b->max_steps);
     } catch (...) {
         cudaGraph_t dummy;
         cudaStreamEndCapture(b->gstream, &dummy);
@@ -550,7 +624,7 @@ gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double
         const gcmg_params &p = params[i];
         if (!phi_dev[i] || check_params(p) != GCMG_OK || p.dim != 2 || p.precision != 1 || p.gamma != 1 ||
             p.nu1 != params[0].nu1 || p.nu2 != params[0].nu2 || p.lambda != params[0].lambda ||
-            p.junction_sweeps != params[0].junction_sweeps)
+            p.junction_sweeps != params[0].junction_sweeps || p.junction_solve != params[0].junction_solve)
             return GCMG_E_ARG;
     }
     gcmg_batch *b = new (std::nothrow) gcmg_batch;
@@ -611,6 +685,8 @@ gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double
         ck(cudaMalloc(&b->d_r0, count * sizeof(double)), "cudaMalloc");
         ck(cudaMalloc(&b->d_rel, (size_t)count * 257 * sizeof(double)), "cudaMalloc");
         ck(cudaMalloc(&b->d_m, sizeof(int)), "cudaMalloc");
+        ck(cudaMalloc(&b->d_active, count * sizeof(int)), "cudaMalloc");
+        ck(cudaMalloc(&b->d_steps, count * sizeof(int)), "cudaMalloc");
         return GCMG_OK;
     })
 }
@@ -621,7 +697,9 @@ void gcmg_batch_destroy(gcmg_batch *b) {
     if (b->gstream) cudaStreamSynchronize(b->gstream);
     free_tables(b);
     for (gcmg_ctx *c : b->doms) gcmg_destroy(c);
-    for (void *p : {(void *)b->d_norms, (void *)b->d_r0, (void *)b->d_rel, (void *)b->d_m}) cudaFree(p);
+    for (void *p : {(void *)b->d_norms, (void *)b->d_r0, (void *)b->d_rel, (void *)b->d_m, (void *)b->d_active,
+                    (void *)b->d_steps})
+        cudaFree(p);
     if (b->gstream) cudaStreamDestroy(b->gstream);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -675,13 +753,53 @@ gcmg_status gcmg_batch_solve(gcmg_batch *b, gcmg_stats *stats, int *steps) {
                 upload_inverse(b->doms[dirty[i]]);
             }
         }
-        if (stale(b)) {
+        bool rebuilt = false;
+        {   // exact junction solves out of date: rebuild on host threads, then upload
+            std::vector<std::pair<int, int>> dirty;   // (domain, level)
+            for (int d = 0; d < (int)b->doms.size(); d++) {
+                gcmg_ctx *c = b->doms[d];
+                if (!c->p.junction_solve) continue;
+                for (int l = 0; l < (int)c->H.size(); l++)
+                    if (c->H[l].js_dirty) dirty.push_back({d, l});
+            }
+            std::vector<std::string> errs(dirty.size());
+            std::atomic<int> next{0};
+            const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+            std::vector<std::thread> pool;
+            for (unsigned t = 0; t < nt; t++)
+                pool.emplace_back([&]() {
+                    for (int i = next++; i < (int)dirty.size(); i = next++) {
+                        gcmg_ctx *c = b->doms[dirty[i].first];
+                        try {
+                            build_junction_solve(c->H[dirty[i].second], c->p.junction_radius);
+                        } catch (const GeomError &g) {
+                            errs[i] = g.msg;
+                        }
+                    }
+                });
+            for (auto &t : pool) t.join();
+            for (size_t i = 0; i < dirty.size(); i++) {
+                const int d = dirty[i].first, l = dirty[i].second;
+                if (!errs[i].empty()) return bfail(b, GCMG_E_GEOM, "domain " + std::to_string(d) + ": " + errs[i]);
+                upload_js(b->doms[d], l);
+                b->doms[d]->H[l].js_dirty = false;
+                rebuilt = true;
+            }
+        }
+        if (rebuilt || stale(b)) {
             build_tables(b);
             build_graph(b);
         }
         const int nd = (int)b->doms.size();
         cudaStream_t s = b->stream;
         const BItem *in = b->d_items + b->items64_nodes, *ig = b->d_items + b->items64_ghosts;
+        {   // every domain starts active; the step kernels skip the inactive ones
+            std::vector<int> ones(nd, 1), zeros(nd, 0);
+            ck(cudaMemcpyAsync(b->d_active, ones.data(), nd * sizeof(int), cudaMemcpyHostToDevice, s), "active");
+            ck(cudaMemcpyAsync(b->d_steps, zeros.data(), nd * sizeof(int), cudaMemcpyHostToDevice, s), "steps");
+            ck(cudaMemsetAsync(b->d_rel, 0, (size_t)nd * 257 * sizeof(double), s), "memset");
+            ck(cudaStreamSynchronize(s), "sync");   // the staging vectors die at scope end
+        }
         for (gcmg_ctx *c : b->doms)
             ck(cudaMemsetAsync(c->D64[0].u, 0, c->H[0].nn * sizeof(double), s), "memset");
         // ||r0|| = ||(f, g)|| per domain
@@ -715,16 +833,18 @@ gcmg_status gcmg_batch_solve(gcmg_batch *b, gcmg_stats *stats, int *steps) {
         g_launches += 4 + b->graph_kernels * m;
         std::vector<double> rel((size_t)nd * 257, 0.0);
         ck(cudaMemcpy(rel.data(), b->d_rel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost), "rel");
+        std::vector<int> steps_of(nd, 0);
+        ck(cudaMemcpy(steps_of.data(), b->d_steps, nd * sizeof(int), cudaMemcpyDeviceToHost), "steps");
         bool all = true;
         for (int d = 0; d < nd; d++) {
-            const int kept = std::min(m, 256);
+            const int kept = std::min(steps_of[d], 256);
             const double last = kept > 0 ? rel[(size_t)d * 257 + kept] : 1.0;
             const bool ok = last <= b->rtol;
             all = all && ok;
             if (stats) {
                 gcmg_stats &st = stats[d];
                 std::memset(&st, 0, sizeof(st));
-                st.cycles = m;
+                st.cycles = steps_of[d];
                 st.converged = ok ? 1 : 0;
                 st.rel_residual = last;
                 st.r0_norm = r0[d];
@@ -758,6 +878,10 @@ gcmg_status gcmg_batch_autotune(gcmg_batch *b, int *best, double *ms) {
         cudaEvent_t e0, e1;
         ck(cudaEventCreate(&e0), "event");
         ck(cudaEventCreate(&e1), "event");
+        {   // time the sweeps of every domain
+            std::vector<int> ones(b->doms.size(), 1);
+            ck(cudaMemcpy(b->d_active, ones.data(), ones.size() * sizeof(int), cudaMemcpyHostToDevice), "active");
+        }
         double bestms = 1e30;
         int bestv = b->variant;
         for (int v = 0; v < kVariants; v++) {

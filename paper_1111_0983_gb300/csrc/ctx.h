@@ -24,6 +24,7 @@ struct gcmg_ctx {
     std::vector<DevData<double>> D64;
     std::vector<DevData<float>> D32;
     bool rhs_set = false;
+    bool js64 = false;                      // FP64 junction-solve inverses kept (single relaxations)
     unsigned long long *d_norm = nullptr;   // two slots: defect norm, rhs norm
     unsigned long long *h_norm = nullptr;   // pinned
     // the solve loop as one CUDA graph: a device-side while loop over cycles
@@ -97,6 +98,9 @@ void prepare_levels(const gcmg_params &p, const double *phi_host, std::vector<Ho
 gcmg_status check_params(const gcmg_params &p);
 // Rebuilds (if out of date) and uploads the coarsest inverse; upload only.
 void ensure_inverse(gcmg_ctx *c);
+// builds and uploads the exact junction solves that are out of date with bc
+void ensure_junction_solve(gcmg_ctx *c);
+void upload_js(gcmg_ctx *c, int l);
 void upload_inverse(gcmg_ctx *c);
 // Creates a context from prepared levels (uploads everything to the current device).
 gcmg_status create_from_levels(const gcmg_params &p, std::vector<HostLevel> &&H, cudaStream_t stream, gcmg_ctx **out);

@@ -72,6 +72,14 @@ struct HostLevel {
     // shared-memory relaxation programs: the junction zone (depends on bc)
     // and, in 2D, the boundary blocks of the lambda extra sweeps
     LocalProgram junction, boundary;
+    // exact junction solve (2D): the solved set split into independent
+    // components; per component its nodes (increasing), their ghost numbers
+    // (-1: inside node) and the dense inverse of their equations
+    std::vector<int32_t> js_off;        // ncomp + 1 offsets into js_node
+    std::vector<int32_t> js_node, js_ghost;
+    std::vector<int64_t> js_aoff;       // ncomp + 1 offsets into js_inv
+    std::vector<double> js_inv;         // per component m x m, row major
+    bool js_dirty = true;               // out of date with bc
     // coarsest level: unknowns (node, ghost number or -1) and dense inverse
     std::vector<int32_t> unk_node, unk_ghost;
     std::vector<double> Ainv;           // nunk * nunk, row major
@@ -92,6 +100,14 @@ void number_coarse_unknowns(HostLevel &L);
 void build_coarse_inverse(HostLevel &L);
 // Junction zone of the level's current bc (radius in h).
 void build_junction(HostLevel &L, double radius);
+// The zone's unknowns as a mask (1 / 0, nn bytes).
+std::vector<uint8_t> junction_zone_mask(const HostLevel &L, double radius);
+// Exact junction solve of the level's current bc: the zone within radius h,
+// grown by its ghosts' stencils and stripped of ghosts whose stencil leaves
+// it, in components with the inverses of their equations (throws GeomError).
+void build_junction_solve(HostLevel &L, double radius);
+// Largest component of an exact junction solve.
+constexpr int JS_MAX = 4096;
 // 2D boundary blocks of the extra sweeps: block x block tiles with a halo
 // covering the dependency cone of one ghost sweep + lambda (R, B, G) sweeps.
 void build_boundary_blocks(HostLevel &L, int lambda, int block);
@@ -126,6 +142,10 @@ struct DevGeom {
     int32_t *unk_node = nullptr, *unk_ghost = nullptr;
     std::vector<int> wave;       // host copy of the wavefront offsets
     LocalDev jz, bz;             // junction zone / boundary blocks
+    // exact junction solve: js_n rows in js_ncomp components
+    int js_n = 0, js_ncomp = 0;
+    int32_t *js_node = nullptr, *js_ghost = nullptr, *js_comp = nullptr, *js_off = nullptr;
+    int64_t *js_aoff = nullptr;
 };
 
 // Floating-point data of a level in precision T.
@@ -139,6 +159,8 @@ struct DevData {
     T *ew = nullptr;     // EMAX * ne extension weights, slot major
     T *gt_val = nullptr; // ghost transfer weights to the next level
     T *Ainv = nullptr;   // nunk * nunk (coarsest level)
+    T *js_inv = nullptr; // inverses of the junction-solve components
+    T *js_r = nullptr;   // js_n defects of the junction-solve equations
 };
 
 // Kernel view of one level in precision T (passed by value).

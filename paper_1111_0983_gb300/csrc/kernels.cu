@@ -322,6 +322,35 @@ void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv,
     k_coarse_solve<T><<<blocks, threads, (size_t)m * sizeof(T), s>>>(v, g.unk_node, g.unk_ghost, Ainv, m);
 }
 
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads) k_js_defect(LevelView<T> v, const int32_t *__restrict__ node,
+                                                        const int32_t *__restrict__ ghost, T *__restrict__ r, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) r[k] = dev::js_defect<T, D>(v, node[k], ghost[k]);
+}
+
+constexpr int kJsRowsPerBlock = 8;   // one warp per row
+
+template <typename T>
+__global__ void __launch_bounds__(kJsRowsPerBlock * 32)
+    k_js_apply(T *__restrict__ u, const int32_t *__restrict__ node, const int32_t *__restrict__ comp,
+               const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const T *__restrict__ inv,
+               const T *__restrict__ r, int n) {
+    const int k = blockIdx.x * kJsRowsPerBlock + (threadIdx.x >> 5);
+    if (k < n) dev::js_apply_row<T>(u, node, comp, off, aoff, inv, r, k, threadIdx.x & 31);
+}
+
+template <typename T>
+void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv, T *r, cudaStream_t s) {
+    const int n = g.js_n;
+    if (n <= 0) return;
+    g_launches += 2;
+    if (g.dim == 2) k_js_defect<T, 2><<<blocks_for(n), kThreads, 0, s>>>(v, g.js_node, g.js_ghost, r, n);
+    else k_js_defect<T, 3><<<blocks_for(n), kThreads, 0, s>>>(v, g.js_node, g.js_ghost, r, n);
+    k_js_apply<T><<<(unsigned)((n + kJsRowsPerBlock - 1) / kJsRowsPerBlock), kJsRowsPerBlock * 32, 0, s>>>(
+        v.u, g.js_node, g.js_comp, g.js_off, g.js_aoff, inv, r, n);
+}
+
 template <typename T>
 size_t local_smem_bytes(const LocalView<T> &J, int dim) {
     const int K = dim == 2 ? 9 : 27;
@@ -378,6 +407,7 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_prolong<T>(const LevelView<T> &, const LevelView<T> &, int, const T *, T *, bool,  \
                                     cudaStream_t);                                                       \
     template void launch_coarse_solve<T>(const LevelView<T> &, const DevGeom &, const T *, cudaStream_t); \
+    template void launch_junction_solve<T>(const LevelView<T> &, const DevGeom &, const T *, T *, cudaStream_t); \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
     template size_t local_smem_bytes<T>(const LocalView<T> &, int);                                 \
     template void launch_local<T>(const LocalView<T> &, int, int, int, cudaStream_t);               \

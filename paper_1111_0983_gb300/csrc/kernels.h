@@ -36,6 +36,10 @@ void launch_prolong(const LevelView<T> &F, const LevelView<T> &C, int dim, const
                     cudaStream_t s);
 template <typename T>
 void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv, cudaStream_t s);
+// exact junction solve: defects of the solved equations into r, then
+// u += A_ZZ^-1 r per component
+template <typename T>
+void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv, T *r, cudaStream_t s);
 template <typename T>
 void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s);
 

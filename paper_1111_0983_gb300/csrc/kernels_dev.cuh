@@ -397,6 +397,42 @@ __device__ __forceinline__ void prolong_node(const LevelView<T> &F, const LevelV
 }
 
 // --------------------------------------------------------------- coarsest
+// ---------------------------------------------------- exact junction solve
+// Defect of the equation of row k of the junction solve: at an inside node
+// f + Lap_h u (as a sum of differences), at ghost q g - L_G u.
+template <typename T, int D>
+__device__ __forceinline__ T js_defect(const LevelView<T> &v, int32_t p, int32_t q) {
+    if (q >= 0) {
+        constexpr int K = D == 2 ? 9 : 27;
+        T s = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) s += v.gw[(int64_t)k * v.ng + q] * v.u[v.gstn[(int64_t)k * v.ng + q]];
+        return v.gg[q] - s;
+    }
+    const T up = v.u[p];
+    T lap = (v.u[p - 1] - up) + (v.u[p + 1] - up) + (v.u[p - v.s0] - up) + (v.u[p + v.s0] - up);
+    if (D == 3) lap += (v.u[p - v.s1] - up) + (v.u[p + v.s1] - up);
+    return v.f[p] + lap * v.inv_h2;
+}
+
+// u(node k) += sum_j Ainv_c[k - off_c, j] r[off_c + j] for row k of component
+// c: one warp per row, lanes striding the row.
+template <typename T>
+__device__ __forceinline__ void js_apply_row(T *__restrict__ u, const int32_t *__restrict__ node,
+                                             const int32_t *__restrict__ comp, const int32_t *__restrict__ off,
+                                             const int64_t *__restrict__ aoff, const T *__restrict__ inv,
+                                             const T *__restrict__ r, int k, int lane) {
+    const int c = comp[k];
+    const int o = off[c];
+    const int m = off[c + 1] - o;
+    const T *a = inv + aoff[c] + (int64_t)(k - o) * m;
+    const T *rr = r + o;
+    T s = 0;
+    for (int j = lane; j < m; j += 32) s += a[j] * rr[j];
+    for (int w = 16; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+    if (lane == 0) u[node[k]] += s;
+}
+
 // e = A^-1 b on the coarsest level, rows blk, blk + nblk, ... of one CTA: b
 // gathered into shared memory from f (inside) and the ghost data, each warp
 // computing row dot products of the dense inverse.

@@ -530,11 +530,11 @@ struct ProgramBuilder {
 // holds a ghost of the other boundary type.  Split into components closed
 // under the reads of their updates (inside node: axis neighbours; ghost: its
 // stencil), so each can be relaxed on its own.
-void build_junction(HostLevel &L, double radius) {
+// Unknowns within radius h of a junction ghost: a ghost whose 3^d
+// neighbourhood holds a ghost of the other boundary type.
+static std::vector<uint8_t> junction_marks(const HostLevel &L, double radius, const std::vector<int32_t> &ghost_of) {
     Idx I{L};
     const int d = L.dim;
-    LocalProgram prog;
-    ProgramBuilder PB(L, prog);
     std::vector<uint8_t> zone(L.nn, 0);
     const int R = (int)std::ceil(radius);
     const int cube = d == 2 ? 9 : 27;
@@ -546,7 +546,7 @@ void build_junction(HostLevel &L, double radius) {
             int k[3] = {0, 0, 0}, rem = c;
             for (int a = d - 1; a >= 0; a--) { k[a] = j[a] + rem % 3 - 1; rem /= 3; }
             if (!I.inside_box(k)) continue;
-            const int32_t g2 = PB.ghost_of[I.join(k)];
+            const int32_t g2 = ghost_of[I.join(k)];
             if (g2 >= 0 && L.bc[g2] != L.bc[q]) junction = true;
         }
         if (!junction) continue;
@@ -566,6 +566,19 @@ void build_junction(HostLevel &L, double radius) {
             if (unknown(L, P)) zone[P] = 1;
         }
     }
+    return zone;
+}
+
+std::vector<uint8_t> junction_zone_mask(const HostLevel &L, double radius) {
+    std::vector<int32_t> ghost_of(L.nn, -1);
+    for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;
+    return junction_marks(L, radius, ghost_of);
+}
+
+void build_junction(HostLevel &L, double radius) {
+    LocalProgram prog;
+    ProgramBuilder PB(L, prog);
+    const std::vector<uint8_t> zone = junction_marks(L, radius, PB.ghost_of);
     std::vector<int64_t> zn;
     for (int64_t P = 0; P < L.nn; P++)
         if (zone[P]) zn.push_back(P);
@@ -815,50 +828,173 @@ void number_coarse_unknowns(HostLevel &L) {
 
 // Dense inverse of the coarsest system (Eq. discr with the level's bc):
 // Gauss-Jordan elimination with partial pivoting on [A | I].
+namespace {
+
+// Inverse of an m x m system given row by row as (column, value) pairs, by
+// an LU factorisation with partial pivoting confined to the band of the
+// matrix, then m triangular solves.  Unknowns numbered in node order couple
+// within about one grid row, so this costs O(m bw^2 + m^2 bw) rather than
+// the O(m^3) of eliminating the full matrix.  X: row major, m x m.
+using Rows = std::vector<std::vector<std::pair<int64_t, double>>>;
+
+void invert_rows(int64_t m, const Rows &rows, std::vector<double> &X, const char *singular) {
+    std::vector<double> A((size_t)(m * m), 0.0);
+    int64_t bl = 0, bu = 0;
+    for (int64_t i = 0; i < m; i++)
+        for (const auto &cv : rows[i]) {
+            A[i * m + cv.first] += cv.second;
+            bl = std::max(bl, i - cv.first);
+            bu = std::max(bu, cv.first - i);
+        }
+    const int64_t ub = bu + bl;   // upper bandwidth once rows have been swapped
+    std::vector<int64_t> piv(m);
+    for (int64_t c = 0; c < m; c++) {
+        const int64_t last = std::min(m - 1, c + bl);
+        int64_t p = c;
+        for (int64_t i = c + 1; i <= last; i++)
+            if (std::fabs(A[i * m + c]) > std::fabs(A[p * m + c])) p = i;
+        if (!(std::fabs(A[p * m + c]) > 0.0)) throw GeomError{singular};
+        piv[c] = p;
+        // the interchange moves the U part only; the multipliers already
+        // stored stay where they are and the solves apply the interchanges
+        // one elimination step at a time, in the same order
+        const int64_t j1 = std::min(m - 1, c + ub);
+        if (p != c)
+            for (int64_t jj = c; jj <= j1; jj++) std::swap(A[c * m + jj], A[p * m + jj]);
+        const double inv = 1.0 / A[c * m + c];
+        for (int64_t i = c + 1; i <= last; i++) {
+            const double f = A[i * m + c] * inv;
+            A[i * m + c] = f;
+            if (f == 0.0) continue;
+            for (int64_t jj = c + 1; jj <= j1; jj++) A[i * m + jj] -= f * A[c * m + jj];
+        }
+    }
+    X.assign((size_t)(m * m), 0.0);
+    std::vector<double> b(m);
+    for (int64_t col = 0; col < m; col++) {
+        std::fill(b.begin(), b.end(), 0.0);
+        b[col] = 1.0;
+        for (int64_t c = 0; c < m; c++) {
+            if (piv[c] != c) std::swap(b[c], b[piv[c]]);
+            const double bc = b[c];
+            if (bc == 0.0) continue;
+            const int64_t last = std::min(m - 1, c + bl);
+            for (int64_t i = c + 1; i <= last; i++) b[i] -= A[i * m + c] * bc;
+        }
+        for (int64_t c = m - 1; c >= 0; c--) {
+            double t = b[c];
+            const int64_t j1 = std::min(m - 1, c + ub);
+            for (int64_t jj = c + 1; jj <= j1; jj++) t -= A[c * m + jj] * b[jj];
+            b[c] = t / A[c * m + c];
+        }
+        for (int64_t i = 0; i < m; i++) X[i * m + col] = b[i];
+    }
+}
+
+// The equation of unknown p (inside: -Lap_h; ghost q: its boundary condition
+// with the current type) over the columns id[] gives; nodes without a column
+// (id < 0) are held fixed and left out.
+void equation_row(const HostLevel &L, int64_t p, int32_t q, const std::vector<int64_t> &id,
+                  std::vector<std::pair<int64_t, double>> &row) {
+    row.clear();
+    if (q < 0) {
+        const double ih2 = 1.0 / (L.h * L.h);
+        row.emplace_back(id[p], 2.0 * L.dim * ih2);
+        for (int a = 0; a < L.dim; a++)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const int64_t P = p + sg * L.stride[a];
+                if (id[P] >= 0) row.emplace_back(id[P], -ih2);
+            }
+    } else {
+        const double *w = (L.bc[q] ? L.wN.data() : L.wD.data()) + (int64_t)q * KMAX;
+        for (int k = 0; k < KMAX; k++) {
+            const int64_t P = L.stn[(int64_t)q * KMAX + k];
+            if (w[k] != 0.0 && id[P] >= 0) row.emplace_back(id[P], w[k]);
+        }
+    }
+}
+
+}  // namespace
+
 void build_coarse_inverse(HostLevel &L) {
     std::vector<int64_t> id(L.nn, -1);
     for (size_t i = 0; i < L.unk_node.size(); i++) id[L.unk_node[i]] = (int64_t)i;
     const int64_t m = (int64_t)L.unk_node.size();
-    std::vector<double> A(m * m, 0.0), X(m * m, 0.0);
-    const double ih2 = 1.0 / (L.h * L.h);
-    for (int64_t i = 0; i < m; i++) {
-        const int64_t p = L.unk_node[i];
-        X[i * m + i] = 1.0;
-        if (L.unk_ghost[i] < 0) {
-            A[i * m + i] += 2.0 * L.dim * ih2;
-            for (int a = 0; a < L.dim; a++) {
-                A[i * m + id[p + L.stride[a]]] -= ih2;
-                A[i * m + id[p - L.stride[a]]] -= ih2;
-            }
-        } else {
-            const int64_t q = L.unk_ghost[i];
-            const double *w = (L.bc[q] ? L.wN.data() : L.wD.data()) + q * KMAX;
-            for (int k = 0; k < KMAX; k++)
-                if (w[k] != 0.0) A[i * m + id[L.stn[q * KMAX + k]]] += w[k];
-        }
-    }
-    for (int64_t c = 0; c < m; c++) {
-        int64_t piv = c;
-        for (int64_t i = c + 1; i < m; i++)
-            if (std::fabs(A[i * m + c]) > std::fabs(A[piv * m + c])) piv = i;
-        if (!(std::fabs(A[piv * m + c]) > 0.0)) throw GeomError{"singular coarsest-level system"};
-        if (piv != c) {
-            std::swap_ranges(A.begin() + c * m, A.begin() + (c + 1) * m, A.begin() + piv * m);
-            std::swap_ranges(X.begin() + c * m, X.begin() + (c + 1) * m, X.begin() + piv * m);
-        }
-        const double inv = 1.0 / A[c * m + c];
-        for (int64_t j = 0; j < m; j++) { A[c * m + j] *= inv; X[c * m + j] *= inv; }
-        for (int64_t i = 0; i < m; i++) {
-            if (i == c) continue;
-            const double f = A[i * m + c];
-            if (f == 0.0) continue;
-            double *ai = &A[i * m], *xi = &X[i * m];
-            const double *ac = &A[c * m], *xc = &X[c * m];
-            for (int64_t j = 0; j < m; j++) { ai[j] -= f * ac[j]; xi[j] -= f * xc[j]; }
-        }
-    }
-    L.Ainv.swap(X);
+    Rows rows(m);
+    for (int64_t i = 0; i < m; i++) equation_row(L, L.unk_node[i], L.unk_ghost[i], id, rows[i]);
+    invert_rows(m, rows, L.Ainv, "singular coarsest-level system");
     L.ainv_dirty = false;
+}
+
+void build_junction_solve(HostLevel &L, double radius) {
+    std::vector<int32_t> ghost_of(L.nn, -1);
+    for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;
+    std::vector<uint8_t> in = junction_marks(L, radius, ghost_of);
+    // grow by the stencils of the zone's ghosts (unused slots name the ghost)
+    const std::vector<uint8_t> zone = in;
+    for (int64_t q = 0; q < L.ng(); q++)
+        if (zone[L.ghost_node[q]])
+            for (int k = 0; k < KMAX; k++) in[L.stn[q * KMAX + k]] = 1;
+    // strip ghosts whose stencil leaves the set, until none does
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (int64_t q = 0; q < L.ng(); q++) {
+            const int64_t G = L.ghost_node[q];
+            if (!in[G]) continue;
+            for (int k = 0; k < KMAX; k++)
+                if (!in[L.stn[q * KMAX + k]]) { in[G] = 0; changed = true; break; }
+        }
+    }
+    // components: unknowns joined by the couplings of their equations
+    std::vector<int64_t> nodes;
+    for (int64_t P = 0; P < L.nn; P++)
+        if (in[P]) nodes.push_back(P);
+    std::vector<int64_t> id(L.nn, -1);
+    for (size_t i = 0; i < nodes.size(); i++) id[nodes[i]] = (int64_t)i;
+    std::vector<int64_t> parent(nodes.size());
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int64_t x) {
+        while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
+        return x;
+    };
+    std::vector<std::pair<int64_t, double>> row;
+    for (size_t i = 0; i < nodes.size(); i++) {
+        equation_row(L, nodes[i], ghost_of[nodes[i]], id, row);
+        for (const auto &cv : row) {
+            const int64_t a = find((int64_t)i), b = find(cv.first);
+            if (a != b) parent[std::max(a, b)] = std::min(a, b);
+        }
+    }
+    std::vector<int64_t> comp_of_root(nodes.size(), -1);
+    std::vector<std::vector<int64_t>> comps;
+    for (size_t i = 0; i < nodes.size(); i++) {
+        const int64_t r = find((int64_t)i);
+        if (comp_of_root[r] < 0) { comp_of_root[r] = (int64_t)comps.size(); comps.emplace_back(); }
+        comps[comp_of_root[r]].push_back(nodes[i]);
+    }
+    L.js_off.assign(1, 0);
+    L.js_aoff.assign(1, 0);
+    L.js_node.clear();
+    L.js_ghost.clear();
+    L.js_inv.clear();
+    std::vector<int64_t> lid(L.nn, -1);
+    std::vector<double> X;
+    for (const auto &cz : comps) {
+        const int64_t m = (int64_t)cz.size();
+        if (m > JS_MAX) throw GeomError{"junction zone component larger than " + std::to_string(JS_MAX)};
+        for (int64_t i = 0; i < m; i++) lid[cz[i]] = i;
+        Rows rows(m);
+        for (int64_t i = 0; i < m; i++) equation_row(L, cz[i], ghost_of[cz[i]], lid, rows[i]);
+        invert_rows(m, rows, X, "singular junction-zone system");
+        for (int64_t i = 0; i < m; i++) {
+            L.js_node.push_back((int32_t)cz[i]);
+            L.js_ghost.push_back(ghost_of[cz[i]]);
+            lid[cz[i]] = -1;
+        }
+        L.js_inv.insert(L.js_inv.end(), X.begin(), X.end());
+        L.js_off.push_back((int32_t)L.js_node.size());
+        L.js_aoff.push_back((int64_t)L.js_inv.size());
+    }
 }
 
 }  // namespace gcmg

@@ -25,7 +25,8 @@ class Params(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int), ("n_coarse", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("lam", C.c_int), ("gamma", C.c_int), ("delta_over_h", C.c_double), ("c_dirichlet", C.c_double),
                 ("c_neumann_factor", C.c_double), ("precision", C.c_int), ("max_cycles", C.c_int),
-                ("rtol", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double)]
+                ("rtol", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double),
+                ("junction_solve", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -80,6 +81,7 @@ def lib():
             "gcmg_kernel_timing": (st, [vp, C.POINTER(i64), C.POINTER(dbl)]),
             "gcmg_launch_counter": (i64, []),
             "gcmg_junction_zone": (st, [vp, i32, vp]),
+            "gcmg_junction_solve_set": (st, [vp, i32, vp]),
             "gcmg_defect_noalloc": (st, [i32, i32, dbl, vp, vp, vp, i64, vp, vp, vp, vp, vp, C.POINTER(dbl), vp]),
             "gcmg_batch_create": (st, [i32, C.POINTER(Params), C.POINTER(vp), vp, C.POINTER(vp)]),
             "gcmg_batch_destroy": (None, [vp]),
@@ -199,6 +201,11 @@ class Solver:
     def junction_zone(self, l):
         out = np.empty(self.shape(l), np.uint8)
         self._check(lib().gcmg_junction_zone(self._h, l, _ptr(out)))
+        return out
+
+    def junction_solve_set(self, l):
+        out = np.empty(self.shape(l), np.uint8)
+        self._check(lib().gcmg_junction_solve_set(self._h, l, _ptr(out)))
         return out
 
     def node_types(self, l):
@@ -326,3 +333,4 @@ class Batch:
         ms = (C.c_double * 3)()
         self._check(lib().gcmg_batch_autotune(self._h, C.byref(best), ms))
         return best.value, list(ms)
+
