@@ -55,7 +55,8 @@ typedef enum {
                             degenerate normal, or a singular coarsest system */
     GCMG_E_NOCONV = 5,   /* max_cycles reached, or a NaN/Inf defect */
     GCMG_E_STATE = 6,    /* call out of order (e.g. solve before set_rhs) */
-    GCMG_E_SIZE = 7      /* problem larger than a fixed-capacity entry point accepts */
+    GCMG_E_SIZE = 7,     /* problem larger than a fixed-capacity entry point accepts */
+    GCMG_E_TIMEOUT = 8   /* a bounded device-side wait ran out (the context stays usable) */
 } gcmg_status;
 
 /* Cycle parameters (Sec. 2.4, Sec. 3.2).  gcmg_default_params fills the

@@ -15,9 +15,9 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgcmg.so")
 
-GCMG_OK, GCMG_E_ARG, GCMG_E_CUDA, GCMG_E_OOM, GCMG_E_GEOM, GCMG_E_NOCONV, GCMG_E_STATE, GCMG_E_SIZE = range(8)
+GCMG_OK, GCMG_E_ARG, GCMG_E_CUDA, GCMG_E_OOM, GCMG_E_GEOM, GCMG_E_NOCONV, GCMG_E_STATE, GCMG_E_SIZE, GCMG_E_TIMEOUT = range(9)
 STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_OOM", 4: "E_GEOM", 5: "E_NOCONV", 6: "E_STATE",
-                7: "E_SIZE"}
+                7: "E_SIZE", 8: "E_TIMEOUT"}
 KMAX = 27
 
 
