@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="domains of the batched secondary / stars256 run")
     ap.add_argument("--cpu-sample-cycles", type=int, default=2)
+    ap.add_argument("--learned", type=int, default=8,
+                    help="held-out 513^2 star problems for the learned-guess comparison (0 to skip)")
     return ap.parse_args()
 
 
@@ -449,6 +451,13 @@ def run_gcmg(args):
                              "converged": len(bad) == 0, "not_converged": bad,
                              "worst_rel": max(st["rel_residual"] for st in bst)}
             B.close()
+        if args.learned and world == 1:
+            from paper_1111_0983_gb300 import learn
+            t0 = time.perf_counter()
+            cmp = learn.compare_forms(learn.load_weights(), [learn.TEST_BASE + i for i in range(args.learned)])
+            cmp["workload"] = f"learned guess, {args.learned} held-out stars at 513^2, Gaussian f, g = 0"
+            cmp["wall_s"] = time.perf_counter() - t0
+            line["learned"] = cmp
         if world == 1 and not args.no_cpu_baseline:
             sec, nu_o, _ = oracle_cycle_sample(P, n, nc, args.gamma, args.cpu_sample_cycles)
             cyc = cycles_reference(args.config, args.precision) or statistics.median(cycles)

@@ -35,7 +35,7 @@ typedef struct gcmg_cnn gcmg_cnn;
 int64_t gcmg_cnn_num_params(void);
 
 /* A network for batches of `batch` images of H x W pixels; dilations[6]
- * (each in [1, 16]; NULL: 1, 2, 4, 8, 16, 1).  Parameters start at zero. */
+ * (each in [1, 96]; NULL: 1, 3, 9, 27, 81, 1).  Parameters start at zero. */
 gcmg_status gcmg_cnn_create(int batch, int H, int W, const int *dilations, void *stream, gcmg_cnn **out);
 void gcmg_cnn_destroy(gcmg_cnn *net);
 const char *gcmg_cnn_last_error(const gcmg_cnn *net);
@@ -57,10 +57,17 @@ gcmg_status gcmg_cnn_activation(gcmg_cnn *net, int layer, float *dst_dev);
 gcmg_status gcmg_cnn_backward(gcmg_cnn *net, const float *dout_dev, float *grad_dev);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
- * masked squared error L = sum(mask (out - target)^2) / mask_count of the
- * batch (target, mask: [batch][2][H][W]); loss_host receives L before the step. */
+ * batch's loss (target, mask: [batch][2][H][W])
+ *   L = sum(m_0 (out_0 - target_0)^2) / mask_count
+ *     + lap_weight sum_{m_1 = 1} s^2 / lap_count,
+ * where e = (out_0 - target_0) m_0 is the error of channel 0 and
+ * s = e_N + e_S + e_E + e_W - 4 e (h^2 times its 5-point Laplacian) is taken
+ * at the pixels whose mask channel 1 is 1 (and not on the image edge): the
+ * second term weighs the error by the residual it leaves.  lap_weight = 0
+ * drops it; output channel 1 is not trained.  loss_host receives L before
+ * the step. */
 gcmg_status gcmg_cnn_train_step(gcmg_cnn *net, const float *in_dev, const float *target_dev, const float *mask_dev,
-                                float mask_count, float lr, double *loss_host);
+                                float mask_count, float lap_weight, float lap_count, float lr, double *loss_host);
 
 #ifdef __cplusplus
 }

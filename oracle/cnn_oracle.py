@@ -21,7 +21,7 @@ accumulation order and by BF16 rounding decisions that order can flip.
 import numpy as np
 
 LAYERS = [(4, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 2)]
-DILATIONS = (1, 2, 4, 8, 16, 1)
+DILATIONS = (1, 3, 9, 27, 81, 1)
 
 
 def bf16_round(x):
@@ -116,3 +116,26 @@ def masked_mse(out, target, mask):
     cnt = max(float(mask.sum()), 1.0)
     diff = (out - target) * mask
     return float((diff * diff).sum() / cnt), 2.0 * diff / cnt
+
+
+def laplacian_loss(out, target, mask, beta):
+    """Residual term of the training loss: with e = (out_0 - target_0) m_0 (the
+    error of channel 0 on the unknowns), s = e_N + e_S + e_E + e_W - 4 e (h^2
+    times the 5-point Laplacian) at the nodes where m_1 = 1 (away from the
+    image edge), L = beta sum(s^2) / sum(m_1); returns (L, dL/dout)."""
+    e = (out[:, 0] - target[:, 0]) * mask[:, 0]
+    inner = np.zeros_like(e, dtype=bool)
+    inner[:, 1:-1, 1:-1] = mask[:, 1, 1:-1, 1:-1] > 0
+    s = np.zeros_like(e)
+    s[:, 1:-1, 1:-1] = (e[:, :-2, 1:-1] + e[:, 2:, 1:-1] + e[:, 1:-1, :-2] + e[:, 1:-1, 2:]
+                        - 4.0 * e[:, 1:-1, 1:-1])
+    s = np.where(inner, s, 0.0)
+    cnt = max(float(inner.sum()), 1.0)
+    g = -4.0 * s
+    g[:, 1:, :] += s[:, :-1, :]
+    g[:, :-1, :] += s[:, 1:, :]
+    g[:, :, 1:] += s[:, :, :-1]
+    g[:, :, :-1] += s[:, :, 1:]
+    dout = np.zeros_like(out)
+    dout[:, 0] = 2.0 * beta / cnt * g * mask[:, 0]
+    return float(beta * (s * s).sum() / cnt), dout

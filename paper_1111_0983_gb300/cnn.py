@@ -7,7 +7,7 @@ import numpy as np
 from . import gcmg
 
 LAYERS = [(4, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 2)]
-DILATIONS = (1, 2, 4, 8, 16, 1)
+DILATIONS = (1, 3, 9, 27, 81, 1)
 
 _bound = False
 
@@ -27,7 +27,7 @@ def _lib():
             "gcmg_cnn_forward": (st, [vp, vp, vp]),
             "gcmg_cnn_activation": (st, [vp, i32, vp]),
             "gcmg_cnn_backward": (st, [vp, vp, vp]),
-            "gcmg_cnn_train_step": (st, [vp, vp, vp, vp, f32, f32, C.POINTER(dbl)]),
+            "gcmg_cnn_train_step": (st, [vp, vp, vp, vp, f32, f32, f32, f32, C.POINTER(dbl)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -105,8 +105,9 @@ class Net:
     def backward(self, dout, grad):
         self._check(_lib().gcmg_cnn_backward(self._h, gcmg._ptr(dout), gcmg._ptr(grad)))
 
-    def train_step(self, inp, target, mask, mask_count, lr):
+    def train_step(self, inp, target, mask, mask_count, lr, lap_weight=0.0, lap_count=0.0):
         loss = C.c_double()
         self._check(_lib().gcmg_cnn_train_step(self._h, gcmg._ptr(inp), gcmg._ptr(target), gcmg._ptr(mask),
-                                               float(mask_count), float(lr), C.byref(loss)))
+                                               float(mask_count), float(lap_weight), float(lap_count), float(lr),
+                                               C.byref(loss)))
         return loss.value

@@ -38,7 +38,7 @@ constexpr int kLayers = 6;
 constexpr int kCin[kLayers] = {4, 32, 32, 32, 32, 32};
 constexpr int kCout[kLayers] = {32, 32, 32, 32, 32, 2};
 constexpr int kTile = 128;            // pixels per CTA (M)
-constexpr int kMaxDil = 16;
+constexpr int kMaxDil = 96;
 constexpr int kSeg = kTile + 2 * kMaxDil;   // staged pixels per row segment
 constexpr long kWaitLimit = 1L << 24; // bounded mbarrier polls
 
@@ -395,12 +395,14 @@ __global__ void k_pack_dout(const float *__restrict__ d, uint4 *__restrict__ x, 
     x[(size_t)geo.npix + q] = make_uint4(0, 0, 0, 0);
 }
 
-// masked squared error: dout = 2 (out - t) m / count, loss += sum (out - t)^2 m / count
+// masked squared error of channel 0 ([B][2][plane] arrays): dout_0 = 2 (out_0 -
+// t_0) m_0 / count, dout_1 = 0, loss += sum (out_0 - t_0)^2 m_0 / count
 __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t, const float *__restrict__ m,
-                      float *__restrict__ dout, size_t n, float inv_count, double *loss) {
+                      float *__restrict__ dout, size_t n, size_t plane, float inv_count, double *loss) {
     double s = 0.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const float df = (out[e] - t[e]) * m[e];
+        const bool ch0 = (e / plane) % 2 == 0;
+        const float df = ch0 ? (out[e] - t[e]) * m[e] : 0.0f;
         dout[e] = 2.0f * df * inv_count;
         s += (double)df * df;
     }
@@ -412,6 +414,54 @@ __global__ void k_mse(const float *__restrict__ out, const float *__restrict__ t
         double tot = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += part[w];
         atomicAdd(loss, tot * inv_count);
+    }
+}
+
+// Residual term of the loss, two passes over [B][H][W]: e = (out_0 - t_0) m_0,
+// s = e_N + e_S + e_E + e_W - 4 e where m_1 = 1 (inside the image edge), else
+// 0; loss += beta sum s^2 / count; then dout_0 += 2 beta / count *
+// (-4 s + s_N + s_S + s_E + s_W) m_0.
+__global__ void k_lap_s(const float *__restrict__ out, const float *__restrict__ t, const float *__restrict__ m,
+                        float *__restrict__ s, int B, int H, int W, float scale, double *loss) {
+    const size_t plane = (size_t)H * W;
+    double acc = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)B * plane;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = e / plane, p = e - b * plane;
+        const int i = (int)(p / W), j = (int)(p - (size_t)i * W);
+        const float *o0 = out + b * 2 * plane, *t0 = t + b * 2 * plane, *m0 = m + b * 2 * plane;
+        float v = 0.0f;
+        if (i > 0 && i < H - 1 && j > 0 && j < W - 1 && m0[plane + p] > 0.0f) {
+            auto err = [&](size_t q) { return (o0[q] - t0[q]) * m0[q]; };
+            v = err(p - W) + err(p + W) + err(p - 1) + err(p + 1) - 4.0f * err(p);
+        }
+        s[e] = v;
+        acc += (double)v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += part[w];
+        atomicAdd(loss, tot * scale);
+    }
+}
+
+__global__ void k_lap_grad(const float *__restrict__ s, const float *__restrict__ m, float *__restrict__ dout, int B,
+                           int H, int W, float scale2) {
+    const size_t plane = (size_t)H * W;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)B * plane;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = e / plane, p = e - b * plane;
+        const int i = (int)(p / W), j = (int)(p - (size_t)i * W);
+        float g = -4.0f * s[e];
+        if (i > 0) g += s[e - W];
+        if (i < H - 1) g += s[e + W];
+        if (j > 0) g += s[e - 1];
+        if (j < W - 1) g += s[e + 1];
+        dout[b * 2 * plane + p] += scale2 * g * m[b * 2 * plane + p];
     }
 }
 
@@ -474,7 +524,7 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 // ------------------------------------------------------------------ context
 struct gcmg_cnn {
     int batch = 0, H = 0, W = 0, P = 0;
-    int dil[kLayers] = {1, 2, 4, 8, 16, 1};
+    int dil[kLayers] = {1, 3, 9, 27, 81, 1};
     Geo geo{};
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -484,7 +534,7 @@ struct gcmg_cnn {
     uint16_t *wf[kLayers] = {}, *wb[kLayers] = {};
     uint4 *act[kLayers] = {};    // act[0] = packed input, act[l] = output of layer l (l = 1..5)
     uint4 *dz[2] = {};           // ping-pong gradients
-    float *out = nullptr, *dout = nullptr;
+    float *out = nullptr, *dout = nullptr, *lap_s = nullptr;
     double *d_loss = nullptr;
     int *d_err = nullptr;
     int adam_t = 0;
@@ -643,7 +693,7 @@ gcmg_status gcmg_cnn_create(int batch, int H, int W, const int *dilations, void 
     if (dilations)
         for (int l = 0; l < kLayers; l++) {
             if (dilations[l] < 1 || dilations[l] > kMaxDil) {
-                c->err = "dilations must lie in [1, 16]";
+                c->err = "dilations must lie in [1, 96]";
                 return GCMG_E_ARG;
             }
             c->dil[l] = dilations[l];
@@ -689,6 +739,7 @@ gcmg_status gcmg_cnn_create(int batch, int H, int W, const int *dilations, void 
         c->dz[1] = alloc<uint4>(c, 4 * np);
         c->out = alloc<float>(c, (size_t)batch * 2 * H * W);
         c->dout = alloc<float>(c, (size_t)batch * 2 * H * W);
+        c->lap_s = alloc<float>(c, (size_t)batch * H * W);
         c->d_loss = alloc<double>(c, 1);
         c->d_err = alloc<int>(c, 1);
         ck(cudaMemset(c->d_err, 0, sizeof(int)), "memset");
@@ -790,13 +841,22 @@ gcmg_status gcmg_cnn_backward(gcmg_cnn *c, const float *dout_dev, float *grad_de
 }
 
 gcmg_status gcmg_cnn_train_step(gcmg_cnn *c, const float *in_dev, const float *target_dev, const float *mask_dev,
-                                float mask_count, float lr, double *loss_host) {
-    if (!c || !in_dev || !target_dev || !mask_dev || !(mask_count > 0.0f)) return GCMG_E_ARG;
+                                float mask_count, float lap_weight, float lap_count, float lr, double *loss_host) {
+    if (!c || !in_dev || !target_dev || !mask_dev || !(mask_count > 0.0f) || lap_weight < 0.0f ||
+        (lap_weight > 0.0f && !(lap_count > 0.0f)))
+        return GCMG_E_ARG;
     CNN_GUARD(c, {
         forward(c, in_dev, c->out);
         ck(cudaMemsetAsync(c->d_loss, 0, sizeof(double), c->stream), "memset");
         const size_t n = (size_t)c->batch * 2 * c->H * c->W;
-        k_mse<<<256, 256, 0, c->stream>>>(c->out, target_dev, mask_dev, c->dout, n, 1.0f / mask_count, c->d_loss);
+        k_mse<<<256, 256, 0, c->stream>>>(c->out, target_dev, mask_dev, c->dout, n, (size_t)c->H * c->W,
+                                          1.0f / mask_count, c->d_loss);
+        if (lap_weight > 0.0f) {
+            k_lap_s<<<256, 256, 0, c->stream>>>(c->out, target_dev, mask_dev, c->lap_s, c->batch, c->H, c->W,
+                                                lap_weight / lap_count, c->d_loss);
+            k_lap_grad<<<256, 256, 0, c->stream>>>(c->lap_s, mask_dev, c->dout, c->batch, c->H, c->W,
+                                                   2.0f * lap_weight / lap_count);
+        }
         backward(c, c->dout);
         c->adam_t++;
         const float b1 = 0.9f, b2 = 0.999f;

@@ -10,7 +10,12 @@ FP64 refinement, relative residual 1e-10).
 Network input (4 channels): phi, f / F_SCALE on Omega_h (0 elsewhere), g at
 the ghosts (0 here), and the boundary-type mask (+1 Dirichlet ghost, -1
 Neumann ghost, 0 elsewhere).  Output channel 0 is u / U_SCALE, trained with
-the squared error over Omega_h u Gamma_h; channel 1 is not trained.
+the squared error over Omega_h u Gamma_h plus LAP_WEIGHT times the squared
+h^2-scaled residual of that error on Omega_h; channel 1 is not trained.
+
+The solve keeps the network's guess only if its FP64 defect is smaller than
+that of u = 0 (guessed_start): the V-cycle remains the fallback and the
+judge of the guess, so the converged result never depends on the network.
 
     python -m paper_1111_0983_gb300.learn --train 4096 --steps 6000 --out weights.npz
 """
@@ -27,6 +32,7 @@ N_GRID = 513
 N_COARSE = 33
 F_SCALE = 10.0
 U_SCALE = 1.0
+LAP_WEIGHT = 1e6
 TEST_BASE = 10 ** 6
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "weights", "guess513.npz")
@@ -41,7 +47,8 @@ def problem(i, n=N_GRID):
 
 
 def network_input(S, P, f, n=N_GRID):
-    """[4][n][n] FP32 input of a domain whose solver S has its bc types set."""
+    """[4][n][n] FP32 input of a domain whose solver S has its bc types set,
+    and its masks: unknowns (Omega_h u Gamma_h) and inside nodes (Omega_h)."""
     T = S.node_types(0) & 3
     G = S.ghosts(0)
     bc = P.bc_types(G["B"])
@@ -51,7 +58,7 @@ def network_input(S, P, f, n=N_GRID):
     mask = np.zeros(n * n, np.float32)
     mask[G["node"]] = np.where(bc, -1.0, 1.0)
     x[3] = mask.reshape(n, n)
-    return x, (T > 0)
+    return x, np.stack([T > 0, T == 1])
 
 
 def solve_chunk(ids, stream=None, n=N_GRID, rtol=1e-10):
@@ -81,15 +88,16 @@ def solve_chunk(ids, stream=None, n=N_GRID, rtol=1e-10):
     return np.stack(xs), torch.stack(us), np.stack(ms), ok
 
 
-def make_dataset(ids, chunk=128, stream=None, log=print):
-    """Device tensors X [N][4][n][n], U [N][n][n], M [N][n][n] (FP32) of the
-    domains whose solve converged, and the number left out."""
+def make_dataset(ids, chunk=128, stream=None, log=print, n=N_GRID):
+    """Device tensors X [N][4][n][n], U [N][n][n], M [N][2][n][n] (FP32: the
+    unknowns, the inside nodes) of the domains whose solve converged, and the
+    number left out."""
     import torch
     X, U, M = [], [], []
     t0 = time.perf_counter()
     bad = 0
     for s in range(0, len(ids), chunk):
-        x, u, m, ok = solve_chunk(ids[s:s + chunk], stream)
+        x, u, m, ok = solve_chunk(ids[s:s + chunk], stream, n)
         keep = [k for k, o in enumerate(ok) if o]   # a target must be a converged solution
         bad += len(ok) - len(keep)
         X.append(torch.from_numpy(x[keep]).cuda())
@@ -99,8 +107,10 @@ def make_dataset(ids, chunk=128, stream=None, log=print):
     return torch.cat(X), torch.cat(U), torch.cat(M), bad
 
 
-def train(X, U, M, steps, batch=8, lr=1e-3, seed=0, log=print, params=None):
-    """Adam on the GPU kernels; returns (parameter vector, loss history)."""
+def train(X, U, M, steps, batch=8, lr=1e-3, seed=0, log=print, params=None, lap_weight=LAP_WEIGHT):
+    """Adam on the GPU kernels; returns (parameter vector, loss history).  The
+    loss is the squared error of u on the unknowns plus lap_weight times the
+    squared h^2-scaled residual of that error on the inside nodes."""
     import torch
     n = X.shape[-1]
     net = cnn.Net(batch, n, n)
@@ -120,10 +130,11 @@ def train(X, U, M, steps, batch=8, lr=1e-3, seed=0, log=print, params=None):
         idx = torch.from_numpy(rng.integers(0, X.shape[0], batch)).cuda()
         xb = X.index_select(0, idx).contiguous()
         tgt[:, 0] = U.index_select(0, idx) / U_SCALE
-        msk[:, 0] = M.index_select(0, idx)
+        msk.copy_(M.index_select(0, idx))
         # cosine decay of the learning rate
         lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * it / steps))
-        loss = net.train_step(xb, tgt, msk, float(msk.sum().item()), lr_t)
+        loss = net.train_step(xb, tgt, msk, float(msk[:, 0].sum().item()), lr_t, lap_weight,
+                              float(msk[:, 1].sum().item()))
         hist.append(loss)
         if it % 500 == 0 or it == steps - 1:
             log(f"step {it} loss {loss:.3e} lr {lr_t:.2e} {time.perf_counter() - t0:.1f}s")
@@ -132,33 +143,51 @@ def train(X, U, M, steps, batch=8, lr=1e-3, seed=0, log=print, params=None):
     return p, hist
 
 
-def evaluate(params, ids, rtol=1e-10, precision=1, log=print):
+def guessed_start(S, net, xd, md, out, fd, g0, r):
+    """Initial u from the network, kept only if its FP64 defect is below the
+    defect of u = 0: the V-cycle that follows is the judge of the guess.
+    Returns (u, kept, relative defect of the guess)."""
+    import torch
+    net.forward(xd, out)
+    u = torch.where(md, out[0, 0].double() * U_SCALE, torch.zeros_like(r))
+    rg = S.defect(0, u, fd, g0, r)
+    r0 = S.defect(0, torch.zeros_like(u), fd, g0, r)
+    if not rg < r0:
+        u.zero_()
+    return u, bool(rg < r0), rg / r0
+
+
+def evaluate(params, ids, rtol=1e-10, precision=1, log=print, n=N_GRID):
     """Per test domain: cycles and device time to rtol from u = 0 and from the
     network's guess (guess time included), and the guess's relative error."""
     import torch
-    n = N_GRID
     net = cnn.Net(1, n, n)
     net.set_params(params)
     out = torch.zeros((1, 2, n, n), dtype=torch.float32, device="cuda")
     rows = []
     for i in ids:
-        P, f = problem(i)
+        P, f = problem(i, n)
         S = gcmg.Solver(P.phi_grid(n), N_COARSE, precision=precision, rtol=rtol, max_cycles=100)
         for l in range(S.nlev):
             S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
         S.set_rhs(torch.from_numpy(f).cuda(), torch.zeros(S.num_ghosts(0), dtype=torch.float64, device="cuda"))
-        x, m = network_input(S, P, f)
+        x, masks = network_input(S, P, f, n)
+        m = masks[0]
         xd = torch.from_numpy(x[None]).cuda()
         md = torch.from_numpy(m).cuda()
+        fd = torch.from_numpy(f).cuda()
+        g0 = torch.zeros(S.num_ghosts(0), dtype=torch.float64, device="cuda")
+        r = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        rg = float("nan")
         res = {}
         for name in ("zero", "zero", "guess", "guess"):   # second of each pair is timed warm
             u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
+            kept = False
             if name == "guess":
-                net.forward(xd, out)
-                u.copy_(torch.where(md, out[0, 0].double() * U_SCALE, torch.zeros_like(u)))
+                u, kept, rg = guessed_start(S, net, xd, md, out, fd, g0, r)
             st = S.solve(u)
             b.record()
             torch.cuda.synchronize()
@@ -169,7 +198,8 @@ def evaluate(params, ids, rtol=1e-10, precision=1, log=print):
         rows.append(dict(id=int(i), cycles_zero=res["zero"][0], cycles_guess=res["guess"][0],
                          ms_zero=res["zero"][1], ms_guess=res["guess"][1],
                          converged=bool(res["zero"][2] and res["guess"][2]), guess_rel_err=err,
-                         unknowns=int(m.sum())))
+                         guess_rel_residual=float(rg), guess_kept=kept, unknowns=int(m.sum()),
+                         solution_rel_diff=float((res["guess"][3] - u_star).abs().max() / u_star.abs().max())))
         S.close()
     net.close()
     return rows
@@ -186,11 +216,38 @@ def summary(rows):
                 unknowns_per_s_zero=float(unk.sum() / (tz.sum() / 1e3)),
                 unknowns_per_s_guess=float(unk.sum() / (tg.sum() / 1e3)),
                 guess_rel_err_median=float(np.median([r["guess_rel_err"] for r in rows])),
+                guess_rel_residual_median=float(np.median([r["guess_rel_residual"] for r in rows])),
+                guesses_kept=int(sum(r["guess_kept"] for r in rows)),
+                solution_rel_diff_max=float(max(r["solution_rel_diff"] for r in rows)),
                 all_converged=bool(all(r["converged"] for r in rows)))
+
+
+def compare_forms(params, ids, rtol=1e-10, n=N_GRID):
+    """Device time and cycles to rtol on domains `ids` for the three forms:
+    plain FP64 V-cycles from u = 0, FP32 V-cycles inside FP64 refinement from
+    u = 0, and the same started from the learned guess (inference and its
+    defect check included)."""
+    f64 = evaluate(params, ids, rtol, precision=0, n=n)
+    mix = evaluate(params, ids, rtol, precision=1, n=n)
+    unk = sum(r["unknowns"] for r in mix)
+
+    def form(rows, key):
+        ms = sum(r["ms_" + key] for r in rows)
+        return dict(ms_per_solve=ms / len(rows), unknowns_per_s=unk / (ms / 1e3),
+                    cycles_mean=float(np.mean([r["cycles_" + key] for r in rows])))
+    return dict(domains=len(ids), grid=n, unknowns=unk, rtol=rtol,
+                f64=form(f64, "zero"), mixed=form(mix, "zero"), mixed_learned=form(mix, "guess"),
+                guesses_kept=int(sum(r["guess_kept"] for r in mix)),
+                guess_rel_err_median=float(np.median([r["guess_rel_err"] for r in mix])),
+                guess_rel_residual_median=float(np.median([r["guess_rel_residual"] for r in mix])),
+                all_converged=bool(all(r["converged"] for r in f64 + mix)))
 
 
 def load_weights(path=WEIGHTS):
     return np.load(path)["params"].astype(np.float32)
+
+
+VAL_BASE = 2 * 10 ** 6
 
 
 def main():
@@ -199,18 +256,29 @@ def main():
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lap-weights", default="0,1e3,1e4",
+                    help="residual-term weights to train; the one whose guesses save most time on the "
+                         "validation seeds is kept")
+    ap.add_argument("--val", type=int, default=16)
     ap.add_argument("--test", type=int, default=64)
     ap.add_argument("--out", default=WEIGHTS)
     args = ap.parse_args()
     X, U, M, bad = make_dataset(list(range(args.train)))
-    params, hist = train(X, U, M, args.steps, args.batch, args.lr)
+    best = None
+    for beta in [float(b) for b in args.lap_weights.split(",")]:
+        params, hist = train(X, U, M, args.steps, args.batch, args.lr, lap_weight=beta)
+        sm = summary(evaluate(params, [VAL_BASE + i for i in range(args.val)]))
+        print(json.dumps(dict(lap_weight=beta, final_loss=float(np.mean(hist[-50:])), **sm)), flush=True)
+        if best is None or sm["ms_guess_mean"] < best[0]:
+            best = (sm["ms_guess_mean"], beta, params, hist)
+    _, beta, params, hist = best
     del X, U, M
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.savez(args.out, params=params, loss=np.array(hist, np.float32), train=args.train, steps=args.steps,
-             batch=args.batch, lr=args.lr, unconverged_targets=bad)
+             batch=args.batch, lr=args.lr, lap_weight=beta, unconverged_targets=bad)
     rows = evaluate(params, [TEST_BASE + i for i in range(args.test)])
-    print(json.dumps(dict(summary(rows), train=args.train, steps=args.steps, final_loss=hist[-1],
-                          unconverged_targets=bad)), flush=True)
+    print(json.dumps(dict(summary(rows), train=args.train, steps=args.steps, lap_weight=beta,
+                          final_loss=float(np.mean(hist[-50:])), unconverged_targets=bad)), flush=True)
 
 
 if __name__ == "__main__":

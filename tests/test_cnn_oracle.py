@@ -86,3 +86,31 @@ def test_bf16_mode_is_close_to_exact():
     assert np.abs(bf - ex).max() < 0.05 * np.abs(ex).max()
     for a in acts:    # every stored activation is a BF16 value
         assert np.array_equal(a, cnn.bf16_round(a))
+
+
+def test_laplacian_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(9)
+    out = rng.standard_normal((2, 2, 9, 8))
+    t = rng.standard_normal((2, 2, 9, 8))
+    m = np.zeros((2, 2, 9, 8))
+    m[:, 0] = rng.uniform(size=(2, 9, 8)) < 0.8
+    m[:, 1] = (rng.uniform(size=(2, 9, 8)) < 0.6) * m[:, 0]
+    L, g = cnn.laplacian_loss(out, t, m, 3.0)
+    # closed form: a unit error at one node, the term taken at that node
+    # only: s = -4 there, L = 16
+    e = np.zeros_like(out)
+    e[0, 0, 4, 4] = 1.0
+    mm = np.zeros_like(m)
+    mm[0, 0] = 1.0
+    mm[0, 1, 4, 4] = 1.0
+    assert abs(cnn.laplacian_loss(e, 0 * e, mm, 1.0)[0] - 16.0) < 1e-12
+    eps = 1e-6
+    for _ in range(20):
+        idx = tuple(rng.integers(0, s) for s in out.shape)
+        o0 = out[idx]
+        out[idx] = o0 + eps
+        lp = cnn.laplacian_loss(out, t, m, 3.0)[0]
+        out[idx] = o0 - eps
+        lm = cnn.laplacian_loss(out, t, m, 3.0)[0]
+        out[idx] = o0
+        assert abs((lp - lm) / (2 * eps) - g[idx]) <= 1e-6 * max(1.0, abs(g[idx]))

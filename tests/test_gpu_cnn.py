@@ -110,3 +110,13 @@ def test_train_step_reduces_a_fitting_loss():
     losses = [net.train_step(x, td, md, float(m.sum()), 3e-3) for _ in range(60)]
     assert abs(losses[0] - l_ref) <= 1e-5 * l_ref
     assert losses[-1] < 0.2 * losses[0], losses[::10]
+    # with the residual term (mask channel 1: the pixels where it is taken)
+    m2 = m.copy()
+    m2[:, 1] = (np.random.default_rng(2).uniform(size=(B, H, W)) < 0.5).astype(np.float32)
+    net.forward(x, out)
+    o = out.cpu().numpy().astype(np.float64)
+    l_lap, _ = co.laplacian_loss(o, t, m2, 50.0)
+    inner = float((m2[:, 1, 1:-1, 1:-1] > 0).sum())
+    l_ref = co.masked_mse(o, t, m)[0] + l_lap
+    got = net.train_step(x, td, torch.from_numpy(m2).cuda(), float(m.sum()), 1e-4, 50.0, inner)
+    assert abs(got - l_ref) <= 1e-4 * l_ref
