@@ -273,17 +273,12 @@ void cycle(gcmg_ctx *c, int l) {
         return;
     }
     for (int k = 0; k < c->p.nu1; k++) relax<T>(c, v, l, true);
-    timer_mark(c, GCMG_KERNEL_DEFECT, l);
-    launch_defect<T>(v, dim, false, nullptr, c->stream);
-    timer_mark(c, GCMG_KERNEL_DEFECT, l);
     const LevelView<T> vc = view<T>(c, l + 1, D[l + 1]);
+    // defect (TGCS step 3), composite restriction (step 4) with the defect
+    // extension at the coarse ghosts (Sec. 2.6), and e_2h = 0: one launch
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
-    launch_restrict_interior<T>(v, vc, dim, D[l + 1].f, c->stream);
-    // defect extension (Sec. 2.6) and the transfer at the coarse ghosts, composed
-    launch_ghost_transfer<T>(D[l].r, c->G[l].gnode, c->G[l].gt_ptr, c->G[l].gt_col, D[l].gt_val, D[l + 1].gg,
-                             c->G[l + 1].ng, c->stream);
+    launch_descend<T>(v, vc, c->G[l], D[l].gt_val, D[l + 1].f, D[l + 1].gg, D[l + 1].u, c->stream);
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
-    ck(cudaMemsetAsync(D[l + 1].u, 0, c->H[l + 1].nn * sizeof(T), c->stream), "memset");
     const int gam = (l + 1 == last) ? 1 : c->p.gamma;
     for (int k = 0; k < gam; k++) cycle<T>(c, l + 1);
     timer_mark(c, GCMG_KERNEL_PROLONG, l);

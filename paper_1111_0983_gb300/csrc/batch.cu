@@ -109,36 +109,14 @@ __global__ void __launch_bounds__(kJsRows * 32) kb_js_apply(const BView32 *__res
         js_apply_row<float>(w.v.u, w.js_node, w.js_comp, w.js_off, w.js_aoff, w.js_inv, w.js_r, k, threadIdx.x & 31);
 }
 
-__global__ void kb_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
-    const BItem b = it[blockIdx.x];
-    if (!V[b.view].active[V[b.view].dom]) return;
-    const LevelView<float> &v = V[b.view].v;
-    const int64_t p = (int64_t)b.start + threadIdx.x;
-    if (p < v.nn) defect_node<float, 2>(v, p, false);
-}
-
-__global__ void kb_defect_ghost(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
-    const BItem b = it[blockIdx.x];
-    if (!V[b.view].active[V[b.view].dom]) return;
-    const LevelView<float> &v = V[b.view].v;
-    const int q = b.start + threadIdx.x;
-    if (q < v.ng) defect_ghost_item<float, 9>(v, q);
-}
-
-__global__ void kb_restrict(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+// defect, restriction with the coarse-ghost transfer, and zero coarse u in
+// one pass over the coarser level's nodes and ghosts
+__global__ void kb_descend(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
-    const int64_t X = (int64_t)b.start + threadIdx.x;
-    if (X < w.c.nn) restrict_node<float, 2>(w.v, w.c, X, w.cf);
-}
-
-__global__ void kb_transfer(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
-    const BItem b = it[blockIdx.x];
-    if (!V[b.view].active[V[b.view].dom]) return;
-    const BView32 &w = V[b.view];
-    const int q = b.start + threadIdx.x;
-    if (q < w.c.ng) ghost_transfer_row<float>(w.v.r, w.v.gnode, w.gt_ptr, w.gt_col, w.gt_val, w.cg, q);
+    descend_item<float, 2>(w.v, w.c, w.cf, w.cg, w.c.u, w.gt_ptr, w.gt_col, w.gt_val,
+                           (int64_t)b.start + threadIdx.x);
 }
 
 // zero u of the view's level (coarse = 0) or of its coarser level (coarse = 1)
@@ -258,8 +236,7 @@ inline void ck(cudaError_t e, const char *what) {
 
 // a captured launch: kernel kind, item range and parameters
 struct Launch {
-    enum Kind { FUSED, BOUNDARY, JUNCTION, JS_DEFECT, JS_APPLY, DEFECT, DEFECT_GHOST, RESTRICT, TRANSFER,
-                ZERO_COARSE, PROLONG, COARSE, ZERO };
+    enum Kind { FUSED, BOUNDARY, JUNCTION, JS_DEFECT, JS_APPLY, DESCEND, PROLONG, COARSE, ZERO };
     Kind kind;
     size_t off, count;
     size_t smem;
@@ -463,28 +440,9 @@ void build_tables(gcmg_batch *b) {
         size_t s0 = items.size();
         for (int d = 0; d < nd; d++) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
-            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].nn);
+            if (l >= 0) dense(b->view_of[d][l], std::max<int64_t>(b->doms[d]->H[l + 1].nn, b->doms[d]->H[l + 1].ng()));
         }
-        add_launch(Launch::DEFECT, s0, 0);
-        s0 = items.size();
-        for (int d = 0; d < nd; d++) {
-            const int l = (int)b->doms[d]->H.size() - 1 - k;
-            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].ng());
-        }
-        add_launch(Launch::DEFECT_GHOST, s0, 0);
-        s0 = items.size();
-        for (int d = 0; d < nd; d++) {
-            const int l = (int)b->doms[d]->H.size() - 1 - k;
-            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l + 1].nn);
-        }
-        add_launch(Launch::RESTRICT, s0, 0);
-        add_launch(Launch::ZERO_COARSE, s0, 0);   // same items: the coarser grid's nodes
-        s0 = items.size();
-        for (int d = 0; d < nd; d++) {
-            const int l = (int)b->doms[d]->H.size() - 1 - k;
-            if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l + 1].ng());
-        }
-        add_launch(Launch::TRANSFER, s0, 0);
+        add_launch(Launch::DESCEND, s0, 0);
     }
     {
         size_t s0 = items.size();
@@ -543,11 +501,7 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
         case Launch::JUNCTION: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps); break;
         case Launch::JS_DEFECT: kb_js_defect<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
         case Launch::JS_APPLY: kb_js_apply<<<n, kJsRows * 32, 0, s>>>(b->d_v32, it); break;
-        case Launch::DEFECT: kb_defect<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
-        case Launch::DEFECT_GHOST: kb_defect_ghost<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
-        case Launch::RESTRICT: kb_restrict<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
-        case Launch::ZERO_COARSE: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 1); break;
-        case Launch::TRANSFER: kb_transfer<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::DESCEND: kb_descend<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
         case Launch::ZERO: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 0); break;
         case Launch::COARSE: kb_coarse<<<n, 512, L.smem, s>>>(b->d_v32, it); break;
         case Launch::PROLONG: kb_prolong<<<n, kThreads, 0, s>>>(b->d_v32, it); break;

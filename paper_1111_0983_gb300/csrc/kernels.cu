@@ -152,6 +152,14 @@ __global__ void k_restrict_interior(LevelView<T> F, LevelView<T> C, T *__restric
     if (X < C.nn) restrict_node<T, D>(F, C, X, fc);
 }
 
+template <typename T, int D, bool FROM_R>
+__global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T *__restrict__ gc,
+                          T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                          const T *__restrict__ val) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    descend_item<T, D, FROM_R>(F, C, fc, gc, uc, ptr, col, val, i);
+}
+
 template <typename T, int D>
 __global__ void k_restrict_ghost(LevelView<T> F, LevelView<T> C, T *__restrict__ gc) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,6 +305,19 @@ void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *f
 }
 
 template <typename T>
+void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
+                    T *uc, cudaStream_t s) {
+    const int64_t n = std::max<int64_t>(C.nn, C.ng);
+    constexpr bool from_r = sizeof(T) == 8;   // FP64: one defect pass first (see descend_item)
+    if (from_r) launch_defect<T>(F, gf.dim, false, nullptr, s);
+    g_launches++;
+    if (gf.dim == 2)
+        k_descend<T, 2, from_r><<<blocks_for(n), kThreads, 0, s>>>(F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
+    else
+        k_descend<T, 3, from_r><<<blocks_for(n), kThreads, 0, s>>>(F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
+}
+
+template <typename T>
 void launch_ghost_transfer(const T *rf, const int32_t *fgnode, const int32_t *ptr, const int32_t *col, const T *val,
                            T *gc, int ngc, cudaStream_t s) {
     if (ngc <= 0) return;
@@ -408,6 +429,8 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
                                     cudaStream_t);                                                       \
     template void launch_coarse_solve<T>(const LevelView<T> &, const DevGeom &, const T *, cudaStream_t); \
     template void launch_junction_solve<T>(const LevelView<T> &, const DevGeom &, const T *, T *, cudaStream_t); \
+    template void launch_descend<T>(const LevelView<T> &, const LevelView<T> &, const DevGeom &, const T *, T *, T *, \
+                                    T *, cudaStream_t);                                                            \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
     template size_t local_smem_bytes<T>(const LocalView<T> &, int);                                 \
     template void launch_local<T>(const LocalView<T> &, int, int, int, cudaStream_t);               \

@@ -28,6 +28,11 @@ template <typename T>
 void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, T *gc, cudaStream_t s);
 template <typename T>
 void launch_restrict_interior(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, cudaStream_t s);
+// one descent of the cycle: coarse f = restricted fine defect (computed on the
+// spot), coarse ghost data = transferred fine ghost defects, coarse u = 0
+template <typename T>
+void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
+                    T *uc, cudaStream_t s);
 template <typename T>
 void launch_ghost_transfer(const T *rf, const int32_t *fgnode, const int32_t *ptr, const int32_t *col, const T *val,
                            T *gc, int ngc, cudaStream_t s);

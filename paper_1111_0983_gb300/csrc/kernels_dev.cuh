@@ -260,8 +260,21 @@ __device__ __forceinline__ double w1d(int iv, int o) {
     }
 }
 
-template <typename T, int D>
-__device__ T partial_transfer(const LevelView<T> &F, int64_t p, bool interior) {
+template <int D>
+__device__ __forceinline__ int64_t fine_image(int64_t X, int64_t cs0, int64_t cs1, int64_t fs0, int64_t fs1) {
+    int64_t rem = X;
+    if (D == 2) {
+        const int64_t j0 = rem / cs0, j1 = rem - j0 * cs0;
+        return 2 * j0 * fs0 + 2 * j1;
+    }
+    const int64_t j0 = rem / cs0;
+    rem -= j0 * cs0;
+    const int64_t j1 = rem / cs1, j2 = rem - j1 * cs1;
+    return 2 * j0 * fs0 + 2 * j1 * fs1 + 2 * j2;
+}
+
+template <typename T, int D, typename Get>
+__device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior, Get value) {
     const int cube = D == 2 ? 9 : 27;
     const unsigned full = (1u << cube) - 1u;
     unsigned member = 0;
@@ -315,23 +328,63 @@ __device__ T partial_transfer(const LevelView<T> &F, int64_t p, bool interior) {
             }
             w /= count;
         }
-        if (w != 0.0) acc += w * (double)F.r[q];
+        if (w != 0.0) acc += w * (double)value(q);
     }
     return (T)acc;
 }
 
-template <int D>
-__device__ __forceinline__ int64_t fine_image(int64_t X, int64_t cs0, int64_t cs1, int64_t fs0, int64_t fs1) {
-    int64_t rem = X;
-    if (D == 2) {
-        const int64_t j0 = rem / cs0, j1 = rem - j0 * cs0;
-        return 2 * j0 * fs0 + 2 * j1;
-    }
-    const int64_t j0 = rem / cs0;
-    rem -= j0 * cs0;
-    const int64_t j1 = rem / cs1, j2 = rem - j1 * cs1;
-    return 2 * j0 * fs0 + 2 * j1 * fs1 + 2 * j2;
+template <typename T, int D>
+__device__ T partial_transfer(const LevelView<T> &F, int64_t p, bool interior) {
+    return partial_transfer_of<T, D>(F, p, interior, [&](int64_t q) { return F.r[q]; });
 }
+
+// the defect f + Lap_h u at inside node p (the expression of defect_node)
+template <typename T, int D>
+__device__ __forceinline__ T inside_defect(const LevelView<T> &v, int64_t p) {
+    const T up = v.u[p];
+    T lap = (v.u[p - 1] - up) + (v.u[p + 1] - up) + (v.u[p - v.s0] - up) + (v.u[p + v.s0] - up);
+    if (D == 3) lap += (v.u[p - v.s1] - up) + (v.u[p + v.s1] - up);
+    return v.f[p] + lap * v.inv_h2;
+}
+
+// the defect g - L_G u at ghost q (the expression of defect_ghost_item)
+template <typename T, int K>
+__device__ __forceinline__ T ghost_defect(const LevelView<T> &v, int q) {
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) s += v.gw[(int64_t)k * v.ng + q] * v.u[v.gstn[(int64_t)k * v.ng + q]];
+    return v.gg[q] - s;
+}
+
+// One descent of the cycle at coarse index i (TGCS steps 3-5 up to the
+// coarse solve): the restricted defect at coarse inside node i (the fine
+// defects it needs computed on the spot), the transferred defect at coarse
+// ghost i (extension + partial transfer of the fine ghost defects), and a
+// zero coarse correction.
+// FROM_R: the fine defects are read from F.r (written by a defect pass)
+// instead of being computed here: where arithmetic rather than latency is
+// the bound (FP64), each fine defect is then computed once instead of once
+// per coarse node whose 3^d neighbourhood holds it (9/4 times on average in
+// 2D).
+template <typename T, int D, bool FROM_R = false>
+__device__ __forceinline__ void descend_item(const LevelView<T> &F, const LevelView<T> &C, T *__restrict__ fc,
+                                             T *__restrict__ gc, T *__restrict__ uc, const int32_t *__restrict__ ptr,
+                                             const int32_t *__restrict__ col, const T *__restrict__ val, int64_t i) {
+    if (i < C.nn) {
+        uc[i] = 0;
+        fc[i] = (C.type[i] & NODE_KIND) == NODE_IN
+                    ? partial_transfer_of<T, D>(F, fine_image<D>(i, C.s0, C.s1, F.s0, F.s1), true,
+                                                [&](int64_t q) { return FROM_R ? F.r[q] : inside_defect<T, D>(F, q); })
+                    : (T)0;
+    }
+    if (i < C.ng) {
+        T s = 0;
+        for (int j = ptr[i]; j < ptr[i + 1]; j++)
+            s += val[j] * (FROM_R ? F.r[F.gnode[col[j]]] : ghost_defect<T, D == 2 ? 9 : 27>(F, col[j]));
+        gc[i] = s;
+    }
+}
+
 
 // coarse node X: transfer over Omega_h at coarse inside nodes, 0 elsewhere
 template <typename T, int D>

@@ -250,6 +250,32 @@ def load_weights(path=WEIGHTS):
 VAL_BASE = 2 * 10 ** 6
 
 
+def time_forward(reps, batch=8, n=N_GRID):
+    """Device time of the network's forward pass on `batch` images (seeded
+    inputs), with the tensor-core FLOPs of the six layers (padding included)."""
+    import torch
+    net = cnn.Net(batch, n, n)
+    net.set_params(load_weights())
+    x = torch.from_numpy(np.random.default_rng(0).standard_normal((batch, 4, n, n)).astype(np.float32)).cuda()
+    out = torch.zeros((batch, 2, n, n), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        net.forward(x, out)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        net.forward(x, out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    pad = 2 * max(cnn.DILATIONS)
+    pix = batch * (n + pad) ** 2
+    # MMA shapes: K = 16 (layer 1, 4 channels padded) or 32 input channels,
+    # N = 32 output channels (16 for the last layer)
+    flops = 2 * 9 * pix * (16 * 32 + 4 * 32 * 32 + 32 * 16)
+    net.close()
+    return dict(batch=batch, grid=n, ms_per_forward=ms, tensor_tflops=flops / (ms / 1e3) / 1e12)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=4096)
@@ -262,7 +288,12 @@ def main():
     ap.add_argument("--val", type=int, default=16)
     ap.add_argument("--test", type=int, default=64)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--forward-only", type=int, default=0,
+                    help="only time this many forward passes of a batch at 513^2 with the stored weights")
     args = ap.parse_args()
+    if args.forward_only:
+        print(json.dumps(time_forward(args.forward_only, args.batch)), flush=True)
+        return
     X, U, M, bad = make_dataset(list(range(args.train)))
     best = None
     for beta in [float(b) for b in args.lap_weights.split(",")]:
