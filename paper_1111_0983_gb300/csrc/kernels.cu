@@ -19,6 +19,27 @@ namespace {
 using namespace dev;
 constexpr int kThreads = 256;
 
+// Launches with programmatic stream serialization: the kernel may be set up
+// while its predecessor in the stream finishes; every kernel of this file
+// starts with pdl_wait (griddepcontrol.wait), which returns once the
+// predecessor has completed and its writes are visible.
+template <typename... P, typename... A>
+void pdl_launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+
+
 inline unsigned blocks_for(int64_t total, int threads = kThreads) {
     int64_t b = (total + threads - 1) / threads;
     return (unsigned)(b > 0 ? b : 1);
@@ -49,6 +70,7 @@ __device__ __forceinline__ bool decode_colour(int n, int color, int64_t t, int64
 // Gauss-Seidel form of Eq. (jac2d) on the inside nodes of one colour.
 template <typename T, int D>
 __global__ void k_rb_interior(LevelView<T> v, int color) {
+    pdl_wait();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t p;
     if (!decode_colour<D>(v.n, color, t, v.s0, v.s1, p)) return;
@@ -60,12 +82,14 @@ __global__ void k_rb_interior(LevelView<T> v, int color) {
 // both colours in one pass over the active 2D tiles
 template <typename T, int TR, int TC>
 __global__ void __launch_bounds__(256) k_rb_fused2d(LevelView<T> v, const int32_t *__restrict__ tiles) {
+    pdl_wait();
     rb_fused2d_body<T, TR, TC>(v, tiles[blockIdx.x]);
 }
 
 // Same update over a compact list of band nodes of one colour (Sec. 3.2).
 template <typename T, int D>
 __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
     const int64_t p = list[i];
@@ -76,6 +100,7 @@ __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int 
 // Ghost relaxation, Eqs. (dir2d)/(neu2d): new value from the current values.
 template <typename T, int K>
 __global__ void k_ghost_new(LevelView<T> v) {
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= v.ng) return;
     T s = 0;
@@ -87,6 +112,7 @@ __global__ void k_ghost_new(LevelView<T> v) {
 // same update restricted to a list of ghost numbers
 template <typename T, int K>
 __global__ void k_ghost_new_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
     const int q = list[i];
@@ -98,6 +124,7 @@ __global__ void k_ghost_new_list(LevelView<T> v, const int32_t *__restrict__ lis
 
 template <typename T>
 __global__ void k_ghost_store_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
     const int q = list[i];
@@ -106,6 +133,7 @@ __global__ void k_ghost_store_list(LevelView<T> v, const int32_t *__restrict__ l
 
 template <typename T>
 __global__ void k_ghost_store(LevelView<T> v) {
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= v.ng) return;
     v.u[v.gnode[q]] = v.gtmp[q];
@@ -114,12 +142,14 @@ __global__ void k_ghost_store(LevelView<T> v) {
 // shared-memory programs (junction zones, 2D boundary blocks), one CTA per component
 template <typename T, int D>
 __global__ void __launch_bounds__(LOCAL_THREADS) k_local(LocalView<T> J, int lead_ghost, int reps) {
+    pdl_wait();
     local_body<T, D>(J, blockIdx.x, lead_ghost, reps);
 }
 
 // ------------------------------------------------------------------ defect
 template <typename T, int D>
 __global__ void k_defect_interior(LevelView<T> v, bool zero_rest, unsigned long long *norm) {
+    pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const double val = p < v.nn ? defect_node<T, D>(v, p, zero_rest) : 0.0;
     reduce_norm(norm, val);
@@ -127,6 +157,7 @@ __global__ void k_defect_interior(LevelView<T> v, bool zero_rest, unsigned long 
 
 template <typename T, int K>
 __global__ void k_defect_ghost(LevelView<T> v, unsigned long long *norm) {
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const double val = q < v.ng ? defect_ghost_item<T, K>(v, q) : 0.0;
     reduce_norm(norm, val);
@@ -137,6 +168,7 @@ __global__ void k_defect_ghost(LevelView<T> v, unsigned long long *norm) {
 template <typename T>
 __global__ void k_extend(T *__restrict__ r, const int32_t *__restrict__ node, const uint8_t *__restrict__ cnt,
                          const int32_t *__restrict__ src, const T *__restrict__ w, int ne, int begin, int end) {
+    pdl_wait();
     const int i = begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= end) return;
     T s = 0;
@@ -148,6 +180,7 @@ __global__ void k_extend(T *__restrict__ r, const int32_t *__restrict__ node, co
 // ------------------------------------------------------------- restriction
 template <typename T, int D>
 __global__ void k_restrict_interior(LevelView<T> F, LevelView<T> C, T *__restrict__ fc) {
+    pdl_wait();
     const int64_t X = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (X < C.nn) restrict_node<T, D>(F, C, X, fc);
 }
@@ -156,12 +189,14 @@ template <typename T, int D, bool FROM_R>
 __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T *__restrict__ gc,
                           T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const T *__restrict__ val) {
+    pdl_wait();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     descend_item<T, D, FROM_R>(F, C, fc, gc, uc, ptr, col, val, i);
 }
 
 template <typename T, int D>
 __global__ void k_restrict_ghost(LevelView<T> F, LevelView<T> C, T *__restrict__ gc) {
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < C.ng) restrict_ghost_item<T, D>(F, C, q, gc);
 }
@@ -170,6 +205,7 @@ template <typename T>
 __global__ void k_ghost_transfer(const T *__restrict__ rf, const int32_t *__restrict__ fgnode,
                                  const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                  const T *__restrict__ val, T *__restrict__ gc, int ngc) {
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < ngc) ghost_transfer_row<T>(rf, fgnode, ptr, col, val, gc, q);
 }
@@ -177,6 +213,7 @@ __global__ void k_ghost_transfer(const T *__restrict__ rf, const int32_t *__rest
 // ------------------------------------------------------------ interpolation
 template <typename T, int D>
 __global__ void k_prolong(LevelView<T> F, LevelView<T> C, const T *__restrict__ e, T *__restrict__ out, bool add) {
+    pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p < F.nn) prolong_node<T, D>(F, C, e, out, add, p);
 }
@@ -185,6 +222,7 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> C, const T *__restrict__ 
 template <typename T>
 __global__ void k_coarse_solve(LevelView<T> v, const int32_t *__restrict__ unk_node,
                                const int32_t *__restrict__ unk_ghost, const T *__restrict__ Ainv, int m) {
+    pdl_wait();
     coarse_rows<T>(v, unk_node, unk_ghost, Ainv, m, blockIdx.x, gridDim.x);
 }
 
@@ -192,6 +230,7 @@ __global__ void k_coarse_solve(LevelView<T> v, const int32_t *__restrict__ unk_n
 // FP64 defect -> FP32 right-hand side of the correction problem
 __global__ void k_defect_to_f32(const uint8_t *__restrict__ type, const double *__restrict__ r64, float *__restrict__ f32,
                                 int64_t nn) {
+    pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nn) return;
     f32[p] = ((type[p] & NODE_KIND) == NODE_IN) ? (float)r64[p] : 0.0f;
@@ -199,6 +238,7 @@ __global__ void k_defect_to_f32(const uint8_t *__restrict__ type, const double *
 
 __global__ void k_ghost_defect_to_f32(const int32_t *__restrict__ gnode, const double *__restrict__ r64,
                                       float *__restrict__ g32, int ng) {
+    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < ng) g32[q] = (float)r64[gnode[q]];
 }
@@ -206,6 +246,7 @@ __global__ void k_ghost_defect_to_f32(const int32_t *__restrict__ gnode, const d
 // u64 += e32 on Omega_h u Gamma_h
 __global__ void k_add_correction(const uint8_t *__restrict__ type, double *__restrict__ u64, const float *__restrict__ e32,
                                  int64_t nn) {
+    pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nn) return;
     const uint8_t k = type[p] & NODE_KIND;
@@ -215,6 +256,7 @@ __global__ void k_add_correction(const uint8_t *__restrict__ type, double *__res
 // keep u = 0 off Omega_h u Gamma_h
 template <typename T>
 __global__ void k_mask_unknowns(const uint8_t *__restrict__ type, T *__restrict__ u, int64_t nn) {
+    pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nn) return;
     const uint8_t k = type[p] & NODE_KIND;
@@ -228,51 +270,51 @@ template <typename T>
 void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s) {
     const int hc = (v.n + 1) / 2;
     g_launches++;
-    if (dim == 2) k_rb_interior<T, 2><<<blocks_for((int64_t)v.n * hc), kThreads, 0, s>>>(v, color);
-    else k_rb_interior<T, 3><<<blocks_for((int64_t)v.n * v.n * hc), kThreads, 0, s>>>(v, color);
+    if (dim == 2) pdl_launch(k_rb_interior<T, 2>, dim3(blocks_for((int64_t)v.n * hc)), dim3(kThreads), 0, s, v, color);
+    else pdl_launch(k_rb_interior<T, 3>, dim3(blocks_for((int64_t)v.n * v.n * hc)), dim3(kThreads), 0, s, v, color);
 }
 
 template <typename T>
 void launch_rb_fused2d(const LevelView<T> &v, const int32_t *tiles, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return;
     g_launches++;
-    k_rb_fused2d<T, TILE_R, TILE_C><<<ntiles, 256, 0, s>>>(v, tiles);
+    pdl_launch(k_rb_fused2d<T, TILE_R, TILE_C>, dim3(ntiles), dim3(256), 0, s, v, tiles);
 }
 
 template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s) {
     if (cnt <= 0) return;
     g_launches++;
-    if (dim == 2) k_rb_list<T, 2><<<blocks_for(cnt), kThreads, 0, s>>>(v, list, cnt);
-    else k_rb_list<T, 3><<<blocks_for(cnt), kThreads, 0, s>>>(v, list, cnt);
+    if (dim == 2) pdl_launch(k_rb_list<T, 2>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+    else pdl_launch(k_rb_list<T, 3>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
 }
 
 template <typename T>
 void launch_ghost_relax(const LevelView<T> &v, int dim, cudaStream_t s) {
     if (v.ng <= 0) return;
     g_launches += 2;
-    if (dim == 2) k_ghost_new<T, 9><<<blocks_for(v.ng), kThreads, 0, s>>>(v);
-    else k_ghost_new<T, 27><<<blocks_for(v.ng), kThreads, 0, s>>>(v);
-    k_ghost_store<T><<<blocks_for(v.ng), kThreads, 0, s>>>(v);
+    if (dim == 2) pdl_launch(k_ghost_new<T, 9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v);
+    else pdl_launch(k_ghost_new<T, 27>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v);
+    pdl_launch(k_ghost_store<T>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v);
 }
 
 template <typename T>
 void launch_ghost_relax_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s) {
     if (cnt <= 0) return;
     g_launches += 2;
-    if (dim == 2) k_ghost_new_list<T, 9><<<blocks_for(cnt), kThreads, 0, s>>>(v, list, cnt);
-    else k_ghost_new_list<T, 27><<<blocks_for(cnt), kThreads, 0, s>>>(v, list, cnt);
-    k_ghost_store_list<T><<<blocks_for(cnt), kThreads, 0, s>>>(v, list, cnt);
+    if (dim == 2) pdl_launch(k_ghost_new_list<T, 9>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+    else pdl_launch(k_ghost_new_list<T, 27>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+    pdl_launch(k_ghost_store_list<T>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
 }
 
 template <typename T>
 void launch_defect(const LevelView<T> &v, int dim, bool zero_rest, unsigned long long *norm, cudaStream_t s) {
     g_launches += v.ng > 0 ? 2 : 1;
-    if (dim == 2) k_defect_interior<T, 2><<<blocks_for(v.nn), kThreads, 0, s>>>(v, zero_rest, norm);
-    else k_defect_interior<T, 3><<<blocks_for(v.nn), kThreads, 0, s>>>(v, zero_rest, norm);
+    if (dim == 2) pdl_launch(k_defect_interior<T, 2>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, zero_rest, norm);
+    else pdl_launch(k_defect_interior<T, 3>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, zero_rest, norm);
     if (v.ng > 0) {
-        if (dim == 2) k_defect_ghost<T, 9><<<blocks_for(v.ng), kThreads, 0, s>>>(v, norm);
-        else k_defect_ghost<T, 27><<<blocks_for(v.ng), kThreads, 0, s>>>(v, norm);
+        if (dim == 2) pdl_launch(k_defect_ghost<T, 9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm);
+        else pdl_launch(k_defect_ghost<T, 27>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm);
     }
 }
 
@@ -281,26 +323,26 @@ void launch_extend(T *r, const DevGeom &g, const T *ew, cudaStream_t s) {
     for (size_t w = 1; w < g.wave.size(); w++) {
         const int b = g.wave[w - 1], e = g.wave[w];
         if (e > b) g_launches++;
-        if (e > b) k_extend<T><<<blocks_for(e - b), kThreads, 0, s>>>(r, g.enode, g.ecnt, g.esrc, ew, g.ne, b, e);
+        if (e > b) pdl_launch(k_extend<T>, dim3(blocks_for(e - b)), dim3(kThreads), 0, s, r, g.enode, g.ecnt, g.esrc, ew, g.ne, b, e);
     }
 }
 
 template <typename T>
 void launch_restrict_interior(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, cudaStream_t s) {
     g_launches++;
-    if (dim == 2) k_restrict_interior<T, 2><<<blocks_for(C.nn), kThreads, 0, s>>>(F, C, fc);
-    else k_restrict_interior<T, 3><<<blocks_for(C.nn), kThreads, 0, s>>>(F, C, fc);
+    if (dim == 2) pdl_launch(k_restrict_interior<T, 2>, dim3(blocks_for(C.nn)), dim3(kThreads), 0, s, F, C, fc);
+    else pdl_launch(k_restrict_interior<T, 3>, dim3(blocks_for(C.nn)), dim3(kThreads), 0, s, F, C, fc);
 }
 
 template <typename T>
 void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *fc, T *gc, cudaStream_t s) {
     g_launches += C.ng > 0 ? 2 : 1;
     if (dim == 2) {
-        k_restrict_interior<T, 2><<<blocks_for(C.nn), kThreads, 0, s>>>(F, C, fc);
-        if (C.ng > 0) k_restrict_ghost<T, 2><<<blocks_for(C.ng), kThreads, 0, s>>>(F, C, gc);
+        pdl_launch(k_restrict_interior<T, 2>, dim3(blocks_for(C.nn)), dim3(kThreads), 0, s, F, C, fc);
+        if (C.ng > 0) pdl_launch(k_restrict_ghost<T, 2>, dim3(blocks_for(C.ng)), dim3(kThreads), 0, s, F, C, gc);
     } else {
-        k_restrict_interior<T, 3><<<blocks_for(C.nn), kThreads, 0, s>>>(F, C, fc);
-        if (C.ng > 0) k_restrict_ghost<T, 3><<<blocks_for(C.ng), kThreads, 0, s>>>(F, C, gc);
+        pdl_launch(k_restrict_interior<T, 3>, dim3(blocks_for(C.nn)), dim3(kThreads), 0, s, F, C, fc);
+        if (C.ng > 0) pdl_launch(k_restrict_ghost<T, 3>, dim3(blocks_for(C.ng)), dim3(kThreads), 0, s, F, C, gc);
     }
 }
 
@@ -312,9 +354,9 @@ void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom 
     if (from_r) launch_defect<T>(F, gf.dim, false, nullptr, s);
     g_launches++;
     if (gf.dim == 2)
-        k_descend<T, 2, from_r><<<blocks_for(n), kThreads, 0, s>>>(F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
+        pdl_launch(k_descend<T, 2, from_r>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
     else
-        k_descend<T, 3, from_r><<<blocks_for(n), kThreads, 0, s>>>(F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
+        pdl_launch(k_descend<T, 3, from_r>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
 }
 
 template <typename T>
@@ -322,15 +364,15 @@ void launch_ghost_transfer(const T *rf, const int32_t *fgnode, const int32_t *pt
                            T *gc, int ngc, cudaStream_t s) {
     if (ngc <= 0) return;
     g_launches++;
-    k_ghost_transfer<T><<<blocks_for(ngc), kThreads, 0, s>>>(rf, fgnode, ptr, col, val, gc, ngc);
+    pdl_launch(k_ghost_transfer<T>, dim3(blocks_for(ngc)), dim3(kThreads), 0, s, rf, fgnode, ptr, col, val, gc, ngc);
 }
 
 template <typename T>
 void launch_prolong(const LevelView<T> &F, const LevelView<T> &C, int dim, const T *e, T *out, bool add,
                     cudaStream_t s) {
     g_launches++;
-    if (dim == 2) k_prolong<T, 2><<<blocks_for(F.nn), kThreads, 0, s>>>(F, C, e, out, add);
-    else k_prolong<T, 3><<<blocks_for(F.nn), kThreads, 0, s>>>(F, C, e, out, add);
+    if (dim == 2) pdl_launch(k_prolong<T, 2>, dim3(blocks_for(F.nn)), dim3(kThreads), 0, s, F, C, e, out, add);
+    else pdl_launch(k_prolong<T, 3>, dim3(blocks_for(F.nn)), dim3(kThreads), 0, s, F, C, e, out, add);
 }
 
 template <typename T>
@@ -340,12 +382,13 @@ void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv,
     g_launches++;
     const int threads = 512;
     const unsigned blocks = (unsigned)std::min(1024, (m + 15) / 16);
-    k_coarse_solve<T><<<blocks, threads, (size_t)m * sizeof(T), s>>>(v, g.unk_node, g.unk_ghost, Ainv, m);
+    pdl_launch(k_coarse_solve<T>, dim3(blocks), dim3(threads), (size_t)m * sizeof(T), s, v, g.unk_node, g.unk_ghost, Ainv, m);
 }
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_js_defect(LevelView<T> v, const int32_t *__restrict__ node,
                                                         const int32_t *__restrict__ ghost, T *__restrict__ r, int n) {
+    pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) r[k] = dev::js_defect<T, D>(v, node[k], ghost[k]);
 }
@@ -357,6 +400,7 @@ __global__ void __launch_bounds__(kJsRowsPerBlock * 32)
     k_js_apply(T *__restrict__ u, const int32_t *__restrict__ node, const int32_t *__restrict__ comp,
                const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const T *__restrict__ inv,
                const T *__restrict__ r, int n) {
+    pdl_wait();
     const int k = blockIdx.x * kJsRowsPerBlock + (threadIdx.x >> 5);
     if (k < n) dev::js_apply_row<T>(u, node, comp, off, aoff, inv, r, k, threadIdx.x & 31);
 }
@@ -366,10 +410,10 @@ void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv
     const int n = g.js_n;
     if (n <= 0) return;
     g_launches += 2;
-    if (g.dim == 2) k_js_defect<T, 2><<<blocks_for(n), kThreads, 0, s>>>(v, g.js_node, g.js_ghost, r, n);
-    else k_js_defect<T, 3><<<blocks_for(n), kThreads, 0, s>>>(v, g.js_node, g.js_ghost, r, n);
-    k_js_apply<T><<<(unsigned)((n + kJsRowsPerBlock - 1) / kJsRowsPerBlock), kJsRowsPerBlock * 32, 0, s>>>(
-        v.u, g.js_node, g.js_comp, g.js_off, g.js_aoff, inv, r, n);
+    if (g.dim == 2) pdl_launch(k_js_defect<T, 2>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, r, n);
+    else pdl_launch(k_js_defect<T, 3>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, r, n);
+    pdl_launch(k_js_apply<T>, dim3((unsigned)((n + kJsRowsPerBlock - 1) / kJsRowsPerBlock)),
+               dim3(kJsRowsPerBlock * 32), 0, s, v.u, g.js_node, g.js_comp, g.js_off, g.js_aoff, inv, r, n);
 }
 
 template <typename T>
@@ -385,8 +429,8 @@ void launch_local(const LocalView<T> &J, int dim, int lead_ghost, int reps, cuda
     if (J.ncomp <= 0 || (reps <= 0 && !lead_ghost)) return;
     g_launches++;
     const size_t smem = local_smem_bytes(J, dim);
-    if (dim == 2) k_local<T, 2><<<J.ncomp, LOCAL_THREADS, smem, s>>>(J, lead_ghost, reps);
-    else k_local<T, 3><<<J.ncomp, LOCAL_THREADS, smem, s>>>(J, lead_ghost, reps);
+    if (dim == 2) pdl_launch(k_local<T, 2>, dim3(J.ncomp), dim3(LOCAL_THREADS), smem, s, J, lead_ghost, reps);
+    else pdl_launch(k_local<T, 3>, dim3(J.ncomp), dim3(LOCAL_THREADS), smem, s, J, lead_ghost, reps);
 }
 
 template <typename T>
@@ -399,18 +443,18 @@ void local_prepare(int dim, size_t smem) {
 template <typename T>
 void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s) {
     g_launches++;
-    k_mask_unknowns<T><<<blocks_for(nn), kThreads, 0, s>>>(type, u, nn);
+    pdl_launch(k_mask_unknowns<T>, dim3(blocks_for(nn)), dim3(kThreads), 0, s, type, u, nn);
 }
 
 void launch_defect_to_f32(const DevGeom &g, const double *r64, float *f32, float *g32, cudaStream_t s) {
     g_launches += g.ng > 0 ? 2 : 1;
-    k_defect_to_f32<<<blocks_for(g.nn), kThreads, 0, s>>>(g.type, r64, f32, g.nn);
-    if (g.ng > 0) k_ghost_defect_to_f32<<<blocks_for(g.ng), kThreads, 0, s>>>(g.gnode, r64, g32, g.ng);
+    pdl_launch(k_defect_to_f32, dim3(blocks_for(g.nn)), dim3(kThreads), 0, s, g.type, r64, f32, g.nn);
+    if (g.ng > 0) pdl_launch(k_ghost_defect_to_f32, dim3(blocks_for(g.ng)), dim3(kThreads), 0, s, g.gnode, r64, g32, g.ng);
 }
 
 void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cudaStream_t s) {
     g_launches++;
-    k_add_correction<<<blocks_for(g.nn), kThreads, 0, s>>>(g.type, u64, e32, g.nn);
+    pdl_launch(k_add_correction, dim3(blocks_for(g.nn)), dim3(kThreads), 0, s, g.type, u64, e32, g.nn);
 }
 
 #define GCMG_INSTANTIATE(T)                                                                              \

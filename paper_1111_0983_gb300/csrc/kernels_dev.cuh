@@ -16,6 +16,10 @@ constexpr int LOCAL_EPT = 4;     // inside entries per thread and colour in loca
 
 // max-norm reduction on the bit pattern of a non-negative double (monotone
 // for non-negative IEEE values); NaN is folded into +Inf so that it is seen.
+// waits for the preceding kernel of the stream (programmatic dependent launch;
+// a no-op when the kernel was launched without it)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void atomic_max_abs(unsigned long long *bits, double v) {
     v = fabs(v);
     if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);
