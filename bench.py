@@ -294,8 +294,26 @@ def secondary(name, rtol, precision, args, stream, flush):
                 break
         else:
             k = max(1, min(args.steps, 3))
-            out["f64" if prec == 0 else "mixed"] = {"value": S.num_unknowns(0) * k / (ms / 1e3),
-                                                   "unit": "unknowns/s", "ms_per_solve": ms / k, "cycles": cyc}
+            rec = {"value": S.num_unknowns(0) * k / (ms / 1e3), "unit": "unknowns/s", "ms_per_solve": ms / k,
+                   "cycles": cyc}
+            # the fine-level fused sweep of this form, timed live with CUDA events
+            # around each launch in one instrumented solve
+            if P.dim == 2:
+                n_in = int(((S.node_types(0) & 3) == 1).sum())
+                flush.zero_()
+                u.zero_()
+                S.set_kernel_timing(S.KERNEL_SMOOTH)
+                S.solve(u)
+                kl, kms = S.kernel_timing()
+                S.set_kernel_timing(-1)
+                if kl:
+                    alg = (24 if prec == 0 else 12) * n_in
+                    gbs = alg / (kms / kl / 1e3) / 1e9
+                    peak = measured_peaks()[0].get("hbm_gbs")
+                    rec["fine_sweep"] = {"kernel": "k_rb_fused2d", "alg_bytes_per_launch": alg,
+                                         "avg_launch_ms": kms / kl, "achieved_GBs": gbs,
+                                         "frac_of_measured_hbm": gbs / peak if peak else None}
+            out["f64" if prec == 0 else "mixed"] = rec
         out["unknowns"] = S.num_unknowns(0)
         out["setup_s_" + ("f64" if prec == 0 else "mixed")] = time.perf_counter() - t0
         S.close()

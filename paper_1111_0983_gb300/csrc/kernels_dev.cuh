@@ -63,8 +63,10 @@ __device__ __forceinline__ T neighbour_sum(const T *__restrict__ u, int64_t p, i
 // neighbouring tiles compute for their own nodes), then black nodes on the
 // tile; the tile's inside nodes are stored.  Equal to a red half-sweep
 // followed by a black half-sweep over the whole grid.
+// FP64 form: one flat index over the staged region, f read at inside nodes
+// only (the FP64 pipe, not instruction issue, bounds this form)
 template <typename T, int TR, int TC>
-__device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, int tile) {
+__device__ __forceinline__ void rb_fused2d_flat(const LevelView<T> &v, int tile) {
     constexpr int UR = TR + 4, UC = TC + 4, FR = TR + 2, FC = TC + 2;
     __shared__ T su[UR][UC];
     __shared__ T sf[FR][FC];
@@ -105,6 +107,86 @@ __device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, int tile)
         if (sk[r + 1][cc + 1] != NODE_IN) continue;
         v.u[(int64_t)(i0 + r) * v.s0 + (j0 + cc)] = su[r + 2][cc + 2];
     }
+}
+
+template <typename T, int TR, int TC>
+__device__ __forceinline__ void rb_fused2d_cols(const LevelView<T> &v, int tile) {
+    // FP32 form: 256 threads as TY rows x TC columns: a thread owns a column (and the
+    // halo columns TC + tx for the first few tx) and steps through rows, so
+    // no index is divided and addresses advance by a constant stride
+    static_assert(256 % TC == 0 && TC >= 4, "tile width");
+    constexpr int TY = 256 / TC;
+    constexpr int UR = TR + 4, UC = TC + 4, FR = TR + 2, FC = TC + 2;
+    __shared__ T su[UR][UC];
+    __shared__ T sf[FR][FC];
+    __shared__ uint8_t sk[FR][FC];
+    const int i0 = (tile >> 16) * TR, j0 = (tile & 0xffff) * TC;
+    const int n = v.n;
+    const int tx = threadIdx.x % TC, ty = threadIdx.x / TC;
+    // u with a 2-node halo; f and node types with a 1-node halo (f is read
+    // whatever the node type: only inside nodes use it); all loads independent
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int cc = tx + k * TC;
+        if (k == 1 && tx >= 4) break;
+        const int gj = j0 - 2 + cc;
+        const bool jok = gj >= 0 && gj < n;
+#pragma unroll 4
+        for (int r = ty; r < UR; r += TY) {
+            const int gi = i0 - 2 + r;
+            su[r][cc] = (jok && gi >= 0 && gi < n) ? v.u[(int64_t)gi * v.s0 + gj] : (T)0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int cc = tx + k * TC;
+        if (k == 1 && tx >= 2) break;
+        const int gj = j0 - 1 + cc;
+        const bool jok = gj >= 0 && gj < n;
+#pragma unroll 4
+        for (int r = ty; r < FR; r += TY) {
+            const int gi = i0 - 1 + r;
+            const bool in = jok && gi >= 0 && gi < n;
+            const int64_t p = in ? (int64_t)gi * v.s0 + gj : 0;
+            const uint8_t kk = v.type[p];
+            const T f = v.f[p];
+            sk[r][cc] = in ? (uint8_t)(kk & NODE_KIND) : (uint8_t)NODE_OUT;
+            sf[r][cc] = v.h2 * f;
+        }
+    }
+    __syncthreads();
+    // red nodes of the tile and its 1-node halo
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int cc = tx + k * TC;
+        if (k == 1 && tx >= 2) break;
+#pragma unroll 4
+        for (int r = ty; r < FR; r += TY) {
+            if (sk[r][cc] != NODE_IN || (((i0 - 1 + r) + (j0 - 1 + cc)) & 1)) continue;
+            const int ur = r + 1, uc = cc + 1;
+            su[ur][uc] = (sf[r][cc] + su[ur - 1][uc] + su[ur + 1][uc] + su[ur][uc - 1] + su[ur][uc + 1]) * (T)0.25;
+        }
+    }
+    __syncthreads();
+    // black nodes of the tile
+#pragma unroll 4
+    for (int r = ty; r < TR; r += TY) {
+        if (sk[r + 1][tx + 1] != NODE_IN || (((i0 + r) + (j0 + tx)) & 1) == 0) continue;
+        const int ur = r + 2, uc = tx + 2;
+        su[ur][uc] = (sf[r + 1][tx + 1] + su[ur - 1][uc] + su[ur + 1][uc] + su[ur][uc - 1] + su[ur][uc + 1]) * (T)0.25;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = ty; r < TR; r += TY) {
+        if (sk[r + 1][tx + 1] != NODE_IN) continue;
+        v.u[(int64_t)(i0 + r) * v.s0 + (j0 + tx)] = su[r + 2][tx + 2];
+    }
+}
+
+template <typename T, int TR, int TC>
+__device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, int tile) {
+    if constexpr (sizeof(T) == 8) rb_fused2d_flat<T, TR, TC>(v, tile);
+    else rb_fused2d_cols<T, TR, TC>(v, tile);
 }
 
 // ------------------------------------------------------- local programs
