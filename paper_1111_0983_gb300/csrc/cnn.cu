@@ -132,6 +132,7 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 
 struct Geo {
     int npix, Hp, Wp, H, W, P;
+    int gs;        // rows between channel groups (npix plus zero guard rows on both sides)
     __device__ __forceinline__ bool interior(int q, int *b, int *i, int *j) const {
         const int plane = Hp * Wp;
         *b = q / plane;
@@ -145,7 +146,7 @@ struct Geo {
 // stages the three row segments (di = -1, 0, 1) of G channel groups around
 // pixels [q0, q0 + 128): smem[g][s][r] = x[g][q0 + (s-1) d Wp - d + r]
 template <int G>
-__device__ __forceinline__ void stage_halo(uint4 *sm, const uint4 *__restrict__ x, int npix, int q0, int Wp,
+__device__ __forceinline__ void stage_halo(uint4 *sm, const uint4 *__restrict__ x, int npix, int gs, int q0, int Wp,
                                            int dil) {
     const int len = kTile + 2 * dil;
     for (int e = threadIdx.x; e < G * 3 * len; e += blockDim.x) {
@@ -154,7 +155,7 @@ __device__ __forceinline__ void stage_halo(uint4 *sm, const uint4 *__restrict__ 
         const int s = rem / len, r = rem - s * len;
         const int q = q0 + (s - 1) * dil * Wp - dil + r;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (q >= 0 && q < npix) v = x[(size_t)g * npix + q];
+        if (q >= 0 && q < npix) v = x[(size_t)g * gs + q];
         sm[(g * 3 + s) * kSeg + r] = v;
     }
 }
@@ -174,89 +175,142 @@ struct ConvArgs {
     int *err;
 };
 
+// bulk copy of `bytes` (a multiple of 16) from global to shared memory,
+// completing as transaction bytes on `mbar`
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Persistent convolution: a CTA keeps the layer's weights in shared memory
+// and walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The three
+// input row segments of the next tile are brought in by bulk copies into the
+// other half of a double buffer while the current tile's MMAs and epilogue
+// run.  The activation buffers carry zero guard rows before and after each
+// channel group, so every segment lies inside the allocation.
 template <int GIN, int NOUT, int MODE>
-__global__ void __launch_bounds__(128) k_conv(ConvArgs a) {
+__global__ void __launch_bounds__(128) k_conv(ConvArgs a, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint4 *sx = reinterpret_cast<uint4 *>(smem);                 // GIN * 3 * kSeg rows
-    uint4 *sw = sx + GIN * 3 * kSeg;                              // 9 * GIN * NOUT rows
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sw + 9 * GIN * NOUT);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    constexpr int HALO = GIN * 3 * kSeg;                          // rows per buffer
+    uint4 *sx = reinterpret_cast<uint4 *>(smem);                  // 2 buffers
+    uint4 *sw = sx + 2 * HALO;                                    // 9 * GIN * NOUT rows
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sw + 9 * GIN * NOUT);   // full[2], mma
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 3);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q0 = blockIdx.x * kTile;
+    const int len = kTile + 2 * a.dil;
+    const uint32_t seg_bytes = (uint32_t)len * 16;
+    const uint32_t full0 = smem_u32(&mbar[0]), full1 = smem_u32(&mbar[1]), mma_bar = smem_u32(&mbar[2]);
 
     if (warp == 0) tmem_alloc<32>(smem_u32(tslot));
-    if (threadIdx.x == 0) mbar_init(smem_u32(mbar));
+    if (threadIdx.x == 0) {
+        mbar_init(full0);
+        mbar_init(full1);
+        mbar_init(mma_bar);
+    }
     for (int e = threadIdx.x; e < 9 * GIN * NOUT; e += blockDim.x) sw[e] = a.w[e];
-    stage_halo<GIN>(sx, a.x, a.geo.npix, q0, a.geo.Wp, a.dil);
     fence_async_smem();
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tslot;
 
-    if (threadIdx.x == 0) {
-        constexpr uint32_t idesc = idesc_bf16(kTile, NOUT, 0, 0);
-        const uint32_t xa = smem_u32(sx), wa = smem_u32(sw);
-        uint32_t acc = 0;
+    // the producer: the segments of tile t into buffer b
+    auto load_tile = [&](int t, int b) {
+        const uint32_t fb = b ? full1 : full0;
+        mbar_expect(fb, (uint32_t)(GIN * 3) * seg_bytes);
+        const int q0 = t * kTile;
+        for (int g = 0; g < GIN; g++)
+            for (int sgm = 0; sgm < 3; sgm++) {
+                const int q = q0 + (sgm - 1) * a.dil * a.geo.Wp - a.dil;
+                bulk_g2s(smem_u32(sx + b * HALO + (g * 3 + sgm) * kSeg), a.x + (size_t)g * a.geo.gs + q, seg_bytes,
+                         fb);
+            }
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) load_tile(blockIdx.x, 0);
+
+    uint32_t ph_full[2] = {0, 0}, ph_mma = 0;
+    bool ok = true;
+    int k = 0;
 #pragma unroll 1
-        for (int t = 0; t < 9; t++) {
-            const int s = t / 3, dj = t % 3 - 1;
-            const int r0 = a.dil + dj * a.dil;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, k++) {
+        const int b = k & 1;
+        const bool w1 = mbar_wait(b ? full1 : full0, ph_full[b]);
+        ph_full[b] ^= 1;
+        ok = ok && w1;
+        if (threadIdx.x == 0) {
+            constexpr uint32_t idesc = idesc_bf16(kTile, NOUT, 0, 0);
+            const uint32_t xa = smem_u32(sx + b * HALO), wa = smem_u32(sw);
+            uint32_t acc = 0;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; tap++) {
+                const int sgm = tap / 3, dj = tap % 3 - 1;
+                const int r0 = a.dil + dj * a.dil;
 #pragma unroll
-            for (int gp = 0; gp < GIN / 2; gp++) {
-                const uint64_t ad = sdesc(xa + ((2 * gp * 3 + s) * kSeg + r0) * 16, 3 * kSeg * 16, 128);
-                const uint64_t bd = sdesc(wa + ((t * GIN + 2 * gp) * NOUT) * 16, NOUT * 16, 128);
-                mma_bf16(tmem, ad, bd, idesc, acc);
-                acc = 1;
-            }
-        }
-        mma_commit(smem_u32(mbar));
-    }
-    __syncwarp();
-    bool ok = mbar_wait(smem_u32(mbar), 0);
-    tc_after();
-    if (!ok) {
-        if (lane == 0) atomicExch(a.err, 1);
-        mbar_wait(smem_u32(mbar), 0);   // let the MMAs drain before freeing TMEM
-    }
-
-    float v[NOUT];
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    tmem_ld16(lane_addr, v);
-    if (NOUT == 32) tmem_ld16(lane_addr + 16, v + 16);
-
-    const int q = q0 + warp * 32 + lane;
-    int b, i, j;
-    if (q < a.geo.npix) {
-        const bool in = a.geo.interior(q, &b, &i, &j) && ok;
-        if (MODE == 1) {
-            if (in) {
-                const int H = a.geo.H, W = a.geo.W, P = a.geo.P;
-                for (int c = 0; c < 2; c++)
-                    a.out[(((size_t)b * 2 + c) * H + (i - P)) * W + (j - P)] = v[c] + a.bias[c];
-            }
-        } else {
-#pragma unroll
-            for (int g = 0; g < NOUT / 8; g++) {
-                float o[8];
-                if (MODE == 0) {
-#pragma unroll
-                    for (int k = 0; k < 8; k++) o[k] = in ? fmaxf(v[8 * g + k] + a.bias[8 * g + k], 0.0f) : 0.0f;
-                } else {
-                    const uint4 gt = a.gate[(size_t)g * a.geo.npix + q];
-                    const uint32_t gw[4] = {gt.x, gt.y, gt.z, gt.w};
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        o[2 * k] = (in && bf16_lo(gw[k]) > 0.0f) ? v[8 * g + 2 * k] : 0.0f;
-                        o[2 * k + 1] = (in && bf16_hi(gw[k]) > 0.0f) ? v[8 * g + 2 * k + 1] : 0.0f;
-                    }
+                for (int gp = 0; gp < GIN / 2; gp++) {
+                    const uint64_t ad = sdesc(xa + ((2 * gp * 3 + sgm) * kSeg + r0) * 16, 3 * kSeg * 16, 128);
+                    const uint64_t bd = sdesc(wa + ((tap * GIN + 2 * gp) * NOUT) * 16, NOUT * 16, 128);
+                    mma_bf16(tmem, ad, bd, idesc, acc);
+                    acc = 1;
                 }
-                a.y[(size_t)g * a.geo.npix + q] =
-                    make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
+            }
+            mma_commit(mma_bar);
+            // the other buffer held the previous tile, whose MMAs completed
+            // before its epilogue (below, in the previous iteration)
+            if (t + (int)gridDim.x < ntiles) load_tile(t + gridDim.x, b ^ 1);
+        }
+        __syncwarp();
+        const bool w2 = mbar_wait(mma_bar, ph_mma);
+        ph_mma ^= 1;
+        ok = ok && w2;
+        tc_after();
+
+        float v[NOUT];
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        tmem_ld16(lane_addr, v);
+        if (NOUT == 32) tmem_ld16(lane_addr + 16, v + 16);
+
+        const int q = t * kTile + warp * 32 + lane;
+        int bb, i, j;
+        if (q < a.geo.npix) {
+            const bool in = a.geo.interior(q, &bb, &i, &j) && ok;
+            if (MODE == 1) {
+                if (in) {
+                    const int H = a.geo.H, W = a.geo.W, P = a.geo.P;
+                    for (int c = 0; c < 2; c++)
+                        a.out[(((size_t)bb * 2 + c) * H + (i - P)) * W + (j - P)] = v[c] + a.bias[c];
+                }
+            } else {
+#pragma unroll
+                for (int g = 0; g < NOUT / 8; g++) {
+                    float o[8];
+                    if (MODE == 0) {
+#pragma unroll
+                        for (int e = 0; e < 8; e++) o[e] = in ? fmaxf(v[8 * g + e] + a.bias[8 * g + e], 0.0f) : 0.0f;
+                    } else {
+                        const uint4 gt = a.gate[(size_t)g * a.geo.gs + q];
+                        const uint32_t gw[4] = {gt.x, gt.y, gt.z, gt.w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            o[2 * e] = (in && bf16_lo(gw[e]) > 0.0f) ? v[8 * g + 2 * e] : 0.0f;
+                            o[2 * e + 1] = (in && bf16_hi(gw[e]) > 0.0f) ? v[8 * g + 2 * e + 1] : 0.0f;
+                        }
+                    }
+                    a.y[(size_t)g * a.geo.gs + q] = make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]),
+                                                               pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
+                }
             }
         }
+        // the accumulator is read before the next tile's MMAs overwrite it
+        tc_before();
+        __syncthreads();
+        tc_after();
     }
-    tc_before();
+    if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
     __syncthreads();
     if (warp == 0) {
         tc_after();
@@ -314,9 +368,9 @@ __global__ void __launch_bounds__(128, 1) k_conv_dw(DwArgs a) {
         for (int e = threadIdx.x; e < GA * kTile; e += blockDim.x) {
             const int g = e / kTile, r = e - g * kTile;
             const int q = q0 + r;
-            sa[e] = q < a.geo.npix ? a.dz[(size_t)g * a.geo.npix + q] : make_uint4(0, 0, 0, 0);
+            sa[e] = q < a.geo.npix ? a.dz[(size_t)g * a.geo.gs + q] : make_uint4(0, 0, 0, 0);
         }
-        stage_halo<GB>(sx, a.x, a.geo.npix, q0, a.geo.Wp, a.dil);
+        stage_halo<GB>(sx, a.x, a.geo.npix, a.geo.gs, q0, a.geo.Wp, a.dil);
         fence_async_smem();
         tc_before();
         __syncthreads();
@@ -377,7 +431,7 @@ __global__ void k_pack_input(const float *__restrict__ in, uint4 *__restrict__ x
         for (int k = 0; k < 4; k++) c[k] = in[((size_t)b * 4 + k) * plane + off];
     }
     x[q] = make_uint4(pack_bf16(c[0], c[1]), pack_bf16(c[2], c[3]), 0, 0);
-    x[(size_t)geo.npix + q] = make_uint4(0, 0, 0, 0);
+    x[(size_t)geo.gs + q] = make_uint4(0, 0, 0, 0);
 }
 
 // dL/dout [B][2][H][W] FP32 -> [2][npix] rows (channels 2..15 zero)
@@ -392,7 +446,7 @@ __global__ void k_pack_dout(const float *__restrict__ d, uint4 *__restrict__ x, 
         for (int k = 0; k < 2; k++) c[k] = d[((size_t)b * 2 + k) * plane + off];
     }
     x[q] = make_uint4(pack_bf16(c[0], c[1]), 0, 0, 0);
-    x[(size_t)geo.npix + q] = make_uint4(0, 0, 0, 0);
+    x[(size_t)geo.gs + q] = make_uint4(0, 0, 0, 0);
 }
 
 // masked squared error of channel 0 ([B][2][plane] arrays): dout_0 = 2 (out_0 -
@@ -466,11 +520,11 @@ __global__ void k_lap_grad(const float *__restrict__ s, const float *__restrict_
 }
 
 // db[c] += sum over pixels of the G-group gradient rows (BF16 values)
-__global__ void k_bias_grad(const uint4 *__restrict__ dz, int G, int cout, int npix, float *db) {
+__global__ void k_bias_grad(const uint4 *__restrict__ dz, int G, int cout, int npix, int gs, float *db) {
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int g = blockIdx.y;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npix; q += gridDim.x * blockDim.x) {
-        const uint4 v = dz[(size_t)g * npix + q];
+        const uint4 v = dz[(size_t)g * gs + q];
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
         for (int k = 0; k < 4; k++) {
             acc[2 * k] += bf16_lo(w[k]);
@@ -538,6 +592,8 @@ struct gcmg_cnn {
     double *d_loss = nullptr;
     int *d_err = nullptr;
     int adam_t = 0;
+    int sms = 148;
+    size_t guard = 0;            // zero rows before and after each channel group
     size_t smem_conv4 = 0, smem_conv2 = 0, smem_dw = 0;
     std::string err;
     std::vector<void *> allocs;
@@ -572,7 +628,7 @@ int groups_in(int l) { return l == 0 ? 2 : 4; }
 int nout_of(int l) { return l == kLayers - 1 ? 16 : 32; }
 
 size_t conv_smem(int gin, int nout, size_t slack) {
-    const size_t need = (size_t)(gin * 3 * kSeg + 9 * gin * nout) * 16 + 16;
+    const size_t need = (size_t)(2 * gin * 3 * kSeg + 9 * gin * nout) * 16 + 32;
     return std::max(need, slack);
 }
 
@@ -602,8 +658,11 @@ void prep_weights(gcmg_cnn *c) {
 
 template <int GIN, int NOUT, int MODE>
 void launch_conv(gcmg_cnn *c, const ConvArgs &a, size_t smem) {
-    const unsigned grid = (unsigned)((c->geo.npix + kTile - 1) / kTile);
-    k_conv<GIN, NOUT, MODE><<<grid, 128, smem, c->stream>>>(a);
+    const int ntiles = (c->geo.npix + kTile - 1) / kTile;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv<GIN, NOUT, MODE>, 128, smem);
+    const unsigned grid = (unsigned)std::min(ntiles, std::max(per_sm, 1) * c->sms);
+    k_conv<GIN, NOUT, MODE><<<grid, 128, smem, c->stream>>>(a, ntiles);
     ck(cudaGetLastError(), "conv launch");
 }
 
@@ -638,8 +697,7 @@ void backward(gcmg_cnn *c, const float *dout) {
     k_pack_dout<<<(g.npix + 255) / 256, 256, 0, c->stream>>>(dout, c->dz[0], g);
     int cur = 0;
     const int ntiles = (g.npix + kTile - 1) / kTile;
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int sms = c->sms;
     for (int l = kLayers - 1; l >= 0; l--) {
         const int ga = l == kLayers - 1 ? 2 : 4;
         DwArgs d{};
@@ -657,7 +715,8 @@ void backward(gcmg_cnn *c, const float *dout) {
         else if (l == 0) k_conv_dw<4, 2><<<grid, 128, c->smem_dw, c->stream>>>(d);
         else k_conv_dw<4, 4><<<grid, 128, c->smem_dw, c->stream>>>(d);
         ck(cudaGetLastError(), "dw launch");
-        k_bias_grad<<<dim3(64, ga), 256, 0, c->stream>>>(c->dz[cur], ga, kCout[l], g.npix, c->grad + c->boff[l]);
+        k_bias_grad<<<dim3(64, ga), 256, 0, c->stream>>>(c->dz[cur], ga, kCout[l], g.npix, g.gs,
+                                                         c->grad + c->boff[l]);
         if (l == 0) break;
         ConvArgs a{};
         a.x = c->dz[cur];
@@ -709,7 +768,9 @@ gcmg_status gcmg_cnn_create(int batch, int H, int W, const int *dilations, void 
     c->H = H;
     c->W = W;
     c->P = P;
-    c->geo = Geo{(int)npix, H + 2 * P, W + 2 * P, H, W, P};
+    // guard rows: the furthest tap of the last pixel of a tile, on either side
+    c->guard = (size_t)P * (W + 2 * P) + P + kTile;
+    c->geo = Geo{(int)npix, H + 2 * P, W + 2 * P, H, W, P, (int)((size_t)npix + 2 * c->guard)};
     c->stream = (cudaStream_t)stream;
     CNN_GUARD(c, {
         ck(cudaGetDevice(&c->device), "cudaGetDevice");
@@ -732,11 +793,13 @@ gcmg_status gcmg_cnn_create(int batch, int H, int W, const int *dilations, void 
             c->wf[l] = alloc<uint16_t>(c, (size_t)9 * groups_in(l) * nout_of(l) * 8);
             if (l > 0) c->wb[l] = alloc<uint16_t>(c, (size_t)9 * (l == kLayers - 1 ? 2 : 4) * 32 * 8);
         }
-        const size_t np = (size_t)c->geo.npix;
-        c->act[0] = alloc<uint4>(c, 2 * np);
-        for (int l = 1; l < kLayers; l++) c->act[l] = alloc<uint4>(c, 4 * np);
-        c->dz[0] = alloc<uint4>(c, 4 * np);
-        c->dz[1] = alloc<uint4>(c, 4 * np);
+        ck(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device), "attr");
+        const size_t gs = (size_t)c->geo.gs;
+        // each buffer: G groups of gs rows; the pointer skips the first guard
+        c->act[0] = alloc<uint4>(c, 2 * gs) + c->guard;
+        for (int l = 1; l < kLayers; l++) c->act[l] = alloc<uint4>(c, 4 * gs) + c->guard;
+        c->dz[0] = alloc<uint4>(c, 4 * gs) + c->guard;
+        c->dz[1] = alloc<uint4>(c, 4 * gs) + c->guard;
         c->out = alloc<float>(c, (size_t)batch * 2 * H * W);
         c->dout = alloc<float>(c, (size_t)batch * 2 * H * W);
         c->lap_s = alloc<float>(c, (size_t)batch * H * W);
@@ -756,10 +819,10 @@ gcmg_status gcmg_cnn_create(int batch, int H, int W, const int *dilations, void 
         ck(cudaFuncSetAttribute(k_conv_dw<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_dw), "attr");
         ck(cudaFuncSetAttribute(k_conv_dw<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_dw), "attr");
         ck(cudaFuncSetAttribute(k_conv_dw<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_dw), "attr");
-        // zero every activation once: borders stay zero from then on
-        for (int l = 0; l < kLayers; l++) ck(cudaMemset(c->act[l], 0, (l ? 4 : 2) * np * 16), "memset");
-        ck(cudaMemset(c->dz[0], 0, 4 * np * 16), "memset");
-        ck(cudaMemset(c->dz[1], 0, 4 * np * 16), "memset");
+        // zero every activation once: borders and guards stay zero from then on
+        for (int l = 0; l < kLayers; l++) ck(cudaMemset(c->act[l] - c->guard, 0, (l ? 4 : 2) * gs * 16), "memset");
+        ck(cudaMemset(c->dz[0] - c->guard, 0, 4 * gs * 16), "memset");
+        ck(cudaMemset(c->dz[1] - c->guard, 0, 4 * gs * 16), "memset");
         return GCMG_OK;
     })
 }
@@ -810,7 +873,10 @@ gcmg_status gcmg_cnn_activation(gcmg_cnn *c, int layer, float *dst_dev) {
         const int G = layer == 0 ? 2 : 4, C = layer == 0 ? 4 : 32;
         const size_t np = (size_t)c->geo.npix;
         std::vector<uint16_t> h((size_t)G * np * 8);
-        ck(cudaMemcpyAsync(h.data(), c->act[layer], h.size() * 2, cudaMemcpyDeviceToHost, c->stream), "act");
+        for (int g = 0; g < G; g++)
+            ck(cudaMemcpyAsync(h.data() + (size_t)g * np * 8, c->act[layer] + (size_t)g * c->geo.gs, np * 16,
+                               cudaMemcpyDeviceToHost, c->stream),
+               "act");
         ck(cudaStreamSynchronize(c->stream), "sync");
         std::vector<float> o((size_t)c->batch * C * c->H * c->W);
         for (int b = 0; b < c->batch; b++)
