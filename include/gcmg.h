@@ -88,6 +88,9 @@ typedef struct {
                                 is first grown by its ghosts' stencils, then stripped of
                                 ghosts whose stencil leaves it; components of at most 4096
                                 unknowns (larger: GCMG_E_GEOM at the solve) */
+    int fused_coarse_n;      /* 2D FP32 V-cycles: the levels with at most this many nodes a side
+                                run as one launch (a cluster of CTAs with barriers between the
+                                steps; same results); 0: one launch per step */
 } gcmg_params;
 
 /* Per-solve report.  rel[m] = ||r^(m)||_inf / ||r^(0)||_inf for m = 0..cycles

@@ -18,14 +18,6 @@ using namespace gcmg;
 
 namespace {
 
-struct CudaFail {
-    cudaError_t e;
-    const char *what;
-};
-
-inline void ck(cudaError_t e, const char *what) {
-    if (e != cudaSuccess) throw CudaFail{e, what};
-}
 
 template <typename T>
 T *dalloc(gcmg_ctx *c, size_t count) {
@@ -97,9 +89,11 @@ void alloc_data(gcmg_ctx *c, int l, DevData<T> &D, bool grids) {
     ck(cudaStreamSynchronize(c->stream), "sync");
     if (grids) {
         D.u = dalloc<T>(c, L.nn);
+        D.u2 = dalloc<T>(c, L.nn);
         D.f = dalloc<T>(c, L.nn);
         D.r = dalloc<T>(c, L.nn);
         ck(cudaMemsetAsync(D.u, 0, L.nn * sizeof(T), c->stream), "memset");
+        ck(cudaMemsetAsync(D.u2, 0, L.nn * sizeof(T), c->stream), "memset");
         ck(cudaMemsetAsync(D.f, 0, L.nn * sizeof(T), c->stream), "memset");
         ck(cudaMemsetAsync(D.r, 0, L.nn * sizeof(T), c->stream), "memset");
     }
@@ -153,7 +147,7 @@ void free_tracked(gcmg_ctx *c, void *p) {
 void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     int32_t **arrs[] = {&z.node_off, &z.wb_cnt, &z.lnode, &z.int_off, &z.red_cnt, &z.int_glob,
                         &z.int_me, &z.int_nb, &z.gh_off, &z.gh_me, &z.gh_q, &z.gh_stn,
-                        &z.zred, &z.zblack, &z.zghost};
+                        &z.zred, &z.zblack, &z.zghost, &z.wb_list};
     for (int32_t **a : arrs) { free_tracked(c, *a); *a = nullptr; }
     z.ncomp = J.ncomp();
     z.max_nodes = J.max_nodes;
@@ -179,6 +173,11 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     z.zred = upload<int32_t>(c, J.zred.data(), J.zred.size());
     z.zblack = upload<int32_t>(c, J.zblack.data(), J.zblack.size());
     z.zghost = upload<int32_t>(c, J.zghost.data(), J.zghost.size());
+    std::vector<int32_t> wb;
+    for (int k = 0; k < z.ncomp; k++)
+        wb.insert(wb.end(), J.lnode.begin() + J.node_off[k], J.lnode.begin() + J.node_off[k] + J.wb_cnt[k]);
+    z.nwb = (int)wb.size();
+    z.wb_list = upload<int32_t>(c, wb.data(), wb.size());
     ck(cudaStreamSynchronize(c->stream), "sync");
 }
 
@@ -201,16 +200,20 @@ void timer_mark(gcmg_ctx *c, int kind, int l) {
     ck(cudaEventRecord(c->events[c->events_used++], c->stream), "cudaEventRecord");
 }
 
-// one relaxation R_h followed by the lambda extra sweeps (Sec. 2.4, 3.2) and
-// the junction sweeps
+// One relaxation R_h followed by the lambda extra sweeps (Sec. 2.4, 3.2) and
+// the junction relaxation.  2D: the sweep reads v.u and writes `out`, every
+// later step works on `out` in place; 3D: in place on v.u.  `wb` is a free
+// grid that takes the boundary blocks' write-back.  Returns the grid that
+// holds u afterwards.
 template <typename T>
-void relax(gcmg_ctx *c, const LevelView<T> &v, int l, bool extra) {
+T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
     const int dim = c->p.dim;
     const DevGeom &g = c->G[l];
     if (dim == 2) {
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
-        launch_rb_fused2d<T>(v, g.tiles, g.ntiles, c->stream);
+        launch_rb_fused2d<T>(v, out, g.tiles, g.ntiles, c->stream);
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+        v.u = out;
     } else {
         for (int colour = 0; colour < 2; colour++) {
             timer_mark(c, GCMG_KERNEL_SMOOTH, l);
@@ -220,10 +223,10 @@ void relax(gcmg_ctx *c, const LevelView<T> &v, int l, bool extra) {
     }
     if (extra && g.bz.ncomp > 0 && g.bz.in_smem) {
         // ghost sweep + lambda band sweeps in one shared-memory launch
-        launch_local<T>(lview<T>(g.bz, v), dim, 1, c->p.lambda, c->stream);
+        launch_local<T>(lview<T>(g.bz, v, wb), dim, 1, c->p.lambda, c->stream);
     } else {
         launch_ghost_relax<T>(v, dim, c->stream);
-        if (!extra) return;
+        if (!extra) return v.u;
         for (int k = 0; k < c->p.lambda; k++) {
             launch_rb_list<T>(v, dim, g.red, g.nred, c->stream);
             launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
@@ -244,6 +247,7 @@ void relax(gcmg_ctx *c, const LevelView<T> &v, int l, bool extra) {
             }
         }
     }
+    return v.u;
 }
 
 // decides whether a program's components fit in shared memory
@@ -261,30 +265,42 @@ void check_program_fits(gcmg_ctx *c, LocalDev &z) {
 }
 
 // TGCS (Sec. 2.4) applied recursively: V (gamma = 1) or W (gamma = 2) cycle
+// on level l starting from u (one of the level's two grids); returns the grid
+// that holds the level's u at the end.
 template <typename T>
-void cycle(gcmg_ctx *c, int l) {
+T *cycle(gcmg_ctx *c, int l, T *u) {
     std::vector<DevData<T>> &D = data<T>(c);
     const int last = (int)c->H.size() - 1;
-    const LevelView<T> v = view<T>(c, l, D[l]);
     const int dim = c->p.dim;
-    if (l == last) {
-        ck(cudaMemsetAsync(D[l].u, 0, c->H[l].nn * sizeof(T), c->stream), "memset");
-        launch_coarse_solve<T>(v, c->G[l], D[l].Ainv, c->stream);
-        return;
+    auto at = [&](int k, T *p) {
+        LevelView<T> v = view<T>(c, k, D[k]);
+        v.u = p;
+        return v;
+    };
+    auto other = [&](T *p) { return p == D[l].u ? D[l].u2 : D[l].u; };
+    if (sizeof(T) == 4 && l == c->coarse_l0) {   // the rest of the cycle in one launch (from D[l].u)
+        launch_coarse_cycle(c);
+        return ((c->p.nu1 + c->p.nu2) & 1) ? D[l].u2 : D[l].u;
     }
-    for (int k = 0; k < c->p.nu1; k++) relax<T>(c, v, l, true);
-    const LevelView<T> vc = view<T>(c, l + 1, D[l + 1]);
+    if (l == last) {
+        launch_coarse_solve<T>(at(l, u), c->G[l], D[l].Ainv, c->stream);
+        return u;
+    }
+    for (int k = 0; k < c->p.nu1; k++) u = relax<T>(c, at(l, u), other(u), D[l].r, l, true);
     // defect (TGCS step 3), composite restriction (step 4) with the defect
     // extension at the coarse ghosts (Sec. 2.6), and e_2h = 0: one launch
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
-    launch_descend<T>(v, vc, c->G[l], D[l].gt_val, D[l + 1].f, D[l + 1].gg, D[l + 1].u, c->stream);
+    launch_descend<T>(at(l, u), at(l + 1, D[l + 1].u), c->G[l], D[l].gt_val, D[l + 1].f, D[l + 1].gg, D[l + 1].u,
+                      c->stream);
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
     const int gam = (l + 1 == last) ? 1 : c->p.gamma;
-    for (int k = 0; k < gam; k++) cycle<T>(c, l + 1);
+    T *uc = D[l + 1].u;
+    for (int k = 0; k < gam; k++) uc = cycle<T>(c, l + 1, uc);
     timer_mark(c, GCMG_KERNEL_PROLONG, l);
-    launch_prolong<T>(v, vc, dim, D[l + 1].u, D[l].u, true, c->stream);
+    launch_prolong<T>(at(l, u), at(l + 1, uc), dim, uc, u, true, c->stream);
     timer_mark(c, GCMG_KERNEL_PROLONG, l);
-    for (int k = 0; k < c->p.nu2; k++) relax<T>(c, v, l, true);
+    for (int k = 0; k < c->p.nu2; k++) u = relax<T>(c, at(l, u), other(u), D[l].r, l, true);
+    return u;
 }
 
 __global__ void k_rhs_norm(const uint8_t *type, const double *f, int64_t nn, const double *g, int ng,
@@ -341,13 +357,17 @@ void loop_body(gcmg_ctx *c) {
     const DevGeom &g0 = c->G[0];
     const HostLevel &L0 = c->H[0];
     if (c->p.precision == 0) {
-        cycle<double>(c, 0);
+        double *u = cycle<double>(c, 0, c->D64[0].u);
+        // an odd number of 2D sweeps leaves u in the second grid: the loop
+        // body must end where it starts
+        if (u != c->D64[0].u)
+            ck(cudaMemcpyAsync(c->D64[0].u, u, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "copy");
     } else {
         DevData<float> &F0 = c->D32[0];
         launch_defect_to_f32(g0, c->D64[0].r, F0.f, F0.gg, c->stream);
         ck(cudaMemsetAsync(F0.u, 0, L0.nn * sizeof(float), c->stream), "memset");   // e = 0
-        cycle<float>(c, 0);
-        launch_add_correction(g0, c->D64[0].u, F0.u, c->stream);
+        float *e = cycle<float>(c, 0, F0.u);
+        launch_add_correction(g0, c->D64[0].u, e, c->stream);
     }
     ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
     launch_defect<double>(view<double>(c, 0, c->D64[0]), c->p.dim, false, c->d_norm, c->stream);
@@ -441,7 +461,7 @@ gcmg_status check_params(const gcmg_params &q) {
     if (p->gamma < 1 || p->gamma > 2 || p->nu1 < 0 || p->nu2 < 0 || p->lambda < 0) return GCMG_E_ARG;
     if (p->precision < 0 || p->precision > 1 || p->max_cycles < 1 || p->max_cycles > 256) return GCMG_E_ARG;
     if (p->junction_sweeps < 0 || p->junction_radius < 0.0 || p->junction_radius > 64.0) return GCMG_E_ARG;
-    if (p->junction_solve < 0 || p->junction_solve > 1) return GCMG_E_ARG;
+    if (p->junction_solve < 0 || p->junction_solve > 1 || p->fused_coarse_n < 0) return GCMG_E_ARG;
     return GCMG_OK;
 }
 
@@ -579,6 +599,7 @@ gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
     p->junction_solve = dim == 2 ? 1 : 0;
     p->junction_sweeps = dim == 3 ? 10 : 0;
     p->junction_radius = dim == 3 ? 2.0 : 20.0;
+    p->fused_coarse_n = 0;   // measured slower than the per-level launches on GB300
     return GCMG_OK;
 }
 
@@ -620,6 +641,7 @@ void gcmg_destroy(gcmg_ctx *c) {
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
+    if (c->d_coarse) cudaFree(c->d_coarse);
     if (c->h_norm) cudaFreeHost(c->h_norm);
     delete c;
 }
@@ -719,6 +741,7 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
         const DevGeom &g0 = c->G[0];
         ensure_inverse(c);
         ensure_junction_solve(c);
+        if (!c->gexec) coarse_prepare(c);   // the captured graph keeps the chosen path
         double *u = c->D64[0].u;   // internal buffer: the captured graph uses fixed pointers
         if (u_dev != u)
             ck(cudaMemcpyAsync(u, u_dev, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u in");
@@ -836,11 +859,22 @@ gcmg_status gcmg_relax(gcmg_ctx *c, int l, double *u, const double *f, const dou
             }
             ck(cudaStreamSynchronize(c->stream), "sync");
         }
+        // the sweep writes into a scratch grid (initialised with u), the other
+        // steps work there, and the result goes back into u
+        const size_t nn = (size_t)c->H[l].nn;
+        if (!c->relax_a) {
+            size_t mx = 0;
+            for (const auto &L : c->H) mx = std::max(mx, (size_t)L.nn);
+            c->relax_a = dalloc<double>(c, mx);
+            c->relax_b = dalloc<double>(c, mx);
+        }
+        ck(cudaMemcpyAsync(c->relax_a, u, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "copy");
         LevelView<double> v = view<double>(c, l, c->D64[l]);
         v.u = u;
         v.f = f;
         v.gg = g;
-        relax<double>(c, v, l, with_extra != 0);
+        double *res = relax<double>(c, v, c->relax_a, c->relax_b, l, with_extra != 0);
+        if (res != u) ck(cudaMemcpyAsync(u, res, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "copy");
         check_launch();
         ck(cudaStreamSynchronize(c->stream), "sync");
         return GCMG_OK;

@@ -38,7 +38,8 @@ struct BItem {
 
 // one level of one domain, in FP32 (the cycle precision of the batch)
 struct BView32 {
-    LevelView<float> v;      // this level
+    LevelView<float> v;      // this level (v.u: its first u grid)
+    float *u2, *c_u2;        // second u grids of this level and of the next coarser one
     LevelView<float> c;      // next coarser level (when it exists)
     float *cf, *cg;          // coarser level's f and ghost data (restriction targets)
     const int32_t *tiles;    // active tiles of the selected shape
@@ -61,7 +62,7 @@ struct BView32 {
 // level 0 of one domain in FP64 plus its FP32 correction arrays
 struct BView64 {
     LevelView<double> v;
-    float *f32, *g32, *e32;
+    float *f32, *g32, *e32, *e32b;   // e32b: level 0's second FP32 grid
     int dom;
     const int *active;
 };
@@ -73,50 +74,75 @@ const int kTileR[kVariants] = {16, 8, 32};
 const int kTileC[kVariants] = {64, 128, 32};
 
 // ---------------------------------------------------------------- kernels
+// Launch argument `cur` / `src`: which of the level's two u grids holds u
+// (0: v.u, 1: u2); the sweep reads that grid and writes the other.
+__device__ __forceinline__ float *ugrid(const BView32 &w, int k) { return k ? w.u2 : w.v.u; }
+
 template <int TR, int TC>
-__global__ void __launch_bounds__(256) kb_fused(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+__global__ void __launch_bounds__(256) kb_fused(const BView32 *__restrict__ V, const BItem *__restrict__ it, int src) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
-    rb_fused2d_body<float, TR, TC>(V[b.view].v, V[b.view].tiles[b.start]);
+    const BView32 &w = V[b.view];
+    LevelView<float> v = w.v;
+    v.u = ugrid(w, src);
+    rb_fused2d_body<float, TR, TC>(v, ugrid(w, src ^ 1), w.tiles[b.start]);
+}
+
+__global__ void __launch_bounds__(256) kb_local_copyback(const BView32 *__restrict__ V, const BItem *__restrict__ it,
+                                                         int cur) {
+    const BItem b = it[blockIdx.x];
+    if (!V[b.view].active[V[b.view].dom]) return;
+    LocalView<float> J = V[b.view].bz;
+    J.u = ugrid(V[b.view], cur);
+    local_copyback<float>(J, b.start + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(LOCAL_THREADS) kb_local(const BView32 *__restrict__ V, const BItem *__restrict__ it,
-                                                          int junction, int lead_ghost, int reps) {
+                                                          int junction, int lead_ghost, int reps, int cur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
-    local_body<float, 2>(junction ? V[b.view].jz : V[b.view].bz, b.start, lead_ghost, reps);
+    LocalView<float> J = junction ? V[b.view].jz : V[b.view].bz;
+    J.u = ugrid(V[b.view], cur);
+    local_body<float, 2>(J, b.start, lead_ghost, reps);
 }
 
 // exact junction solve: defects of the solved equations (256 rows per item),
 // then u += A_ZZ^-1 r (one warp per row, kJsRows rows per item)
 constexpr int kJsRows = 8;
 
-__global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+__global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
+    LevelView<float> v = w.v;
+    v.u = ugrid(w, cur);
     const int k = b.start + threadIdx.x;
-    if (k < w.js_n) w.js_r[k] = js_defect<float, 2>(w.v, w.js_node[k], w.js_ghost[k]);
+    if (k < w.js_n) w.js_r[k] = js_defect<float, 2>(v, w.js_node[k], w.js_ghost[k]);
 }
 
 __global__ void __launch_bounds__(kJsRows * 32) kb_js_apply(const BView32 *__restrict__ V,
-                                                            const BItem *__restrict__ it) {
+                                                            const BItem *__restrict__ it, int cur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     const int k = b.start + (threadIdx.x >> 5);
     if (k < w.js_n)
-        js_apply_row<float>(w.v.u, w.js_node, w.js_comp, w.js_off, w.js_aoff, w.js_inv, w.js_r, k, threadIdx.x & 31);
+        js_apply_row<float>(ugrid(w, cur), w.js_node, w.js_comp, w.js_off, w.js_aoff, w.js_inv, w.js_r, k,
+                            threadIdx.x & 31);
 }
 
 // defect, restriction with the coarse-ghost transfer, and zero coarse u in
 // one pass over the coarser level's nodes and ghosts
-__global__ void kb_descend(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+// defect, restriction with the coarse-ghost transfer, and zero coarse u in
+// one pass over the coarser level's nodes and ghosts (fine u in grid `cur`,
+// coarse u = 0 into its first grid)
+__global__ void kb_descend(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
-    descend_item<float, 2>(w.v, w.c, w.cf, w.cg, w.c.u, w.gt_ptr, w.gt_col, w.gt_val,
-                           (int64_t)b.start + threadIdx.x);
+    LevelView<float> v = w.v;
+    v.u = ugrid(w, cur);
+    descend_item<float, 2>(v, w.c, w.cf, w.cg, w.c.u, w.gt_ptr, w.gt_col, w.gt_val, (int64_t)b.start + threadIdx.x);
 }
 
 // zero u of the view's level (coarse = 0) or of its coarser level (coarse = 1)
@@ -128,12 +154,13 @@ __global__ void kb_zero(const BView32 *__restrict__ V, const BItem *__restrict__
     if (p < v.nn) v.u[p] = 0.f;
 }
 
-__global__ void kb_prolong(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
+__global__ void kb_prolong(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur, int ccur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     const int64_t p = (int64_t)b.start + threadIdx.x;
-    if (p < w.v.nn) prolong_node<float, 2>(w.v, w.c, w.c.u, w.v.u, true, p);
+    float *e = ccur ? w.c_u2 : w.c.u;
+    if (p < w.v.nn) prolong_node<float, 2>(w.v, w.c, e, ugrid(w, cur), true, p);
 }
 
 __global__ void kb_coarse(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
@@ -194,14 +221,14 @@ __global__ void kb_to_f32(const BView64 *__restrict__ V, const BItem *__restrict
 }
 
 // u64 += e32 on Omega_h u Gamma_h
-__global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ it) {
+__global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ it, int cur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView64 &w = V[b.view];
     const int64_t p = (int64_t)b.start + threadIdx.x;
     if (p >= w.v.nn) return;
     const uint8_t k = w.v.type[p] & NODE_KIND;
-    if (k == NODE_IN || k == NODE_GHOST) w.v.u[p] += (double)w.e32[p];
+    if (k == NODE_IN || k == NODE_GHOST) w.v.u[p] += (double)(cur ? w.e32b : w.e32)[p];
 }
 
 // end of one refinement step: per-domain relative residual, loop condition
@@ -226,20 +253,14 @@ __global__ void kb_check(cudaGraphConditionalHandle h, const unsigned long long 
     }
 }
 
-struct CudaFail {
-    cudaError_t e;
-    const char *what;
-};
-inline void ck(cudaError_t e, const char *what) {
-    if (e != cudaSuccess) throw CudaFail{e, what};
-}
 
 // a captured launch: kernel kind, item range and parameters
 struct Launch {
-    enum Kind { FUSED, BOUNDARY, JUNCTION, JS_DEFECT, JS_APPLY, DESCEND, PROLONG, COARSE, ZERO };
+    enum Kind { FUSED, BOUNDARY, BOUNDARY_COPY, JUNCTION, JS_DEFECT, JS_APPLY, DESCEND, PROLONG, COARSE, ZERO };
     Kind kind;
     size_t off, count;
     size_t smem;
+    int cur = 0, ccur = 0;   // which u grid holds u (this level, the next coarser one)
 };
 
 }  // namespace
@@ -249,6 +270,7 @@ struct gcmg_batch {
     cudaStream_t stream = nullptr, gstream = nullptr;
     int device = 0;
     int variant = 0;
+    int add_cur = 0;    // the u grid that holds level 0's correction after a cycle
     double rtol = 1e-10;
     int max_steps = 100;
     // device tables
@@ -309,7 +331,8 @@ std::vector<int32_t> tiles_for(const HostLevel &L, int tr, int tc) {
     const int nr = (L.n + tr - 1) / tr, ncol = (L.n + tc - 1) / tc;
     std::vector<uint8_t> act((size_t)nr * ncol, 0);
     for (int64_t p = 0; p < L.nn; p++)
-        if ((L.type[p] & NODE_KIND) == NODE_IN) act[(p / L.n) / tr * ncol + (p % L.n) / tc] = 1;
+        if ((L.type[p] & NODE_KIND) == NODE_IN || (L.type[p] & NODE_KIND) == NODE_GHOST)
+            act[(p / L.n) / tr * ncol + (p % L.n) / tc] = 1;
     std::vector<int32_t> t;
     for (int a = 0; a < nr; a++)
         for (int c = 0; c < ncol; c++)
@@ -340,8 +363,10 @@ void build_tables(gcmg_batch *b) {
             BView32 w;
             std::memset(&w, 0, sizeof(w));
             w.v = view<float>(c, l, c->D32[l]);
+            w.u2 = c->D32[l].u2;
             if (l + 1 < nl) {
                 w.c = view<float>(c, l + 1, c->D32[l + 1]);
+                w.c_u2 = c->D32[l + 1].u2;
                 w.cf = c->D32[l + 1].f;
                 w.cg = c->D32[l + 1].gg;
             }
@@ -352,7 +377,7 @@ void build_tables(gcmg_batch *b) {
             if (!t.empty()) ck(cudaMemcpy(dt, t.data(), t.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
             w.tiles = dt;
             ntile.push_back((int)t.size());
-            w.bz = lview<float>(c->G[l].bz, w.v);
+            w.bz = lview<float>(c->G[l].bz, w.v, c->D32[l].r);
             w.jz = lview<float>(c->G[l].jz, w.v);
             w.gt_ptr = c->G[l].gt_ptr;
             w.gt_col = c->G[l].gt_col;
@@ -382,6 +407,7 @@ void build_tables(gcmg_batch *b) {
         w64.f32 = c->D32[0].f;
         w64.g32 = c->D32[0].gg;
         w64.e32 = c->D32[0].u;
+        w64.e32b = c->D32[0].u2;
         w64.dom = d;
         w64.active = b->d_active;
         v64.push_back(w64);
@@ -391,8 +417,15 @@ void build_tables(gcmg_batch *b) {
     auto dense = [&](int view, int64_t count) {
         for (int64_t s = 0; s < count; s += kThreads) items.push_back({view, (int32_t)s});
     };
-    auto add_launch = [&](Launch::Kind k, size_t before, size_t smem) {
-        if (items.size() > before) b->cycle.push_back({k, before, items.size() - before, smem});
+    // u grid per depth (every domain level at one depth has the same history)
+    std::vector<int> cur(kmax + 1, 0);
+    auto add_launch = [&](Launch::Kind k, size_t before, size_t smem, int cu = 0, int ccu = 0) {
+        if (items.size() > before) {
+            Launch L{k, before, items.size() - before, smem};
+            L.cur = cu;
+            L.ccur = ccu;
+            b->cycle.push_back(L);
+        }
     };
     const gcmg_params &p0 = b->doms[0]->p;
     auto relax = [&](int k) {
@@ -403,7 +436,8 @@ void build_tables(gcmg_batch *b) {
             const int vi = b->view_of[d][l];
             for (int i = 0; i < ntile[vi]; i++) items.push_back({vi, (int32_t)i});
         }
-        add_launch(Launch::FUSED, s0, 0);
+        add_launch(Launch::FUSED, s0, 0, cur[k]);   // reads grid cur[k], writes the other
+        cur[k] ^= 1;
         for (int which = 0; which < 2; which++) {
             s0 = items.size();
             size_t smem = 0;
@@ -416,7 +450,15 @@ void build_tables(gcmg_batch *b) {
                 for (int c = 0; c < J.ncomp; c++) items.push_back({vi, c});
                 if (J.ncomp) smem = std::max(smem, smem_of(J));
             }
-            add_launch(which ? Launch::JUNCTION : Launch::BOUNDARY, s0, smem);
+            add_launch(which ? Launch::JUNCTION : Launch::BOUNDARY, s0, smem, cur[k]);
+            if (!which) {   // the boundary blocks' write-back, once all of them have staged
+                s0 = items.size();
+                for (int d = 0; d < nd; d++) {
+                    const int l = (int)b->doms[d]->H.size() - 1 - k;
+                    if (l >= 0) dense(b->view_of[d][l], v32[b->view_of[d][l]].bz.nwb);
+                }
+                add_launch(Launch::BOUNDARY_COPY, s0, 0, cur[k]);
+            }
         }
         if (p0.junction_solve) {
             s0 = items.size();
@@ -424,7 +466,7 @@ void build_tables(gcmg_batch *b) {
                 const int l = (int)b->doms[d]->H.size() - 1 - k;
                 if (l >= 0) dense(b->view_of[d][l], v32[b->view_of[d][l]].js_n);
             }
-            add_launch(Launch::JS_DEFECT, s0, 0);
+            add_launch(Launch::JS_DEFECT, s0, 0, cur[k]);
             s0 = items.size();
             for (int d = 0; d < nd; d++) {
                 const int l = (int)b->doms[d]->H.size() - 1 - k;
@@ -432,17 +474,18 @@ void build_tables(gcmg_batch *b) {
                 const int vi = b->view_of[d][l];
                 for (int r = 0; r < v32[vi].js_n; r += kJsRows) items.push_back({vi, (int32_t)r});
             }
-            add_launch(Launch::JS_APPLY, s0, 0);
+            add_launch(Launch::JS_APPLY, s0, 0, cur[k]);
         }
     };
     for (int k = kmax; k >= 1; k--) {
+        cur[k] = 0;   // a level starts from u = 0 in its first grid
         for (int r = 0; r < p0.nu1; r++) relax(k);
         size_t s0 = items.size();
         for (int d = 0; d < nd; d++) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
             if (l >= 0) dense(b->view_of[d][l], std::max<int64_t>(b->doms[d]->H[l + 1].nn, b->doms[d]->H[l + 1].ng()));
         }
-        add_launch(Launch::DESCEND, s0, 0);
+        add_launch(Launch::DESCEND, s0, 0, cur[k]);
     }
     {
         size_t s0 = items.size();
@@ -462,9 +505,10 @@ void build_tables(gcmg_batch *b) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
             if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].nn);
         }
-        add_launch(Launch::PROLONG, s0, 0);
+        add_launch(Launch::PROLONG, s0, 0, cur[k], cur[k - 1]);
         for (int r = 0; r < p0.nu2; r++) relax(k);
     }
+    b->add_cur = cur[kmax];   // every depth ends a cycle with the same grid
     // FP64 level-0 items (view index = domain)
     b->items64_nodes = items.size();
     for (int d = 0; d < nd; d++) dense(d, b->doms[d]->H[0].nn);
@@ -484,7 +528,7 @@ void build_tables(gcmg_batch *b) {
 
 template <int TR, int TC>
 void launch_fused(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
-    kb_fused<TR, TC><<<(unsigned)L.count, 256, 0, s>>>(b->d_v32, b->d_items + L.off);
+    kb_fused<TR, TC><<<(unsigned)L.count, 256, 0, s>>>(b->d_v32, b->d_items + L.off, L.cur);
 }
 
 void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
@@ -497,14 +541,17 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
             else if (b->variant == 1) launch_fused<8, 128>(b, L, s);
             else launch_fused<32, 32>(b, L, s);
             break;
-        case Launch::BOUNDARY: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda); break;
-        case Launch::JUNCTION: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps); break;
-        case Launch::JS_DEFECT: kb_js_defect<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
-        case Launch::JS_APPLY: kb_js_apply<<<n, kJsRows * 32, 0, s>>>(b->d_v32, it); break;
-        case Launch::DESCEND: kb_descend<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::BOUNDARY: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda, L.cur); break;
+        case Launch::BOUNDARY_COPY: kb_local_copyback<<<n, 256, 0, s>>>(b->d_v32, it, L.cur); break;
+        case Launch::JUNCTION:
+            kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps, L.cur);
+            break;
+        case Launch::JS_DEFECT: kb_js_defect<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur); break;
+        case Launch::JS_APPLY: kb_js_apply<<<n, kJsRows * 32, 0, s>>>(b->d_v32, it, L.cur); break;
+        case Launch::DESCEND: kb_descend<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur); break;
         case Launch::ZERO: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 0); break;
         case Launch::COARSE: kb_coarse<<<n, 512, L.smem, s>>>(b->d_v32, it); break;
-        case Launch::PROLONG: kb_prolong<<<n, kThreads, 0, s>>>(b->d_v32, it); break;
+        case Launch::PROLONG: kb_prolong<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.ccur); break;
     }
 }
 
@@ -514,7 +561,7 @@ void step_body(gcmg_batch *b, cudaStream_t s) {
     kb_to_f32<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, 0);
     if (b->n_items64_ghosts) kb_to_f32<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, 1);
     for (const Launch &L : b->cycle) launch_one(b, L, s);
-    kb_add<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in);
+    kb_add<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->add_cur);
     ck(cudaMemsetAsync(b->d_norms, 0, b->doms.size() * sizeof(unsigned long long), s), "memset");
     kb_defect64<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0);
     if (b->n_items64_ghosts) kb_defect64<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1);

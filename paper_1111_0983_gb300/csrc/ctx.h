@@ -25,6 +25,12 @@ struct gcmg_ctx {
     std::vector<DevData<float>> D32;
     bool rhs_set = false;
     bool js64 = false;                      // FP64 junction-solve inverses kept (single relaxations)
+    // the fused coarse cycle (coarse.cu): its first level (-1: per-level
+    // launches), level table on the device, dynamic shared memory
+    int coarse_l0 = -1;
+    double *relax_a = nullptr, *relax_b = nullptr;   // scratch grids of the single-step relaxation
+    void *d_coarse = nullptr;
+    size_t coarse_smem = 0;
     unsigned long long *d_norm = nullptr;   // two slots: defect norm, rhs norm
     unsigned long long *h_norm = nullptr;   // pinned
     // the solve loop as one CUDA graph: a device-side while loop over cycles
@@ -48,6 +54,17 @@ struct gcmg_ctx {
 
 
 namespace gcmg {
+
+// a failed CUDA call, thrown by ck() and turned into GCMG_E_CUDA by the
+// entry points (one type for every translation unit of the library)
+struct CudaFail {
+    cudaError_t e;
+    const char *what;
+};
+
+inline void ck(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw CudaFail{e, what};
+}
 
 template <typename T>
 LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
@@ -76,8 +93,9 @@ LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
 }
 
 template <typename T>
-LocalView<T> lview(const LocalDev &z, const LevelView<T> &v) {
+LocalView<T> lview(const LocalDev &z, const LevelView<T> &v, T *wb = nullptr) {
     LocalView<T> J;
+    J.wb = wb;
     J.ncomp = z.ncomp;
     J.max_nodes = z.max_nodes;
     J.max_int = z.max_int;
@@ -86,6 +104,8 @@ LocalView<T> lview(const LocalDev &z, const LevelView<T> &v) {
     J.node_off = z.node_off; J.wb_cnt = z.wb_cnt; J.lnode = z.lnode;
     J.int_off = z.int_off; J.red_cnt = z.red_cnt; J.int_glob = z.int_glob; J.int_me = z.int_me; J.int_nb = z.int_nb;
     J.gh_off = z.gh_off; J.gh_me = z.gh_me; J.gh_q = z.gh_q; J.gh_stn = z.gh_stn;
+    J.wb_list = z.wb_list;
+    J.nwb = z.nwb;
     J.u = v.u; J.f = v.f; J.gg = v.gg; J.gc = v.gc; J.gw = v.gw;
     J.h2 = v.h2;
     return J;
@@ -102,6 +122,9 @@ void ensure_inverse(gcmg_ctx *c);
 void ensure_junction_solve(gcmg_ctx *c);
 void upload_js(gcmg_ctx *c, int l);
 void upload_inverse(gcmg_ctx *c);
+// the fused coarse end of the V-cycle (coarse.cu)
+void coarse_prepare(gcmg_ctx *c);
+void launch_coarse_cycle(gcmg_ctx *c);
 // Creates a context from prepared levels (uploads everything to the current device).
 gcmg_status create_from_levels(const gcmg_params &p, std::vector<HostLevel> &&H, cudaStream_t stream, gcmg_ctx **out);
 

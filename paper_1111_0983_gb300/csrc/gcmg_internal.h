@@ -121,6 +121,8 @@ struct LocalDev {
     int32_t *gh_off = nullptr, *gh_me = nullptr, *gh_q = nullptr, *gh_stn = nullptr;
     int nzred = 0, nzblack = 0, nzghost = 0;
     int32_t *zred = nullptr, *zblack = nullptr, *zghost = nullptr;
+    int nwb = 0;
+    int32_t *wb_list = nullptr;   // every component's write-back nodes, one flat list
     bool in_smem = true;       // false: relaxed by per-sweep launches over the union lists
 };
 
@@ -152,6 +154,7 @@ struct DevGeom {
 template <typename T>
 struct DevData {
     T *u = nullptr, *f = nullptr, *r = nullptr;   // grids (may be null if unused)
+    T *u2 = nullptr;     // second u grid: the 2D sweep reads one buffer and writes the other
     T *gw = nullptr;     // KMAX * ng ghost weights for the current bc, slot major
     T *gc = nullptr;     // ng relaxation coefficient mu dt
     T *gg = nullptr;     // ng boundary data (level 0) or restricted boundary defect
@@ -192,6 +195,9 @@ struct LocalView {
     const int32_t *int_off, *red_cnt, *int_glob, *int_me, *int_nb;
     const int32_t *gh_off, *gh_me, *gh_q, *gh_stn;
     T *u;
+    T *wb;    // non-null: write-back target (boundary blocks, whose halos overlap); copied into u afterwards
+    const int32_t *wb_list;   // the write-back nodes of all components (nwb)
+    int nwb;
     const T *f, *gg, *gc, *gw;
     T h2;
 };

@@ -81,9 +81,10 @@ __global__ void k_rb_interior(LevelView<T> v, int color) {
 
 // both colours in one pass over the active 2D tiles
 template <typename T, int TR, int TC>
-__global__ void __launch_bounds__(256) k_rb_fused2d(LevelView<T> v, const int32_t *__restrict__ tiles) {
+__global__ void __launch_bounds__(256) k_rb_fused2d(LevelView<T> v, T *__restrict__ out,
+                                                    const int32_t *__restrict__ tiles) {
     pdl_wait();
-    rb_fused2d_body<T, TR, TC>(v, tiles[blockIdx.x]);
+    rb_fused2d_body<T, TR, TC>(v, out, tiles[blockIdx.x]);
 }
 
 // Same update over a compact list of band nodes of one colour (Sec. 3.2).
@@ -275,10 +276,10 @@ void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_rb_fused2d(const LevelView<T> &v, const int32_t *tiles, int ntiles, cudaStream_t s) {
+void launch_rb_fused2d(const LevelView<T> &v, T *out, const int32_t *tiles, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return;
     g_launches++;
-    pdl_launch(k_rb_fused2d<T, TILE_R, TILE_C>, dim3(ntiles), dim3(256), 0, s, v, tiles);
+    pdl_launch(k_rb_fused2d<T, TILE_R, TILE_C>, dim3(ntiles), dim3(256), 0, s, v, out, tiles);
 }
 
 template <typename T>
@@ -425,12 +426,22 @@ size_t local_smem_bytes(const LocalView<T> &J, int dim) {
 bool local_fits_registers(int max_int_per_colour) { return max_int_per_colour <= LOCAL_THREADS * LOCAL_EPT; }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_local_copyback(LocalView<T> J) {
+    pdl_wait();
+    local_copyback<T>(J, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename T>
 void launch_local(const LocalView<T> &J, int dim, int lead_ghost, int reps, cudaStream_t s) {
     if (J.ncomp <= 0 || (reps <= 0 && !lead_ghost)) return;
     g_launches++;
     const size_t smem = local_smem_bytes(J, dim);
     if (dim == 2) pdl_launch(k_local<T, 2>, dim3(J.ncomp), dim3(LOCAL_THREADS), smem, s, J, lead_ghost, reps);
     else pdl_launch(k_local<T, 3>, dim3(J.ncomp), dim3(LOCAL_THREADS), smem, s, J, lead_ghost, reps);
+    if (J.wb) {
+        g_launches++;
+        pdl_launch(k_local_copyback<T>, dim3(blocks_for(J.nwb)), dim3(256), 0, s, J);
+    }
 }
 
 template <typename T>
@@ -460,7 +471,7 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
 #define GCMG_INSTANTIATE(T)                                                                              \
     template void launch_rb<T>(const LevelView<T> &, int, int, cudaStream_t);                            \
     template void launch_rb_list<T>(const LevelView<T> &, int, const int32_t *, int, cudaStream_t);     \
-    template void launch_rb_fused2d<T>(const LevelView<T> &, const int32_t *, int, cudaStream_t);       \
+    template void launch_rb_fused2d<T>(const LevelView<T> &, T *, const int32_t *, int, cudaStream_t);  \
     template void launch_ghost_relax<T>(const LevelView<T> &, int, cudaStream_t);                         \
     template void launch_ghost_relax_list<T>(const LevelView<T> &, int, const int32_t *, int, cudaStream_t); \
     template void launch_defect<T>(const LevelView<T> &, int, bool, unsigned long long *, cudaStream_t); \

@@ -12,8 +12,9 @@ extern std::atomic<long long> g_launches;   // kernels launched by this library
 
 template <typename T>
 void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s);
+// both colours of a 2D sweep over the active tiles: reads v.u, writes out
 template <typename T>
-void launch_rb_fused2d(const LevelView<T> &v, const int32_t *tiles, int ntiles, cudaStream_t s);
+void launch_rb_fused2d(const LevelView<T> &v, T *out, const int32_t *tiles, int ntiles, cudaStream_t s);
 template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s);
 template <typename T>

@@ -61,12 +61,12 @@ __device__ __forceinline__ T neighbour_sum(const T *__restrict__ u, int64_t p, i
 // tile): u staged with a 2-node halo, f and node types with a 1-node halo;
 // red nodes updated on the tile and its 1-node halo (the values the
 // neighbouring tiles compute for their own nodes), then black nodes on the
-// tile; the tile's inside nodes are stored.  Equal to a red half-sweep
-// followed by a black half-sweep over the whole grid.
+// tile; the tile's inside nodes are stored (into a second buffer).  Equal to
+// a red half-sweep followed by a black half-sweep over the whole grid.
 // FP64 form: one flat index over the staged region, f read at inside nodes
 // only (the FP64 pipe, not instruction issue, bounds this form)
 template <typename T, int TR, int TC>
-__device__ __forceinline__ void rb_fused2d_flat(const LevelView<T> &v, int tile) {
+__device__ __forceinline__ void rb_fused2d_flat(const LevelView<T> &v, T *__restrict__ out, int tile) {
     constexpr int UR = TR + 4, UC = TC + 4, FR = TR + 2, FC = TC + 2;
     __shared__ T su[UR][UC];
     __shared__ T sf[FR][FC];
@@ -104,13 +104,13 @@ __device__ __forceinline__ void rb_fused2d_flat(const LevelView<T> &v, int tile)
     __syncthreads();
     for (int idx = threadIdx.x; idx < TR * TC; idx += blockDim.x) {
         const int r = idx / TC, cc = idx - r * TC;
-        if (sk[r + 1][cc + 1] != NODE_IN) continue;
-        v.u[(int64_t)(i0 + r) * v.s0 + (j0 + cc)] = su[r + 2][cc + 2];
+        if (sk[r + 1][cc + 1] == NODE_OUT) continue;   // inside: new value; ghost: carried over
+        out[(int64_t)(i0 + r) * v.s0 + (j0 + cc)] = su[r + 2][cc + 2];
     }
 }
 
 template <typename T, int TR, int TC>
-__device__ __forceinline__ void rb_fused2d_cols(const LevelView<T> &v, int tile) {
+__device__ __forceinline__ void rb_fused2d_cols(const LevelView<T> &v, T *__restrict__ out, int tile) {
     // FP32 form: 256 threads as TY rows x TC columns: a thread owns a column (and the
     // halo columns TC + tx for the first few tx) and steps through rows, so
     // no index is divided and addresses advance by a constant stride
@@ -178,15 +178,18 @@ __device__ __forceinline__ void rb_fused2d_cols(const LevelView<T> &v, int tile)
     __syncthreads();
 #pragma unroll 4
     for (int r = ty; r < TR; r += TY) {
-        if (sk[r + 1][tx + 1] != NODE_IN) continue;
-        v.u[(int64_t)(i0 + r) * v.s0 + (j0 + tx)] = su[r + 2][tx + 2];
+        if (sk[r + 1][tx + 1] == NODE_OUT) continue;   // inside: new value; ghost: carried over
+        out[(int64_t)(i0 + r) * v.s0 + (j0 + tx)] = su[r + 2][tx + 2];
     }
 }
 
+// Reads v.u and writes into out (another buffer): every tile stages the values
+// before the sweep whatever order the tiles run in.  Ghosts of the tile are
+// copied unchanged; tiles cover every inside node and ghost.
 template <typename T, int TR, int TC>
-__device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, int tile) {
-    if constexpr (sizeof(T) == 8) rb_fused2d_flat<T, TR, TC>(v, tile);
-    else rb_fused2d_cols<T, TR, TC>(v, tile);
+__device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, T *__restrict__ out, int tile) {
+    if constexpr (sizeof(T) == 8) rb_fused2d_flat<T, TR, TC>(v, out, tile);
+    else rb_fused2d_cols<T, TR, TC>(v, out, tile);
 }
 
 // ------------------------------------------------------- local programs
@@ -278,8 +281,21 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, int c, int lea
         __syncthreads();
         ghost_sweep();
     }
+    // components whose halos overlap (boundary blocks) write into J.wb, copied
+    // into u by local_copyback once every component has staged its halo, so
+    // the result does not depend on the order in which the components run
+    T *dst = J.wb ? J.wb : J.u;
     const int nw = J.wb_cnt[c];
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) J.u[J.lnode[n0 + i]] = val[i];
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[J.lnode[n0 + i]] = val[i];
+}
+
+// write-back node i of the flat list: u = wb
+template <typename T>
+__device__ __forceinline__ void local_copyback(const LocalView<T> &J, int i) {
+    if (i < J.nwb) {
+        const int32_t p = J.wb_list[i];
+        J.u[p] = J.wb[p];
+    }
 }
 
 // ------------------------------------------------------------------ defect

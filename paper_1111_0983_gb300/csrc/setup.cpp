@@ -796,8 +796,11 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
         if (dim == 2) {
             const int tr = (L.n + TILE_R - 1) / TILE_R, tc = (L.n + TILE_C - 1) / TILE_C;
             std::vector<uint8_t> active((size_t)tr * tc, 0);
+            // tiles holding inside nodes or ghosts (the sweep writes the one
+            // and carries the other into the other buffer)
             for (int64_t p = 0; p < L.nn; p++)
-                if ((L.type[p] & NODE_KIND) == NODE_IN) active[(p / L.n) / TILE_R * tc + (p % L.n) / TILE_C] = 1;
+                if ((L.type[p] & NODE_KIND) == NODE_IN || (L.type[p] & NODE_KIND) == NODE_GHOST)
+                    active[(p / L.n) / TILE_R * tc + (p % L.n) / TILE_C] = 1;
             for (int a = 0; a < tr; a++)
                 for (int b = 0; b < tc; b++)
                     if (active[(size_t)a * tc + b]) L.tiles.push_back((a << 16) | b);

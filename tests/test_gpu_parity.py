@@ -247,3 +247,23 @@ def test_nan_rhs_reports_noconv():
     u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
     st = S.solve(u)
     assert not st["converged"]
+
+
+@pytest.mark.parametrize("P,n,nc", [(inputs.flower(), 1025, 33), (inputs.star(27), 257, 33),
+                                    (inputs.disk(), 65, 17)])
+def test_fused_coarse_cycle_equals_per_level_launches(P, n, nc):
+    """The coarse end of the FP32 V-cycle in one cluster launch runs the same
+    steps in the same order as one launch per step: the same solution bit for
+    bit and the same residual history."""
+    sols, hists = [], []
+    for fused in (0, 257):
+        S = solver_for(P, n, nc, rtol=1e-10, max_cycles=100, precision=1, fused_coarse_n=fused)
+        set_problem_rhs(S, P, n)
+        u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+        st = S.solve(u)
+        assert st["converged"]
+        sols.append(host(u))
+        hists.append(st["rel"])
+        S.close()
+    assert np.array_equal(sols[0], sols[1])
+    assert np.array_equal(hists[0], hists[1])
