@@ -518,7 +518,10 @@ void upload_inverse(gcmg_ctx *c) {
 void upload_js(gcmg_ctx *c, int l) {
     const HostLevel &L = c->H[l];
     DevGeom &g = c->G[l];
-    for (int32_t **a : {&g.js_node, &g.js_ghost, &g.js_comp, &g.js_off}) { free_tracked(c, *a); *a = nullptr; }
+    for (int32_t **a : {&g.js_node, &g.js_ghost, &g.js_comp, &g.js_off, &g.js_roff, &g.js_rpos}) {
+        free_tracked(c, *a);
+        *a = nullptr;
+    }
     free_tracked(c, g.js_aoff);
     g.js_aoff = nullptr;
     auto drop = [&](auto &D) {
@@ -531,24 +534,52 @@ void upload_js(gcmg_ctx *c, int l) {
     if (!c->D32.empty()) drop(c->D32[l]);
     g.js_n = (int)L.js_node.size();
     g.js_ncomp = L.js_off.empty() ? 0 : (int)L.js_off.size() - 1;
+    g.js_rlen = 0;
     if (g.js_n == 0) return;
-    std::vector<int32_t> comp(g.js_n);
-    for (int k = 0; k < g.js_ncomp; k++)
-        for (int i = L.js_off[k]; i < L.js_off[k + 1]; i++) comp[i] = k;
+    // padded device layout: component c's rows have mp = m rounded up to a
+    // multiple of 4 entries, its defects occupy mp slots from roff[c]
+    std::vector<int32_t> comp(g.js_n), rpos(g.js_n), roff(g.js_ncomp + 1);
+    std::vector<int64_t> aoff(g.js_ncomp + 1);
+    int64_t na = 0;
+    int32_t nr = 0;
+    for (int k = 0; k < g.js_ncomp; k++) {
+        const int m = L.js_off[k + 1] - L.js_off[k], mp = (m + 3) & ~3;
+        aoff[k] = na;
+        roff[k] = nr;
+        for (int i = 0; i < m; i++) {
+            comp[L.js_off[k] + i] = k;
+            rpos[L.js_off[k] + i] = nr + i;
+        }
+        na += (int64_t)m * mp;
+        nr += mp;
+    }
+    aoff[g.js_ncomp] = na;
+    roff[g.js_ncomp] = nr;
+    g.js_rlen = nr;
+    std::vector<double> inv((size_t)na, 0.0);
+    for (int k = 0; k < g.js_ncomp; k++) {
+        const int m = L.js_off[k + 1] - L.js_off[k], mp = (m + 3) & ~3;
+        for (int i = 0; i < m; i++)
+            std::copy_n(L.js_inv.begin() + L.js_aoff[k] + (int64_t)i * m, m, inv.begin() + aoff[k] + (int64_t)i * mp);
+    }
     g.js_node = upload<int32_t>(c, L.js_node.data(), L.js_node.size());
     g.js_ghost = upload<int32_t>(c, L.js_ghost.data(), L.js_ghost.size());
     g.js_comp = upload<int32_t>(c, comp.data(), comp.size());
     g.js_off = upload<int32_t>(c, L.js_off.data(), L.js_off.size());
-    g.js_aoff = upload<int64_t>(c, L.js_aoff.data(), L.js_aoff.size());
-    // FP64 for FP64 cycles and single relaxations (gcmg_relax), FP32 for FP32 cycles
+    g.js_roff = upload<int32_t>(c, roff.data(), roff.size());
+    g.js_rpos = upload<int32_t>(c, rpos.data(), rpos.size());
+    g.js_aoff = upload<int64_t>(c, aoff.data(), aoff.size());
+    // FP64 for FP64 cycles and single relaxations (gcmg_relax), FP32 for FP32
+    // cycles; the defect vectors start at zero and their pads stay zero
     if (c->p.precision == 0 || c->js64) {
-        c->D64[l].js_inv = upload<double>(c, L.js_inv.data(), L.js_inv.size());
-        c->D64[l].js_r = dalloc<double>(c, g.js_n);
+        const std::vector<double> zero(nr, 0.0);
+        c->D64[l].js_inv = upload<double>(c, inv.data(), inv.size());
+        c->D64[l].js_r = upload<double>(c, zero.data(), zero.size());
     }
     if (!c->D32.empty()) {
-        std::vector<float> inv(L.js_inv.begin(), L.js_inv.end());
-        c->D32[l].js_inv = upload<float>(c, inv.data(), inv.size());
-        c->D32[l].js_r = dalloc<float>(c, g.js_n);
+        const std::vector<float> inv32(inv.begin(), inv.end()), zero(nr, 0.f);
+        c->D32[l].js_inv = upload<float>(c, inv32.data(), inv32.size());
+        c->D32[l].js_r = upload<float>(c, zero.data(), zero.size());
     }
     ck(cudaStreamSynchronize(c->stream), "sync");   // the staging vectors die at return
 }
@@ -852,12 +883,10 @@ gcmg_status gcmg_relax(gcmg_ctx *c, int l, double *u, const double *f, const dou
         if (c->p.junction_solve && !c->js64) {   // FP64 inverses for FP64 relaxations
             c->js64 = true;
             for (int k = 0; k < (int)c->H.size(); k++) {
-                const HostLevel &L = c->H[k];
-                if (L.js_node.empty() || c->D64[k].js_inv) continue;
-                c->D64[k].js_inv = upload<double>(c, L.js_inv.data(), L.js_inv.size());
-                c->D64[k].js_r = dalloc<double>(c, L.js_node.size());
+                if (c->H[k].js_node.empty() || c->D64[k].js_inv) continue;
+                destroy_graph(c);   // a captured graph holds the arrays reallocated below
+                upload_js(c, k);
             }
-            ck(cudaStreamSynchronize(c->stream), "sync");
         }
         // the sweep writes into a scratch grid (initialised with u), the other
         // steps work there, and the result goes back into u

@@ -36,6 +36,7 @@ struct BItem {
     int32_t start;   // tile / component / first node / first ghost / block
 };
 
+
 // one level of one domain, in FP32 (the cycle precision of the batch)
 struct BView32 {
     LevelView<float> v;      // this level (v.u: its first u grid)
@@ -52,7 +53,7 @@ struct BView32 {
     int dom;
     const int *active;       // per-domain flag: still iterating
     // exact junction solve of this level
-    const int32_t *js_node, *js_ghost, *js_comp, *js_off;
+    const int32_t *js_node, *js_ghost, *js_comp, *js_off, *js_roff, *js_rpos;
     const int64_t *js_aoff;
     const float *js_inv;
     float *js_r;
@@ -68,6 +69,15 @@ struct BView64 {
 };
 
 constexpr int kThreads = 256;
+
+// A dense item covers npt * kThreads consecutive indexes (nodes, ghosts,
+// rows): thread t takes start + e * kThreads + t for e < npt.  npt is chosen
+// per launch (launch argument): large launches take several indexes a thread
+// so that the chain item -> view -> active flag is paid once for all of them.
+template <class F>
+__device__ __forceinline__ void for_span(const BItem &b, int npt, F &&f) {
+    for (int e = 0; e < npt; e++) f((int64_t)b.start + (int64_t)e * kThreads + threadIdx.x);
+}
 constexpr int kCoarseBlocks = 4;     // CTAs per domain for the coarsest solve
 constexpr int kVariants = 3;         // tile shapes of the fused sweep
 const int kTileR[kVariants] = {16, 8, 32};
@@ -89,78 +99,79 @@ __global__ void __launch_bounds__(256) kb_fused(const BView32 *__restrict__ V, c
 }
 
 __global__ void __launch_bounds__(256) kb_local_copyback(const BView32 *__restrict__ V, const BItem *__restrict__ it,
-                                                         int cur) {
+                                                         int cur, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
-    LocalView<float> J = V[b.view].bz;
-    J.u = ugrid(V[b.view], cur);
-    local_copyback<float>(J, b.start + threadIdx.x);
+    float *u = ugrid(V[b.view], cur);
+    for_span(b, npt, [&](int64_t i) { local_copyback<float>(V[b.view].bz, u, (int)i); });
 }
 
-__global__ void __launch_bounds__(LOCAL_THREADS) kb_local(const BView32 *__restrict__ V, const BItem *__restrict__ it,
-                                                          int junction, int lead_ghost, int reps, int cur) {
+__global__ void __launch_bounds__(LOCAL_THREADS, 2) kb_local(const BView32 *__restrict__ V,
+                                                             const BItem *__restrict__ it, int junction,
+                                                             int lead_ghost, int reps, int cur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
-    LocalView<float> J = junction ? V[b.view].jz : V[b.view].bz;
-    J.u = ugrid(V[b.view], cur);
-    local_body<float, 2>(J, b.start, lead_ghost, reps);
+    const LocalView<float> &J = junction ? V[b.view].jz : V[b.view].bz;
+    float *u = ugrid(V[b.view], cur);
+    local_body<float, 2>(J, u, J.wb ? J.wb : u, b.start, lead_ghost, reps);
 }
 
-// exact junction solve: defects of the solved equations (256 rows per item),
-// then u += A_ZZ^-1 r (one warp per row, kJsRows rows per item)
-constexpr int kJsRows = 8;
+// exact junction solve: defects of the solved equations (dense items), then
+// u += A_ZZ^-1 r (kJsWarpRows rows a warp, kJsRows rows an item)
+constexpr int kJsWarpRows = 4;
+constexpr int kJsRows = 8 * kJsWarpRows;
 
-__global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur) {
+__global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     LevelView<float> v = w.v;
     v.u = ugrid(w, cur);
-    const int k = b.start + threadIdx.x;
-    if (k < w.js_n) w.js_r[k] = js_defect<float, 2>(v, w.js_node[k], w.js_ghost[k]);
+    for_span(b, npt, [&](int64_t k) {
+        if (k < w.js_n) w.js_r[w.js_rpos[k]] = js_defect<float, 2>(v, w.js_node[k], w.js_ghost[k]);
+    });
 }
 
-__global__ void __launch_bounds__(kJsRows * 32) kb_js_apply(const BView32 *__restrict__ V,
+__global__ void __launch_bounds__(256) kb_js_apply(const BView32 *__restrict__ V,
                                                             const BItem *__restrict__ it, int cur) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
-    const int k = b.start + (threadIdx.x >> 5);
-    if (k < w.js_n)
-        js_apply_row<float>(ugrid(w, cur), w.js_node, w.js_comp, w.js_off, w.js_aoff, w.js_inv, w.js_r, k,
-                            threadIdx.x & 31);
+    const int k0 = b.start + (threadIdx.x >> 5) * kJsWarpRows;
+    js_apply_span<float, kJsWarpRows>(ugrid(w, cur), w.js_node, w.js_comp, w.js_off, w.js_aoff, w.js_roff, w.js_inv,
+                                      w.js_r, k0, min(k0 + kJsWarpRows, w.js_n), threadIdx.x & 31);
 }
 
 // defect, restriction with the coarse-ghost transfer, and zero coarse u in
-// one pass over the coarser level's nodes and ghosts
-// defect, restriction with the coarse-ghost transfer, and zero coarse u in
 // one pass over the coarser level's nodes and ghosts (fine u in grid `cur`,
 // coarse u = 0 into its first grid)
-__global__ void kb_descend(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur) {
+__global__ void kb_descend(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
     LevelView<float> v = w.v;
     v.u = ugrid(w, cur);
-    descend_item<float, 2>(v, w.c, w.cf, w.cg, w.c.u, w.gt_ptr, w.gt_col, w.gt_val, (int64_t)b.start + threadIdx.x);
+    for_span(b, npt, [&](int64_t i) {
+        descend_item<float, 2>(v, w.c, w.cf, w.cg, w.c.u, w.gt_ptr, w.gt_col, w.gt_val, i);
+    });
 }
 
 // zero u of the view's level (coarse = 0) or of its coarser level (coarse = 1)
-__global__ void kb_zero(const BView32 *__restrict__ V, const BItem *__restrict__ it, int coarse) {
+__global__ void kb_zero(const BView32 *__restrict__ V, const BItem *__restrict__ it, int coarse, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const LevelView<float> &v = coarse ? V[b.view].c : V[b.view].v;
-    const int64_t p = (int64_t)b.start + threadIdx.x;
-    if (p < v.nn) v.u[p] = 0.f;
+    for_span(b, npt, [&](int64_t p) { if (p < v.nn) v.u[p] = 0.f; });
 }
 
-__global__ void kb_prolong(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur, int ccur) {
+__global__ void kb_prolong(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur, int ccur,
+                           int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
-    const int64_t p = (int64_t)b.start + threadIdx.x;
     float *e = ccur ? w.c_u2 : w.c.u;
-    if (p < w.v.nn) prolong_node<float, 2>(w.v, w.c, e, ugrid(w, cur), true, p);
+    float *u = ugrid(w, cur);
+    for_span(b, npt, [&](int64_t p) { if (p < w.v.nn) prolong_node<float, 2>(w.v, w.c, e, u, true, p); });
 }
 
 __global__ void kb_coarse(const BView32 *__restrict__ V, const BItem *__restrict__ it) {
@@ -171,64 +182,68 @@ __global__ void kb_coarse(const BView32 *__restrict__ V, const BItem *__restrict
 }
 
 // FP64 level 0: defect with per-domain norms (nodes, then ghosts)
+// largest |x| over a thread's indexes; NaN wins
+__device__ __forceinline__ double max_abs(double m, double x) {
+    double a = fabs(x);
+    if (a != a) a = __longlong_as_double(0x7ff0000000000000ll);
+    return a > m ? a : m;
+}
+
 __global__ void kb_defect64(const BView64 *__restrict__ V, const BItem *__restrict__ it, unsigned long long *norms,
-                            int ghosts) {
+                            int ghosts, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;   // uniform per block
     const LevelView<double> &v = V[b.view].v;
-    double val = 0.0;
+    double m = 0.0;
     if (!ghosts) {
-        const int64_t p = (int64_t)b.start + threadIdx.x;
-        if (p < v.nn) val = defect_node<double, 2>(v, p, false);
+        for_span(b, npt, [&](int64_t p) { if (p < v.nn) m = max_abs(m, defect_node<double, 2>(v, p, false)); });
     } else {
-        const int q = b.start + threadIdx.x;
-        if (q < v.ng) val = defect_ghost_item<double, 9>(v, q);
+        for_span(b, npt, [&](int64_t q) { if (q < v.ng) m = max_abs(m, defect_ghost_item<double, 9>(v, (int)q)); });
     }
-    reduce_norm(norms + V[b.view].dom, val);
+    reduce_norm(norms + V[b.view].dom, m);
 }
 
 // ||(f, g)|| per domain
 __global__ void kb_rhs_norm(const BView64 *__restrict__ V, const BItem *__restrict__ it, unsigned long long *norms,
-                            int ghosts) {
+                            int ghosts, int npt) {
     const BItem b = it[blockIdx.x];
     const LevelView<double> &v = V[b.view].v;
-    double val = 0.0;
+    double m = 0.0;
     if (!ghosts) {
-        const int64_t p = (int64_t)b.start + threadIdx.x;
-        if (p < v.nn && (v.type[p] & NODE_KIND) == NODE_IN) val = v.f[p];
+        for_span(b, npt, [&](int64_t p) { if (p < v.nn && (v.type[p] & NODE_KIND) == NODE_IN) m = max_abs(m, v.f[p]); });
     } else {
-        const int q = b.start + threadIdx.x;
-        if (q < v.ng) val = v.gg[q];
+        for_span(b, npt, [&](int64_t q) { if (q < v.ng) m = max_abs(m, v.gg[q]); });
     }
-    reduce_norm(norms + V[b.view].dom, val);
+    reduce_norm(norms + V[b.view].dom, m);
 }
 
 // FP64 defect -> FP32 right-hand side; e32 = 0
-__global__ void kb_to_f32(const BView64 *__restrict__ V, const BItem *__restrict__ it, int ghosts) {
+__global__ void kb_to_f32(const BView64 *__restrict__ V, const BItem *__restrict__ it, int ghosts, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView64 &w = V[b.view];
     if (!ghosts) {
-        const int64_t p = (int64_t)b.start + threadIdx.x;
-        if (p < w.v.nn) {
+        for_span(b, npt, [&](int64_t p) {
+            if (p >= w.v.nn) return;
             w.f32[p] = ((w.v.type[p] & NODE_KIND) == NODE_IN) ? (float)w.v.r[p] : 0.f;
             w.e32[p] = 0.f;
-        }
+        });
     } else {
-        const int q = b.start + threadIdx.x;
-        if (q < w.v.ng) w.g32[q] = (float)w.v.r[w.v.gnode[q]];
+        for_span(b, npt, [&](int64_t q) { if (q < w.v.ng) w.g32[q] = (float)w.v.r[w.v.gnode[q]]; });
     }
 }
 
 // u64 += e32 on Omega_h u Gamma_h
-__global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ it, int cur) {
+__global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ it, int cur, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView64 &w = V[b.view];
-    const int64_t p = (int64_t)b.start + threadIdx.x;
-    if (p >= w.v.nn) return;
-    const uint8_t k = w.v.type[p] & NODE_KIND;
-    if (k == NODE_IN || k == NODE_GHOST) w.v.u[p] += (double)(cur ? w.e32b : w.e32)[p];
+    const float *e = cur ? w.e32b : w.e32;
+    for_span(b, npt, [&](int64_t p) {
+        if (p >= w.v.nn) return;
+        const uint8_t k = w.v.type[p] & NODE_KIND;
+        if (k == NODE_IN || k == NODE_GHOST) w.v.u[p] += (double)e[p];
+    });
 }
 
 // end of one refinement step: per-domain relative residual, loop condition
@@ -261,6 +276,7 @@ struct Launch {
     size_t off, count;
     size_t smem;
     int cur = 0, ccur = 0;   // which u grid holds u (this level, the next coarser one)
+    int npt = 1;             // indexes a thread of a dense item
 };
 
 }  // namespace
@@ -281,6 +297,7 @@ struct gcmg_batch {
     std::vector<int32_t *> tile_bufs;         // tile lists per view for the selected shape
     std::vector<Launch> cycle;                // FP32 V-cycle over all domains
     size_t items64_nodes = 0, items64_ghosts = 0, n_items64_nodes = 0, n_items64_ghosts = 0;
+    int npt64_nodes = 1, npt64_ghosts = 1;
     unsigned long long *d_norms = nullptr;
     double *d_r0 = nullptr, *d_rel = nullptr;
     int *d_m = nullptr;
@@ -394,6 +411,8 @@ void build_tables(gcmg_batch *b) {
             w.js_comp = c->G[l].js_comp;
             w.js_off = c->G[l].js_off;
             w.js_aoff = c->G[l].js_aoff;
+            w.js_roff = c->G[l].js_roff;
+            w.js_rpos = c->G[l].js_rpos;
             w.js_inv = c->D32[l].js_inv;
             w.js_r = c->D32[l].js_r;
             b->view_of[d].push_back((int)v32.size());
@@ -414,18 +433,42 @@ void build_tables(gcmg_batch *b) {
     }
     // items
     std::vector<BItem> items;
+    // dense ranges of the launch being built; emit_dense turns them into
+    // items of npt * kThreads indexes, npt doubling (up to 8) while the
+    // launch keeps at least four waves of 8 CTAs on every SM
+    int nsm = 0;
+    ck(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device), "attr");
+    const int64_t fill = (int64_t)nsm * 8 * 4;
+    std::vector<std::pair<int, int64_t>> pending;
     auto dense = [&](int view, int64_t count) {
-        for (int64_t s = 0; s < count; s += kThreads) items.push_back({view, (int32_t)s});
+        if (count > 0) pending.push_back({view, count});
+    };
+    auto emit_dense = [&]() {
+        int64_t blocks = 0;
+        for (const auto &pc : pending) blocks += (pc.second + kThreads - 1) / kThreads;
+        int npt = 1;
+        while (npt < 8 && blocks / (2 * npt) >= fill) npt *= 2;
+        for (const auto &pc : pending)
+            for (int64_t s = 0; s < pc.second; s += (int64_t)kThreads * npt) items.push_back({pc.first, (int32_t)s});
+        pending.clear();
+        return npt;
     };
     // u grid per depth (every domain level at one depth has the same history)
     std::vector<int> cur(kmax + 1, 0);
-    auto add_launch = [&](Launch::Kind k, size_t before, size_t smem, int cu = 0, int ccu = 0) {
+    auto add_launch = [&](Launch::Kind k, size_t before, size_t smem, int cu = 0, int ccu = 0, int npt = 1) {
         if (items.size() > before) {
             Launch L{k, before, items.size() - before, smem};
             L.cur = cu;
             L.ccur = ccu;
+            L.npt = npt;
             b->cycle.push_back(L);
         }
+    };
+    // a launch over the pending dense ranges
+    auto add_dense = [&](Launch::Kind k, int cu = 0, int ccu = 0) {
+        const size_t before = items.size();
+        const int npt = emit_dense();
+        add_launch(k, before, 0, cu, ccu, npt);
     };
     const gcmg_params &p0 = b->doms[0]->p;
     auto relax = [&](int k) {
@@ -452,21 +495,19 @@ void build_tables(gcmg_batch *b) {
             }
             add_launch(which ? Launch::JUNCTION : Launch::BOUNDARY, s0, smem, cur[k]);
             if (!which) {   // the boundary blocks' write-back, once all of them have staged
-                s0 = items.size();
                 for (int d = 0; d < nd; d++) {
                     const int l = (int)b->doms[d]->H.size() - 1 - k;
                     if (l >= 0) dense(b->view_of[d][l], v32[b->view_of[d][l]].bz.nwb);
                 }
-                add_launch(Launch::BOUNDARY_COPY, s0, 0, cur[k]);
+                add_dense(Launch::BOUNDARY_COPY, cur[k]);
             }
         }
         if (p0.junction_solve) {
-            s0 = items.size();
             for (int d = 0; d < nd; d++) {
                 const int l = (int)b->doms[d]->H.size() - 1 - k;
                 if (l >= 0) dense(b->view_of[d][l], v32[b->view_of[d][l]].js_n);
             }
-            add_launch(Launch::JS_DEFECT, s0, 0, cur[k]);
+            add_dense(Launch::JS_DEFECT, cur[k]);
             s0 = items.size();
             for (int d = 0; d < nd; d++) {
                 const int l = (int)b->doms[d]->H.size() - 1 - k;
@@ -480,18 +521,16 @@ void build_tables(gcmg_batch *b) {
     for (int k = kmax; k >= 1; k--) {
         cur[k] = 0;   // a level starts from u = 0 in its first grid
         for (int r = 0; r < p0.nu1; r++) relax(k);
-        size_t s0 = items.size();
         for (int d = 0; d < nd; d++) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
             if (l >= 0) dense(b->view_of[d][l], std::max<int64_t>(b->doms[d]->H[l + 1].nn, b->doms[d]->H[l + 1].ng()));
         }
-        add_launch(Launch::DESCEND, s0, 0, cur[k]);
+        add_dense(Launch::DESCEND, cur[k]);
     }
     {
-        size_t s0 = items.size();
         for (int d = 0; d < nd; d++) dense(b->view_of[d].back(), b->doms[d]->H.back().nn);
-        add_launch(Launch::ZERO, s0, 0);
-        s0 = items.size();
+        add_dense(Launch::ZERO);
+        const size_t s0 = items.size();
         size_t smem = 0;
         for (int d = 0; d < nd; d++) {
             for (int blk = 0; blk < kCoarseBlocks; blk++) items.push_back({b->view_of[d].back(), blk});
@@ -500,21 +539,22 @@ void build_tables(gcmg_batch *b) {
         add_launch(Launch::COARSE, s0, smem);
     }
     for (int k = 1; k <= kmax; k++) {
-        size_t s0 = items.size();
         for (int d = 0; d < nd; d++) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
             if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].nn);
         }
-        add_launch(Launch::PROLONG, s0, 0, cur[k], cur[k - 1]);
+        add_dense(Launch::PROLONG, cur[k], cur[k - 1]);
         for (int r = 0; r < p0.nu2; r++) relax(k);
     }
     b->add_cur = cur[kmax];   // every depth ends a cycle with the same grid
     // FP64 level-0 items (view index = domain)
     b->items64_nodes = items.size();
     for (int d = 0; d < nd; d++) dense(d, b->doms[d]->H[0].nn);
+    b->npt64_nodes = emit_dense();
     b->n_items64_nodes = items.size() - b->items64_nodes;
     b->items64_ghosts = items.size();
     for (int d = 0; d < nd; d++) dense(d, b->doms[d]->H[0].ng());
+    b->npt64_ghosts = emit_dense();
     b->n_items64_ghosts = items.size() - b->items64_ghosts;
     ck(cudaMalloc(&b->d_v32, v32.size() * sizeof(BView32)), "cudaMalloc");
     ck(cudaMalloc(&b->d_v64, v64.size() * sizeof(BView64)), "cudaMalloc");
@@ -542,29 +582,31 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
             else launch_fused<32, 32>(b, L, s);
             break;
         case Launch::BOUNDARY: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda, L.cur); break;
-        case Launch::BOUNDARY_COPY: kb_local_copyback<<<n, 256, 0, s>>>(b->d_v32, it, L.cur); break;
+        case Launch::BOUNDARY_COPY: kb_local_copyback<<<n, 256, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
         case Launch::JUNCTION:
             kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps, L.cur);
             break;
-        case Launch::JS_DEFECT: kb_js_defect<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur); break;
-        case Launch::JS_APPLY: kb_js_apply<<<n, kJsRows * 32, 0, s>>>(b->d_v32, it, L.cur); break;
-        case Launch::DESCEND: kb_descend<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur); break;
-        case Launch::ZERO: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 0); break;
+        case Launch::JS_DEFECT: kb_js_defect<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
+        case Launch::JS_APPLY: kb_js_apply<<<n, 256, 0, s>>>(b->d_v32, it, L.cur); break;
+        case Launch::DESCEND: kb_descend<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
+        case Launch::ZERO: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 0, L.npt); break;
         case Launch::COARSE: kb_coarse<<<n, 512, L.smem, s>>>(b->d_v32, it); break;
-        case Launch::PROLONG: kb_prolong<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.ccur); break;
+        case Launch::PROLONG: kb_prolong<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.ccur, L.npt); break;
     }
 }
 
 // one refinement step of every domain, then the FP64 defect norms
 void step_body(gcmg_batch *b, cudaStream_t s) {
     const BItem *in = b->d_items + b->items64_nodes, *ig = b->d_items + b->items64_ghosts;
-    kb_to_f32<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, 0);
-    if (b->n_items64_ghosts) kb_to_f32<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, 1);
+    kb_to_f32<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, 0, b->npt64_nodes);
+    if (b->n_items64_ghosts)
+        kb_to_f32<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, 1, b->npt64_ghosts);
     for (const Launch &L : b->cycle) launch_one(b, L, s);
-    kb_add<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->add_cur);
+    kb_add<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->add_cur, b->npt64_nodes);
     ck(cudaMemsetAsync(b->d_norms, 0, b->doms.size() * sizeof(unsigned long long), s), "memset");
-    kb_defect64<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0);
-    if (b->n_items64_ghosts) kb_defect64<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1);
+    kb_defect64<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0, b->npt64_nodes);
+    if (b->n_items64_ghosts)
+            kb_defect64<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1, b->npt64_ghosts);
 }
 
 long long step_kernels(const gcmg_batch *b) {
@@ -805,8 +847,9 @@ gcmg_status gcmg_batch_solve(gcmg_batch *b, gcmg_stats *stats, int *steps) {
             ck(cudaMemsetAsync(c->D64[0].u, 0, c->H[0].nn * sizeof(double), s), "memset");
         // ||r0|| = ||(f, g)|| per domain
         ck(cudaMemsetAsync(b->d_norms, 0, nd * sizeof(unsigned long long), s), "memset");
-        kb_rhs_norm<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0);
-        if (b->n_items64_ghosts) kb_rhs_norm<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1);
+        kb_rhs_norm<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0, b->npt64_nodes);
+        if (b->n_items64_ghosts)
+            kb_rhs_norm<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1, b->npt64_ghosts);
         std::vector<unsigned long long> bits(nd);
         ck(cudaMemcpyAsync(bits.data(), b->d_norms, nd * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s), "r0");
         ck(cudaStreamSynchronize(s), "sync");
@@ -818,8 +861,9 @@ gcmg_status gcmg_batch_solve(gcmg_batch *b, gcmg_stats *stats, int *steps) {
         ck(cudaMemcpyAsync(b->d_r0, r0.data(), nd * sizeof(double), cudaMemcpyHostToDevice, s), "r0");
         // defect of u = 0 (the FP64 defect every step starts from)
         ck(cudaMemsetAsync(b->d_norms, 0, nd * sizeof(unsigned long long), s), "memset");
-        kb_defect64<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0);
-        if (b->n_items64_ghosts) kb_defect64<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1);
+        kb_defect64<<<(unsigned)b->n_items64_nodes, kThreads, 0, s>>>(b->d_v64, in, b->d_norms, 0, b->npt64_nodes);
+        if (b->n_items64_ghosts)
+            kb_defect64<<<(unsigned)b->n_items64_ghosts, kThreads, 0, s>>>(b->d_v64, ig, b->d_norms, 1, b->npt64_ghosts);
         ck(cudaGetLastError(), "kernel launch");
         const int zero = 0;
         ck(cudaMemcpyAsync(b->d_m, &zero, sizeof(int), cudaMemcpyHostToDevice, s), "m");

@@ -33,7 +33,7 @@ struct CoarseLevel {
     const int32_t *tiles;
     int ntiles;
     int js_n;
-    const int32_t *js_node, *js_ghost, *js_comp, *js_off;
+    const int32_t *js_node, *js_ghost, *js_comp, *js_off, *js_roff, *js_rpos;
     const int64_t *js_aoff;
     const float *js_inv;
     float *js_r;
@@ -62,23 +62,22 @@ __device__ int cc_relax(const CoarseLevel &L, int cur, int lambda, int rank) {
     }
     cluster_barrier();
     v.u = out;
-    LocalView<float> bz = L.bz;
-    bz.u = out;
+    const LocalView<float> &bz = L.bz;
     for (int cpt = rank; cpt < bz.ncomp; cpt += CC_SIZE) {
-        dev::local_body<float, 2>(bz, cpt, 1, lambda);
+        dev::local_body<float, 2>(bz, out, bz.wb, cpt, 1, lambda);
         __syncthreads();
     }
     cluster_barrier();
     for (int i = rank * CC_THREADS + threadIdx.x; i < bz.nwb; i += CC_SIZE * CC_THREADS)
-        dev::local_copyback<float>(bz, i);
+        dev::local_copyback<float>(bz, out, i);
     cluster_barrier();
     if (L.js_n > 0) {
         for (int k = rank * CC_THREADS + threadIdx.x; k < L.js_n; k += CC_SIZE * CC_THREADS)
-            L.js_r[k] = dev::js_defect<float, 2>(v, L.js_node[k], L.js_ghost[k]);
+            L.js_r[L.js_rpos[k]] = dev::js_defect<float, 2>(v, L.js_node[k], L.js_ghost[k]);
         cluster_barrier();
         constexpr int warps = CC_THREADS / 32;
         for (int row = rank * warps + (threadIdx.x >> 5); row < L.js_n; row += CC_SIZE * warps)
-            dev::js_apply_row<float>(out, L.js_node, L.js_comp, L.js_off, L.js_aoff, L.js_inv, L.js_r, row,
+            dev::js_apply_row<float>(out, L.js_node, L.js_comp, L.js_off, L.js_aoff, L.js_roff, L.js_inv, L.js_r, row,
                                      threadIdx.x & 31);
         cluster_barrier();
     }
@@ -161,6 +160,8 @@ void coarse_prepare(gcmg_ctx *c) {
         L.js_comp = g.js_comp;
         L.js_off = g.js_off;
         L.js_aoff = g.js_aoff;
+        L.js_roff = g.js_roff;
+        L.js_rpos = g.js_rpos;
         L.js_inv = D.js_inv;
         L.js_r = D.js_r;
         L.gt_ptr = g.gt_ptr;

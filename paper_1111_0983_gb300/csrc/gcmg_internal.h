@@ -144,9 +144,15 @@ struct DevGeom {
     int32_t *unk_node = nullptr, *unk_ghost = nullptr;
     std::vector<int> wave;       // host copy of the wavefront offsets
     LocalDev jz, bz;             // junction zone / boundary blocks
-    // exact junction solve: js_n rows in js_ncomp components
+    // exact junction solve: js_n rows in js_ncomp components.  On the device
+    // each component's inverse has rows padded to a multiple of 4 entries
+    // (zeros) and starts at js_aoff[c], a multiple of 4; its defects sit at
+    // js_roff[c] (a multiple of 4) in the padded defect vector, row k's at
+    // js_rpos[k], so that rows and defects are read as 16-byte vectors.
     int js_n = 0, js_ncomp = 0;
     int32_t *js_node = nullptr, *js_ghost = nullptr, *js_comp = nullptr, *js_off = nullptr;
+    int32_t *js_roff = nullptr, *js_rpos = nullptr;
+    int js_rlen = 0;                    // length of the padded defect vector
     int64_t *js_aoff = nullptr;
 };
 
@@ -163,7 +169,7 @@ struct DevData {
     T *gt_val = nullptr; // ghost transfer weights to the next level
     T *Ainv = nullptr;   // nunk * nunk (coarsest level)
     T *js_inv = nullptr; // inverses of the junction-solve components
-    T *js_r = nullptr;   // js_n defects of the junction-solve equations
+    T *js_r = nullptr;   // defects of the junction-solve equations (padded layout, zero pads)
 };
 
 // Kernel view of one level in precision T (passed by value).

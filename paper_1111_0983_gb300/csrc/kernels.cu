@@ -51,13 +51,13 @@ __device__ __forceinline__ bool decode_colour(int n, int color, int64_t t, int64
     const int hc = (n + 1) >> 1;
     int i0, i1 = 0, jj;
     if (D == 2) {
-        i0 = (int)(t / hc);
+        i0 = (int)dev::idx_div(t, hc);
         jj = (int)(t - (int64_t)i0 * hc);
     } else {
-        jj = (int)(t % hc);
-        const int64_t rest = t / hc;
-        i1 = (int)(rest % n);
-        i0 = (int)(rest / n);
+        const int64_t rest = dev::idx_div(t, hc);
+        jj = (int)(t - rest * hc);
+        i0 = (int)dev::idx_div(rest, n);
+        i1 = (int)(rest - (int64_t)i0 * n);
     }
     if (i0 >= n) return false;
     const int last = 2 * jj + ((i0 + i1 + color) & 1);
@@ -140,11 +140,14 @@ __global__ void k_ghost_store(LevelView<T> v) {
     v.u[v.gnode[q]] = v.gtmp[q];
 }
 
-// shared-memory programs (junction zones, 2D boundary blocks), one CTA per component
+// shared-memory programs (junction zones, 2D boundary blocks), one CTA per
+// component; two CTAs per SM for the FP32 2D programs (64 registers, no
+// spills), the FP64 and 3D ones need more registers than that
 template <typename T, int D>
-__global__ void __launch_bounds__(LOCAL_THREADS) k_local(LocalView<T> J, int lead_ghost, int reps) {
+__global__ void __launch_bounds__(LOCAL_THREADS, sizeof(T) == 4 && D == 2 ? 2 : 1)
+    k_local(LocalView<T> J, int lead_ghost, int reps) {
     pdl_wait();
-    local_body<T, D>(J, blockIdx.x, lead_ghost, reps);
+    local_body<T, D>(J, J.u, J.wb ? J.wb : J.u, blockIdx.x, lead_ghost, reps);
 }
 
 // ------------------------------------------------------------------ defect
@@ -388,22 +391,25 @@ void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv,
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads) k_js_defect(LevelView<T> v, const int32_t *__restrict__ node,
-                                                        const int32_t *__restrict__ ghost, T *__restrict__ r, int n) {
+                                                        const int32_t *__restrict__ ghost,
+                                                        const int32_t *__restrict__ rpos, T *__restrict__ r, int n) {
     pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) r[k] = dev::js_defect<T, D>(v, node[k], ghost[k]);
+    if (k < n) r[rpos[k]] = dev::js_defect<T, D>(v, node[k], ghost[k]);
 }
 
-constexpr int kJsRowsPerBlock = 8;   // one warp per row
+constexpr int kJsWarpRows = 4;                      // rows a warp
+constexpr int kJsRowsPerBlock = 8 * kJsWarpRows;     // 8 warps a CTA
 
 template <typename T>
-__global__ void __launch_bounds__(kJsRowsPerBlock * 32)
+__global__ void __launch_bounds__(256)
     k_js_apply(T *__restrict__ u, const int32_t *__restrict__ node, const int32_t *__restrict__ comp,
-               const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const T *__restrict__ inv,
-               const T *__restrict__ r, int n) {
+               const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
+               const T *__restrict__ inv, const T *__restrict__ r, int n) {
     pdl_wait();
-    const int k = blockIdx.x * kJsRowsPerBlock + (threadIdx.x >> 5);
-    if (k < n) dev::js_apply_row<T>(u, node, comp, off, aoff, inv, r, k, threadIdx.x & 31);
+    const int k0 = blockIdx.x * kJsRowsPerBlock + (threadIdx.x >> 5) * kJsWarpRows;
+    dev::js_apply_span<T, kJsWarpRows>(u, node, comp, off, aoff, roff, inv, r, k0, min(k0 + kJsWarpRows, n),
+                                       threadIdx.x & 31);
 }
 
 template <typename T>
@@ -411,10 +417,14 @@ void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv
     const int n = g.js_n;
     if (n <= 0) return;
     g_launches += 2;
-    if (g.dim == 2) pdl_launch(k_js_defect<T, 2>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, r, n);
-    else pdl_launch(k_js_defect<T, 3>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, r, n);
-    pdl_launch(k_js_apply<T>, dim3((unsigned)((n + kJsRowsPerBlock - 1) / kJsRowsPerBlock)),
-               dim3(kJsRowsPerBlock * 32), 0, s, v.u, g.js_node, g.js_comp, g.js_off, g.js_aoff, inv, r, n);
+    if (g.dim == 2)
+        pdl_launch(k_js_defect<T, 2>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, g.js_rpos,
+                   r, n);
+    else
+        pdl_launch(k_js_defect<T, 3>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, g.js_rpos,
+                   r, n);
+    pdl_launch(k_js_apply<T>, dim3((unsigned)((n + kJsRowsPerBlock - 1) / kJsRowsPerBlock)), dim3(256), 0, s, v.u, g.js_node, g.js_comp, g.js_off, g.js_aoff, g.js_roff, inv, r,
+               n);
 }
 
 template <typename T>
@@ -428,7 +438,7 @@ bool local_fits_registers(int max_int_per_colour) { return max_int_per_colour <=
 template <typename T>
 __global__ void __launch_bounds__(256) k_local_copyback(LocalView<T> J) {
     pdl_wait();
-    local_copyback<T>(J, blockIdx.x * blockDim.x + threadIdx.x);
+    local_copyback<T>(J, J.u, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename T>

@@ -200,9 +200,16 @@ __device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, T *__rest
 // (red, black, Jacobi ghosts); the write-back nodes are stored.  Junction
 // zones are components closed under their reads; 2D boundary blocks carry a
 // halo covering the dependency cone of the sweeps, so the written values
-// equal those of the global sweeps.
+// equal those of the global sweeps.  The component is staged from grid
+// `src` and its write-back nodes are stored into `dst` (the same grid for
+// junction zones; for boundary blocks, whose halos overlap, a separate grid
+// that local_copyback copies into u once every block has staged its halo, so
+// the result does not depend on the order in which the blocks run).  The
+// grids are arguments rather than fields of J so that J stays a reference to
+// kernel-parameter or global memory instead of a copy held in registers.
 template <typename T, int D>
-__device__ __forceinline__ void local_body(const LocalView<T> &J, int c, int lead_ghost, int reps) {
+__device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, T *dst, int c, int lead_ghost,
+                                           int reps) {
     constexpr int K = D == 2 ? 9 : 27;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int n0 = J.node_off[c], nl = J.node_off[c + 1] - n0;
@@ -215,7 +222,7 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, int c, int lea
     T *gt = gcv + J.max_gh;
     int *gst = reinterpret_cast<int *>(gt + J.max_gh);   // K per ghost
     int *gme = gst + (size_t)K * J.max_gh;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) val[i] = J.u[J.lnode[n0 + i]];
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) val[i] = src[J.lnode[n0 + i]];
     for (int e = threadIdx.x; e < ngh; e += blockDim.x) {
         const int q = J.gh_q[g0 + e];
         gv[e] = J.gg[q];
@@ -281,20 +288,16 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, int c, int lea
         __syncthreads();
         ghost_sweep();
     }
-    // components whose halos overlap (boundary blocks) write into J.wb, copied
-    // into u by local_copyback once every component has staged its halo, so
-    // the result does not depend on the order in which the components run
-    T *dst = J.wb ? J.wb : J.u;
     const int nw = J.wb_cnt[c];
     for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[J.lnode[n0 + i]] = val[i];
 }
 
 // write-back node i of the flat list: u = wb
 template <typename T>
-__device__ __forceinline__ void local_copyback(const LocalView<T> &J, int i) {
+__device__ __forceinline__ void local_copyback(const LocalView<T> &J, T *u, int i) {
     if (i < J.nwb) {
         const int32_t p = J.wb_list[i];
-        J.u[p] = J.wb[p];
+        u[p] = J.wb[p];
     }
 }
 
@@ -353,25 +356,34 @@ __device__ __forceinline__ unsigned box_mask(int b) {
     return m;
 }
 
-__device__ __forceinline__ double w1d(int iv, int o) {
+// 1D factor of the box weights (exact in any binary precision)
+template <typename T>
+__device__ __forceinline__ T w1d(int iv, int o) {
     switch (iv) {
-        case 0: return o == 0 ? 0.5 : 0.25;
-        case 1: return o == 1 ? 0.0 : 0.5;
-        case 2: return o == -1 ? 0.0 : 0.5;
-        default: return o == 0 ? 1.0 : 0.0;
+        case 0: return o == 0 ? (T)0.5 : (T)0.25;
+        case 1: return o == 1 ? (T)0 : (T)0.5;
+        case 2: return o == -1 ? (T)0 : (T)0.5;
+        default: return o == 0 ? (T)1 : (T)0;
     }
+}
+
+// a / b for non-negative grid indexes: 32-bit division where a fits (every
+// grid the solver accepts), the 64-bit one otherwise
+__device__ __forceinline__ int64_t idx_div(int64_t a, int64_t b) {
+    if (a <= 0x7fffffffll && b <= 0x7fffffffll) return (int64_t)((uint32_t)a / (uint32_t)b);
+    return a / b;
 }
 
 template <int D>
 __device__ __forceinline__ int64_t fine_image(int64_t X, int64_t cs0, int64_t cs1, int64_t fs0, int64_t fs1) {
     int64_t rem = X;
     if (D == 2) {
-        const int64_t j0 = rem / cs0, j1 = rem - j0 * cs0;
+        const int64_t j0 = idx_div(rem, cs0), j1 = rem - j0 * cs0;
         return 2 * j0 * fs0 + 2 * j1;
     }
-    const int64_t j0 = rem / cs0;
+    const int64_t j0 = idx_div(rem, cs0);
     rem -= j0 * cs0;
-    const int64_t j1 = rem / cs1, j2 = rem - j1 * cs1;
+    const int64_t j1 = idx_div(rem, cs1), j2 = rem - j1 * cs1;
     return 2 * j0 * fs0 + 2 * j1 * fs1 + 2 * j2;
 }
 
@@ -405,7 +417,9 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
         }
         if (count == 0) return (T)0;
     }
-    double acc = 0.0;
+    // weights and sum in T: the weights are dyadic or 1/count, an FP32 cycle
+    // keeps its arithmetic on the FP32 pipe
+    T acc = 0;
     for (int c = 0; c < cube; c++) {
         if (!((member >> c) & 1u)) continue;
         int rem = c;
@@ -416,23 +430,23 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
             rem /= 3;
             q += o[a] * (a == D - 1 ? (int64_t)1 : (a == 0 ? F.s0 : F.s1));
         }
-        double w = 0.0;
+        T w = 0;
         if (member == full) {
-            w = 1.0;
-            for (int a = 0; a < D; a++) w *= w1d(0, o[a]);
+            w = 1;
+            for (int a = 0; a < D; a++) w *= w1d<T>(0, o[a]);
         } else {
             for (int b = 0; b < nbox; b++) {
                 const unsigned m = box_mask<D>(b);
                 if ((m & ~member) || __popc(m) != best) continue;
-                double wb = 1.0;
-                for (int a = 0; a < D; a++) wb *= w1d((b >> (2 * a)) & 3, o[a]);
+                T wb = 1;
+                for (int a = 0; a < D; a++) wb *= w1d<T>((b >> (2 * a)) & 3, o[a]);
                 w += wb;
             }
-            w /= count;
+            w /= (T)count;
         }
-        if (w != 0.0) acc += w * (double)value(q);
+        if (w != (T)0) acc += w * value(q);
     }
-    return (T)acc;
+    return acc;
 }
 
 template <typename T, int D>
@@ -525,12 +539,12 @@ __device__ __forceinline__ void prolong_node(const LevelView<T> &F, const LevelV
     }
     int j[3] = {0, 0, 0};
     int64_t rem = p;
-    j[0] = (int)(rem / F.s0);
+    j[0] = (int)idx_div(rem, F.s0);
     rem -= (int64_t)j[0] * F.s0;
     if (D == 2) {
         j[1] = (int)rem;
     } else {
-        j[1] = (int)(rem / F.s1);
+        j[1] = (int)idx_div(rem, F.s1);
         j[2] = (int)(rem - (int64_t)j[1] * F.s1);
     }
     T num = 0, den = 0;
@@ -542,7 +556,7 @@ __device__ __forceinline__ void prolong_node(const LevelView<T> &F, const LevelV
                                   (D == 2 ? (int64_t)(j[1] / 2 + b) : (int64_t)(j[1] / 2 + b) * C.s1 + (j[2] / 2 + c));
                 const uint8_t kc = C.type[X] & NODE_KIND;
                 if (kc != NODE_IN && kc != NODE_GHOST) continue;
-                const T w = (T)(1.0 / (n1 * n2 * n3));
+                const T w = (T)1 / (T)(n1 * n2 * n3);   // a power of two: exact
                 num += w * e[X];
                 den += w;
             }
@@ -570,22 +584,99 @@ __device__ __forceinline__ T js_defect(const LevelView<T> &v, int32_t p, int32_t
     return v.f[p] + lap * v.inv_h2;
 }
 
-// u(node k) += sum_j Ainv_c[k - off_c, j] r[off_c + j] for row k of component
-// c: one warp per row, lanes striding the row.
+// 16-byte vectors of T and their dot product (in component order)
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    static __device__ __forceinline__ float dot(float s, float4 a, float4 b) {
+        s = fmaf(a.x, b.x, s);
+        s = fmaf(a.y, b.y, s);
+        s = fmaf(a.z, b.z, s);
+        return fmaf(a.w, b.w, s);
+    }
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    static __device__ __forceinline__ double dot(double s, double2 a, double2 b) {
+        s = fma(a.x, b.x, s);
+        return fma(a.y, b.y, s);
+    }
+};
+
+// u(node k) += sum_j Ainv_c[k - off_c, j] r_c[j] for rows k0 .. k0 + nr - 1
+// (nr <= R) of one component c, by one warp: each lane takes 16-byte
+// vectors of the padded rows and of the component's padded defects (both
+// 16-byte aligned, zero pads), the defect vector shared by the R rows and
+// U vectors a row in flight.  A lane sums its vectors of a row in index
+// order, whatever R and U, so every row's value is independent of how rows
+// are grouped.
+template <typename T, int R, int U = 2>
+__device__ __forceinline__ void js_apply_rows(T *__restrict__ u, const int32_t *__restrict__ node,
+                                              const int32_t *__restrict__ off, const int64_t *__restrict__ aoff,
+                                              const int32_t *__restrict__ roff, const T *__restrict__ inv,
+                                              const T *__restrict__ r, int c, int k0, int nr, int lane) {
+    using V = typename Vec16<T>::type;
+    const int o = off[c];
+    const int mp = (off[c + 1] - o + 3) & ~3;
+    const V *a = reinterpret_cast<const V *>(inv + aoff[c] + (int64_t)(k0 - o) * mp);
+    const V *rr = reinterpret_cast<const V *>(r + roff[c]);
+    const int nv = mp / Vec16<T>::n, rs = nv;   // row stride in vectors
+    T s[R];
+#pragma unroll
+    for (int i = 0; i < R; i++) s[i] = 0;
+    for (int j0 = lane; j0 < nv; j0 += 32 * U) {
+        V rv[U], av[R][U];
+#pragma unroll
+        for (int e = 0; e < U; e++)
+            if (j0 + 32 * e < nv) {
+                rv[e] = rr[j0 + 32 * e];
+#pragma unroll
+                for (int i = 0; i < R; i++)
+                    if (i < nr) av[i][e] = a[(int64_t)i * rs + j0 + 32 * e];
+            }
+#pragma unroll
+        for (int e = 0; e < U; e++)
+            if (j0 + 32 * e < nv)
+#pragma unroll
+                for (int i = 0; i < R; i++)
+                    if (i < nr) s[i] = Vec16<T>::dot(s[i], av[i][e], rv[e]);
+    }
+#pragma unroll
+    for (int i = 0; i < R; i++) {
+        T t = s[i];
+        for (int w = 16; w > 0; w >>= 1) t += __shfl_xor_sync(0xffffffffu, t, w);
+        if (lane == 0 && i < nr) u[node[k0 + i]] += t;
+    }
+}
+
+// rows k0 .. k1 - 1 of the junction solve (any components) by one warp, in
+// groups of at most R rows of one component
+template <typename T, int R>
+__device__ __forceinline__ void js_apply_span(T *__restrict__ u, const int32_t *__restrict__ node,
+                                              const int32_t *__restrict__ comp, const int32_t *__restrict__ off,
+                                              const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
+                                              const T *__restrict__ inv, const T *__restrict__ r, int k0, int k1,
+                                              int lane) {
+    for (int k = k0; k < k1;) {
+        const int c = comp[k];
+        const int e = min(min(k1, off[c + 1]), k + R);
+        js_apply_rows<T, R>(u, node, off, aoff, roff, inv, r, c, k, e - k, lane);
+        k = e;
+    }
+}
+
+// one row k (the form of the fused coarse cycle)
 template <typename T>
 __device__ __forceinline__ void js_apply_row(T *__restrict__ u, const int32_t *__restrict__ node,
                                              const int32_t *__restrict__ comp, const int32_t *__restrict__ off,
-                                             const int64_t *__restrict__ aoff, const T *__restrict__ inv,
-                                             const T *__restrict__ r, int k, int lane) {
-    const int c = comp[k];
-    const int o = off[c];
-    const int m = off[c + 1] - o;
-    const T *a = inv + aoff[c] + (int64_t)(k - o) * m;
-    const T *rr = r + o;
-    T s = 0;
-    for (int j = lane; j < m; j += 32) s += a[j] * rr[j];
-    for (int w = 16; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
-    if (lane == 0) u[node[k]] += s;
+                                             const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
+                                             const T *__restrict__ inv, const T *__restrict__ r, int k, int lane) {
+    js_apply_rows<T, 1>(u, node, off, aoff, roff, inv, r, comp[k], k, 1, lane);
 }
 
 // e = A^-1 b on the coarsest level, rows blk, blk + nblk, ... of one CTA: b
