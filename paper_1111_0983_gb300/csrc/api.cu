@@ -181,6 +181,18 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     ck(cudaStreamSynchronize(c->stream), "sync");
 }
 
+// sets NODE_WB in the device type grid of level l at the boundary blocks'
+// write-back nodes (the host types stay as built)
+void mark_writeback(gcmg_ctx *c, int l) {
+    const HostLevel &L = c->H[l];
+    const LocalProgram &J = L.boundary;
+    if (J.ncomp() == 0) return;
+    std::vector<uint8_t> t(L.type);
+    for (int k = 0; k < J.ncomp(); k++)
+        for (int i = J.node_off[k]; i < J.node_off[k] + J.wb_cnt[k]; i++) t[J.lnode[i]] |= NODE_WB;
+    ck(cudaMemcpy(c->G[l].type, t.data(), t.size(), cudaMemcpyHostToDevice), "types");
+}
+
 template <typename T>
 std::vector<DevData<T>> &data(gcmg_ctx *c);
 template <>
@@ -221,9 +233,13 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
             timer_mark(c, GCMG_KERNEL_SMOOTH, l);
         }
     }
+    LocalView<T> bzv{};
+    const LocalView<T> *pending = nullptr;   // boundary-block write-back still to do
     if (extra && g.bz.ncomp > 0 && g.bz.in_smem) {
         // ghost sweep + lambda band sweeps in one shared-memory launch
-        launch_local<T>(lview<T>(g.bz, v, wb), dim, 1, c->p.lambda, c->stream);
+        bzv = lview<T>(g.bz, v, wb);
+        launch_local<T>(bzv, dim, 1, c->p.lambda, c->stream);
+        if (bzv.wb) pending = &bzv;
     } else {
         launch_ghost_relax<T>(v, dim, c->stream);
         if (!extra) return v.u;
@@ -235,8 +251,11 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
     }
     if (c->p.junction_solve) {
         const DevData<T> &D = data<T>(c)[l];
-        launch_junction_solve<T>(v, g, D.js_inv, D.js_r, c->stream);
-    } else if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
+        launch_junction_solve<T>(v, g, D.js_inv, D.js_r, c->stream, pending);
+        return v.u;
+    }
+    if (pending) launch_local_copyback<T>(*pending, c->stream);
+    if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
         if (g.jz.in_smem) {
             launch_local<T>(lview<T>(g.jz, v), dim, 0, c->p.junction_sweeps, c->stream);
         } else {
@@ -487,6 +506,7 @@ gcmg_status create_from_levels(const gcmg_params &q, std::vector<HostLevel> &&H,
             for (int l = 0; l < nl; l++) {
                 upload_program(c, c->H[l].boundary, c->G[l].bz);
                 check_program_fits(c, c->G[l].bz);
+                mark_writeback(c, l);
             }
         c->D64.resize(nl);
         for (int l = 0; l < nl; l++) alloc_data<double>(c, l, c->D64[l], p->precision == 0 || l == 0);

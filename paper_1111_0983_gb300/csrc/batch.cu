@@ -121,6 +121,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 2) kb_local(const BView32 *__re
 constexpr int kJsWarpRows = 4;
 constexpr int kJsRows = 8 * kJsWarpRows;
 
+// WB: the boundary blocks' write-back is performed here too (items cover
+// max(js_n, nwb) indexes); the defects read the write-back nodes from the
+// write-back grid
+template <bool WB>
 __global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restrict__ it, int cur, int npt) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
@@ -128,7 +132,8 @@ __global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restr
     LevelView<float> v = w.v;
     v.u = ugrid(w, cur);
     for_span(b, npt, [&](int64_t k) {
-        if (k < w.js_n) w.js_r[w.js_rpos[k]] = js_defect<float, 2>(v, w.js_node[k], w.js_ghost[k]);
+        if (WB) local_copyback<float>(w.bz, v.u, (int)k);
+        if (k < w.js_n) w.js_r[w.js_rpos[k]] = js_defect<float, 2, WB>(v, w.js_node[k], w.js_ghost[k], w.bz.wb);
     });
 }
 
@@ -489,12 +494,13 @@ void build_tables(gcmg_batch *b) {
                 if (l < 0) continue;
                 const int vi = b->view_of[d][l];
                 const LocalView<float> &J = which ? v32[vi].jz : v32[vi].bz;
-                if (which && b->doms[d]->p.junction_sweeps <= 0) continue;
+                // junction sweeps only without the exact solve (as in a single solve)
+                if (which && (b->doms[d]->p.junction_sweeps <= 0 || p0.junction_solve)) continue;
                 for (int c = 0; c < J.ncomp; c++) items.push_back({vi, c});
                 if (J.ncomp) smem = std::max(smem, smem_of(J));
             }
             add_launch(which ? Launch::JUNCTION : Launch::BOUNDARY, s0, smem, cur[k]);
-            if (!which) {   // the boundary blocks' write-back, once all of them have staged
+            if (!which && !p0.junction_solve) {   // the boundary blocks' write-back, once all have staged
                 for (int d = 0; d < nd; d++) {
                     const int l = (int)b->doms[d]->H.size() - 1 - k;
                     if (l >= 0) dense(b->view_of[d][l], v32[b->view_of[d][l]].bz.nwb);
@@ -503,9 +509,13 @@ void build_tables(gcmg_batch *b) {
             }
         }
         if (p0.junction_solve) {
+            // with the boundary blocks' write-back (all views of a batch have
+            // boundary programs with a write-back grid)
             for (int d = 0; d < nd; d++) {
                 const int l = (int)b->doms[d]->H.size() - 1 - k;
-                if (l >= 0) dense(b->view_of[d][l], v32[b->view_of[d][l]].js_n);
+                if (l < 0) continue;
+                const BView32 &w = v32[b->view_of[d][l]];
+                dense(b->view_of[d][l], std::max<int64_t>(w.js_n, w.bz.wb ? w.bz.nwb : 0));
             }
             add_dense(Launch::JS_DEFECT, cur[k]);
             s0 = items.size();
@@ -586,7 +596,7 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
         case Launch::JUNCTION:
             kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps, L.cur);
             break;
-        case Launch::JS_DEFECT: kb_js_defect<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
+        case Launch::JS_DEFECT: kb_js_defect<true><<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
         case Launch::JS_APPLY: kb_js_apply<<<n, 256, 0, s>>>(b->d_v32, it, L.cur); break;
         case Launch::DESCEND: kb_descend<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
         case Launch::ZERO: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 0, L.npt); break;

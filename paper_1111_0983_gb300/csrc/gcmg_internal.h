@@ -17,7 +17,9 @@ constexpr int TILE_R = 16; // 2D interior tiles: rows (axis 0)
 constexpr int TILE_C = 64; //                    columns (axis 1, contiguous)
 constexpr int EMAX = 6;    // extension sources (2 d)
 
-enum : uint8_t { NODE_OUT = 0, NODE_IN = 1, NODE_GHOST = 2, NODE_KIND = 3, NODE_BAND = 4 };
+// NODE_WB marks, in the device copy of the type grid only, the nodes that the
+// 2D boundary blocks write back through the write-back grid
+enum : uint8_t { NODE_OUT = 0, NODE_IN = 1, NODE_GHOST = 2, NODE_KIND = 3, NODE_BAND = 4, NODE_WB = 8 };
 enum : uint8_t { STENCIL_QUAD = 0, STENCIL_LIN = 1, STENCIL_CORNER = 2, STENCIL_AXIS = 3 };
 
 struct GeomError {

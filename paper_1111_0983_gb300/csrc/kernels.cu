@@ -389,42 +389,70 @@ void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv,
     pdl_launch(k_coarse_solve<T>, dim3(blocks), dim3(threads), (size_t)m * sizeof(T), s, v, g.unk_node, g.unk_ghost, Ainv, m);
 }
 
-template <typename T, int D>
+// defects of the junction-solve rows; with a pending boundary-block
+// write-back (J.wb set) the same launch also copies the write-back nodes into
+// u, the defects reading those nodes from the write-back grid
+template <typename T, int D, bool WB>
 __global__ void __launch_bounds__(kThreads) k_js_defect(LevelView<T> v, const int32_t *__restrict__ node,
                                                         const int32_t *__restrict__ ghost,
-                                                        const int32_t *__restrict__ rpos, T *__restrict__ r, int n) {
+                                                        const int32_t *__restrict__ rpos, T *__restrict__ r, int n,
+                                                        LocalView<T> J) {
     pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) r[rpos[k]] = dev::js_defect<T, D>(v, node[k], ghost[k]);
+    if (WB) local_copyback<T>(J, v.u, k);
+    if (k < n) r[rpos[k]] = dev::js_defect<T, D, WB>(v, node[k], ghost[k], J.wb);
 }
 
-constexpr int kJsWarpRows = 4;                      // rows a warp
-constexpr int kJsRowsPerBlock = 8 * kJsWarpRows;     // 8 warps a CTA
-
-template <typename T>
+// R rows a warp, 8 warps a CTA: R = 4 amortises the per-CTA address chain
+// over 4 rows once the launch fills the GPU several times over; a small
+// launch (a single domain: about a thousand rows a level) keeps one row a
+// warp so that it spreads over more SMs
+template <typename T, int R>
 __global__ void __launch_bounds__(256)
     k_js_apply(T *__restrict__ u, const int32_t *__restrict__ node, const int32_t *__restrict__ comp,
                const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
                const T *__restrict__ inv, const T *__restrict__ r, int n) {
     pdl_wait();
-    const int k0 = blockIdx.x * kJsRowsPerBlock + (threadIdx.x >> 5) * kJsWarpRows;
-    dev::js_apply_span<T, kJsWarpRows>(u, node, comp, off, aoff, roff, inv, r, k0, min(k0 + kJsWarpRows, n),
-                                       threadIdx.x & 31);
+    const int k0 = blockIdx.x * 8 * R + (threadIdx.x >> 5) * R;
+    dev::js_apply_span<T, R>(u, node, comp, off, aoff, roff, inv, r, k0, min(k0 + R, n), threadIdx.x & 31);
+}
+
+// SMs of the current device (queried once)
+int num_sms() {
+    static int count = 0;
+    if (count <= 0) {
+        int d = 0, m = 0;
+        if (cudaGetDevice(&d) == cudaSuccess && cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, d) ==
+                                                     cudaSuccess)
+            count = m;
+    }
+    return count > 0 ? count : 1;
 }
 
 template <typename T>
-void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv, T *r, cudaStream_t s) {
+void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv, T *r, cudaStream_t s,
+                           const LocalView<T> *pending) {
     const int n = g.js_n;
-    if (n <= 0) return;
+    if (n <= 0) {
+        if (pending) launch_local_copyback<T>(*pending, s);
+        return;
+    }
     g_launches += 2;
-    if (g.dim == 2)
-        pdl_launch(k_js_defect<T, 2>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, g.js_rpos,
-                   r, n);
+    if (pending)   // 2D boundary blocks only
+        pdl_launch(k_js_defect<T, 2, true>, dim3(blocks_for(std::max(n, pending->nwb))), dim3(kThreads), 0, s, v,
+                   g.js_node, g.js_ghost, g.js_rpos, r, n, *pending);
+    else if (g.dim == 2)
+        pdl_launch(k_js_defect<T, 2, false>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost,
+                   g.js_rpos, r, n, LocalView<T>{});
     else
-        pdl_launch(k_js_defect<T, 3>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost, g.js_rpos,
-                   r, n);
-    pdl_launch(k_js_apply<T>, dim3((unsigned)((n + kJsRowsPerBlock - 1) / kJsRowsPerBlock)), dim3(256), 0, s, v.u, g.js_node, g.js_comp, g.js_off, g.js_aoff, g.js_roff, inv, r,
-               n);
+        pdl_launch(k_js_defect<T, 3, false>, dim3(blocks_for(n)), dim3(kThreads), 0, s, v, g.js_node, g.js_ghost,
+                   g.js_rpos, r, n, LocalView<T>{});
+    if (n >= 8 * 4 * 4 * num_sms())   // at least four CTAs of 4-row warps an SM
+        pdl_launch(k_js_apply<T, 4>, dim3((unsigned)((n + 31) / 32)), dim3(256), 0, s, v.u, g.js_node, g.js_comp,
+                   g.js_off, g.js_aoff, g.js_roff, inv, r, n);
+    else
+        pdl_launch(k_js_apply<T, 1>, dim3((unsigned)((n + 7) / 8)), dim3(256), 0, s, v.u, g.js_node, g.js_comp,
+                   g.js_off, g.js_aoff, g.js_roff, inv, r, n);
 }
 
 template <typename T>
@@ -442,16 +470,19 @@ __global__ void __launch_bounds__(256) k_local_copyback(LocalView<T> J) {
 }
 
 template <typename T>
+void launch_local_copyback(const LocalView<T> &J, cudaStream_t s) {
+    if (!J.wb || J.nwb <= 0) return;
+    g_launches++;
+    pdl_launch(k_local_copyback<T>, dim3(blocks_for(J.nwb)), dim3(256), 0, s, J);
+}
+
+template <typename T>
 void launch_local(const LocalView<T> &J, int dim, int lead_ghost, int reps, cudaStream_t s) {
     if (J.ncomp <= 0 || (reps <= 0 && !lead_ghost)) return;
     g_launches++;
     const size_t smem = local_smem_bytes(J, dim);
     if (dim == 2) pdl_launch(k_local<T, 2>, dim3(J.ncomp), dim3(LOCAL_THREADS), smem, s, J, lead_ghost, reps);
     else pdl_launch(k_local<T, 3>, dim3(J.ncomp), dim3(LOCAL_THREADS), smem, s, J, lead_ghost, reps);
-    if (J.wb) {
-        g_launches++;
-        pdl_launch(k_local_copyback<T>, dim3(blocks_for(J.nwb)), dim3(256), 0, s, J);
-    }
 }
 
 template <typename T>
@@ -493,12 +524,14 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_prolong<T>(const LevelView<T> &, const LevelView<T> &, int, const T *, T *, bool,  \
                                     cudaStream_t);                                                       \
     template void launch_coarse_solve<T>(const LevelView<T> &, const DevGeom &, const T *, cudaStream_t); \
-    template void launch_junction_solve<T>(const LevelView<T> &, const DevGeom &, const T *, T *, cudaStream_t); \
+    template void launch_junction_solve<T>(const LevelView<T> &, const DevGeom &, const T *, T *, cudaStream_t, \
+                                           const LocalView<T> *);                                                \
     template void launch_descend<T>(const LevelView<T> &, const LevelView<T> &, const DevGeom &, const T *, T *, T *, \
                                     T *, cudaStream_t);                                                            \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
     template size_t local_smem_bytes<T>(const LocalView<T> &, int);                                 \
     template void launch_local<T>(const LocalView<T> &, int, int, int, cudaStream_t);               \
+    template void launch_local_copyback<T>(const LocalView<T> &, cudaStream_t);                      \
     template void local_prepare<T>(int, size_t);
 
 GCMG_INSTANTIATE(float)

@@ -43,16 +43,22 @@ void launch_prolong(const LevelView<T> &F, const LevelView<T> &C, int dim, const
 template <typename T>
 void launch_coarse_solve(const LevelView<T> &v, const DevGeom &g, const T *Ainv, cudaStream_t s);
 // exact junction solve: defects of the solved equations into r, then
-// u += A_ZZ^-1 r per component
+// u += A_ZZ^-1 r per component.  pending: a 2D boundary-block program whose
+// write-back into v.u is still to be done; the defect launch performs it.
 template <typename T>
-void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv, T *r, cudaStream_t s);
+void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv, T *r, cudaStream_t s,
+                           const LocalView<T> *pending = nullptr);
 template <typename T>
 void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s);
 
 template <typename T>
 size_t local_smem_bytes(const LocalView<T> &J, int dim);
+// shared-memory programs; a program with a write-back grid (J.wb) leaves its
+// write-back to launch_local_copyback or to launch_junction_solve
 template <typename T>
 void launch_local(const LocalView<T> &J, int dim, int lead_ghost, int reps, cudaStream_t s);
+template <typename T>
+void launch_local_copyback(const LocalView<T> &J, cudaStream_t s);
 template <typename T>
 void local_prepare(int dim, size_t smem);
 // whether a program's largest component keeps its inside entries in registers

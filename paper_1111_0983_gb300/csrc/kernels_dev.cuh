@@ -569,18 +569,22 @@ __device__ __forceinline__ void prolong_node(const LevelView<T> &F, const LevelV
 // ---------------------------------------------------- exact junction solve
 // Defect of the equation of row k of the junction solve: at an inside node
 // f + Lap_h u (as a sum of differences), at ghost q g - L_G u.
-template <typename T, int D>
-__device__ __forceinline__ T js_defect(const LevelView<T> &v, int32_t p, int32_t q) {
+// WB: the boundary blocks' write-back into u is still pending (it runs in the
+// same launch), so the nodes marked NODE_WB are read from the write-back grid
+// wb, which holds the values being copied into u.
+template <typename T, int D, bool WB = false>
+__device__ __forceinline__ T js_defect(const LevelView<T> &v, int32_t p, int32_t q, const T *wb = nullptr) {
+    auto rd = [&](int64_t x) -> T { return (WB && (v.type[x] & NODE_WB)) ? wb[x] : v.u[x]; };
     if (q >= 0) {
         constexpr int K = D == 2 ? 9 : 27;
         T s = 0;
 #pragma unroll
-        for (int k = 0; k < K; k++) s += v.gw[(int64_t)k * v.ng + q] * v.u[v.gstn[(int64_t)k * v.ng + q]];
+        for (int k = 0; k < K; k++) s += v.gw[(int64_t)k * v.ng + q] * rd(v.gstn[(int64_t)k * v.ng + q]);
         return v.gg[q] - s;
     }
-    const T up = v.u[p];
-    T lap = (v.u[p - 1] - up) + (v.u[p + 1] - up) + (v.u[p - v.s0] - up) + (v.u[p + v.s0] - up);
-    if (D == 3) lap += (v.u[p - v.s1] - up) + (v.u[p + v.s1] - up);
+    const T up = rd(p);
+    T lap = (rd(p - 1) - up) + (rd(p + 1) - up) + (rd(p - v.s0) - up) + (rd(p + v.s0) - up);
+    if (D == 3) lap += (rd(p - v.s1) - up) + (rd(p + v.s1) - up);
     return v.f[p] + lap * v.inv_h2;
 }
 
