@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--cpu-sample-cycles", type=int, default=2)
     ap.add_argument("--learned", type=int, default=8,
                     help="held-out 513^2 star problems for the learned-guess comparison (0 to skip)")
+    ap.add_argument("--write-traffic", nargs=3, metavar=("CSV", "KERNEL_REGEX", "KEY"),
+                    help="record in profiles/traffic.json, under KEY, the mean DRAM bytes per launch of the "
+                         "kernels matching KERNEL_REGEX in an ncu CSV (dram__bytes_read.sum, "
+                         "dram__bytes_write.sum) and exit; a regex ending in '@largest' keeps only the "
+                         "launches with the largest grid (the fine level)")
     return ap.parse_args()
 
 
@@ -136,9 +141,21 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+KERNEL_SOURCES = ("kernels.cu", "kernels_dev.cuh", "gcmg_internal.h")
+
+
+def kernels_sha():
+    """Hash of the per-level kernels' device sources."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1111_0983_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source is unchanged since it was captured."""
+    sources are unchanged since it was captured."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh).get(kernel_key)
@@ -146,9 +163,47 @@ def traffic_for(kernel_key):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1111_0983_gb300", "csrc", "kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec.get("dram_bytes_per_launch") if rec.get("kernels_cu_sha") == sha else None
+    return rec.get("dram_bytes_per_launch") if rec.get("kernels_sha") == kernels_sha() else None
+
+
+def write_traffic(csv_path, kernel_regex, key):
+    """Mean dram__bytes_read.sum + dram__bytes_write.sum per launch of the
+    matching kernels in an ncu --csv log, into profiles/traffic.json."""
+    import csv
+    import re
+    per, grid = {}, {}
+    largest = kernel_regex.endswith("@largest")
+    pattern = kernel_regex[:-len("@largest")] if largest else kernel_regex
+    with open(csv_path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    rows = list(csv.reader(lines))
+    head = rows[0]
+    ci, cn, cm, cv, cu, cg = (head.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Value",
+                                                        "Metric Unit", "Grid Size"))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    for r in rows[1:]:
+        if not re.search(pattern, r[cn]) or r[cm] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        per[r[ci]] = per.get(r[ci], 0.0) + float(r[cv].replace(",", "")) * scale.get(r[cu], 1)
+        dims = [int(x) for x in re.findall(r"\d+", r[cg])]
+        grid[r[ci]] = dims[0] * dims[1] * dims[2] if len(dims) == 3 else 0
+    if largest and per:
+        top = max(grid.values())
+        per = {i: b for i, b in per.items() if grid[i] == top}
+    if not per:
+        raise SystemExit(f"no launches of {kernel_regex} with DRAM byte counts in {csv_path}")
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except (OSError, ValueError):
+        data = {}
+    data[key] = {"dram_bytes_per_launch": sum(per.values()) / len(per), "launches": len(per),
+                 "kernel_regex": kernel_regex, "kernels_sha": kernels_sha()}
+    with open(path, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    print(json.dumps({key: data[key]}))
 
 
 # ------------------------------------------------------------------ problem
@@ -380,14 +435,23 @@ def run_gcmg(args):
     wall = time.perf_counter() - t_wall0
     launches = gcmg.launch_counter() - launches0
     clk = clocks.stop()
-    # second pass of the same solves with CUDA events around every fine-level
-    # launch of the smoother (events cannot live inside the graph's loop body)
+    # further passes of the same solves with CUDA events around every
+    # fine-level launch of the smoother, then around every boundary-block
+    # launch (events cannot live inside the graph's loop body)
     S.set_kernel_timing(S.KERNEL_SMOOTH)
     for k in range(args.steps):
         flush.zero_()
         u.zero_()
         S.solve(u)
     k_launches, k_ms = S.kernel_timing()
+    b_launches, b_ms, b_bytes = 0, 0.0, 0.0
+    if P.dim == 2:
+        S.set_kernel_timing(S.KERNEL_BOUNDARY)
+        for k in range(args.steps):
+            flush.zero_()
+            u.zero_()
+            S.solve(u)
+        b_launches, b_ms, b_bytes = S.kernel_timing_ex()
     S.set_kernel_timing(-1)
     ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
@@ -427,10 +491,23 @@ def run_gcmg(args):
     kname = f"rb_{'fused2d' if P.dim == 2 else 'interior'}_{'f64' if precision == 0 else 'f32'}_{args.config}"
     kdesc = ("k_rb_fused2d (fine level, red + black sweep)" if P.dim == 2
              else "k_rb_interior (fine level, one colour)")
-    roofline = {"bound": "hbm", "kernel": kdesc, "achieved": achieved,
-                "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
-                "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),
-                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms, "launches_timed": k_launches}
+    sweep = {"bound": "hbm", "kernel": kdesc, "achieved": achieved,
+             "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+             "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),
+             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms, "launches_timed": k_launches}
+    if b_launches:
+        # 2D: the boundary blocks lead the launch list (profiles/launches_*): the
+        # dominant kernel; bytes per launch averaged over its launches on all levels
+        bname = f"local_bz_{'f64' if precision == 0 else 'f32'}_{args.config}"
+        b_ach = (b_bytes / b_launches) / (b_ms / b_launches / 1e3) / 1e9 if b_ms > 0 else None
+        roofline = {"bound": "hbm", "kernel": "k_local (2D boundary blocks: ghost sweep + lambda band sweeps "
+                    "in shared memory, every level)", "achieved": b_ach, "peak": peak,
+                    "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                    "frac": (b_ach / peak) if b_ach and peak else None, "traffic": traffic_for(bname),
+                    "alg_bytes_per_launch": b_bytes / b_launches, "avg_launch_ms": b_ms / b_launches,
+                    "launches_timed": b_launches}
+    else:
+        roofline = sweep
 
     line = None
     if rank == 0:
@@ -443,7 +520,7 @@ def run_gcmg(args):
                            "cycle": "V(2,1)" if args.gamma == 1 else "W(2,1)", "lambda": 5,
                            "cycles_per_solve": cycles, "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "clocks": clk, "gpu_launches": launches,
+                "roofline": roofline, "sweep_roofline": sweep, "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": int(f_h.nbytes + g_h.nbytes),
                         "d2h_bytes_per_step": int(u_pin.nbytes)},
                 "wall_s": wall}
@@ -490,6 +567,9 @@ def run_gcmg(args):
 
 def main():
     args = parse()
+    if args.write_traffic:
+        write_traffic(*args.write_traffic)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -209,20 +209,29 @@ gcmg_status gcmg_prolong(gcmg_ctx *ctx, int level, const double *ec_dev, double 
 
 /* ---- measurement */
 
-/* Kernel classes whose fine-level launches can be timed. */
+/* Kernel classes whose launches can be timed: the fine-level launches of
+ * classes 0-3, the launches of every level of class 4. */
 enum {
     GCMG_KERNEL_SMOOTH = 0,   /* red-black interior half-sweep (Eq. jac2d) */
     GCMG_KERNEL_DEFECT = 1,   /* defect (TGCS step 3) */
     GCMG_KERNEL_PROLONG = 2,  /* interpolation and correction (Sec. 2.6) */
-    GCMG_KERNEL_RESTRICT = 3  /* composite restriction (Sec. 2.5) */
+    GCMG_KERNEL_RESTRICT = 3, /* composite restriction (Sec. 2.5) */
+    GCMG_KERNEL_BOUNDARY = 4  /* 2D boundary blocks: ghost sweep + lambda band sweeps (Sec. 3.2)
+                                 of one relaxation in shared memory, every level */
 };
 
-/* With kind >= 0, later solves bracket every fine-level launch of that
- * kernel class with CUDA events on the context's stream (kind = -1: off).
- * gcmg_kernel_timing synchronises the stream and returns the number of timed
- * launches and their summed device time since the last call or enable. */
+/* With kind >= 0, later solves bracket every timed launch of that kernel
+ * class with CUDA events on the context's stream (kind = -1: off); graph
+ * capture is off meanwhile.  gcmg_kernel_timing synchronises the stream and
+ * returns the number of timed launches and their summed device time since
+ * the last call or enable. */
 gcmg_status gcmg_set_kernel_timing(gcmg_ctx *ctx, int kind);
 gcmg_status gcmg_kernel_timing(gcmg_ctx *ctx, int64_t *launches, double *total_ms);
+/* As gcmg_kernel_timing, plus the algorithmic bytes of the timed launches
+ * (class 4 only, else 0): per launch each distinct staged node's u read, each
+ * distinct inside node's f read, each distinct ghost's 3^d weights, g and
+ * mu dt read, each written-back node's u write, in the cycle precision. */
+gcmg_status gcmg_kernel_timing_ex(gcmg_ctx *ctx, int64_t *launches, double *total_ms, double *alg_bytes);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t gcmg_launch_counter(void);

@@ -200,9 +200,31 @@ std::vector<DevData<double>> &data<double>(gcmg_ctx *c) { return c->D64; }
 template <>
 std::vector<DevData<float>> &data<float>(gcmg_ctx *c) { return c->D32; }
 
-// events around fine-level launches of the kernel class being timed
-void timer_mark(gcmg_ctx *c, int kind, int l) {
-    if (c->timing_kind != kind || l != 0) return;
+// values moved by one boundary-block launch of level l: each distinct
+// staged node (u read), inside entry (f read), ghost (3^d weights, g, mu dt)
+// and write-back node (u write) once; halo re-reads of overlapping blocks
+// and the program's index arrays are not counted
+int64_t boundary_units(const HostLevel &L) {
+    const LocalProgram &J = L.boundary;
+    if (J.ncomp() == 0) return 0;
+    std::vector<uint8_t> seen(L.nn, 0), gseen(L.ng(), 0);
+    int64_t units = 0;
+    for (int32_t p : J.lnode)
+        if (!(seen[p] & 1)) { seen[p] |= 1; units++; }
+    for (int32_t p : J.int_glob)
+        if (!(seen[p] & 2)) { seen[p] |= 2; units++; }
+    const int K = L.dim == 2 ? 9 : 27;
+    for (int32_t q : J.gh_q)
+        if (!gseen[q]) { gseen[q] = 1; units += K + 2; }
+    for (int32_t w : J.wb_cnt) units += w;
+    return units;
+}
+
+// events around the launches of the kernel class being timed (fine level;
+// every level for the boundary blocks); `bytes`: that launch's algorithmic bytes
+void timer_mark(gcmg_ctx *c, int kind, int l, double bytes = 0.0) {
+    if (c->timing_kind != kind || (l != 0 && kind != GCMG_KERNEL_BOUNDARY)) return;
+    if (c->events_used % 2 == 0) c->timed_bytes += bytes;
     if (c->events_used == c->events.size()) {
         if (c->events.size() >= 65536) return;
         cudaEvent_t e;
@@ -238,7 +260,10 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
     if (extra && g.bz.ncomp > 0 && g.bz.in_smem) {
         // ghost sweep + lambda band sweeps in one shared-memory launch
         bzv = lview<T>(g.bz, v, wb);
+        const double bytes = c->timing_kind == GCMG_KERNEL_BOUNDARY ? (double)c->bz_units[l] * sizeof(T) : 0.0;
+        timer_mark(c, GCMG_KERNEL_BOUNDARY, l, bytes);
         launch_local<T>(bzv, dim, 1, c->p.lambda, c->stream);
+        timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         if (bzv.wb) pending = &bzv;
     } else {
         launch_ghost_relax<T>(v, dim, c->stream);
@@ -970,14 +995,22 @@ gcmg_status gcmg_prolong(gcmg_ctx *c, int l, const double *ec, double *out) {
 }
 
 gcmg_status gcmg_set_kernel_timing(gcmg_ctx *c, int kind) {
-    if (!c || kind < -1 || kind > GCMG_KERNEL_RESTRICT) return fail(c, GCMG_E_ARG, "bad kernel class");
+    if (!c || kind < -1 || kind > GCMG_KERNEL_BOUNDARY) return fail(c, GCMG_E_ARG, "bad kernel class");
+    if (kind == GCMG_KERNEL_BOUNDARY && c->bz_units.empty())
+        for (const HostLevel &L : c->H) c->bz_units.push_back(boundary_units(L));
     c->timing_kind = kind;
     c->events_used = 0;
+    c->timed_bytes = 0.0;
     return GCMG_OK;
 }
 
 gcmg_status gcmg_kernel_timing(gcmg_ctx *c, int64_t *launches, double *total_ms) {
-    if (!c || !launches || !total_ms) return fail(c, GCMG_E_ARG, "null pointer");
+    double bytes = 0.0;
+    return gcmg_kernel_timing_ex(c, launches, total_ms, &bytes);
+}
+
+gcmg_status gcmg_kernel_timing_ex(gcmg_ctx *c, int64_t *launches, double *total_ms, double *alg_bytes) {
+    if (!c || !launches || !total_ms || !alg_bytes) return fail(c, GCMG_E_ARG, "null pointer");
     GCMG_GUARD(c, {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         ck(cudaStreamSynchronize(c->stream), "sync");
@@ -989,7 +1022,9 @@ gcmg_status gcmg_kernel_timing(gcmg_ctx *c, int64_t *launches, double *total_ms)
         }
         *launches = (int64_t)(c->events_used / 2);
         *total_ms = tot;
+        *alg_bytes = c->timed_bytes;
         c->events_used = 0;
+        c->timed_bytes = 0.0;
         return GCMG_OK;
     })
 }

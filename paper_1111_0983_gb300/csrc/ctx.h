@@ -47,6 +47,8 @@ struct gcmg_ctx {
     int timing_kind = -1;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
+    double timed_bytes = 0.0;              // algorithmic bytes of the timed launches
+    std::vector<int64_t> bz_units;         // per level: distinct values a boundary-block launch moves
     std::vector<void *> allocs;
     std::string err;
     int version = 0;                        // bumped when the boundary types change

@@ -79,6 +79,7 @@ def lib():
             "gcmg_prolong": (st, [vp, i32, vp, vp]),
             "gcmg_set_kernel_timing": (st, [vp, i32]),
             "gcmg_kernel_timing": (st, [vp, C.POINTER(i64), C.POINTER(dbl)]),
+            "gcmg_kernel_timing_ex": (st, [vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
             "gcmg_launch_counter": (i64, []),
             "gcmg_junction_zone": (st, [vp, i32, vp]),
             "gcmg_junction_solve_set": (st, [vp, i32, vp]),
@@ -258,7 +259,7 @@ class Solver:
         self._check(lib().gcmg_prolong(self._h, l, _ptr(ec), _ptr(out)))
 
     # ---- measurement
-    KERNEL_SMOOTH, KERNEL_DEFECT, KERNEL_PROLONG, KERNEL_RESTRICT = 0, 1, 2, 3
+    KERNEL_SMOOTH, KERNEL_DEFECT, KERNEL_PROLONG, KERNEL_RESTRICT, KERNEL_BOUNDARY = 0, 1, 2, 3, 4
 
     def set_kernel_timing(self, kind):
         self._check(lib().gcmg_set_kernel_timing(self._h, int(kind)))
@@ -267,6 +268,12 @@ class Solver:
         n, ms = C.c_int64(), C.c_double()
         self._check(lib().gcmg_kernel_timing(self._h, C.byref(n), C.byref(ms)))
         return n.value, ms.value
+
+    def kernel_timing_ex(self):
+        """(launches, total ms, algorithmic bytes) of the timed launches."""
+        n, ms, b = C.c_int64(), C.c_double(), C.c_double()
+        self._check(lib().gcmg_kernel_timing_ex(self._h, C.byref(n), C.byref(ms), C.byref(b)))
+        return n.value, ms.value, b.value
 
 
 def launch_counter():

@@ -221,6 +221,29 @@ def test_solve_host_equals_device():
     assert sth["cycles"] == st["cycles"]
 
 
+def test_boundary_block_timing():
+    """Timing the boundary blocks (every level) leaves the result bit for bit
+    unchanged, times every launch of every relaxation, and reports bytes."""
+    P, n, nc = inputs.flower(), 257, 33
+    S = solver_for(P, n, nc, precision=1)
+    set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    ut = torch.zeros_like(u)
+    S.set_kernel_timing(S.KERNEL_BOUNDARY)
+    stt = S.solve(ut)
+    launches, ms, nbytes = S.kernel_timing_ex()
+    S.set_kernel_timing(-1)
+    assert stt["cycles"] == st["cycles"]
+    assert torch.equal(u, ut)
+    per_cycle = 3 * (S.nlev - 1)     # nu1 + nu2 relaxations on every level above the coarsest
+    assert launches == st["cycles"] * per_cycle
+    assert ms > 0 and nbytes > 0
+    # every launch reads and writes at least each band node of its level (FP32)
+    band = [int(((S.node_types(l) & 4) > 0).sum()) for l in range(S.nlev - 1)]
+    assert nbytes >= st["cycles"] * 3 * sum(2 * 4 * b for b in band)
+
+
 def test_errors_are_reported():
     gcmg = _gcmg()
     X = inputs.coords(2, 65)
