@@ -145,11 +145,16 @@ KERNEL_SOURCES = ("kernels.cu", "kernels_dev.cuh", "gcmg_internal.h")
 
 
 def kernels_sha():
-    """Hash of the per-level kernels' device sources."""
+    """Hash of the per-level kernels' device sources, comments and
+    whitespace removed (an edited comment does not invalidate a capture)."""
+    import re
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1111_0983_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1111_0983_gb300", "csrc", name)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -17,7 +17,9 @@ constexpr int LOCAL_EPT = 4;     // inside entries per thread and colour in loca
 // max-norm reduction on the bit pattern of a non-negative double (monotone
 // for non-negative IEEE values); NaN is folded into +Inf so that it is seen.
 // waits for the preceding kernel of the stream (programmatic dependent launch;
-// a no-op when the kernel was launched without it)
+// a no-op when the kernel was launched without it).  No kernel triggers its
+// dependents early: measured, a 1025^2 solve went from 4.84 to 5.13 ms when
+// every kernel did, the waiting CTAs taking SM slots from the running grid.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ void atomic_max_abs(unsigned long long *bits, double v) {
