@@ -545,7 +545,7 @@ def run_gcmg(args):
                              "ms_per_solve": bms, "refinement_steps": bcyc, "setup_s": setup_s,
                              "cycles_max": max(st["cycles"] for st in bst),
                              "cycles_median": statistics.median(st["cycles"] for st in bst),
-                             "tile_variant": ["16x64", "8x128", "32x32"][best],
+                             "tile_variant": ["strips of 8 rows", "strips of 16 rows", "strips of 32 rows"][best],
                              "autotune_ms_fused_sweeps_per_cycle": tune_ms,
                              "fused_sweep_GBs": fused_bytes / (min(tune_ms) / 1e3) / 1e9,
                              "converged": len(bad) == 0, "not_converged": bad,

@@ -266,11 +266,12 @@ gcmg_status gcmg_batch_solve(gcmg_batch *batch, gcmg_stats *stats, int *steps);
 /* Copies the solution of domain i to u_dev (device, n_i^2 doubles). */
 gcmg_status gcmg_batch_get_solution(gcmg_batch *batch, int i, double *u_dev);
 
-/* Tile shape of the fused interior sweep: 0 = 16 x 64, 1 = 8 x 128, 2 = 32 x 32. */
+/* Height of the strips of the interior sweep (each strip: 60 owned columns,
+ * one warp): 0 = 8 rows, 1 = 16 rows, 2 = 32 rows. */
 gcmg_status gcmg_batch_set_tiles(gcmg_batch *batch, int variant);
 
-/* Autotuner: times the batched interior sweeps of one cycle with every tile
- * shape, selects the fastest (*best) and reports each time in ms[0..2]. */
+/* Autotuner: times the batched interior sweeps of one cycle with every strip
+ * height, selects the fastest (*best) and reports each time in ms[0..2]. */
 gcmg_status gcmg_batch_autotune(gcmg_batch *batch, int *best, double *ms);
 
 /* ---- allocation-free defect (no counterpart in the paper: a service for

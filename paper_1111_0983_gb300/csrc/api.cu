@@ -116,6 +116,15 @@ void upload_geometry(gcmg_ctx *c, int l) {
     g.red = upload<int32_t>(c, L.band_red.data(), L.band_red.size());
     g.ntiles = (int)L.tiles.size();
     g.tiles = upload<int32_t>(c, L.tiles.data(), L.tiles.size());
+    if (L.dim == 2 && L.n_in >= STRIP_MIN_INSIDE) {
+        // FP32 sweeps of large levels use strips of 8 rows (measured at 4097^2:
+        // 1.73 TB/s against 1.42 for the tiles; the tiles stay faster on
+        // smaller levels and in FP64)
+        const std::vector<int32_t> st = strips_for(L, 8);
+        g.strip_rows = 8;
+        g.nstrips = (int)st.size();
+        g.strips = upload<int32_t>(c, st.data(), st.size());
+    }
     g.black = upload<int32_t>(c, L.band_black.data(), L.band_black.size());
     g.enode = upload<int32_t>(c, L.ext_node.data(), L.ext_node.size());
     g.ecnt = upload<uint8_t>(c, L.ext_cnt.data(), L.ext_cnt.size());
@@ -245,7 +254,8 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
     const DevGeom &g = c->G[l];
     if (dim == 2) {
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
-        launch_rb_fused2d<T>(v, out, g.tiles, g.ntiles, c->stream);
+        if (sizeof(T) == 4 && g.nstrips > 0) launch_rb_strip<T>(v, out, g, c->stream);
+        else launch_rb_fused2d<T>(v, out, g.tiles, g.ntiles, c->stream);
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
         v.u = out;
     } else {

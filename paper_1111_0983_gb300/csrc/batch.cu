@@ -43,7 +43,8 @@ struct BView32 {
     float *u2, *c_u2;        // second u grids of this level and of the next coarser one
     LevelView<float> c;      // next coarser level (when it exists)
     float *cf, *cg;          // coarser level's f and ghost data (restriction targets)
-    const int32_t *tiles;    // active tiles of the selected shape
+    const int32_t *tiles;    // active sweep strips of the selected height
+    int ntiles;
     LocalView<float> bz, jz; // boundary blocks, junction zone
     const int32_t *gt_ptr, *gt_col;
     const float *gt_val;
@@ -79,23 +80,25 @@ __device__ __forceinline__ void for_span(const BItem &b, int npt, F &&f) {
     for (int e = 0; e < npt; e++) f((int64_t)b.start + (int64_t)e * kThreads + threadIdx.x);
 }
 constexpr int kCoarseBlocks = 4;     // CTAs per domain for the coarsest solve
-constexpr int kVariants = 3;         // tile shapes of the fused sweep
-const int kTileR[kVariants] = {16, 8, 32};
-const int kTileC[kVariants] = {64, 128, 32};
+constexpr int kVariants = 3;         // rows of the sweep strips (STRIP_W owned columns each)
+const int kStripRows[kVariants] = {8, 16, 32};
 
 // ---------------------------------------------------------------- kernels
 // Launch argument `cur` / `src`: which of the level's two u grids holds u
 // (0: v.u, 1: u2); the sweep reads that grid and writes the other.
 __device__ __forceinline__ float *ugrid(const BView32 &w, int k) { return k ? w.u2 : w.v.u; }
 
-template <int TR, int TC>
-__global__ void __launch_bounds__(256) kb_fused(const BView32 *__restrict__ V, const BItem *__restrict__ it, int src) {
+// both colours of the sweep: an item is 4 consecutive strips of one view, one a warp
+template <int SR>
+__global__ void __launch_bounds__(128, 8) kb_fused(const BView32 *__restrict__ V, const BItem *__restrict__ it, int src) {
     const BItem b = it[blockIdx.x];
     if (!V[b.view].active[V[b.view].dom]) return;
     const BView32 &w = V[b.view];
+    const int s = b.start + (threadIdx.x >> 5);
+    if (s >= w.ntiles) return;   // uniform over the warp
     LevelView<float> v = w.v;
     v.u = ugrid(w, src);
-    rb_fused2d_body<float, TR, TC>(v, ugrid(w, src ^ 1), w.tiles[b.start]);
+    rb_strip<float, SR>(v, ugrid(w, src ^ 1), w.tiles[s]);
 }
 
 __global__ void __launch_bounds__(256) kb_local_copyback(const BView32 *__restrict__ V, const BItem *__restrict__ it,
@@ -348,20 +351,6 @@ void free_tables(gcmg_batch *b) {
     b->cycle.clear();
 }
 
-// tiles of shape tr x tc holding inside nodes (packed row tile << 16 | column tile)
-std::vector<int32_t> tiles_for(const HostLevel &L, int tr, int tc) {
-    const int nr = (L.n + tr - 1) / tr, ncol = (L.n + tc - 1) / tc;
-    std::vector<uint8_t> act((size_t)nr * ncol, 0);
-    for (int64_t p = 0; p < L.nn; p++)
-        if ((L.type[p] & NODE_KIND) == NODE_IN || (L.type[p] & NODE_KIND) == NODE_GHOST)
-            act[(p / L.n) / tr * ncol + (p % L.n) / tc] = 1;
-    std::vector<int32_t> t;
-    for (int a = 0; a < nr; a++)
-        for (int c = 0; c < ncol; c++)
-            if (act[(size_t)a * ncol + c]) t.push_back((a << 16) | c);
-    return t;
-}
-
 size_t smem_of(const LocalView<float> &J) {
     LocalView<float> tmp = J;
     return local_smem_bytes<float>(tmp, 2);
@@ -376,7 +365,7 @@ void build_tables(gcmg_batch *b) {
     std::vector<int> ntile;   // tiles per view
     b->view_of.assign(nd, {});
     int kmax = 0;
-    const int tr = kTileR[b->variant], tc = kTileC[b->variant];
+    const int rows = kStripRows[b->variant];
     for (int d = 0; d < nd; d++) {
         gcmg_ctx *c = b->doms[d];
         const int nl = (int)c->H.size();
@@ -392,12 +381,13 @@ void build_tables(gcmg_batch *b) {
                 w.cf = c->D32[l + 1].f;
                 w.cg = c->D32[l + 1].gg;
             }
-            std::vector<int32_t> t = tiles_for(c->H[l], tr, tc);
+            std::vector<int32_t> t = strips_for(c->H[l], rows);
             int32_t *dt = nullptr;
             ck(cudaMalloc(&dt, std::max<size_t>(t.size(), 1) * sizeof(int32_t)), "cudaMalloc");
             b->tile_bufs.push_back(dt);
             if (!t.empty()) ck(cudaMemcpy(dt, t.data(), t.size() * sizeof(int32_t), cudaMemcpyHostToDevice), "tiles");
             w.tiles = dt;
+            w.ntiles = (int)t.size();
             ntile.push_back((int)t.size());
             w.bz = lview<float>(c->G[l].bz, w.v, c->D32[l].r);
             w.jz = lview<float>(c->G[l].jz, w.v);
@@ -482,7 +472,7 @@ void build_tables(gcmg_batch *b) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
             if (l < 0) continue;
             const int vi = b->view_of[d][l];
-            for (int i = 0; i < ntile[vi]; i++) items.push_back({vi, (int32_t)i});
+            for (int i = 0; i < ntile[vi]; i += 4) items.push_back({vi, (int32_t)i});
         }
         add_launch(Launch::FUSED, s0, 0, cur[k]);   // reads grid cur[k], writes the other
         cur[k] ^= 1;
@@ -576,9 +566,9 @@ void build_tables(gcmg_batch *b) {
     for (gcmg_ctx *c : b->doms) b->versions.push_back(c->version);
 }
 
-template <int TR, int TC>
+template <int SR>
 void launch_fused(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
-    kb_fused<TR, TC><<<(unsigned)L.count, 256, 0, s>>>(b->d_v32, b->d_items + L.off, L.cur);
+    kb_fused<SR><<<(unsigned)L.count, 128, 0, s>>>(b->d_v32, b->d_items + L.off, L.cur);
 }
 
 void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
@@ -587,9 +577,11 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
     const int junction_sweeps = b->doms[0]->p.junction_sweeps, lambda = b->doms[0]->p.lambda;
     switch (L.kind) {
         case Launch::FUSED:
-            if (b->variant == 0) launch_fused<16, 64>(b, L, s);
-            else if (b->variant == 1) launch_fused<8, 128>(b, L, s);
-            else launch_fused<32, 32>(b, L, s);
+            switch (kStripRows[b->variant]) {   // the height the strip lists were built with
+                case 8: launch_fused<8>(b, L, s); break;
+                case 16: launch_fused<16>(b, L, s); break;
+                default: launch_fused<32>(b, L, s); break;
+            }
             break;
         case Launch::BOUNDARY: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda, L.cur); break;
         case Launch::BOUNDARY_COPY: kb_local_copyback<<<n, 256, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;

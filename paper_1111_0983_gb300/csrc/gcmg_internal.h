@@ -13,6 +13,8 @@
 namespace gcmg {
 
 constexpr int KMAX = 27;   // ghost stencil slots (3^3)
+constexpr int STRIP_W = 60; // 2D sweep strips: owned columns (a warp holds 64)
+constexpr int64_t STRIP_MIN_INSIDE = 2000000;   // FP32 levels swept by strips (single domain)
 constexpr int TILE_R = 16; // 2D interior tiles: rows (axis 0)
 constexpr int TILE_C = 64; //                    columns (axis 1, contiguous)
 constexpr int EMAX = 6;    // extension sources (2 d)
@@ -104,6 +106,9 @@ void build_coarse_inverse(HostLevel &L);
 void build_junction(HostLevel &L, double radius);
 // The zone's unknowns as a mask (1 / 0, nn bytes).
 std::vector<uint8_t> junction_zone_mask(const HostLevel &L, double radius);
+// 2D sweep strips of `rows` x STRIP_W owned nodes holding inside nodes or
+// ghosts, packed (row block << 16 | column block).
+std::vector<int32_t> strips_for(const HostLevel &L, int rows);
 // Exact junction solve of the level's current bc: the zone within radius h,
 // grown by its ghosts' stencils and stripped of ghosts whose stencil leaves
 // it, in components with the inverses of their equations (throws GeomError).
@@ -139,6 +144,8 @@ struct DevGeom {
     int32_t *red = nullptr, *black = nullptr;
     int ntiles = 0;
     int32_t *tiles = nullptr;    // active 2D interior tiles
+    int nstrips = 0, strip_rows = 0;
+    int32_t *strips = nullptr;   // active 2D sweep strips (strip_rows x STRIP_W owned nodes)
     int32_t *enode = nullptr;    // ne
     uint8_t *ecnt = nullptr;     // ne
     int32_t *esrc = nullptr;     // EMAX * ne, slot major

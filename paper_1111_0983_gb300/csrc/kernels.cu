@@ -278,6 +278,25 @@ void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s) {
     else pdl_launch(k_rb_interior<T, 3>, dim3(blocks_for((int64_t)v.n * v.n * hc)), dim3(kThreads), 0, s, v, color);
 }
 
+// both colours in one pass over the active 2D strips: 4 warps a CTA, one strip a warp
+template <typename T, int SR>
+__global__ void __launch_bounds__(128) k_rb_strip(LevelView<T> v, T *__restrict__ out,
+                                                  const int32_t *__restrict__ strips, int ns) {
+    pdl_wait();
+    const int s = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (s < ns) rb_strip<T, SR>(v, out, strips[s]);   // uniform over the warp
+}
+
+template <typename T>
+void launch_rb_strip(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s) {
+    if (g.nstrips <= 0) return;
+    g_launches++;
+    const dim3 grid((unsigned)((g.nstrips + 3) / 4));
+    if (g.strip_rows == 32) pdl_launch(k_rb_strip<T, 32>, grid, dim3(128), 0, s, v, out, g.strips, g.nstrips);
+    else if (g.strip_rows == 16) pdl_launch(k_rb_strip<T, 16>, grid, dim3(128), 0, s, v, out, g.strips, g.nstrips);
+    else pdl_launch(k_rb_strip<T, 8>, grid, dim3(128), 0, s, v, out, g.strips, g.nstrips);
+}
+
 template <typename T>
 void launch_rb_fused2d(const LevelView<T> &v, T *out, const int32_t *tiles, int ntiles, cudaStream_t s) {
     if (ntiles <= 0) return;
@@ -513,6 +532,7 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_rb<T>(const LevelView<T> &, int, int, cudaStream_t);                            \
     template void launch_rb_list<T>(const LevelView<T> &, int, const int32_t *, int, cudaStream_t);     \
     template void launch_rb_fused2d<T>(const LevelView<T> &, T *, const int32_t *, int, cudaStream_t);  \
+    template void launch_rb_strip<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);           \
     template void launch_ghost_relax<T>(const LevelView<T> &, int, cudaStream_t);                         \
     template void launch_ghost_relax_list<T>(const LevelView<T> &, int, const int32_t *, int, cudaStream_t); \
     template void launch_defect<T>(const LevelView<T> &, int, bool, unsigned long long *, cudaStream_t); \

@@ -12,6 +12,10 @@ extern std::atomic<long long> g_launches;   // kernels launched by this library
 
 template <typename T>
 void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s);
+// both colours of a 2D sweep over the active strips (one warp a strip, rows
+// in registers): reads v.u, writes out
+template <typename T>
+void launch_rb_strip(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s);
 // both colours of a 2D sweep over the active tiles: reads v.u, writes out
 template <typename T>
 void launch_rb_fused2d(const LevelView<T> &v, T *out, const int32_t *tiles, int ntiles, cudaStream_t s);

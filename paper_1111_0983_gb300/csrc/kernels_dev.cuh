@@ -185,6 +185,128 @@ __device__ __forceinline__ void rb_fused2d_cols(const LevelView<T> &v, T *__rest
     }
 }
 
+// ------------------------------------------------------------- strip sweep
+// Both colours of the Gauss-Seidel form of Eq. (jac2d) over one strip, by one
+// warp, without shared memory: lane l holds columns j0 + 2l and j0 + 2l + 1 of
+// the strip's 64 (lanes 1-30 own theirs, lanes 0 and 31 are the strip's
+// halo) and the warp walks down the strip's rows, keeping three rows of old u
+// and of red-updated values in registers (horizontal neighbours by warp
+// shuffles) and loading STRIP_PD rows ahead.  Per node, R = the red update at
+// red inside nodes, else the old value; the result = the black update (from
+// R) at black inside nodes, else R; inside nodes and ghosts are stored into
+// `out`.  The sums are those of rb_fused2d_* in the same order, so the values
+// are the same.  Loads are clamped to the grid: the setup keeps inside nodes
+// and ghosts off the box boundary, so clamped values only reach outside nodes,
+// which are not stored.  strip = row block << 16 | column block.
+constexpr int STRIP_PD = 3;    // rows loaded ahead
+
+// h^2 f rounded on its own (never contracted into the sum that follows)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename T, int SR>
+__device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ out, int strip) {
+    constexpr int PD = STRIP_PD;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int n = v.n;
+    const int64_t s0 = v.s0;
+    const int i0 = (strip >> 16) * SR, j0 = (strip & 0xffff) * STRIP_W - 2;
+    const int c0 = j0 + 2 * lane, c1 = c0 + 1;
+    const int q0 = min(max(c0, 0), n - 1), q1 = min(max(c1, 0), n - 1);
+    const bool own = lane >= 1 && lane <= 30;
+    const T h2 = v.h2;
+    const T *__restrict__ u = v.u;
+    const T *__restrict__ f = v.f;
+    const uint8_t *__restrict__ ty = v.type;
+    auto rowb = [&](int x) -> int64_t { return (int64_t)min(max(x, 0), n - 1) * s0; };
+    // at row x: ua/ub/uc = u rows x-1, x, x+1; qu[k] = u row x+2+k;
+    // fc/kc = f, type of row x; fq/kq[k] = row x+1+k
+    T ua0, ua1, ub0, ub1, uc0, uc1, qu0[PD], qu1[PD], fc0, fc1, fq0[PD], fq1[PD];
+    uint8_t kc0, kc1, kq0[PD], kq1[PD];
+    {
+        int64_t b = rowb(i0 - 2);
+        ua0 = u[b + q0];
+        ua1 = u[b + q1];
+        b = rowb(i0 - 1);
+        ub0 = u[b + q0];
+        ub1 = u[b + q1];
+        fc0 = f[b + q0];
+        fc1 = f[b + q1];
+        kc0 = ty[b + q0];
+        kc1 = ty[b + q1];
+        b = rowb(i0);
+        uc0 = u[b + q0];
+        uc1 = u[b + q1];
+#pragma unroll
+        for (int k = 0; k < PD; k++) {
+            const int64_t bu = rowb(i0 + 1 + k), bf = rowb(i0 + k);
+            qu0[k] = u[bu + q0];
+            qu1[k] = u[bu + q1];
+            fq0[k] = f[bf + q0];
+            fq1[k] = f[bf + q1];
+            kq0[k] = ty[bf + q0];
+            kq1[k] = ty[bf + q1];
+        }
+    }
+    T ra0 = 0, ra1 = 0, rb0 = 0, rb1 = 0, fp0 = 0, fp1 = 0;   // R rows x-2, x-1; f of row x-1
+    uint8_t kp0 = NODE_OUT, kp1 = NODE_OUT;                     // types of row x-1
+    for (int x = i0 - 1; x <= i0 + SR; x++) {
+        const T uL = __shfl_up_sync(FULL, ub1, 1), uR = __shfl_down_sync(FULL, ub0, 1);
+        const bool red0 = ((x + c0) & 1) == 0;   // c1 has the other colour
+        T r0 = ub0, r1 = ub1;
+        if ((kc0 & NODE_KIND) == NODE_IN && red0) r0 = (mul_rn(h2, fc0) + ua0 + uc0 + uL + ub1) * (T)0.25;
+        if ((kc1 & NODE_KIND) == NODE_IN && !red0) r1 = (mul_rn(h2, fc1) + ua1 + uc1 + ub0 + uR) * (T)0.25;
+        if (x > i0) {   // row o = x - 1 of the strip is complete (warp-uniform)
+            const int o = x - 1;
+            const T RL = __shfl_up_sync(FULL, rb1, 1), RR = __shfl_down_sync(FULL, rb0, 1);
+            // a column's colour flips from row to row: c0 is black in row o when it is red in row x
+            T o0 = rb0, o1 = rb1;
+            if ((kp0 & NODE_KIND) == NODE_IN && red0) o0 = (mul_rn(h2, fp0) + ra0 + r0 + RL + rb1) * (T)0.25;
+            if ((kp1 & NODE_KIND) == NODE_IN && !red0) o1 = (mul_rn(h2, fp1) + ra1 + r1 + rb0 + RR) * (T)0.25;
+            if (own && o < n) {
+                const int64_t b = (int64_t)o * s0;
+                if ((kp0 & NODE_KIND) != NODE_OUT && c0 < n) out[b + c0] = o0;
+                if ((kp1 & NODE_KIND) != NODE_OUT && c1 < n) out[b + c1] = o1;
+            }
+        }
+        ra0 = rb0;
+        ra1 = rb1;
+        rb0 = r0;
+        rb1 = r1;
+        fp0 = fc0;
+        fp1 = fc1;
+        kp0 = kc0;
+        kp1 = kc1;
+        fc0 = fq0[0];
+        fc1 = fq1[0];
+        kc0 = kq0[0];
+        kc1 = kq1[0];
+        ua0 = ub0;
+        ua1 = ub1;
+        ub0 = uc0;
+        ub1 = uc1;
+        uc0 = qu0[0];
+        uc1 = qu1[0];
+#pragma unroll
+        for (int k = 0; k + 1 < PD; k++) {
+            qu0[k] = qu0[k + 1];
+            qu1[k] = qu1[k + 1];
+            fq0[k] = fq0[k + 1];
+            fq1[k] = fq1[k + 1];
+            kq0[k] = kq0[k + 1];
+            kq1[k] = kq1[k + 1];
+        }
+        const int64_t bu = rowb(x + 3 + PD - 1), bf = rowb(x + 2 + PD - 1);
+        qu0[PD - 1] = u[bu + q0];
+        qu1[PD - 1] = u[bu + q1];
+        fq0[PD - 1] = f[bf + q0];
+        fq1[PD - 1] = f[bf + q1];
+        kq0[PD - 1] = ty[bf + q0];
+        kq1[PD - 1] = ty[bf + q1];
+    }
+}
+
 // Reads v.u and writes into out (another buffer): every tile stages the values
 // before the sweep whatever order the tiles run in.  Ghosts of the tile are
 // copied unchanged; tiles cover every inside node and ghost.

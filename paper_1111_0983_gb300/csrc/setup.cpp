@@ -569,6 +569,20 @@ static std::vector<uint8_t> junction_marks(const HostLevel &L, double radius, co
     return zone;
 }
 
+std::vector<int32_t> strips_for(const HostLevel &L, int rows) {
+    const int sr = (L.n + rows - 1) / rows, sc = (L.n + STRIP_W - 1) / STRIP_W;
+    std::vector<uint8_t> active((size_t)sr * sc, 0);
+    for (int64_t p = 0; p < L.nn; p++) {
+        const uint8_t k = L.type[p] & NODE_KIND;
+        if (k == NODE_IN || k == NODE_GHOST) active[(size_t)(p / L.n / rows) * sc + (p % L.n) / STRIP_W] = 1;
+    }
+    std::vector<int32_t> out;
+    for (int a = 0; a < sr; a++)
+        for (int b = 0; b < sc; b++)
+            if (active[(size_t)a * sc + b]) out.push_back((a << 16) | b);
+    return out;
+}
+
 std::vector<uint8_t> junction_zone_mask(const HostLevel &L, double radius) {
     std::vector<int32_t> ghost_of(L.nn, -1);
     for (int64_t q = 0; q < L.ng(); q++) ghost_of[L.ghost_node[q]] = (int32_t)q;

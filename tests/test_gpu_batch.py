@@ -2,7 +2,7 @@
 
 Each domain's converged solution must equal the single-domain solver's and
 the FP64 oracle's converged discrete solution within 1e-10 relative max-norm;
-every tile shape of the fused sweep gives the same result; the autotuner picks
+every strip height of the fused sweep gives the same result; the autotuner picks
 one of them.
 """
 import numpy as np
@@ -61,7 +61,7 @@ def test_batch_matches_single_domain_and_oracle():
     B.close()
 
 
-def test_batch_tile_shapes_agree_and_autotune():
+def test_batch_strip_heights_agree_and_autotune():
     ids, sizes = [4, 6, 9], [257, 129, 257]
     B, probs, _ = make_batch(ids, sizes)
     sols = []
