@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--cpu-sample-cycles", type=int, default=2)
     ap.add_argument("--learned", type=int, default=8,
                     help="held-out 513^2 star problems for the learned-guess comparison (0 to skip)")
+    ap.add_argument("--fmg", default="flower1025",
+                    help="workload of the full-multigrid comparison (plain FP64; '' to skip)")
     ap.add_argument("--write-traffic", nargs=3, metavar=("CSV", "KERNEL_REGEX", "KEY"),
                     help="record in profiles/traffic.json, under KEY, the mean DRAM bytes per launch of the "
                          "kernels matching KERNEL_REGEX in an ncu CSV (dram__bytes_read.sum, "
@@ -316,6 +318,78 @@ def run_batch_measure(B, steps, warmup, stream, flush):
     return ms / steps, cyc, best, tune_ms, bad, stats
 
 
+def fmg_entry(name, stream, flush):
+    """Time to discretisation accuracy in plain FP64: full multigrid with nu
+    cycles a level against V-cycles from u = 0 (device time, CUDA events)."""
+    import torch
+    from paper_1111_0983_gb300 import gcmg
+    P, n, nc, desc = build_problem(name)
+    S = gcmg.Solver(P.phi_grid(n), nc, stream=stream, precision=0, rtol=1e-300, max_cycles=1)
+    for l in range(S.nlev):
+        S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+    rhs = []
+    for l in range(S.nlev):
+        nl = S.shape(l)[0]
+        G = S.ghosts(l)
+        g = P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))
+        rhs.append((torch.from_numpy(P.f_grid(nl)).cuda(), torch.from_numpy(g).cuda()))
+    S.set_rhs(*rhs[0])
+    T = S.node_types(0) & 3
+    ue = torch.from_numpy(P.u_grid(n)).cuda()
+    m = torch.from_numpy(T == 1).cuda()
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+
+    def err():
+        return float((u - ue).abs()[m].max())
+
+    def timed(fn):
+        flush.zero_()
+        u.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    # discretisation error: the converged solution's
+    S2 = gcmg.Solver(P.phi_grid(n), nc, stream=stream, precision=0, rtol=1e-12, max_cycles=200)
+    for l in range(S2.nlev):
+        S2.set_bc_types(l, P.bc_types(S2.ghosts(l)["B"]))
+    S2.set_rhs(*rhs[0])
+    u.zero_()
+    S2.solve(u)
+    disc = err()
+    out = {"workload": name, "description": desc, "precision": "f64", "disc_error": disc, "fmg": [], "vcycles": None}
+
+    def fmg(nu):
+        for l in range(1, S.nlev):
+            S.set_rhs_level(l, *rhs[l])
+        S.fmg(nu, u)
+
+    for nu in (1, 2, 3, 6):
+        fmg(nu)   # warm
+        ms = timed(lambda: fmg(nu))
+        out["fmg"].append({"nu": nu, "ms": ms, "error": err(), "error_over_disc": err() / disc})
+    # fewest V-cycles from 0 that reach 1.1 x the discretisation error, timed as one solve
+    for k in range(1, 40):
+        S3 = gcmg.Solver(P.phi_grid(n), nc, stream=stream, precision=0, rtol=1e-300, max_cycles=k)
+        for l in range(S3.nlev):
+            S3.set_bc_types(l, P.bc_types(S3.ghosts(l)["B"]))
+        S3.set_rhs(*rhs[0])
+        u.zero_()   # the solve starts from u
+        S3.solve(u)
+        if err() <= 1.1 * disc:
+            ms = timed(lambda: S3.solve(u))
+            out["vcycles"] = {"cycles": k, "ms": ms, "error": err(), "error_over_disc": err() / disc}
+            S3.close()
+            break
+        S3.close()
+    S.close()
+    S2.close()
+    return out
+
+
 # ----------------------------------------------------------------- gcmg arm
 def secondary(name, rtol, precision, args, stream, flush):
     """Time the same form on another workload (plain FP64 and mixed)."""
@@ -551,6 +625,8 @@ def run_gcmg(args):
                              "converged": len(bad) == 0, "not_converged": bad,
                              "worst_rel": max(st["rel_residual"] for st in bst)}
             B.close()
+        if args.fmg and world == 1:
+            line["fmg"] = fmg_entry(args.fmg, stream, flush)
         if args.learned and world == 1:
             from paper_1111_0983_gb300 import learn
             t0 = time.perf_counter()

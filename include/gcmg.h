@@ -178,6 +178,22 @@ gcmg_status gcmg_solve(gcmg_ctx *ctx, double *u_dev, gcmg_stats *stats);
 gcmg_status gcmg_solve_host(gcmg_ctx *ctx, const double *f_host, const double *g_host, double *u_host,
                             gcmg_stats *stats);
 
+/* f and g of level `level` (device: n_l^d doubles, and one double per ghost
+ * of that level in the order of gcmg_ghosts): the problem's data sampled on
+ * that level, as gcmg_fmg needs it.  Plain FP64 contexts (precision 0) only:
+ * GCMG_E_STATE otherwise. */
+gcmg_status gcmg_set_rhs_level(gcmg_ctx *ctx, int level, const double *f_dev, const double *g_dev);
+
+/* Full multigrid (nested iteration; the paper notes it derives from the
+ * cycle, Sec. 2.4): the coarsest level's problem solved exactly, then on each
+ * finer level the interpolation (Sec. 2.6) of the coarser level's solution
+ * improved by nu >= 0 cycles with that level as the finest.  Needs f and g on
+ * every level (gcmg_set_rhs for level 0, gcmg_set_rhs_level for the others);
+ * the cycles overwrite the coarser levels' f and g with restricted defects,
+ * so they must be set again before another call.  u_dev (device, n^d
+ * doubles) receives the fine-grid result.  Plain FP64 contexts only. */
+gcmg_status gcmg_fmg(gcmg_ctx *ctx, int nu, double *u_dev);
+
 /* ---- single steps of the cycle on caller buffers, for tests and tools.
  * Each works on level `level` of the hierarchy, in FP64, on device grid
  * arrays of that level's size (n_l^d doubles) and per-ghost arrays. */

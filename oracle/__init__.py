@@ -63,6 +63,8 @@ def lib():
         L.orc_destroy.argtypes = [vp]
         L.orc_set_bc.argtypes = [vp, C.c_int, vp]
         L.orc_set_rhs.argtypes = [vp, vp, vp]
+        L.orc_set_rhs_level.argtypes = [vp, C.c_int, vp, vp]
+        L.orc_fmg.argtypes = [vp, C.c_int, vp]
         L.orc_get_types.argtypes = [vp, C.c_int, vp]
         L.orc_get_band.argtypes = [vp, C.c_int, vp]
         L.orc_get_jzone.argtypes = [vp, C.c_int, vp]
@@ -200,6 +202,21 @@ class Oracle:
         g = np.ascontiguousarray(g, dtype=np.float64)
         assert f.shape == self.shape(0) and g.shape == (self.num_ghosts(0),)
         lib().orc_set_rhs(self._h, _p(f), _p(g))
+
+    def set_rhs_level(self, l, f, g):
+        """f and g of level l (the problem's data sampled there), for fmg."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.shape == self.shape(l) and g.shape == (self.num_ghosts(l),)
+        lib().orc_set_rhs_level(self._h, l, _p(f), _p(g))
+
+    def fmg(self, nu=1):
+        """Full multigrid: exact coarsest solve, then per finer level the
+        interpolated coarser solution improved by nu cycles.  Needs every
+        level's f and g (set_rhs_level; level 0 may come from set_rhs)."""
+        u = np.zeros(self.shape(0))
+        lib().orc_fmg(self._h, int(nu), _p(u))
+        return u
 
     # ---- operators
     def defect(self, u, l=0):

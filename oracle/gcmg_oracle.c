@@ -1217,6 +1217,34 @@ void orc_set_rhs(void *h, const double *f, const double *g) {
     for (int64_t q = 0; q < L->ng; q++) L->g[q] = g[q];
 }
 
+/* f and g of level l: the problem's data sampled on that level (f at its
+ * nodes, g at its ghosts' boundary points); used by orc_fmg */
+void orc_set_rhs_level(void *h, int l, const double *f, const double *g) {
+    Oracle *O = (Oracle *)h;
+    Level *L = &O->L[l];
+    for (int64_t i = 0; i < L->nn; i++) L->f[i] = (L->type[i] == T_INT) ? f[i] : 0.0;
+    for (int64_t q = 0; q < L->ng; q++) L->g[q] = g[q];
+}
+
+/* Full multigrid (nested iteration; the paper notes it derives from the
+ * V-cycle, Sec. 2.4): the coarsest level's problem solved exactly, then on
+ * each finer level l in turn its solution started from the interpolation
+ * (Sec. 2.6) of level l+1's and improved by nu cycles with level l as the
+ * finest.  Every level's f and g must have been set (orc_set_rhs_level);
+ * the cycles at level l overwrite the f and g of the coarser levels, which
+ * are not needed again.  u: the fine-grid result. */
+void orc_fmg(void *h, int nu, double *u) {
+    Oracle *O = (Oracle *)h;
+    coarse_solve(&O->L[O->nlev - 1]);
+    for (int l = O->nlev - 2; l >= 0; l--) {
+        Level *F = &O->L[l];
+        const Level *C = &O->L[l + 1];
+        for (int64_t P = 0; P < F->nn; P++) F->u[P] = is_unknown(F, P) ? prolong_at(F, C, P, C->u) : 0.0;
+        for (int k = 0; k < nu; k++) cycle(O, l);
+    }
+    memcpy(u, O->L[0].u, sizeof(double) * (size_t)O->L[0].nn);
+}
+
 void orc_get_types(void *h, int l, uint8_t *out) {
     Level *L = &((Oracle *)h)->L[l];
     memcpy(out, L->type, (size_t)L->nn);

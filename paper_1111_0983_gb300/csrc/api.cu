@@ -818,6 +818,48 @@ gcmg_status gcmg_set_rhs(gcmg_ctx *c, const double *f_dev, const double *g_dev) 
     })
 }
 
+gcmg_status gcmg_set_rhs_level(gcmg_ctx *c, int l, const double *f_dev, const double *g_dev) {
+    if (!valid_level(c, l) || !f_dev || (!g_dev && c->H[l].ng() > 0)) return fail(c, GCMG_E_ARG, "bad argument");
+    if (c->p.precision != 0) return fail(c, GCMG_E_STATE, "per-level data needs a plain FP64 context");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        const HostLevel &L = c->H[l];
+        ck(cudaMemcpyAsync(c->D64[l].f, f_dev, L.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "f");
+        if (L.ng() > 0)
+            ck(cudaMemcpyAsync(c->D64[l].gg, g_dev, L.ng() * sizeof(double), cudaMemcpyDeviceToDevice, c->stream),
+               "g");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        if (l == 0) c->rhs_set = true;
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_fmg(gcmg_ctx *c, int nu, double *u_dev) {
+    if (!c || !u_dev || nu < 0) return fail(c, GCMG_E_ARG, "bad argument");
+    if (c->p.precision != 0) return fail(c, GCMG_E_STATE, "full multigrid runs in a plain FP64 context");
+    if (!c->rhs_set) return fail(c, GCMG_E_STATE, "gcmg_set_rhs has not been called");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        ensure_inverse(c);
+        ensure_junction_solve(c);
+        const int last = (int)c->H.size() - 1;
+        std::vector<DevData<double>> &D = c->D64;
+        launch_coarse_solve<double>(view<double>(c, last, D[last]), c->G[last], D[last].Ainv, c->stream);
+        double *uc = D[last].u;   // the grid that holds the current level's solution
+        for (int l = last - 1; l >= 0; l--) {
+            LevelView<double> F = view<double>(c, l, D[l]), C = view<double>(c, l + 1, D[l + 1]);
+            launch_prolong<double>(F, C, c->p.dim, uc, D[l].u, false, c->stream);
+            double *u = D[l].u;
+            for (int k = 0; k < nu; k++) u = cycle<double>(c, l, u);
+            uc = u;
+        }
+        check_launch();
+        ck(cudaMemcpyAsync(u_dev, uc, c->H[0].nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u out");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        return GCMG_OK;
+    })
+}
+
 gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
     if (!c || !u_dev) return fail(c, GCMG_E_ARG, "null pointer");
     if (!c->rhs_set) return fail(c, GCMG_E_STATE, "gcmg_set_rhs has not been called");

@@ -80,6 +80,8 @@ def lib():
             "gcmg_set_kernel_timing": (st, [vp, i32]),
             "gcmg_kernel_timing": (st, [vp, C.POINTER(i64), C.POINTER(dbl)]),
             "gcmg_kernel_timing_ex": (st, [vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
+            "gcmg_set_rhs_level": (st, [vp, i32, vp, vp]),
+            "gcmg_fmg": (st, [vp, i32, vp]),
             "gcmg_launch_counter": (i64, []),
             "gcmg_junction_zone": (st, [vp, i32, vp]),
             "gcmg_junction_solve_set": (st, [vp, i32, vp]),
@@ -222,6 +224,14 @@ class Solver:
 
     def set_rhs(self, f, g):
         self._check(lib().gcmg_set_rhs(self._h, _ptr(f), _ptr(g)))
+
+    def set_rhs_level(self, l, f, g):
+        """f and g of level l (device tensors), for fmg (plain FP64 solvers)."""
+        self._check(lib().gcmg_set_rhs_level(self._h, int(l), _ptr(f), _ptr(g)))
+
+    def fmg(self, nu, u):
+        """Full multigrid with nu cycles a level into the device tensor u."""
+        self._check(lib().gcmg_fmg(self._h, int(nu), _ptr(u)))
 
     def solve(self, u):
         st = Stats()

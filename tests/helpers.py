@@ -54,6 +54,20 @@ def problem_rhs(O, P, n):
     return P.f_grid(n), P.g_values(G["B"], G["nu"], types)
 
 
+def level_rhs(O, P, l):
+    """f and g of problem P sampled on level l of a hierarchy (the level's
+    nodes and its ghosts' boundary points)."""
+    n = O.level_n(l)
+    G = O.ghosts(l)
+    return P.f_grid(n), P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))
+
+
+def set_level_rhs(O, P):
+    """f and g on every level of an oracle hierarchy (for full multigrid)."""
+    for l in range(O.nlev):
+        O.set_rhs_level(l, *level_rhs(O, P, l))
+
+
 def rel_maxdiff(a, b, mask):
     return np.abs(a - b)[mask].max() / max(np.abs(b)[mask].max(), 1e-300)
 

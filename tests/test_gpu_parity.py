@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from paper_1111_0983_gb300 import inputs  # noqa: E402
-from helpers import oracle_for, problem_rhs, rel_maxdiff  # noqa: E402
+from helpers import level_rhs, oracle_for, problem_rhs, rel_maxdiff, set_level_rhs  # noqa: E402
 
 PARITY = 1e-10
 
@@ -242,6 +242,36 @@ def test_boundary_block_timing():
     # every launch reads and writes at least each band node of its level (FP32)
     band = [int(((S.node_types(l) & 4) > 0).sum()) for l in range(S.nlev - 1)]
     assert nbytes >= st["cycles"] * 3 * sum(2 * 4 * b for b in band)
+
+
+@pytest.mark.parametrize("P,n,nc,nu", [(inputs.disk(), 129, 17, 2), (inputs.flower(), 257, 33, 2),
+                                       (inputs.star(3), 257, 33, 1), (inputs.torus(), 65, 17, 1)])
+def test_fmg_matches_oracle(P, n, nc, nu):
+    """Full multigrid (plain FP64): the fine result equals the oracle's element
+    by element (same steps, summation order and the junction solve's explicit
+    inverse against LU aside)."""
+    S = solver_for(P, n, nc, precision=0)
+    set_problem_rhs(S, P, n)
+    O = oracle_for(P, n, nc)
+    for l in range(1, S.nlev):
+        f, g = level_rhs(O, P, l)
+        S.set_rhs_level(l, dev(f), dev(g))
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    S.fmg(nu, u)
+    set_level_rhs(O, P)
+    uo = O.fmg(nu)
+    assert rel_maxdiff(host(u), uo, O.types(0) > 0) < 1e-9
+
+
+def test_fmg_needs_plain_fp64():
+    gcmg = _gcmg()
+    P, n = inputs.disk(), 65
+    S = solver_for(P, n, 17, precision=1)
+    set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    with pytest.raises(gcmg.GcmgError) as e:
+        S.fmg(1, u)
+    assert e.value.status == gcmg.GCMG_E_STATE
 
 
 def test_errors_are_reported():

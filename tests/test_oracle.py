@@ -25,7 +25,7 @@ import pytest
 
 import oracle
 from paper_1111_0983_gb300 import inputs
-from helpers import direct_solve, oracle_for, problem_rhs, rel_maxdiff, rho_homogeneous
+from helpers import direct_solve, oracle_for, problem_rhs, rel_maxdiff, rho_homogeneous, set_level_rhs
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -425,3 +425,55 @@ def test_geometry_errors_reported():
         oracle.Oracle(np.hypot(X[0], X[1]) - 0.99, 9)       # touches the box edge
     with pytest.raises(oracle.OracleError):
         oracle.Oracle(np.zeros((n, n)) - 1.0, 9)            # everything inside
+
+
+# ------------------------------------------------------------ full multigrid
+def test_fmg_single_level_is_direct_solve():
+    """With one level, full multigrid is the coarsest solve: the direct
+    solution of the assembled system."""
+    P = inputs.disk()
+    O = oracle_for(P, 17, 17)
+    assert O.nlev == 1
+    set_level_rhs(O, P)
+    f, g = problem_rhs(O, P, 17)
+    u = O.fmg(1)
+    ud = direct_solve(O, f, g)
+    assert rel_maxdiff(u, ud, O.types(0) > 0) < 1e-12
+
+
+def test_fmg_many_cycles_reach_the_discrete_solution():
+    """Enough cycles per level make every level's result its discrete
+    solution, so the fine result is the direct solve's."""
+    P = inputs.flower()
+    O = oracle_for(P, 129, 33)
+    set_level_rhs(O, P)
+    f, g = problem_rhs(O, P, 129)
+    u = O.fmg(20)
+    assert rel_maxdiff(u, direct_solve(O, f, g), O.types(0) > 0) < 1e-9
+
+
+def test_fmg_error_falls_with_cycles():
+    """The error against the exact solution falls as cycles are added, towards
+    the discretisation error; on the torus (boundary smooth on the coarsest
+    grid) one cycle a level already reaches it, the property that defines
+    full multigrid.  (Near a 2D boundary the method's interpolation is first
+    order for a full solution, so one cycle a level does not reach it there.)"""
+    P = inputs.flower()
+    errs = []
+    for nu in (1, 2, 3, 6):
+        O = oracle_for(P, 257, 33)
+        set_level_rhs(O, P)
+        m = O.types(0) == 1
+        errs.append(np.abs(O.fmg(nu) - P.u_grid(257))[m].max())
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    O = oracle_for(P, 257, 33)
+    uc = O.solve(np.zeros(O.shape(0)), rtol=1e-12, max_cycles=100)[0]
+    assert errs[-1] <= 1.1 * np.abs(uc - P.u_grid(257))[O.types(0) == 1].max()
+    T = inputs.torus()
+    O = oracle_for(T, 65, 17)
+    set_level_rhs(O, T)
+    m = O.types(0) == 1
+    e1 = np.abs(O.fmg(1) - T.u_grid(65))[m].max()
+    O = oracle_for(T, 65, 17)
+    uc = O.solve(np.zeros(O.shape(0)), rtol=1e-12, max_cycles=100)[0]
+    assert e1 <= 1.05 * np.abs(uc - T.u_grid(65))[m].max()
