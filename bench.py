@@ -444,7 +444,8 @@ def secondary(name, rtol, precision, args, stream, flush):
                     alg = (24 if prec == 0 else 12) * n_in
                     gbs = alg / (kms / kl / 1e3) / 1e9
                     peak = measured_peaks()[0].get("hbm_gbs")
-                    rec["fine_sweep"] = {"kernel": "k_rb_fused2d", "alg_bytes_per_launch": alg,
+                    rec["fine_sweep"] = {"kernel": "k_rb_fused2d" if prec == 0 else "k_rb_strip",
+                                         "alg_bytes_per_launch": alg,
                                          "avg_launch_ms": kms / kl, "achieved_GBs": gbs,
                                          "frac_of_measured_hbm": gbs / peak if peak else None}
             out["f64" if prec == 0 else "mixed"] = rec
@@ -567,9 +568,11 @@ def run_gcmg(args):
     avg_ms = k_ms / max(k_launches, 1)
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if k_launches else None
     peak = peaks.get("hbm_gbs")
-    kname = f"rb_{'fused2d' if P.dim == 2 else 'interior'}_{'f64' if precision == 0 else 'f32'}_{args.config}"
-    kdesc = ("k_rb_fused2d (fine level, red + black sweep)" if P.dim == 2
-             else "k_rb_interior (fine level, one colour)")
+    kern = ("strip" if precision else "fused2d") if P.dim == 2 else "interior"
+    kname = f"rb_{kern}_{'f64' if precision == 0 else 'f32'}_{args.config}"
+    kdesc = {"strip": "k_rb_strip (fine level, red + black sweep)",
+             "fused2d": "k_rb_fused2d (fine level, red + black sweep)",
+             "interior": "k_rb_interior (fine level, one colour)"}[kern]
     sweep = {"bound": "hbm", "kernel": kdesc, "achieved": achieved,
              "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
              "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),

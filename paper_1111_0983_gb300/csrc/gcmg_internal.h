@@ -14,7 +14,6 @@ namespace gcmg {
 
 constexpr int KMAX = 27;   // ghost stencil slots (3^3)
 constexpr int STRIP_W = 60; // 2D sweep strips: owned columns (a warp holds 64)
-constexpr int64_t STRIP_MIN_INSIDE = 2000000;   // FP32 levels swept by strips (single domain)
 constexpr int TILE_R = 16; // 2D interior tiles: rows (axis 0)
 constexpr int TILE_C = 64; //                    columns (axis 1, contiguous)
 constexpr int EMAX = 6;    // extension sources (2 d)

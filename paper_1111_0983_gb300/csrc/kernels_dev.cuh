@@ -219,13 +219,15 @@ __device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ 
     const T *__restrict__ u = v.u;
     const T *__restrict__ f = v.f;
     const uint8_t *__restrict__ ty = v.type;
-    auto rowb = [&](int x) -> int64_t { return (int64_t)min(max(x, 0), n - 1) * s0; };
+    // row offsets in 32 bits: every grid the solver accepts has fewer than 2^31 nodes
+    const int pitch = (int)s0;
+    auto rowb = [&](int x) -> int { return min(max(x, 0), n - 1) * pitch; };
     // at row x: ua/ub/uc = u rows x-1, x, x+1; qu[k] = u row x+2+k;
     // fc/kc = f, type of row x; fq/kq[k] = row x+1+k
     T ua0, ua1, ub0, ub1, uc0, uc1, qu0[PD], qu1[PD], fc0, fc1, fq0[PD], fq1[PD];
     uint8_t kc0, kc1, kq0[PD], kq1[PD];
     {
-        int64_t b = rowb(i0 - 2);
+        int b = rowb(i0 - 2);
         ua0 = u[b + q0];
         ua1 = u[b + q1];
         b = rowb(i0 - 1);
@@ -240,7 +242,7 @@ __device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ 
         uc1 = u[b + q1];
 #pragma unroll
         for (int k = 0; k < PD; k++) {
-            const int64_t bu = rowb(i0 + 1 + k), bf = rowb(i0 + k);
+            const int bu = rowb(i0 + 1 + k), bf = rowb(i0 + k);
             qu0[k] = u[bu + q0];
             qu1[k] = u[bu + q1];
             fq0[k] = f[bf + q0];
@@ -251,6 +253,7 @@ __device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ 
     }
     T ra0 = 0, ra1 = 0, rb0 = 0, rb1 = 0, fp0 = 0, fp1 = 0;   // R rows x-2, x-1; f of row x-1
     uint8_t kp0 = NODE_OUT, kp1 = NODE_OUT;                     // types of row x-1
+#pragma unroll   // SR + 2 rows: the load ring becomes register renaming
     for (int x = i0 - 1; x <= i0 + SR; x++) {
         const T uL = __shfl_up_sync(FULL, ub1, 1), uR = __shfl_down_sync(FULL, ub0, 1);
         const bool red0 = ((x + c0) & 1) == 0;   // c1 has the other colour
@@ -265,7 +268,7 @@ __device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ 
             if ((kp0 & NODE_KIND) == NODE_IN && red0) o0 = (mul_rn(h2, fp0) + ra0 + r0 + RL + rb1) * (T)0.25;
             if ((kp1 & NODE_KIND) == NODE_IN && !red0) o1 = (mul_rn(h2, fp1) + ra1 + r1 + rb0 + RR) * (T)0.25;
             if (own && o < n) {
-                const int64_t b = (int64_t)o * s0;
+                const int b = o * pitch;
                 if ((kp0 & NODE_KIND) != NODE_OUT && c0 < n) out[b + c0] = o0;
                 if ((kp1 & NODE_KIND) != NODE_OUT && c1 < n) out[b + c1] = o1;
             }
@@ -297,7 +300,7 @@ __device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ 
             kq0[k] = kq0[k + 1];
             kq1[k] = kq1[k + 1];
         }
-        const int64_t bu = rowb(x + 3 + PD - 1), bf = rowb(x + 2 + PD - 1);
+        const int bu = rowb(x + 3 + PD - 1), bf = rowb(x + 2 + PD - 1);
         qu0[PD - 1] = u[bu + q0];
         qu1[PD - 1] = u[bu + q1];
         fq0[PD - 1] = f[bf + q0];
