@@ -116,6 +116,17 @@ gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse);
  * exists to read the message from; destroy it with gcmg_destroy. */
 gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *stream, gcmg_ctx **out);
 
+/* Reinitialisation of a level set (Eq. sdf, Sec. 2.1), for a phi0 that is not
+ * a signed distance function, before gcmg_create: phi_dev (device, n^dim
+ * doubles of the box [-1,1]^dim) receives the result of `steps` explicit steps
+ * of phi_t = sgn(phi0)(1 - |grad phi|) from phi0_dev, with dt = h / dim, the
+ * Godunov upwind form of |grad phi| and, at nodes next to the zero set of
+ * phi0, the subcell fix that keeps the zero set in place.  phi0_dev and
+ * phi_dev must not alias; one scratch grid is allocated for the call; runs on
+ * `stream` and synchronises it.  GCMG_E_ARG: dim not 2 or 3, n < 3, steps < 0
+ * or bad pointers; GCMG_E_OOM, GCMG_E_CUDA. */
+gcmg_status gcmg_reinit(int dim, int n, const double *phi0_dev, int steps, double *phi_dev, void *stream);
+
 void gcmg_destroy(gcmg_ctx *ctx);
 const char *gcmg_last_error(const gcmg_ctx *ctx);
 

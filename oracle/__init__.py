@@ -64,6 +64,7 @@ def lib():
         L.orc_set_bc.argtypes = [vp, C.c_int, vp]
         L.orc_set_rhs.argtypes = [vp, vp, vp]
         L.orc_set_rhs_level.argtypes = [vp, C.c_int, vp, vp]
+        L.orc_reinit.argtypes = [C.c_int, C.c_int, vp, C.c_int, vp]
         L.orc_fmg.argtypes = [vp, C.c_int, vp]
         L.orc_get_types.argtypes = [vp, C.c_int, vp]
         L.orc_get_band.argtypes = [vp, C.c_int, vp]
@@ -93,6 +94,15 @@ def _p(a):
 
 class OracleError(RuntimeError):
     pass
+
+
+def reinit(phi0, steps):
+    """Level set phi0 (n^dim nodes of [-1,1]^dim) after `steps` steps of the
+    reinitialisation equation phi_t = sgn(phi0)(1 - |grad phi|) (Sec. 2.1)."""
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    out = np.empty_like(phi0)
+    lib().orc_reinit(phi0.ndim, phi0.shape[0], _p(phi0), int(steps), _p(out))
+    return out
 
 
 class Oracle:

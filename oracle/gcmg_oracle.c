@@ -1075,6 +1075,66 @@ static void cycle(Oracle *O, int l) {
     smooth(O, L, O->p.nu2);
 }
 
+/* ------------------------------------- reinitialisation (Eq. sdf, Sec. 2.1)
+ * phi_t = sgn(phi0) (1 - |grad phi|) from phi = phi0, explicit steps of
+ * dt = h / d.  Reading: the paper fixes neither the discretisation nor the
+ * number of steps ("a few"); the form taken is the one of the reinitialisation
+ * reference it cites (Russo & Smereka): Godunov upwinding of |grad phi| with
+ * the sign of phi0 and, at nodes with an axis neighbour across the zero set
+ * of phi0, the subcell fix that moves phi towards h phi0 / Delta phi0 (Delta
+ * phi0 the largest centred or one-sided difference of phi0 over the axes), so
+ * that the zero set stays where phi0 puts it.  Outside the box a node's own
+ * value is used (one-sided differences vanish there). */
+static double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+static void reinit_step(int dim, int n, const double *p0, const double *p, double *q) {
+    const double h = 2.0 / (n - 1), dt = h / dim;
+    int64_t st[MAXD], nn = 1;
+    for (int a = dim - 1; a >= 0; a--) { st[a] = nn; nn *= n; }
+    for (int64_t i = 0; i < nn; i++) {
+        int j[MAXD];
+        int64_t rem = i;
+        for (int a = 0; a < dim; a++) { j[a] = (int)(rem / st[a]); rem -= (int64_t)j[a] * st[a]; }
+        const double s = sgn(p0[i]);
+        int near = 0;
+        double dmax = 0.0, g = 0.0;
+        for (int a = 0; a < dim; a++) {
+            const int64_t im = j[a] > 0 ? i - st[a] : i, ip = j[a] < n - 1 ? i + st[a] : i;
+            if (p0[im] * p0[i] < 0.0 || p0[ip] * p0[i] < 0.0) near = 1;
+            double d = fabs(p0[ip] - p0[im]) / 2.0;
+            if (fabs(p0[ip] - p0[i]) > d) d = fabs(p0[ip] - p0[i]);
+            if (fabs(p0[i] - p0[im]) > d) d = fabs(p0[i] - p0[im]);
+            if (d > dmax) dmax = d;
+            const double bm = (p[i] - p[im]) / h, fw = (p[ip] - p[i]) / h;   /* backward, forward */
+            double u2, v2;
+            if (s > 0.0) {
+                u2 = bm > 0.0 ? bm * bm : 0.0;
+                v2 = fw < 0.0 ? fw * fw : 0.0;
+            } else {
+                u2 = bm < 0.0 ? bm * bm : 0.0;
+                v2 = fw > 0.0 ? fw * fw : 0.0;
+            }
+            g += u2 > v2 ? u2 : v2;
+        }
+        if (s == 0.0) q[i] = p[i];
+        else if (near && dmax > 0.0) q[i] = p[i] - dt / h * (s * fabs(p[i]) - h * p0[i] / dmax);
+        else q[i] = p[i] - dt * s * (sqrt(g) - 1.0);
+    }
+}
+
+/* phi after `steps` steps from phi0 (n^dim nodes of the box [-1,1]^dim) */
+void orc_reinit(int dim, int n, const double *phi0, int steps, double *phi) {
+    int64_t nn = 1;
+    for (int a = 0; a < dim; a++) nn *= n;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)nn);
+    memcpy(phi, phi0, sizeof(double) * (size_t)nn);
+    for (int k = 0; k < steps; k++) {
+        reinit_step(dim, n, phi0, phi, tmp);
+        memcpy(phi, tmp, sizeof(double) * (size_t)nn);
+    }
+    free(tmp);
+}
+
 /* ------------------------------------------------------------ public API */
 
 static void free_level(Level *L) {

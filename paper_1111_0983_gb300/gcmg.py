@@ -82,6 +82,7 @@ def lib():
             "gcmg_kernel_timing_ex": (st, [vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
             "gcmg_set_rhs_level": (st, [vp, i32, vp, vp]),
             "gcmg_fmg": (st, [vp, i32, vp]),
+            "gcmg_reinit": (st, [i32, i32, vp, i32, vp, vp]),
             "gcmg_launch_counter": (i64, []),
             "gcmg_junction_zone": (st, [vp, i32, vp]),
             "gcmg_junction_solve_set": (st, [vp, i32, vp]),
@@ -288,6 +289,19 @@ class Solver:
 
 def launch_counter():
     return lib().gcmg_launch_counter()
+
+
+def reinit(phi0, steps, stream=None):
+    """Level set phi0 (device tensor, n^dim doubles) after `steps` steps of the
+    reinitialisation equation (gcmg_reinit); returns a new device tensor."""
+    import torch
+    phi0 = phi0.contiguous()
+    out = torch.empty_like(phi0)
+    s = lib().gcmg_reinit(phi0.dim(), phi0.shape[0], _ptr(phi0), int(steps), _ptr(out),
+                          C.c_void_p(stream.cuda_stream) if stream else None)
+    if s != GCMG_OK:
+        raise GcmgError(s, "gcmg_reinit failed")
+    return out
 
 
 class Batch:

@@ -6,6 +6,8 @@ seeded inputs, then whole solves: the converged solution must match the
 oracle's converged discrete solution within 1e-10 relative max-norm over
 Omega_h u Gamma_h, and the per-cycle convergence factors are compared.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -272,6 +274,65 @@ def test_fmg_needs_plain_fp64():
     with pytest.raises(gcmg.GcmgError) as e:
         S.fmg(1, u)
     assert e.value.status == gcmg.GCMG_E_STATE
+
+
+def _ellipse_phi(dim, n):
+    """The paper's rotated ellipse (Sec. 4, not a distance function); in 3D an
+    ellipsoid with the same profile."""
+    X = inputs.coords(dim, n)
+    c, s = math.cos(math.pi / 6), math.sin(math.pi / 6)
+    xr, yr = c * X[0] - s * X[1], s * X[0] + c * X[1]
+    phi = (xr - math.sqrt(2) / 20) ** 2 / 0.563 ** 2 + (yr - math.sqrt(3) / 30) ** 2 / 0.263 ** 2 - 1
+    if dim == 3:
+        phi = phi + X[2] ** 2 / 0.4 ** 2
+    return np.ascontiguousarray(phi)
+
+
+@pytest.mark.parametrize("dim,n,steps", [(2, 129, 20), (2, 65, 7), (2, 65, 0), (3, 33, 12)])
+def test_reinit_matches_oracle(dim, n, steps):
+    gcmg = _gcmg()
+    phi0 = _ellipse_phi(dim, n)
+    out = host(gcmg.reinit(dev(phi0), steps))
+    ref = oracle.reinit(phi0, steps)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.array_equal(np.sign(out), np.sign(phi0))
+
+
+def test_reinit_arguments():
+    gcmg = _gcmg()
+    lib = gcmg.lib()
+    phi = dev(_ellipse_phi(2, 33))
+    assert lib.gcmg_reinit(4, 33, gcmg._ptr(phi), 3, gcmg._ptr(torch.empty_like(phi)), None) == gcmg.GCMG_E_ARG
+    assert lib.gcmg_reinit(2, 33, gcmg._ptr(phi), 3, gcmg._ptr(phi), None) == gcmg.GCMG_E_ARG
+
+
+def test_reinitialised_ellipse_solve_matches_oracle():
+    """End to end: the ellipse level set reinitialised on the GPU, the
+    hierarchy built on it, solved to 1e-10, equals the oracle's solution on
+    its own reinitialisation of the same level set."""
+    gcmg = _gcmg()
+    n, nc = 257, 33
+    phi0 = _ellipse_phi(2, n)
+    phi = host(gcmg.reinit(dev(phi0), 20))
+    P = inputs.circle_paper()   # its u, f and its D/N split (Neumann where B_x > 0)
+    S = gcmg.Solver(phi, nc, rtol=1e-11, max_cycles=200)
+    O = oracle.Oracle(oracle.reinit(phi0, 20), nc)
+    for l in range(S.nlev):
+        S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+        O.set_bc(l, P.bc_types(O.ghosts(l)["B"]))
+    for T in (S, O):
+        G = T.ghosts(0)
+        f, g = P.f_grid(n), P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))
+        if T is S:
+            T.set_rhs(dev(f), dev(g))
+        else:
+            T.set_rhs(f, g)
+    u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    assert st["converged"]
+    uo = O.solve(np.zeros((n, n)), rtol=1e-12, max_cycles=200)[0]
+    assert np.array_equal(S.node_types(0) & 3, O.types(0))
+    assert rel_maxdiff(host(u), uo, O.types(0) > 0) < PARITY
 
 
 def test_errors_are_reported():
