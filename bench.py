@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--impl", default="gcmg", choices=["gcmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="domains of the batched secondary / stars256 run")
+    ap.add_argument("--batch-profile", action="store_true",
+                    help="after the batch measurement, one more batch solve as plain launches between "
+                         "profiler start and stop (for ncu --profile-from-start off)")
     ap.add_argument("--cpu-sample-cycles", type=int, default=2)
     ap.add_argument("--learned", type=int, default=8,
                     help="held-out 513^2 star problems for the learned-guess comparison (0 to skip)")
@@ -615,6 +618,7 @@ def run_gcmg(args):
             t0 = time.perf_counter()
             B, sizes, bun, fused_bytes = build_batch(args.batch, stream)
             setup_s = time.perf_counter() - t0
+            profile_batch = args.batch_profile
             bms, bcyc, best, tune_ms, bad, bst = run_batch_measure(B, max(1, min(args.steps, 3)), 2, stream, flush)
             line["batch"] = {"workload": f"stars{args.batch}", "domains": args.batch,
                              "grid_sizes": {str(n): sizes.count(n) for n in sorted(set(sizes))},
@@ -627,6 +631,15 @@ def run_gcmg(args):
                              "fused_sweep_GBs": fused_bytes / (min(tune_ms) / 1e3) / 1e9,
                              "converged": len(bad) == 0, "not_converged": bad,
                              "worst_rel": max(st["rel_residual"] for st in bst)}
+            if profile_batch:
+                B.set_graph(False)
+                B.solve()   # warm the plain-launch form
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
+                B.solve()
+                torch.cuda.synchronize()
+                torch.cuda.profiler.stop()
+                B.set_graph(True)
             B.close()
         if args.fmg and world == 1:
             line["fmg"] = fmg_entry(args.fmg, stream, flush)

@@ -293,6 +293,12 @@ gcmg_status gcmg_batch_solve(gcmg_batch *batch, gcmg_stats *stats, int *steps);
 /* Copies the solution of domain i to u_dev (device, n_i^2 doubles). */
 gcmg_status gcmg_batch_get_solution(gcmg_batch *batch, int i, double *u_dev);
 
+/* on = 0: later solves run their steps as plain kernel launches from a host
+ * loop that reads the stop condition after each step (the same kernels and
+ * results; for profilers, which cannot look inside the graph's while node);
+ * on = 1 (default): one graph launch per solve. */
+gcmg_status gcmg_batch_set_graph(gcmg_batch *batch, int on);
+
 /* Height of the strips of the interior sweep (each strip: 60 owned columns,
  * one warp): 0 = 8 rows, 1 = 16 rows, 2 = 32 rows. */
 gcmg_status gcmg_batch_set_tiles(gcmg_batch *batch, int variant);

@@ -255,8 +255,9 @@ __global__ void kb_add(const BView64 *__restrict__ V, const BItem *__restrict__ 
 }
 
 // end of one refinement step: per-domain relative residual, loop condition
+// (graph mode: sets the while node's condition; plain launches: writes it to *go)
 __global__ void kb_check(cudaGraphConditionalHandle h, const unsigned long long *norms, const double *r0, double *rel,
-                         int *m, int *active, int *steps_of, int ndom, double rtol, int max_steps) {
+                         int *m, int *active, int *steps_of, int ndom, double rtol, int max_steps, int *go) {
     __shared__ int pending;
     if (threadIdx.x == 0) pending = 0;
     __syncthreads();
@@ -272,7 +273,9 @@ __global__ void kb_check(cudaGraphConditionalHandle h, const unsigned long long 
     __syncthreads();
     if (threadIdx.x == 0) {
         *m = k;
-        cudaGraphSetConditional(h, (pending > 0 && k < max_steps) ? 1u : 0u);
+        const unsigned more = (pending > 0 && k < max_steps) ? 1u : 0u;
+        if (go) *go = (int)more;
+        else cudaGraphSetConditional(h, more);
     }
 }
 
@@ -295,6 +298,8 @@ struct gcmg_batch {
     int device = 0;
     int variant = 0;
     int add_cur = 0;    // the u grid that holds level 0's correction after a cycle
+    bool use_graph = true;   // false: the steps as plain launches (for profilers)
+    int *d_go = nullptr;     // loop condition of the plain-launch form
     double rtol = 1e-10;
     int max_steps = 100;
     // device tables
@@ -637,7 +642,7 @@ void build_graph(gcmg_batch *b) {
     try {
         step_body(b, b->gstream);
         kb_check<<<1, 256, 0, b->gstream>>>(h, b->d_norms, b->d_r0, b->d_rel, b->d_m, b->d_active, b->d_steps,
-                                            (int)b->doms.size(), b->rtol, b->max_steps);
+                                            (int)b->doms.size(), b->rtol, b->max_steps, nullptr);
     } catch (...) {
         cudaGraph_t dummy;
         cudaStreamEndCapture(b->gstream, &dummy);
@@ -732,6 +737,7 @@ gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double
         ck(cudaMalloc(&b->d_m, sizeof(int)), "cudaMalloc");
         ck(cudaMalloc(&b->d_active, count * sizeof(int)), "cudaMalloc");
         ck(cudaMalloc(&b->d_steps, count * sizeof(int)), "cudaMalloc");
+        ck(cudaMalloc(&b->d_go, sizeof(int)), "cudaMalloc");
         return GCMG_OK;
     })
 }
@@ -743,7 +749,7 @@ void gcmg_batch_destroy(gcmg_batch *b) {
     free_tables(b);
     for (gcmg_ctx *c : b->doms) gcmg_destroy(c);
     for (void *p : {(void *)b->d_norms, (void *)b->d_r0, (void *)b->d_rel, (void *)b->d_m, (void *)b->d_active,
-                    (void *)b->d_steps})
+                    (void *)b->d_steps, (void *)b->d_go})
         cudaFree(p);
     if (b->gstream) cudaStreamDestroy(b->gstream);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -757,6 +763,12 @@ int gcmg_batch_size(const gcmg_batch *b) { return b ? (int)b->doms.size() : 0; }
 
 gcmg_ctx *gcmg_batch_domain(gcmg_batch *b, int i) {
     return (b && i >= 0 && i < (int)b->doms.size()) ? b->doms[i] : nullptr;
+}
+
+gcmg_status gcmg_batch_set_graph(gcmg_batch *b, int on) {
+    if (!b) return GCMG_E_ARG;
+    b->use_graph = on != 0;
+    return GCMG_OK;
 }
 
 gcmg_status gcmg_batch_set_tiles(gcmg_batch *b, int variant) {
@@ -871,7 +883,18 @@ gcmg_status gcmg_batch_solve(gcmg_batch *b, gcmg_stats *stats, int *steps) {
         ck(cudaMemcpyAsync(b->d_m, &zero, sizeof(int), cudaMemcpyHostToDevice, s), "m");
         ck(cudaEventRecord(b->ev_in, s), "event");
         ck(cudaStreamWaitEvent(b->gstream, b->ev_in, 0), "wait");
-        ck(cudaGraphLaunch(b->gexec, b->gstream), "cudaGraphLaunch");
+        if (b->use_graph) {
+            ck(cudaGraphLaunch(b->gexec, b->gstream), "cudaGraphLaunch");
+        } else {   // the same steps as plain launches, the loop condition read back each step
+            for (int go = 1; go;) {
+                step_body(b, b->gstream);
+                kb_check<<<1, 256, 0, b->gstream>>>(cudaGraphConditionalHandle{}, b->d_norms, b->d_r0, b->d_rel,
+                                                    b->d_m, b->d_active, b->d_steps, nd, b->rtol, b->max_steps,
+                                                    b->d_go);
+                ck(cudaMemcpyAsync(&go, b->d_go, sizeof(int), cudaMemcpyDeviceToHost, b->gstream), "go");
+                ck(cudaStreamSynchronize(b->gstream), "sync");
+            }
+        }
         ck(cudaEventRecord(b->ev_out, b->gstream), "event");
         ck(cudaStreamWaitEvent(s, b->ev_out, 0), "wait");
         int m = 0;

@@ -95,6 +95,7 @@ def lib():
             "gcmg_batch_solve": (st, [vp, C.POINTER(Stats), C.POINTER(i32)]),
             "gcmg_batch_get_solution": (st, [vp, i32, vp]),
             "gcmg_batch_set_tiles": (st, [vp, i32]),
+            "gcmg_batch_set_graph": (st, [vp, i32]),
             "gcmg_batch_autotune": (st, [vp, C.POINTER(i32), C.POINTER(dbl)]),
         }
         for name, (res, args) in sig.items():
@@ -358,6 +359,10 @@ class Batch:
 
     def set_tiles(self, variant):
         self._check(lib().gcmg_batch_set_tiles(self._h, int(variant)))
+
+    def set_graph(self, on):
+        """False: solves as plain launches (same results; for profilers)."""
+        self._check(lib().gcmg_batch_set_graph(self._h, int(bool(on))))
 
     def autotune(self):
         best = C.c_int()

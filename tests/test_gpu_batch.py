@@ -82,3 +82,25 @@ def test_batch_strip_heights_agree_and_autotune():
     stats, _ = B.solve()
     assert all(s["converged"] for s in stats)
     B.close()
+
+
+def test_batch_plain_launches_equal_graph():
+    """The plain-launch form of a batched solve (for profilers) runs the same
+    kernels: the same steps and bit-identical solutions."""
+    ids, sizes = [4, 9], [257, 129]
+    B, probs, _ = make_batch(ids, sizes)
+    out = []
+    for graph in (True, False):
+        B.set_graph(graph)
+        stats, steps = B.solve()
+        assert all(s["converged"] for s in stats)
+        sols = []
+        for k, n in enumerate(sizes):
+            u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+            B.solution(k, u)
+            sols.append(u.cpu().numpy())
+        out.append((steps, sols))
+    assert out[0][0] == out[1][0]
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
+    B.close()
