@@ -590,6 +590,8 @@ void upload_js(gcmg_ctx *c, int l) {
     g.js_n = (int)L.js_node.size();
     g.js_ncomp = L.js_off.empty() ? 0 : (int)L.js_off.size() - 1;
     g.js_rlen = 0;
+    g.js_aoff_h.clear();
+    g.js_roff_h.clear();
     if (g.js_n == 0) return;
     // padded device layout: component c's rows have mp = m rounded up to a
     // multiple of 4 entries, its defects occupy mp slots from roff[c]
@@ -611,6 +613,8 @@ void upload_js(gcmg_ctx *c, int l) {
     aoff[g.js_ncomp] = na;
     roff[g.js_ncomp] = nr;
     g.js_rlen = nr;
+    g.js_aoff_h = aoff;
+    g.js_roff_h = roff;
     std::vector<double> inv((size_t)na, 0.0);
     for (int k = 0; k < g.js_ncomp; k++) {
         const int m = L.js_off[k + 1] - L.js_off[k], mp = (m + 3) & ~3;

@@ -36,6 +36,16 @@ struct BItem {
     int32_t start;   // tile / component / first node / first ghost / block
 };
 
+// the junction-solve product of up to kJsRows rows of one component of one
+// domain level, with every address resolved on the host
+struct JsItem {
+    const float *a;          // the first row of the chunk in the component's padded inverse
+    const float *r;          // the component's padded defect vector
+    const int32_t *node;     // the chunk's row nodes
+    float *u0, *u1;          // the level's two u grids
+    int rows, mp, dom, pad;  // rows of the chunk, padded row length, domain
+};
+
 
 // one level of one domain, in FP32 (the cycle precision of the batch)
 struct BView32 {
@@ -140,14 +150,46 @@ __global__ void kb_js_defect(const BView32 *__restrict__ V, const BItem *__restr
     });
 }
 
-__global__ void __launch_bounds__(256) kb_js_apply(const BView32 *__restrict__ V,
-                                                            const BItem *__restrict__ it, int cur) {
-    const BItem b = it[blockIdx.x];
-    if (!V[b.view].active[V[b.view].dom]) return;
-    const BView32 &w = V[b.view];
-    const int k0 = b.start + (threadIdx.x >> 5) * kJsWarpRows;
-    js_apply_span<float, kJsWarpRows>(ugrid(w, cur), w.js_node, w.js_comp, w.js_off, w.js_aoff, w.js_roff, w.js_inv,
-                                      w.js_r, k0, min(k0 + kJsWarpRows, w.js_n), threadIdx.x & 31);
+// one chunk a CTA, kJsWarpRows rows a warp (each lane sums its vectors of a
+// row in index order, as js_apply_rows); chain: descriptor -> active flag -> rows
+__global__ void __launch_bounds__(256) kb_js_apply_chunk(const JsItem *__restrict__ items,
+                                                        const int *__restrict__ active, int cur) {
+    const JsItem q = items[blockIdx.x];
+    if (!active[q.dom]) return;
+    using V = Vec16<float>::type;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = w * kJsWarpRows;
+    const int nr = min(kJsWarpRows, q.rows - i0);
+    if (nr <= 0) return;   // uniform over the warp
+    const int nv = q.mp / 4;
+    const V *a = reinterpret_cast<const V *>(q.a + (int64_t)i0 * q.mp);
+    const V *rr = reinterpret_cast<const V *>(q.r);
+    constexpr int U = 2;
+    float s[kJsWarpRows] = {};
+    for (int j0 = lane; j0 < nv; j0 += 32 * U) {
+        V rv[U], av[kJsWarpRows][U];
+#pragma unroll
+        for (int e = 0; e < U; e++)
+            if (j0 + 32 * e < nv) {
+                rv[e] = rr[j0 + 32 * e];
+#pragma unroll
+                for (int i = 0; i < kJsWarpRows; i++)
+                    if (i < nr) av[i][e] = a[(int64_t)i * nv + j0 + 32 * e];
+            }
+#pragma unroll
+        for (int e = 0; e < U; e++)
+            if (j0 + 32 * e < nv)
+#pragma unroll
+                for (int i = 0; i < kJsWarpRows; i++)
+                    if (i < nr) s[i] = Vec16<float>::dot(s[i], av[i][e], rv[e]);
+    }
+    float *u = cur ? q.u1 : q.u0;
+#pragma unroll
+    for (int i = 0; i < kJsWarpRows; i++) {
+        float t = s[i];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0 && i < nr) u[q.node[i0 + i]] += t;
+    }
 }
 
 // defect, restriction with the coarse-ghost transfer, and zero coarse u in
@@ -307,6 +349,7 @@ struct gcmg_batch {
     BView32 *d_v32 = nullptr;
     BView64 *d_v64 = nullptr;
     BItem *d_items = nullptr;
+    JsItem *d_jsitems = nullptr;              // junction-solve chunks (JS_APPLY launches)
     std::vector<int32_t *> tile_bufs;         // tile lists per view for the selected shape
     std::vector<Launch> cycle;                // FP32 V-cycle over all domains
     size_t items64_nodes = 0, items64_ghosts = 0, n_items64_nodes = 0, n_items64_ghosts = 0;
@@ -347,10 +390,11 @@ void free_tables(gcmg_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     b->gexec = nullptr;
     b->graph = nullptr;
-    for (void *p : {(void *)b->d_v32, (void *)b->d_v64, (void *)b->d_items}) cudaFree(p);
+    for (void *p : {(void *)b->d_v32, (void *)b->d_v64, (void *)b->d_items, (void *)b->d_jsitems}) cudaFree(p);
     b->d_v32 = nullptr;
     b->d_v64 = nullptr;
     b->d_items = nullptr;
+    b->d_jsitems = nullptr;
     for (int32_t *t : b->tile_bufs) cudaFree(t);
     b->tile_bufs.clear();
     b->cycle.clear();
@@ -433,6 +477,7 @@ void build_tables(gcmg_batch *b) {
     }
     // items
     std::vector<BItem> items;
+    std::vector<JsItem> jsitems;
     // dense ranges of the launch being built; emit_dense turns them into
     // items of npt * kThreads indexes, npt doubling (up to 8) while the
     // launch keeps at least four waves of 8 CTAs on every SM
@@ -513,14 +558,36 @@ void build_tables(gcmg_batch *b) {
                 dense(b->view_of[d][l], std::max<int64_t>(w.js_n, w.bz.wb ? w.bz.nwb : 0));
             }
             add_dense(Launch::JS_DEFECT, cur[k]);
-            s0 = items.size();
+            // chunks of at most kJsRows rows of one component, addresses resolved here
+            const size_t j0 = jsitems.size();
             for (int d = 0; d < nd; d++) {
                 const int l = (int)b->doms[d]->H.size() - 1 - k;
                 if (l < 0) continue;
-                const int vi = b->view_of[d][l];
-                for (int r = 0; r < v32[vi].js_n; r += kJsRows) items.push_back({vi, (int32_t)r});
+                gcmg_ctx *c = b->doms[d];
+                const DevGeom &g = c->G[l];
+                const DevData<float> &D = c->D32[l];
+                const std::vector<int32_t> &off = c->H[l].js_off;
+                for (int cc = 0; cc < g.js_ncomp; cc++) {
+                    const int o = off[cc], m = off[cc + 1] - o, mp = (m + 3) & ~3;
+                    for (int r0 = o; r0 < o + m; r0 += kJsRows) {
+                        JsItem q{};
+                        q.a = D.js_inv + g.js_aoff_h[cc] + (int64_t)(r0 - o) * mp;
+                        q.r = D.js_r + g.js_roff_h[cc];
+                        q.node = g.js_node + r0;
+                        q.u0 = D.u;
+                        q.u1 = D.u2;
+                        q.rows = std::min(kJsRows, o + m - r0);
+                        q.mp = mp;
+                        q.dom = d;
+                        jsitems.push_back(q);
+                    }
+                }
             }
-            add_launch(Launch::JS_APPLY, s0, 0, cur[k]);
+            if (jsitems.size() > j0) {
+                Launch L{Launch::JS_APPLY, j0, jsitems.size() - j0, 0};
+                L.cur = cur[k];
+                b->cycle.push_back(L);
+            }
         }
     };
     for (int k = kmax; k >= 1; k--) {
@@ -567,6 +634,10 @@ void build_tables(gcmg_batch *b) {
     ck(cudaMemcpy(b->d_v32, v32.data(), v32.size() * sizeof(BView32), cudaMemcpyHostToDevice), "views");
     ck(cudaMemcpy(b->d_v64, v64.data(), v64.size() * sizeof(BView64), cudaMemcpyHostToDevice), "views");
     ck(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice), "items");
+    ck(cudaMalloc(&b->d_jsitems, std::max<size_t>(jsitems.size(), 1) * sizeof(JsItem)), "cudaMalloc");
+    if (!jsitems.empty())
+        ck(cudaMemcpy(b->d_jsitems, jsitems.data(), jsitems.size() * sizeof(JsItem), cudaMemcpyHostToDevice),
+           "junction items");
     b->versions.clear();
     for (gcmg_ctx *c : b->doms) b->versions.push_back(c->version);
 }
@@ -594,7 +665,9 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
             kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps, L.cur);
             break;
         case Launch::JS_DEFECT: kb_js_defect<true><<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
-        case Launch::JS_APPLY: kb_js_apply<<<n, 256, 0, s>>>(b->d_v32, it, L.cur); break;
+        case Launch::JS_APPLY:
+            kb_js_apply_chunk<<<n, 256, 0, s>>>(b->d_jsitems + L.off, b->d_active, L.cur);
+            break;
         case Launch::DESCEND: kb_descend<<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
         case Launch::ZERO: kb_zero<<<n, kThreads, 0, s>>>(b->d_v32, it, 0, L.npt); break;
         case Launch::COARSE: kb_coarse<<<n, 512, L.smem, s>>>(b->d_v32, it); break;

@@ -161,6 +161,8 @@ struct DevGeom {
     int32_t *js_node = nullptr, *js_ghost = nullptr, *js_comp = nullptr, *js_off = nullptr;
     int32_t *js_roff = nullptr, *js_rpos = nullptr;
     int js_rlen = 0;                    // length of the padded defect vector
+    std::vector<int64_t> js_aoff_h;     // host copies of the padded offsets (ncomp + 1)
+    std::vector<int32_t> js_roff_h;
     int64_t *js_aoff = nullptr;
 };
 
