@@ -270,8 +270,9 @@ int64_t gcmg_launch_counter(void);
  * rtol -- is one CUDA-graph launch with a device-side loop. */
 typedef struct gcmg_batch gcmg_batch;
 
-/* Creates `count` domains: params[i] (dim 2, precision 1, gamma 1; nu1, nu2,
- * lambda, junction_sweeps and junction_solve equal across domains; rtol and max_cycles of
+/* Creates `count` domains: params[i] (dim 2, precision 1; gamma (V or W cycles),
+ * nu1, nu2, lambda, junction_sweeps and junction_solve equal across domains; with
+ * gamma = 2 every domain must have the same number of levels; rtol and max_cycles of
  * params[0] apply to the batch) and phi_dev[i] (device, n_i^2 doubles).  The
  * host geometry of the domains is built in parallel threads. */
 gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double *const *phi_dev, void *stream,

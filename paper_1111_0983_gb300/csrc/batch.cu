@@ -590,35 +590,42 @@ void build_tables(gcmg_batch *b) {
             }
         }
     };
-    for (int k = kmax; k >= 1; k--) {
-        cur[k] = 0;   // a level starts from u = 0 in its first grid
+    // the cycle at depth k (0: the coarsest level of every domain), as cycle()
+    // of a single domain: nu1 relaxations, the descent (the coarser level then
+    // starts from u = 0 in its first grid), gamma visits of depth k - 1 (one
+    // when that is the coarsest), the interpolation, nu2 relaxations
+    auto visit = [&](auto &self, int k) -> void {
+        if (k == 0) {
+            for (int d = 0; d < nd; d++) dense(b->view_of[d].back(), b->doms[d]->H.back().nn);
+            add_dense(Launch::ZERO);
+            const size_t s0 = items.size();
+            size_t smem = 0;
+            for (int d = 0; d < nd; d++) {
+                for (int blk = 0; blk < kCoarseBlocks; blk++) items.push_back({b->view_of[d].back(), blk});
+                smem = std::max(smem, sizeof(float) * (size_t)v32[b->view_of[d].back()].nunk);
+            }
+            add_launch(Launch::COARSE, s0, smem);
+            return;
+        }
         for (int r = 0; r < p0.nu1; r++) relax(k);
         for (int d = 0; d < nd; d++) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
             if (l >= 0) dense(b->view_of[d][l], std::max<int64_t>(b->doms[d]->H[l + 1].nn, b->doms[d]->H[l + 1].ng()));
         }
         add_dense(Launch::DESCEND, cur[k]);
-    }
-    {
-        for (int d = 0; d < nd; d++) dense(b->view_of[d].back(), b->doms[d]->H.back().nn);
-        add_dense(Launch::ZERO);
-        const size_t s0 = items.size();
-        size_t smem = 0;
-        for (int d = 0; d < nd; d++) {
-            for (int blk = 0; blk < kCoarseBlocks; blk++) items.push_back({b->view_of[d].back(), blk});
-            smem = std::max(smem, sizeof(float) * (size_t)v32[b->view_of[d].back()].nunk);
-        }
-        add_launch(Launch::COARSE, s0, smem);
-    }
-    for (int k = 1; k <= kmax; k++) {
+        cur[k - 1] = 0;
+        const int gam = k - 1 == 0 ? 1 : p0.gamma;
+        for (int g = 0; g < gam; g++) self(self, k - 1);
         for (int d = 0; d < nd; d++) {
             const int l = (int)b->doms[d]->H.size() - 1 - k;
             if (l >= 0) dense(b->view_of[d][l], b->doms[d]->H[l].nn);
         }
         add_dense(Launch::PROLONG, cur[k], cur[k - 1]);
         for (int r = 0; r < p0.nu2; r++) relax(k);
-    }
-    b->add_cur = cur[kmax];   // every depth ends a cycle with the same grid
+    };
+    cur[kmax] = 0;   // level 0's correction starts from 0 in its first grid
+    visit(visit, kmax);
+    b->add_cur = cur[kmax];
     // FP64 level-0 items (view index = domain)
     b->items64_nodes = items.size();
     for (int d = 0; d < nd; d++) dense(d, b->doms[d]->H[0].nn);
@@ -745,7 +752,7 @@ gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double
     if (count <= 0 || !params || !phi_dev) return GCMG_E_ARG;
     for (int i = 0; i < count; i++) {
         const gcmg_params &p = params[i];
-        if (!phi_dev[i] || check_params(p) != GCMG_OK || p.dim != 2 || p.precision != 1 || p.gamma != 1 ||
+        if (!phi_dev[i] || check_params(p) != GCMG_OK || p.dim != 2 || p.precision != 1 || p.gamma != params[0].gamma ||
             p.nu1 != params[0].nu1 || p.nu2 != params[0].nu2 || p.lambda != params[0].lambda ||
             p.junction_sweeps != params[0].junction_sweeps || p.junction_solve != params[0].junction_solve)
             return GCMG_E_ARG;
@@ -797,6 +804,13 @@ gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double
             }
             b->doms.push_back(c);
         }
+        // W-cycles: the schedule is built per depth from the coarsest level up, so a
+        // domain with fewer levels would sit under a parent depth it does not have
+        // and be cycled gamma times a step
+        if (params[0].gamma > 1)
+            for (gcmg_ctx *c : b->doms)
+                if (c->H.size() != b->doms[0]->H.size())
+                    return bfail(b, GCMG_E_ARG, "W-cycle batches need domains with the same number of levels");
         int smax = 0;
         ck(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device), "attr");
         ck(cudaFuncSetAttribute(kb_local, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "attr");

@@ -104,3 +104,38 @@ def test_batch_plain_launches_equal_graph():
     for a, b in zip(out[0][1], out[1][1]):
         assert np.array_equal(a, b)
     B.close()
+
+
+def test_batch_w_cycle_matches_single_domain_and_oracle():
+    """W-cycles (gamma = 2) in a batch of domains with the same number of
+    levels: the solution of each domain equals a single domain's W-cycle solve
+    and the oracle's, with about as many steps; domains with different numbers
+    of levels are refused."""
+    from paper_1111_0983_gb300 import gcmg
+    with pytest.raises(gcmg.GcmgError) as e:
+        make_batch([0, 1], [129, 257], gamma=2)
+    assert e.value.status == gcmg.GCMG_E_ARG
+    ids, sizes = [1, 3, 8], [257, 257, 257]
+    B, probs, rhs = make_batch(ids, sizes, gamma=2)
+    stats, steps = B.solve()
+    assert all(s["converged"] for s in stats), [s["rel_residual"] for s in stats]
+    for k, (P, n) in enumerate(zip(probs, sizes)):
+        u = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        B.solution(k, u)
+        ub = u.cpu().numpy()
+        S = gcmg.Solver(P.phi_grid(n), 33, precision=1, gamma=2, rtol=1e-11, max_cycles=100)
+        for l in range(S.nlev):
+            S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+        f, g = rhs[k]
+        S.set_rhs(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda())
+        us = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        st = S.solve(us)
+        assert st["converged"] and abs(st["cycles"] - stats[k]["cycles"]) <= 1
+        T = (S.node_types(0) & 3) > 0
+        assert rel_maxdiff(ub, us.cpu().numpy(), T) < PARITY, k
+        if k == 0:
+            O = oracle_for(P, n, 33, gamma=2)
+            uo, _, _ = O.solve(rtol=1e-13, max_cycles=60)
+            assert rel_maxdiff(ub, uo, T) < PARITY
+        S.close()
+    B.close()
