@@ -255,9 +255,12 @@ enum {
 gcmg_status gcmg_set_kernel_timing(gcmg_ctx *ctx, int kind);
 gcmg_status gcmg_kernel_timing(gcmg_ctx *ctx, int64_t *launches, double *total_ms);
 /* As gcmg_kernel_timing, plus the algorithmic bytes of the timed launches
- * (class 4 only, else 0): per launch each distinct staged node's u read, each
- * distinct inside node's f read, each distinct ghost's 3^d weights, g and
- * mu dt read, each written-back node's u write, in the cycle precision. */
+ * that carry the boundary blocks (else 0): per launch each distinct staged
+ * node's u read, each distinct inside node's f read, each distinct ghost's
+ * 3^d weights, g and mu dt read, each written-back node's u write, in the
+ * cycle precision; for the FP32 2D relaxation in one launch (interior sweep
+ * and boundary blocks together; timed under class 0 or 4) also the interior
+ * sweep's u and f read and u written once per inside node. */
 gcmg_status gcmg_kernel_timing_ex(gcmg_ctx *ctx, int64_t *launches, double *total_ms, double *alg_bytes);
 
 /* Number of CUDA kernels this library has launched in the process so far. */

@@ -8,6 +8,7 @@
 #include <exception>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -156,7 +157,8 @@ void free_tracked(gcmg_ctx *c, void *p) {
 void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     int32_t **arrs[] = {&z.node_off, &z.wb_cnt, &z.lnode, &z.int_off, &z.red_cnt, &z.int_glob,
                         &z.int_me, &z.int_nb, &z.gh_off, &z.gh_me, &z.gh_q, &z.gh_stn,
-                        &z.zred, &z.zblack, &z.zghost, &z.wb_list};
+                        &z.zred, &z.zblack, &z.zghost, &z.wb_list, &z.node_base,
+                        &z.pre_off, &z.pre_red_cnt, &z.pre_me, &z.pre_nb, &z.pre_glob};
     for (int32_t **a : arrs) { free_tracked(c, *a); *a = nullptr; }
     z.ncomp = J.ncomp();
     z.max_nodes = J.max_nodes;
@@ -167,6 +169,13 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     z.node_off = upload<int32_t>(c, J.node_off.data(), J.node_off.size());
     z.wb_cnt = upload<int32_t>(c, J.wb_cnt.data(), J.wb_cnt.size());
     z.lnode = upload<int32_t>(c, J.lnode.data(), J.lnode.size());
+    z.node_base = upload<int32_t>(c, J.node_base.data(), J.node_base.size());
+    z.has_pre = !J.pre_me.empty();
+    z.pre_off = upload<int32_t>(c, J.pre_off.data(), J.pre_off.size());
+    z.pre_red_cnt = upload<int32_t>(c, J.pre_red_cnt.data(), J.pre_red_cnt.size());
+    z.pre_me = upload<int32_t>(c, J.pre_me.data(), J.pre_me.size());
+    z.pre_nb = upload<int32_t>(c, J.pre_nb.data(), J.pre_nb.size());
+    z.pre_glob = upload<int32_t>(c, J.pre_glob.data(), J.pre_glob.size());
     z.int_off = upload<int32_t>(c, J.int_off.data(), J.int_off.size());
     z.red_cnt = upload<int32_t>(c, J.red_cnt.data(), J.red_cnt.size());
     z.int_glob = upload<int32_t>(c, J.int_glob.data(), J.int_glob.size());
@@ -252,6 +261,39 @@ template <typename T>
 T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
     const int dim = c->p.dim;
     const DevGeom &g = c->G[l];
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 2D: the interior sweep, the ghost sweep and the band sweeps in one
+        // launch (strips and boundary blocks both read v.u, write out); the
+        // blocks store straight into out, so no write-back is pending
+        if (dim == 2 && extra && g.nstrips > 0 && g.bz.ncomp > 0 && g.bz.in_smem && g.bz.has_pre) {
+            // algorithmic bytes: the interior sweep's (u, f read and u written
+            // once per inside node) and the boundary blocks' distinct values
+            const double bytes = c->timing_kind >= 0
+                                     ? ((double)c->bz_units[l] + 3.0 * (double)c->H[l].n_in) * sizeof(T)
+                                     : 0.0;
+            timer_mark(c, GCMG_KERNEL_SMOOTH, l, bytes);
+            timer_mark(c, GCMG_KERNEL_BOUNDARY, l, bytes);
+            launch_relax2d(v, out, g, lview<T>(g.bz, v), c->p.lambda, c->stream);
+            timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
+            timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+            v.u = out;
+            if (c->p.junction_solve) {
+                const DevData<T> &D = data<T>(c)[l];
+                launch_junction_solve<T>(v, g, D.js_inv, D.js_r, c->stream, nullptr);
+            } else if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
+                if (g.jz.in_smem) {
+                    launch_local<T>(lview<T>(g.jz, v), dim, 0, c->p.junction_sweeps, c->stream);
+                } else {
+                    for (int k = 0; k < c->p.junction_sweeps; k++) {
+                        launch_rb_list<T>(v, dim, g.jz.zred, g.jz.nzred, c->stream);
+                        launch_rb_list<T>(v, dim, g.jz.zblack, g.jz.nzblack, c->stream);
+                        launch_ghost_relax_list<T>(v, dim, g.jz.zghost, g.jz.nzghost, c->stream);
+                    }
+                }
+            }
+            return v.u;
+        }
+    }
     if (dim == 2) {
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
         if (sizeof(T) == 4 && g.nstrips > 0) launch_rb_strip<T>(v, out, g, c->stream);
@@ -1052,7 +1094,7 @@ gcmg_status gcmg_prolong(gcmg_ctx *c, int l, const double *ec, double *out) {
 
 gcmg_status gcmg_set_kernel_timing(gcmg_ctx *c, int kind) {
     if (!c || kind < -1 || kind > GCMG_KERNEL_BOUNDARY) return fail(c, GCMG_E_ARG, "bad kernel class");
-    if (kind == GCMG_KERNEL_BOUNDARY && c->bz_units.empty())
+    if (kind >= 0 && c->bz_units.empty())
         for (const HostLevel &L : c->H) c->bz_units.push_back(boundary_units(L));
     c->timing_kind = kind;
     c->events_used = 0;

@@ -103,7 +103,9 @@ LocalView<T> lview(const LocalDev &z, const LevelView<T> &v, T *wb = nullptr) {
     J.max_int = z.max_int;
     J.max_gh = z.max_gh;
     J.ng = v.ng;
-    J.node_off = z.node_off; J.wb_cnt = z.wb_cnt; J.lnode = z.lnode;
+    J.node_off = z.node_off; J.wb_cnt = z.wb_cnt; J.lnode = z.lnode; J.node_base = z.node_base;
+    J.pre_off = z.pre_off; J.pre_red_cnt = z.pre_red_cnt; J.pre_me = z.pre_me; J.pre_nb = z.pre_nb;
+    J.pre_glob = z.pre_glob;
     J.int_off = z.int_off; J.red_cnt = z.red_cnt; J.int_glob = z.int_glob; J.int_me = z.int_me; J.int_nb = z.int_nb;
     J.gh_off = z.gh_off; J.gh_me = z.gh_me; J.gh_q = z.gh_q; J.gh_stn = z.gh_stn;
     J.wb_list = z.wb_list;

@@ -34,8 +34,14 @@ struct GeomError {
 // inside nodes, black inside nodes, Jacobi ghosts) on its updated nodes.
 struct LocalProgram {
     std::vector<int32_t> node_off{0}, wb_cnt, lnode;
+    std::vector<int32_t> node_base;   // per component: staged nodes without the pre-sweep's (they come last)
     std::vector<int32_t> int_off{0}, red_cnt, int_glob, int_me, int_nb;   // nb: 2 dim per entry
     std::vector<int32_t> gh_off{0}, gh_me, gh_q, gh_stn;                  // stn: 3^dim per entry
+    // optional pre-sweep (2D boundary blocks): the interior red then black
+    // update over every inside node the component reads, from the grid
+    // before the relaxation's interior sweep (entries: slot, 2 dim neighbour
+    // slots, global node for f)
+    std::vector<int32_t> pre_off{0}, pre_red_cnt, pre_me, pre_nb, pre_glob;
     std::vector<int32_t> zred, zblack, zghost;   // union over components (global fallback)
     int max_nodes = 0, max_int = 0, max_gh = 0;
     int ncomp() const { return (int)wb_cnt.size(); }
@@ -122,7 +128,9 @@ void build_boundary_blocks(HostLevel &L, int lambda, int block);
 // A LocalProgram on the device.
 struct LocalDev {
     int ncomp = 0, max_nodes = 0, max_int = 0, max_gh = 0;
-    int32_t *node_off = nullptr, *wb_cnt = nullptr, *lnode = nullptr;
+    int32_t *node_off = nullptr, *wb_cnt = nullptr, *lnode = nullptr, *node_base = nullptr;
+    int32_t *pre_off = nullptr, *pre_red_cnt = nullptr, *pre_me = nullptr, *pre_nb = nullptr, *pre_glob = nullptr;
+    bool has_pre = false;
     int32_t *int_off = nullptr, *red_cnt = nullptr, *int_glob = nullptr, *int_me = nullptr, *int_nb = nullptr;
     int32_t *gh_off = nullptr, *gh_me = nullptr, *gh_q = nullptr, *gh_stn = nullptr;
     int nzred = 0, nzblack = 0, nzghost = 0;
@@ -207,7 +215,8 @@ struct LevelView {
 template <typename T>
 struct LocalView {
     int ncomp, max_nodes, max_int, max_gh, ng;
-    const int32_t *node_off, *wb_cnt, *lnode;
+    const int32_t *node_off, *wb_cnt, *lnode, *node_base;
+    const int32_t *pre_off, *pre_red_cnt, *pre_me, *pre_nb, *pre_glob;
     const int32_t *int_off, *red_cnt, *int_glob, *int_me, *int_nb;
     const int32_t *gh_off, *gh_me, *gh_q, *gh_stn;
     T *u;

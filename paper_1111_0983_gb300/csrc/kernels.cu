@@ -278,6 +278,46 @@ void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s) {
     else pdl_launch(k_rb_interior<T, 3>, dim3(blocks_for((int64_t)v.n * v.n * hc)), dim3(kThreads), 0, s, v, color);
 }
 
+// One FP32 2D relaxation in one launch: the first nsc CTAs sweep the strips
+// (one a warp) and store the inside nodes outside the band; the others run
+// the boundary blocks from the same grid v.u -- each block first takes the
+// interior sweep over what it reads, then the ghost sweep and the band
+// sweeps -- and store their band nodes and ghosts.  Every CTA reads only
+// v.u and the stored node sets are disjoint, so nothing is written twice and
+// no CTA reads a value another one writes.
+template <int SR>
+__global__ void __launch_bounds__(LOCAL_THREADS, 2)
+    k_relax2d(LevelView<float> v, float *__restrict__ out, const int32_t *__restrict__ strips, int ns, int nsc,
+              LocalView<float> J, int lambda) {
+    pdl_wait();
+    if ((int)blockIdx.x < nsc) {
+        const int s = blockIdx.x * (LOCAL_THREADS / 32) + (threadIdx.x >> 5);
+        if (s < ns) rb_strip<float, SR, true>(v, out, strips[s]);   // uniform over the warp
+        return;
+    }
+    local_body<float, 2>(J, v.u, out, (int)blockIdx.x - nsc, 1, lambda, true);
+}
+
+void launch_relax2d(const LevelView<float> &v, float *out, const DevGeom &g, const LocalView<float> &J, int lambda,
+                    cudaStream_t s) {
+    g_launches++;
+    const int per = LOCAL_THREADS / 32;
+    const int nsc = (g.nstrips + per - 1) / per;
+    const size_t smem = local_smem_bytes(J, 2);
+    static size_t opted[3] = {0, 0, 0};   // dynamic shared memory opted in, per strip height
+    const int vi = g.strip_rows == 32 ? 2 : g.strip_rows == 16 ? 1 : 0;
+    if (smem > opted[vi]) {
+        if (vi == 2) cudaFuncSetAttribute(k_relax2d<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else if (vi == 1) cudaFuncSetAttribute(k_relax2d<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else cudaFuncSetAttribute(k_relax2d<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        opted[vi] = smem;
+    }
+    const dim3 grid((unsigned)(nsc + J.ncomp));
+    if (vi == 2) pdl_launch(k_relax2d<32>, grid, dim3(LOCAL_THREADS), smem, s, v, out, g.strips, g.nstrips, nsc, J, lambda);
+    else if (vi == 1) pdl_launch(k_relax2d<16>, grid, dim3(LOCAL_THREADS), smem, s, v, out, g.strips, g.nstrips, nsc, J, lambda);
+    else pdl_launch(k_relax2d<8>, grid, dim3(LOCAL_THREADS), smem, s, v, out, g.strips, g.nstrips, nsc, J, lambda);
+}
+
 // both colours in one pass over the active 2D strips: 4 warps a CTA, one strip a warp
 template <typename T, int SR>
 __global__ void __launch_bounds__(128) k_rb_strip(LevelView<T> v, T *__restrict__ out,

@@ -12,6 +12,10 @@ extern std::atomic<long long> g_launches;   // kernels launched by this library
 
 template <typename T>
 void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s);
+// one FP32 2D relaxation (interior sweep, ghost sweep, band sweeps) in one
+// launch: strips and boundary blocks both read v.u and write out
+void launch_relax2d(const LevelView<float> &v, float *out, const DevGeom &g, const LocalView<float> &J, int lambda,
+                    cudaStream_t s);
 // both colours of a 2D sweep over the active strips (one warp a strip, rows
 // in registers): reads v.u, writes out
 template <typename T>

@@ -204,7 +204,9 @@ constexpr int STRIP_PD = 3;    // rows loaded ahead
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-template <typename T, int SR>
+// INTERIOR_ONLY: store only the inside nodes outside the boundary band (the
+// boundary blocks of the same launch store the band nodes and the ghosts)
+template <typename T, int SR, bool INTERIOR_ONLY = false>
 __device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ out, int strip) {
     constexpr int PD = STRIP_PD;
     constexpr unsigned FULL = 0xffffffffu;
@@ -269,8 +271,11 @@ __device__ __forceinline__ void rb_strip(const LevelView<T> &v, T *__restrict__ 
             if ((kp1 & NODE_KIND) == NODE_IN && !red0) o1 = (mul_rn(h2, fp1) + ra1 + r1 + rb0 + RR) * (T)0.25;
             if (own && o < n) {
                 const int b = o * pitch;
-                if ((kp0 & NODE_KIND) != NODE_OUT && c0 < n) out[b + c0] = o0;
-                if ((kp1 & NODE_KIND) != NODE_OUT && c1 < n) out[b + c1] = o1;
+                auto stored = [](uint8_t k) {
+                    return INTERIOR_ONLY ? (k & (NODE_KIND | NODE_BAND)) == NODE_IN : (k & NODE_KIND) != NODE_OUT;
+                };
+                if (stored(kp0) && c0 < n) out[b + c0] = o0;
+                if (stored(kp1) && c1 < n) out[b + c1] = o1;
             }
         }
         ra0 = rb0;
@@ -334,12 +339,16 @@ __device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, T *__rest
 // the result does not depend on the order in which the blocks run).  The
 // grids are arguments rather than fields of J so that J stays a reference to
 // kernel-parameter or global memory instead of a copy held in registers.
+// pre: also stage the pre-sweep's nodes and run its red then black interior
+// update first (the relaxation's interior sweep over what the component
+// reads, from `src` holding the grid before that sweep; the same sums as the
+// sweep kernels: h^2 f rounded on its own, neighbours in axis order)
 template <typename T, int D>
 __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, T *dst, int c, int lead_ghost,
-                                           int reps) {
+                                           int reps, bool pre = false) {
     constexpr int K = D == 2 ? 9 : 27;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    const int n0 = J.node_off[c], nl = J.node_off[c + 1] - n0;
+    const int n0 = J.node_off[c], nl = pre ? J.node_off[c + 1] - n0 : J.node_base[c];
     const int i0 = J.int_off[c], ni = J.int_off[c + 1] - i0, nred = J.red_cnt[c];
     const int g0 = J.gh_off[c], ngh = J.gh_off[c + 1] - g0;
     T *val = reinterpret_cast<T *>(smem_dyn);
@@ -382,6 +391,20 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
     }
     __syncthreads();
     const T inv = (T)(1.0 / (2 * D));
+    if (pre) {
+        const int p0 = J.pre_off[c], np = J.pre_off[c + 1] - p0, npr = J.pre_red_cnt[c];
+        auto update = [&](int e) {
+            const int k = p0 + e;
+            T s = mul_rn(J.h2, J.f[J.pre_glob[k]]);
+#pragma unroll
+            for (int a = 0; a < 2 * D; a++) s += val[J.pre_nb[(size_t)k * (2 * D) + a]];
+            val[J.pre_me[k]] = s * inv;
+        };
+        for (int e = threadIdx.x; e < npr; e += blockDim.x) update(e);
+        __syncthreads();
+        for (int e = npr + threadIdx.x; e < np; e += blockDim.x) update(e);
+        __syncthreads();
+    }
     auto ghost_sweep = [&]() {
         for (int e = threadIdx.x; e < ngh; e += blockDim.x) {
             T s = 0;

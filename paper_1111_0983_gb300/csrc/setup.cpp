@@ -466,7 +466,11 @@ struct ProgramBuilder {
         }
         return par & 1;
     }
-    void add(const std::vector<int64_t> &upd, const std::vector<int64_t> &wb) {
+    // presweep (2D boundary blocks): the component also takes the relaxation's
+    // interior red / black update over every inside node it reads (red over
+    // those and the red neighbours of their black ones), with the values that
+    // update reads staged after the base nodes
+    void add(const std::vector<int64_t> &upd, const std::vector<int64_t> &wb, bool presweep = false) {
         std::vector<int64_t> nodes(wb);
         std::vector<uint8_t> in_wb_tmp;
         for (int64_t p : wb) local[p] = 0;
@@ -482,10 +486,51 @@ struct ProgramBuilder {
         std::sort(halo.begin(), halo.end());
         halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
         nodes.insert(nodes.end(), halo.begin(), halo.end());
-        for (size_t i = 0; i < nodes.size(); i++) {
-            local[nodes[i]] = (int32_t)i;
-            P.lnode.push_back((int32_t)nodes[i]);
+        for (size_t i = 0; i < nodes.size(); i++) local[nodes[i]] = (int32_t)i;
+        const size_t base = nodes.size();
+        std::vector<int64_t> pre_red, pre_black;
+        if (presweep) {
+            auto inside = [&](int64_t p) { return (L.type[p] & NODE_KIND) == NODE_IN; };
+            for (size_t i = 0; i < base; i++)
+                if (inside(nodes[i])) (parity(nodes[i]) ? pre_black : pre_red).push_back(nodes[i]);
+            std::vector<int64_t> more;   // red neighbours of the black ones, not staged yet
+            for (int64_t p : pre_black) {
+                reads(p, rd);
+                for (int64_t q : rd)
+                    if (inside(q) && local[q] < 0) more.push_back(q);
+            }
+            std::sort(more.begin(), more.end());
+            more.erase(std::unique(more.begin(), more.end()), more.end());
+            for (int64_t q : more) {
+                local[q] = (int32_t)nodes.size();
+                nodes.push_back(q);
+                pre_red.push_back(q);
+            }
+            std::vector<int64_t> ring;   // values the updates read, not staged yet
+            for (const std::vector<int64_t> *set : {&pre_red, &pre_black})
+                for (int64_t p : *set) {
+                    reads(p, rd);
+                    for (int64_t q : rd)
+                        if (local[q] < 0) ring.push_back(q);
+                }
+            std::sort(ring.begin(), ring.end());
+            ring.erase(std::unique(ring.begin(), ring.end()), ring.end());
+            for (int64_t q : ring) {
+                local[q] = (int32_t)nodes.size();
+                nodes.push_back(q);
+            }
+            for (const std::vector<int64_t> *set : {&pre_red, &pre_black})
+                for (int64_t p : *set) {
+                    P.pre_me.push_back(local[p]);
+                    P.pre_glob.push_back((int32_t)p);
+                    reads(p, rd);
+                    for (int64_t q : rd) P.pre_nb.push_back(local[q]);
+                }
         }
+        P.pre_off.push_back((int32_t)P.pre_me.size());
+        P.pre_red_cnt.push_back((int32_t)pre_red.size());
+        for (int64_t p : nodes) P.lnode.push_back((int32_t)p);
+        P.node_base.push_back((int32_t)base);
         P.node_off.push_back((int32_t)P.lnode.size());
         P.wb_cnt.push_back((int32_t)wb.size());
         int nred = 0, nint = 0, ngh = 0;
@@ -657,7 +702,7 @@ void build_boundary_blocks(HostLevel &L, int lambda, int block) {
                     const int64_t p = (int64_t)i * n + j;
                     if (updated(p)) upd.push_back(p);
                 }
-            PB.add(upd, wb);
+            PB.add(upd, wb, true);
             all.insert(all.end(), wb.begin(), wb.end());
         }
     std::sort(all.begin(), all.end());
