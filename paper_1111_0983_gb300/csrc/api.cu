@@ -164,6 +164,10 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     z.max_nodes = J.max_nodes;
     z.max_int = J.max_int;
     z.max_gh = J.max_gh;
+    z.max_pre = J.max_pre;
+    z.max_colour = 0;
+    for (int k = 0; k < J.ncomp(); k++)
+        z.max_colour = std::max({z.max_colour, J.red_cnt[k], J.int_off[k + 1] - J.int_off[k] - J.red_cnt[k]});
     z.nzred = z.nzblack = z.nzghost = 0;
     if (z.ncomp == 0) return;
     z.node_off = upload<int32_t>(c, J.node_off.data(), J.node_off.size());
@@ -265,7 +269,7 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         // FP32 2D: the interior sweep, the ghost sweep and the band sweeps in one
         // launch (strips and boundary blocks both read v.u, write out); the
         // blocks store straight into out, so no write-back is pending
-        if (dim == 2 && extra && g.nstrips > 0 && g.bz.ncomp > 0 && g.bz.in_smem && g.bz.has_pre) {
+        if (dim == 2 && extra && g.nstrips > 0 && g.bz.ncomp > 0 && g.bz.in_smem && g.bz.pre_in_smem) {
             // algorithmic bytes: the interior sweep's (u, f read and u written
             // once per inside node) and the boundary blocks' distinct values
             const double bytes = c->timing_kind >= 0
@@ -355,6 +359,8 @@ void check_program_fits(gcmg_ctx *c, LocalDev &z) {
     ck(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
     z.in_smem = need <= (size_t)dev_max && local_fits_registers(z.max_int);
     if (!z.in_smem) return;    // relaxed from global memory instead
+    LevelView<float> dummy32{};
+    z.pre_in_smem = z.has_pre && local_smem_bytes<float>(lview<float>(z, dummy32), c->p.dim, true) <= (size_t)dev_max;
     // the attribute is per kernel: allow the device maximum once for all levels
     local_prepare<double>(c->p.dim, (size_t)dev_max);
     local_prepare<float>(c->p.dim, (size_t)dev_max);

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(256) kb_local_copyback(const BView32 *__restri
     for_span(b, npt, [&](int64_t i) { local_copyback<float>(V[b.view].bz, u, (int)i); });
 }
 
+template <int EPT>
 __global__ void __launch_bounds__(LOCAL_THREADS, 2) kb_local(const BView32 *__restrict__ V,
                                                              const BItem *__restrict__ it, int junction,
                                                              int lead_ghost, int reps, int cur) {
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 2) kb_local(const BView32 *__re
     if (!V[b.view].active[V[b.view].dom]) return;
     const LocalView<float> &J = junction ? V[b.view].jz : V[b.view].bz;
     float *u = ugrid(V[b.view], cur);
-    local_body<float, 2>(J, u, J.wb ? J.wb : u, b.start, lead_ghost, reps);
+    local_body<float, 2, EPT>(J, u, J.wb ? J.wb : u, b.start, lead_ghost, reps);
 }
 
 // exact junction solve: defects of the solved equations (dense items), then
@@ -330,6 +331,7 @@ struct Launch {
     size_t smem;
     int cur = 0, ccur = 0;   // which u grid holds u (this level, the next coarser one)
     int npt = 1;             // indexes a thread of a dense item
+    int ept = LOCAL_EPT;     // shared-memory programs: inside entries per thread and colour
 };
 
 }  // namespace
@@ -529,6 +531,7 @@ void build_tables(gcmg_batch *b) {
         for (int which = 0; which < 2; which++) {
             s0 = items.size();
             size_t smem = 0;
+            int most = 0;   // most inside entries of one colour in a component
             for (int d = 0; d < nd; d++) {
                 const int l = (int)b->doms[d]->H.size() - 1 - k;
                 if (l < 0) continue;
@@ -538,8 +541,11 @@ void build_tables(gcmg_batch *b) {
                 if (which && (b->doms[d]->p.junction_sweeps <= 0 || p0.junction_solve)) continue;
                 for (int c = 0; c < J.ncomp; c++) items.push_back({vi, c});
                 if (J.ncomp) smem = std::max(smem, smem_of(J));
+                if (J.ncomp) most = std::max(most, J.max_colour);
             }
+            const size_t ncycle = b->cycle.size();
             add_launch(which ? Launch::JUNCTION : Launch::BOUNDARY, s0, smem, cur[k]);
+            if (b->cycle.size() > ncycle && most <= LOCAL_THREADS) b->cycle.back().ept = 1;
             if (!which && !p0.junction_solve) {   // the boundary blocks' write-back, once all have staged
                 for (int d = 0; d < nd; d++) {
                     const int l = (int)b->doms[d]->H.size() - 1 - k;
@@ -666,10 +672,14 @@ void launch_one(const gcmg_batch *b, const Launch &L, cudaStream_t s) {
                 default: launch_fused<32>(b, L, s); break;
             }
             break;
-        case Launch::BOUNDARY: kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda, L.cur); break;
+        case Launch::BOUNDARY:
+            if (L.ept == 1) kb_local<1><<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda, L.cur);
+            else kb_local<LOCAL_EPT><<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 0, 1, lambda, L.cur);
+            break;
         case Launch::BOUNDARY_COPY: kb_local_copyback<<<n, 256, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
         case Launch::JUNCTION:
-            kb_local<<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps, L.cur);
+            if (L.ept == 1) kb_local<1><<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps, L.cur);
+            else kb_local<LOCAL_EPT><<<n, LOCAL_THREADS, L.smem, s>>>(b->d_v32, it, 1, 0, junction_sweeps, L.cur);
             break;
         case Launch::JS_DEFECT: kb_js_defect<true><<<n, kThreads, 0, s>>>(b->d_v32, it, L.cur, L.npt); break;
         case Launch::JS_APPLY:
@@ -813,7 +823,8 @@ gcmg_status gcmg_batch_create(int count, const gcmg_params *params, const double
                     return bfail(b, GCMG_E_ARG, "W-cycle batches need domains with the same number of levels");
         int smax = 0;
         ck(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device), "attr");
-        ck(cudaFuncSetAttribute(kb_local, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "attr");
+        ck(cudaFuncSetAttribute(kb_local<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "attr");
+        ck(cudaFuncSetAttribute(kb_local<LOCAL_EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "attr");
         ck(cudaFuncSetAttribute(kb_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, smax), "attr");
         ck(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
         ck(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "cudaEventCreate");

@@ -102,6 +102,8 @@ LocalView<T> lview(const LocalDev &z, const LevelView<T> &v, T *wb = nullptr) {
     J.max_nodes = z.max_nodes;
     J.max_int = z.max_int;
     J.max_gh = z.max_gh;
+    J.max_pre = z.max_pre;
+    J.max_colour = z.max_colour;
     J.ng = v.ng;
     J.node_off = z.node_off; J.wb_cnt = z.wb_cnt; J.lnode = z.lnode; J.node_base = z.node_base;
     J.pre_off = z.pre_off; J.pre_red_cnt = z.pre_red_cnt; J.pre_me = z.pre_me; J.pre_nb = z.pre_nb;

@@ -43,7 +43,7 @@ struct LocalProgram {
     // slots, global node for f)
     std::vector<int32_t> pre_off{0}, pre_red_cnt, pre_me, pre_nb, pre_glob;
     std::vector<int32_t> zred, zblack, zghost;   // union over components (global fallback)
-    int max_nodes = 0, max_int = 0, max_gh = 0;
+    int max_nodes = 0, max_int = 0, max_gh = 0, max_pre = 0;
     int ncomp() const { return (int)wb_cnt.size(); }
 };
 
@@ -127,10 +127,12 @@ void build_boundary_blocks(HostLevel &L, int lambda, int block);
 // --------------------------------------------------------------- device side
 // A LocalProgram on the device.
 struct LocalDev {
-    int ncomp = 0, max_nodes = 0, max_int = 0, max_gh = 0;
+    int ncomp = 0, max_nodes = 0, max_int = 0, max_gh = 0, max_pre = 0;
+    int max_colour = 0;   // most inside entries of one colour in a component
     int32_t *node_off = nullptr, *wb_cnt = nullptr, *lnode = nullptr, *node_base = nullptr;
     int32_t *pre_off = nullptr, *pre_red_cnt = nullptr, *pre_me = nullptr, *pre_nb = nullptr, *pre_glob = nullptr;
     bool has_pre = false;
+    bool pre_in_smem = false;  // the FP32 program with its pre-sweep lists fits in shared memory
     int32_t *int_off = nullptr, *red_cnt = nullptr, *int_glob = nullptr, *int_me = nullptr, *int_nb = nullptr;
     int32_t *gh_off = nullptr, *gh_me = nullptr, *gh_q = nullptr, *gh_stn = nullptr;
     int nzred = 0, nzblack = 0, nzghost = 0;
@@ -214,7 +216,7 @@ struct LevelView {
 // Kernel view of a LocalDev program in precision T.
 template <typename T>
 struct LocalView {
-    int ncomp, max_nodes, max_int, max_gh, ng;
+    int ncomp, max_nodes, max_int, max_gh, max_pre, max_colour, ng;
     const int32_t *node_off, *wb_cnt, *lnode, *node_base;
     const int32_t *pre_off, *pre_red_cnt, *pre_me, *pre_nb, *pre_glob;
     const int32_t *int_off, *red_cnt, *int_glob, *int_me, *int_nb;

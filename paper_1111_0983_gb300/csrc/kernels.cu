@@ -285,7 +285,8 @@ void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s) {
 // sweeps -- and store their band nodes and ghosts.  Every CTA reads only
 // v.u and the stored node sets are disjoint, so nothing is written twice and
 // no CTA reads a value another one writes.
-template <int SR>
+// EPT: inside entries per thread and colour the boundary blocks need
+template <int SR, int EPT>
 __global__ void __launch_bounds__(LOCAL_THREADS, 2)
     k_relax2d(LevelView<float> v, float *__restrict__ out, const int32_t *__restrict__ strips, int ns, int nsc,
               LocalView<float> J, int lambda) {
@@ -295,7 +296,18 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 2)
         if (s < ns) rb_strip<float, SR, true>(v, out, strips[s]);   // uniform over the warp
         return;
     }
-    local_body<float, 2>(J, v.u, out, (int)blockIdx.x - nsc, 1, lambda, true);
+    local_body<float, 2, EPT>(J, v.u, out, (int)blockIdx.x - nsc, 1, lambda, true);
+}
+
+template <int SR, int EPT>
+void launch_relax2d_as(dim3 grid, size_t smem, cudaStream_t s, const LevelView<float> &v, float *out,
+                       const DevGeom &g, int nsc, const LocalView<float> &J, int lambda) {
+    static size_t opted = 0;   // dynamic shared memory opted in for this instance
+    if (smem > opted) {
+        cudaFuncSetAttribute(k_relax2d<SR, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        opted = smem;
+    }
+    pdl_launch(k_relax2d<SR, EPT>, grid, dim3(LOCAL_THREADS), smem, s, v, out, g.strips, g.nstrips, nsc, J, lambda);
 }
 
 void launch_relax2d(const LevelView<float> &v, float *out, const DevGeom &g, const LocalView<float> &J, int lambda,
@@ -303,19 +315,17 @@ void launch_relax2d(const LevelView<float> &v, float *out, const DevGeom &g, con
     g_launches++;
     const int per = LOCAL_THREADS / 32;
     const int nsc = (g.nstrips + per - 1) / per;
-    const size_t smem = local_smem_bytes(J, 2);
-    static size_t opted[3] = {0, 0, 0};   // dynamic shared memory opted in, per strip height
-    const int vi = g.strip_rows == 32 ? 2 : g.strip_rows == 16 ? 1 : 0;
-    if (smem > opted[vi]) {
-        if (vi == 2) cudaFuncSetAttribute(k_relax2d<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        else if (vi == 1) cudaFuncSetAttribute(k_relax2d<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        else cudaFuncSetAttribute(k_relax2d<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        opted[vi] = smem;
-    }
+    const size_t smem = local_smem_bytes(J, 2, true);
     const dim3 grid((unsigned)(nsc + J.ncomp));
-    if (vi == 2) pdl_launch(k_relax2d<32>, grid, dim3(LOCAL_THREADS), smem, s, v, out, g.strips, g.nstrips, nsc, J, lambda);
-    else if (vi == 1) pdl_launch(k_relax2d<16>, grid, dim3(LOCAL_THREADS), smem, s, v, out, g.strips, g.nstrips, nsc, J, lambda);
-    else pdl_launch(k_relax2d<8>, grid, dim3(LOCAL_THREADS), smem, s, v, out, g.strips, g.nstrips, nsc, J, lambda);
+    if (J.max_colour <= LOCAL_THREADS) {
+        if (g.strip_rows == 32) launch_relax2d_as<32, 1>(grid, smem, s, v, out, g, nsc, J, lambda);
+        else if (g.strip_rows == 16) launch_relax2d_as<16, 1>(grid, smem, s, v, out, g, nsc, J, lambda);
+        else launch_relax2d_as<8, 1>(grid, smem, s, v, out, g, nsc, J, lambda);
+    } else {
+        if (g.strip_rows == 32) launch_relax2d_as<32, LOCAL_EPT>(grid, smem, s, v, out, g, nsc, J, lambda);
+        else if (g.strip_rows == 16) launch_relax2d_as<16, LOCAL_EPT>(grid, smem, s, v, out, g, nsc, J, lambda);
+        else launch_relax2d_as<8, LOCAL_EPT>(grid, smem, s, v, out, g, nsc, J, lambda);
+    }
 }
 
 // both colours in one pass over the active 2D strips: 4 warps a CTA, one strip a warp
@@ -515,9 +525,12 @@ void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv
 }
 
 template <typename T>
-size_t local_smem_bytes(const LocalView<T> &J, int dim) {
+size_t local_smem_bytes(const LocalView<T> &J, int dim, bool pre) {
     const int K = dim == 2 ? 9 : 27;
-    return sizeof(T) * ((size_t)J.max_nodes + (size_t)(K + 3) * J.max_gh) + sizeof(int) * (size_t)(K + 1) * J.max_gh;
+    size_t b = sizeof(T) * ((size_t)J.max_nodes + (size_t)(K + 3) * J.max_gh + J.max_int) +
+               sizeof(int) * ((size_t)(K + 2) * J.max_gh + J.max_nodes + J.max_int);
+    if (pre) b = (b + sizeof(T) - 1) / sizeof(T) * sizeof(T) + (sizeof(T) + sizeof(int) * (2 + 2 * dim)) * (size_t)J.max_pre;
+    return b;
 }
 
 bool local_fits_registers(int max_int_per_colour) { return max_int_per_colour <= LOCAL_THREADS * LOCAL_EPT; }
@@ -589,7 +602,7 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_descend<T>(const LevelView<T> &, const LevelView<T> &, const DevGeom &, const T *, T *, T *, \
                                     T *, cudaStream_t);                                                            \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
-    template size_t local_smem_bytes<T>(const LocalView<T> &, int);                                 \
+    template size_t local_smem_bytes<T>(const LocalView<T> &, int, bool);                                 \
     template void launch_local<T>(const LocalView<T> &, int, int, int, cudaStream_t);               \
     template void launch_local_copyback<T>(const LocalView<T> &, cudaStream_t);                      \
     template void local_prepare<T>(int, size_t);

@@ -60,7 +60,7 @@ template <typename T>
 void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s);
 
 template <typename T>
-size_t local_smem_bytes(const LocalView<T> &J, int dim);
+size_t local_smem_bytes(const LocalView<T> &J, int dim, bool pre = false);
 // shared-memory programs; a program with a write-back grid (J.wb) leaves its
 // write-back to launch_local_copyback or to launch_junction_solve
 template <typename T>

@@ -12,7 +12,7 @@ namespace gcmg {
 namespace dev {
 
 constexpr int LOCAL_THREADS = 512;
-constexpr int LOCAL_EPT = 4;     // inside entries per thread and colour in local programs
+constexpr int LOCAL_EPT = 4;     // inside entries per thread and colour in local programs (at most)
 
 // max-norm reduction on the bit pattern of a non-negative double (monotone
 // for non-negative IEEE values); NaN is folded into +Inf so that it is seen.
@@ -20,6 +20,27 @@ constexpr int LOCAL_EPT = 4;     // inside entries per thread and colour in loca
 // a no-op when the kernel was launched without it).  No kernel triggers its
 // dependents early: measured, a 1025^2 solve went from 4.84 to 5.13 ms when
 // every kernel did, the waiting CTAs taking SM slots from the running grid.
+// asynchronous global -> shared copy of one word (4 or 8 bytes): no register
+// holds it and the issuing thread does not wait for it
+template <typename W>
+__device__ __forceinline__ void cp_async(W *smem, const W *gmem) {
+    static_assert(sizeof(W) == 4 || sizeof(W) == 8, "4- or 8-byte words");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(W) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem) : "memory");
+}
+// waits until this thread's asynchronous copies have landed (and are visible to it)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// start of the pre-sweep lists in a local program's shared memory: the end
+// of the other lists rounded up to a word of T
+template <typename T>
+__device__ __forceinline__ void *local_pre_base(int *end) {
+    return (void *)(((uintptr_t)end + sizeof(T) - 1) & ~(uintptr_t)(sizeof(T) - 1));
+}
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ void atomic_max_abs(unsigned long long *bits, double v) {
@@ -339,11 +360,15 @@ __device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, T *__rest
 // the result does not depend on the order in which the blocks run).  The
 // grids are arguments rather than fields of J so that J stays a reference to
 // kernel-parameter or global memory instead of a copy held in registers.
+// The prologue is two waves of asynchronous copies: the index lists, then
+// the gathers through them (each thread gathers through the entries it copied
+// itself), so a component costs two memory round trips to stage whatever its
+// size.
 // pre: also stage the pre-sweep's nodes and run its red then black interior
 // update first (the relaxation's interior sweep over what the component
 // reads, from `src` holding the grid before that sweep; the same sums as the
 // sweep kernels: h^2 f rounded on its own, neighbours in axis order)
-template <typename T, int D>
+template <typename T, int D, int EPT = LOCAL_EPT>
 __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, T *dst, int c, int lead_ghost,
                                            int reps, bool pre = false) {
     constexpr int K = D == 2 ? 9 : 27;
@@ -356,49 +381,74 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
     T *gv = gw + (size_t)K * J.max_gh;
     T *gcv = gv + J.max_gh;
     T *gt = gcv + J.max_gh;
-    int *gst = reinterpret_cast<int *>(gt + J.max_gh);   // K per ghost
+    T *sf = gt + J.max_gh;                                // f of the inside entries
+    int *gst = reinterpret_cast<int *>(sf + J.max_int);   // K per ghost
     int *gme = gst + (size_t)K * J.max_gh;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) val[i] = src[J.lnode[n0 + i]];
-    for (int e = threadIdx.x; e < ngh; e += blockDim.x) {
-        const int q = J.gh_q[g0 + e];
-        gv[e] = J.gg[q];
-        gcv[e] = J.gc[q];
-        gme[e] = J.gh_me[g0 + e];
-        for (int k = 0; k < K; k++) {
-            gw[e * K + k] = J.gw[(int64_t)k * J.ng + q];
-            gst[e * K + k] = J.gh_stn[(size_t)(g0 + e) * K + k];
-        }
+    int *sln = gme + J.max_gh;                            // staged global nodes
+    int *sgq = sln + J.max_nodes;                         // ghost numbers
+    int *sig = sgq + J.max_gh;                            // inside entries' global nodes
+    T *pf = reinterpret_cast<T *>(local_pre_base<T>(sig + J.max_int));   // pre-sweep: f, slot, node, neighbours
+    int *pme = reinterpret_cast<int *>(pf + J.max_pre);
+    int *pgl = pme + J.max_pre;
+    int *pnb = pgl + J.max_pre;
+    const int p0 = pre ? J.pre_off[c] : 0, np = pre ? J.pre_off[c + 1] - p0 : 0;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < nl; i += nt) cp_async(&sln[i], &J.lnode[n0 + i]);
+    for (int e = tid; e < ngh; e += nt) {
+        cp_async(&sgq[e], &J.gh_q[g0 + e]);
+        cp_async(&gme[e], &J.gh_me[g0 + e]);
     }
-    int rme[LOCAL_EPT], rnb[LOCAL_EPT][2 * D], bme[LOCAL_EPT], bnb[LOCAL_EPT][2 * D];
-    T rf[LOCAL_EPT], bf[LOCAL_EPT];
+    for (int i = tid; i < ngh * K; i += nt) cp_async(&gst[i], &J.gh_stn[(size_t)g0 * K + i]);
+    for (int i = tid; i < ni; i += nt) cp_async(&sig[i], &J.int_glob[i0 + i]);
+    for (int i = tid; i < np; i += nt) {
+        cp_async(&pme[i], &J.pre_me[p0 + i]);
+        cp_async(&pgl[i], &J.pre_glob[p0 + i]);
+    }
+    for (int i = tid; i < np * 2 * D; i += nt) cp_async(&pnb[i], &J.pre_nb[(size_t)p0 * 2 * D + i]);
+    int rme[EPT], rnb[EPT][2 * D], bme[EPT], bnb[EPT][2 * D];
+    T rf[EPT], bf[EPT];
 #pragma unroll
-    for (int e = 0; e < LOCAL_EPT; e++) {
-        const int ir = threadIdx.x + e * blockDim.x, ib = nred + threadIdx.x + e * blockDim.x;
+    for (int e = 0; e < EPT; e++) {
+        const int ir = tid + e * nt, ib = nred + tid + e * nt;
         rme[e] = -1;
         bme[e] = -1;
         if (ir < nred) {
             rme[e] = J.int_me[i0 + ir];
-            rf[e] = J.h2 * J.f[J.int_glob[i0 + ir]];
 #pragma unroll
             for (int a = 0; a < 2 * D; a++) rnb[e][a] = J.int_nb[(size_t)(i0 + ir) * (2 * D) + a];
         }
         if (ib < ni) {
             bme[e] = J.int_me[i0 + ib];
-            bf[e] = J.h2 * J.f[J.int_glob[i0 + ib]];
 #pragma unroll
             for (int a = 0; a < 2 * D; a++) bnb[e][a] = J.int_nb[(size_t)(i0 + ib) * (2 * D) + a];
         }
     }
+    cp_async_wait_all();
+    for (int i = tid; i < nl; i += nt) cp_async(&val[i], &src[sln[i]]);
+    for (int e = tid; e < ngh; e += nt) {
+        const int q = sgq[e];
+        cp_async(&gv[e], &J.gg[q]);
+        cp_async(&gcv[e], &J.gc[q]);
+        for (int k = 0; k < K; k++) cp_async(&gw[e * K + k], &J.gw[(int64_t)k * J.ng + q]);
+    }
+    for (int i = tid; i < ni; i += nt) cp_async(&sf[i], &J.f[sig[i]]);
+    for (int i = tid; i < np; i += nt) cp_async(&pf[i], &J.f[pgl[i]]);
+    cp_async_wait_all();
     __syncthreads();
+#pragma unroll
+    for (int e = 0; e < EPT; e++) {
+        const int ir = tid + e * nt, ib = nred + tid + e * nt;
+        if (ir < nred) rf[e] = J.h2 * sf[ir];
+        if (ib < ni) bf[e] = J.h2 * sf[ib];
+    }
     const T inv = (T)(1.0 / (2 * D));
     if (pre) {
-        const int p0 = J.pre_off[c], np = J.pre_off[c + 1] - p0, npr = J.pre_red_cnt[c];
+        const int npr = J.pre_red_cnt[c];
         auto update = [&](int e) {
-            const int k = p0 + e;
-            T s = mul_rn(J.h2, J.f[J.pre_glob[k]]);
+            T s = mul_rn(J.h2, pf[e]);
 #pragma unroll
-            for (int a = 0; a < 2 * D; a++) s += val[J.pre_nb[(size_t)k * (2 * D) + a]];
-            val[J.pre_me[k]] = s * inv;
+            for (int a = 0; a < 2 * D; a++) s += val[pnb[e * 2 * D + a]];
+            val[pme[e]] = s * inv;
         };
         for (int e = threadIdx.x; e < npr; e += blockDim.x) update(e);
         __syncthreads();
@@ -419,7 +469,7 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
     if (lead_ghost) ghost_sweep();
     for (int it = 0; it < reps; it++) {
 #pragma unroll
-        for (int e = 0; e < LOCAL_EPT; e++)
+        for (int e = 0; e < EPT; e++)
             if (rme[e] >= 0) {
                 T s = rf[e];
 #pragma unroll
@@ -428,7 +478,7 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
             }
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < LOCAL_EPT; e++)
+        for (int e = 0; e < EPT; e++)
             if (bme[e] >= 0) {
                 T s = bf[e];
 #pragma unroll
@@ -439,7 +489,7 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
         ghost_sweep();
     }
     const int nw = J.wb_cnt[c];
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[J.lnode[n0 + i]] = val[i];
+    for (int i = tid; i < nw; i += nt) dst[sln[i]] = val[i];
 }
 
 // write-back node i of the flat list: u = wb

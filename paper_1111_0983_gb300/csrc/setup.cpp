@@ -558,6 +558,7 @@ struct ProgramBuilder {
         P.max_nodes = std::max(P.max_nodes, (int)nodes.size());
         P.max_int = std::max(P.max_int, nint);
         P.max_gh = std::max(P.max_gh, ngh);
+        P.max_pre = std::max(P.max_pre, P.pre_off.back() - P.pre_off[P.pre_off.size() - 2]);
         for (int64_t p : nodes) local[p] = -1;
     }
     // union lists of the updated nodes of all components (global fallback)
