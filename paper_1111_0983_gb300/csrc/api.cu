@@ -434,10 +434,19 @@ double read_norm(gcmg_ctx *c) {
     return v;
 }
 
-// FP64 defect of level 0 and its norm
-double fine_defect_norm(gcmg_ctx *c) {
+// FP64 defect of level 0 and its norm; in the mixed form it also sets up
+// the next FP32 correction problem (see launch_defect_mixed)
+void fine_defect(gcmg_ctx *c) {
     ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
-    launch_defect<double>(view<double>(c, 0, c->D64[0]), c->p.dim, false, c->d_norm, c->stream);
+    if (c->p.precision == 0)
+        launch_defect<double>(view<double>(c, 0, c->D64[0]), c->p.dim, false, c->d_norm, c->stream);
+    else
+        launch_defect_mixed(view<double>(c, 0, c->D64[0]), c->p.dim, c->d_norm, c->D32[0].f, c->D32[0].gg,
+                            c->D32[0].u, c->stream);
+}
+
+double fine_defect_norm(gcmg_ctx *c) {
+    fine_defect(c);
     return read_norm(c);
 }
 
@@ -465,14 +474,12 @@ void loop_body(gcmg_ctx *c) {
         if (u != c->D64[0].u)
             ck(cudaMemcpyAsync(c->D64[0].u, u, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "copy");
     } else {
-        DevData<float> &F0 = c->D32[0];
-        launch_defect_to_f32(g0, c->D64[0].r, F0.f, F0.gg, c->stream);
-        ck(cudaMemsetAsync(F0.u, 0, L0.nn * sizeof(float), c->stream), "memset");   // e = 0
-        float *e = cycle<float>(c, 0, F0.u);
+        // the FP32 problem (right-hand side, e = 0) was set up by the FP64
+        // defect that ended the previous iteration or preceded the loop
+        float *e = cycle<float>(c, 0, c->D32[0].u);
         launch_add_correction(g0, c->D64[0].u, e, c->stream);
     }
-    ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
-    launch_defect<double>(view<double>(c, 0, c->D64[0]), c->p.dim, false, c->d_norm, c->stream);
+    fine_defect(c);
 }
 
 void destroy_graph(gcmg_ctx *c) {

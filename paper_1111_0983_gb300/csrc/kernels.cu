@@ -194,8 +194,11 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
                           T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const T *__restrict__ val) {
     pdl_wait();
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    descend_item<T, D, FROM_R>(F, C, fc, gc, uc, ptr, col, val, i);
+    // the first 32 C.ng threads take the coarse ghost rows, a warp each; the
+    // rest the coarse nodes, a thread each
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nw = 32 * (int64_t)C.ng;
+    if (t < nw) descend_ghost_row_warp<T, D, FROM_R>(F, gc, ptr, col, val, (int)(t >> 5));   // uniform over the warp
+    else if (t - nw < C.nn) descend_node<T, D, FROM_R>(F, C, fc, uc, t - nw);
 }
 
 template <typename T, int D>
@@ -231,20 +234,34 @@ __global__ void k_coarse_solve(LevelView<T> v, const int32_t *__restrict__ unk_n
 }
 
 // ------------------------------------------------------- mixed precision
-// FP64 defect -> FP32 right-hand side of the correction problem
-__global__ void k_defect_to_f32(const uint8_t *__restrict__ type, const double *__restrict__ r64, float *__restrict__ f32,
-                                int64_t nn) {
+// FP64 defect of the finest level (r, its norm) that also sets up the next
+// FP32 correction problem: right-hand side = the defect rounded to FP32 at
+// inside nodes, 0 elsewhere; initial correction e32 = 0 everywhere
+template <int D>
+__global__ void k_defect_interior_mixed(LevelView<double> v, unsigned long long *norm, float *__restrict__ f32,
+                                        float *__restrict__ e32) {
     pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= nn) return;
-    f32[p] = ((type[p] & NODE_KIND) == NODE_IN) ? (float)r64[p] : 0.0f;
+    double val = 0.0;
+    if (p < v.nn) {
+        val = defect_node<double, D>(v, p, false);   // 0 off Omega_h
+        f32[p] = (float)val;
+        e32[p] = 0.0f;
+    }
+    reduce_norm(norm, val);
 }
 
-__global__ void k_ghost_defect_to_f32(const int32_t *__restrict__ gnode, const double *__restrict__ r64,
-                                      float *__restrict__ g32, int ng) {
+// ... and its ghost rows: the ghost defects rounded to FP32
+template <int K>
+__global__ void k_defect_ghost_mixed(LevelView<double> v, unsigned long long *norm, float *__restrict__ g32) {
     pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < ng) g32[q] = (float)r64[gnode[q]];
+    double val = 0.0;
+    if (q < v.ng) {
+        val = defect_ghost_item<double, K>(v, q);
+        g32[q] = (float)val;
+    }
+    reduce_norm(norm, val);
 }
 
 // u64 += e32 on Omega_h u Gamma_h
@@ -422,7 +439,7 @@ void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *f
 template <typename T>
 void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
                     T *uc, cudaStream_t s) {
-    const int64_t n = std::max<int64_t>(C.nn, C.ng);
+    const int64_t n = C.nn + 32 * (int64_t)C.ng;
     constexpr bool from_r = sizeof(T) == 8;   // FP64: one defect pass first (see descend_item)
     if (from_r) launch_defect<T>(F, gf.dim, false, nullptr, s);
     g_launches++;
@@ -570,10 +587,15 @@ void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s)
     pdl_launch(k_mask_unknowns<T>, dim3(blocks_for(nn)), dim3(kThreads), 0, s, type, u, nn);
 }
 
-void launch_defect_to_f32(const DevGeom &g, const double *r64, float *f32, float *g32, cudaStream_t s) {
-    g_launches += g.ng > 0 ? 2 : 1;
-    pdl_launch(k_defect_to_f32, dim3(blocks_for(g.nn)), dim3(kThreads), 0, s, g.type, r64, f32, g.nn);
-    if (g.ng > 0) pdl_launch(k_ghost_defect_to_f32, dim3(blocks_for(g.ng)), dim3(kThreads), 0, s, g.gnode, r64, g32, g.ng);
+void launch_defect_mixed(const LevelView<double> &v, int dim, unsigned long long *norm, float *f32, float *g32,
+                         float *e32, cudaStream_t s) {
+    g_launches += v.ng > 0 ? 2 : 1;
+    if (dim == 2) pdl_launch(k_defect_interior_mixed<2>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, norm, f32, e32);
+    else pdl_launch(k_defect_interior_mixed<3>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, norm, f32, e32);
+    if (v.ng > 0) {
+        if (dim == 2) pdl_launch(k_defect_ghost_mixed<9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32);
+        else pdl_launch(k_defect_ghost_mixed<27>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32);
+    }
 }
 
 void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cudaStream_t s) {

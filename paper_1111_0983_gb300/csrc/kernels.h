@@ -72,7 +72,11 @@ void local_prepare(int dim, size_t smem);
 // whether a program's largest component keeps its inside entries in registers
 bool local_fits_registers(int max_int_per_colour);
 
-void launch_defect_to_f32(const DevGeom &g, const double *r64, float *f32, float *g32, cudaStream_t s);
+// FP64 defect of level 0 and its norm (as launch_defect), also writing the
+// next FP32 correction problem: f32 = defect at inside nodes (0 elsewhere),
+// g32 = ghost defects, e32 = 0
+void launch_defect_mixed(const LevelView<double> &v, int dim, unsigned long long *norm, float *f32, float *g32,
+                         float *e32, cudaStream_t s);
 void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cudaStream_t s);
 
 }  // namespace gcmg

@@ -682,23 +682,56 @@ __device__ __forceinline__ T ghost_defect(const LevelView<T> &v, int q) {
 // the bound (FP64), each fine defect is then computed once instead of once
 // per coarse node whose 3^d neighbourhood holds it (9/4 times on average in
 // 2D).
+template <typename T, int D, bool FROM_R>
+__device__ __forceinline__ void descend_node(const LevelView<T> &F, const LevelView<T> &C, T *__restrict__ fc,
+                                             T *__restrict__ uc, int64_t i) {
+    uc[i] = 0;
+    fc[i] = (C.type[i] & NODE_KIND) == NODE_IN
+                ? partial_transfer_of<T, D>(F, fine_image<D>(i, C.s0, C.s1, F.s0, F.s1), true,
+                                            [&](int64_t q) { return FROM_R ? F.r[q] : inside_defect<T, D>(F, q); })
+                : (T)0;
+}
+
+// the fine ghost defect that entry col of a ghost-transfer row weighs
+template <typename T, int D, bool FROM_R>
+__device__ __forceinline__ T transfer_term(const LevelView<T> &F, int col) {
+    return FROM_R ? F.r[F.gnode[col]] : ghost_defect<T, D == 2 ? 9 : 27>(F, col);
+}
+
+// both parts at index i, the ghost row summed by one thread
 template <typename T, int D, bool FROM_R = false>
 __device__ __forceinline__ void descend_item(const LevelView<T> &F, const LevelView<T> &C, T *__restrict__ fc,
                                              T *__restrict__ gc, T *__restrict__ uc, const int32_t *__restrict__ ptr,
                                              const int32_t *__restrict__ col, const T *__restrict__ val, int64_t i) {
-    if (i < C.nn) {
-        uc[i] = 0;
-        fc[i] = (C.type[i] & NODE_KIND) == NODE_IN
-                    ? partial_transfer_of<T, D>(F, fine_image<D>(i, C.s0, C.s1, F.s0, F.s1), true,
-                                                [&](int64_t q) { return FROM_R ? F.r[q] : inside_defect<T, D>(F, q); })
-                    : (T)0;
-    }
+    if (i < C.nn) descend_node<T, D, FROM_R>(F, C, fc, uc, i);
     if (i < C.ng) {
         T s = 0;
-        for (int j = ptr[i]; j < ptr[i + 1]; j++)
-            s += val[j] * (FROM_R ? F.r[F.gnode[col[j]]] : ghost_defect<T, D == 2 ? 9 : 27>(F, col[j]));
+        for (int j = ptr[i]; j < ptr[i + 1]; j++) s = fma(val[j], transfer_term<T, D, FROM_R>(F, col[j]), s);
         gc[i] = s;
     }
+}
+
+// Coarse ghost row q of the descent by one warp: the lanes fetch the row's
+// terms at once (each a chain of dependent loads), then every lane sums them
+// in the row's order, as descend_item does.
+template <typename T, int D, bool FROM_R>
+__device__ __forceinline__ void descend_ghost_row_warp(const LevelView<T> &F, T *__restrict__ gc,
+                                                       const int32_t *__restrict__ ptr,
+                                                       const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                       int q) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, j0 = ptr[q], len = ptr[q + 1] - j0;
+    T s = 0;
+    for (int base = 0; base < len; base += 32) {
+        T w = 0, x = 0;
+        if (base + lane < len) {
+            w = val[j0 + base + lane];
+            x = transfer_term<T, D, FROM_R>(F, col[j0 + base + lane]);
+        }
+        const int cnt = min(32, len - base);
+        for (int k = 0; k < cnt; k++) s = fma(__shfl_sync(FULL, w, k), __shfl_sync(FULL, x, k), s);
+    }
+    if (lane == 0) gc[q] = s;
 }
 
 
