@@ -193,6 +193,7 @@ template <typename T, int D, bool FROM_R>
 __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T *__restrict__ gc,
                           T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const T *__restrict__ val) {
+    pdl_trigger();
     pdl_wait();
     // the first 32 C.ng threads take the coarse ghost rows, a warp each; the
     // rest the coarse nodes, a thread each
@@ -220,6 +221,7 @@ __global__ void k_ghost_transfer(const T *__restrict__ rf, const int32_t *__rest
 // ------------------------------------------------------------ interpolation
 template <typename T, int D>
 __global__ void k_prolong(LevelView<T> F, LevelView<T> C, const T *__restrict__ e, T *__restrict__ out, bool add) {
+    pdl_trigger();
     pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p < F.nn) prolong_node<T, D>(F, C, e, out, add, p);
@@ -307,13 +309,14 @@ template <int SR, int EPT>
 __global__ void __launch_bounds__(LOCAL_THREADS, 2)
     k_relax2d(LevelView<float> v, float *__restrict__ out, const int32_t *__restrict__ strips, int ns, int nsc,
               LocalView<float> J, int lambda) {
-    pdl_wait();
     if ((int)blockIdx.x < nsc) {
+        pdl_wait();
         const int s = blockIdx.x * (LOCAL_THREADS / 32) + (threadIdx.x >> 5);
         if (s < ns) rb_strip<float, SR, true>(v, out, strips[s]);   // uniform over the warp
         return;
     }
-    local_body<float, 2, EPT>(J, v.u, out, (int)blockIdx.x - nsc, 1, lambda, true);
+    // the block copies its index lists before waiting for the previous launch
+    local_body<float, 2, EPT>(J, v.u, out, (int)blockIdx.x - nsc, 1, lambda, true, true);
 }
 
 template <int SR, int EPT>
@@ -498,6 +501,7 @@ __global__ void __launch_bounds__(256)
     k_js_apply(T *__restrict__ u, const int32_t *__restrict__ node, const int32_t *__restrict__ comp,
                const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
                const T *__restrict__ inv, const T *__restrict__ r, int n) {
+    pdl_trigger();
     pdl_wait();
     const int k0 = blockIdx.x * 8 * R + (threadIdx.x >> 5) * R;
     dev::js_apply_span<T, R>(u, node, comp, off, aoff, roff, inv, r, k0, min(k0 + R, n), threadIdx.x & 31);

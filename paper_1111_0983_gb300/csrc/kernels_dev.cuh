@@ -42,6 +42,10 @@ __device__ __forceinline__ void *local_pre_base(int *end) {
 }
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the launch that depends on this grid start its CTAs now: they run
+// whatever precedes their pdl_wait (reads of data no launch writes) while
+// this grid works
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void atomic_max_abs(unsigned long long *bits, double v) {
     v = fabs(v);
@@ -364,13 +368,15 @@ __device__ __forceinline__ void rb_fused2d_body(const LevelView<T> &v, T *__rest
 // the gathers through them (each thread gathers through the entries it copied
 // itself), so a component costs two memory round trips to stage whatever its
 // size.
+// wait_lists: the caller has not waited for the launches it depends on yet;
+// the index lists (static) are copied first, then it waits.
 // pre: also stage the pre-sweep's nodes and run its red then black interior
 // update first (the relaxation's interior sweep over what the component
 // reads, from `src` holding the grid before that sweep; the same sums as the
 // sweep kernels: h^2 f rounded on its own, neighbours in axis order)
 template <typename T, int D, int EPT = LOCAL_EPT>
 __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, T *dst, int c, int lead_ghost,
-                                           int reps, bool pre = false) {
+                                           int reps, bool pre = false, bool wait_lists = false) {
     constexpr int K = D == 2 ? 9 : 27;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int n0 = J.node_off[c], nl = pre ? J.node_off[c + 1] - n0 : J.node_base[c];
@@ -424,6 +430,7 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
         }
     }
     cp_async_wait_all();
+    if (wait_lists) pdl_wait();   // the gathers read what earlier launches wrote
     for (int i = tid; i < nl; i += nt) cp_async(&val[i], &src[sln[i]]);
     for (int e = tid; e < ngh; e += nt) {
         const int q = sgq[e];
