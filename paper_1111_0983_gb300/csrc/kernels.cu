@@ -309,6 +309,7 @@ template <int SR, int EPT>
 __global__ void __launch_bounds__(LOCAL_THREADS, 2)
     k_relax2d(LevelView<float> v, float *__restrict__ out, const int32_t *__restrict__ strips, int ns, int nsc,
               LocalView<float> J, int lambda) {
+    pdl_trigger();
     if ((int)blockIdx.x < nsc) {
         pdl_wait();
         const int s = blockIdx.x * (LOCAL_THREADS / 32) + (threadIdx.x >> 5);
@@ -486,10 +487,36 @@ __global__ void __launch_bounds__(kThreads) k_js_defect(LevelView<T> v, const in
                                                         const int32_t *__restrict__ ghost,
                                                         const int32_t *__restrict__ rpos, T *__restrict__ r, int n,
                                                         LocalView<T> J) {
-    pdl_wait();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (WB) local_copyback<T>(J, v.u, k);
-    if (k < n) r[rpos[k]] = dev::js_defect<T, D, WB>(v, node[k], ghost[k], J.wb);
+    if (WB) {
+        pdl_wait();
+        local_copyback<T>(J, v.u, k);
+        if (k < n) r[rpos[k]] = dev::js_defect<T, D, WB>(v, node[k], ghost[k], J.wb);
+        return;
+    }
+    // the row's static data (node, ghost stencil and weights) is read before
+    // waiting for the relaxation, u, f and g after it
+    pdl_trigger();
+    if (k >= n) return;
+    const int32_t p = node[k], q = ghost[k], rp = rpos[k];
+    if (q >= 0) {
+        constexpr int K = D == 2 ? 9 : 27;
+        int32_t st[K];
+        T w[K];
+#pragma unroll
+        for (int a = 0; a < K; a++) {
+            st[a] = v.gstn[(int64_t)a * v.ng + q];
+            w[a] = v.gw[(int64_t)a * v.ng + q];
+        }
+        pdl_wait();
+        T s = 0;
+#pragma unroll
+        for (int a = 0; a < K; a++) s += w[a] * v.u[st[a]];   // as js_defect
+        r[rp] = v.gg[q] - s;
+    } else {
+        pdl_wait();
+        r[rp] = dev::js_defect<T, D, false>(v, p, -1);
+    }
 }
 
 // R rows a warp, 8 warps a CTA: R = 4 amortises the per-CTA address chain
@@ -502,8 +529,13 @@ __global__ void __launch_bounds__(256)
                const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
                const T *__restrict__ inv, const T *__restrict__ r, int n) {
     pdl_trigger();
-    pdl_wait();
     const int k0 = blockIdx.x * 8 * R + (threadIdx.x >> 5) * R;
+    if (R == 1) {   // one row a warp: its part of the inverse is loaded before the wait
+        if (k0 < n) dev::js_apply_row_early<T, 8>(u, node, comp, off, aoff, roff, inv, r, k0, threadIdx.x & 31);
+        else pdl_wait();
+        return;
+    }
+    pdl_wait();
     dev::js_apply_span<T, R>(u, node, comp, off, aoff, roff, inv, r, k0, min(k0 + R, n), threadIdx.x & 31);
 }
 

@@ -914,6 +914,38 @@ __device__ __forceinline__ void js_apply_span(T *__restrict__ u, const int32_t *
     }
 }
 
+// one row k by one warp, launched before the defects it needs are written:
+// the row of the inverse (up to MAXV vectors a lane, the rest after) and the
+// row's node are loaded, then the warp waits for the previous launch
+// (pdl_wait) and reads the defects and u.  The same sums as js_apply_rows.
+template <typename T, int MAXV>
+__device__ __forceinline__ void js_apply_row_early(T *__restrict__ u, const int32_t *__restrict__ node,
+                                                   const int32_t *__restrict__ comp, const int32_t *__restrict__ off,
+                                                   const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
+                                                   const T *__restrict__ inv, const T *__restrict__ r, int k,
+                                                   int lane) {
+    using V = typename Vec16<T>::type;
+    const int c = comp[k], o = off[c];
+    const int mp = (off[c + 1] - o + 3) & ~3;
+    const V *a = reinterpret_cast<const V *>(inv + aoff[c] + (int64_t)(k - o) * mp);
+    const int nv = mp / Vec16<T>::n;
+    V av[MAXV];
+#pragma unroll
+    for (int e = 0; e < MAXV; e++)
+        if (lane + 32 * e < nv) av[e] = a[lane + 32 * e];
+    const int nd = node[k];
+    const V *rr = reinterpret_cast<const V *>(r + roff[c]);
+    pdl_wait();
+    const T uo = lane == 0 ? u[nd] : (T)0;
+    T s = 0;
+#pragma unroll
+    for (int e = 0; e < MAXV; e++)
+        if (lane + 32 * e < nv) s = Vec16<T>::dot(s, av[e], rr[lane + 32 * e]);
+    for (int j = lane + 32 * MAXV; j < nv; j += 32) s = Vec16<T>::dot(s, a[j], rr[j]);
+    for (int w = 16; w > 0; w >>= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+    if (lane == 0) u[nd] = uo + s;
+}
+
 // one row k (the form of the fused coarse cycle)
 template <typename T>
 __device__ __forceinline__ void js_apply_row(T *__restrict__ u, const int32_t *__restrict__ node,
