@@ -194,12 +194,12 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
                           T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const T *__restrict__ val) {
     pdl_trigger();
-    pdl_wait();
     // the first 32 C.ng threads take the coarse ghost rows, a warp each; the
-    // rest the coarse nodes, a thread each
+    // rest the coarse nodes, a thread each; both read their static data
+    // before waiting for the previous launch
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nw = 32 * (int64_t)C.ng;
-    if (t < nw) descend_ghost_row_warp<T, D, FROM_R>(F, gc, ptr, col, val, (int)(t >> 5));   // uniform over the warp
-    else if (t - nw < C.nn) descend_node<T, D, FROM_R>(F, C, fc, uc, t - nw);
+    if (t < nw) descend_ghost_row_warp_early<T, D, FROM_R>(F, gc, ptr, col, val, (int)(t >> 5));   // uniform over the warp
+    else if (t - nw < C.nn) descend_node_early<T, D, FROM_R>(F, C, fc, uc, t - nw);
 }
 
 template <typename T, int D>
@@ -222,15 +222,15 @@ __global__ void k_ghost_transfer(const T *__restrict__ rf, const int32_t *__rest
 template <typename T, int D>
 __global__ void k_prolong(LevelView<T> F, LevelView<T> C, const T *__restrict__ e, T *__restrict__ out, bool add) {
     pdl_trigger();
-    pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p < F.nn) prolong_node<T, D>(F, C, e, out, add, p);
+    if (p < F.nn) prolong_node_early<T, D>(F, C, e, out, add, p);   // waits after reading the types
 }
 
 // --------------------------------------------------------------- coarsest
 template <typename T>
 __global__ void k_coarse_solve(LevelView<T> v, const int32_t *__restrict__ unk_node,
                                const int32_t *__restrict__ unk_ghost, const T *__restrict__ Ainv, int m) {
+    pdl_trigger();
     pdl_wait();
     coarse_rows<T>(v, unk_node, unk_ghost, Ainv, m, blockIdx.x, gridDim.x);
 }
@@ -242,6 +242,7 @@ __global__ void k_coarse_solve(LevelView<T> v, const int32_t *__restrict__ unk_n
 template <int D>
 __global__ void k_defect_interior_mixed(LevelView<double> v, unsigned long long *norm, float *__restrict__ f32,
                                         float *__restrict__ e32) {
+    pdl_trigger();
     pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double val = 0.0;
@@ -256,6 +257,7 @@ __global__ void k_defect_interior_mixed(LevelView<double> v, unsigned long long 
 // ... and its ghost rows: the ghost defects rounded to FP32
 template <int K>
 __global__ void k_defect_ghost_mixed(LevelView<double> v, unsigned long long *norm, float *__restrict__ g32) {
+    pdl_trigger();
     pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     double val = 0.0;
@@ -269,6 +271,7 @@ __global__ void k_defect_ghost_mixed(LevelView<double> v, unsigned long long *no
 // u64 += e32 on Omega_h u Gamma_h
 __global__ void k_add_correction(const uint8_t *__restrict__ type, double *__restrict__ u64, const float *__restrict__ e32,
                                  int64_t nn) {
+    pdl_trigger();
     pdl_wait();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= nn) return;

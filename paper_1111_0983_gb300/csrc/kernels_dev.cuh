@@ -594,8 +594,10 @@ __device__ __forceinline__ int64_t fine_image(int64_t X, int64_t cs0, int64_t cs
     return 2 * j0 * fs0 + 2 * j1 * fs1 + 2 * j2;
 }
 
+// wait: call pdl_wait once the node types are read, before any value (the
+// types are fixed while a solve runs; the values come from earlier launches)
 template <typename T, int D, typename Get>
-__device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior, Get value) {
+__device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior, Get value, bool wait = false) {
     const int cube = D == 2 ? 9 : 27;
     const unsigned full = (1u << cube) - 1u;
     unsigned member = 0;
@@ -622,8 +624,9 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
             if (sz > best) { best = sz; count = 1; }
             else if (sz == best) count++;
         }
-        if (count == 0) return (T)0;
     }
+    if (wait) pdl_wait();
+    if (member != full && count == 0) return (T)0;   // no box inside the set
     // weights and sum in T: the weights are dyadic or 1/count, an FP32 cycle
     // keeps its arithmetic on the FP32 pipe
     T acc = 0;
@@ -705,6 +708,21 @@ __device__ __forceinline__ T transfer_term(const LevelView<T> &F, int col) {
     return FROM_R ? F.r[F.gnode[col]] : ghost_defect<T, D == 2 ? 9 : 27>(F, col);
 }
 
+// descend_node in a launch that starts before its predecessor ends: the
+// node types are read first, then pdl_wait, then the defects
+template <typename T, int D, bool FROM_R>
+__device__ __forceinline__ void descend_node_early(const LevelView<T> &F, const LevelView<T> &C,
+                                                   T *__restrict__ fc, T *__restrict__ uc, int64_t i) {
+    T v = 0;
+    if ((C.type[i] & NODE_KIND) == NODE_IN)
+        v = partial_transfer_of<T, D>(F, fine_image<D>(i, C.s0, C.s1, F.s0, F.s1), true,
+                                      [&](int64_t q) { return FROM_R ? F.r[q] : inside_defect<T, D>(F, q); }, true);
+    else
+        pdl_wait();
+    uc[i] = 0;
+    fc[i] = v;
+}
+
 // both parts at index i, the ghost row summed by one thread
 template <typename T, int D, bool FROM_R = false>
 __device__ __forceinline__ void descend_item(const LevelView<T> &F, const LevelView<T> &C, T *__restrict__ fc,
@@ -737,6 +755,60 @@ __device__ __forceinline__ void descend_ghost_row_warp(const LevelView<T> &F, T 
         }
         const int cnt = min(32, len - base);
         for (int k = 0; k < cnt; k++) s = fma(__shfl_sync(FULL, w, k), __shfl_sync(FULL, x, k), s);
+    }
+    if (lane == 0) gc[q] = s;
+}
+
+// descend_ghost_row_warp in a launch that starts before its predecessor
+// ends: the first 32 terms' static data (entry, weight, the fine ghost's
+// stencil nodes and weights) is read, then pdl_wait, then u and g.  The
+// same sums as ghost_defect and descend_item.
+template <typename T, int D, bool FROM_R>
+__device__ __forceinline__ void descend_ghost_row_warp_early(const LevelView<T> &F, T *__restrict__ gc,
+                                                             const int32_t *__restrict__ ptr,
+                                                             const int32_t *__restrict__ col,
+                                                             const T *__restrict__ val, int q) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int K = D == 2 ? 9 : 27;
+    const int lane = threadIdx.x & 31, j0 = ptr[q], len = ptr[q + 1] - j0;
+    T w = 0, x = 0;
+    int cl = 0, gn = 0, st[K];
+    T gw[K];
+    if (lane < len) {
+        w = val[j0 + lane];
+        cl = col[j0 + lane];
+        if (FROM_R) {
+            gn = F.gnode[cl];
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                st[k] = F.gstn[(int64_t)k * F.ng + cl];
+                gw[k] = F.gw[(int64_t)k * F.ng + cl];
+            }
+        }
+    }
+    pdl_wait();
+    if (lane < len) {
+        if (FROM_R) {
+            x = F.r[gn];
+        } else {
+            T t = 0;
+#pragma unroll
+            for (int k = 0; k < K; k++) t += gw[k] * F.u[st[k]];
+            x = F.gg[cl] - t;
+        }
+    }
+    T s = 0;
+    const int cnt = min(32, len);
+    for (int k = 0; k < cnt; k++) s = fma(__shfl_sync(FULL, w, k), __shfl_sync(FULL, x, k), s);
+    for (int base = 32; base < len; base += 32) {   // rows longer than a warp
+        T w2 = 0, x2 = 0;
+        if (base + lane < len) {
+            w2 = val[j0 + base + lane];
+            x2 = transfer_term<T, D, FROM_R>(F, col[j0 + base + lane]);
+        }
+        const int c2 = min(32, len - base);
+        for (int k = 0; k < c2; k++) s = fma(__shfl_sync(FULL, w2, k), __shfl_sync(FULL, x2, k), s);
     }
     if (lane == 0) gc[q] = s;
 }
@@ -800,6 +872,55 @@ __device__ __forceinline__ void prolong_node(const LevelView<T> &F, const LevelV
                 num += w * e[X];
                 den += w;
             }
+    const T val = den > (T)0 ? num / den : (T)0;
+    if (add) out[p] += val;
+    else out[p] = val;
+}
+
+// prolong_node in a launch that starts before its predecessor ends: the
+// node's and its parents' types are read first, then pdl_wait, then e and
+// out.  The same sums as prolong_node.
+template <typename T, int D>
+__device__ __forceinline__ void prolong_node_early(const LevelView<T> &F, const LevelView<T> &C,
+                                                   const T *__restrict__ e, T *__restrict__ out, bool add, int64_t p) {
+    const uint8_t k = F.type[p] & NODE_KIND;
+    const bool on = k == NODE_IN || k == NODE_GHOST;
+    int j[3] = {0, 0, 0};
+    int64_t rem = p;
+    j[0] = (int)idx_div(rem, F.s0);
+    rem -= (int64_t)j[0] * F.s0;
+    if (D == 2) {
+        j[1] = (int)rem;
+    } else {
+        j[1] = (int)idx_div(rem, F.s1);
+        j[2] = (int)(rem - (int64_t)j[1] * F.s1);
+    }
+    const int n1 = (j[0] & 1) ? 2 : 1, n2 = (j[1] & 1) ? 2 : 1, n3 = (D == 3 && (j[2] & 1)) ? 2 : 1;
+    int64_t X[8];
+    unsigned use = 0;   // parents in Omega_2h u Gamma_2h, in (a, b, c) order
+    int np = 0;
+    if (on)
+        for (int a = 0; a < n1; a++)
+            for (int b = 0; b < n2; b++)
+                for (int c = 0; c < n3; c++) {
+                    const int64_t x = (int64_t)(j[0] / 2 + a) * C.s0 +
+                                      (D == 2 ? (int64_t)(j[1] / 2 + b) : (int64_t)(j[1] / 2 + b) * C.s1 + (j[2] / 2 + c));
+                    const uint8_t kc = C.type[x] & NODE_KIND;
+                    if (kc == NODE_IN || kc == NODE_GHOST) use |= 1u << np;
+                    X[np++] = x;
+                }
+    pdl_wait();
+    if (!on) {
+        if (!add) out[p] = 0;
+        return;
+    }
+    T num = 0, den = 0;
+    const T w = (T)1 / (T)(n1 * n2 * n3);   // a power of two: exact
+    for (int i = 0; i < np; i++)
+        if ((use >> i) & 1u) {
+            num += w * e[X[i]];
+            den += w;
+        }
     const T val = den > (T)0 ? num / den : (T)0;
     if (add) out[p] += val;
     else out[p] = val;
