@@ -462,6 +462,34 @@ __global__ void k_loop_check(cudaGraphConditionalHandle h, const unsigned long l
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
+// start of a graph solve: r0 = ||(f, g)|| (slot 1 of d_norm) and the
+// defect's norm (slot 0) are on the device; records r0 and rel[0], zeroes
+// the cycle count and opens the loop unless the start already converged
+__global__ void k_loop_start(cudaGraphConditionalHandle h, const unsigned long long *bits, double *r0_out,
+                             double *rel, int *m, double rtol) {
+    const double r0 = __longlong_as_double((long long)bits[1]);
+    const double rel0 = r0 > 0.0 ? __longlong_as_double((long long)bits[0]) / r0 : 0.0;
+    *r0_out = r0;
+    rel[0] = rel0;
+    *m = 0;
+    cudaGraphSetConditional(h, (r0 > 0.0 && !(rel0 <= rtol)) ? 1u : 0u);
+}
+
+// what precedes the loop in a graph solve: ||(f, g)||, the first defect and
+// its norm (in the mixed form also the first FP32 problem), k_loop_start
+void solve_prologue(gcmg_ctx *c, cudaGraphConditionalHandle h) {
+    const DevGeom &g0 = c->G[0];
+    const HostLevel &L0 = c->H[0];
+    ck(cudaMemsetAsync(c->d_norm + 1, 0, sizeof(unsigned long long), c->stream), "memset");
+    const int64_t cnt = std::max<int64_t>(L0.nn, L0.ng());
+    const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 4096);
+    k_rhs_norm<<<nb, 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn, c->D64[0].gg, g0.ng, c->d_norm + 1);
+    g_launches++;
+    fine_defect(c);
+    k_loop_start<<<1, 1, 0, c->stream>>>(h, c->d_norm, c->d_r0, c->d_rel, c->d_m, c->p.rtol);
+    g_launches++;
+}
+
 // one iteration of the solve loop: a cycle (plain) or a refinement step
 // (mixed), then the FP64 defect and its norm
 void loop_body(gcmg_ctx *c) {
@@ -494,9 +522,42 @@ void build_graph(gcmg_ctx *c) {
     if (!c->gstream) ck(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
     if (!c->ev_in) ck(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "cudaEventCreate");
     if (!c->ev_out) ck(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+    if (!c->h_res) ck(cudaMallocHost((void **)&c->h_res, sizeof(gcmg_ctx::SolveResult)), "cudaMallocHost");
     ck(cudaGraphCreate(&c->graph, 0), "cudaGraphCreate");
     cudaGraphConditionalHandle h;
     ck(cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault), "conditional handle");
+    // the prologue, captured into the graph ahead of the loop node
+    cudaStream_t saved0 = c->stream;
+    c->stream = c->gstream;
+    ck(cudaStreamBeginCaptureToGraph(c->gstream, c->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+       "begin capture");
+    const long long before0 = g_launches.load();
+    try {
+        solve_prologue(c, h);
+        c->graph_pro_kernels = g_launches.load() - before0;
+        g_launches -= c->graph_pro_kernels;   // counted when executed
+    } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(c->gstream, &dummy);
+        c->stream = saved0;
+        throw;
+    }
+    c->stream = saved0;
+    {
+        cudaGraph_t captured;
+        ck(cudaStreamEndCapture(c->gstream, &captured), "end capture");
+    }
+    // the prologue is a chain: its one node without dependents precedes the loop
+    size_t nn = 0;
+    ck(cudaGraphGetNodes(c->graph, nullptr, &nn), "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(nn);
+    ck(cudaGraphGetNodes(c->graph, nodes.data(), &nn), "graph nodes");
+    std::vector<cudaGraphNode_t> leaves;
+    for (cudaGraphNode_t x : nodes) {
+        size_t nd = 0;
+        ck(cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &nd), "graph edges");
+        if (nd == 0) leaves.push_back(x);
+    }
     alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)] = {};
     cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_raw);
     np.type = cudaGraphNodeTypeConditional;
@@ -504,7 +565,7 @@ void build_graph(gcmg_ctx *c) {
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     cudaGraphNode_t node;
-    ck(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &np), "cudaGraphAddNode");
+    ck(cudaGraphAddNode(&node, c->graph, leaves.data(), nullptr, leaves.size(), &np), "cudaGraphAddNode");
     cudaGraph_t body = np.conditional.phGraph_out[0];
     cudaStream_t saved = c->stream;
     c->stream = c->gstream;
@@ -788,6 +849,7 @@ void gcmg_destroy(gcmg_ctx *c) {
     for (void *p : c->allocs) cudaFree(p);
     if (c->d_coarse) cudaFree(c->d_coarse);
     if (c->h_norm) cudaFreeHost(c->h_norm);
+    if (c->h_res) cudaFreeHost(c->h_res);
     delete c;
 }
 
@@ -933,42 +995,47 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
         if (u_dev != u)
             ck(cudaMemcpyAsync(u, u_dev, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u in");
         launch_mask_unknowns<double>(g0.type, u, L0.nn, c->stream);
-        // ||r0|| = ||(f, g)||
-        ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
-        {
-            const int64_t cnt = std::max<int64_t>(L0.nn, L0.ng());
-            const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 4096);
-            k_rhs_norm<<<nb, 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn, c->D64[0].gg, g0.ng, c->d_norm);
-            g_launches++;
-        }
-        check_launch();
-        const double r0 = read_norm(c);
         gcmg_stats st;
         std::memset(&st, 0, sizeof(st));
-        st.r0_norm = r0;
-        double rel = 0.0;
-        if (r0 > 0.0) rel = fine_defect_norm(c) / r0;
-        st.rel[0] = rel;
         int m = 0;
-        bool ok = (r0 == 0.0) || rel <= c->p.rtol;
-        if (!ok && c->use_graph && c->timing_kind < 0) {
+        double rel = 0.0;
+        bool ok = false;
+        if (c->use_graph && c->timing_kind < 0) {
+            // one graph: ||(f, g)||, the first defect, then the loop; one
+            // read-back at the end
             if (!c->gexec) build_graph(c);
-            const int zero = 0;
-            ck(cudaMemcpyAsync(c->d_r0, &r0, sizeof(double), cudaMemcpyHostToDevice, c->stream), "r0");
-            ck(cudaMemcpyAsync(c->d_m, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream), "m");
             ck(cudaEventRecord(c->ev_in, c->stream), "event");
             ck(cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "wait");
             ck(cudaGraphLaunch(c->gexec, c->gstream), "cudaGraphLaunch");
             ck(cudaEventRecord(c->ev_out, c->gstream), "event");
             ck(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "wait");
-            ck(cudaMemcpyAsync(&m, c->d_m, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "m");
+            gcmg_ctx::SolveResult *R = c->h_res;
+            ck(cudaMemcpyAsync(&R->r0, c->d_r0, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "r0");
+            ck(cudaMemcpyAsync(R->rel, c->d_rel, sizeof(R->rel), cudaMemcpyDeviceToHost, c->stream), "rel");
+            ck(cudaMemcpyAsync(&R->m, c->d_m, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "m");
             ck(cudaStreamSynchronize(c->stream), "sync");
-            g_launches += c->graph_kernels * m;
+            m = R->m;
+            g_launches += c->graph_pro_kernels + c->graph_kernels * m;
             const int kept = std::min(m, 256);
-            ck(cudaMemcpy(&st.rel[1], c->d_rel + 1, kept * sizeof(double), cudaMemcpyDeviceToHost), "rel");
+            std::memcpy(st.rel, R->rel, (kept + 1) * sizeof(double));
+            st.r0_norm = R->r0;
             rel = st.rel[kept];
-            ok = rel <= c->p.rtol;
+            ok = R->r0 == 0.0 || rel <= c->p.rtol;
         } else {
+            // ||r0|| = ||(f, g)||
+            ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
+            {
+                const int64_t cnt = std::max<int64_t>(L0.nn, L0.ng());
+                const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 4096);
+                k_rhs_norm<<<nb, 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn, c->D64[0].gg, g0.ng, c->d_norm);
+                g_launches++;
+            }
+            check_launch();
+            const double r0 = read_norm(c);
+            st.r0_norm = r0;
+            if (r0 > 0.0) rel = fine_defect_norm(c) / r0;
+            st.rel[0] = rel;
+            ok = (r0 == 0.0) || rel <= c->p.rtol;
             while (!ok && m < c->p.max_cycles) {
                 loop_body(c);
                 check_launch();

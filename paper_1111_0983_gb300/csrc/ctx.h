@@ -43,6 +43,12 @@ struct gcmg_ctx {
     int *d_m = nullptr;
     bool use_graph = true;
     long long graph_kernels = 0;            // kernels in one loop iteration
+    long long graph_pro_kernels = 0;        // kernels before the loop
+    struct SolveResult {                    // what a graph solve reports back (pinned)
+        double r0;
+        double rel[257];
+        int m;
+    } *h_res = nullptr;
     // event timing of one fine-level kernel class during solves
     int timing_kind = -1;
     std::vector<cudaEvent_t> events;
