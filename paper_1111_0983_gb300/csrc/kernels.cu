@@ -193,9 +193,16 @@ template <typename T, int D, bool FROM_R>
 __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T *__restrict__ gc,
                           T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const T *__restrict__ val) {
-    pdl_trigger();
-    // the first 32 C.ng threads take the coarse ghost rows, a warp each; the
-    // rest the coarse nodes, a thread each; both read their static data
+    if (sizeof(T) == 4) pdl_trigger();
+    if (D == 3 || sizeof(T) == 8) {
+        // 3D ghost-transfer rows are long (tens to hundreds of terms): the
+        // thread-per-index form, which measured 8x faster there
+        pdl_wait();
+        descend_item<T, D, FROM_R>(F, C, fc, gc, uc, ptr, col, val, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+        return;
+    }
+    // 2D: the first 32 C.ng threads take the coarse ghost rows, a warp each;
+    // the rest the coarse nodes, a thread each; both read their static data
     // before waiting for the previous launch
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nw = 32 * (int64_t)C.ng;
     if (t < nw) descend_ghost_row_warp_early<T, D, FROM_R>(F, gc, ptr, col, val, (int)(t >> 5));   // uniform over the warp
@@ -221,7 +228,7 @@ __global__ void k_ghost_transfer(const T *__restrict__ rf, const int32_t *__rest
 // ------------------------------------------------------------ interpolation
 template <typename T, int D>
 __global__ void k_prolong(LevelView<T> F, LevelView<T> C, const T *__restrict__ e, T *__restrict__ out, bool add) {
-    pdl_trigger();
+    if (sizeof(T) == 4) pdl_trigger();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p < F.nn) prolong_node_early<T, D>(F, C, e, out, add, p);   // waits after reading the types
 }
@@ -230,7 +237,7 @@ __global__ void k_prolong(LevelView<T> F, LevelView<T> C, const T *__restrict__ 
 template <typename T>
 __global__ void k_coarse_solve(LevelView<T> v, const int32_t *__restrict__ unk_node,
                                const int32_t *__restrict__ unk_ghost, const T *__restrict__ Ainv, int m) {
-    pdl_trigger();
+    if (sizeof(T) == 4) pdl_trigger();
     pdl_wait();
     coarse_rows<T>(v, unk_node, unk_ghost, Ainv, m, blockIdx.x, gridDim.x);
 }
@@ -314,9 +321,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 2)
               LocalView<float> J, int lambda) {
     pdl_trigger();
     if ((int)blockIdx.x < nsc) {
-        pdl_wait();
         const int s = blockIdx.x * (LOCAL_THREADS / 32) + (threadIdx.x >> 5);
-        if (s < ns) rb_strip<float, SR, true>(v, out, strips[s]);   // uniform over the warp
+        const int32_t st = s < ns ? strips[s] : 0;   // static: read before the wait
+        pdl_wait();
+        if (s < ns) rb_strip<float, SR, true>(v, out, st);   // uniform over the warp
         return;
     }
     // the block copies its index lists before waiting for the previous launch
@@ -446,7 +454,7 @@ void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *f
 template <typename T>
 void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
                     T *uc, cudaStream_t s) {
-    const int64_t n = C.nn + 32 * (int64_t)C.ng;
+    const int64_t n = (gf.dim == 3 || sizeof(T) == 8) ? std::max<int64_t>(C.nn, C.ng) : C.nn + 32 * (int64_t)C.ng;
     constexpr bool from_r = sizeof(T) == 8;   // FP64: one defect pass first (see descend_item)
     if (from_r) launch_defect<T>(F, gf.dim, false, nullptr, s);
     g_launches++;
@@ -499,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_js_defect(LevelView<T> v, const in
     }
     // the row's static data (node, ghost stencil and weights) is read before
     // waiting for the relaxation, u, f and g after it
-    pdl_trigger();
+    if (sizeof(T) == 4) pdl_trigger();
     if (k >= n) return;
     const int32_t p = node[k], q = ghost[k], rp = rpos[k];
     if (q >= 0) {
@@ -531,7 +539,7 @@ __global__ void __launch_bounds__(256)
     k_js_apply(T *__restrict__ u, const int32_t *__restrict__ node, const int32_t *__restrict__ comp,
                const int32_t *__restrict__ off, const int64_t *__restrict__ aoff, const int32_t *__restrict__ roff,
                const T *__restrict__ inv, const T *__restrict__ r, int n) {
-    pdl_trigger();
+    if (sizeof(T) == 4) pdl_trigger();
     const int k0 = blockIdx.x * 8 * R + (threadIdx.x >> 5) * R;
     if (R == 1) {   // one row a warp: its part of the inverse is loaded before the wait
         if (k0 < n) dev::js_apply_row_early<T, 8>(u, node, comp, off, aoff, roff, inv, r, k0, threadIdx.x & 31);
