@@ -212,6 +212,37 @@ def test_mixed_precision_refinement_matches_oracle(P, n, nc):
     assert rn <= 2e-11 * st["r0_norm"]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_solve_start(precision):
+    """A graph solve computes ||(f, g)|| and the first defect on the device and
+    opens its loop there: r0, rel[0], the cycles and the solution equal those of
+    the launch-by-launch loop (kernel timing on); a start that already meets the
+    tolerance runs no cycle and leaves u as it was; a zero right-hand side
+    returns at once with u = 0."""
+    P, n, nc = inputs.flower(), 129, 33
+    S = solver_for(P, n, nc, precision=precision, rtol=1e-10, max_cycles=100)
+    f, g = set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    S.set_kernel_timing(S.KERNEL_SMOOTH)
+    u2 = torch.zeros_like(u)
+    st2 = S.solve(u2)
+    S.set_kernel_timing(-1)
+    assert st["converged"] and st2["converged"]
+    assert st["r0_norm"] == st2["r0_norm"] > 0 and st["rel"][0] == st2["rel"][0] == 1.0
+    assert st["cycles"] == st2["cycles"] > 0
+    assert np.array_equal(host(u), host(u2))
+    u3 = u.clone()
+    st3 = S.solve(u3)
+    assert st3["converged"] and st3["cycles"] == 0 and st3["rel"][0] <= 1e-10
+    assert torch.equal(u3, u)
+    S.set_rhs(dev(np.zeros_like(f)), dev(np.zeros_like(g)))
+    u4 = torch.zeros_like(u)
+    st4 = S.solve(u4)
+    assert st4["converged"] and st4["cycles"] == 0 and st4["r0_norm"] == 0.0
+    assert not torch.any(u4)
+
+
 def test_solve_host_equals_device():
     P, n, nc = inputs.flower(), 257, 33
     S = solver_for(P, n, nc)
