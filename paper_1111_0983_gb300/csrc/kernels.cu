@@ -193,10 +193,13 @@ template <typename T, int D, bool FROM_R>
 __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T *__restrict__ gc,
                           T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
                           const T *__restrict__ val) {
+    // FP32 instances let their dependents start now; FP64 ones do not (their
+    // dependents are large FP64 launches whose early CTAs measured slower)
     if (sizeof(T) == 4) pdl_trigger();
     if (D == 3 || sizeof(T) == 8) {
-        // 3D ghost-transfer rows are long (tens to hundreds of terms): the
-        // thread-per-index form, which measured 8x faster there
+        // the thread-per-index form: 3D ghost-transfer rows are long (tens
+        // to hundreds of terms), where it measured 8x faster than a warp a
+        // row; in FP64 the terms are plain reads of r
         pdl_wait();
         descend_item<T, D, FROM_R>(F, C, fc, gc, uc, ptr, col, val, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
         return;
