@@ -91,6 +91,13 @@ typedef struct {
     int fused_coarse_n;      /* 2D FP32 V-cycles: the levels with at most this many nodes a side
                                 run as one launch (a cluster of CTAs with barriers between the
                                 steps; same results); 0: one launch per step */
+    int smoother;            /* 0: the paper's relaxation (ghost relaxation + lambda band sweeps);
+                                1: its Kaczmarz comparison (Sec. 4, "Comparison with the
+                                Kaczmarz and the block relaxations"): a Gauss-Seidel sweep over
+                                the inside nodes, then lambda Kaczmarz sweeps over the ghost
+                                equations and the band's inside equations, rows ordered by the
+                                colour sum_a (j_a mod 5) 5^a of their node.  2D, plain FP64
+                                (precision 0), junction relaxation off; else GCMG_E_ARG */
 } gcmg_params;
 
 /* Per-solve report.  rel[m] = ||r^(m)||_inf / ||r^(0)||_inf for m = 0..cycles

@@ -39,7 +39,7 @@ class Params(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("lam", C.c_int), ("gamma", C.c_int),
                 ("mode", C.c_int), ("extra_once", C.c_int), ("delta_over_h", C.c_double),
                 ("c_dirichlet", C.c_double), ("c_neumann_factor", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double),
-                ("junction_solve", C.c_int)]
+                ("junction_solve", C.c_int), ("smoother", C.c_int)]
 
 
 _lib = None
@@ -80,6 +80,7 @@ def lib():
         L.orc_restrict_weights.argtypes = [vp, C.c_int, i64, C.c_int, vp]
         L.orc_prolong.argtypes = [vp, C.c_int, vp, vp]
         L.orc_relax.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
+        L.orc_kaczmarz_row.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp]
         L.orc_assemble.restype = i64
         L.orc_assemble.argtypes = [vp, C.c_int, vp, vp, vp, vp]
         L.orc_solve.restype = C.c_int
@@ -110,7 +111,7 @@ class Oracle:
 
     def __init__(self, phi, n_coarse, nu1=2, nu2=1, lam=5, gamma=1, mode=0, extra_once=0,
                  delta_over_h=3.0, c_dirichlet=0.9, c_neumann_factor=0.9, junction_sweeps=None, junction_radius=None,
-                 junction_solve=None):
+                 junction_solve=None, smoother=0):
         phi = np.ascontiguousarray(phi, dtype=np.float64)
         self.dim = phi.ndim
         # junction relaxation defaults: 2D an exact solve of the zone within
@@ -125,7 +126,7 @@ class Oracle:
         self.n = phi.shape[0]
         assert all(s == self.n for s in phi.shape)
         self.params = Params(nu1, nu2, lam, gamma, mode, extra_once, delta_over_h, c_dirichlet,
-                             c_neumann_factor, junction_sweeps, junction_radius, junction_solve)
+                             c_neumann_factor, junction_sweeps, junction_radius, junction_solve, smoother)
         L = lib()
         self._h = L.orc_create(self.dim, self.n, n_coarse, _p(phi), C.byref(self.params))
         if not self._h:
@@ -257,6 +258,15 @@ class Oracle:
         out = np.empty(self.shape(l))
         lib().orc_prolong(self._h, l, _p(e), _p(out))
         return out
+
+    def kaczmarz_row(self, i, u, f, g, l=0):
+        """One Kaczmarz step (Sec. 4 comparison) on the row of node i of level
+        l: an inside node of the band or a ghost."""
+        u = np.array(u, dtype=np.float64, order="C", copy=True)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        lib().orc_kaczmarz_row(self._h, l, C.c_int64(int(i)), _p(u), _p(f), _p(g))
+        return u
 
     def relax(self, u, f, g, l=0, with_extra=True):
         u = np.array(u, dtype=np.float64, order="C", copy=True)

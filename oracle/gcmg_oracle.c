@@ -47,6 +47,8 @@ typedef struct {
     int junction_sweeps;   /* mu_J: local sweeps near Dirichlet/Neumann junctions (0: none) */
     double junction_radius;/* R_J: junction zone radius, in units of h of each level */
     int junction_solve;    /* 1: solve the zone's equations exactly instead of mu_J sweeps */
+    int smoother;          /* 0: the paper's relaxation; 1: its Kaczmarz comparison (Sec. 4,
+                              "Comparison with the Kaczmarz and the block relaxations") */
 } orc_params;
 
 typedef struct {
@@ -783,7 +785,76 @@ static void extra_sweeps(Oracle *O, Level *L) {
     }
 }
 
+/* ----------------------------------------- Kaczmarz comparison smoother
+ * Sec. 4, "Comparison with the Kaczmarz and the block relaxations": a
+ * Gauss-Seidel sweep over the inside nodes, then lambda Kaczmarz sweeps over
+ * the set J of the ghost equations and the inside equations within delta of
+ * the boundary (the band).  A Kaczmarz step on row j of L u = b moves u along
+ * the row: u += (b_j - <l_j, u>) / ||l_j||^2 l_j.
+ * Rows: an inside node i, scaled by h^2 (the step does not depend on a row's
+ * scale): 2d u_i - sum of its 2d neighbours = h^2 f_i; a ghost q: its
+ * boundary equation, sum_k w_k u_k = g_q.
+ * Reading: the paper leaves the order of J open ("for j in J").  The order
+ * taken: colour c(i) = sum_a (j_a mod 5) 5^a of the row's node, colours in
+ * increasing c, nodes in increasing index within a colour.  A row's support
+ * lies within 2 nodes of its node on every axis, so two rows of one colour
+ * (5 or more apart on some axis) share no unknown: within a colour the order
+ * does not change the result, and the colours can be swept in parallel. */
+static int kaczmarz_colour(const Level *L, int64_t i) {
+    int j[MAXD];
+    idx_to_j(L, i, j);
+    int c = 0, m = 1;
+    for (int a = 0; a < L->dim; a++) { c += (j[a] % 5) * m; m *= 5; }
+    return c;
+}
+
+/* one Kaczmarz step on the row of node i (an inside band node or a ghost);
+ * sums in the order written, each product rounded on its own */
+static void kaczmarz_row(Level *L, int64_t i) {
+    double *u = L->u;
+    if (L->type[i] == T_INT) {
+        const int d = L->dim;
+        double s = 0.0;
+        for (int a = 0; a < d; a++) s += u[i + L->st[a]] + u[i - L->st[a]];
+        const double r = (L->h * L->h * L->f[i] + s) - 2.0 * d * u[i];
+        const double t = r / (double)(4 * d * d + 2 * d);
+        u[i] += 2.0 * d * t;
+        for (int a = 0; a < d; a++) { u[i + L->st[a]] -= t; u[i - L->st[a]] -= t; }
+    } else if (L->type[i] == T_GHOST) {
+        const int64_t q = L->gid[i];
+        const double *w = (L->bc[q] == BC_D) ? L->wD : L->wN;
+        double s = 0.0, n2 = 0.0;
+        for (int k = 0; k < L->nk[q]; k++) {
+            s += w[q * MAXK + k] * u[L->stn[q * MAXK + k]];
+            n2 += w[q * MAXK + k] * w[q * MAXK + k];
+        }
+        const double t = (L->g[q] - s) / n2;
+        for (int k = 0; k < L->nk[q]; k++) u[L->stn[q * MAXK + k]] += t * w[q * MAXK + k];
+    }
+}
+
+static int in_kaczmarz_set(const Level *L, int64_t i) {
+    return (L->type[i] == T_INT && L->band[i]) || L->type[i] == T_GHOST;
+}
+
+static void kaczmarz_sweep(Level *L) {
+    const int ncol = L->dim == 2 ? 25 : 125;
+    for (int c = 0; c < ncol; c++)
+        for (int64_t i = 0; i < L->nn; i++)
+            if (in_kaczmarz_set(L, i) && kaczmarz_colour(L, i) == c) kaczmarz_row(L, i);
+}
+
+static void kaczmarz_relax(Oracle *O, Level *L, int with_extra) {
+    rb_sweep(L, 0);
+    const int sweeps = with_extra ? O->p.lambda : 1;
+    for (int m = 0; m < sweeps; m++) kaczmarz_sweep(L);
+}
+
 static void smooth(Oracle *O, Level *L, int nu) {
+    if (O->p.smoother == 1) {
+        for (int k = 0; k < nu; k++) kaczmarz_relax(O, L, 1);
+        return;
+    }
     for (int k = 0; k < nu; k++) {
         base_relax(O, L);
         if (!O->p.extra_once) extra_sweeps(O, L);
@@ -1177,6 +1248,11 @@ void *orc_create(int dim, int n, int n_coarse, const double *phi, const orc_para
         strcpy(O->err, "bad grid sizes");
         return O;
     }
+    if (p->smoother < 0 || p->smoother > 1) {
+        O->status = ORC_E_ARG;
+        strcpy(O->err, "bad smoother");
+        return O;
+    }
     int nlev = 1, m = n;
     while (m > n_coarse) {
         if ((m - 1) % 2) { O->status = ORC_E_ARG; strcpy(O->err, "n-1 not a power-of-two multiple of n_coarse-1"); return O; }
@@ -1396,11 +1472,27 @@ void orc_relax(void *h, int l, double *u, const double *f, const double *g, int 
     memcpy(L->u, u, sizeof(double) * (size_t)L->nn);
     for (int64_t i = 0; i < L->nn; i++) L->f[i] = (L->type[i] == T_INT) ? f[i] : 0.0;
     memcpy(L->g, g, sizeof(double) * (size_t)L->ng);
+    if (O->p.smoother == 1) {
+        kaczmarz_relax(O, L, with_extra);
+        memcpy(u, L->u, sizeof(double) * (size_t)L->nn);
+        return;
+    }
     base_relax(O, L);
     if (with_extra) {
         extra_sweeps(O, L);
         if (O->p.junction_sweeps || O->p.junction_solve) junction_relax(O, L);
     }
+    memcpy(u, L->u, sizeof(double) * (size_t)L->nn);
+}
+
+/* One Kaczmarz step (Sec. 4) on the row of node i of level l, applied to u
+ * in place, with the level's right-hand side f, g (inside f at inside nodes). */
+void orc_kaczmarz_row(void *h, int l, int64_t i, double *u, const double *f, const double *g) {
+    Level *L = &((Oracle *)h)->L[l];
+    memcpy(L->u, u, sizeof(double) * (size_t)L->nn);
+    for (int64_t k = 0; k < L->nn; k++) L->f[k] = (L->type[k] == T_INT) ? f[k] : 0.0;
+    memcpy(L->g, g, sizeof(double) * (size_t)L->ng);
+    kaczmarz_row(L, i);
     memcpy(u, L->u, sizeof(double) * (size_t)L->nn);
 }
 

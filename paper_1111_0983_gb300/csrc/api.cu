@@ -42,6 +42,34 @@ T *upload(gcmg_ctx *c, const T *host, size_t count) {
 
 int kslots(int dim) { return dim == 2 ? 9 : 27; }
 
+// Rows of the Kaczmarz comparison smoother on level l (2D): the ghosts and the
+// inside nodes of the band, grouped by the colour (i mod 5) + 5 (j mod 5) of
+// their node, increasing node index within a colour
+void build_kaczmarz_rows(gcmg_ctx *c, int l) {
+    const HostLevel &L = c->H[l];
+    std::vector<int32_t> gid(L.nn, -1);
+    for (int64_t q = 0; q < L.ng(); q++) gid[L.ghost_node[q]] = (int32_t)q;
+    std::vector<std::vector<int32_t>> by(25);
+    for (int64_t p = 0; p < L.nn; p++) {
+        const int kind = L.type[p] & NODE_KIND;
+        const bool in = kind == NODE_IN && (L.type[p] & NODE_BAND);
+        if (!in && kind != NODE_GHOST) continue;
+        const int64_t i = p / L.n, j = p % L.n;
+        by[(int)(i % 5) + 5 * (int)(j % 5)].push_back(in ? (int32_t)p : -(gid[p] + 1));
+    }
+    std::vector<int32_t> rows, off{0};
+    for (const auto &b : by) {
+        rows.insert(rows.end(), b.begin(), b.end());
+        off.push_back((int32_t)rows.size());
+    }
+    if ((int)c->kz_rows.size() <= l) {
+        c->kz_rows.resize(l + 1, nullptr);
+        c->kz_off.resize(l + 1);
+    }
+    c->kz_rows[l] = upload<int32_t>(c, rows.data(), rows.size());
+    c->kz_off[l] = off;
+}
+
 // slot-major copies of per-ghost / per-extension-node arrays
 template <typename S, typename T>
 std::vector<T> slot_major(const std::vector<S> &src, int64_t count, int width, int used) {
@@ -304,6 +332,11 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         else launch_rb_fused2d<T>(v, out, g.tiles, g.ntiles, c->stream);
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
         v.u = out;
+        if (c->p.smoother == 1) {   // the Kaczmarz comparison (plain FP64 only)
+            if constexpr (std::is_same<T, double>::value)
+                launch_kaczmarz(v, c->kz_rows[l], c->kz_off[l], extra ? c->p.lambda : 1, c->stream);
+            return v.u;
+        }
     } else {
         for (int colour = 0; colour < 2; colour++) {
             timer_mark(c, GCMG_KERNEL_SMOOTH, l);
@@ -632,6 +665,9 @@ gcmg_status check_params(const gcmg_params &q) {
     if (p->precision < 0 || p->precision > 1 || p->max_cycles < 1 || p->max_cycles > 256) return GCMG_E_ARG;
     if (p->junction_sweeps < 0 || p->junction_radius < 0.0 || p->junction_radius > 64.0) return GCMG_E_ARG;
     if (p->junction_solve < 0 || p->junction_solve > 1 || p->fused_coarse_n < 0) return GCMG_E_ARG;
+    if (p->smoother < 0 || p->smoother > 1) return GCMG_E_ARG;
+    if (p->smoother == 1 && (p->dim != 2 || p->precision != 0 || p->junction_solve || p->junction_sweeps))
+        return GCMG_E_ARG;
     return GCMG_OK;
 }
 
@@ -653,6 +689,8 @@ gcmg_status create_from_levels(const gcmg_params &q, std::vector<HostLevel> &&H,
         ck(cudaGetDevice(&c->device), "cudaGetDevice");
         const int nl = (int)c->H.size();
         for (int l = 0; l < nl; l++) upload_geometry(c, l);
+        if (p->smoother == 1)
+            for (int l = 0; l < nl; l++) build_kaczmarz_rows(c, l);
         if (p->dim == 2)
             for (int l = 0; l < nl; l++) {
                 upload_program(c, c->H[l].boundary, c->G[l].bz);
@@ -806,6 +844,7 @@ gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
     p->junction_sweeps = dim == 3 ? 10 : 0;
     p->junction_radius = dim == 3 ? 2.0 : 20.0;
     p->fused_coarse_n = 0;   // measured slower than the per-level launches on GB300
+    p->smoother = 0;
     return GCMG_OK;
 }
 

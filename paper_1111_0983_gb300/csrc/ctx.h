@@ -31,6 +31,11 @@ struct gcmg_ctx {
     double *relax_a = nullptr, *relax_b = nullptr;   // scratch grids of the single-step relaxation
     void *d_coarse = nullptr;
     size_t coarse_smem = 0;
+    // Kaczmarz comparison smoother (smoother = 1): per level, the rows (an
+    // inside band node p as p, ghost q as -(q + 1)) grouped by colour, and
+    // the 26 colour offsets
+    std::vector<int32_t *> kz_rows;
+    std::vector<std::vector<int32_t>> kz_off;
     unsigned long long *d_norm = nullptr;   // two slots: defect norm, rhs norm
     unsigned long long *h_norm = nullptr;   // pinned
     // the solve loop as one CUDA graph: a device-side while loop over cycles

@@ -10,6 +10,12 @@ namespace gcmg {
 
 extern std::atomic<long long> g_launches;   // kernels launched by this library
 
+// Kaczmarz comparison smoother (kaczmarz.cu): `sweeps` sweeps, each over the
+// colours c = 0..24 in order, a launch each, of the rows rows[off[c] ..
+// off[c + 1]) (inside band node p as p, ghost q as -(q + 1)); in place on v.u
+void launch_kaczmarz(const LevelView<double> &v, const int32_t *rows, const std::vector<int32_t> &off, int sweeps,
+                     cudaStream_t s);
+
 template <typename T>
 void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s);
 // one FP32 2D relaxation (interior sweep, ghost sweep, band sweeps) in one

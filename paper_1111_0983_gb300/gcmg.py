@@ -26,7 +26,7 @@ class Params(C.Structure):
                 ("lam", C.c_int), ("gamma", C.c_int), ("delta_over_h", C.c_double), ("c_dirichlet", C.c_double),
                 ("c_neumann_factor", C.c_double), ("precision", C.c_int), ("max_cycles", C.c_int),
                 ("rtol", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double),
-                ("junction_solve", C.c_int), ("fused_coarse_n", C.c_int)]
+                ("junction_solve", C.c_int), ("fused_coarse_n", C.c_int), ("smoother", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -412,3 +412,71 @@ def test_fused_coarse_cycle_equals_per_level_launches(P, n, nc):
         S.close()
     assert np.array_equal(sols[0], sols[1])
     assert np.array_equal(hists[0], hists[1])
+
+
+# ------------------------------------------------ Kaczmarz comparison (Sec. 4)
+KACZ = dict(smoother=1, junction_solve=0, junction_sweeps=0)
+
+
+def test_kaczmarz_relaxation_matches_oracle():
+    """The Kaczmarz comparison smoother (Sec. 4), plain FP64: one relaxation
+    (Gauss-Seidel over the inside nodes, then lambda Kaczmarz sweeps over the
+    ghosts and the band's inside nodes, colour by colour) on every level equals
+    the oracle's element by element."""
+    P, n, nc = inputs.disk(), 65, 17
+    S = solver_for(P, n, nc, **KACZ)
+    O = oracle_for(P, n, nc, rhs=False, **KACZ)
+    rng = np.random.default_rng(5)
+    for l in range(S.nlev - 1):
+        shape = S.shape(l)
+        T = O.types(l)
+        unk = T > 0
+        u = np.where(unk, rng.uniform(-1, 1, shape), 0.0)
+        f = np.where(T == 1, rng.uniform(-1, 1, shape), 0.0)
+        g = rng.uniform(-1, 1, O.num_ghosts(l))
+        u_d = dev(u)
+        S.relax(l, u_d, dev(f), dev(g), True)
+        assert rel_maxdiff(host(u_d), O.relax(u, f, g, l, True), unk) < 1e-12, l
+
+
+def test_kaczmarz_solve_matches_oracle():
+    """V-cycles with the Kaczmarz comparison smoother: the converged solution
+    matches the oracle's within 1e-10 and the per-cycle factors match; the
+    factor is reported beside the paper relaxation's (it falls more slowly
+    with lambda, Sec. 4)."""
+    import time
+    P, n, nc = inputs.disk(), 65, 17
+    S = solver_for(P, n, nc, rtol=1e-11, max_cycles=200, **KACZ)
+    set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    O, u_o, norms = oracle_solution(P, n, nc, **KACZ)
+    T = O.types(0)
+    assert st["converged"], st["rel"]
+    assert rel_maxdiff(host(u), u_o, T > 0) < PARITY
+    k = min(6, st["cycles"], len(norms) - 1)
+    rel_o = norms[: k + 1] / norms[0]
+    assert np.allclose(st["rel"][1: k + 1], rel_o[1: k + 1], rtol=1e-6, atol=1e-11)
+    for sm, kw in (("kaczmarz", KACZ), ("paper", dict(junction_solve=0, junction_sweeps=0))):
+        for lam in (3, 5):
+            S2 = solver_for(P, n, nc, rtol=1e-10, max_cycles=200, lam=lam, **kw)
+            set_problem_rhs(S2, P, n)
+            u2 = torch.zeros_like(u)
+            S2.solve(u2)
+            u2.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = S2.solve(u2)
+            ms = (time.perf_counter() - t0) * 1e3
+            rho = s2["rel"][-1] ** (1.0 / s2["cycles"])
+            print(f"disk 65^2 FP64 {sm} lambda={lam}: cycles {s2['cycles']} rho {rho:.3f} {ms:.2f} ms")
+
+
+def test_kaczmarz_needs_plain_fp64_2d():
+    gcmg = _gcmg()
+    for P, n, nc, kw in ((inputs.disk(), 65, 17, dict(smoother=1)),
+                         (inputs.disk(), 65, 17, dict(KACZ, precision=1)),
+                         (inputs.torus(), 33, 17, dict(KACZ))):
+        with pytest.raises(gcmg.GcmgError) as e:
+            solver_for(P, n, nc, **kw)
+        assert e.value.status == gcmg.GCMG_E_ARG

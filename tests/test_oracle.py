@@ -505,3 +505,74 @@ def test_reinit_distance_function(dim, n):
         assert np.array_equal(np.sign(q)[sdf != 0], np.sign(sdf)[sdf != 0])
         errs.append(err)
     assert errs[0] / errs[1] > 1.7, errs
+
+
+# ------------------------------------------------ Kaczmarz comparison (Sec. 4)
+def _kaczmarz_oracle(P, n, nc, lam=5, **kw):
+    return oracle_for(P, n, nc, smoother=1, lam=lam, junction_solve=0, junction_sweeps=0, **kw)
+
+
+def test_kaczmarz_step_moves_along_its_row_and_satisfies_it():
+    """Sec. 4, Kaczmarz iteration: a step on row j changes u only on the row's
+    support, by a multiple of the row (inside node: 2d t at the node, -t at
+    each neighbour; ghost: t w_k at its stencil nodes), and leaves that row's
+    equation satisfied."""
+    P, n = inputs.disk(), 33
+    O = _kaczmarz_oracle(P, n, 9)
+    f, g = problem_rhs(O, P, n)
+    T = O.types(0)
+    band = O.band(0)
+    rng = np.random.default_rng(7)
+    u0 = np.where(T > 0, rng.standard_normal(T.shape), 0.0)
+    r0, _ = O.defect(u0)
+    # an inside node of the band
+    i = int(np.flatnonzero(((T == 1) & (band > 0)).ravel())[17])
+    u1 = O.kaczmarz_row(i, u0, f, g).ravel()
+    d = u1 - u0.ravel()
+    nb = [i + 1, i - 1, i + n, i - n]
+    assert set(np.flatnonzero(d)) <= set([i] + nb)
+    t = -d[nb[0]]
+    assert t != 0.0 and np.allclose(d[nb], -t, rtol=1e-12, atol=0) and d[i] == pytest.approx(4 * t, rel=1e-12)
+    r1, _ = O.defect(u1.reshape(T.shape))
+    assert abs(r1.ravel()[i]) <= 1e-12 * abs(r0.ravel()[i])
+    # a ghost
+    G = O.ghosts(0)
+    q = 5
+    u2 = O.kaczmarz_row(int(G["node"][q]), u0, f, g).ravel()
+    d = u2 - u0.ravel()
+    types = P.bc_types(G["B"])
+    w = (G["wN"] if types[q] else G["wD"])[q, : G["nk"][q]]
+    stn = G["stn"][q, : G["nk"][q]]
+    assert set(np.flatnonzero(d)) <= set(stn.tolist())
+    m = w != 0
+    ratio = d[stn[m]] / w[m]
+    assert np.allclose(ratio, ratio[0], rtol=1e-10, atol=0) and ratio[0] != 0.0
+    r2, _ = O.defect(u2.reshape(T.shape))
+    assert abs(r2.ravel()[G["node"][q]]) <= 1e-12 * abs(r0.ravel()[G["node"][q]])
+
+
+@pytest.mark.parametrize("P,n,nc", [(inputs.disk(), 33, 9), (inputs.flower(), 65, 17)])
+def test_kaczmarz_relaxation_fixes_the_discrete_solution(P, n, nc):
+    """The exact discrete solution (a direct sparse solve) is a fixed point of
+    the Kaczmarz comparison relaxation: every row it steps on is satisfied."""
+    O = _kaczmarz_oracle(P, n, nc)
+    f, g = problem_rhs(O, P, n)
+    us = direct_solve(O, f, g)
+    u1 = O.relax(us, f, g, 0, True)
+    assert np.max(np.abs(u1 - us)) <= 1e-11 * np.max(np.abs(us))
+
+
+def test_kaczmarz_comparison_falls_slower_than_the_paper_relaxation():
+    """Sec. 4 (Fig. convFactLambda): the V-cycle factor with the Kaczmarz
+    comparison falls with lambda but more slowly than with the paper's
+    relaxation; at lambda = 5 the cycle converges."""
+    P, n, nc = inputs.disk(), 65, 17
+    rho = {}
+    for sm in (0, 1):
+        for lam in (3, 5):
+            O = oracle_for(P, n, nc, smoother=sm, lam=lam, junction_solve=0, junction_sweeps=0)
+            _, norms, _ = O.solve(rtol=1e-10, max_cycles=100)
+            k = len(norms) - 1
+            rho[sm, lam] = (norms[-1] / norms[0]) ** (1.0 / k)
+    assert rho[1, 5] < rho[1, 3] < 1.0
+    assert rho[0, 3] < rho[1, 3] and rho[0, 5] < rho[1, 5]
