@@ -92,7 +92,7 @@ typedef struct {
                                 run as one launch (a cluster of CTAs with barriers between the
                                 steps; same results); 0: one launch per step */
     int smoother;            /* 0: the paper's relaxation (ghost relaxation + lambda band sweeps);
-                                1: its Kaczmarz comparison (Sec. 4, "Comparison with the
+                                1: its Kaczmarz comparison (Sec. 3.3, "Comparison with the
                                 Kaczmarz and the block relaxations"): a Gauss-Seidel sweep over
                                 the inside nodes, then lambda Kaczmarz sweeps over the ghost
                                 equations and the band's inside equations, rows ordered by the

@@ -260,7 +260,7 @@ class Oracle:
         return out
 
     def kaczmarz_row(self, i, u, f, g, l=0):
-        """One Kaczmarz step (Sec. 4 comparison) on the row of node i of level
+        """One Kaczmarz step (Sec. 3.3 comparison) on the row of node i of level
         l: an inside node of the band or a ghost."""
         u = np.array(u, dtype=np.float64, order="C", copy=True)
         f = np.ascontiguousarray(f, dtype=np.float64)

@@ -47,7 +47,7 @@ typedef struct {
     int junction_sweeps;   /* mu_J: local sweeps near Dirichlet/Neumann junctions (0: none) */
     double junction_radius;/* R_J: junction zone radius, in units of h of each level */
     int junction_solve;    /* 1: solve the zone's equations exactly instead of mu_J sweeps */
-    int smoother;          /* 0: the paper's relaxation; 1: its Kaczmarz comparison (Sec. 4,
+    int smoother;          /* 0: the paper's relaxation; 1: its Kaczmarz comparison (Sec. 3.3,
                               "Comparison with the Kaczmarz and the block relaxations") */
 } orc_params;
 
@@ -786,7 +786,7 @@ static void extra_sweeps(Oracle *O, Level *L) {
 }
 
 /* ----------------------------------------- Kaczmarz comparison smoother
- * Sec. 4, "Comparison with the Kaczmarz and the block relaxations": a
+ * Sec. 3.3, "Comparison with the Kaczmarz and the block relaxations": a
  * Gauss-Seidel sweep over the inside nodes, then lambda Kaczmarz sweeps over
  * the set J of the ghost equations and the inside equations within delta of
  * the boundary (the band).  A Kaczmarz step on row j of L u = b moves u along
@@ -1485,7 +1485,7 @@ void orc_relax(void *h, int l, double *u, const double *f, const double *g, int 
     memcpy(u, L->u, sizeof(double) * (size_t)L->nn);
 }
 
-/* One Kaczmarz step (Sec. 4) on the row of node i of level l, applied to u
+/* One Kaczmarz step (Sec. 3.3) on the row of node i of level l, applied to u
  * in place, with the level's right-hand side f, g (inside f at inside nodes). */
 void orc_kaczmarz_row(void *h, int l, int64_t i, double *u, const double *f, const double *g) {
     Level *L = &((Oracle *)h)->L[l];

@@ -1,4 +1,4 @@
-// Kaczmarz comparison smoother (Sec. 4, "Comparison with the Kaczmarz and
+// Kaczmarz comparison smoother (Sec. 3.3, "Comparison with the Kaczmarz and
 // the block relaxations"): after the Gauss-Seidel sweep over the inside
 // nodes, lambda sweeps of Kaczmarz steps u += (b_j - <l_j, u>) / ||l_j||^2 l_j
 // over the ghost equations and the band's inside equations.  The rows are

@@ -308,7 +308,7 @@ def test_fmg_needs_plain_fp64():
 
 
 def _ellipse_phi(dim, n):
-    """The paper's rotated ellipse (Sec. 4, not a distance function); in 3D an
+    """The paper's rotated ellipse (Sec. 3.3, not a distance function); in 3D an
     ellipsoid with the same profile."""
     X = inputs.coords(dim, n)
     c, s = math.cos(math.pi / 6), math.sin(math.pi / 6)
@@ -414,12 +414,12 @@ def test_fused_coarse_cycle_equals_per_level_launches(P, n, nc):
     assert np.array_equal(hists[0], hists[1])
 
 
-# ------------------------------------------------ Kaczmarz comparison (Sec. 4)
+# ------------------------------------------------ Kaczmarz comparison (Sec. 3.3)
 KACZ = dict(smoother=1, junction_solve=0, junction_sweeps=0)
 
 
 def test_kaczmarz_relaxation_matches_oracle():
-    """The Kaczmarz comparison smoother (Sec. 4), plain FP64: one relaxation
+    """The Kaczmarz comparison smoother (Sec. 3.3), plain FP64: one relaxation
     (Gauss-Seidel over the inside nodes, then lambda Kaczmarz sweeps over the
     ghosts and the band's inside nodes, colour by colour) on every level equals
     the oracle's element by element."""
@@ -443,7 +443,7 @@ def test_kaczmarz_solve_matches_oracle():
     """V-cycles with the Kaczmarz comparison smoother: the converged solution
     matches the oracle's within 1e-10 and the per-cycle factors match; the
     factor is reported beside the paper relaxation's (it falls more slowly
-    with lambda, Sec. 4)."""
+    with lambda, Sec. 3.3)."""
     import time
     P, n, nc = inputs.disk(), 65, 17
     S = solver_for(P, n, nc, rtol=1e-11, max_cycles=200, **KACZ)

@@ -507,13 +507,13 @@ def test_reinit_distance_function(dim, n):
     assert errs[0] / errs[1] > 1.7, errs
 
 
-# ------------------------------------------------ Kaczmarz comparison (Sec. 4)
+# ------------------------------------------------ Kaczmarz comparison (Sec. 3.3)
 def _kaczmarz_oracle(P, n, nc, lam=5, **kw):
     return oracle_for(P, n, nc, smoother=1, lam=lam, junction_solve=0, junction_sweeps=0, **kw)
 
 
 def test_kaczmarz_step_moves_along_its_row_and_satisfies_it():
-    """Sec. 4, Kaczmarz iteration: a step on row j changes u only on the row's
+    """Sec. 3.3, Kaczmarz iteration: a step on row j changes u only on the row's
     support, by a multiple of the row (inside node: 2d t at the node, -t at
     each neighbour; ghost: t w_k at its stencil nodes), and leaves that row's
     equation satisfied."""
@@ -563,7 +563,7 @@ def test_kaczmarz_relaxation_fixes_the_discrete_solution(P, n, nc):
 
 
 def test_kaczmarz_comparison_falls_slower_than_the_paper_relaxation():
-    """Sec. 4 (Fig. convFactLambda): the V-cycle factor with the Kaczmarz
+    """Sec. 3.3 (Fig. convFactLambda): the V-cycle factor with the Kaczmarz
     comparison falls with lambda but more slowly than with the paper's
     relaxation; at lambda = 5 the cycle converges."""
     P, n, nc = inputs.disk(), 65, 17
