@@ -273,7 +273,7 @@ gcmg_status gcmg_kernel_timing_ex(gcmg_ctx *ctx, int64_t *launches, double *tota
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t gcmg_launch_counter(void);
 
-/* ---- batched solves of many domains (BASELINE batching; not in the paper).
+/* ---- batched solves of many domains (not in the paper).
  * Independent 2D domains of uneven grid sizes are solved together: each step
  * of the cycle is one kernel launch over all domains and the whole solve --
  * FP32 V-cycles inside FP64 iterative refinement until every domain reaches

@@ -14,8 +14,8 @@ the squared error over Omega_h u Gamma_h plus LAP_WEIGHT times the squared
 h^2-scaled residual of that error on Omega_h; channel 1 is not trained.
 
 The solve keeps the network's guess only if its FP64 defect is smaller than
-that of u = 0 (guessed_start): the V-cycle remains the fallback and the
-judge of the guess, so the converged result never depends on the network.
+that of u = 0 (guessed_start): the V-cycle remains the fallback and decides
+whether the guess is used, so the converged result never depends on the network.
 
     python -m paper_1111_0983_gb300.learn --train 4096 --steps 6000 --out weights.npz
 """
@@ -145,7 +145,7 @@ def train(X, U, M, steps, batch=8, lr=1e-3, seed=0, log=print, params=None, lap_
 
 def guessed_start(S, net, xd, md, out, fd, g0, r):
     """Initial u from the network, kept only if its FP64 defect is below the
-    defect of u = 0: the V-cycle that follows is the judge of the guess.
+    defect of u = 0; the V-cycle that follows converges from either start.
     Returns (u, kept, relative defect of the guess)."""
     import torch
     net.forward(xd, out)
