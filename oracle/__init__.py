@@ -10,6 +10,7 @@ axis 0 (x) slowest; node j of an n-point axis sits at -1 + j h, h = 2/(n-1).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -45,10 +46,10 @@ class Params(C.Structure):
 _lib = None
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def _load(path):
+    """Loads a compiled oracle library and declares its functions."""
+    if True:
+        L = C.CDLL(path)
         vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
         L.orc_create.restype = vp
         L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, vp, C.POINTER(Params)]
@@ -85,8 +86,38 @@ def lib():
         L.orc_assemble.argtypes = [vp, C.c_int, vp, vp, vp, vp]
         L.orc_solve.restype = C.c_int
         L.orc_solve.argtypes = [vp, vp, dbl, C.c_int, vp, C.POINTER(C.c_int)]
-        _lib = L
+    return L
+
+
+def lib():
+    """The oracle library in use (compiled on first use)."""
+    global _lib
+    if _lib is None:
+        _lib = _load(build())
     return _lib
+
+
+def build_variant(source: str, out_dir: str) -> str:
+    """Compiles a modified copy of the oracle source (the planted-slip tests
+    plant one mistake in it) into out_dir; returns the library path."""
+    src = os.path.join(out_dir, "gcmg_oracle_variant.c")
+    out = os.path.join(out_dir, "liboracle_variant.so")
+    with open(src, "w") as fh:
+        fh.write(source)
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, src, "-lm"])
+    return out
+
+
+@contextlib.contextmanager
+def variant(path: str):
+    """Within the block, new Oracle objects use the library at `path`."""
+    global _lib
+    saved = lib()
+    _lib = _load(path)
+    try:
+        yield _lib
+    finally:
+        _lib = saved
 
 
 def _p(a):
@@ -127,7 +158,7 @@ class Oracle:
         assert all(s == self.n for s in phi.shape)
         self.params = Params(nu1, nu2, lam, gamma, mode, extra_once, delta_over_h, c_dirichlet,
                              c_neumann_factor, junction_sweeps, junction_radius, junction_solve, smoother)
-        L = lib()
+        L = self._L = lib()   # kept: a variant build may be swapped in later
         self._h = L.orc_create(self.dim, self.n, n_coarse, _p(phi), C.byref(self.params))
         if not self._h:
             raise MemoryError("oracle allocation failed")
@@ -141,41 +172,41 @@ class Oracle:
 
     def __del__(self):
         if getattr(self, "_h", None):
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     # ---- geometry
     def level_n(self, l):
-        return lib().orc_level_n(self._h, l)
+        return self._L.orc_level_n(self._h, l)
 
     def level_h(self, l):
-        return lib().orc_level_h(self._h, l)
+        return self._L.orc_level_h(self._h, l)
 
     def shape(self, l):
         return (self.level_n(l),) * self.dim
 
     def num_ghosts(self, l):
-        return lib().orc_num_ghosts(self._h, l)
+        return self._L.orc_num_ghosts(self._h, l)
 
     def types(self, l):
         out = np.empty(self.shape(l), np.uint8)
-        lib().orc_get_types(self._h, l, _p(out))
+        self._L.orc_get_types(self._h, l, _p(out))
         return out
 
     def band(self, l):
         out = np.empty(self.shape(l), np.uint8)
-        lib().orc_get_band(self._h, l, _p(out))
+        self._L.orc_get_band(self._h, l, _p(out))
         return out
 
     def junction_zone(self, l):
         out = np.empty(self.shape(l), np.uint8)
-        lib().orc_get_jzone(self._h, l, _p(out))
+        self._L.orc_get_jzone(self._h, l, _p(out))
         return out
 
     def junction_solve_set(self, l):
         """Mask of the unknowns whose equations the exact junction solve solves."""
         out = np.empty(self.shape(l), np.uint8)
-        lib().orc_get_jsolve(self._h, l, _p(out))
+        self._L.orc_get_jsolve(self._h, l, _p(out))
         return out
 
     def ghosts(self, l):
@@ -184,79 +215,79 @@ class Oracle:
                    t=np.empty((ng, d)), s=np.empty((ng, d), np.int8), case=np.empty(ng, np.uint8),
                    nk=np.empty(ng, np.int32), stn=np.empty((ng, MAXK), np.int64),
                    wD=np.empty((ng, MAXK)), wN=np.empty((ng, MAXK)))
-        lib().orc_get_ghosts(self._h, l, *[_p(rec[k]) for k in
+        self._L.orc_get_ghosts(self._h, l, *[_p(rec[k]) for k in
                                            ("node", "B", "nu", "t", "s", "case", "nk", "stn", "wD", "wN")])
         return rec
 
     def extension(self, l):
-        ne = lib().orc_num_ext(self._h, l)
+        ne = self._L.orc_num_ext(self._h, l)
         out = dict(node=np.empty(ne, np.int64), nsrc=np.empty(ne, np.int32),
                    src=np.empty((ne, 6), np.int64), w=np.empty((ne, 6)))
         if ne:
-            lib().orc_get_ext(self._h, l, _p(out["node"]), _p(out["nsrc"]), _p(out["src"]), _p(out["w"]))
+            self._L.orc_get_ext(self._h, l, _p(out["node"]), _p(out["nsrc"]), _p(out["src"]), _p(out["w"]))
         return out
 
     def coarse_unknowns(self):
-        return lib().orc_num_coarse_unknowns(self._h)
+        return self._L.orc_num_coarse_unknowns(self._h)
 
     # ---- data
     def set_bc(self, l, bc):
         bc = np.ascontiguousarray(bc, dtype=np.uint8)
         assert bc.shape == (self.num_ghosts(l),)
-        lib().orc_set_bc(self._h, l, _p(bc))
-        st = lib().orc_status(self._h)
+        self._L.orc_set_bc(self._h, l, _p(bc))
+        st = self._L.orc_status(self._h)
         if st != 0:
-            raise OracleError(f"oracle status {st}: {lib().orc_error(self._h).decode()}")
+            raise OracleError(f"oracle status {st}: {self._L.orc_error(self._h).decode()}")
 
     def set_rhs(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
         assert f.shape == self.shape(0) and g.shape == (self.num_ghosts(0),)
-        lib().orc_set_rhs(self._h, _p(f), _p(g))
+        self._L.orc_set_rhs(self._h, _p(f), _p(g))
 
     def set_rhs_level(self, l, f, g):
         """f and g of level l (the problem's data sampled there), for fmg."""
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
         assert f.shape == self.shape(l) and g.shape == (self.num_ghosts(l),)
-        lib().orc_set_rhs_level(self._h, l, _p(f), _p(g))
+        self._L.orc_set_rhs_level(self._h, l, _p(f), _p(g))
 
     def fmg(self, nu=1):
         """Full multigrid: exact coarsest solve, then per finer level the
         interpolated coarser solution improved by nu cycles.  Needs every
         level's f and g (set_rhs_level; level 0 may come from set_rhs)."""
         u = np.zeros(self.shape(0))
-        lib().orc_fmg(self._h, int(nu), _p(u))
+        self._L.orc_fmg(self._h, int(nu), _p(u))
         return u
 
     # ---- operators
     def defect(self, u, l=0):
         u = np.ascontiguousarray(u, dtype=np.float64)
         r = np.empty_like(u)
-        nrm = lib().orc_defect(self._h, l, _p(u), _p(r))
+        nrm = self._L.orc_defect(self._h, l, _p(u), _p(r))
         return r, nrm
 
     def extend(self, r, l=0):
         r = np.array(r, dtype=np.float64, order="C", copy=True)
-        lib().orc_extend(self._h, l, _p(r))
+        self._L.orc_extend(self._h, l, _p(r))
         return r
 
     def restrict(self, r, l=0):
         r = np.ascontiguousarray(r, dtype=np.float64)
         fc = np.zeros(self.shape(l + 1))
         gc = np.zeros(max(self.num_ghosts(l + 1), 1))
-        lib().orc_restrict(self._h, l, _p(r), _p(fc), _p(gc))
+        self._L.orc_restrict(self._h, l, _p(r), _p(fc), _p(gc))
         return fc, gc[: self.num_ghosts(l + 1)]
 
     def restrict_weights(self, l, X, interior_set):
         wt = np.zeros(3 ** self.dim)
-        ok = lib().orc_restrict_weights(self._h, l, int(X), int(interior_set), _p(wt))
+        ok = self._L.orc_restrict_weights(self._h, l, int(X), int(interior_set), _p(wt))
         return (wt.reshape((3,) * self.dim) if ok else None)
 
     def prolong(self, e_coarse, l=0):
         e = np.ascontiguousarray(e_coarse, dtype=np.float64)
         out = np.empty(self.shape(l))
-        lib().orc_prolong(self._h, l, _p(e), _p(out))
+        self._L.orc_prolong(self._h, l, _p(e), _p(out))
         return out
 
     def kaczmarz_row(self, i, u, f, g, l=0):
@@ -265,20 +296,20 @@ class Oracle:
         u = np.array(u, dtype=np.float64, order="C", copy=True)
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
-        lib().orc_kaczmarz_row(self._h, l, C.c_int64(int(i)), _p(u), _p(f), _p(g))
+        self._L.orc_kaczmarz_row(self._h, l, C.c_int64(int(i)), _p(u), _p(f), _p(g))
         return u
 
     def relax(self, u, f, g, l=0, with_extra=True):
         u = np.array(u, dtype=np.float64, order="C", copy=True)
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
-        lib().orc_relax(self._h, l, _p(u), _p(f), _p(g), int(with_extra))
+        self._L.orc_relax(self._h, l, _p(u), _p(f), _p(g), int(with_extra))
         return u
 
     def assemble(self, l=0):
         """COO triplets of the level-l system over unknowns in increasing node order,
         and the node -> unknown map (-1 off Omega_h u Gamma_h)."""
-        L = lib()
+        L = self._L
         nnz = L.orc_assemble(self._h, l, None, None, None, None)
         rows = np.empty(nnz, np.int64)
         cols = np.empty(nnz, np.int64)
@@ -293,5 +324,5 @@ class Oracle:
         u = np.zeros(self.shape(0)) if u0 is None else np.array(u0, dtype=np.float64, order="C", copy=True)
         norms = np.zeros(max_cycles + 1)
         st = C.c_int(0)
-        m = lib().orc_solve(self._h, _p(u), rtol, max_cycles, _p(norms), C.byref(st))
+        m = self._L.orc_solve(self._h, _p(u), rtol, max_cycles, _p(norms), C.byref(st))
         return u, norms[: m + 1], st.value == 0
