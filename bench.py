@@ -4,11 +4,14 @@
 Metric: unknowns (|Omega_h| + |Gamma_h|) solved per second from u = 0 to
 relative residual 1e-10 (||r||_inf / ||r0||_inf, r0 = (f, g)).  One step is
 one whole solve of the workload with f and g already resident in HBM; an L2
-flush (a 256 MB write) separates steps.  `e2e` repeats the measurement
-through the host-buffer entry point (host -> device copies of f and g and the
-device -> host copy of u inside the timed region).
+flush (a 256 MB write) separates steps.  The default workload is the largest
+single-GPU configuration, the 3D torus on 513^3 nodes (FP32 cycles inside
+FP64 refinement), with the plain FP64 GPU solve of the same workload beside
+it.  `e2e` repeats the measurement through the host-buffer entry point (host
+-> device copies of f and g and the device -> host copy of u inside the
+timed region).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config flower4097]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config torus513]
                     [--precision mixed|fp64] [--impl gcmg|reference]
 
 Under torchrun every rank solves its own replica (the single-grid solve does
@@ -27,6 +30,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -47,6 +52,12 @@ WORKLOADS = {
     "stars256": (None, None, 33, "256 seeded 2D stars, n in {129,257,513,1025}, mixed D/N, one batched solve"),
 }
 L2_FLUSH_BYTES = 256 << 20
+# plain FP64 stalls above 1e-10 on the finest grids: the rounding of u in the
+# FP64 smoother, times the 2d/h^2 of an interior row, keeps the defect of its
+# iterates near these fractions of ||(f, g)|| (FP32 cycles inside FP64
+# refinement only add small corrections to u and go lower); the plain FP64
+# comparison is timed to these targets there
+FP64_FLOOR_RTOL = {"torus513": 5e-10, "flower4097": 1e-9}
 
 
 def parse():
@@ -54,9 +65,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="flower1025", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="torus513", choices=sorted(WORKLOADS))
     ap.add_argument("--rtol", type=float, default=1e-10)
-    ap.add_argument("--also", default="flower4097:1e-9,torus257:1e-10",
+    ap.add_argument("--also", default="flower1025:1e-10,flower4097:1e-9,torus257:1e-10",
                     help="comma-separated secondary workload:rtol pairs measured after the main one ('' to skip)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--gamma", type=int, default=1)
@@ -66,7 +77,16 @@ def parse():
     ap.add_argument("--batch-profile", action="store_true",
                     help="after the batch measurement, one more batch solve as plain launches between "
                          "profiler start and stop (for ncu --profile-from-start off)")
-    ap.add_argument("--cpu-sample-cycles", type=int, default=2)
+    ap.add_argument("--fp64", type=int, default=1,
+                    help="time the plain FP64 solve of the workload beside the mixed form (1) or not (0)")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="after the measurement, one more solve of the workload as plain launches between "
+                         "profiler start and stop (for ncu --profile-from-start off)")
+    ap.add_argument("--cpu-sample-cycles", type=int, default=1)
+    ap.add_argument("--cpu-single", type=int, default=1,
+                    help="also time the oracle's sample on one host core (1) or not (0)")
+    ap.add_argument("--paper", default="flower1025",
+                    help="workload of the paper's-method comparison (junction relaxation off, V and W; '' to skip)")
     ap.add_argument("--learned", type=int, default=8,
                     help="held-out 513^2 star problems for the learned-guess comparison (0 to skip)")
     ap.add_argument("--fmg", default="flower1025",
@@ -222,8 +242,24 @@ def build_problem(name):
     return fac(), n, nc, desc
 
 
-def oracle_cycle_sample(P, n, nc, gamma, cycles):
-    """Seconds per cycle of the FP64 CPU oracle on the full workload."""
+def host_cpu():
+    """(nproc, CPU model) of this host."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+    return os.cpu_count() or 1, model or platform.machine()
+
+
+def oracle_problem(P, n, nc, gamma):
+    """The FP64 CPU oracle on the full workload, its data set (not timed)."""
     import oracle
     O = oracle.Oracle(P.phi_grid(n), nc, gamma=gamma)
     for l in range(O.nlev):
@@ -231,15 +267,21 @@ def oracle_cycle_sample(P, n, nc, gamma, cycles):
     G = O.ghosts(0)
     types = P.bc_types(G["B"])
     O.set_rhs(P.f_grid(n), P.g_values(G["B"], G["nu"], types))
+    return O, int((O.types(0) > 0).sum())
+
+
+def oracle_cycle_seconds(O, threads, cycles):
+    """Seconds per oracle cycle (from u = 0, its defects included) with
+    `threads` threads; returns (seconds, threads in effect)."""
+    import oracle
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
-    _, norms, _ = O.solve(rtol=0.0, max_cycles=cycles)
-    dt = time.perf_counter() - t0
-    nunk = int((O.types(0) > 0).sum())
-    return dt / max(len(norms) - 1, 1), nunk, norms
+    O.solve(rtol=0.0, max_cycles=cycles)
+    return (time.perf_counter() - t0) / cycles, used
 
 
-def cycles_reference(name, precision):
-    """Cycles to 1e-10 of the oracle on this workload (written by
+def cycles_reference(name):
+    """Cycles to the workload's target of the oracle (written by
     tests/golden/make_bench_cycles.py, which calls only the oracle)."""
     try:
         with open(os.path.join(ROOT, "tests", "golden", "bench_cycles.json")) as fh:
@@ -248,18 +290,42 @@ def cycles_reference(name, precision):
         return None
 
 
+def cpu_baseline(P, n, nc, gamma, name, cycles_sample, single, fallback_cycles):
+    """The oracle as it stands on this host: one cycle of the full workload
+    with every host thread (its OpenMP loops) and, if `single`, with one,
+    scaled by the oracle's own cycle count to 1e-10."""
+    nproc, model = host_cpu()
+    O, nunk = oracle_problem(P, n, nc, gamma)
+    cyc = cycles_reference(name) or fallback_cycles
+    s_all, used = oracle_cycle_seconds(O, nproc, cycles_sample)
+    out = {"value": nunk / (s_all * cyc), "unit": "unknowns/s", "cores": used, "kind": "oracle",
+           "sample": f"{cycles_sample} oracle cycle(s) of the full {name} problem ({nunk} unknowns) on {used} "
+                     f"threads, {s_all:.2f} s per cycle, scaled by the oracle's {cyc} cycles to the target; "
+                     f"oracle setup not timed",
+           "nproc": nproc, "cpu": model, "s_per_cycle": s_all, "cycles_to_target": cyc}
+    if single:
+        s_one, _ = oracle_cycle_seconds(O, 1, cycles_sample)
+        out["single_core"] = {"value": nunk / (s_one * cyc), "unit": "unknowns/s", "cores": 1,
+                              "s_per_cycle": s_one}
+    import oracle
+    oracle.set_threads(1)
+    return out
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     rank, world, _ = dist()
     if rank != 0:
         return
     P, n, nc, desc = build_problem(args.config)
-    cyc = cycles_reference(args.config, args.precision)
-    per_cycle = []
-    nunk = None
+    cyc = cycles_reference(args.config)
+    nproc, model = host_cpu()
     t_total0 = time.perf_counter()
+    O, nunk = oracle_problem(P, n, nc, args.gamma)
+    per_cycle = []
+    used = 1
     for i in range(args.warmup + args.steps):
-        sec, nunk, _ = oracle_cycle_sample(P, n, nc, args.gamma, 1)
+        sec, used = oracle_cycle_seconds(O, nproc, 1)
         if i >= args.warmup:
             per_cycle.append(sec)
     wall = time.perf_counter() - t_total0
@@ -268,10 +334,13 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.config, "description": desc, "unknowns": nunk, "cycle": "V" if args.gamma == 1 else "W"},
-            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one oracle cycle per step on the full {args.config} problem; "
-                                       f"unknowns/s = unknowns / (s per cycle x {cyc} cycles to 1e-10 of the oracle)"},
+            "config": {"workload": args.config, "description": desc, "unknowns": nunk,
+                       "cycle": "V(2,1)" if args.gamma == 1 else "W(2,1)"},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": used, "kind": "oracle",
+                             "nproc": nproc, "cpu": model,
+                             "sample": f"one oracle cycle per step on the full {args.config} problem on {used} "
+                                       f"threads; unknowns/s = unknowns / (s per cycle x the oracle's {cyc} "
+                                       f"cycles to 1e-10); oracle setup not timed"},
             "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
@@ -435,23 +504,23 @@ def secondary(name, rtol, precision, args, stream, flush):
                    "cycles": cyc}
             # the fine-level fused sweep of this form, timed live with CUDA events
             # around each launch in one instrumented solve
-            if P.dim == 2:
-                n_in = int(((S.node_types(0) & 3) == 1).sum())
-                flush.zero_()
-                u.zero_()
-                S.set_kernel_timing(S.KERNEL_SMOOTH)
-                S.solve(u)
-                kl, kms, kbytes = S.kernel_timing_ex()
-                S.set_kernel_timing(-1)
-                if kl:
-                    alg = kbytes / kl if kbytes > 0 else (24 if prec == 0 else 12) * n_in
-                    gbs = alg / (kms / kl / 1e3) / 1e9
-                    peak = measured_peaks()[0].get("hbm_gbs")
-                    rec["fine_sweep"] = {"kernel": "k_rb_fused2d" if prec == 0 or kbytes <= 0 else
-                                         "k_relax2d (interior sweep + ghost and band sweeps)",
-                                         "alg_bytes_per_launch": alg,
-                                         "avg_launch_ms": kms / kl, "achieved_GBs": gbs,
-                                         "frac_of_measured_hbm": gbs / peak if peak else None}
+            n_in = int(((S.node_types(0) & 3) == 1).sum())
+            flush.zero_()
+            u.zero_()
+            S.set_kernel_timing(S.KERNEL_SMOOTH)
+            S.solve(u)
+            kl, kms, kbytes = S.kernel_timing_ex()
+            S.set_kernel_timing(-1)
+            if kl:
+                alg = kbytes / kl if kbytes > 0 else (24 if prec == 0 else 12) * n_in
+                gbs = alg / (kms / kl / 1e3) / 1e9
+                peak = measured_peaks()[0].get("hbm_gbs")
+                kernel = ("k_rb_zmarch (red + black 7-point sweep, one pass)" if P.dim == 3 else
+                          "k_rb_fused2d" if prec == 0 or kbytes <= 0 else
+                          "k_relax2d (interior sweep + ghost and band sweeps)")
+                rec["fine_sweep"] = {"kernel": kernel, "alg_bytes_per_launch": alg,
+                                     "avg_launch_ms": kms / kl, "achieved_GBs": gbs,
+                                     "frac_of_measured_hbm": gbs / peak if peak else None}
             out["f64" if prec == 0 else "mixed"] = rec
         out["unknowns"] = S.num_unknowns(0)
         out["setup_s_" + ("f64" if prec == 0 else "mixed")] = time.perf_counter() - t0
@@ -459,8 +528,85 @@ def secondary(name, rtol, precision, args, stream, flush):
     return out
 
 
+def make_solver(P, n, nc, stream, precision, gamma, rtol, **kw):
+    import torch
+    from paper_1111_0983_gb300 import gcmg
+    S = gcmg.Solver(P.phi_grid(n), nc, stream=stream, precision=precision, gamma=gamma, rtol=rtol,
+                    max_cycles=256, **kw)
+    for l in range(S.nlev):
+        S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+    G = S.ghosts(0)
+    f_h = P.f_grid(n)
+    g_h = P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))
+    S.set_rhs(torch.from_numpy(f_h).cuda(), torch.from_numpy(g_h).cuda())
+    return S, f_h, g_h
+
+
+def timed_solves(S, u, steps, stream, flush):
+    """Device ms of `steps` solves from u = 0 (CUDA events on the stream, L2
+    flushed before each) and their cycle counts."""
+    import torch
+    ms, cyc, st = 0.0, [], None
+    for _ in range(steps):
+        flush.zero_()
+        u.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = S.solve(u)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        cyc.append(st["cycles"])
+        if not st["converged"]:
+            raise RuntimeError(f"solve did not converge: {st}")
+    return ms / steps, cyc, st
+
+
+def paper_method_entry(name, stream, flush, steps):
+    """The paper's method on a workload (plain FP64, the junction relaxation
+    off, V(2,1) and W(2,1) cycles, lambda = 5): device time, cycles and the
+    convergence factor beside the oracle's (same algorithm) on the same
+    problem, next to the default cycle with the junction solve."""
+    import torch
+    P, n, nc, desc = build_problem(name)
+    out = {"workload": name, "description": desc, "precision": "f64", "forms": []}
+    for label, gamma, kw in (("paper V(2,1)", 1, dict(junction_solve=0, junction_sweeps=0)),
+                             ("paper W(2,1)", 2, dict(junction_solve=0, junction_sweeps=0)),
+                             ("V(2,1) + junction solve", 1, {})):
+        S, _, _ = make_solver(P, n, nc, stream, 0, gamma, 1e-10, **kw)
+        u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+        S.solve(u)
+        try:
+            ms, cyc, st = timed_solves(S, u, max(1, min(steps, 2)), stream, flush)
+            ok = True
+        except RuntimeError:
+            u.zero_()
+            st, ms, cyc, ok = S.solve(u), None, [S.solve(u)["cycles"]], False
+        rel = st["rel"]
+        rho = float(np.median(rel[2:] / rel[1:-1])) if len(rel) > 3 else None
+        rec = {"form": label, "converged": ok, "cycles": cyc[-1], "ms_per_solve": ms,
+               "unknowns_per_s": S.num_unknowns(0) / (ms / 1e3) if ms else None, "rho_median": rho,
+               "diverged": bool(st.get("diverged", False))}
+        out["unknowns"] = S.num_unknowns(0)
+        S.close()
+        # the oracle's factor on the same problem and cycle (paper-mode forms only)
+        if kw:
+            import oracle
+            O = oracle.Oracle(P.phi_grid(n), nc, gamma=gamma, junction_solve=0, junction_sweeps=0)
+            for l in range(O.nlev):
+                O.set_bc(l, P.bc_types(O.ghosts(l)["B"]))
+            G = O.ghosts(0)
+            O.set_rhs(P.f_grid(n), P.g_values(G["B"], G["nu"], P.bc_types(G["B"])))
+            oracle.set_threads(os.cpu_count() or 1)
+            _, norms, _ = O.solve(rtol=1e-10, max_cycles=min(len(rel) - 1, 12))
+            oracle.set_threads(1)
+            r = norms[2:] / norms[1:-1]
+            rec["oracle_rho_median"] = float(np.median(r)) if len(r) else None
+        out["forms"].append(rec)
+    return out
+
+
 def run_gcmg(args):
-    import numpy as np
     import torch
     import torch.distributed as tdist
 
@@ -474,17 +620,9 @@ def run_gcmg(args):
 
     P, n, nc, desc = build_problem(args.config)
     precision = 1 if args.precision == "mixed" else 0
-    phi = P.phi_grid(n)
-    S = gcmg.Solver(phi, nc, stream=stream, precision=precision, gamma=args.gamma, rtol=args.rtol, max_cycles=256)
-    for l in range(S.nlev):
-        S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
-    G = S.ghosts(0)
-    types = P.bc_types(G["B"])
-    f_h = P.f_grid(n)
-    g_h = P.g_values(G["B"], G["nu"], types)
-    f = torch.from_numpy(f_h).cuda()
-    g = torch.from_numpy(g_h).cuda()
-    S.set_rhs(f, g)
+    t_setup = time.perf_counter()
+    S, f_h, g_h = make_solver(P, n, nc, stream, precision, args.gamma, args.rtol)
+    setup_s = time.perf_counter() - t_setup
     u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
     nunk = S.num_unknowns(0)
     n_in = int(((S.node_types(0) & 3) == 1).sum())
@@ -498,7 +636,7 @@ def run_gcmg(args):
 
     for _ in range(args.warmup):
         u.zero_()
-        st = S.solve(u)
+        S.solve(u)
     barrier()
     clocks = Clocks(local)
     clocks.start()
@@ -506,6 +644,7 @@ def run_gcmg(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     cycles = []
     t_wall0 = time.perf_counter()
+    st = None
     for k in range(args.steps):
         flush.zero_()
         u.zero_()
@@ -519,9 +658,10 @@ def run_gcmg(args):
     wall = time.perf_counter() - t_wall0
     launches = gcmg.launch_counter() - launches0
     clk = clocks.stop()
+    rel_hist = st["rel"]
     # further passes of the same solves with CUDA events around every
-    # fine-level launch of the smoother, then around every boundary-block
-    # launch (events cannot live inside the graph's loop body)
+    # fine-level launch of the interior sweep (and, in 2D, of every
+    # boundary-block launch): events cannot live inside the graph's loop body
     S.set_kernel_timing(S.KERNEL_SMOOTH)
     for k in range(args.steps):
         flush.zero_()
@@ -536,6 +676,17 @@ def run_gcmg(args):
             u.zero_()
             S.solve(u)
         b_launches, b_ms, b_bytes = S.kernel_timing_ex()
+    if args.profile_solve:
+        # plain launches (kernel timing keeps the graph off) inside the profiler range
+        S.set_kernel_timing(S.KERNEL_DEFECT)
+        u.zero_()
+        S.solve(u)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        u.zero_()
+        S.solve(u)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     S.set_kernel_timing(-1)
     ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
@@ -555,7 +706,7 @@ def run_gcmg(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, st_h = S.solve_host(f_pin, g_pin, u_pin)
+        S.solve_host(f_pin, g_pin, u_pin)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_t)
     if world > 1:
@@ -565,28 +716,28 @@ def run_gcmg(args):
     e2e_value = nunk * args.steps * world / e2e_s
 
     peaks, peak_kind = measured_peaks()
-    # 2D: one fused red+black sweep per launch reads u and f and writes u once per
-    # inside node; 3D: one colour half-sweep per launch (half of that)
-    bytes_per_node = (24 if precision == 0 else 12) if P.dim == 2 else (12 if precision == 0 else 6)
-    # the FP32 2D relaxation runs as one launch (interior sweep + boundary
-    # blocks): the library gives its algorithmic bytes
-    merged = k_bytes > 0
-    alg_bytes = k_bytes / k_launches if merged else bytes_per_node * n_in
+    peak = peaks.get("hbm_gbs")
+    # the interior sweep: both colours in one launch (2D strips / tiles, 3D
+    # z-march) reading u and f and writing u once per inside node, plus in
+    # the merged FP32 2D relaxation the boundary blocks' values (the library
+    # gives those bytes)
+    elt = 4 if precision else 8
+    alg_bytes = k_bytes / k_launches if k_launches and k_bytes > 0 else 3 * elt * n_in
     avg_ms = k_ms / max(k_launches, 1)
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if k_launches else None
-    peak = peaks.get("hbm_gbs")
-    kern = ("relax2d" if merged else "fused2d") if P.dim == 2 else "interior"
+    merged = P.dim == 2 and precision == 1 and b_launches > 0
+    kern = ("relax2d" if merged else "fused2d") if P.dim == 2 else "zmarch"
     kname = f"rb_{kern}_{'f64' if precision == 0 else 'f32'}_{args.config}"
     kdesc = {"relax2d": "k_relax2d (fine level: interior sweep + ghost and band sweeps in one launch)",
              "fused2d": "k_rb_fused2d (fine level, red + black sweep)",
-             "interior": "k_rb_interior (fine level, one colour)"}[kern]
+             "zmarch": "k_rb_zmarch (fine level: red + black 7-point sweep in one pass, z-marching tiles)"}[kern]
     sweep = {"bound": "hbm", "kernel": kdesc, "achieved": achieved,
              "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
              "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),
-             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms, "launches_timed": k_launches}
+             "alg_bytes_per_launch": alg_bytes, "alg_bytes_note": f"{3 * elt} B x {n_in} inside nodes"
+             if P.dim == 3 else None, "avg_launch_ms": avg_ms, "launches_timed": k_launches}
+    roofline = sweep
     if b_launches:
-        # 2D: the boundary blocks lead the launch list (profiles/launches_*): the
-        # dominant kernel; bytes per launch averaged over its launches on all levels
         bname = f"{'relax2d' if merged else 'local_bz'}_{'f64' if precision == 0 else 'f32'}_{args.config}"
         b_ach = (b_bytes / b_launches) / (b_ms / b_launches / 1e3) / 1e9 if b_ms > 0 else None
         bdesc = ("k_relax2d (one FP32 relaxation: interior strips and boundary blocks in one launch, every level)"
@@ -597,8 +748,6 @@ def run_gcmg(args):
                     "frac": (b_ach / peak) if b_ach and peak else None, "traffic": traffic_for(bname),
                     "alg_bytes_per_launch": b_bytes / b_launches, "avg_launch_ms": b_ms / b_launches,
                     "launches_timed": b_launches}
-    else:
-        roofline = sweep
 
     line = None
     if rank == 0:
@@ -608,35 +757,61 @@ def run_gcmg(args):
                 "dtype": "f32 cycles + f64 refinement" if precision else "f64", "data": "synthetic",
                 "config": {"workload": args.config, "description": desc, "unknowns": nunk, "inside": n_in,
                            "ghosts": S.num_ghosts(0), "levels": S.nlev, "n_coarse": nc,
-                           "cycle": "V(2,1)" if args.gamma == 1 else "W(2,1)", "lambda": 5,
+                           "cycle": "V(2,1)" if args.gamma == 1 else "W(2,1)", "lambda": 5, "rtol": args.rtol,
                            "cycles_per_solve": cycles, "l2": "flushed between steps (256 MB write)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}", "setup_s": setup_s},
+                "rho": [float(x) for x in (rel_hist[1:] / rel_hist[:-1])],
                 "roofline": roofline, "sweep_roofline": sweep, "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": int(f_h.nbytes + g_h.nbytes),
                         "d2h_bytes_per_step": int(u_pin.nbytes)},
                 "wall_s": wall}
+        S.close()
+        del S
+        if precision == 1 and world == 1 and args.fp64:
+            # the plain FP64 GPU solve of the same workload (the metric's comparison)
+            t0 = time.perf_counter()
+            rt64 = max(args.rtol, FP64_FLOOR_RTOL.get(args.config, args.rtol))
+            S64, _, _ = make_solver(P, n, nc, stream, 0, args.gamma, rt64)
+            setup64 = time.perf_counter() - t0
+            u.zero_()
+            S64.solve(u)
+            ms64, cyc64, st64 = timed_solves(S64, u, max(1, min(args.steps, 3)), stream, flush)
+            line["fp64"] = {"value": nunk / (ms64 / 1e3), "unit": "unknowns/s", "ms_per_solve": ms64,
+                            "cycles": cyc64, "rtol": rt64, "rel_residual": st64["rel_residual"],
+                            "setup_s": setup64}
+            if rt64 > args.rtol:
+                line["fp64"]["note"] = (f"plain FP64 cannot reach {args.rtol:g} on this grid (the rounding of u in "
+                                        f"its smoother keeps the defect near {rt64:g} of ||(f, g)||); timed to "
+                                        f"{rt64:g}, so the speed-up understates the mixed form's")
+            line["speedup_vs_fp64"] = (ms64 * args.steps) / ms
+            S64.close()
+            del S64
         if args.also and world == 1:
             line["also"] = []
             for item in args.also.split(","):
                 name, rt = item.split(":")
+                if name == args.config:
+                    continue
                 line["also"].append(secondary(name, float(rt), precision, args, stream, flush))
+        if args.paper and world == 1:
+            line["paper_method"] = paper_method_entry(args.paper, stream, flush, args.steps)
         if args.batch and world == 1:
             t0 = time.perf_counter()
             B, sizes, bun, fused_bytes = build_batch(args.batch, stream)
-            setup_s = time.perf_counter() - t0
+            bsetup_s = time.perf_counter() - t0
             profile_batch = args.batch_profile
             bms, bcyc, best, tune_ms, bad, bst = run_batch_measure(B, max(1, min(args.steps, 3)), 2, stream, flush)
             line["batch"] = {"workload": f"stars{args.batch}", "domains": args.batch,
-                             "grid_sizes": {str(n): sizes.count(n) for n in sorted(set(sizes))},
+                             "grid_sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
                              "unknowns": bun, "value": bun / (bms / 1e3), "unit": "unknowns/s",
-                             "ms_per_solve": bms, "refinement_steps": bcyc, "setup_s": setup_s,
-                             "cycles_max": max(st["cycles"] for st in bst),
-                             "cycles_median": statistics.median(st["cycles"] for st in bst),
+                             "ms_per_solve": bms, "refinement_steps": bcyc, "setup_s": bsetup_s,
+                             "cycles_max": max(x["cycles"] for x in bst),
+                             "cycles_median": statistics.median(x["cycles"] for x in bst),
                              "tile_variant": ["strips of 8 rows", "strips of 16 rows", "strips of 32 rows"][best],
                              "autotune_ms_fused_sweeps_per_cycle": tune_ms,
                              "fused_sweep_GBs": fused_bytes / (min(tune_ms) / 1e3) / 1e9,
                              "converged": len(bad) == 0, "not_converged": bad,
-                             "worst_rel": max(st["rel_residual"] for st in bst)}
+                             "worst_rel": max(x["rel_residual"] for x in bst)}
             if profile_batch:
                 B.set_graph(False)
                 B.solve()   # warm the plain-launch form
@@ -657,11 +832,8 @@ def run_gcmg(args):
             cmp["wall_s"] = time.perf_counter() - t0
             line["learned"] = cmp
         if world == 1 and not args.no_cpu_baseline:
-            sec, nu_o, _ = oracle_cycle_sample(P, n, nc, args.gamma, args.cpu_sample_cycles)
-            cyc = cycles_reference(args.config, args.precision) or statistics.median(cycles)
-            line["cpu_baseline"] = {"value": nu_o / (sec * cyc), "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"{args.cpu_sample_cycles} oracle cycles on the full problem, "
-                                              f"{sec:.2f} s/cycle, scaled by {cyc} cycles to 1e-10"}
+            line["cpu_baseline"] = cpu_baseline(P, n, nc, args.gamma, args.config, args.cpu_sample_cycles,
+                                                bool(args.cpu_single), statistics.median(cycles))
         print(json.dumps(line), flush=True)
     if world > 1:
         tdist.barrier()

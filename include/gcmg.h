@@ -8,8 +8,9 @@
  *
  *     -Lap u = f  in Omega = {phi < 0},   u = g_D on Gamma_D,   du/dn = g_N on Gamma_N,
  *
- * discretised on the vertex grid of D = [-1,1]^d (d = 2 or 3) with n = N+1
- * nodes per axis, h = 2/N, node j at -1 + j h (Sec. 2.3).  The unknowns are
+ * discretised on a vertex grid with n = N+1 nodes per axis, spacing h and
+ * node j at origin + j h (Sec. 2.3); by default the box D = [-1,1]^d
+ * (d = 2 or 3), h = 2/N, origin -1.  The unknowns are
  * the inside nodes Omega_h (phi < 0) and the ghost nodes Gamma_h (outside
  * nodes with an axis neighbour inside).  Each ghost G carries the boundary
  * condition at its closest boundary point B (Eq. clpt), interpolated on an
@@ -53,7 +54,8 @@ typedef enum {
     GCMG_E_GEOM = 4,     /* geometry unusable: an unknown, ghost stencil or extension
                             node on the box boundary, no usable ghost stencil, a
                             degenerate normal, or a singular coarsest system */
-    GCMG_E_NOCONV = 5,   /* max_cycles reached, or a NaN/Inf defect */
+    GCMG_E_NOCONV = 5,   /* max_cycles reached, a NaN/Inf defect, or a defect that grew
+                            in diverge_cycles consecutive cycles (rho > 1) */
     GCMG_E_STATE = 6,    /* call out of order (e.g. solve before set_rhs) */
     GCMG_E_SIZE = 7,     /* problem larger than a fixed-capacity entry point accepts */
     GCMG_E_TIMEOUT = 8   /* a bounded device-side wait ran out (the context stays usable) */
@@ -63,7 +65,7 @@ typedef enum {
  * paper's values: nu1 = 2, nu2 = 1, lambda = 5, delta = 3h, mu_D dt = 0.9,
  * mu_N dt = 0.9 * 2h / (3 sqrt(d)), V-cycle; plus the junction relaxation
  * that this library adds for mixed boundaries (2D: an exact solve of the
- * zone within R_J = 12 h; 3D: mu_J = 10 sweeps within R_J = 2 h; the paper
+ * zone within R_J = 20 h; 3D: mu_J = 10 sweeps within R_J = 2 h; the paper
  * has no counterpart -- without it the V-cycle factor of a mixed problem
  * grows as h shrinks). */
 typedef struct {
@@ -98,7 +100,22 @@ typedef struct {
                                 equations and the band's inside equations, rows ordered by the
                                 colour sum_a (j_a mod 5) 5^a of their node.  2D, plain FP64
                                 (precision 0), junction relaxation off; else GCMG_E_ARG */
+    double h;                /* fine grid spacing (Sec. 2.3); 0: 2 / (n - 1), the box [-1,1]^d */
+    double origin[3];        /* coordinates of node 0 on each axis (the first dim used); the
+                                defaults are -1; B of gcmg_ghost_geometry is given in them */
+    int diverge_cycles;      /* stop with GCMG_E_NOCONV once the defect has grown in this many
+                                consecutive cycles (rho > 1); 0: only NaN/Inf and max_cycles */
 } gcmg_params;
+
+/* Grid of the problem statement (Sec. 2.1, Eq. mainpr; Sec. 2.3): n[a] nodes on
+ * axis a (all equal: the hierarchy halves every axis), spacing h, node j of
+ * axis a at origin[a] + j h. */
+typedef struct {
+    int dim;
+    int64_t n[3];
+    double h;
+    double origin[3];
+} gcmg_grid;
 
 /* Per-solve report.  rel[m] = ||r^(m)||_inf / ||r^(0)||_inf for m = 0..cycles
  * (max 256 kept), over Omega_h u Gamma_h, in FP64; the ratio of consecutive
@@ -109,6 +126,7 @@ typedef struct {
     double rel_residual;
     double r0_norm;
     double rel[257];
+    int diverged;    /* 1: stopped because the defect grew diverge_cycles cycles in a row */
 } gcmg_stats;
 
 /* Fills p with the defaults above for (dim, n, n_coarse). */
@@ -122,6 +140,13 @@ gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse);
  * cudaStream_t (NULL: default).  On failure *out is NULL unless a context
  * exists to read the message from; destroy it with gcmg_destroy. */
 gcmg_status gcmg_create(const gcmg_params *p, const double *phi_dev, void *stream, gcmg_ctx **out);
+
+/* gcmg_create on an explicit grid: grid->dim, n[0] (= n[1] = n[2] for the axes
+ * used), h and origin replace the corresponding fields of p (p's other
+ * fields, n_coarse included, are used as given).  phi_dev holds the level set
+ * at the grid's nodes.  GCMG_E_ARG: unequal n, h <= 0 or not finite. */
+gcmg_status gcmg_create_grid(const gcmg_grid *grid, const double *phi_dev, const gcmg_params *p, void *stream,
+                             gcmg_ctx **out);
 
 /* Reinitialisation of a level set (Eq. sdf, Sec. 2.1), for a phi0 that is not
  * a signed distance function, before gcmg_create: phi_dev (device, n^dim
@@ -181,15 +206,37 @@ gcmg_status gcmg_junction_solve_set(gcmg_ctx *ctx, int level, uint8_t *mask_host
  * dense inverse. */
 gcmg_status gcmg_set_bc_types(gcmg_ctx *ctx, int level, const uint8_t *types_host);
 
+/* The boundary types a level's ghosts carry now (host, count bytes, 0
+ * Dirichlet, 1 Neumann): those of gcmg_set_bc_types or of the mask below. */
+gcmg_status gcmg_bc_types(const gcmg_ctx *ctx, int level, uint8_t *types_host);
+
+/* Boundary types of every level from a Dirichlet/Neumann mask on the fine
+ * grid (Sec. 2.1: Gamma = Gamma_D u Gamma_N; a ghost's type is that of the
+ * part its B lies on, Sec. 2.3): mask_dev (device, n^d bytes, 0 Dirichlet,
+ * nonzero Neumann).  For each ghost of each level the mask is read at the
+ * fine node nearest B (per axis round((B_a - origin_a) / h); a tie goes to the
+ * side of the ghost G itself), on the device; the types then take effect as
+ * with gcmg_set_bc_types on every level.  Synchronises the stream. */
+gcmg_status gcmg_set_bc_types_from_mask(gcmg_ctx *ctx, const uint8_t *mask_dev);
+
 /* Right-hand side: f_dev (device, n^d doubles; values at inside nodes are
  * used) and g_dev (device, one double per fine ghost: g_D(B) or g_N(B)). */
 gcmg_status gcmg_set_rhs(gcmg_ctx *ctx, const double *f_dev, const double *g_dev);
 
 /* Multigrid solve: u_dev (device, n^d doubles) holds the initial guess on
  * entry and the solution on exit (0 off Omega_h u Gamma_h).  Stops at
- * rel <= rtol or max_cycles; returns GCMG_E_NOCONV if not converged.  stats
- * may be NULL. */
+ * rel <= rtol, after max_cycles, at a NaN/Inf defect or once the defect has
+ * grown in diverge_cycles consecutive cycles (stats->diverged = 1); returns
+ * GCMG_E_NOCONV if not converged.  stats may be NULL. */
 gcmg_status gcmg_solve(gcmg_ctx *ctx, double *u_dev, gcmg_stats *stats);
+
+/* FP64 defect of a fine-grid function (TGCS step 3, Eq. discr): r_dev
+ * (device, n^d doubles) = f + Lap_h u on Omega_h, g - L_h u on Gamma_h (stored
+ * at the ghost node), 0 elsewhere, with the f and g of gcmg_set_rhs; u_dev
+ * (device, n^d doubles) is read at Omega_h u Gamma_h.  rel_norm (host, may
+ * be NULL) = ||r||_inf / ||(f, g)||_inf over Omega_h u Gamma_h (the solve's
+ * relative residual; 0 if f = g = 0).  GCMG_E_STATE before gcmg_set_rhs. */
+gcmg_status gcmg_residual(gcmg_ctx *ctx, const double *u_dev, double *r_dev, double *rel_norm);
 
 /* Same solve with host buffers: copies f_host (n^d), g_host (fine ghosts) to
  * the device, solves from u = 0 and copies the solution to u_host (n^d). */
@@ -269,6 +316,16 @@ gcmg_status gcmg_kernel_timing(gcmg_ctx *ctx, int64_t *launches, double *total_m
  * and boundary blocks together; timed under class 0 or 4) also the interior
  * sweep's u and f read and u written once per inside node. */
 gcmg_status gcmg_kernel_timing_ex(gcmg_ctx *ctx, int64_t *launches, double *total_ms, double *alg_bytes);
+
+/* The 3D boundary relaxation (ghost sweep, lambda band sweeps and the
+ * junction sweeps, Sec. 3.2) runs by default as one launch per phase;
+ * enable = 1 runs it as one launch whose phases are separated by grid-wide
+ * barriers (same results; measured slower on GB300).  Each barrier wait
+ * gives up after spin_limit polls (default 4,194,304, about a second) and
+ * the solve then returns GCMG_E_TIMEOUT with the context still usable;
+ * phantom_blocks > 0 makes every barrier wait for that many CTAs that do not
+ * exist, so that a test can make the waits run out.  Not in the paper. */
+gcmg_status gcmg_debug_barrier(gcmg_ctx *ctx, int enable, int phantom_blocks, unsigned spin_limit);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t gcmg_launch_counter(void);

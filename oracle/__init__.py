@@ -30,10 +30,19 @@ def build(force: bool = False) -> str:
     """Compile the oracle shared library next to its source."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        _compile(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def _compile(src, out):
+    """gcc with OpenMP where it is available (the loops it splits are
+    order-independent: results do not depend on the thread count)."""
+    base = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, src, "-lm"]
+    try:
+        subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+    except (subprocess.CalledProcessError, OSError):
+        subprocess.check_call(base)
 
 
 class Params(C.Structure):
@@ -84,6 +93,8 @@ def _load(path):
         L.orc_kaczmarz_row.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp]
         L.orc_assemble.restype = i64
         L.orc_assemble.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+        L.orc_set_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_solve.restype = C.c_int
         L.orc_solve.argtypes = [vp, vp, dbl, C.c_int, vp, C.POINTER(C.c_int)]
     return L
@@ -104,7 +115,7 @@ def build_variant(source: str, out_dir: str) -> str:
     out = os.path.join(out_dir, "liboracle_variant.so")
     with open(src, "w") as fh:
         fh.write(source)
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", out, src, "-lm"])
+    _compile(src, out)
     return out
 
 
@@ -118,6 +129,12 @@ def variant(path: str):
         yield _lib
     finally:
         _lib = saved
+
+
+def set_threads(k: int) -> int:
+    """Threads of the oracle's parallel loops (1: serial); returns the count
+    in effect (1 when the library was built without OpenMP)."""
+    return lib().orc_set_threads(int(k))
 
 
 def _p(a):

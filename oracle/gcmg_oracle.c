@@ -20,9 +20,20 @@
  * order (x slowest, Sec. 2.4 GS-LEX).
  *
  * Build: gcc -O2 -std=c99 -ffp-contract=off -fPIC -shared (no FMA
- * contraction, so x86 and Arm hosts round identically).
+ * contraction, so x86 and Arm hosts round identically), with -fopenmp where
+ * the compiler has it.  OpenMP only splits loops whose iterations are
+ * independent (one colour of a red-black sweep, the Jacobi ghost update, the
+ * defect, the restriction, the interpolation, the band marks), so the
+ * results are bitwise the same for any number of threads; orc_set_threads
+ * sets the count (1: serial).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -455,6 +466,7 @@ static int build_ghost(Oracle *O, Level *L, int64_t q) {
  * interior node P is estimated by -phi(P)/|grad_h phi(P)|.
  */
 static void build_band(Level *L, double delta) {
+    ORC_PARALLEL_FOR
     for (int64_t i = 0; i < L->nn; i++) {
         L->band[i] = 0;
         if (L->type[i] != T_INT) continue;
@@ -598,19 +610,23 @@ static void interior_update(Level *L, int64_t i) {
 
 /* red (even sum of indices) then black half sweep; band_only restricts to band */
 static void rb_sweep(Level *L, int band_only) {
-    for (int color = 0; color < 2; color++)
+    for (int color = 0; color < 2; color++) {
+        ORC_PARALLEL_FOR
         for (int64_t i = 0; i < L->nn; i++) {
             if (L->type[i] != T_INT) continue;
             if (band_only && !L->band[i]) continue;
             if (parity(L, i) != color) continue;
             interior_update(L, i);
         }
+    }
 }
 
 /* simultaneous (Jacobi) update of all ghosts from the current values */
 static void ghost_jacobi(Level *L) {
+    ORC_PARALLEL_FOR
     for (int64_t q = 0; q < L->ng; q++)
         L->gtmp[q] = L->u[L->gnode[q]] + L->c[q] * (L->g[q] - ghost_operator(L, q, L->u));
+    ORC_PARALLEL_FOR
     for (int64_t q = 0; q < L->ng; q++) L->u[L->gnode[q]] = L->gtmp[q];
 }
 
@@ -642,11 +658,15 @@ static void base_relax(Oracle *O, Level *L) {
  * sweeps (red, black, then Jacobi on the ghosts; zone_sweep) or by solving
  * their equations exactly (zone_solve, below). */
 static void zone_sweep(Level *L) {
-    for (int color = 0; color < 2; color++)
+    for (int color = 0; color < 2; color++) {
+        ORC_PARALLEL_FOR
         for (int64_t i = 0; i < L->nn; i++)
             if (L->type[i] == T_INT && L->jzone[i] && parity(L, i) == color) interior_update(L, i);
+    }
+    ORC_PARALLEL_FOR
     for (int64_t q = 0; q < L->ng; q++)
         if (L->jzone[L->gnode[q]]) L->gtmp[q] = L->u[L->gnode[q]] + L->c[q] * (L->g[q] - ghost_operator(L, q, L->u));
+    ORC_PARALLEL_FOR
     for (int64_t q = 0; q < L->ng; q++)
         if (L->jzone[L->gnode[q]]) L->u[L->gnode[q]] = L->gtmp[q];
 }
@@ -867,6 +887,7 @@ static void smooth(Oracle *O, Level *L, int nu) {
  * r = f + Delta_h u on Omega_h, r = g - L_h u on Gamma_h, 0 elsewhere.
  */
 static void defect(const Level *L, const double *u, double *r) {
+    ORC_PARALLEL_FOR
     for (int64_t i = 0; i < L->nn; i++) {
         if (L->type[i] == T_INT) {
             double lap = -2.0 * L->dim * u[i];
@@ -979,6 +1000,7 @@ static double partial_transfer(const Level *F, const int jf[MAXD], int interior_
 }
 
 static void restrict_defect(const Level *F, Level *C, const double *r, double *fc, double *gc) {
+    ORC_PARALLEL_FOR
     for (int64_t X = 0; X < C->nn; X++) {
         int J[MAXD], jf[MAXD];
         idx_to_j(C, X, J);
@@ -1023,6 +1045,7 @@ static double prolong_at(const Level *F, const Level *C, int64_t P, const double
 }
 
 static void prolong_correct(Level *F, const Level *C) {
+    ORC_PARALLEL_FOR
     for (int64_t P = 0; P < F->nn; P++)
         if (is_unknown(F, P)) F->u[P] += prolong_at(F, C, P, C->u);
 }
@@ -1223,6 +1246,18 @@ void orc_destroy(void *h) {
     for (int l = 0; l < O->nlev; l++) free_level(&O->L[l]);
     free(O->L);
     free(O);
+}
+
+/* threads of the loops marked ORC_PARALLEL_FOR (1: serial); returns the
+ * count in effect (always 1 without OpenMP) */
+int orc_set_threads(int k) {
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+    return omp_get_max_threads();
+#else
+    (void)k;
+    return 1;
+#endif
 }
 
 int orc_status(void *h) { return ((Oracle *)h)->status; }

@@ -154,6 +154,17 @@ void upload_geometry(gcmg_ctx *c, int l) {
         g.nstrips = (int)st.size();
         g.strips = upload<int32_t>(c, st.data(), st.size());
     }
+    if (!L.zm.empty()) {
+        g.nzm = (int)(L.zm.size() / 2);
+        g.zm = upload<int32_t>(c, L.zm.data(), L.zm.size());
+        g.zm_moff = upload<int32_t>(c, L.zm_moff.data(), L.zm_moff.size());
+        g.zm_mask = upload<uint32_t>(c, L.zm_mask.data(), L.zm_mask.size());
+    }
+    if (!L.chunk.empty()) {
+        g.nchunks = (int64_t)L.chunk.size();
+        g.chunks = upload<int32_t>(c, L.chunk.data(), L.chunk.size());
+        g.chunk_len = upload<uint8_t>(c, L.chunk_len.data(), L.chunk_len.size());
+    }
     g.black = upload<int32_t>(c, L.band_black.data(), L.band_black.size());
     g.enode = upload<int32_t>(c, L.ext_node.data(), L.ext_node.size());
     g.ecnt = upload<uint8_t>(c, L.ext_cnt.data(), L.ext_cnt.size());
@@ -337,6 +348,13 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
                 launch_kaczmarz(v, c->kz_rows[l], c->kz_off[l], extra ? c->p.lambda : 1, c->stream);
             return v.u;
         }
+    } else if (g.nzm > 0) {
+        // 3D: both colours in one pass over the active tiles (reads v.u, writes out)
+        const double bytes = c->timing_kind >= 0 ? 3.0 * (double)c->H[l].n_in * sizeof(T) : 0.0;
+        timer_mark(c, GCMG_KERNEL_SMOOTH, l, bytes);
+        launch_rb_zmarch<T>(v, out, g, c->stream);
+        timer_mark(c, GCMG_KERNEL_SMOOTH, l);
+        v.u = out;
     } else {
         for (int colour = 0; colour < 2; colour++) {
             timer_mark(c, GCMG_KERNEL_SMOOTH, l);
@@ -355,13 +373,44 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         if (bzv.wb) pending = &bzv;
     } else {
-        launch_ghost_relax<T>(v, dim, c->stream);
-        if (!extra) return v.u;
-        for (int k = 0; k < c->p.lambda; k++) {
-            launch_rb_list<T>(v, dim, g.red, g.nred, c->stream);
-            launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
-            launch_ghost_relax<T>(v, dim, c->stream);
+        // 3D: the ghost sweep, the band sweeps and (on global lists) the
+        // junction sweeps as one launch with grid-wide barriers
+        bool done = false, zdone = false;
+        if (dim == 3 && c->coop3d && c->p.smoother == 0 && g.ng > 0) {
+            BoundaryProgram3 P;
+            P.red = g.red;
+            P.nred = g.nred;
+            P.black = g.black;
+            P.nblack = g.nblack;
+            P.lambda = extra ? c->p.lambda : 0;
+            zdone = extra && !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 && !g.jz.in_smem;
+            if (zdone) {
+                P.zred = g.jz.zred;
+                P.nzred = g.jz.nzred;
+                P.zblack = g.jz.zblack;
+                P.nzblack = g.jz.nzblack;
+                P.zghost = g.jz.zghost;
+                P.nzghost = g.jz.nzghost;
+                P.mu = c->p.junction_sweeps;
+            }
+            P.bar = c->d_bar;
+            P.err = c->d_err;
+            P.spin = c->bar_spin;
+            timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
+            done = launch_boundary3d<T>(v, P, c->bar_phantom, c->stream);
+            timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
+            if (!done) zdone = false;
         }
+        if (!done) {
+            launch_ghost_relax<T>(v, dim, c->stream);
+            if (extra)
+                for (int k = 0; k < c->p.lambda; k++) {
+                    launch_rb_list<T>(v, dim, g.red, g.nred, c->stream);
+                    launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
+                    launch_ghost_relax<T>(v, dim, c->stream);
+                }
+        }
+        if (!extra || zdone) return v.u;
     }
     if (c->p.junction_solve) {
         const DevData<T> &D = data<T>(c)[l];
@@ -438,13 +487,23 @@ T *cycle(gcmg_ctx *c, int l, T *u) {
     return u;
 }
 
-__global__ void k_rhs_norm(const uint8_t *type, const double *f, int64_t nn, const double *g, int ng,
-                           unsigned long long *bits) {
+// ||(f, g)||_inf: f over the inside nodes (those of the active chunks where
+// the level has them), g over the ghosts
+__global__ void k_rhs_norm(LevelView<double> lv, const double *g, int ng, unsigned long long *bits) {
     __shared__ double wmax[32];
+    const uint8_t *type = lv.type;
+    const double *f = lv.f;
+    const int64_t nt = lv.chunks ? lv.nchunks * CHUNK : lv.nn;
     double v = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn || i < ng;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt || i < ng;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < nn && (type[i] & NODE_KIND) == NODE_IN) v = fmax(v, fabs(f[i]));
+        int64_t p = i;
+        bool ok = i < nt;
+        if (ok && lv.chunks) {   // thread i: node i % CHUNK of chunk i / CHUNK
+            ok = (int)(i % CHUNK) < (lv.clen[i / CHUNK] & 63);
+            p = (int64_t)lv.chunks[i / CHUNK] + i % CHUNK;
+        }
+        if (ok && (type[p] & NODE_KIND) == NODE_IN) v = fmax(v, fabs(f[p]));
         if (i < ng) v = fmax(v, fabs(g[i]));
         if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);
     }
@@ -483,15 +542,35 @@ double fine_defect_norm(gcmg_ctx *c) {
     return read_norm(c);
 }
 
-// end of one loop iteration: records rel[m] and sets the while condition
-__global__ void k_loop_check(cudaGraphConditionalHandle h, const unsigned long long *bits, const double *r0,
-                             double *rel, int *m, double rtol, int max_cycles) {
+// whether a bounded barrier wait of k_boundary3d ran out since the last
+// check (synchronises the stream); if so the flag and the barrier words are
+// cleared for the next launch
+bool barrier_timed_out(gcmg_ctx *c) {
+    if (!c->d_err) return false;
+    int e = 0;
+    ck(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "err");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    if (!e) return false;
+    ck(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
+    ck(cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream), "memset");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    return true;
+}
+
+// end of one loop iteration: records rel[m] and sets the while condition;
+// r0[1] holds the previous relative residual, m[1] the number of consecutive
+// cycles whose defect grew (the loop stops once it reaches `diverge` > 0)
+__global__ void k_loop_check(cudaGraphConditionalHandle h, const unsigned long long *bits, double *r0,
+                             double *rel, int *m, double rtol, int max_cycles, int diverge) {
     const double nr = __longlong_as_double((long long)*bits);
-    const int k = *m + 1;
-    *m = k;
-    const double v = nr / *r0;
+    const int k = m[0] + 1;
+    m[0] = k;
+    const double v = nr / r0[0];
     if (k <= 256) rel[k] = v;
-    const bool go = (v == v) && !isinf(v) && v > rtol && k < max_cycles;
+    m[1] = v > r0[1] ? m[1] + 1 : 0;
+    r0[1] = v;
+    const bool grew = diverge > 0 && m[1] >= diverge;
+    const bool go = (v == v) && !isinf(v) && v > rtol && k < max_cycles && !grew;
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
@@ -502,9 +581,11 @@ __global__ void k_loop_start(cudaGraphConditionalHandle h, const unsigned long l
                              double *rel, int *m, double rtol) {
     const double r0 = __longlong_as_double((long long)bits[1]);
     const double rel0 = r0 > 0.0 ? __longlong_as_double((long long)bits[0]) / r0 : 0.0;
-    *r0_out = r0;
+    r0_out[0] = r0;
+    r0_out[1] = rel0;
     rel[0] = rel0;
-    *m = 0;
+    m[0] = 0;
+    m[1] = 0;
     cudaGraphSetConditional(h, (r0 > 0.0 && !(rel0 <= rtol)) ? 1u : 0u);
 }
 
@@ -514,9 +595,10 @@ void solve_prologue(gcmg_ctx *c, cudaGraphConditionalHandle h) {
     const DevGeom &g0 = c->G[0];
     const HostLevel &L0 = c->H[0];
     ck(cudaMemsetAsync(c->d_norm + 1, 0, sizeof(unsigned long long), c->stream), "memset");
-    const int64_t cnt = std::max<int64_t>(L0.nn, L0.ng());
+    const LevelView<double> lv = view<double>(c, 0, c->D64[0]);
+    const int64_t cnt = std::max<int64_t>(lv.chunks ? lv.nchunks * CHUNK : L0.nn, L0.ng());
     const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 4096);
-    k_rhs_norm<<<nb, 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn, c->D64[0].gg, g0.ng, c->d_norm + 1);
+    k_rhs_norm<<<nb, 256, 0, c->stream>>>(lv, c->D64[0].gg, g0.ng, c->d_norm + 1);
     g_launches++;
     fine_defect(c);
     k_loop_start<<<1, 1, 0, c->stream>>>(h, c->d_norm, c->d_r0, c->d_rel, c->d_m, c->p.rtol);
@@ -607,7 +689,8 @@ void build_graph(gcmg_ctx *c) {
     const long long before = g_launches.load();
     try {
         loop_body(c);
-        k_loop_check<<<1, 1, 0, c->gstream>>>(h, c->d_norm, c->d_r0, c->d_rel, c->d_m, c->p.rtol, c->p.max_cycles);
+        k_loop_check<<<1, 1, 0, c->gstream>>>(h, c->d_norm, c->d_r0, c->d_rel, c->d_m, c->p.rtol, c->p.max_cycles,
+                                              c->p.diverge_cycles);
         g_launches++;
         c->graph_kernels = g_launches.load() - before;
         g_launches -= c->graph_kernels;   // counted when executed
@@ -666,13 +749,16 @@ gcmg_status check_params(const gcmg_params &q) {
     if (p->junction_sweeps < 0 || p->junction_radius < 0.0 || p->junction_radius > 64.0) return GCMG_E_ARG;
     if (p->junction_solve < 0 || p->junction_solve > 1 || p->fused_coarse_n < 0) return GCMG_E_ARG;
     if (p->smoother < 0 || p->smoother > 1) return GCMG_E_ARG;
+    if (!(p->h >= 0.0) || !std::isfinite(p->h) || p->diverge_cycles < 0) return GCMG_E_ARG;
+    for (int a = 0; a < p->dim; a++)
+        if (!std::isfinite(p->origin[a])) return GCMG_E_ARG;
     if (p->smoother == 1 && (p->dim != 2 || p->precision != 0 || p->junction_solve || p->junction_sweeps))
         return GCMG_E_ARG;
     return GCMG_OK;
 }
 
 void prepare_levels(const gcmg_params &p, const double *phi_host, std::vector<HostLevel> &H) {
-    build_hierarchy(p.dim, p.n, p.n_coarse, phi_host, p.delta_over_h, H);
+    build_hierarchy(p.dim, p.n, p.n_coarse, phi_host, p.delta_over_h, H, p.h, p.origin);
     if (p.dim == 2)
         for (auto &L : H) build_boundary_blocks(L, p.lambda, 32);
 }
@@ -705,8 +791,12 @@ gcmg_status create_from_levels(const gcmg_params &q, std::vector<HostLevel> &&H,
         }
         c->d_norm = dalloc<unsigned long long>(c, 2);
         c->d_rel = dalloc<double>(c, 257);
-        c->d_r0 = dalloc<double>(c, 1);
-        c->d_m = dalloc<int>(c, 1);
+        c->d_r0 = dalloc<double>(c, 2);   // r0, the last relative residual
+        c->d_m = dalloc<int>(c, 2);       // cycles, consecutive growing cycles
+        c->d_bar = dalloc<unsigned>(c, 2);
+        c->d_err = dalloc<int>(c, 1);
+        ck(cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream), "memset");
+        ck(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
         ck(cudaMallocHost((void **)&c->h_norm, 2 * sizeof(unsigned long long)), "cudaMallocHost");
         ck(cudaStreamSynchronize(c->stream), "sync");
         return GCMG_OK;
@@ -820,6 +910,22 @@ void ensure_inverse(gcmg_ctx *c) {
 
 extern "C" {
 
+gcmg_status gcmg_create_grid(const gcmg_grid *grid, const double *phi_dev, const gcmg_params *p, void *stream,
+                             gcmg_ctx **out) {
+    if (out) *out = nullptr;
+    if (!grid || !p || !phi_dev || !out) return GCMG_E_ARG;
+    if (grid->dim < 2 || grid->dim > 3 || !(grid->h > 0.0) || !std::isfinite(grid->h)) return GCMG_E_ARG;
+    for (int a = 1; a < grid->dim; a++)
+        if (grid->n[a] != grid->n[0]) return GCMG_E_ARG;
+    if (grid->n[0] < 3 || grid->n[0] > 65537) return GCMG_E_ARG;
+    gcmg_params q = *p;
+    q.dim = grid->dim;
+    q.n = (int)grid->n[0];
+    q.h = grid->h;
+    for (int a = 0; a < 3; a++) q.origin[a] = a < grid->dim ? grid->origin[a] : -1.0;
+    return gcmg_create(&q, phi_dev, stream, out);
+}
+
 gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
     if (!p) return GCMG_E_ARG;
     std::memset(p, 0, sizeof(*p));
@@ -845,6 +951,9 @@ gcmg_status gcmg_default_params(gcmg_params *p, int dim, int n, int n_coarse) {
     p->junction_radius = dim == 3 ? 2.0 : 20.0;
     p->fused_coarse_n = 0;   // measured slower than the per-level launches on GB300
     p->smoother = 0;
+    p->h = 0.0;               // 2 / (n - 1): the box [-1,1]^d
+    p->origin[0] = p->origin[1] = p->origin[2] = -1.0;
+    p->diverge_cycles = 3;
     return GCMG_OK;
 }
 
@@ -963,6 +1072,100 @@ gcmg_status gcmg_set_bc_types(gcmg_ctx *c, int l, const uint8_t *types) {
     })
 }
 
+gcmg_status gcmg_debug_barrier(gcmg_ctx *c, int enable, int phantom_blocks, unsigned spin_limit) {
+    if (!c || phantom_blocks < 0 || spin_limit == 0) return fail(c, GCMG_E_ARG, "bad argument");
+    destroy_graph(c);   // a captured graph holds the old launch parameters
+    c->coop3d = enable ? 1 : 0;
+    c->bar_phantom = phantom_blocks;
+    c->bar_spin = spin_limit;
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_bc_types(const gcmg_ctx *c, int l, uint8_t *types) {
+    if (!valid_level(c, l) || !types) return GCMG_E_ARG;
+    const HostLevel &L = c->H[l];
+    if (L.ng() > 0) std::memcpy(types, L.bc.data(), (size_t)L.ng());
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_set_bc_types_from_mask(gcmg_ctx *c, const uint8_t *mask_dev) {
+    if (!c || !mask_dev) return fail(c, GCMG_E_ARG, "null pointer");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        const HostLevel &F = c->H[0];
+        int64_t mx = 0;
+        for (const HostLevel &L : c->H) mx = std::max<int64_t>(mx, L.ng());
+        if (mx == 0) return GCMG_OK;
+        std::vector<void *> tmp;   // call-scoped device buffers
+        auto scratch = [&](size_t bytes) {
+            void *p = nullptr;
+            if (cudaMalloc(&p, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                for (void *q : tmp) cudaFree(q);
+                throw std::bad_alloc();
+            }
+            tmp.push_back(p);
+            return p;
+        };
+        double *B = static_cast<double *>(scratch((size_t)mx * F.dim * sizeof(double)));
+        int32_t *gn = static_cast<int32_t *>(scratch((size_t)mx * sizeof(int32_t)));
+        uint8_t *ty = static_cast<uint8_t *>(scratch((size_t)mx));
+        std::vector<uint8_t> types;
+        gcmg_status st = GCMG_OK;
+        try {
+            for (int l = 0; l < (int)c->H.size() && st == GCMG_OK; l++) {
+                const HostLevel &L = c->H[l];
+                const int64_t ng = L.ng();
+                if (ng == 0) continue;
+                ck(cudaMemcpyAsync(B, L.B.data(), ng * L.dim * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                   "B");
+                ck(cudaMemcpyAsync(gn, L.ghost_node.data(), ng * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream),
+                   "ghost nodes");
+                launch_mask_types(L.dim, F.n, F.h, F.origin, 1 << l, L.n, B, gn, (int)ng, mask_dev, ty, c->stream);
+                types.resize(ng);
+                ck(cudaMemcpyAsync(types.data(), ty, ng, cudaMemcpyDeviceToHost, c->stream), "types");
+                ck(cudaStreamSynchronize(c->stream), "sync");
+                st = gcmg_set_bc_types(c, l, types.data());
+            }
+        } catch (...) {
+            cudaStreamSynchronize(c->stream);
+            for (void *q : tmp) cudaFree(q);
+            throw;
+        }
+        for (void *q : tmp) cudaFree(q);
+        return st;
+    })
+}
+
+gcmg_status gcmg_residual(gcmg_ctx *c, const double *u_dev, double *r_dev, double *rel_norm) {
+    if (!c || !u_dev || !r_dev) return fail(c, GCMG_E_ARG, "null pointer");
+    if (!c->rhs_set) return fail(c, GCMG_E_STATE, "gcmg_set_rhs has not been called");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        const HostLevel &L0 = c->H[0];
+        const DevGeom &g0 = c->G[0];
+        LevelView<double> v = view<double>(c, 0, c->D64[0]);
+        // ||(f, g)|| into slot 1, the defect's norm into slot 0
+        ck(cudaMemsetAsync(c->d_norm, 0, 2 * sizeof(unsigned long long), c->stream), "memset");
+        const int64_t cnt = std::max<int64_t>(v.chunks ? v.nchunks * CHUNK : L0.nn, L0.ng());
+        const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 4096);
+        k_rhs_norm<<<nb, 256, 0, c->stream>>>(v, c->D64[0].gg, g0.ng, c->d_norm + 1);
+        g_launches++;
+        v.u = const_cast<double *>(u_dev);
+        v.r = r_dev;
+        launch_defect<double>(v, c->p.dim, true, c->d_norm, c->stream);
+        check_launch();
+        ck(cudaMemcpyAsync(c->h_norm, c->d_norm, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           c->stream), "norms");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        double rn, r0;
+        std::memcpy(&rn, &c->h_norm[0], sizeof(double));
+        std::memcpy(&r0, &c->h_norm[1], sizeof(double));
+        if (rel_norm) *rel_norm = r0 > 0.0 ? rn / r0 : 0.0;
+        return GCMG_OK;
+    })
+}
+
 gcmg_status gcmg_set_rhs(gcmg_ctx *c, const double *f_dev, const double *g_dev) {
     if (!c || !f_dev || (!g_dev && c->H[0].ng() > 0)) return fail(c, GCMG_E_ARG, "null pointer");
     GCMG_GUARD(c, {
@@ -1038,7 +1241,7 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
         std::memset(&st, 0, sizeof(st));
         int m = 0;
         double rel = 0.0;
-        bool ok = false;
+        bool ok = false, diverged = false;
         if (c->use_graph && c->timing_kind < 0) {
             // one graph: ||(f, g)||, the first defect, then the loop; one
             // read-back at the end
@@ -1051,9 +1254,10 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
             gcmg_ctx::SolveResult *R = c->h_res;
             ck(cudaMemcpyAsync(&R->r0, c->d_r0, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "r0");
             ck(cudaMemcpyAsync(R->rel, c->d_rel, sizeof(R->rel), cudaMemcpyDeviceToHost, c->stream), "rel");
-            ck(cudaMemcpyAsync(&R->m, c->d_m, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "m");
+            ck(cudaMemcpyAsync(R->m, c->d_m, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream), "m");
             ck(cudaStreamSynchronize(c->stream), "sync");
-            m = R->m;
+            m = R->m[0];
+            diverged = c->p.diverge_cycles > 0 && R->m[1] >= c->p.diverge_cycles;
             g_launches += c->graph_pro_kernels + c->graph_kernels * m;
             const int kept = std::min(m, 256);
             std::memcpy(st.rel, R->rel, (kept + 1) * sizeof(double));
@@ -1064,9 +1268,10 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
             // ||r0|| = ||(f, g)||
             ck(cudaMemsetAsync(c->d_norm, 0, sizeof(unsigned long long), c->stream), "memset");
             {
-                const int64_t cnt = std::max<int64_t>(L0.nn, L0.ng());
+                const LevelView<double> lv = view<double>(c, 0, c->D64[0]);
+                const int64_t cnt = std::max<int64_t>(lv.chunks ? lv.nchunks * CHUNK : L0.nn, L0.ng());
                 const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 4096);
-                k_rhs_norm<<<nb, 256, 0, c->stream>>>(g0.type, c->D64[0].f, L0.nn, c->D64[0].gg, g0.ng, c->d_norm);
+                k_rhs_norm<<<nb, 256, 0, c->stream>>>(lv, c->D64[0].gg, g0.ng, c->d_norm);
                 g_launches++;
             }
             check_launch();
@@ -1075,24 +1280,35 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
             if (r0 > 0.0) rel = fine_defect_norm(c) / r0;
             st.rel[0] = rel;
             ok = (r0 == 0.0) || rel <= c->p.rtol;
+            int grow = 0;
             while (!ok && m < c->p.max_cycles) {
                 loop_body(c);
                 check_launch();
                 m++;
+                const double prev = rel;
                 rel = read_norm(c) / r0;
                 if (m <= 256) st.rel[m] = rel;
                 if (!(rel == rel) || std::isinf(rel)) break;
                 ok = rel <= c->p.rtol;
+                grow = rel > prev ? grow + 1 : 0;
+                if (!ok && c->p.diverge_cycles > 0 && grow >= c->p.diverge_cycles) {
+                    diverged = true;
+                    break;
+                }
             }
         }
         if (u_dev != u)
             ck(cudaMemcpyAsync(u_dev, u, L0.nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "u out");
         ck(cudaStreamSynchronize(c->stream), "sync");
+        if (barrier_timed_out(c)) return fail(c, GCMG_E_TIMEOUT, "a grid barrier of the 3D boundary relaxation "
+                                                                "gave up waiting");
         st.cycles = m;
         st.converged = ok ? 1 : 0;
+        st.diverged = (!ok && diverged) ? 1 : 0;
         st.rel_residual = rel;
         if (stats) *stats = st;
-        if (!ok) return fail(c, GCMG_E_NOCONV, "not converged");
+        if (!ok) return fail(c, GCMG_E_NOCONV, st.diverged ? "diverged: the defect grew in consecutive cycles"
+                                                         : "not converged");
         return GCMG_OK;
     })
 }
@@ -1168,6 +1384,7 @@ gcmg_status gcmg_relax(gcmg_ctx *c, int l, double *u, const double *f, const dou
         if (res != u) ck(cudaMemcpyAsync(u, res, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "copy");
         check_launch();
         ck(cudaStreamSynchronize(c->stream), "sync");
+        if (barrier_timed_out(c)) return fail(c, GCMG_E_TIMEOUT, "a grid barrier gave up waiting");
         return GCMG_OK;
     })
 }

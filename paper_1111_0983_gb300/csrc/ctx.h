@@ -46,13 +46,22 @@ struct gcmg_ctx {
     double *d_rel = nullptr;                // rel[0..256]
     double *d_r0 = nullptr;
     int *d_m = nullptr;
+    // the 3D boundary relaxation in one launch (k_boundary3d): barrier words,
+    // timeout flag; coop3d = 0 (default: measured faster, about 5 us a
+    // barrier against 2-3 us a launch) runs it as one launch per phase;
+    // phantom > 0 and spin make its barriers wait for CTAs that never arrive
+    // (the timeout test)
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr;
+    int coop3d = 0, bar_phantom = 0;
+    unsigned bar_spin = 1u << 22;
     bool use_graph = true;
     long long graph_kernels = 0;            // kernels in one loop iteration
     long long graph_pro_kernels = 0;        // kernels before the loop
     struct SolveResult {                    // what a graph solve reports back (pinned)
         double r0;
         double rel[257];
-        int m;
+        int m[2];                           // cycles done, consecutive cycles whose defect grew
     } *h_res = nullptr;
     // event timing of one fine-level kernel class during solves
     int timing_kind = -1;
@@ -102,6 +111,9 @@ LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
     v.gc = D.gc;
     v.gg = D.gg;
     v.gtmp = D.gtmp;
+    v.chunks = g.chunks;
+    v.clen = g.chunk_len;
+    v.nchunks = g.nchunks;
     return v;
 }
 

@@ -17,6 +17,14 @@ constexpr int STRIP_W = 60; // 2D sweep strips: owned columns (a warp holds 64)
 constexpr int TILE_R = 16; // 2D interior tiles: rows (axis 0)
 constexpr int TILE_C = 64; //                    columns (axis 1, contiguous)
 constexpr int EMAX = 6;    // extension sources (2 d)
+constexpr int CHUNK = 32;  // 3D active chunks: nodes along the contiguous axis (a warp)
+// 3D fused sweep (k_rb_zmarch): a CTA owns ZM_TY rows (axis 1) x ZM_TX columns
+// (axis 2, contiguous) and marches along axis 0 over at most ZM_SEG planes
+constexpr int ZM_TY = 16, ZM_TX = 64, ZM_SEG = 32;
+// its inside-node masks: per plane (ZM_TY + 2) rows of ZM_TX + 2 bits (the
+// tile and a 1-node halo), ZM_MROW words a row, planes padded to 16 bytes
+constexpr int ZM_MROW = (ZM_TX + 2 + 31) / 32;
+constexpr int ZM_MPLANE = ((ZM_TY + 2) * ZM_MROW + 3) / 4 * 4;
 
 // NODE_WB marks, in the device copy of the type grid only, the nodes that the
 // 2D boundary blocks write back through the write-back grid
@@ -51,6 +59,7 @@ struct LocalProgram {
 struct HostLevel {
     int dim = 2, n = 0;
     double h = 0;
+    double origin[3] = {-1.0, -1.0, -1.0};   // coordinates of node 0
     int64_t nn = 0;
     int64_t stride[3] = {0, 0, 0};
     std::vector<double> phi;
@@ -67,6 +76,18 @@ struct HostLevel {
     std::vector<int32_t> band_red, band_black;
     // 2D tiles (TILE_R x TILE_C) holding inside nodes, packed (tile row << 16 | tile column)
     std::vector<int32_t> tiles;
+    // 3D active chunks: runs of CHUNK nodes along the contiguous axis (start
+    // at a multiple of CHUNK) holding an inside node or a ghost; first node
+    // and length (the last run of a row is shorter)
+    std::vector<int32_t> chunk;
+    std::vector<uint8_t> chunk_len;
+    // 3D fused-sweep work: pairs (tile row << 16 | tile column, first plane
+    // << 16 | end plane), the planes of a tile that hold inside nodes or ghosts
+    std::vector<int32_t> zm;
+    // per item: offset (in ZM_MPLANE-word planes) of its inside-node masks
+    // for planes first - 1 .. end, in zm_mask
+    std::vector<int32_t> zm_moff;
+    std::vector<uint32_t> zm_mask;
     // defect extension of this level (before restricting to the next coarser one)
     std::vector<int32_t> ext_node;      // ordered by upwind wavefront
     std::vector<uint8_t> ext_cnt;
@@ -97,9 +118,11 @@ struct HostLevel {
     int64_t ng() const { return (int64_t)ghost_node.size(); }
 };
 
-// Builds all levels (throws GeomError).  phi: fine grid, n^dim values.
+// Builds all levels (throws GeomError).  phi: fine grid, n^dim values; h0:
+// fine spacing (0: 2 / (n - 1)); origin: coordinates of node 0 (null: -1 on
+// every axis).
 void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
-                     std::vector<HostLevel> &levels);
+                     std::vector<HostLevel> &levels, double h0 = 0.0, const double *origin = nullptr);
 // Partial-transfer weights (Sec. 2.5) at the fine image p of a coarse node over
 // the inside set (interior) or its complement; wt[3^dim], axis 0 slowest.
 bool partial_transfer_weights(const HostLevel &F, int64_t p, bool interior, double *wt);
@@ -155,6 +178,13 @@ struct DevGeom {
     int32_t *tiles = nullptr;    // active 2D interior tiles
     int nstrips = 0, strip_rows = 0;
     int32_t *strips = nullptr;   // active 2D sweep strips (strip_rows x STRIP_W owned nodes)
+    int nzm = 0;                 // 3D fused-sweep work items (HostLevel::zm pairs)
+    int32_t *zm = nullptr;
+    int32_t *zm_moff = nullptr;  // and their inside-node masks
+    uint32_t *zm_mask = nullptr;
+    int64_t nchunks = 0;         // 3D active chunks (HostLevel::chunk)
+    int32_t *chunks = nullptr;
+    uint8_t *chunk_len = nullptr;
     int32_t *enode = nullptr;    // ne
     uint8_t *ecnt = nullptr;     // ne
     int32_t *esrc = nullptr;     // EMAX * ne, slot major
@@ -211,6 +241,27 @@ struct LevelView {
     const T *gc;
     const T *gg;
     T *gtmp;
+    // 3D: the active chunks (null in 2D: kernels over nodes then cover the box)
+    const int32_t *chunks = nullptr;
+    const uint8_t *clen = nullptr;
+    int64_t nchunks = 0;
+};
+
+// One 3D boundary relaxation as a single launch (k_boundary3d): the Jacobi
+// ghost sweep, lambda x (band red, band black, ghost sweep) and mu x the same
+// over the junction-zone lists, with grid-wide barriers between the phases.
+struct BoundaryProgram3 {
+    const int32_t *red = nullptr, *black = nullptr;
+    int nred = 0, nblack = 0;
+    const int32_t *zred = nullptr, *zblack = nullptr, *zghost = nullptr;
+    int nzred = 0, nzblack = 0, nzghost = 0;
+    int lead = 1;       // start with the ghost sweep of the relaxation itself
+    int lambda = 0;     // band sweeps
+    int mu = 0;         // junction-zone sweeps over the global lists (0: none or done elsewhere)
+    unsigned *bar = nullptr;   // barrier words: arrivals, generation (zero when idle)
+    int *err = nullptr;        // set to 1 when a barrier wait ran out (GCMG_E_TIMEOUT)
+    unsigned nbar = 0;         // CTAs the barrier waits for (the grid; more only in the timeout test)
+    unsigned spin = 0;         // polls before a wait gives up
 };
 
 // Kernel view of a LocalDev program in precision T.

@@ -4,6 +4,7 @@
 // consecutive words.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "gcmg_internal.h"
@@ -18,6 +19,7 @@ namespace {
 
 using namespace dev;
 constexpr int kThreads = 256;
+constexpr unsigned kNormBlocks = 2048;   // grid cap of the kernels that reduce a max-norm
 
 // Launches with programmatic stream serialization: the kernel may be set up
 // while its predecessor in the stream finishes; every kernel of this file
@@ -39,6 +41,13 @@ void pdl_launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaSt
 }
 
 
+
+// threads of a launch over a level's nodes (level_node): its active chunks
+// where it has them and `chunked` allows, else the whole box
+template <typename T>
+inline int64_t level_threads(const LevelView<T> &v, bool chunked) {
+    return chunked && v.chunks ? v.nchunks * CHUNK : v.nn;
+}
 
 inline unsigned blocks_for(int64_t total, int threads = kThreads) {
     int64_t b = (total + threads - 1) / threads;
@@ -73,9 +82,15 @@ __global__ void k_rb_interior(LevelView<T> v, int color) {
     pdl_wait();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t p;
-    if (!decode_colour<D>(v.n, color, t, v.s0, v.s1, p)) return;
+    if (D == 3 && v.chunks) {
+        // over the active chunks: a chunk starts at an even index of its row,
+        // bit 7 of its length byte holds the parity of the row's (i0 + i1)
+        if (!level_node(v, t, p) || (((v.clen[t >> 5] >> 7) + (int)(t & 31)) & 1) != color) return;
+    } else if (!decode_colour<D>(v.n, color, t, v.s0, v.s1, p)) {
+        return;
+    }
     if ((v.type[p] & NODE_KIND) != NODE_IN) return;
-    const T s = v.h2 * v.f[p] + neighbour_sum<T, D>(v.u, p, v.s0, v.s1);
+    const T s = mul_rn(v.h2, v.f[p]) + neighbour_sum<T, D>(v.u, p, v.s0, v.s1);   // h^2 f rounded on its own
     v.u[p] = s * (T)(1.0 / (2 * D));
 }
 
@@ -87,6 +102,280 @@ __global__ void __launch_bounds__(256) k_rb_fused2d(LevelView<T> v, T *__restric
     rb_fused2d_body<T, TR, TC>(v, out, tiles[blockIdx.x]);
 }
 
+// ------------------------------------------------ boundary types from a mask
+// Ghost q of a level: the type of its boundary point B is the mask value at
+// the fine node nearest B; on a tie (B halfway between two fine nodes along
+// an axis) the node on the ghost's side is taken.
+__global__ void k_mask_types(int dim, int n, double h, double o0, double o1, double o2, int step, int n_l,
+                             const double *__restrict__ B, const int32_t *__restrict__ gnode, int ng,
+                             const uint8_t *__restrict__ mask, uint8_t *__restrict__ types) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ng) return;
+    const double org[3] = {o0, o1, o2};
+    int gj[3] = {0, 0, 0};
+    int64_t rem = gnode[q];
+    for (int a = dim - 1; a >= 0; a--) {   // the ghost's index on its own level
+        gj[a] = (int)(rem % n_l);
+        rem /= n_l;
+    }
+    int64_t node = 0;
+    for (int a = 0; a < dim; a++) {
+        const double x = (B[(int64_t)q * dim + a] - org[a]) / h;   // fine index coordinate of B
+        const double fl = floor(x), fr = x - fl;
+        const int g = gj[a] * step;                                   // the ghost's fine index
+        int j = (int)fl + (fr > 0.5 ? 1 : 0);
+        if (fr == 0.5) j = (double)g > x ? (int)fl + 1 : (int)fl;
+        j = min(max(j, 0), n - 1);
+        node = node * n + j;
+    }
+    types[q] = mask[node] ? 1 : 0;
+}
+
+// ------------------------------------------------ 3D fused red-black sweep
+// One Gauss-Seidel sweep of Eq. (jac2d) (7-point form) in red-black order,
+// both colours in one pass over the grid: a CTA owns a ZM_TY x ZM_TX tile of
+// the (axis 1, axis 2) plane and marches along axis 0 over the planes
+// [a, b) of its work item.  At step j it computes the red half-sweep on
+// plane j over the tile and a 1-node halo (from the old values of planes
+// j-1..j+1, staged with a 2-node halo) and the black half-sweep on plane
+// j-1 over the tile (from the half-swept planes j-2..j), and stores plane
+// j-1 into `out`.  Old u, f and the item's inside-node masks reach shared
+// memory through asynchronous copies issued two steps before they are
+// needed (u four planes ahead, f and masks three).  Every CTA reads only
+// v.u and writes only its own nodes of `out`, so the result does not depend
+// on the order of the CTAs; it equals the red sweep followed by the black
+// sweep in place.  Sums in the order of the in-place kernels: h^2 f rounded
+// on its own, then neighbours along axis 2, axis 0, then axis 1.
+constexpr int ZM_THREADS = 512;
+
+template <typename W>
+__device__ __forceinline__ void cp_async_zfill(W *smem, const W *gmem, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    const unsigned bytes = valid ? (unsigned)sizeof(W) : 0u;   // 0: the word is zero-filled
+    if constexpr (sizeof(W) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gmem), "r"(bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(bytes) : "memory");
+}
+// 16 bytes, both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits for all but this thread's two most recent groups of copies
+__device__ __forceinline__ void cp_async_wait_but2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+
+constexpr int ZM_UPLANES = 6, ZM_FPLANES = 5;   // ring depths of old u and of f (and the masks)
+
+template <typename T>
+constexpr size_t zmarch_smem_bytes() {
+    return (size_t)(ZM_UPLANES * (ZM_TY + 4) * (ZM_TX + 4) + (ZM_FPLANES + 3) * (ZM_TY + 2) * (ZM_TX + 2)) *
+               sizeof(T) +
+           (size_t)ZM_FPLANES * ZM_MPLANE * sizeof(uint32_t);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ZM_THREADS, sizeof(T) == 4 ? 3 : 1)
+    k_rb_zmarch(LevelView<T> v, T *__restrict__ out, const int2 *__restrict__ items,
+                const int32_t *__restrict__ moff, const uint32_t *__restrict__ masks) {
+    constexpr int UX = ZM_TX + 4, US = (ZM_TY + 4) * UX;   // old u: 2-node halo
+    constexpr int RX = ZM_TX + 2, RS = (ZM_TY + 2) * RX;   // red region: 1-node halo
+    static_assert((ZM_UPLANES * US + (ZM_FPLANES + 3) * RS) % 4 == 0, "masks start 16-byte aligned");
+    extern __shared__ __align__(16) unsigned char zm_smem[];
+    T *su = reinterpret_cast<T *>(zm_smem);                         // ZM_UPLANES planes of old u
+    T *sf = su + ZM_UPLANES * US;                                   // ZM_FPLANES planes of f
+    T *sh = sf + ZM_FPLANES * RS;                                   // 3 half-swept planes
+    uint32_t *sm = reinterpret_cast<uint32_t *>(sh + 3 * RS);       // ZM_FPLANES mask planes
+    const int tid = threadIdx.x;
+    const int2 item = items[blockIdx.x];
+    const int r0 = (item.x >> 16) * ZM_TY, c0 = (item.x & 0xffff) * ZM_TX;
+    const int a = item.y >> 16, b = item.y & 0xffff;
+    const uint32_t *__restrict__ mg = masks + (int64_t)moff[blockIdx.x] * ZM_MPLANE;   // plane a - 1 first
+    const int n = v.n;
+    const int64_t s0 = v.s0;
+    const T h2 = v.h2, sixth = (T)(1.0 / 6.0);
+    const T *__restrict__ ug = v.u;
+    const T *__restrict__ fg = v.f;
+    auto u_slot = [&](int i) { return su + ((i + ZM_UPLANES) % ZM_UPLANES) * US; };   // i >= -1
+    auto f_slot = [&](int i) { return sf + (i % ZM_FPLANES) * RS; };                  // i >= 0
+    auto m_slot = [&](int i) { return sm + (i % ZM_FPLANES) * ZM_MPLANE; };
+    auto h_slot = [&](int i) { return sh + (i % 3) * RS; };
+    auto load_u = [&](int i) {   // plane i of old u (zeros outside the box)
+        T *dst = u_slot(i);
+        const bool pin = i >= 0 && i < n;
+        for (int idx = tid; idx < US; idx += ZM_THREADS) {
+            const int ry = idx / UX, gj = r0 - 2 + ry, gk = c0 - 2 + (idx - ry * UX);
+            const bool ok = pin && gj >= 0 && gj < n && gk >= 0 && gk < n;
+            cp_async_zfill(dst + idx, ok ? ug + (int64_t)i * s0 + (int64_t)gj * n + gk : ug, ok);
+        }
+    };
+    auto load_f = [&](int i) {   // plane i of f over the red region, and its inside-node mask
+        T *dst = f_slot(i);
+        const bool pin = i >= 0 && i < n;
+        for (int idx = tid; idx < RS; idx += ZM_THREADS) {
+            const int ry = idx / RX, gj = r0 - 1 + ry, gk = c0 - 1 + (idx - ry * RX);
+            const bool ok = pin && gj >= 0 && gj < n && gk >= 0 && gk < n;
+            cp_async_zfill(dst + idx, ok ? fg + (int64_t)i * s0 + (int64_t)gj * n + gk : fg, ok);
+        }
+        if (tid < ZM_MPLANE / 4) cp_async16(m_slot(i) + 4 * tid, mg + (int64_t)(i - a + 1) * ZM_MPLANE + 4 * tid);
+    };
+    auto inside = [](const uint32_t *m, int ry, int rx) {
+        return (m[ry * ZM_MROW + (rx >> 5)] >> (rx & 31)) & 1u;
+    };
+
+    pdl_wait();   // u comes from the previous launch
+    // groups: {u a-2..a, f a-1}, then the groups of "steps" a-3 and a-2
+    load_u(a - 2);
+    load_u(a - 1);
+    load_u(a);
+    load_f(a - 1);
+    cp_async_commit();
+    load_u(a + 1);
+    load_f(a);
+    cp_async_commit();
+    if (a + 2 <= b + 1) load_u(a + 2);
+    if (a + 1 <= b) load_f(a + 1);
+    cp_async_commit();
+    cp_async_wait_but2();
+    __syncthreads();
+    for (int j = a - 1; j <= b; j++) {
+        if (j + 4 <= b + 1) load_u(j + 4);
+        if (j + 3 <= b) load_f(j + 3);
+        cp_async_commit();   // possibly empty: one group per step keeps the count
+        {   // red half-sweep on plane j, tile + 1-node halo
+            const T *um = u_slot(j - 1), *uc = u_slot(j), *up = u_slot(j + 1);
+            const T *fj = f_slot(j);
+            const uint32_t *mj = m_slot(j);
+            T *hj = h_slot(j);
+            for (int idx = tid; idx < RS; idx += ZM_THREADS) {
+                const int ry = idx / RX, rx = idx - ry * RX;
+                const int ui = (ry + 1) * UX + rx + 1;
+                T val = uc[ui];
+                if (inside(mj, ry, rx) && ((j + ry + rx) & 1) == 0) {   // r0, c0 even
+                    const T nb = (((uc[ui - 1] + uc[ui + 1]) + um[ui]) + up[ui]) + (uc[ui - UX] + uc[ui + UX]);
+                    val = (mul_rn(h2, fj[idx]) + nb) * sixth;
+                }
+                hj[idx] = val;
+            }
+        }
+        __syncthreads();
+        if (j - 1 >= a) {   // black half-sweep on plane j - 1, the tile; store the plane
+            const int i = j - 1;
+            const T *hm = h_slot(i - 1), *hc = h_slot(i), *hp = h_slot(i + 1);
+            const T *fi = f_slot(i);
+            const uint32_t *mi = m_slot(i);
+            for (int idx = tid; idx < ZM_TY * ZM_TX; idx += ZM_THREADS) {
+                const int oy = idx / ZM_TX, ox = idx - oy * ZM_TX;
+                const int gj = r0 + oy, gk = c0 + ox;
+                if (gj >= n || gk >= n) continue;
+                const int ri = (oy + 1) * RX + ox + 1;
+                T val = hc[ri];
+                if (inside(mi, oy + 1, ox + 1) && ((i + oy + ox) & 1) == 1) {
+                    const T nb = (((hc[ri - 1] + hc[ri + 1]) + hm[ri]) + hp[ri]) + (hc[ri - RX] + hc[ri + RX]);
+                    val = (mul_rn(h2, fi[ri]) + nb) * sixth;
+                }
+                out[(int64_t)i * s0 + (int64_t)gj * n + gk] = val;
+            }
+        }
+        cp_async_wait_but2();
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------- 3D boundary phase in one launch
+// Grid-wide barrier for k_boundary3d, whose CTAs are all resident at once
+// (the grid is sized by the kernel's occupancy and the launch does not
+// overlap another kernel of the stream).  bar[0] counts arrivals, bar[1] is
+// the generation.  A wait gives up after `spin` polls: it sets *err (reported
+// as GCMG_E_TIMEOUT) and returns, and once *err is set no later barrier
+// waits, so the launch always ends.  Writes before the barrier are visible
+// to every CTA after it (fences on both sides; u is read with L2-coherent
+// loads, see ldu).
+__device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned nbar, int *err, unsigned spin) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        volatile int *verr = err;
+        const unsigned g = atomicAdd(bar + 1, 0u);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nbar - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned it = 0;
+            while (*gen == g && !*verr) {
+                if (++it > spin) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// u is written by other CTAs between the phases of one launch: read it
+// through L2 (ld.global.cg), never from a possibly stale L1 line
+template <typename T>
+__device__ __forceinline__ T ldu(const T *p) { return __ldcg(p); }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_boundary3d(LevelView<T> v, BoundaryProgram3 P) {
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    T *__restrict__ u = v.u;
+    auto band = [&](const int32_t *__restrict__ list, int cnt) {   // Gauss-Seidel form of Eq. (jac2d), 7 points
+        for (int64_t i = t0; i < cnt; i += st) {
+            const int64_t p = list[i];
+            T nb = ldu(u + p - 1) + ldu(u + p + 1) + ldu(u + p - v.s0) + ldu(u + p + v.s0);
+            nb += ldu(u + p - v.s1) + ldu(u + p + v.s1);
+            u[p] = (mul_rn(v.h2, v.f[p]) + nb) * (T)(1.0 / 6.0);
+        }
+    };
+    auto ghost_new = [&](const int32_t *__restrict__ list, int cnt) {   // Eqs. (dir2d)/(neu2d), Jacobi
+        for (int64_t i = t0; i < cnt; i += st) {
+            const int q = list ? list[i] : (int)i;
+            T s = 0;
+#pragma unroll
+            for (int k = 0; k < 27; k++) s += v.gw[(int64_t)k * v.ng + q] * ldu(u + v.gstn[(int64_t)k * v.ng + q]);
+            v.gtmp[q] = ldu(u + v.gnode[q]) + v.gc[q] * (v.gg[q] - s);
+        }
+    };
+    auto ghost_store = [&](const int32_t *__restrict__ list, int cnt) {
+        for (int64_t i = t0; i < cnt; i += st) {
+            const int q = list ? list[i] : (int)i;
+            u[v.gnode[q]] = __ldcg(v.gtmp + q);
+        }
+    };
+    auto sync = [&]() { grid_barrier(P.bar, P.nbar, P.err, P.spin); };
+    pdl_wait();
+    bool first = true;
+    auto phase_sync = [&]() {   // a barrier before every phase but the first
+        if (!first) sync();
+        first = false;
+    };
+    if (P.lead) {
+        phase_sync(); ghost_new(nullptr, v.ng);
+        phase_sync(); ghost_store(nullptr, v.ng);
+    }
+    for (int k = 0; k < P.lambda; k++) {
+        phase_sync(); band(P.red, P.nred);
+        phase_sync(); band(P.black, P.nblack);
+        phase_sync(); ghost_new(nullptr, v.ng);
+        phase_sync(); ghost_store(nullptr, v.ng);
+    }
+    for (int k = 0; k < P.mu; k++) {
+        phase_sync(); band(P.zred, P.nzred);
+        phase_sync(); band(P.zblack, P.nzblack);
+        phase_sync(); ghost_new(P.zghost, P.nzghost);
+        phase_sync(); ghost_store(P.zghost, P.nzghost);
+    }
+}
+
 // Same update over a compact list of band nodes of one colour (Sec. 3.2).
 template <typename T, int D>
 __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
@@ -94,7 +383,7 @@ __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
     const int64_t p = list[i];
-    const T s = v.h2 * v.f[p] + neighbour_sum<T, D>(v.u, p, v.s0, v.s1);
+    const T s = mul_rn(v.h2, v.f[p]) + neighbour_sum<T, D>(v.u, p, v.s0, v.s1);   // h^2 f rounded on its own
     v.u[p] = s * (T)(1.0 / (2 * D));
 }
 
@@ -151,12 +440,25 @@ __global__ void __launch_bounds__(LOCAL_THREADS, sizeof(T) == 4 && D == 2 ? 2 : 
 }
 
 // ------------------------------------------------------------------ defect
+// |v| for a max-norm that keeps NaN visible (as +Inf; fmax would drop it)
+__device__ __forceinline__ double abs_keep_nan(double v) {
+    const double a = fabs(v);
+    return a != a ? __longlong_as_double(0x7ff0000000000000ll) : a;
+}
+
+// grid-stride over the level's nodes: a capped grid keeps the number of
+// atomic updates of the norm word small
 template <typename T, int D>
 __global__ void k_defect_interior(LevelView<T> v, bool zero_rest, unsigned long long *norm) {
     pdl_wait();
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const double val = p < v.nn ? defect_node<T, D>(v, p, zero_rest) : 0.0;
-    reduce_norm(norm, val);
+    if (zero_rest) v.chunks = nullptr;   // every node of r is written: the whole box
+    const int64_t nt = v.chunks ? v.nchunks * CHUNK : v.nn;
+    double m = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p;
+        if (level_node(v, t, p)) m = fmax(m, abs_keep_nan(defect_node<T, D>(v, p, zero_rest)));
+    }
+    reduce_norm(norm, m);
 }
 
 template <typename T, int K>
@@ -196,10 +498,16 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
     // FP32 instances let their dependents start now; FP64 ones do not (their
     // dependents are large FP64 launches whose early CTAs measured slower)
     if (sizeof(T) == 4) pdl_trigger();
-    if (D == 3 || sizeof(T) == 8) {
-        // the thread-per-index form: 3D ghost-transfer rows are long (tens
-        // to hundreds of terms), where it measured 8x faster than a warp a
-        // row; in FP64 the terms are plain reads of r
+    if (D == 3) {
+        // 3D: the coarse nodes only, a thread each (the coarse ghost rows are
+        // summed by k_ghost_rows)
+        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        pdl_wait();
+        if (i < C.nn) descend_node<T, D, FROM_R>(F, C, fc, uc, i);
+        return;
+    }
+    if (sizeof(T) == 8) {
+        // the thread-per-index form: in FP64 the terms are plain reads of r
         pdl_wait();
         descend_item<T, D, FROM_R>(F, C, fc, gc, uc, ptr, col, val, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
         return;
@@ -210,6 +518,36 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nw = 32 * (int64_t)C.ng;
     if (t < nw) descend_ghost_row_warp_early<T, D, FROM_R>(F, gc, ptr, col, val, (int)(t >> 5));   // uniform over the warp
     else if (t - nw < C.nn) descend_node_early<T, D, FROM_R>(F, C, fc, uc, t - nw);
+}
+
+// 3D descent, coarse ghost rows (extension + partial transfer at coarse ghost
+// q as one sparse row over the fine ghost defects): a warp per row, the lanes
+// over every 32nd term, then a butterfly sum.  The fine ghost defects come
+// from rg[column] (FP32: computed once by k_ghost_defects) or, with GATHER,
+// from rg[gnode[column]] (FP64: the defect grid).
+template <typename T, bool GATHER>
+__global__ void k_ghost_rows(const T *__restrict__ rg, const int32_t *__restrict__ gnode, T *__restrict__ gc,
+                             const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                             const T *__restrict__ val, int nrows) {
+    if (sizeof(T) == 4) pdl_trigger();
+    pdl_wait();
+    const int q = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (q >= nrows) return;   // uniform over the warp
+    T s = 0;
+    const int end = ptr[q + 1];
+    for (int j = ptr[q] + lane; j < end; j += 32) s = fma(val[j], rg[GATHER ? gnode[col[j]] : col[j]], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) gc[q] = s;
+}
+
+// g - L_G u at every ghost of a level into v.gtmp (free between
+// relaxations), for the 3D FP32 descent
+template <typename T, int K>
+__global__ void k_ghost_defects(LevelView<T> v) {
+    pdl_trigger();
+    pdl_wait();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < v.ng) v.gtmp[q] = ghost_defect<T, K>(v, q);
 }
 
 template <typename T, int D>
@@ -232,8 +570,12 @@ __global__ void k_ghost_transfer(const T *__restrict__ rf, const int32_t *__rest
 template <typename T, int D>
 __global__ void k_prolong(LevelView<T> F, LevelView<T> C, const T *__restrict__ e, T *__restrict__ out, bool add) {
     if (sizeof(T) == 4) pdl_trigger();
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p < F.nn) prolong_node_early<T, D>(F, C, e, out, add, p);   // waits after reading the types
+    if (!add) F.chunks = nullptr;   // every node of out is written: the whole box
+    int64_t p;
+    if (level_node(F, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, p))
+        prolong_node_early<T, D>(F, C, e, out, add, p);   // waits after reading the types
+    else
+        pdl_wait();
 }
 
 // --------------------------------------------------------------- coarsest
@@ -254,14 +596,17 @@ __global__ void k_defect_interior_mixed(LevelView<double> v, unsigned long long 
                                         float *__restrict__ e32) {
     pdl_trigger();
     pdl_wait();
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double val = 0.0;
-    if (p < v.nn) {
-        val = defect_node<double, D>(v, p, false);   // 0 off Omega_h
+    const int64_t nt = v.chunks ? v.nchunks * CHUNK : v.nn;
+    double m = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p;
+        if (!level_node(v, t, p)) continue;   // nodes off the chunks stay 0
+        const double val = defect_node<double, D>(v, p, false);   // 0 off Omega_h
         f32[p] = (float)val;
         e32[p] = 0.0f;
+        m = fmax(m, abs_keep_nan(val));
     }
-    reduce_norm(norm, val);
+    reduce_norm(norm, m);
 }
 
 // ... and its ghost rows: the ghost defects rounded to FP32
@@ -279,12 +624,12 @@ __global__ void k_defect_ghost_mixed(LevelView<double> v, unsigned long long *no
 }
 
 // u64 += e32 on Omega_h u Gamma_h
-__global__ void k_add_correction(const uint8_t *__restrict__ type, double *__restrict__ u64, const float *__restrict__ e32,
-                                 int64_t nn) {
+__global__ void k_add_correction(LevelView<double> v, double *__restrict__ u64, const float *__restrict__ e32) {
     pdl_trigger();
     pdl_wait();
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= nn) return;
+    const uint8_t *__restrict__ type = v.type;
+    int64_t p;
+    if (!level_node(v, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, p)) return;
     const uint8_t k = type[p] & NODE_KIND;
     if (k == NODE_IN || k == NODE_GHOST) u64[p] += (double)e32[p];
 }
@@ -307,6 +652,7 @@ void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s) {
     const int hc = (v.n + 1) / 2;
     g_launches++;
     if (dim == 2) pdl_launch(k_rb_interior<T, 2>, dim3(blocks_for((int64_t)v.n * hc)), dim3(kThreads), 0, s, v, color);
+    else if (v.chunks) pdl_launch(k_rb_interior<T, 3>, dim3(blocks_for(v.nchunks * CHUNK)), dim3(kThreads), 0, s, v, color);
     else pdl_launch(k_rb_interior<T, 3>, dim3(blocks_for((int64_t)v.n * v.n * hc)), dim3(kThreads), 0, s, v, color);
 }
 
@@ -389,6 +735,58 @@ void launch_rb_fused2d(const LevelView<T> &v, T *out, const int32_t *tiles, int 
     pdl_launch(k_rb_fused2d<T, TILE_R, TILE_C>, dim3(ntiles), dim3(256), 0, s, v, out, tiles);
 }
 
+void launch_mask_types(int dim, int n, double h, const double *origin, int step, int n_l, const double *B,
+                       const int32_t *gnode, int ng, const uint8_t *mask, uint8_t *types, cudaStream_t s) {
+    if (ng <= 0) return;
+    g_launches++;
+    k_mask_types<<<blocks_for(ng), kThreads, 0, s>>>(dim, n, h, origin[0], origin[1], origin[2], step, n_l, B, gnode,
+                                                     ng, mask, types);
+}
+
+template <typename T>
+bool launch_boundary3d(const LevelView<T> &v, BoundaryProgram3 P, int phantom, cudaStream_t s) {
+    // CTAs resident at once (per device; the first launch asks the runtime)
+    static int dev_seen = -1, resident = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (dev != dev_seen) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_boundary3d<T>, kThreads, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        resident = per_sm * sms;
+        dev_seen = dev;
+    }
+    if (resident <= 0) return false;
+    // enough CTAs for the largest phase at four entries a thread, at most
+    // one wave: fewer CTAs make each barrier cheaper
+    const int64_t work = std::max<int64_t>({(int64_t)v.ng, P.nred, P.nblack, P.nzred, P.nzblack, 1});
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, (work + 4 * kThreads - 1) /
+                                                                                       (4 * kThreads)));
+    P.nbar = nb + (unsigned)std::max(phantom, 0);
+    g_launches++;
+    // a plain launch: it starts after the previous kernel of the stream has
+    // finished and no CTA of another kernel of this stream runs beside it
+    k_boundary3d<T><<<nb, kThreads, 0, s>>>(v, P);
+    return true;
+}
+
+template <typename T>
+void launch_rb_zmarch(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s) {
+    if (g.nzm <= 0) return;
+    constexpr size_t smem = zmarch_smem_bytes<T>();
+    static bool opted = false;
+    if (!opted) {
+        cudaFuncSetAttribute(k_rb_zmarch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        opted = true;
+    }
+    g_launches++;
+    pdl_launch(k_rb_zmarch<T>, dim3((unsigned)g.nzm), dim3(ZM_THREADS), smem, s, v, out,
+               reinterpret_cast<const int2 *>(g.zm), (const int32_t *)g.zm_moff, (const uint32_t *)g.zm_mask);
+}
+
 template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s) {
     if (cnt <= 0) return;
@@ -418,8 +816,9 @@ void launch_ghost_relax_list(const LevelView<T> &v, int dim, const int32_t *list
 template <typename T>
 void launch_defect(const LevelView<T> &v, int dim, bool zero_rest, unsigned long long *norm, cudaStream_t s) {
     g_launches += v.ng > 0 ? 2 : 1;
-    if (dim == 2) pdl_launch(k_defect_interior<T, 2>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, zero_rest, norm);
-    else pdl_launch(k_defect_interior<T, 3>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, zero_rest, norm);
+    const unsigned nb = std::min(blocks_for(level_threads(v, !zero_rest)), kNormBlocks);
+    if (dim == 2) pdl_launch(k_defect_interior<T, 2>, dim3(nb), dim3(kThreads), 0, s, v, zero_rest, norm);
+    else pdl_launch(k_defect_interior<T, 3>, dim3(nb), dim3(kThreads), 0, s, v, zero_rest, norm);
     if (v.ng > 0) {
         if (dim == 2) pdl_launch(k_defect_ghost<T, 9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm);
         else pdl_launch(k_defect_ghost<T, 27>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm);
@@ -457,9 +856,21 @@ void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *f
 template <typename T>
 void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
                     T *uc, cudaStream_t s) {
-    const int64_t n = (gf.dim == 3 || sizeof(T) == 8) ? std::max<int64_t>(C.nn, C.ng) : C.nn + 32 * (int64_t)C.ng;
+    const bool warp_rows = sizeof(T) == 4 && gf.dim == 2;   // 2D FP32: a warp per coarse ghost row
+    const int64_t n = gf.dim == 3 ? C.nn : warp_rows ? C.nn + 32 * (int64_t)C.ng : std::max<int64_t>(C.nn, C.ng);
     constexpr bool from_r = sizeof(T) == 8;   // FP64: one defect pass first (see descend_item)
     if (from_r) launch_defect<T>(F, gf.dim, false, nullptr, s);
+    if (gf.dim == 3 && C.ng > 0) {
+        // 3D: the fine ghost defects once (FP32: into F.gtmp; FP64: the
+        // defect pass above), then the coarse ghost rows a warp each
+        if (!from_r && F.ng > 0) {
+            g_launches++;
+            pdl_launch(k_ghost_defects<T, 27>, dim3(blocks_for(F.ng)), dim3(kThreads), 0, s, F);
+        }
+        g_launches++;
+        pdl_launch(k_ghost_rows<T, from_r>, dim3(blocks_for(32 * (int64_t)C.ng)), dim3(kThreads), 0, s,
+                   (const T *)(from_r ? F.r : F.gtmp), F.gnode, gc, gf.gt_ptr, gf.gt_col, gt_val, C.ng);
+    }
     g_launches++;
     if (gf.dim == 2)
         pdl_launch(k_descend<T, 2, from_r>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
@@ -479,8 +890,9 @@ template <typename T>
 void launch_prolong(const LevelView<T> &F, const LevelView<T> &C, int dim, const T *e, T *out, bool add,
                     cudaStream_t s) {
     g_launches++;
-    if (dim == 2) pdl_launch(k_prolong<T, 2>, dim3(blocks_for(F.nn)), dim3(kThreads), 0, s, F, C, e, out, add);
-    else pdl_launch(k_prolong<T, 3>, dim3(blocks_for(F.nn)), dim3(kThreads), 0, s, F, C, e, out, add);
+    const int64_t nt = level_threads(F, add);
+    if (dim == 2) pdl_launch(k_prolong<T, 2>, dim3(blocks_for(nt)), dim3(kThreads), 0, s, F, C, e, out, add);
+    else pdl_launch(k_prolong<T, 3>, dim3(blocks_for(nt)), dim3(kThreads), 0, s, F, C, e, out, add);
 }
 
 template <typename T>
@@ -640,8 +1052,9 @@ void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s)
 void launch_defect_mixed(const LevelView<double> &v, int dim, unsigned long long *norm, float *f32, float *g32,
                          float *e32, cudaStream_t s) {
     g_launches += v.ng > 0 ? 2 : 1;
-    if (dim == 2) pdl_launch(k_defect_interior_mixed<2>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, norm, f32, e32);
-    else pdl_launch(k_defect_interior_mixed<3>, dim3(blocks_for(v.nn)), dim3(kThreads), 0, s, v, norm, f32, e32);
+    const unsigned nb = std::min(blocks_for(level_threads(v, true)), kNormBlocks);
+    if (dim == 2) pdl_launch(k_defect_interior_mixed<2>, dim3(nb), dim3(kThreads), 0, s, v, norm, f32, e32);
+    else pdl_launch(k_defect_interior_mixed<3>, dim3(nb), dim3(kThreads), 0, s, v, norm, f32, e32);
     if (v.ng > 0) {
         if (dim == 2) pdl_launch(k_defect_ghost_mixed<9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32);
         else pdl_launch(k_defect_ghost_mixed<27>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32);
@@ -650,7 +1063,13 @@ void launch_defect_mixed(const LevelView<double> &v, int dim, unsigned long long
 
 void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cudaStream_t s) {
     g_launches++;
-    pdl_launch(k_add_correction, dim3(blocks_for(g.nn)), dim3(kThreads), 0, s, g.type, u64, e32, g.nn);
+    LevelView<double> v{};
+    v.nn = g.nn;
+    v.type = g.type;
+    v.chunks = g.chunks;
+    v.clen = g.chunk_len;
+    v.nchunks = g.nchunks;
+    pdl_launch(k_add_correction, dim3(blocks_for(level_threads(v, true))), dim3(kThreads), 0, s, v, u64, e32);
 }
 
 #define GCMG_INSTANTIATE(T)                                                                              \
@@ -674,6 +1093,8 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_descend<T>(const LevelView<T> &, const LevelView<T> &, const DevGeom &, const T *, T *, T *, \
                                     T *, cudaStream_t);                                                            \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
+    template void launch_rb_zmarch<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);    \
+    template bool launch_boundary3d<T>(const LevelView<T> &, BoundaryProgram3, int, cudaStream_t);  \
     template size_t local_smem_bytes<T>(const LocalView<T> &, int, bool);                                 \
     template void launch_local<T>(const LocalView<T> &, int, int, int, cudaStream_t);               \
     template void launch_local_copyback<T>(const LocalView<T> &, cudaStream_t);                      \

@@ -64,6 +64,22 @@ void launch_junction_solve(const LevelView<T> &v, const DevGeom &g, const T *inv
                            const LocalView<T> *pending = nullptr);
 template <typename T>
 void launch_mask_unknowns(const uint8_t *type, T *u, int64_t nn, cudaStream_t s);
+// Boundary types of the ng ghosts of a level (step `step` = 2^l of the fine
+// grid, n_l nodes a side): the fine mask (n^dim bytes) at the fine node
+// nearest each ghost's B (B: ng * dim doubles), ties to the ghost's side
+void launch_mask_types(int dim, int n, double h, const double *origin, int step, int n_l, const double *B,
+                       const int32_t *gnode, int ng, const uint8_t *mask, uint8_t *types, cudaStream_t s);
+// 3D: the boundary phase of one relaxation (ghost sweep, band sweeps,
+// junction sweeps on global lists) as one launch with grid-wide barriers;
+// phantom > 0 makes every barrier wait for CTAs that do not exist (the
+// timeout test).  Returns false if the kernel cannot run here (then nothing
+// was launched).
+template <typename T>
+bool launch_boundary3d(const LevelView<T> &v, BoundaryProgram3 P, int phantom, cudaStream_t s);
+// 3D: one red-black sweep (both colours) over the level's fused-sweep items,
+// reading v.u and writing every node of the items into out
+template <typename T>
+void launch_rb_zmarch(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s);
 
 template <typename T>
 size_t local_smem_bytes(const LocalView<T> &J, int dim, bool pre = false);

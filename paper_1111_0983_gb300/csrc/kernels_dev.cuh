@@ -75,6 +75,22 @@ __device__ __forceinline__ void reduce_norm(unsigned long long *bits, double v) 
     }
 }
 
+// Node of thread t of a launch over a level: over its active chunks where
+// the level has them (3D; CHUNK = 32 threads a chunk), else over the whole
+// box.  False: the thread has no node.
+template <typename T>
+__device__ __forceinline__ bool level_node(const LevelView<T> &v, int64_t t, int64_t &p) {
+    if (v.chunks) {
+        const int64_t c = t >> 5;
+        if (c >= v.nchunks || (int)(t & 31) >= (v.clen[c] & 63)) return false;
+        p = (int64_t)v.chunks[c] + (t & 31);
+        return true;
+    }
+    if (t >= v.nn) return false;
+    p = t;
+    return true;
+}
+
 template <typename T, int D>
 __device__ __forceinline__ T neighbour_sum(const T *__restrict__ u, int64_t p, int64_t s0, int64_t s1) {
     T s = u[p - 1] + u[p + 1] + u[p - s0] + u[p + s0];
@@ -545,22 +561,22 @@ __device__ __forceinline__ double defect_ghost_item(const LevelView<T> &v, int q
 template <int D>
 __device__ __forceinline__ unsigned box_mask(int b) {
     // bit c of the 3^D neighbourhood (axis 0 slowest, offsets -1,0,1) inside box b;
-    // interval code per axis: 0 [-1,1], 1 [-1,0], 2 [0,1], 3 [0,0]
-    unsigned m = 0;
-    const int cube = D == 2 ? 9 : 27;
-    for (int c = 0; c < cube; c++) {
-        int rem = c, ok = 1;
-        for (int a = D - 1; a >= 0; a--) {
-            const int o = rem % 3 - 1;
-            rem /= 3;
-            const int iv = (b >> (2 * a)) & 3;
-            const int lo = (iv == 2 || iv == 3) ? 0 : -1;
-            const int hi = (iv == 1 || iv == 3) ? 0 : 1;
-            if (o < lo || o > hi) ok = 0;
-        }
-        if (ok) m |= 1u << c;
+    // interval code per axis: 0 [-1,1], 1 [-1,0], 2 [0,1], 3 [0,0].  The mask is
+    // the AND of one mask per axis: the offsets an interval holds (bits 0..2 of
+    // s = 7, 3, 6, 2) spread over the cells with that axis digit.
+    auto offs = [](int iv) { return iv == 0 ? 7u : iv == 1 ? 3u : iv == 2 ? 6u : 2u; };
+    auto triple = [](unsigned t, unsigned unit, int shift) {   // unit << (shift * digit) for each digit in t
+        return ((t & 1u) ? unit : 0u) | ((t & 2u) ? unit << shift : 0u) | ((t & 4u) ? unit << (2 * shift) : 0u);
+    };
+    if (D == 2) {
+        const unsigned m0 = triple(offs(b & 3), 0x7u, 3);              // axis 0: rows of 3 cells
+        const unsigned m1 = offs((b >> 2) & 3) * 0x49u;               // axis 1: every 3rd cell
+        return m0 & m1;
     }
-    return m;
+    const unsigned m0 = triple(offs(b & 3), 0x1FFu, 9);                // axis 0: planes of 9 cells
+    const unsigned m1 = triple(offs((b >> 2) & 3), 0x7u, 3) * 0x40201u; // axis 1: rows of 3 in each plane
+    const unsigned m2 = offs((b >> 4) & 3) * 0x1249249u;              // axis 2: every 3rd cell
+    return m0 & m1 & m2;
 }
 
 // 1D factor of the box weights (exact in any binary precision)
@@ -614,6 +630,7 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
     }
     const int nbox = D == 2 ? 16 : 64;
     int best = 0, count = 0;
+    unsigned long long bestset = 0;   // the boxes of the largest size inside the set
     if (member == full) {
         best = 1;  // full weighting fast path
     } else {
@@ -621,8 +638,8 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
             const unsigned m = box_mask<D>(b);
             if (m & ~member) continue;
             const int sz = __popc(m);
-            if (sz > best) { best = sz; count = 1; }
-            else if (sz == best) count++;
+            if (sz > best) { best = sz; count = 1; bestset = 1ull << b; }
+            else if (sz == best) { count++; bestset |= 1ull << b; }
         }
     }
     if (wait) pdl_wait();
@@ -645,9 +662,9 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
             w = 1;
             for (int a = 0; a < D; a++) w *= w1d<T>(0, o[a]);
         } else {
-            for (int b = 0; b < nbox; b++) {
-                const unsigned m = box_mask<D>(b);
-                if ((m & ~member) || __popc(m) != best) continue;
+            // the largest boxes in increasing order (as a scan of all boxes would)
+            for (unsigned long long bs = bestset; bs; bs &= bs - 1) {
+                const int b = __ffsll((long long)bs) - 1;
                 T wb = 1;
                 for (int a = 0; a < D; a++) wb *= w1d<T>((b >> (2 * a)) & 3, o[a]);
                 w += wb;

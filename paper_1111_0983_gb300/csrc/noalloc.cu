@@ -57,7 +57,8 @@ __device__ __forceinline__ double abs_or_inf(double r) {
 }
 
 // Items [0, nn) are grid nodes, [nn, nn + ng) ghosts.  Inside nodes:
-// r = f + Lap_h u; outside nodes: r = 0; ghosts: r = g - sum_k w_k u(stn_k).
+// r = f + Lap_h u; outside nodes: r = 0; ghosts: r = g - sum_k w_k u(stn_k)
+// over the 3^D slots a stencil can use (rows of kStencil slots).
 // Each block stores its maximum |r| in partials[blockIdx.x].
 template <int D>
 __global__ void __launch_bounds__(kThreads)
@@ -85,7 +86,9 @@ k_defect_partials(long long nn, long long ng, long long s0, long long s1, double
         } else if (i < nn + ng) {
             const long long q = i - nn;
             double s = 0.0;
-            for (int j = 0; j < kStencil; j++) s += w[q * kStencil + j] * u[stn[q * kStencil + j]];
+            constexpr int K = D == 2 ? 9 : 27;   // 2D stencils fill the first 9 slots of a row
+#pragma unroll
+            for (int j = 0; j < K; j++) s += w[q * kStencil + j] * u[stn[q * kStencil + j]];
             const double ri = g[q] - s;
             r[gnode[q]] = ri;
             m = fmax(m, abs_or_inf(ri));
@@ -112,9 +115,14 @@ extern "C" gcmg_status gcmg_defect_noalloc(int dim, int n, double h, const uint8
     if ((dim != 2 && dim != 3) || n < 3 || !(h > 0.0) || ng < 0 || !type_dev || !u_dev || !f_dev || !r_dev)
         return GCMG_E_ARG;
     if (ng > 0 && (!gnode_dev || !stn_dev || !w_dev || !g_dev)) return GCMG_E_ARG;
+    // capacity, checked without overflow: n^dim grows one factor at a time
+    if (n > kMaxItems || ng > kMaxItems) return GCMG_E_SIZE;
     long long nn = 1;
-    for (int a = 0; a < dim; a++) nn *= n;
-    if (nn + ng > kMaxItems) return GCMG_E_SIZE;
+    for (int a = 0; a < dim; a++) {
+        nn *= n;
+        if (nn > kMaxItems) return GCMG_E_SIZE;
+    }
+    if (ng > kMaxItems - nn) return GCMG_E_SIZE;
     // one-time set-up per device: the device address of the scratch array
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GCMG_E_CUDA;

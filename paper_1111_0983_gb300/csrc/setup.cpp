@@ -182,7 +182,7 @@ void ghost_equation(HostLevel &L, int64_t q) {
         off[a] = -ph * g[a] / gg;
         const double sg = -ph * g[a];
         sgn[a] = sg > 0.0 ? 1 : (sg < 0.0 ? -1 : 0);
-        L.B[q * d + a] = (-1.0 + jg[a] * L.h) + off[a];
+        L.B[q * d + a] = (L.origin[a] + jg[a] * L.h) + off[a];
         if (sgn[a] == 0) zero_axes.push_back(a);
     }
     const int nz = (int)zero_axes.size();
@@ -818,8 +818,72 @@ static void build_ghost_transfer(HostLevel &F, const HostLevel &C) {
     }
 }
 
+// Work items of the 3D fused sweep: for each ZM_TY x ZM_TX tile of the
+// (axis 1, axis 2) plane, the runs of planes (axis 0) in which the tile holds
+// an inside node or a ghost (runs closer than 3 planes merged), cut into
+// pieces of at most ZM_SEG planes.  Items never overlap, so every unknown is
+// written by exactly one CTA.
+static void build_zmarch_items(HostLevel &L) {
+    const int n = L.n, ty = (n + ZM_TY - 1) / ZM_TY, tx = (n + ZM_TX - 1) / ZM_TX;
+    std::vector<uint8_t> act((size_t)ty * tx * n, 0);
+    for (int64_t p = 0; p < L.nn; p++) {
+        const uint8_t k = L.type[p] & NODE_KIND;
+        if (k != NODE_IN && k != NODE_GHOST) continue;
+        const int64_t i = p / ((int64_t)n * n), j = (p / n) % n, c = p % n;
+        act[((size_t)(j / ZM_TY) * tx + c / ZM_TX) * n + i] = 1;
+    }
+    L.zm.clear();
+    for (int t = 0; t < ty * tx; t++) {
+        const uint8_t *a = &act[(size_t)t * n];
+        int i = 0;
+        while (i < n) {
+            if (!a[i]) { i++; continue; }
+            int end = i + 1;   // [i, end): a run, gaps of up to 2 idle planes merged
+            for (int k = end; k < n; k++) {
+                if (a[k]) end = k + 1;
+                else if (k - end >= 2) break;
+            }
+            for (int s0 = i; s0 < end; s0 += ZM_SEG) {
+                L.zm.push_back(((t / tx) << 16) | (t % tx));
+                L.zm.push_back((s0 << 16) | std::min(end, s0 + ZM_SEG));
+            }
+            i = end;
+        }
+    }
+    // inside-node masks of every item's planes first - 1 .. end (the tile
+    // with a 1-node halo; nodes outside the box are not inside)
+    L.zm_moff.clear();
+    L.zm_mask.clear();
+    int64_t planes = 0;
+    for (size_t k = 0; k < L.zm.size(); k += 2) {
+        L.zm_moff.push_back((int32_t)planes);
+        const int a = L.zm[k + 1] >> 16, b = L.zm[k + 1] & 0xffff;
+        planes += b - a + 2;
+    }
+    L.zm_mask.assign((size_t)planes * ZM_MPLANE, 0u);
+    for (size_t k = 0; k < L.zm.size(); k += 2) {
+        const int r0 = (L.zm[k] >> 16) * ZM_TY, c0 = (L.zm[k] & 0xffff) * ZM_TX;
+        const int a = L.zm[k + 1] >> 16, b = L.zm[k + 1] & 0xffff;
+        uint32_t *m = &L.zm_mask[(size_t)L.zm_moff[k / 2] * ZM_MPLANE];
+        for (int i = a - 1; i <= b; i++, m += ZM_MPLANE) {
+            if (i < 0 || i >= n) continue;
+            for (int ry = 0; ry < ZM_TY + 2; ry++) {
+                const int gj = r0 - 1 + ry;
+                if (gj < 0 || gj >= n) continue;
+                for (int rx = 0; rx < ZM_TX + 2; rx++) {
+                    const int gk = c0 - 1 + rx;
+                    if (gk < 0 || gk >= n) continue;
+                    if ((L.type[((int64_t)i * n + gj) * n + gk] & NODE_KIND) == NODE_IN)
+                        m[ry * ZM_MROW + (rx >> 5)] |= 1u << (rx & 31);
+                }
+            }
+        }
+    }
+}
+
 void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
-                     std::vector<HostLevel> &levels) {
+                     std::vector<HostLevel> &levels, double h0, const double *origin) {
+    if (!(h0 > 0.0)) h0 = 2.0 / (n - 1);
     levels.clear();
     int nl = 1;
     for (int m = n; m > n_coarse; m = (m - 1) / 2 + 1) nl++;
@@ -827,7 +891,8 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
         HostLevel L;
         L.dim = dim;
         L.n = (n - 1) / (1 << l) + 1;
-        L.h = 2.0 / (L.n - 1);
+        L.h = h0 * (double)(1 << l);
+        for (int a = 0; a < 3; a++) L.origin[a] = origin ? origin[a] : -1.0;
         L.nn = 1;
         for (int a = 0; a < dim; a++) L.nn *= L.n;
         L.stride[dim - 1] = 1;
@@ -864,6 +929,23 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
             for (int a = 0; a < tr; a++)
                 for (int b = 0; b < tc; b++)
                     if (active[(size_t)a * tc + b]) L.tiles.push_back((a << 16) | b);
+        } else if (L.nn < ((int64_t)1 << 31)) {
+            build_zmarch_items(L);
+            // active chunks: CHUNK-node runs of a row holding an inside node or a ghost
+            for (int64_t row = 0; row < L.nn; row += L.n)
+                for (int z0 = 0; z0 < L.n; z0 += CHUNK) {
+                    const int len = std::min(CHUNK, L.n - z0);
+                    bool act = false;
+                    for (int z = z0; z < z0 + len && !act; z++) {
+                        const uint8_t k = L.type[row + z] & NODE_KIND;
+                        act = k == NODE_IN || k == NODE_GHOST;
+                    }
+                    if (act) {   // bit 7: parity of the row's (i0 + i1), for the colour of a node
+                        const int64_t r = row / L.n, i0 = r / L.n, i1 = r % L.n;
+                        L.chunk.push_back((int32_t)(row + z0));
+                        L.chunk_len.push_back((uint8_t)(len | (((i0 + i1) & 1) << 7)));
+                    }
+                }
         }
         levels.push_back(std::move(L));
     }

@@ -26,17 +26,23 @@ class Params(C.Structure):
                 ("lam", C.c_int), ("gamma", C.c_int), ("delta_over_h", C.c_double), ("c_dirichlet", C.c_double),
                 ("c_neumann_factor", C.c_double), ("precision", C.c_int), ("max_cycles", C.c_int),
                 ("rtol", C.c_double), ("junction_sweeps", C.c_int), ("junction_radius", C.c_double),
-                ("junction_solve", C.c_int), ("fused_coarse_n", C.c_int), ("smoother", C.c_int)]
+                ("junction_solve", C.c_int), ("fused_coarse_n", C.c_int), ("smoother", C.c_int),
+                ("h", C.c_double), ("origin", C.c_double * 3), ("diverge_cycles", C.c_int)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int64 * 3), ("h", C.c_double), ("origin", C.c_double * 3)]
 
 
 class Stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
-                ("r0_norm", C.c_double), ("rel", C.c_double * 257)]
+                ("r0_norm", C.c_double), ("rel", C.c_double * 257), ("diverged", C.c_int)]
 
     def to_dict(self):
         m = self.cycles
         return dict(cycles=m, converged=bool(self.converged), rel_residual=self.rel_residual,
-                    r0_norm=self.r0_norm, rel=np.array(self.rel[: min(m, 256) + 1]))
+                    r0_norm=self.r0_norm, rel=np.array(self.rel[: min(m, 256) + 1]),
+                    diverged=bool(self.diverged))
 
 
 class GcmgError(RuntimeError):
@@ -59,6 +65,11 @@ def lib():
         sig = {
             "gcmg_default_params": (st, [C.POINTER(Params), i32, i32, i32]),
             "gcmg_create": (st, [C.POINTER(Params), vp, vp, C.POINTER(vp)]),
+            "gcmg_create_grid": (st, [C.POINTER(Grid), vp, C.POINTER(Params), vp, C.POINTER(vp)]),
+            "gcmg_set_bc_types_from_mask": (st, [vp, vp]),
+            "gcmg_bc_types": (st, [vp, i32, vp]),
+            "gcmg_debug_barrier": (st, [vp, i32, i32, C.c_uint]),
+            "gcmg_residual": (st, [vp, vp, vp, C.POINTER(dbl)]),
             "gcmg_destroy": (None, [vp]),
             "gcmg_last_error": (C.c_char_p, [vp]),
             "gcmg_num_levels": (i32, [vp]),
@@ -138,7 +149,8 @@ class Solver:
         self._borrowed = True
         return self
 
-    def __init__(self, phi, n_coarse, stream=None, **params):
+    def __init__(self, phi, n_coarse, stream=None, grid=None, **params):
+        """grid: optional (h, origin) of the nodes (default: the box [-1,1]^d)."""
         import torch
         phi_t = phi if isinstance(phi, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(phi))
         phi_t = phi_t.to(device="cuda", dtype=torch.float64).contiguous()
@@ -147,8 +159,17 @@ class Solver:
         self.params = default_params(self.dim, self.n, n_coarse, **params)
         self.stream = stream
         h = C.c_void_p()
-        s = lib().gcmg_create(C.byref(self.params), _ptr(phi_t), C.c_void_p(stream.cuda_stream) if stream else None,
-                              C.byref(h))
+        sp = C.c_void_p(stream.cuda_stream) if stream else None
+        if grid is None:
+            s = lib().gcmg_create(C.byref(self.params), _ptr(phi_t), sp, C.byref(h))
+        else:
+            g = Grid()
+            g.dim = self.dim
+            for a in range(3):
+                g.n[a] = self.n if a < self.dim else 1
+                g.origin[a] = grid[1][a] if a < self.dim else -1.0
+            g.h = grid[0]
+            s = lib().gcmg_create_grid(C.byref(g), _ptr(phi_t), C.byref(self.params), sp, C.byref(h))
         self._h = h
         if s != GCMG_OK:
             msg = lib().gcmg_last_error(h).decode() if h.value else ""
@@ -224,8 +245,30 @@ class Solver:
         assert t.shape == (self.num_ghosts(l),)
         self._check(lib().gcmg_set_bc_types(self._h, l, _ptr(t)))
 
+    def debug_barrier(self, enable=True, phantom_blocks=0, spin_limit=1 << 22):
+        """3D boundary relaxation: one launch with barriers (enable) or one
+        launch per phase; phantom_blocks > 0 makes its barrier waits run out."""
+        self._check(lib().gcmg_debug_barrier(self._h, int(bool(enable)), int(phantom_blocks), int(spin_limit)))
+
+    def bc_types(self, l):
+        out = np.empty(self.num_ghosts(l), np.uint8)
+        self._check(lib().gcmg_bc_types(self._h, l, _ptr(out)))
+        return out
+
+    def set_bc_types_from_mask(self, mask):
+        """Boundary types of every level from a Dirichlet(0)/Neumann(1) mask on
+        the fine grid (device uint8 tensor, n^d)."""
+        assert mask.dtype.itemsize == 1 and mask.is_cuda and mask.numel() == self.n ** self.dim
+        self._check(lib().gcmg_set_bc_types_from_mask(self._h, _ptr(mask.contiguous())))
+
     def set_rhs(self, f, g):
         self._check(lib().gcmg_set_rhs(self._h, _ptr(f), _ptr(g)))
+
+    def residual(self, u, r):
+        """FP64 defect of u (device tensor) into r; returns ||r|| / ||(f, g)||."""
+        rel = C.c_double()
+        self._check(lib().gcmg_residual(self._h, _ptr(u), _ptr(r), C.byref(rel)))
+        return rel.value
 
     def set_rhs_level(self, l, f, g):
         """f and g of level l (device tensors), for fmg (plain FP64 solvers)."""

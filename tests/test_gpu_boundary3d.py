@@ -1,0 +1,74 @@
+"""The 3D boundary relaxation as one launch (the ghost sweep, the lambda band
+sweeps of Sec. 3.2 and the junction sweeps, with grid-wide barriers between
+the phases) against the same phases launched one by one, and its bounded
+barrier waits: made to run out from the host, the solve reports
+GCMG_E_TIMEOUT and the context stays usable."""
+import numpy as np
+import pytest
+
+from paper_1111_0983_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _solver(precision, n=65, **kw):
+    from paper_1111_0983_gb300 import gcmg
+    P = inputs.torus()
+    S = gcmg.Solver(P.phi_grid(n), 17, precision=precision, rtol=1e-11, max_cycles=100, **kw)
+    for l in range(S.nlev):
+        S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
+    G = S.ghosts(0)
+    g = P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))
+    S.set_rhs(torch.from_numpy(P.f_grid(n)).cuda(), torch.from_numpy(g).cuda())
+    return S
+
+
+@pytest.mark.parametrize("precision,n", [(0, 65), (1, 65), (1, 129)])
+def test_one_launch_equals_one_launch_per_phase(precision, n):
+    """Same arithmetic in the same order: bitwise equal solutions and
+    per-cycle residuals, with and without the junction sweeps of the zone
+    that does not fit in shared memory."""
+    S = _solver(precision, n)
+    S.debug_barrier(enable=True)
+    u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
+    st1 = S.solve(u1)
+    S.debug_barrier(enable=False)
+    u2 = torch.zeros_like(u1)
+    st2 = S.solve(u2)
+    assert st1["converged"] and st2["converged"]
+    assert torch.equal(u1, u2)
+    np.testing.assert_array_equal(st1["rel"], st2["rel"])
+    # the single relaxation of the step API takes the same path
+    S.debug_barrier(enable=True)
+    P = inputs.torus()
+    rng = np.random.default_rng(5)
+    T = torch.from_numpy(S.node_types(0) & 3 > 0).cuda()
+    u = torch.from_numpy(rng.standard_normal((n,) * 3)).cuda() * T
+    f = torch.from_numpy(P.f_grid(n)).cuda()
+    G = S.ghosts(0)
+    g = torch.from_numpy(P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))).cuda()
+    a = u.clone()
+    S.relax(0, a, f, g)
+    S.debug_barrier(enable=False)
+    b = u.clone()
+    S.relax(0, b, f, g)
+    assert torch.equal(a, b)
+
+
+def test_barrier_wait_runs_out_and_context_stays_usable():
+    from paper_1111_0983_gb300 import gcmg
+    S = _solver(1)
+    u = torch.zeros((65,) * 3, dtype=torch.float64, device="cuda")
+    S.debug_barrier(enable=True, phantom_blocks=1, spin_limit=2000)
+    with pytest.raises(gcmg.GcmgError) as e:
+        S.solve(u)
+    assert e.value.status == gcmg.GCMG_E_TIMEOUT
+    S.debug_barrier(enable=True)
+    u.zero_()
+    st = S.solve(u)
+    assert st["converged"]
+    S2 = _solver(1)                  # default: one launch per phase
+    u2 = torch.zeros_like(u)
+    S2.solve(u2)
+    assert torch.equal(u, u2)

@@ -576,3 +576,17 @@ def test_kaczmarz_comparison_falls_slower_than_the_paper_relaxation():
             rho[sm, lam] = (norms[-1] / norms[0]) ** (1.0 / k)
     assert rho[1, 5] < rho[1, 3] < 1.0
     assert rho[0, 3] < rho[1, 3] and rho[0, 5] < rho[1, 5]
+
+
+# ---------------------------------------------------------------- threads
+@pytest.mark.parametrize("P,n,nc", [(inputs.flower(), 129, 33), (inputs.torus(), 33, 17)])
+def test_thread_count_does_not_change_results(P, n, nc):
+    """The oracle's OpenMP loops are order-independent: a solve with one
+    thread and with several gives bitwise the same iterates and norms."""
+    out = []
+    for k in (1, 4):
+        oracle.set_threads(k)
+        u, norms, ok = oracle_for(P, n, nc).solve(rtol=1e-12, max_cycles=12)
+        out.append((u, norms))
+    oracle.set_threads(1)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
