@@ -515,7 +515,7 @@ def secondary(name, rtol, precision, args, stream, flush):
                 alg = kbytes / kl if kbytes > 0 else (24 if prec == 0 else 12) * n_in
                 gbs = alg / (kms / kl / 1e3) / 1e9
                 peak = measured_peaks()[0].get("hbm_gbs")
-                kernel = ("k_rb_zmarch (red + black 7-point sweep, one pass)" if P.dim == 3 else
+                kernel = ("k_rb_stream3d (red + black 7-point sweep, one pass)" if P.dim == 3 else
                           "k_rb_fused2d" if prec == 0 or kbytes <= 0 else
                           "k_relax2d (interior sweep + ghost and band sweeps)")
                 rec["fine_sweep"] = {"kernel": kernel, "alg_bytes_per_launch": alg,
@@ -726,11 +726,12 @@ def run_gcmg(args):
     avg_ms = k_ms / max(k_launches, 1)
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if k_launches else None
     merged = P.dim == 2 and precision == 1 and b_launches > 0
-    kern = ("relax2d" if merged else "fused2d") if P.dim == 2 else "zmarch"
+    kern = ("relax2d" if merged else "fused2d") if P.dim == 2 else "zmarch"   # 3D: k_rb_stream3d
     kname = f"rb_{kern}_{'f64' if precision == 0 else 'f32'}_{args.config}"
     kdesc = {"relax2d": "k_relax2d (fine level: interior sweep + ghost and band sweeps in one launch)",
              "fused2d": "k_rb_fused2d (fine level, red + black sweep)",
-             "zmarch": "k_rb_zmarch (fine level: red + black 7-point sweep in one pass, z-marching tiles)"}[kern]
+             "zmarch": "k_rb_stream3d (fine level: red + black 7-point sweep in one pass, tiles marching along "
+                       "axis 0 with the planes in registers)"}[kern]
     sweep = {"bound": "hbm", "kernel": kdesc, "achieved": achieved,
              "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
              "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),

@@ -317,15 +317,30 @@ gcmg_status gcmg_kernel_timing(gcmg_ctx *ctx, int64_t *launches, double *total_m
  * sweep's u and f read and u written once per inside node. */
 gcmg_status gcmg_kernel_timing_ex(gcmg_ctx *ctx, int64_t *launches, double *total_ms, double *alg_bytes);
 
-/* The 3D boundary relaxation (ghost sweep, lambda band sweeps and the
- * junction sweeps, Sec. 3.2) runs by default as one launch per phase;
- * enable = 1 runs it as one launch whose phases are separated by grid-wide
- * barriers (same results; measured slower on GB300).  Each barrier wait
- * gives up after spin_limit polls (default 4,194,304, about a second) and
- * the solve then returns GCMG_E_TIMEOUT with the context still usable;
+/* How the 3D boundary relaxation (the ghost sweep, the lambda band sweeps
+ * of Sec. 3.2 and the junction sweeps) is launched; every mode gives the same
+ * results bitwise.  mode 0 (default): one launch per phase; 1: on levels
+ * whose ghost and band lists hold at most 65,536 entries all phases as one
+ * thread-block cluster of 16 CTAs with hardware barriers between them, on
+ * larger levels one launch per phase with the junction sweeps as one
+ * cluster; 2: all phases as one grid with software barriers.  Modes 1 and 2
+ * measured slower on GB300 (the per-phase launches overlap inside the solve's
+ * graph and spread each phase's gathers over every SM).  Not in the paper. */
+gcmg_status gcmg_set_boundary3d(gcmg_ctx *ctx, int mode);
+
+/* Mode 2 of gcmg_set_boundary3d with test controls: every software barrier
+ * wait gives up after spin_limit polls (default 4,194,304, about a second)
+ * and the solve then returns GCMG_E_TIMEOUT with the context still usable;
  * phantom_blocks > 0 makes every barrier wait for that many CTAs that do not
- * exist, so that a test can make the waits run out.  Not in the paper. */
+ * exist, so that a test can make the waits run out.  enable = 0 returns to
+ * mode 0.  Not in the paper. */
 gcmg_status gcmg_debug_barrier(gcmg_ctx *ctx, int enable, int phantom_blocks, unsigned spin_limit);
+
+/* Kernel of the 3D interior sweep (red and black in one pass over the active
+ * tiles, Eq. jac2d): 0 tiles of 16 x 64 nodes with the planes staged in
+ * shared memory; 1 (default) tiles of 12 x 28 nodes with the planes in
+ * registers, a warp a row.  Same results bitwise.  Not in the paper. */
+gcmg_status gcmg_set_sweep3d(gcmg_ctx *ctx, int variant);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t gcmg_launch_counter(void);

@@ -42,6 +42,11 @@ T *upload(gcmg_ctx *c, const T *host, size_t count) {
 
 int kslots(int dim) { return dim == 2 ? 9 : 27; }
 
+// 3D levels whose ghost and band lists hold at most this many entries run a
+// relaxation's boundary phases as one thread-block cluster (16 CTAs of 1024
+// threads: four entries a thread a phase)
+constexpr int64_t kClusterWork = 65536;
+
 // Rows of the Kaczmarz comparison smoother on level l (2D): the ghosts and the
 // inside nodes of the band, grouped by the colour (i mod 5) + 5 (j mod 5) of
 // their node, increasing node index within a colour
@@ -159,6 +164,10 @@ void upload_geometry(gcmg_ctx *c, int l) {
         g.zm = upload<int32_t>(c, L.zm.data(), L.zm.size());
         g.zm_moff = upload<int32_t>(c, L.zm_moff.data(), L.zm_moff.size());
         g.zm_mask = upload<uint32_t>(c, L.zm_mask.data(), L.zm_mask.size());
+    }
+    if (!L.sr.empty()) {
+        g.nsr = (int)(L.sr.size() / 2);
+        g.sr = upload<int32_t>(c, L.sr.data(), L.sr.size());
     }
     if (!L.chunk.empty()) {
         g.nchunks = (int64_t)L.chunk.size();
@@ -352,7 +361,8 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         // 3D: both colours in one pass over the active tiles (reads v.u, writes out)
         const double bytes = c->timing_kind >= 0 ? 3.0 * (double)c->H[l].n_in * sizeof(T) : 0.0;
         timer_mark(c, GCMG_KERNEL_SMOOTH, l, bytes);
-        launch_rb_zmarch<T>(v, out, g, c->stream);
+        if (c->sweep3d == 1 && g.nsr > 0) launch_rb_stream3d<T>(v, out, g, c->stream);
+        else launch_rb_zmarch<T>(v, out, g, c->stream);
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
         v.u = out;
     } else {
@@ -373,18 +383,22 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         if (bzv.wb) pending = &bzv;
     } else {
-        // 3D: the ghost sweep, the band sweeps and (on global lists) the
-        // junction sweeps as one launch with grid-wide barriers
-        bool done = false, zdone = false;
-        if (dim == 3 && c->coop3d && c->p.smoother == 0 && g.ng > 0) {
-            BoundaryProgram3 P;
+        // 3D: one launch a phase (default); gcmg_set_boundary3d 1: the ghost
+        // sweep, the band sweeps and (on global lists) the junction sweeps of
+        // small levels as one thread-block cluster with hardware barriers
+        // between the phases, on large levels the junction sweeps alone as
+        // one cluster; 2: all phases as one grid with software barriers
+        bool done = false, zdone = false, zcluster = false;
+        BoundaryProgram3 P;
+        if (dim == 3 && c->p.smoother == 0 && g.ng > 0) {
             P.red = g.red;
             P.nred = g.nred;
             P.black = g.black;
             P.nblack = g.nblack;
             P.lambda = extra ? c->p.lambda : 0;
-            zdone = extra && !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 && !g.jz.in_smem;
-            if (zdone) {
+            const bool jglob =
+                extra && !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 && !g.jz.in_smem;
+            if (jglob) {
                 P.zred = g.jz.zred;
                 P.nzred = g.jz.nzred;
                 P.zblack = g.jz.zblack;
@@ -397,9 +411,19 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
             P.err = c->d_err;
             P.spin = c->bar_spin;
             timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
-            done = launch_boundary3d<T>(v, P, c->bar_phantom, c->stream);
-            timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
-            if (!done) zdone = false;
+            if (c->coop3d) {
+                done = launch_boundary3d<T>(v, P, c->bar_phantom, c->stream);
+                zdone = done && jglob;
+            } else if (c->cluster3d) {
+                const int64_t big = std::max<int64_t>({(int64_t)g.ng, g.nred, g.nblack});
+                if (big <= kClusterWork) {
+                    done = launch_boundary3d_cluster<T>(v, P, c->stream);
+                    zdone = done && jglob;
+                } else {
+                    zcluster = jglob;
+                }
+            }
+            if (done) timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         }
         if (!done) {
             launch_ghost_relax<T>(v, dim, c->stream);
@@ -409,6 +433,13 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
                     launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
                     launch_ghost_relax<T>(v, dim, c->stream);
                 }
+            if (zcluster) {   // the junction-zone sweeps alone, as one cluster
+                BoundaryProgram3 Z = P;
+                Z.lead = 0;
+                Z.lambda = 0;
+                zdone = launch_boundary3d_cluster<T>(v, Z, c->stream);
+            }
+            if (dim == 3 && c->p.smoother == 0 && g.ng > 0) timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         }
         if (!extra || zdone) return v.u;
     }
@@ -1076,8 +1107,24 @@ gcmg_status gcmg_debug_barrier(gcmg_ctx *c, int enable, int phantom_blocks, unsi
     if (!c || phantom_blocks < 0 || spin_limit == 0) return fail(c, GCMG_E_ARG, "bad argument");
     destroy_graph(c);   // a captured graph holds the old launch parameters
     c->coop3d = enable ? 1 : 0;
+    c->cluster3d = 0;
     c->bar_phantom = phantom_blocks;
     c->bar_spin = spin_limit;
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_set_boundary3d(gcmg_ctx *c, int mode) {
+    if (!c || mode < 0 || mode > 2) return fail(c, GCMG_E_ARG, "bad argument");
+    destroy_graph(c);
+    c->cluster3d = mode == 1 ? 1 : 0;
+    c->coop3d = mode == 2 ? 1 : 0;
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_set_sweep3d(gcmg_ctx *c, int variant) {
+    if (!c || variant < 0 || variant > 1) return fail(c, GCMG_E_ARG, "bad argument");
+    destroy_graph(c);
+    c->sweep3d = variant;
     return GCMG_OK;
 }
 

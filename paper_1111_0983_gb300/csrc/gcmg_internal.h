@@ -21,6 +21,10 @@ constexpr int CHUNK = 32;  // 3D active chunks: nodes along the contiguous axis 
 // 3D fused sweep (k_rb_zmarch): a CTA owns ZM_TY rows (axis 1) x ZM_TX columns
 // (axis 2, contiguous) and marches along axis 0 over at most ZM_SEG planes
 constexpr int ZM_TY = 16, ZM_TX = 64, ZM_SEG = 32;
+// 3D register-streaming sweep (k_rb_stream3d): a CTA owns SR_TY rows x SR_W
+// columns, one warp per row (2 halo rows each side), one lane per column (2
+// halo lanes each side), and marches along axis 0 over at most ZM_SEG planes
+constexpr int SR_TY = 12, SR_W = 28;
 // its inside-node masks: per plane (ZM_TY + 2) rows of ZM_TX + 2 bits (the
 // tile and a 1-node halo), ZM_MROW words a row, planes padded to 16 bytes
 constexpr int ZM_MROW = (ZM_TX + 2 + 31) / 32;
@@ -88,6 +92,8 @@ struct HostLevel {
     // for planes first - 1 .. end, in zm_mask
     std::vector<int32_t> zm_moff;
     std::vector<uint32_t> zm_mask;
+    // the same pairs for the SR_TY x SR_W tiles of the register-streaming sweep
+    std::vector<int32_t> sr;
     // defect extension of this level (before restricting to the next coarser one)
     std::vector<int32_t> ext_node;      // ordered by upwind wavefront
     std::vector<uint8_t> ext_cnt;
@@ -182,6 +188,8 @@ struct DevGeom {
     int32_t *zm = nullptr;
     int32_t *zm_moff = nullptr;  // and their inside-node masks
     uint32_t *zm_mask = nullptr;
+    int nsr = 0;                 // register-streaming sweep items (HostLevel::sr pairs)
+    int32_t *sr = nullptr;
     int64_t nchunks = 0;         // 3D active chunks (HostLevel::chunk)
     int32_t *chunks = nullptr;
     uint8_t *chunk_len = nullptr;

@@ -283,6 +283,108 @@ __global__ void __launch_bounds__(ZM_THREADS, sizeof(T) == 4 ? 3 : 1)
     }
 }
 
+// ------------------------------------- 3D fused red-black sweep in registers
+// The same sweep as k_rb_zmarch with the planes in registers: a CTA of
+// SR_TY + 4 warps owns SR_TY rows (axis 1) x SR_W columns (axis 2); warp w
+// holds row r0 - 2 + w, lane l column k0 - 2 + l, and every lane keeps the
+// old values of planes j-1, j, j+1 and the half-swept values of planes j-2,
+// j-1 of its node while the CTA marches along axis 0.  At step j a lane
+// computes the red half-sweep of its node in plane j (rows 1..SR_TY+2,
+// lanes 1..30: the tile and a 1-node halo) and the black half-sweep of its
+// node in plane j-1 (which needs only plane j's own half-swept value and
+// plane j-1's, known from the step before), and stores plane j-1 on the
+// tile.  Neighbours along axis 2 come from the adjacent lanes (shuffles),
+// along axis 1 from the adjacent warps through shared memory (two rows a
+// warp, double buffered: one block barrier a plane).  u, f and node types
+// are loaded three planes ahead into registers that are read only when
+// their plane comes up (the step is unrolled three times, so no register
+// copy waits on a load in flight).  Same sums in the same order as
+// k_rb_zmarch: the results are bitwise equal.
+template <typename T>
+__global__ void __launch_bounds__((SR_TY + 4) * 32, sizeof(T) == 4 ? 3 : 2)
+    k_rb_stream3d(LevelView<T> v, T *__restrict__ out, const int2 *__restrict__ items) {
+    constexpr int NW = SR_TY + 4;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ T sx[2][2][NW][32];   // [step parity][old u of plane j, half-swept plane j-1][warp][lane]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 item = items[blockIdx.x];
+    const int r0 = (item.x >> 16) * SR_TY, k0 = (item.x & 0xffff) * SR_W;
+    const int a = item.y >> 16, b = item.y & 0xffff;
+    const int n = v.n;
+    const int row = r0 - 2 + w, col = k0 - 2 + lane;
+    const bool ok = row >= 0 && row < n && col >= 0 && col < n;
+    const int64_t off = ok ? (int64_t)row * n + col : 0;
+    const int64_t s0 = v.s0;
+    const bool red_here = w >= 1 && w <= NW - 2 && lane >= 1 && lane <= 30;
+    const bool owner = ok && w >= 2 && w <= NW - 3 && lane >= 2 && lane <= SR_W + 1;
+    const int par = (row + col) & 1;   // the node is red in plane i when i + par is even
+    const T h2 = v.h2, sixth = (T)(1.0 / 6.0);
+    const T *__restrict__ ug = v.u;
+    const T *__restrict__ fg = v.f;
+    const uint8_t *__restrict__ tg = v.type;
+    // unconditional loads from a clamped address: a select on the loaded
+    // value would wait for the load at once.  What a lane outside the box or
+    // a plane outside [0, n) loads is never used by an update that is stored:
+    // inside nodes are never on the box boundary, so all their neighbours are
+    // in the box and in planes 1..n-2 (`owner` requires ok, and the node types
+    // are masked with ok where they decide an update)
+    auto at = [&](int i) { return (int64_t)min(max(i, 0), n - 1) * s0 + off; };
+    auto ld_u = [&](int i) -> T { return ug[at(i)]; };
+    auto ld_f = [&](int i) -> T { return fg[at(i)]; };
+    auto ld_t = [&](int i) -> int { return (int)tg[at(i)]; };
+    pdl_wait();   // u comes from the previous launch
+    T om = ld_u(a - 2), oc = ld_u(a - 1), op = ld_u(a);   // old u, planes j-1, j, j+1
+    T hm = 0, hc = 0;                                     // half-swept, planes j-2, j-1
+    T fc = ld_f(a - 1), fm = 0;                           // f, planes j, j-1
+    int tc = ld_t(a - 1), tm = 0;                         // node types, planes j, j-1
+    T uq0 = ld_u(a + 1), uq1 = ld_u(a + 2), uq2 = ld_u(a + 3);
+    T fq0 = ld_f(a), fq1 = ld_f(a + 1), fq2 = ld_f(a + 2);
+    int tq0 = ld_t(a), tq1 = ld_t(a + 1), tq2 = ld_t(a + 2);
+    auto step = [&](int j, T &uq, T &fq, int &tq) {
+        T(*x)[NW][32] = sx[j & 1];
+        x[0][w][lane] = oc;
+        x[1][w][lane] = hc;
+        __syncthreads();
+        // red half-sweep on plane j
+        const T ozm = __shfl_up_sync(FULL, oc, 1), ozp = __shfl_down_sync(FULL, oc, 1);
+        const T oym = w > 0 ? x[0][w - 1][lane] : (T)0, oyp = w < NW - 1 ? x[0][w + 1][lane] : (T)0;
+        T hn = oc;
+        if (red_here && ok && j >= 0 && (tc & NODE_KIND) == NODE_IN && ((j + par) & 1) == 0)
+            hn = (mul_rn(h2, fc) + ((((ozm + ozp) + om) + op) + (oym + oyp))) * sixth;
+        // black half-sweep on plane j - 1, stored on the tile
+        const T hzm = __shfl_up_sync(FULL, hc, 1), hzp = __shfl_down_sync(FULL, hc, 1);
+        const T hym = w > 0 ? x[1][w - 1][lane] : (T)0, hyp = w < NW - 1 ? x[1][w + 1][lane] : (T)0;
+        if (owner && j - 1 >= a) {
+            T o = hc;
+            if ((tm & NODE_KIND) == NODE_IN && ((j - 1 + par) & 1) == 1)
+                o = (mul_rn(h2, fm) + ((((hzm + hzp) + hm) + hn) + (hym + hyp))) * sixth;
+            out[(int64_t)(j - 1) * s0 + off] = o;
+        }
+        // advance one plane; the loads issued now are read three steps later
+        om = oc;
+        oc = op;
+        op = uq;
+        uq = ld_u(j + 5);
+        hm = hc;
+        hc = hn;
+        fm = fc;
+        fc = fq;
+        fq = ld_f(j + 4);
+        tm = tc;
+        tc = tq;
+        tq = ld_t(j + 4);
+    };
+    int j = a - 1;
+    while (true) {
+        step(j, uq0, fq0, tq0);
+        if (++j > b) break;
+        step(j, uq1, fq1, tq1);
+        if (++j > b) break;
+        step(j, uq2, fq2, tq2);
+        if (++j > b) break;
+    }
+}
+
 // ------------------------------------------- 3D boundary phase in one launch
 // Grid-wide barrier for k_boundary3d, whose CTAs are all resident at once
 // (the grid is sized by the kernel's occupancy and the launch does not
@@ -324,8 +426,16 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned nbar, int *
 template <typename T>
 __device__ __forceinline__ T ldu(const T *p) { return __ldcg(p); }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_boundary3d(LevelView<T> v, BoundaryProgram3 P) {
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The phases of one 3D boundary relaxation; between two phases a grid-wide
+// barrier (CLUSTER = false: every CTA of the launch, grid_barrier) or the
+// hardware barrier of a thread-block cluster (CLUSTER = true: the launch is
+// one cluster)
+template <typename T, bool CLUSTER>
+__device__ __forceinline__ void boundary3d_body(LevelView<T> &v, const BoundaryProgram3 &P) {
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
     T *__restrict__ u = v.u;
     auto band = [&](const int32_t *__restrict__ list, int cnt) {   // Gauss-Seidel form of Eq. (jac2d), 7 points
@@ -351,7 +461,10 @@ __global__ void __launch_bounds__(kThreads) k_boundary3d(LevelView<T> v, Boundar
             u[v.gnode[q]] = __ldcg(v.gtmp + q);
         }
     };
-    auto sync = [&]() { grid_barrier(P.bar, P.nbar, P.err, P.spin); };
+    auto sync = [&]() {
+        if (CLUSTER) cluster_sync_all();
+        else grid_barrier(P.bar, P.nbar, P.err, P.spin);
+    };
     pdl_wait();
     bool first = true;
     auto phase_sync = [&]() {   // a barrier before every phase but the first
@@ -374,6 +487,19 @@ __global__ void __launch_bounds__(kThreads) k_boundary3d(LevelView<T> v, Boundar
         phase_sync(); ghost_new(P.zghost, P.nzghost);
         phase_sync(); ghost_store(P.zghost, P.nzghost);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_boundary3d(LevelView<T> v, BoundaryProgram3 P) {
+    boundary3d_body<T, false>(v, P);
+}
+
+// the same as one thread-block cluster of BC_SIZE CTAs (small levels and the
+// junction zone: a few thousand entries a phase)
+constexpr int BC_SIZE = 16, BC_THREADS = 1024;
+template <typename T>
+__global__ void __launch_bounds__(BC_THREADS) k_boundary3d_cluster(LevelView<T> v, BoundaryProgram3 P) {
+    boundary3d_body<T, true>(v, P);
 }
 
 // Same update over a compact list of band nodes of one colour (Sec. 3.2).
@@ -774,6 +900,48 @@ bool launch_boundary3d(const LevelView<T> &v, BoundaryProgram3 P, int phantom, c
 }
 
 template <typename T>
+bool launch_boundary3d_cluster(const LevelView<T> &v, const BoundaryProgram3 &P, cudaStream_t s) {
+    static int opted_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (dev != opted_dev) {   // cluster size 16 is beyond the portable 8
+        if (cudaFuncSetAttribute(k_boundary3d_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        opted_dev = dev;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(BC_SIZE);
+    cfg.blockDim = dim3(BC_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = BC_SIZE;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    if (cudaLaunchKernelEx(&cfg, k_boundary3d_cluster<T>, v, P) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    g_launches++;
+    return true;
+}
+
+template <typename T>
+void launch_rb_stream3d(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s) {
+    if (g.nsr <= 0) return;
+    g_launches++;
+    pdl_launch(k_rb_stream3d<T>, dim3((unsigned)g.nsr), dim3((SR_TY + 4) * 32), 0, s, v, out,
+               reinterpret_cast<const int2 *>(g.sr));
+}
+
+template <typename T>
 void launch_rb_zmarch(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s) {
     if (g.nzm <= 0) return;
     constexpr size_t smem = zmarch_smem_bytes<T>();
@@ -1094,7 +1262,9 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
                                     T *, cudaStream_t);                                                            \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
     template void launch_rb_zmarch<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);    \
+    template void launch_rb_stream3d<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);  \
     template bool launch_boundary3d<T>(const LevelView<T> &, BoundaryProgram3, int, cudaStream_t);  \
+    template bool launch_boundary3d_cluster<T>(const LevelView<T> &, const BoundaryProgram3 &, cudaStream_t); \
     template size_t local_smem_bytes<T>(const LocalView<T> &, int, bool);                                 \
     template void launch_local<T>(const LocalView<T> &, int, int, int, cudaStream_t);               \
     template void launch_local_copyback<T>(const LocalView<T> &, cudaStream_t);                      \

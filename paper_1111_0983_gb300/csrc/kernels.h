@@ -76,10 +76,17 @@ void launch_mask_types(int dim, int n, double h, const double *origin, int step,
 // was launched).
 template <typename T>
 bool launch_boundary3d(const LevelView<T> &v, BoundaryProgram3 P, int phantom, cudaStream_t s);
+// the same phases as one thread-block cluster (hardware barriers); false if
+// the launch failed (nothing was launched)
+template <typename T>
+bool launch_boundary3d_cluster(const LevelView<T> &v, const BoundaryProgram3 &P, cudaStream_t s);
 // 3D: one red-black sweep (both colours) over the level's fused-sweep items,
 // reading v.u and writing every node of the items into out
 template <typename T>
 void launch_rb_zmarch(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s);
+// the same sweep with the planes in registers (a warp a row, a lane a column)
+template <typename T>
+void launch_rb_stream3d(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s);
 
 template <typename T>
 size_t local_smem_bytes(const LocalView<T> &J, int dim, bool pre = false);

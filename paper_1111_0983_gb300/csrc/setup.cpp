@@ -823,16 +823,16 @@ static void build_ghost_transfer(HostLevel &F, const HostLevel &C) {
 // an inside node or a ghost (runs closer than 3 planes merged), cut into
 // pieces of at most ZM_SEG planes.  Items never overlap, so every unknown is
 // written by exactly one CTA.
-static void build_zmarch_items(HostLevel &L) {
-    const int n = L.n, ty = (n + ZM_TY - 1) / ZM_TY, tx = (n + ZM_TX - 1) / ZM_TX;
+static std::vector<int32_t> plane_items(const HostLevel &L, int TY, int TX) {
+    const int n = L.n, ty = (n + TY - 1) / TY, tx = (n + TX - 1) / TX;
     std::vector<uint8_t> act((size_t)ty * tx * n, 0);
     for (int64_t p = 0; p < L.nn; p++) {
         const uint8_t k = L.type[p] & NODE_KIND;
         if (k != NODE_IN && k != NODE_GHOST) continue;
         const int64_t i = p / ((int64_t)n * n), j = (p / n) % n, c = p % n;
-        act[((size_t)(j / ZM_TY) * tx + c / ZM_TX) * n + i] = 1;
+        act[((size_t)(j / TY) * tx + c / TX) * n + i] = 1;
     }
-    L.zm.clear();
+    std::vector<int32_t> items;
     for (int t = 0; t < ty * tx; t++) {
         const uint8_t *a = &act[(size_t)t * n];
         int i = 0;
@@ -844,12 +844,33 @@ static void build_zmarch_items(HostLevel &L) {
                 else if (k - end >= 2) break;
             }
             for (int s0 = i; s0 < end; s0 += ZM_SEG) {
-                L.zm.push_back(((t / tx) << 16) | (t % tx));
-                L.zm.push_back((s0 << 16) | std::min(end, s0 + ZM_SEG));
+                items.push_back(((t / tx) << 16) | (t % tx));
+                items.push_back((s0 << 16) | std::min(end, s0 + ZM_SEG));
             }
             i = end;
         }
     }
+    // launch order: by first plane, then tile (neighbouring tiles run side by
+    // side and share their halo reads in L2)
+    std::vector<size_t> ord(items.size() / 2);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
+        const int ax = items[2 * x + 1] >> 16, ay = items[2 * y + 1] >> 16;
+        return ax != ay ? ax < ay : items[2 * x] < items[2 * y];
+    });
+    std::vector<int32_t> sorted;
+    sorted.reserve(items.size());
+    for (size_t k : ord) {
+        sorted.push_back(items[2 * k]);
+        sorted.push_back(items[2 * k + 1]);
+    }
+    return sorted;
+}
+
+static void build_zmarch_items(HostLevel &L) {
+    const int n = L.n;
+    L.zm = plane_items(L, ZM_TY, ZM_TX);
+    L.sr = plane_items(L, SR_TY, SR_W);
     // inside-node masks of every item's planes first - 1 .. end (the tile
     // with a 1-node halo; nodes outside the box are not inside)
     L.zm_moff.clear();

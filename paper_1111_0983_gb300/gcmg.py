@@ -69,6 +69,8 @@ def lib():
             "gcmg_set_bc_types_from_mask": (st, [vp, vp]),
             "gcmg_bc_types": (st, [vp, i32, vp]),
             "gcmg_debug_barrier": (st, [vp, i32, i32, C.c_uint]),
+            "gcmg_set_sweep3d": (st, [vp, i32]),
+            "gcmg_set_boundary3d": (st, [vp, i32]),
             "gcmg_residual": (st, [vp, vp, vp, C.POINTER(dbl)]),
             "gcmg_destroy": (None, [vp]),
             "gcmg_last_error": (C.c_char_p, [vp]),
@@ -249,6 +251,15 @@ class Solver:
         """3D boundary relaxation: one launch with barriers (enable) or one
         launch per phase; phantom_blocks > 0 makes its barrier waits run out."""
         self._check(lib().gcmg_debug_barrier(self._h, int(bool(enable)), int(phantom_blocks), int(spin_limit)))
+
+    def set_boundary3d(self, mode):
+        """3D boundary relaxation: 0 a launch a phase (default), 1 clusters on
+        small levels, 2 one grid with software barriers."""
+        self._check(lib().gcmg_set_boundary3d(self._h, int(mode)))
+
+    def set_sweep3d(self, variant):
+        """3D interior sweep kernel: 0 shared-memory planes, 1 register planes."""
+        self._check(lib().gcmg_set_sweep3d(self._h, int(variant)))
 
     def bc_types(self, l):
         out = np.empty(self.num_ghosts(l), np.uint8)

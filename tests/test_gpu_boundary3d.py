@@ -27,20 +27,21 @@ def _solver(precision, n=65, **kw):
 @pytest.mark.parametrize("precision,n", [(0, 65), (1, 65), (1, 129)])
 def test_one_launch_equals_one_launch_per_phase(precision, n):
     """Same arithmetic in the same order: bitwise equal solutions and
-    per-cycle residuals, with and without the junction sweeps of the zone
-    that does not fit in shared memory."""
+    per-cycle residuals whether the boundary phases run as one launch each
+    (the default), as thread-block clusters or as one grid with software
+    barriers, with and without junction sweeps on global lists."""
     S = _solver(precision, n)
-    S.debug_barrier(enable=True)
-    u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
-    st1 = S.solve(u1)
-    S.debug_barrier(enable=False)
-    u2 = torch.zeros_like(u1)
-    st2 = S.solve(u2)
-    assert st1["converged"] and st2["converged"]
-    assert torch.equal(u1, u2)
-    np.testing.assert_array_equal(st1["rel"], st2["rel"])
-    # the single relaxation of the step API takes the same path
-    S.debug_barrier(enable=True)
+    runs = []
+    for mode in (0, 1, 2):
+        S.set_boundary3d(mode)
+        u = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
+        runs.append((u, S.solve(u)))
+    for u, st in runs:
+        assert st["converged"]
+        assert torch.equal(u, runs[0][0])
+        np.testing.assert_array_equal(st["rel"], runs[0][1]["rel"])
+    # the single relaxation of the step API takes the same paths
+    S.set_boundary3d(1)
     P = inputs.torus()
     rng = np.random.default_rng(5)
     T = torch.from_numpy(S.node_types(0) & 3 > 0).cuda()
@@ -50,10 +51,14 @@ def test_one_launch_equals_one_launch_per_phase(precision, n):
     g = torch.from_numpy(P.g_values(G["B"], G["nu"], P.bc_types(G["B"]))).cuda()
     a = u.clone()
     S.relax(0, a, f, g)
-    S.debug_barrier(enable=False)
+    S.set_boundary3d(0)
     b = u.clone()
     S.relax(0, b, f, g)
     assert torch.equal(a, b)
+    S.set_boundary3d(2)
+    c = u.clone()
+    S.relax(0, c, f, g)
+    assert torch.equal(a, c)
 
 
 def test_barrier_wait_runs_out_and_context_stays_usable():
@@ -68,7 +73,23 @@ def test_barrier_wait_runs_out_and_context_stays_usable():
     u.zero_()
     st = S.solve(u)
     assert st["converged"]
-    S2 = _solver(1)                  # default: one launch per phase
+    S2 = _solver(1)                  # default: one launch a phase
     u2 = torch.zeros_like(u)
     S2.solve(u2)
     assert torch.equal(u, u2)
+
+
+@pytest.mark.parametrize("precision,n", [(0, 65), (1, 129)])
+def test_sweep_kernels_agree_bitwise(precision, n):
+    """The 3D interior sweep with the planes in registers (default) and with
+    the planes staged in shared memory compute the same sums in the same
+    order: bitwise equal solves."""
+    S = _solver(precision, n)
+    u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
+    st1 = S.solve(u1)
+    S.set_sweep3d(0)
+    u2 = torch.zeros_like(u1)
+    st2 = S.solve(u2)
+    assert st1["converged"] and st2["converged"]
+    assert torch.equal(u1, u2)
+    np.testing.assert_array_equal(st1["rel"], st2["rel"])
