@@ -23,8 +23,8 @@ constexpr int CHUNK = 32;  // 3D active chunks: nodes along the contiguous axis 
 constexpr int ZM_TY = 16, ZM_TX = 64, ZM_SEG = 32;
 // 3D register-streaming sweep (k_rb_stream3d): a CTA owns SR_TY rows x SR_W
 // columns, one warp per row (2 halo rows each side), one lane per column (2
-// halo lanes each side), and marches along axis 0 over at most ZM_SEG planes
-constexpr int SR_TY = 12, SR_W = 28;
+// halo lanes each side), and marches along axis 0 over at most SR_SEG planes
+constexpr int SR_TY = 12, SR_W = 28, SR_SEG = 64;
 // its inside-node masks: per plane (ZM_TY + 2) rows of ZM_TX + 2 bits (the
 // tile and a 1-node halo), ZM_MROW words a row, planes padded to 16 bytes
 constexpr int ZM_MROW = (ZM_TX + 2 + 31) / 32;

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__((SR_TY + 4) * 32, sizeof(T) == 4 ? 3 : 2)
     int tc = ld_t(a - 1), tm = 0;                         // node types, planes j, j-1
     T uq0 = ld_u(a + 1), uq1 = ld_u(a + 2), uq2 = ld_u(a + 3);
     T fq0 = ld_f(a), fq1 = ld_f(a + 1), fq2 = ld_f(a + 2);
-    int tq0 = ld_t(a), tq1 = ld_t(a + 1), tq2 = ld_t(a + 2);
+    int tq0 = ld_t(a), tq1 = ld_t(a + 1), tq2 = ld_t(a + 2);   // (clamped: an item has >= 1 plane)
     auto step = [&](int j, T &uq, T &fq, int &tq) {
         T(*x)[NW][32] = sx[j & 1];
         x[0][w][lane] = oc;
@@ -361,18 +361,19 @@ __global__ void __launch_bounds__((SR_TY + 4) * 32, sizeof(T) == 4 ? 3 : 2)
             out[(int64_t)(j - 1) * s0 + off] = o;
         }
         // advance one plane; the loads issued now are read three steps later
+        // (none past the last plane the item reads: predicated, not selected)
         om = oc;
         oc = op;
         op = uq;
-        uq = ld_u(j + 5);
+        if (j + 5 <= b + 1) uq = ld_u(j + 5);
         hm = hc;
         hc = hn;
         fm = fc;
         fc = fq;
-        fq = ld_f(j + 4);
+        if (j + 4 <= b) fq = ld_f(j + 4);
         tm = tc;
         tc = tq;
-        tq = ld_t(j + 4);
+        if (j + 4 <= b) tq = ld_t(j + 4);
     };
     int j = a - 1;
     while (true) {

@@ -823,7 +823,7 @@ static void build_ghost_transfer(HostLevel &F, const HostLevel &C) {
 // an inside node or a ghost (runs closer than 3 planes merged), cut into
 // pieces of at most ZM_SEG planes.  Items never overlap, so every unknown is
 // written by exactly one CTA.
-static std::vector<int32_t> plane_items(const HostLevel &L, int TY, int TX) {
+static std::vector<int32_t> plane_items(const HostLevel &L, int TY, int TX, int seg) {
     const int n = L.n, ty = (n + TY - 1) / TY, tx = (n + TX - 1) / TX;
     std::vector<uint8_t> act((size_t)ty * tx * n, 0);
     for (int64_t p = 0; p < L.nn; p++) {
@@ -843,9 +843,9 @@ static std::vector<int32_t> plane_items(const HostLevel &L, int TY, int TX) {
                 if (a[k]) end = k + 1;
                 else if (k - end >= 2) break;
             }
-            for (int s0 = i; s0 < end; s0 += ZM_SEG) {
+            for (int s0 = i; s0 < end; s0 += seg) {
                 items.push_back(((t / tx) << 16) | (t % tx));
-                items.push_back((s0 << 16) | std::min(end, s0 + ZM_SEG));
+                items.push_back((s0 << 16) | std::min(end, s0 + seg));
             }
             i = end;
         }
@@ -869,8 +869,8 @@ static std::vector<int32_t> plane_items(const HostLevel &L, int TY, int TX) {
 
 static void build_zmarch_items(HostLevel &L) {
     const int n = L.n;
-    L.zm = plane_items(L, ZM_TY, ZM_TX);
-    L.sr = plane_items(L, SR_TY, SR_W);
+    L.zm = plane_items(L, ZM_TY, ZM_TX, ZM_SEG);
+    L.sr = plane_items(L, SR_TY, SR_W, SR_SEG);
     // inside-node masks of every item's planes first - 1 .. end (the tile
     // with a 1-node halo; nodes outside the box are not inside)
     L.zm_moff.clear();
