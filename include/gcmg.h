@@ -338,9 +338,24 @@ gcmg_status gcmg_debug_barrier(gcmg_ctx *ctx, int enable, int phantom_blocks, un
 
 /* Kernel of the 3D interior sweep (red and black in one pass over the active
  * tiles, Eq. jac2d): 0 tiles of 16 x 64 nodes with the planes staged in
- * shared memory; 1 (default) tiles of 12 x 28 nodes with the planes in
- * registers, a warp a row.  Same results bitwise.  Not in the paper. */
+ * shared memory; 1 tiles of 12 x 28 nodes with the planes in registers, a
+ * warp a row; 2 (default) blocks of 12 rows whose window along the
+ * contiguous axis covers the rows' unknowns, reading and writing only the
+ * spans of unknowns of each row (FP32 cycles; FP64 cycles and levels whose
+ * rows hold more than one interval of inside nodes use 1).  Same results
+ * bitwise.  Not in the paper. */
 gcmg_status gcmg_set_sweep3d(gcmg_ctx *ctx, int variant);
+
+/* Rebuilds the work items of sweep 2 on every 3D level: `columns` nodes a
+ * lane along the contiguous axis (2..5; a window of 32 columns nodes, 0 =
+ * chosen per level by a work model) and items of at most `planes` planes
+ * (1..32; 0 = 32).  Blocks until done; results are unchanged (tuning only).
+ * GCMG_E_ARG for values out of range.  Not in the paper. */
+gcmg_status gcmg_set_span3d(gcmg_ctx *ctx, int columns, int planes);
+
+/* Sweep 2's work on level l: number of items (0: the level uses sweep 1)
+ * and nodes a lane holds.  Not in the paper. */
+gcmg_status gcmg_span3d_info(const gcmg_ctx *ctx, int l, int *items, int *columns);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t gcmg_launch_counter(void);

@@ -169,6 +169,12 @@ void upload_geometry(gcmg_ctx *c, int l) {
         g.nsr = (int)(L.sr.size() / 2);
         g.sr = upload<int32_t>(c, L.sr.data(), L.sr.size());
     }
+    if (!L.sp.empty()) {
+        g.nsp = (int)(L.sp.size() / 4);
+        g.sp_cols = L.sp_cols;
+        g.sp = upload<int32_t>(c, L.sp.data(), L.sp.size());
+        g.sp_rows = upload<int32_t>(c, L.sp_rows.data(), L.sp_rows.size());
+    }
     if (!L.chunk.empty()) {
         g.nchunks = (int64_t)L.chunk.size();
         g.chunks = upload<int32_t>(c, L.chunk.data(), L.chunk.size());
@@ -361,8 +367,11 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         // 3D: both colours in one pass over the active tiles (reads v.u, writes out)
         const double bytes = c->timing_kind >= 0 ? 3.0 * (double)c->H[l].n_in * sizeof(T) : 0.0;
         timer_mark(c, GCMG_KERNEL_SMOOTH, l, bytes);
-        if (c->sweep3d == 1 && g.nsr > 0) launch_rb_stream3d<T>(v, out, g, c->stream);
-        else launch_rb_zmarch<T>(v, out, g, c->stream);
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value)
+            if (c->sweep3d == 2) done = launch_rb_span3d(v, out, g, c->stream);
+        if (!done && c->sweep3d >= 1 && g.nsr > 0) launch_rb_stream3d<T>(v, out, g, c->stream);
+        else if (!done) launch_rb_zmarch<T>(v, out, g, c->stream);
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
         v.u = out;
     } else {
@@ -1122,9 +1131,42 @@ gcmg_status gcmg_set_boundary3d(gcmg_ctx *c, int mode) {
 }
 
 gcmg_status gcmg_set_sweep3d(gcmg_ctx *c, int variant) {
-    if (!c || variant < 0 || variant > 1) return fail(c, GCMG_E_ARG, "bad argument");
+    if (!c || variant < 0 || variant > 2) return fail(c, GCMG_E_ARG, "bad argument");
     destroy_graph(c);
     c->sweep3d = variant;
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_set_span3d(gcmg_ctx *c, int columns, int planes) {
+    if (!c || columns < 0 || (columns > 0 && (columns < SP_CMIN || columns > SP_CMAX)) || planes < 0 ||
+        planes > SP_SEG)
+        return fail(c, GCMG_E_ARG, "bad argument");
+    if (c->p.dim != 3) return GCMG_OK;
+    GCMG_GUARD(c, {
+        destroy_graph(c);
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        for (size_t l = 0; l < c->H.size(); l++) {
+            HostLevel &L = c->H[l];
+            DevGeom &g = c->G[l];
+            if (L.nn >= ((int64_t)1 << 31)) continue;
+            build_span_items(L, columns, planes);
+            g.nsp = 0;
+            g.sp_cols = 0;
+            if (L.sp.empty()) continue;
+            g.sp_cols = L.sp_cols;
+            g.sp = upload<int32_t>(c, L.sp.data(), L.sp.size());
+            g.sp_rows = upload<int32_t>(c, L.sp_rows.data(), L.sp_rows.size());
+            g.nsp = (int)(L.sp.size() / 4);
+        }
+        ck(cudaStreamSynchronize(c->stream), "sync");
+    })
+    return GCMG_OK;
+}
+
+gcmg_status gcmg_span3d_info(const gcmg_ctx *c, int l, int *items, int *columns) {
+    if (!valid_level(c, l) || !items || !columns) return GCMG_E_ARG;
+    *items = c->G[l].nsp;
+    *columns = c->G[l].sp_cols;
     return GCMG_OK;
 }
 

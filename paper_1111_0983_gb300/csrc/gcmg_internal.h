@@ -25,6 +25,13 @@ constexpr int ZM_TY = 16, ZM_TX = 64, ZM_SEG = 32;
 // columns, one warp per row (2 halo rows each side), one lane per column (2
 // halo lanes each side), and marches along axis 0 over at most SR_SEG planes
 constexpr int SR_TY = 12, SR_W = 28, SR_SEG = 64;
+// 3D row-span sweep (k_rb_span3d): a CTA of SP_NW warps owns SP_NW - 4 rows
+// (axis 1), one warp a row with 2 halo rows each side; lane l holds the nodes
+// k0 + l + 32 c (c < C) of its row, a window of 32 C nodes along axis 2 of
+// which the inner 32 C - 2 are owned; it marches along axis 0 over at most
+// SP_SEG planes.  Per (plane, row) the level keeps the span of its unknowns
+// and of its inside nodes, so that nothing outside them is read or written.
+constexpr int SP_NW = 16, SP_J = SP_NW - 4, SP_SEG = 32, SP_CMIN = 2, SP_CMAX = 5;
 // its inside-node masks: per plane (ZM_TY + 2) rows of ZM_TX + 2 bits (the
 // tile and a 1-node halo), ZM_MROW words a row, planes padded to 16 bytes
 constexpr int ZM_MROW = (ZM_TX + 2 + 31) / 32;
@@ -94,6 +101,14 @@ struct HostLevel {
     std::vector<uint32_t> zm_mask;
     // the same pairs for the SR_TY x SR_W tiles of the register-streaming sweep
     std::vector<int32_t> sr;
+    // row-span sweep: per (plane i, row j), i * n + j, two words: the span of
+    // the row's unknowns (lo | hi << 16) and of its inside nodes (the same
+    // form); an empty span is lo = 0xffff, hi = 0.  Items: quadruples (row
+    // block, window origin k0, first plane, end plane); sp_cols = C, the
+    // columns a lane holds.  Empty when some row's inside nodes are not one
+    // interval (the sweep then falls back to the tiles).
+    std::vector<int32_t> sp_rows, sp;
+    int sp_cols = 0;
     // defect extension of this level (before restricting to the next coarser one)
     std::vector<int32_t> ext_node;      // ordered by upwind wavefront
     std::vector<uint8_t> ext_cnt;
@@ -123,6 +138,12 @@ struct HostLevel {
 
     int64_t ng() const { return (int64_t)ghost_node.size(); }
 };
+
+// Rebuilds a 3D level's row-span sweep items for C columns a lane and items
+// of at most seg planes (C = 0: the cheapest C by the work model; seg = 0:
+// SP_SEG).  Returns false (and leaves the level without items) when a row's
+// inside nodes are not one interval.
+bool build_span_items(HostLevel &L, int C = 0, int seg = 0);
 
 // Builds all levels (throws GeomError).  phi: fine grid, n^dim values; h0:
 // fine spacing (0: 2 / (n - 1)); origin: coordinates of node 0 (null: -1 on
@@ -190,6 +211,9 @@ struct DevGeom {
     uint32_t *zm_mask = nullptr;
     int nsr = 0;                 // register-streaming sweep items (HostLevel::sr pairs)
     int32_t *sr = nullptr;
+    int nsp = 0, sp_cols = 0;    // row-span sweep items (HostLevel::sp quadruples), columns a lane
+    int32_t *sp = nullptr;
+    int32_t *sp_rows = nullptr;  // HostLevel::sp_rows
     int64_t nchunks = 0;         // 3D active chunks (HostLevel::chunk)
     int32_t *chunks = nullptr;
     uint8_t *chunk_len = nullptr;

@@ -386,6 +386,172 @@ __global__ void __launch_bounds__((SR_TY + 4) * 32, sizeof(T) == 4 ? 3 : 2)
     }
 }
 
+// ------------------------------------- 3D fused red-black sweep on row spans
+// The same sweep with a window that follows the domain along the contiguous
+// axis: a CTA of SP_NW warps owns SP_J rows (axis 1), warp w holds row
+// r0 - 2 + w, and lane l the nodes k0 + l + 32 c (c < C) of it -- a window
+// of 32 C nodes along axis 2, of which the first and the last are halo.  The
+// lane to the left of node k0 + 32 c is lane 31's column c - 1 and the one
+// to the right of lane 31's column c is lane 0's column c + 1 (one shuffle
+// each way a column); the outer neighbours of the window, k0 - 1 and
+// k0 + 32 C, are loaded by lanes 31 and 0 as an extra column.  Per (plane,
+// row) the level's metadata holds the span of the unknowns and of the inside
+// nodes (the inside nodes of a row are one interval); a CTA stages the
+// metadata of its planes in shared memory before it waits for the previous
+// launch, and then reads u only on unknown spans, f only on inside spans and
+// writes only unknowns, so the traffic follows the domain at 32-byte sector
+// granularity.  Nodes outside the spans read 0; no update that is stored
+// uses them (the neighbours of an inside node are unknowns).  The march is
+// that of k_rb_stream3d: at step j the red half-sweep of plane j (rows
+// 1 .. SP_NW - 2), the black half-sweep of plane j - 1 on the owned rows and
+// columns, loads three planes ahead, one block barrier a plane.  Same sums
+// in the same order: bitwise equal to red then black in place.
+template <int C>
+__global__ void __launch_bounds__(SP_NW * 32, 1)
+    k_rb_span3d(LevelView<float> v, float *__restrict__ out, const int4 *__restrict__ items,
+                const int2 *__restrict__ rows) {
+    constexpr int NW = SP_NW, NP = SP_SEG + 4, PL = 2 * NW * C * 32;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char sp_smem[];
+    int2 *meta = reinterpret_cast<int2 *>(sp_smem);                            // [NP][NW]
+    float *sx = reinterpret_cast<float *>(sp_smem + NP * NW * sizeof(int2));    // [2][old, half][NW][C][32]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 it = items[blockIdx.x];
+    const int r0 = it.x * SP_J, k0 = it.y, a = it.z, b = it.w;
+    const int n = v.n;
+    const int row = r0 - 2 + w;
+    const int64_t s0 = v.s0;
+    const int64_t rbase = (int64_t)row * n + k0 + lane;   // node (0, row, k0 + lane)
+    const bool redrow = w >= 1 && w <= NW - 2, owner = w >= 2 && w <= NW - 3;
+    const int par = (row + k0 + lane) & 1;   // a lane's nodes are red in plane i when i + par is even
+    const float h2 = v.h2, sixth = (float)(1.0 / 6.0);
+    const float *__restrict__ ug = v.u;
+    const float *__restrict__ fg = v.f;
+    // metadata of planes a - 2 .. b + 1 (set up once: read before the wait)
+    const int np = b - a + 4;
+    for (int q = threadIdx.x; q < np * NW; q += NW * 32) {
+        const int p = a - 2 + q / NW, rr = r0 - 2 + q % NW;
+        int2 m = make_int2(0xffff, 0xffff);
+        if (p >= 0 && p < n && rr >= 0 && rr < n) m = rows[(int64_t)p * n + rr];
+        meta[q] = m;
+    }
+    __syncthreads();
+    auto has = [](int sp, int k) { return k >= (sp & 0xffff) && k <= (int)((unsigned)sp >> 16); };
+    auto ld_u = [&](int p, float(&x)[C + 1]) {
+        const int sp = meta[(p - a + 2) * NW + w].x;
+        const float *src = ug + (int64_t)p * s0 + rbase;
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            x[c] = 0.f;
+            if (has(sp, k0 + lane + 32 * c)) x[c] = src[32 * c];
+        }
+        const int ke = lane == 31 ? k0 - 1 : k0 + 32 * C;   // the extra column
+        x[C] = 0.f;
+        if ((lane == 0 || lane == 31) && has(sp, ke)) x[C] = ug[(int64_t)p * s0 + (int64_t)row * n + ke];
+    };
+    auto ld_f = [&](int p, float(&x)[C]) {
+        const int sp = meta[(p - a + 2) * NW + w].y;
+        const float *src = fg + (int64_t)p * s0 + rbase;
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            x[c] = 0.f;
+            if (redrow && has(sp, k0 + lane + 32 * c)) x[c] = src[32 * c];
+        }
+    };
+    float om[C], oc[C + 1], op[C + 1], hm[C], hc[C], fm[C], fc[C];
+    float uq0[C + 1], uq1[C + 1], uq2[C + 1], fq0[C], fq1[C], fq2[C];
+    pdl_wait();   // u comes from the previous launch
+    {
+        float t[C + 1];
+        ld_u(a - 2, t);
+#pragma unroll
+        for (int c = 0; c < C; c++) om[c] = t[c];
+    }
+    ld_u(a - 1, oc);
+    ld_u(a, op);
+#pragma unroll
+    for (int c = 0; c <= C; c++) uq0[c] = uq1[c] = uq2[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < C; c++) hm[c] = hc[c] = fm[c] = fq0[c] = fq1[c] = fq2[c] = 0.f;
+    if (a + 1 <= b + 1) ld_u(a + 1, uq0);
+    if (a + 2 <= b + 1) ld_u(a + 2, uq1);
+    if (a + 3 <= b + 1) ld_u(a + 3, uq2);
+    ld_f(a - 1, fc);
+    ld_f(a, fq0);
+    if (a + 1 <= b) ld_f(a + 1, fq1);
+    if (a + 2 <= b) ld_f(a + 2, fq2);
+    auto step = [&](int j, float(&uq)[C + 1], float(&fq)[C]) {
+        float *x = sx + (j & 1) * PL;
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            x[(w * C + c) * 32 + lane] = oc[c];
+            x[((NW + w) * C + c) * 32 + lane] = hc[c];
+        }
+        __syncthreads();
+        const int2 mj = meta[(j - a + 2) * NW + w];   // plane j
+        const bool red = ((j + par) & 1) == 0;       // red in plane j, black in plane j - 1
+        float hn[C];
+        // red half-sweep on plane j
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            const float sl = lane == 31 ? (c == 0 ? oc[C] : oc[c - 1]) : oc[c];
+            const float sr = lane == 0 ? (c == C - 1 ? oc[C] : oc[c + 1]) : oc[c];
+            const float ozm = __shfl_sync(FULL, sl, (lane + 31) & 31);
+            const float ozp = __shfl_sync(FULL, sr, (lane + 1) & 31);
+            const float oym = w > 0 ? x[((w - 1) * C + c) * 32 + lane] : 0.f;
+            const float oyp = w < NW - 1 ? x[((w + 1) * C + c) * 32 + lane] : 0.f;
+            hn[c] = oc[c];
+            if (redrow && red && has(mj.y, k0 + lane + 32 * c))
+                hn[c] = (mul_rn(h2, fc[c]) + ((((ozm + ozp) + om[c]) + op[c]) + (oym + oyp))) * sixth;
+        }
+        // black half-sweep on plane j - 1, stored on the owned rows and columns
+        if (owner && j - 1 >= a) {
+            const int2 mi = meta[(j - 1 - a + 2) * NW + w];
+            float *o = out + (int64_t)(j - 1) * s0 + rbase;
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                const float sl = lane == 31 ? (c == 0 ? 0.f : hc[c - 1]) : hc[c];
+                const float sr = lane == 0 ? (c == C - 1 ? 0.f : hc[c + 1]) : hc[c];
+                const float hzm = __shfl_sync(FULL, sl, (lane + 31) & 31);
+                const float hzp = __shfl_sync(FULL, sr, (lane + 1) & 31);
+                const float hym = x[((NW + w - 1) * C + c) * 32 + lane];
+                const float hyp = x[((NW + w + 1) * C + c) * 32 + lane];
+                const int k = k0 + lane + 32 * c;
+                float val = hc[c];
+                if (red && has(mi.y, k))
+                    val = (mul_rn(h2, fm[c]) + ((((hzm + hzp) + hm[c]) + hn[c]) + (hym + hyp))) * sixth;
+                const bool own = !(lane == 0 && c == 0) && !(lane == 31 && c == C - 1);
+                if (own && has(mi.x, k)) o[32 * c] = val;
+            }
+        }
+        // advance one plane; the loads issued now are read three steps later
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            om[c] = oc[c];
+            hm[c] = hc[c];
+            hc[c] = hn[c];
+            fm[c] = fc[c];
+            fc[c] = fq[c];
+        }
+#pragma unroll
+        for (int c = 0; c <= C; c++) {
+            oc[c] = op[c];
+            op[c] = uq[c];
+        }
+        if (j + 5 <= b + 1) ld_u(j + 5, uq);
+        if (j + 4 <= b) ld_f(j + 4, fq);
+    };
+    int j = a - 1;
+    while (true) {
+        step(j, uq0, fq0);
+        if (++j > b) break;
+        step(j, uq1, fq1);
+        if (++j > b) break;
+        step(j, uq2, fq2);
+        if (++j > b) break;
+    }
+}
+
 // ------------------------------------------- 3D boundary phase in one launch
 // Grid-wide barrier for k_boundary3d, whose CTAs are all resident at once
 // (the grid is sized by the kernel's occupancy and the launch does not
@@ -940,6 +1106,31 @@ void launch_rb_stream3d(const LevelView<T> &v, T *out, const DevGeom &g, cudaStr
     g_launches++;
     pdl_launch(k_rb_stream3d<T>, dim3((unsigned)g.nsr), dim3((SR_TY + 4) * 32), 0, s, v, out,
                reinterpret_cast<const int2 *>(g.sr));
+}
+
+template <int C>
+static void launch_span3d(const LevelView<float> &v, float *out, const DevGeom &g, cudaStream_t s) {
+    constexpr size_t smem = (size_t)(SP_SEG + 4) * SP_NW * sizeof(int2) + (size_t)4 * SP_NW * C * 32 * sizeof(float);
+    static bool opted = false;
+    if (!opted) {
+        cudaFuncSetAttribute(k_rb_span3d<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        opted = true;
+    }
+    pdl_launch(k_rb_span3d<C>, dim3((unsigned)g.nsp), dim3(SP_NW * 32), smem, s, v, out,
+               reinterpret_cast<const int4 *>(g.sp), reinterpret_cast<const int2 *>(g.sp_rows));
+}
+
+bool launch_rb_span3d(const LevelView<float> &v, float *out, const DevGeom &g, cudaStream_t s) {
+    if (g.nsp <= 0) return false;
+    switch (g.sp_cols) {
+    case 2: launch_span3d<2>(v, out, g, s); break;
+    case 3: launch_span3d<3>(v, out, g, s); break;
+    case 4: launch_span3d<4>(v, out, g, s); break;
+    case 5: launch_span3d<5>(v, out, g, s); break;
+    default: return false;
+    }
+    g_launches++;
+    return true;
 }
 
 template <typename T>

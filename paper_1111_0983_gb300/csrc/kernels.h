@@ -87,6 +87,8 @@ void launch_rb_zmarch(const LevelView<T> &v, T *out, const DevGeom &g, cudaStrea
 // the same sweep with the planes in registers (a warp a row, a lane a column)
 template <typename T>
 void launch_rb_stream3d(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s);
+// the row-span sweep (FP32); false when the level has no items for it
+bool launch_rb_span3d(const LevelView<float> &v, float *out, const DevGeom &g, cudaStream_t s);
 
 template <typename T>
 size_t local_smem_bytes(const LocalView<T> &J, int dim, bool pre = false);

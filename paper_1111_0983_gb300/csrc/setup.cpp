@@ -902,6 +902,126 @@ static void build_zmarch_items(HostLevel &L) {
     }
 }
 
+// Row-span sweep items.  A row block is SP_J consecutive rows (axis 1); per
+// plane its span is the union of its rows' unknown spans.  The planes where
+// that span is not empty form runs (gaps of up to 2 idle planes merged), cut
+// into pieces of at most seg planes; each piece covers the union of its
+// planes' spans [kmin, kmax] with windows of 32 C nodes whose owned parts
+// (the inner 32 C - 2 nodes) tile it: k0 = kmin - 1 + m (32 C - 2).  Items
+// never overlap, so every unknown is written by exactly one CTA.
+static void span_items_for(const HostLevel &L, int C, int seg, std::vector<int32_t> &out) {
+    const int n = L.n, W = 32 * C - 2, nb = (n + SP_J - 1) / SP_J;
+    std::vector<int> lo(n), hi(n);
+    out.clear();
+    for (int jb = 0; jb < nb; jb++) {
+        for (int i = 0; i < n; i++) {
+            int l = n, h = -1;
+            for (int j = jb * SP_J; j < std::min(n, jb * SP_J + SP_J); j++) {
+                const uint32_t sp = (uint32_t)L.sp_rows[2 * ((size_t)i * n + j)];
+                const int sl = (int)(sp & 0xffffu), sh = (int)(sp >> 16);
+                if (sl <= sh) {
+                    l = std::min(l, sl);
+                    h = std::max(h, sh);
+                }
+            }
+            lo[i] = l;
+            hi[i] = h;
+        }
+        int i = 0;
+        while (i < n) {
+            if (lo[i] > hi[i]) { i++; continue; }
+            int end = i + 1;
+            for (int k = end; k < n; k++) {
+                if (lo[k] <= hi[k]) end = k + 1;
+                else if (k - end >= 2) break;
+            }
+            for (int s0 = i; s0 < end; s0 += seg) {
+                const int s1 = std::min(end, s0 + seg);
+                int kmin = n, kmax = -1;
+                for (int p = s0; p < s1; p++)
+                    if (lo[p] <= hi[p]) {
+                        kmin = std::min(kmin, lo[p]);
+                        kmax = std::max(kmax, hi[p]);
+                    }
+                for (int k0 = kmin - 1; k0 + 1 <= kmax; k0 += W) {
+                    out.push_back(jb);
+                    out.push_back(k0);
+                    out.push_back(s0);
+                    out.push_back(s1);
+                }
+            }
+            i = end;
+        }
+    }
+}
+
+bool build_span_items(HostLevel &L, int C, int seg) {
+    L.sp.clear();
+    L.sp_rows.clear();
+    L.sp_cols = 0;
+    if (L.dim != 3 || L.n > 0xfffe) return false;
+    const int n = L.n;
+    seg = seg <= 0 ? SP_SEG : std::min(seg, SP_SEG);   // the CTA stages the metadata of SP_SEG + 4 planes
+    const int32_t EMPTY = 0xffff;
+    L.sp_rows.assign((size_t)2 * n * n, EMPTY);
+    for (int64_t r = 0; r < (int64_t)n * n; r++) {
+        const uint8_t *t = &L.type[(size_t)r * n];
+        int lo = n, hi = -1, ilo = n, ihi = -1, cnt = 0;
+        for (int k = 0; k < n; k++) {
+            const int kind = t[k] & NODE_KIND;
+            if (kind == NODE_IN || kind == NODE_GHOST) {
+                lo = std::min(lo, k);
+                hi = k;
+            }
+            if (kind == NODE_IN) {
+                ilo = std::min(ilo, k);
+                ihi = k;
+                cnt++;
+            }
+        }
+        if (cnt > 0 && cnt != ihi - ilo + 1) {   // inside nodes not one interval
+            L.sp_rows.clear();
+            return false;
+        }
+        if (hi >= lo) L.sp_rows[2 * r] = (int32_t)((uint32_t)lo | ((uint32_t)hi << 16));
+        if (ihi >= ilo) L.sp_rows[2 * r + 1] = (int32_t)((uint32_t)ilo | ((uint32_t)ihi << 16));
+    }
+    // C: the fewest lane-node steps, counting a warp's fixed work per plane
+    // (metadata, barrier, loop) as 1.25 columns and an item's pipeline fill
+    // as 4 planes
+    int best = C;
+    if (best < SP_CMIN || best > SP_CMAX) {
+        double bcost = 0.0;
+        std::vector<int32_t> it;
+        for (int cc = SP_CMIN; cc <= SP_CMAX; cc++) {
+            span_items_for(L, cc, seg, it);
+            double cost = 0.0;
+            for (size_t q = 0; q < it.size(); q += 4) cost += (double)(it[q + 3] - it[q + 2] + 4) * (1.25 + cc);
+            if (best < SP_CMIN || best > SP_CMAX || cost < bcost) {
+                best = cc;
+                bcost = cost;
+            }
+        }
+    }
+    std::vector<int32_t> items;
+    span_items_for(L, best, seg, items);
+    // launch order: by first plane, then row block, then window (neighbouring
+    // blocks run side by side and share their halo rows in L2)
+    const size_t m = items.size() / 4;
+    std::vector<size_t> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
+        if (items[4 * x + 2] != items[4 * y + 2]) return items[4 * x + 2] < items[4 * y + 2];
+        if (items[4 * x] != items[4 * y]) return items[4 * x] < items[4 * y];
+        return items[4 * x + 1] < items[4 * y + 1];
+    });
+    L.sp.reserve(items.size());
+    for (size_t k : ord)
+        for (int e = 0; e < 4; e++) L.sp.push_back(items[4 * k + e]);
+    L.sp_cols = best;
+    return true;
+}
+
 void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
                      std::vector<HostLevel> &levels, double h0, const double *origin) {
     if (!(h0 > 0.0)) h0 = 2.0 / (n - 1);
@@ -952,6 +1072,7 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
                     if (active[(size_t)a * tc + b]) L.tiles.push_back((a << 16) | b);
         } else if (L.nn < ((int64_t)1 << 31)) {
             build_zmarch_items(L);
+            build_span_items(L);
             // active chunks: CHUNK-node runs of a row holding an inside node or a ghost
             for (int64_t row = 0; row < L.nn; row += L.n)
                 for (int z0 = 0; z0 < L.n; z0 += CHUNK) {

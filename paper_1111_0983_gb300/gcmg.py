@@ -70,6 +70,8 @@ def lib():
             "gcmg_bc_types": (st, [vp, i32, vp]),
             "gcmg_debug_barrier": (st, [vp, i32, i32, C.c_uint]),
             "gcmg_set_sweep3d": (st, [vp, i32]),
+            "gcmg_set_span3d": (st, [vp, i32, i32]),
+            "gcmg_span3d_info": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
             "gcmg_set_boundary3d": (st, [vp, i32]),
             "gcmg_residual": (st, [vp, vp, vp, C.POINTER(dbl)]),
             "gcmg_destroy": (None, [vp]),
@@ -258,8 +260,20 @@ class Solver:
         self._check(lib().gcmg_set_boundary3d(self._h, int(mode)))
 
     def set_sweep3d(self, variant):
-        """3D interior sweep kernel: 0 shared-memory planes, 1 register planes."""
+        """3D interior sweep kernel: 0 shared-memory planes, 1 register planes,
+        2 row spans (default)."""
         self._check(lib().gcmg_set_sweep3d(self._h, int(variant)))
+
+    def set_span3d(self, columns=0, planes=0):
+        """Rebuild the row-span sweep's items: columns a lane (2..5, 0 auto),
+        planes an item (1..32, 0 = 32)."""
+        self._check(lib().gcmg_set_span3d(self._h, int(columns), int(planes)))
+
+    def span3d_info(self, l):
+        """(items, columns) of the row-span sweep on level l."""
+        it, co = C.c_int(0), C.c_int(0)
+        self._check(lib().gcmg_span3d_info(self._h, int(l), C.byref(it), C.byref(co)))
+        return it.value, co.value
 
     def bc_types(self, l):
         out = np.empty(self.num_ghosts(l), np.uint8)

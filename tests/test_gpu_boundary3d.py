@@ -79,17 +79,32 @@ def test_barrier_wait_runs_out_and_context_stays_usable():
     assert torch.equal(u, u2)
 
 
-@pytest.mark.parametrize("precision,n", [(0, 65), (1, 129)])
+@pytest.mark.parametrize("precision,n", [(0, 65), (1, 129), (1, 257)])
 def test_sweep_kernels_agree_bitwise(precision, n):
-    """The 3D interior sweep with the planes in registers (default) and with
-    the planes staged in shared memory compute the same sums in the same
-    order: bitwise equal solves."""
+    """The 3D interior sweeps -- row spans (the FP32 default), the planes in
+    registers (the FP64 default) and the planes staged in shared memory --
+    compute the same sums in the same order: bitwise equal solves, also with
+    the row-span items rebuilt for every lane width and for short items."""
     S = _solver(precision, n)
+    if precision == 1:
+        items, cols = S.span3d_info(0)
+        assert items > 0 and 2 <= cols <= 5
     u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
     st1 = S.solve(u1)
-    S.set_sweep3d(0)
-    u2 = torch.zeros_like(u1)
-    st2 = S.solve(u2)
-    assert st1["converged"] and st2["converged"]
-    assert torch.equal(u1, u2)
-    np.testing.assert_array_equal(st1["rel"], st2["rel"])
+    assert st1["converged"]
+    variants = [("sweep", 1), ("sweep", 0)]
+    if precision == 1:
+        variants += [("span", (2, 7)), ("span", (3, 32)), ("span", (5, 1)), ("span", (0, 0))]
+    for kind, arg in variants:
+        if kind == "sweep":
+            S.set_sweep3d(arg)
+        else:
+            S.set_sweep3d(2)
+            S.set_span3d(*arg)
+            if arg[0]:
+                assert S.span3d_info(0)[1] == arg[0]
+        u2 = torch.zeros_like(u1)
+        st2 = S.solve(u2)
+        assert st2["converged"], (kind, arg)
+        assert torch.equal(u1, u2), (kind, arg)
+        np.testing.assert_array_equal(st1["rel"], st2["rel"])

@@ -1,5 +1,5 @@
-"""CPU emulations of the two 3D interior-sweep kernels (k_rb_zmarch,
-k_rb_stream3d): the same work items, the same pipelines of planes (ring
+"""CPU emulations of the three 3D interior-sweep kernels (k_rb_zmarch,
+k_rb_stream3d, k_rb_span3d): the same work items, the same pipelines of planes (ring
 slots, loads issued ahead, register rotations), the same per-lane and
 per-warp indexing, the same shuffles at the warp edges and the same clamped
 or zero-filled loads outside the box.  Each must give bitwise the result of
@@ -50,6 +50,19 @@ def red_black_in_place(u, f, T, h2):
                 continue
             nb = (((u[i, j, k - 1] + u[i, j, k + 1]) + u[i - 1, j, k]) + u[i + 1, j, k]) + (u[i, j - 1, k] + u[i, j + 1, k])
             u[i, j, k] = (np.float32(h2) * f[i, j, k] + nb) * np.float32(1 / 6)
+    return u
+
+
+def red_black_in_place_fast(u, f, T, h2):
+    """The same in-place sweep vectorised per colour (nodes of one colour are
+    not neighbours of each other), the same sums in the same order."""
+    u = u.copy()
+    I, J, K = np.nonzero(T == 1)
+    for colour in (0, 1):
+        m = (I + J + K) % 2 == colour
+        i, j, k = I[m], J[m], K[m]
+        nb = (((u[i, j, k - 1] + u[i, j, k + 1]) + u[i - 1, j, k]) + u[i + 1, j, k]) + (u[i, j - 1, k] + u[i, j + 1, k])
+        u[i, j, k] = (np.float32(h2) * f[i, j, k] + nb) * np.float32(1 / 6)
     return u
 
 
@@ -191,6 +204,158 @@ def emulate_stream3d(u, f, T, h2, TY=12, W=28):
     return out, written
 
 
+def row_spans(T):
+    """Per (plane, row): the span of the unknowns and of the inside nodes
+    (lo, hi; lo > hi when empty), and whether the inside nodes are one
+    interval."""
+    n = T.shape[0]
+    kind = T & 3
+    kk = np.arange(n)
+    unk, ins = (kind == 1) | (kind == 2), kind == 1
+    lo, hi = np.where(unk, kk, n).min(-1), np.where(unk, kk, -1).max(-1)
+    ilo, ihi = np.where(ins, kk, n).min(-1), np.where(ins, kk, -1).max(-1)
+    cnt = ins.sum(-1)
+    simple = bool(((cnt == 0) | (cnt == ihi - ilo + 1)).all())
+    return lo, hi, ilo, ihi, simple
+
+
+def span_items(lo, hi, C, J=12, seg=32):
+    """Row blocks of J rows; per block the runs of planes with unknowns (gaps
+    of up to 2 idle planes merged) cut into at most seg planes; per piece the
+    windows k0 = kmin - 1 + m (32 C - 2) covering [kmin, kmax]."""
+    n = lo.shape[0]
+    W = 32 * C - 2
+    out = []
+    for jb in range((n + J - 1) // J):
+        rs = slice(jb * J, min(n, jb * J + J))
+        l = np.where(lo[:, rs] <= hi[:, rs], lo[:, rs], n).min(1)
+        h = np.where(lo[:, rs] <= hi[:, rs], hi[:, rs], -1).max(1)
+        act = l <= h
+        i = 0
+        while i < n:
+            if not act[i]:
+                i += 1
+                continue
+            end = i + 1
+            for k in range(end, n):
+                if act[k]:
+                    end = k + 1
+                elif k - end >= 2:
+                    break
+            for s0 in range(i, end, seg):
+                s1 = min(end, s0 + seg)
+                kmin, kmax = l[s0:s1][act[s0:s1]].min(), h[s0:s1][act[s0:s1]].max()
+                k0 = kmin - 1
+                while k0 + 1 <= kmax:
+                    out.append((jb, k0, s0, s1))
+                    k0 += W
+            i = end
+    return out
+
+
+def emulate_span3d(u, f, T, h2, C, J=12):
+    n = u.shape[0]
+    NW = J + 4
+    lo, hi, ilo, ihi, simple = row_spans(T)
+    assert simple
+    out, written = np.zeros_like(u), np.zeros(u.shape, int)
+    wv = np.arange(NW)[:, None, None]
+    cv = np.arange(C)[None, :, None]
+    lv = np.arange(32)[None, None, :]
+    sixth, h2 = np.float32(1 / 6), np.float32(h2)
+    for (jb, k0, a, b) in span_items(lo, hi, C, J):
+        r0 = jb * J
+        row = r0 - 2 + wv                      # (NW, 1, 1)
+        k = k0 + lv + 32 * cv                  # (1, C, 32)
+        rok = (row >= 0) & (row < n)
+        rowc = np.clip(row, 0, n - 1)
+        redrow = (wv >= 1) & (wv <= NW - 2)
+        owner = (wv >= 2) & (wv <= NW - 3)
+        par = (row + k0 + lv) & 1
+        own = ~(((lv == 0) & (cv == 0)) | ((lv == 31) & (cv == C - 1)))
+
+        def meta(p):   # spans of the CTA's rows in plane p (empty outside the box)
+            if p < 0 or p >= n:
+                e = np.full((NW, 1, 1), 0xFFFF), np.zeros((NW, 1, 1), int)
+                return e + e
+            m = [x[p, rowc[:, 0, 0]].reshape(NW, 1, 1) for x in (lo, hi, ilo, ihi)]
+            return [np.where(rok, m[0], 0xFFFF), np.where(rok, m[1], 0),
+                    np.where(rok, m[2], 0xFFFF), np.where(rok, m[3], 0)]
+
+        def has(l_, h_, kk):
+            return (kk >= l_) & (kk <= h_)
+
+        def ld_u(p):
+            l_, h_, _, _ = meta(p)
+            pc = min(max(p, 0), n - 1)
+            x = np.where(has(l_, h_, k), u[pc, rowc, np.clip(k, 0, n - 1)], 0).astype(np.float32)
+            ke = np.where(np.arange(32) == 31, k0 - 1, k0 + 32 * C)[None, :]
+            me = ((np.arange(32) == 0) | (np.arange(32) == 31))[None, :] & has(l_[:, 0], h_[:, 0], ke)
+            e = np.where(me, u[pc, rowc[:, 0], np.clip(ke, 0, n - 1)], 0).astype(np.float32)
+            return [x, e]
+
+        def ld_f(p):
+            _, _, l_, h_ = meta(p)
+            pc = min(max(p, 0), n - 1)
+            m = redrow & has(l_, h_, k)
+            return np.where(m, f[pc, rowc, np.clip(k, 0, n - 1)], 0).astype(np.float32)
+
+        def shl(x, e):   # __shfl_sync(., lane - 1) of the kernel's source values
+            s = x.copy()
+            for c in range(C):
+                s[:, c, 31] = e[:, 31] if c == 0 else x[:, c - 1, 31]
+            return np.roll(s, 1, axis=2)
+
+        def shr(x, e):   # __shfl_sync(., lane + 1)
+            s = x.copy()
+            for c in range(C):
+                s[:, c, 0] = e[:, 0] if c == C - 1 else x[:, c + 1, 0]
+            return np.roll(s, -1, axis=2)
+
+        def rows(x):     # the rows of the adjacent warps (0 beyond the CTA)
+            z = np.zeros_like(x[:1])
+            return np.concatenate([z, x[:-1]], 0), np.concatenate([x[1:], z], 0)
+
+        zero = np.zeros((NW, C, 32), np.float32)
+        om = ld_u(a - 2)[0]
+        oc, op = ld_u(a - 1), ld_u(a)
+        uq = [ld_u(a + 1 + s) if a + 1 + s <= b + 1 else [zero, np.zeros((NW, 32), np.float32)] for s in range(3)]
+        hm, hc = zero, zero
+        fc, fm = ld_f(a - 1), zero
+        fq = [ld_f(a + s) if a + s <= b else zero for s in range(3)]
+        j, s = a - 1, 0
+        while True:
+            _, _, il, ih = meta(j)
+            red = ((j + par) & 1) == 0
+            ozm, ozp = shl(*oc), shr(*oc)
+            oym, oyp = rows(oc[0])
+            upd = (h2 * fc + ((((ozm + ozp) + om) + op[0]) + (oym + oyp))) * sixth
+            hn = np.where(redrow & red & has(il, ih, k), upd, oc[0]).astype(np.float32)
+            if j - 1 >= a:
+                ul, uh, il1, ih1 = meta(j - 1)
+                ez = np.zeros((NW, 32), np.float32)
+                hzm, hzp = shl(hc, ez), shr(hc, ez)
+                hym, hyp = rows(hc)
+                upd = (h2 * fm + ((((hzm + hzp) + hm) + hn) + (hym + hyp))) * sixth
+                val = np.where(red & has(il1, ih1, k), upd, hc).astype(np.float32)
+                st = owner & own & has(ul, uh, k) & np.ones((NW, C, 32), bool)
+                wi, ci, li = np.nonzero(st)
+                rr, kk = (r0 - 2 + wi), (k0 + li + 32 * ci)
+                out[j - 1, rr, kk] = val[wi, ci, li]
+                written[j - 1, rr, kk] += 1
+            om, oc, op = oc[0], op, uq[s]
+            hm, hc = hc, hn
+            fm, fc = fc, fq[s]
+            if j + 5 <= b + 1:
+                uq[s] = ld_u(j + 5)
+            if j + 4 <= b:
+                fq[s] = ld_f(j + 4)
+            j, s = j + 1, (s + 1) % 3
+            if j > b:
+                break
+    return out, written
+
+
 def _problem(n):
     T = oracle.Oracle(inputs.torus().phi_grid(n), 9).types(0).astype(np.int64)
     rng = np.random.default_rng(0)
@@ -199,12 +364,30 @@ def _problem(n):
     return u, f, T, (2.0 / (n - 1)) ** 2
 
 
-@pytest.mark.parametrize("kernel,n", [("stream3d", 33), ("stream3d", 65), ("zmarch", 65)])
+@pytest.mark.parametrize("kernel,n", [("stream3d", 33), ("stream3d", 65), ("zmarch", 65),
+                                      ("span3d-2", 65), ("span3d-3", 65), ("span3d-5", 33)])
 def test_sweep_kernel_emulation_equals_red_black_in_place(kernel, n):
     u, f, T, h2 = _problem(n)
-    emulate = emulate_stream3d if kernel == "stream3d" else emulate_zmarch
-    out, written = emulate(u, f, T, h2)
+    if kernel.startswith("span3d"):
+        out, written = emulate_span3d(u, f, T, h2, int(kernel[-1]))
+    else:
+        emulate = emulate_stream3d if kernel == "stream3d" else emulate_zmarch
+        out, written = emulate(u, f, T, h2)
     ref = red_black_in_place(u, f, T, h2)
+    unk = T > 0
+    assert (written[unk] == 1).all() and written.max() <= 1
+    assert np.array_equal(out[unk], ref[unk])
+
+
+def test_span3d_emulation_with_several_windows_a_row():
+    """At 257^3 a row's unknowns span 67 nodes: with 2 columns a lane (62
+    owned nodes a window) the blocks need two windows side by side."""
+    u, f, T, h2 = _problem(257)
+    lo, hi, _, _, _ = row_spans(T)
+    it = span_items(lo, hi, 2)
+    assert len({(jb, a) for (jb, _, a, _) in it}) < len(it)   # some piece has two windows
+    out, written = emulate_span3d(u, f, T, h2, 2)
+    ref = red_black_in_place_fast(u, f, T, h2)
     unk = T > 0
     assert (written[unk] == 1).all() and written.max() <= 1
     assert np.array_equal(out[unk], ref[unk])
