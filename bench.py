@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--batch-profile", action="store_true",
                     help="after the batch measurement, one more batch solve as plain launches between "
                          "profiler start and stop (for ncu --profile-from-start off)")
+    ap.add_argument("--sweep3d", type=int, default=-1,
+                    help="3D interior sweep kernel (gcmg_set_sweep3d; -1: the library's default)")
     ap.add_argument("--fp64", type=int, default=1,
                     help="time the plain FP64 solve of the workload beside the mixed form (1) or not (0)")
     ap.add_argument("--profile-solve", action="store_true",
@@ -475,6 +477,8 @@ def secondary(name, rtol, precision, args, stream, flush):
         t0 = time.perf_counter()
         S = gcmg.Solver(P.phi_grid(n), nc, stream=stream, precision=prec, gamma=args.gamma, rtol=rtol,
                         max_cycles=256)
+        if P.dim == 3 and SWEEP3D >= 0:
+            S.set_sweep3d(SWEEP3D)
         for l in range(S.nlev):
             S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
         G = S.ghosts(0)
@@ -515,7 +519,7 @@ def secondary(name, rtol, precision, args, stream, flush):
                 alg = kbytes / kl if kbytes > 0 else (24 if prec == 0 else 12) * n_in
                 gbs = alg / (kms / kl / 1e3) / 1e9
                 peak = measured_peaks()[0].get("hbm_gbs")
-                kernel = ("k_rb_stream3d (red + black 7-point sweep, one pass)" if P.dim == 3 else
+                kernel = (sweep3d_kernel(prec)[1] if P.dim == 3 else
                           "k_rb_fused2d" if prec == 0 or kbytes <= 0 else
                           "k_relax2d (interior sweep + ghost and band sweeps)")
                 rec["fine_sweep"] = {"kernel": kernel, "alg_bytes_per_launch": alg,
@@ -528,11 +532,31 @@ def secondary(name, rtol, precision, args, stream, flush):
     return out
 
 
+SWEEP3D = -1   # --sweep3d
+
+
+def sweep3d_kernel(precision):
+    """Key and description of the 3D fine-level interior sweep that runs."""
+    mode = 2 if SWEEP3D < 0 else SWEEP3D
+    if mode == 2 and precision == 0:
+        mode = 1   # the row-span kernel is FP32 only
+    return {0: ("zmarch", "k_rb_zmarch (fine level: red + black 7-point sweep in one pass, planes staged in "
+                          "shared memory)"),
+            1: ("stream3d", "k_rb_stream3d (fine level: red + black 7-point sweep in one pass, tiles marching "
+                            "along axis 0 with the planes in registers)"),
+            2: ("span3d", "k_rb_span3d (fine level: red + black 7-point sweep in one pass, windows covering each "
+                          "row's unknowns, planes in registers)"),
+            3: ("rows", "k_rb_rows x 2 (fine level: the red then the black half-sweep in place, a warp a row "
+                        "holding inside nodes; one sweep = two launches, timed together)")}[mode]
+
+
 def make_solver(P, n, nc, stream, precision, gamma, rtol, **kw):
     import torch
     from paper_1111_0983_gb300 import gcmg
     S = gcmg.Solver(P.phi_grid(n), nc, stream=stream, precision=precision, gamma=gamma, rtol=rtol,
                     max_cycles=256, **kw)
+    if P.dim == 3 and SWEEP3D >= 0:
+        S.set_sweep3d(SWEEP3D)
     for l in range(S.nlev):
         S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
     G = S.ghosts(0)
@@ -726,12 +750,10 @@ def run_gcmg(args):
     avg_ms = k_ms / max(k_launches, 1)
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if k_launches else None
     merged = P.dim == 2 and precision == 1 and b_launches > 0
-    kern = ("relax2d" if merged else "fused2d") if P.dim == 2 else "zmarch"   # 3D: k_rb_stream3d
+    kern = ("relax2d" if merged else "fused2d") if P.dim == 2 else sweep3d_kernel(precision)[0]
     kname = f"rb_{kern}_{'f64' if precision == 0 else 'f32'}_{args.config}"
     kdesc = {"relax2d": "k_relax2d (fine level: interior sweep + ghost and band sweeps in one launch)",
-             "fused2d": "k_rb_fused2d (fine level, red + black sweep)",
-             "zmarch": "k_rb_stream3d (fine level: red + black 7-point sweep in one pass, tiles marching along "
-                       "axis 0 with the planes in registers)"}[kern]
+             "fused2d": "k_rb_fused2d (fine level, red + black sweep)"}.get(kern) or sweep3d_kernel(precision)[1]
     sweep = {"bound": "hbm", "kernel": kdesc, "achieved": achieved,
              "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
              "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),
@@ -842,7 +864,9 @@ def run_gcmg(args):
 
 
 def main():
+    global SWEEP3D
     args = parse()
+    SWEEP3D = args.sweep3d
     if args.write_traffic:
         write_traffic(*args.write_traffic)
         return

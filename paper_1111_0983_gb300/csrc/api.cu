@@ -175,6 +175,10 @@ void upload_geometry(gcmg_ctx *c, int l) {
         g.sp = upload<int32_t>(c, L.sp.data(), L.sp.size());
         g.sp_rows = upload<int32_t>(c, L.sp_rows.data(), L.sp_rows.size());
     }
+    if (!L.sp_list.empty()) {
+        g.nspl = (int)(L.sp_list.size() / 2);
+        g.sp_list = upload<int32_t>(c, L.sp_list.data(), L.sp_list.size());
+    }
     if (!L.chunk.empty()) {
         g.nchunks = (int64_t)L.chunk.size();
         g.chunks = upload<int32_t>(c, L.chunk.data(), L.chunk.size());
@@ -367,13 +371,14 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         // 3D: both colours in one pass over the active tiles (reads v.u, writes out)
         const double bytes = c->timing_kind >= 0 ? 3.0 * (double)c->H[l].n_in * sizeof(T) : 0.0;
         timer_mark(c, GCMG_KERNEL_SMOOTH, l, bytes);
-        bool done = false;
+        bool done = false, in_place = false;
+        if (c->sweep3d == 3) done = in_place = launch_rb_rows<T>(v, g, c->stream);
         if constexpr (std::is_same<T, float>::value)
-            if (c->sweep3d == 2) done = launch_rb_span3d(v, out, g, c->stream);
+            if (!done && c->sweep3d == 2) done = launch_rb_span3d(v, out, g, c->stream);
         if (!done && c->sweep3d >= 1 && g.nsr > 0) launch_rb_stream3d<T>(v, out, g, c->stream);
         else if (!done) launch_rb_zmarch<T>(v, out, g, c->stream);
         timer_mark(c, GCMG_KERNEL_SMOOTH, l);
-        v.u = out;
+        if (!in_place) v.u = out;
     } else {
         for (int colour = 0; colour < 2; colour++) {
             timer_mark(c, GCMG_KERNEL_SMOOTH, l);
@@ -1131,7 +1136,7 @@ gcmg_status gcmg_set_boundary3d(gcmg_ctx *c, int mode) {
 }
 
 gcmg_status gcmg_set_sweep3d(gcmg_ctx *c, int variant) {
-    if (!c || variant < 0 || variant > 2) return fail(c, GCMG_E_ARG, "bad argument");
+    if (!c || variant < 0 || variant > 3) return fail(c, GCMG_E_ARG, "bad argument");
     destroy_graph(c);
     c->sweep3d = variant;
     return GCMG_OK;
@@ -1152,7 +1157,10 @@ gcmg_status gcmg_set_span3d(gcmg_ctx *c, int columns, int planes) {
             build_span_items(L, columns, planes);
             g.nsp = 0;
             g.sp_cols = 0;
+            g.nspl = 0;
             if (L.sp.empty()) continue;
+            g.sp_list = upload<int32_t>(c, L.sp_list.data(), L.sp_list.size());
+            g.nspl = (int)(L.sp_list.size() / 2);
             g.sp_cols = L.sp_cols;
             g.sp = upload<int32_t>(c, L.sp.data(), L.sp.size());
             g.sp_rows = upload<int32_t>(c, L.sp_rows.data(), L.sp_rows.size());

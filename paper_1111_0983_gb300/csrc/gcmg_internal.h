@@ -109,6 +109,9 @@ struct HostLevel {
     // interval (the sweep then falls back to the tiles).
     std::vector<int32_t> sp_rows, sp;
     int sp_cols = 0;
+    // the rows holding inside nodes, as pairs (i * n + j, inside span), in
+    // increasing i * n + j: the work of the one-colour row sweep
+    std::vector<int32_t> sp_list;
     // defect extension of this level (before restricting to the next coarser one)
     std::vector<int32_t> ext_node;      // ordered by upwind wavefront
     std::vector<uint8_t> ext_cnt;
@@ -214,6 +217,8 @@ struct DevGeom {
     int nsp = 0, sp_cols = 0;    // row-span sweep items (HostLevel::sp quadruples), columns a lane
     int32_t *sp = nullptr;
     int32_t *sp_rows = nullptr;  // HostLevel::sp_rows
+    int nspl = 0;                // rows of the one-colour row sweep (HostLevel::sp_list pairs)
+    int32_t *sp_list = nullptr;
     int64_t nchunks = 0;         // 3D active chunks (HostLevel::chunk)
     int32_t *chunks = nullptr;
     uint8_t *chunk_len = nullptr;

@@ -552,6 +552,35 @@ __global__ void __launch_bounds__(SP_NW * 32, 1)
     }
 }
 
+// -------------------------------- 3D one-colour sweep over rows, in place
+// One colour of the red-black interior sweep (Eq. jac2d, Sec. 2.4) over the
+// rows that hold inside nodes: a warp a row (i, j), lane l the nodes of the
+// colour at k = k_first + 2 l + 64 m inside the row's inside span, in place
+// (the neighbours of a node are of the other colour, which this launch does
+// not write).  A launch reads u on the rows' spans and their neighbour rows
+// and f on the colour's nodes, and writes the colour's nodes; the black
+// launch right after the red one finds most of them in L2.  The same sums in
+// the same order as the fused sweeps.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rb_rows(LevelView<T> v, const int2 *__restrict__ rows, int nrows, int colour) {
+    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    int2 r = make_int2(0, 0x0000ffff);   // an empty span past the list
+    if (wid < nrows) r = rows[wid];      // set up once: read before the wait
+    pdl_wait();
+    const int n = v.n;
+    const int i = r.x / n, j = r.x - (r.x / n) * n;
+    const int lo = r.y & 0xffff, hi = (int)((unsigned)r.y >> 16);
+    const int64_t base = (int64_t)r.x * n, s0 = v.s0;
+    const T h2 = v.h2, sixth = (T)(1.0 / 6.0);
+    T *u = v.u;
+    const T *__restrict__ f = v.f;
+    for (int k = lo + ((i + j + lo + colour) & 1) + 2 * lane; k <= hi; k += 64) {
+        const int64_t p = base + k;
+        const T nb = (((u[p - 1] + u[p + 1]) + u[p - s0]) + u[p + s0]) + (u[p - n] + u[p + n]);
+        u[p] = (mul_rn(h2, f[p]) + nb) * sixth;
+    }
+}
+
 // ------------------------------------------- 3D boundary phase in one launch
 // Grid-wide barrier for k_boundary3d, whose CTAs are all resident at once
 // (the grid is sized by the kernel's occupancy and the launch does not
@@ -1134,6 +1163,18 @@ bool launch_rb_span3d(const LevelView<float> &v, float *out, const DevGeom &g, c
 }
 
 template <typename T>
+bool launch_rb_rows(const LevelView<T> &v, const DevGeom &g, cudaStream_t s) {
+    if (g.nspl <= 0) return false;
+    const unsigned blocks = (unsigned)(((int64_t)g.nspl * 32 + 255) / 256);
+    for (int colour = 0; colour < 2; colour++) {
+        pdl_launch(k_rb_rows<T>, dim3(blocks), dim3(256), 0, s, v, reinterpret_cast<const int2 *>(g.sp_list),
+                   g.nspl, colour);
+        g_launches++;
+    }
+    return true;
+}
+
+template <typename T>
 void launch_rb_zmarch(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s) {
     if (g.nzm <= 0) return;
     constexpr size_t smem = zmarch_smem_bytes<T>();
@@ -1455,6 +1496,7 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
     template void launch_rb_zmarch<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);    \
     template void launch_rb_stream3d<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);  \
+    template bool launch_rb_rows<T>(const LevelView<T> &, const DevGeom &, cudaStream_t);           \
     template bool launch_boundary3d<T>(const LevelView<T> &, BoundaryProgram3, int, cudaStream_t);  \
     template bool launch_boundary3d_cluster<T>(const LevelView<T> &, const BoundaryProgram3 &, cudaStream_t); \
     template size_t local_smem_bytes<T>(const LocalView<T> &, int, bool);                                 \

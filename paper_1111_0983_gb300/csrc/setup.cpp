@@ -958,6 +958,7 @@ static void span_items_for(const HostLevel &L, int C, int seg, std::vector<int32
 bool build_span_items(HostLevel &L, int C, int seg) {
     L.sp.clear();
     L.sp_rows.clear();
+    L.sp_list.clear();
     L.sp_cols = 0;
     if (L.dim != 3 || L.n > 0xfffe) return false;
     const int n = L.n;
@@ -981,10 +982,15 @@ bool build_span_items(HostLevel &L, int C, int seg) {
         }
         if (cnt > 0 && cnt != ihi - ilo + 1) {   // inside nodes not one interval
             L.sp_rows.clear();
+            L.sp_list.clear();
             return false;
         }
         if (hi >= lo) L.sp_rows[2 * r] = (int32_t)((uint32_t)lo | ((uint32_t)hi << 16));
-        if (ihi >= ilo) L.sp_rows[2 * r + 1] = (int32_t)((uint32_t)ilo | ((uint32_t)ihi << 16));
+        if (ihi >= ilo) {
+            L.sp_rows[2 * r + 1] = (int32_t)((uint32_t)ilo | ((uint32_t)ihi << 16));
+            L.sp_list.push_back((int32_t)r);
+            L.sp_list.push_back(L.sp_rows[2 * r + 1]);
+        }
     }
     // C: the fewest lane-node steps, counting a warp's fixed work per plane
     // (metadata, barrier, loop) as 1.25 columns and an item's pipeline fill

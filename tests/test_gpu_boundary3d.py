@@ -92,7 +92,7 @@ def test_sweep_kernels_agree_bitwise(precision, n):
     u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
     st1 = S.solve(u1)
     assert st1["converged"]
-    variants = [("sweep", 1), ("sweep", 0)]
+    variants = [("sweep", 1), ("sweep", 0), ("sweep", 3)]
     if precision == 1:
         variants += [("span", (2, 7)), ("span", (3, 32)), ("span", (5, 1)), ("span", (0, 0))]
     for kind, arg in variants:
