@@ -537,7 +537,7 @@ SWEEP3D = -1   # --sweep3d
 
 def sweep3d_kernel(precision):
     """Key and description of the 3D fine-level interior sweep that runs."""
-    mode = 2 if SWEEP3D < 0 else SWEEP3D
+    mode = 3 if SWEEP3D < 0 else SWEEP3D
     if mode == 2 and precision == 0:
         mode = 1   # the row-span kernel is FP32 only
     return {0: ("zmarch", "k_rb_zmarch (fine level: red + black 7-point sweep in one pass, planes staged in "
@@ -546,8 +546,8 @@ def sweep3d_kernel(precision):
                             "along axis 0 with the planes in registers)"),
             2: ("span3d", "k_rb_span3d (fine level: red + black 7-point sweep in one pass, windows covering each "
                           "row's unknowns, planes in registers)"),
-            3: ("rows", "k_rb_rows x 2 (fine level: the red then the black half-sweep in place, a warp a row "
-                        "holding inside nodes; one sweep = two launches, timed together)")}[mode]
+            3: ("rows", "k_rb_rows x 2 (fine level: the red then the black half-sweep in place over 64-node "
+                        "segments of the rows holding inside nodes; one sweep = two launches, timed together)")}[mode]
 
 
 def make_solver(P, n, nc, stream, precision, gamma, rtol, **kw):

@@ -339,13 +339,13 @@ gcmg_status gcmg_debug_barrier(gcmg_ctx *ctx, int enable, int phantom_blocks, un
 /* Kernel of the 3D interior sweep (red and black in one pass over the active
  * tiles, Eq. jac2d): 0 tiles of 16 x 64 nodes with the planes staged in
  * shared memory; 1 tiles of 12 x 28 nodes with the planes in registers, a
- * warp a row; 2 (default) blocks of 12 rows whose window along the
+ * warp a row; 2 blocks of 12 rows whose window along the
  * contiguous axis covers the rows' unknowns, reading and writing only the
  * spans of unknowns of each row (FP32 cycles; FP64 cycles and levels whose
- * rows hold more than one interval of inside nodes use 1); 3 the red and
- * the black half-sweeps as two launches in place, a warp a row holding
- * inside nodes (both precisions; the same fallback).  Same results bitwise.
- * Not in the paper. */
+ * rows hold more than one interval of inside nodes use 1); 3 (default)
+ * the red and the black half-sweeps as two launches in place over segments
+ * of up to 64 inside nodes of a row (both precisions, any domain).  Same
+ * results bitwise.  Not in the paper. */
 gcmg_status gcmg_set_sweep3d(gcmg_ctx *ctx, int variant);
 
 /* Rebuilds the work items of sweep 2 on every 3D level: `columns` nodes a

@@ -1157,10 +1157,7 @@ gcmg_status gcmg_set_span3d(gcmg_ctx *c, int columns, int planes) {
             build_span_items(L, columns, planes);
             g.nsp = 0;
             g.sp_cols = 0;
-            g.nspl = 0;
             if (L.sp.empty()) continue;
-            g.sp_list = upload<int32_t>(c, L.sp_list.data(), L.sp_list.size());
-            g.nspl = (int)(L.sp_list.size() / 2);
             g.sp_cols = L.sp_cols;
             g.sp = upload<int32_t>(c, L.sp.data(), L.sp.size());
             g.sp_rows = upload<int32_t>(c, L.sp_rows.data(), L.sp_rows.size());

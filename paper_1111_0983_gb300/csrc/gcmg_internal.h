@@ -109,8 +109,9 @@ struct HostLevel {
     // interval (the sweep then falls back to the tiles).
     std::vector<int32_t> sp_rows, sp;
     int sp_cols = 0;
-    // the rows holding inside nodes, as pairs (i * n + j, inside span), in
-    // increasing i * n + j: the work of the one-colour row sweep
+    // segments of up to 64 consecutive inside nodes of a row, as pairs
+    // (i * n + j, first | last << 16), in increasing node order: the work of
+    // the one-colour row sweep (any domain)
     std::vector<int32_t> sp_list;
     // defect extension of this level (before restricting to the next coarser one)
     std::vector<int32_t> ext_node;      // ordered by upwind wavefront
@@ -217,7 +218,7 @@ struct DevGeom {
     int nsp = 0, sp_cols = 0;    // row-span sweep items (HostLevel::sp quadruples), columns a lane
     int32_t *sp = nullptr;
     int32_t *sp_rows = nullptr;  // HostLevel::sp_rows
-    int nspl = 0;                // rows of the one-colour row sweep (HostLevel::sp_list pairs)
+    int nspl = 0;                // segments of the one-colour row sweep (HostLevel::sp_list pairs)
     int32_t *sp_list = nullptr;
     int64_t nchunks = 0;         // 3D active chunks (HostLevel::chunk)
     int32_t *chunks = nullptr;

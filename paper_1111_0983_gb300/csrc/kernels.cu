@@ -554,30 +554,58 @@ __global__ void __launch_bounds__(SP_NW * 32, 1)
 
 // -------------------------------- 3D one-colour sweep over rows, in place
 // One colour of the red-black interior sweep (Eq. jac2d, Sec. 2.4) over the
-// rows that hold inside nodes: a warp a row (i, j), lane l the nodes of the
-// colour at k = k_first + 2 l + 64 m inside the row's inside span, in place
-// (the neighbours of a node are of the other colour, which this launch does
-// not write).  A launch reads u on the rows' spans and their neighbour rows
-// and f on the colour's nodes, and writes the colour's nodes; the black
-// launch right after the red one finds most of them in L2.  The same sums in
-// the same order as the fused sweeps.
-template <typename T>
-__global__ void __launch_bounds__(256) k_rb_rows(LevelView<T> v, const int2 *__restrict__ rows, int nrows, int colour) {
-    const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    int2 r = make_int2(0, 0x0000ffff);   // an empty span past the list
-    if (wid < nrows) r = rows[wid];      // set up once: read before the wait
+// rows that hold inside nodes, in place (the neighbours of a node are of the
+// other colour, which the launch does not write).  The work is a list of
+// segments, up to 64 consecutive inside nodes of one row (plane i, row j),
+// in plane, row order; a warp takes G segments at once -- lane l the node
+// of the colour at k_first + 2 l of each -- and issues the loads of all of
+// them before the first update, so that G segments cost about one memory
+// round trip; a persistent grid walks the list, prefetching the next group's
+// segments.  The warps running together work on neighbouring rows and
+// share them in L2; the black launch right after the red one finds much of
+// u and f there.  The same sums in the same order as the fused sweeps.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_rb_rows(LevelView<T> v, const int2 *__restrict__ segs, int nseg, int colour) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
+    int2 nx[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) nx[g] = q + g < nseg ? segs[q + g] : make_int2(0, 0x0000ffff);   // static
     pdl_wait();
     const int n = v.n;
-    const int i = r.x / n, j = r.x - (r.x / n) * n;
-    const int lo = r.y & 0xffff, hi = (int)((unsigned)r.y >> 16);
-    const int64_t base = (int64_t)r.x * n, s0 = v.s0;
+    const int64_t s0 = v.s0;
     const T h2 = v.h2, sixth = (T)(1.0 / 6.0);
     T *u = v.u;
     const T *__restrict__ f = v.f;
-    for (int k = lo + ((i + j + lo + colour) & 1) + 2 * lane; k <= hi; k += 64) {
-        const int64_t p = base + k;
-        const T nb = (((u[p - 1] + u[p + 1]) + u[p - s0]) + u[p + s0]) + (u[p - n] + u[p + n]);
-        u[p] = (mul_rn(h2, f[p]) + nb) * sixth;
+    for (; q < nseg; q += nw * G) {
+        int64_t p[G];
+        bool on[G];
+        T zm[G], zp[G], xm[G], xp[G], ym[G], yp[G], fv[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            const int2 sg = nx[g];
+            const int i = sg.x / n, j = sg.x - (sg.x / n) * n;
+            const int k0 = sg.y & 0xffff, k1 = (int)((unsigned)sg.y >> 16);
+            const int k = k0 + ((i + j + k0 + colour) & 1) + 2 * lane;
+            on[g] = k <= k1;
+            p[g] = (int64_t)sg.x * n + k;
+            if (on[g]) {
+                zm[g] = u[p[g] - 1];
+                zp[g] = u[p[g] + 1];
+                xm[g] = u[p[g] - s0];
+                xp[g] = u[p[g] + s0];
+                ym[g] = u[p[g] - n];
+                yp[g] = u[p[g] + n];
+                fv[g] = f[p[g]];
+            }
+        }
+        const int qn = q + nw * G;
+#pragma unroll
+        for (int g = 0; g < G; g++) nx[g] = qn + g < nseg ? segs[qn + g] : make_int2(0, 0x0000ffff);
+#pragma unroll
+        for (int g = 0; g < G; g++)
+            if (on[g]) u[p[g]] = (mul_rn(h2, fv[g]) + ((((zm[g] + zp[g]) + xm[g]) + xp[g]) + (ym[g] + yp[g]))) * sixth;
     }
 }
 
@@ -1165,12 +1193,21 @@ bool launch_rb_span3d(const LevelView<float> &v, float *out, const DevGeom &g, c
 template <typename T>
 bool launch_rb_rows(const LevelView<T> &v, const DevGeom &g, cudaStream_t s) {
     if (g.nspl <= 0) return false;
-    const unsigned blocks = (unsigned)(((int64_t)g.nspl * 32 + 255) / 256);
-    for (int colour = 0; colour < 2; colour++) {
-        pdl_launch(k_rb_rows<T>, dim3(blocks), dim3(256), 0, s, v, reinterpret_cast<const int2 *>(g.sp_list),
-                   g.nspl, colour);
-        g_launches++;
+    constexpr int G = 8;   // segments a warp at once (measured at 513^3: 4 -> 60.7 us a sweep, 8 -> 58.5 us)
+    static int resident = 0;   // the persistent grid: CTAs resident on the device
+    if (resident == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rb_rows<T, G>, 256, 0);
+        resident = std::max(1, sms * std::max(per, 1));
     }
+    const int64_t need = ((int64_t)(g.nspl + G - 1) / G * 32 + 255) / 256;
+    const unsigned blocks = (unsigned)std::min<int64_t>(need, resident);
+    const int2 *segs = reinterpret_cast<const int2 *>(g.sp_list);
+    for (int colour = 0; colour < 2; colour++)
+        pdl_launch(k_rb_rows<T, G>, dim3(blocks), dim3(256), 0, s, v, segs, g.nspl, colour);
+    g_launches += 2;
     return true;
 }
 

@@ -87,8 +87,8 @@ void launch_rb_zmarch(const LevelView<T> &v, T *out, const DevGeom &g, cudaStrea
 // the same sweep with the planes in registers (a warp a row, a lane a column)
 template <typename T>
 void launch_rb_stream3d(const LevelView<T> &v, T *out, const DevGeom &g, cudaStream_t s);
-// both colours of the interior sweep as two in-place launches over the rows
-// holding inside nodes; false when the level has no row list
+// both colours of the interior sweep as two in-place launches over segments
+// of the rows holding inside nodes; false when the level has no segment list
 template <typename T>
 bool launch_rb_rows(const LevelView<T> &v, const DevGeom &g, cudaStream_t s);
 // the row-span sweep (FP32); false when the level has no items for it

@@ -955,10 +955,31 @@ static void span_items_for(const HostLevel &L, int C, int seg, std::vector<int32
     }
 }
 
+// Work of the one-colour row sweep: every run of consecutive inside nodes of
+// a row (i, j), cut into segments of at most 64 nodes, in increasing node
+// order.
+static void build_row_segments(HostLevel &L) {
+    const int n = L.n;
+    L.sp_list.clear();
+    for (int64_t r = 0; r < (int64_t)n * n; r++) {
+        const uint8_t *t = &L.type[(size_t)r * n];
+        int k = 0;
+        while (k < n) {
+            if ((t[k] & NODE_KIND) != NODE_IN) { k++; continue; }
+            int e = k;
+            while (e + 1 < n && (t[e + 1] & NODE_KIND) == NODE_IN) e++;
+            for (int k0 = k; k0 <= e; k0 += 64) {
+                L.sp_list.push_back((int32_t)r);
+                L.sp_list.push_back((int32_t)((uint32_t)k0 | ((uint32_t)std::min(e, k0 + 63) << 16)));
+            }
+            k = e + 1;
+        }
+    }
+}
+
 bool build_span_items(HostLevel &L, int C, int seg) {
     L.sp.clear();
     L.sp_rows.clear();
-    L.sp_list.clear();
     L.sp_cols = 0;
     if (L.dim != 3 || L.n > 0xfffe) return false;
     const int n = L.n;
@@ -982,15 +1003,10 @@ bool build_span_items(HostLevel &L, int C, int seg) {
         }
         if (cnt > 0 && cnt != ihi - ilo + 1) {   // inside nodes not one interval
             L.sp_rows.clear();
-            L.sp_list.clear();
             return false;
         }
         if (hi >= lo) L.sp_rows[2 * r] = (int32_t)((uint32_t)lo | ((uint32_t)hi << 16));
-        if (ihi >= ilo) {
-            L.sp_rows[2 * r + 1] = (int32_t)((uint32_t)ilo | ((uint32_t)ihi << 16));
-            L.sp_list.push_back((int32_t)r);
-            L.sp_list.push_back(L.sp_rows[2 * r + 1]);
-        }
+        if (ihi >= ilo) L.sp_rows[2 * r + 1] = (int32_t)((uint32_t)ilo | ((uint32_t)ihi << 16));
     }
     // C: the fewest lane-node steps, counting a warp's fixed work per plane
     // (metadata, barrier, loop) as 1.25 columns and an item's pipeline fill
@@ -1079,6 +1095,7 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
         } else if (L.nn < ((int64_t)1 << 31)) {
             build_zmarch_items(L);
             build_span_items(L);
+            if (L.n <= 0xfffe) build_row_segments(L);
             // active chunks: CHUNK-node runs of a row holding an inside node or a ghost
             for (int64_t row = 0; row < L.nn; row += L.n)
                 for (int z0 = 0; z0 < L.n; z0 += CHUNK) {

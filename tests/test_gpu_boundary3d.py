@@ -81,10 +81,11 @@ def test_barrier_wait_runs_out_and_context_stays_usable():
 
 @pytest.mark.parametrize("precision,n", [(0, 65), (1, 129), (1, 257)])
 def test_sweep_kernels_agree_bitwise(precision, n):
-    """The 3D interior sweeps -- row spans (the FP32 default), the planes in
-    registers (the FP64 default) and the planes staged in shared memory --
-    compute the same sums in the same order: bitwise equal solves, also with
-    the row-span items rebuilt for every lane width and for short items."""
+    """The 3D interior sweeps -- the two one-colour launches over row
+    segments (the default), the fused sweep over row spans (FP32), the planes
+    in registers and the planes staged in shared memory -- compute the same
+    sums in the same order: bitwise equal solves, also with the row-span items
+    rebuilt for every lane width and for short items."""
     S = _solver(precision, n)
     if precision == 1:
         items, cols = S.span3d_info(0)
@@ -92,7 +93,7 @@ def test_sweep_kernels_agree_bitwise(precision, n):
     u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
     st1 = S.solve(u1)
     assert st1["converged"]
-    variants = [("sweep", 1), ("sweep", 0), ("sweep", 3)]
+    variants = [("sweep", 1), ("sweep", 0), ("sweep", 2)]
     if precision == 1:
         variants += [("span", (2, 7)), ("span", (3, 32)), ("span", (5, 1)), ("span", (0, 0))]
     for kind, arg in variants:

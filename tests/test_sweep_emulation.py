@@ -391,3 +391,62 @@ def test_span3d_emulation_with_several_windows_a_row():
     unk = T > 0
     assert (written[unk] == 1).all() and written.max() <= 1
     assert np.array_equal(out[unk], ref[unk])
+
+
+def row_segments(T):
+    """Runs of consecutive inside nodes of every row (i, j), cut into
+    segments of at most 64 nodes: (i * n + j, first, last)."""
+    n = T.shape[0]
+    ins = (T & 3) == 1
+    out = []
+    for r in np.nonzero(ins.reshape(n * n, n).any(-1))[0]:
+        row = ins.reshape(n * n, n)[r]
+        k = 0
+        while k < n:
+            if not row[k]:
+                k += 1
+                continue
+            e = k
+            while e + 1 < n and row[e + 1]:
+                e += 1
+            for k0 in range(k, e + 1, 64):
+                out.append((r, k0, min(e, k0 + 63)))
+            k = e + 1
+    return out
+
+
+def emulate_rows(u, f, T, h2):
+    """k_rb_rows: the red launch then the black one, in place; per segment
+    lane l updates the node of the colour at k_first + 2 l."""
+    n = u.shape[0]
+    u = u.copy().ravel()
+    ff = f.ravel()
+    s0 = n * n
+    written = np.zeros(u.shape, int)
+    segs = row_segments(T)
+    lane = np.arange(32)
+    for colour in (0, 1):
+        for (r, k0, k1) in segs:
+            i, j = divmod(r, n)
+            k = k0 + ((i + j + k0 + colour) & 1) + 2 * lane
+            k = k[k <= k1]
+            p = r * n + k
+            nb = (((u[p - 1] + u[p + 1]) + u[p - s0]) + u[p + s0]) + (u[p - n] + u[p + n])
+            u[p] = (np.float32(h2) * ff[p] + nb) * np.float32(1 / 6)
+            written[p] += 1
+    return u.reshape(T.shape), written.reshape(T.shape)
+
+
+@pytest.mark.parametrize("n,turn", [(33, False), (129, False), (65, True)])
+def test_row_segment_sweep_emulation_equals_red_black_in_place(n, turn):
+    """turn: the torus with its axis along axis 0, so that a row crosses the
+    ring twice (two runs of inside nodes)."""
+    u, f, T, h2 = _problem(n)
+    if turn:
+        u, f, T = (np.ascontiguousarray(x.transpose(2, 1, 0)) for x in (u, f, T))
+        assert len(row_segments(T)) > len({r for (r, _, _) in row_segments(T)})
+    out, written = emulate_rows(u, f, T, h2)
+    ref = red_black_in_place_fast(u, f, T, h2)
+    ins = (T & 3) == 1
+    assert (written[ins] == 1).all() and (written[~ins] == 0).all()
+    assert np.array_equal(out, ref)
