@@ -79,6 +79,8 @@ def parse():
                          "profiler start and stop (for ncu --profile-from-start off)")
     ap.add_argument("--sweep3d", type=int, default=-1,
                     help="3D interior sweep kernel (gcmg_set_sweep3d; -1: the library's default)")
+    ap.add_argument("--boundary3d", type=int, default=-1,
+                    help="3D boundary relaxation launch mode (gcmg_set_boundary3d; -1: the library's default)")
     ap.add_argument("--fp64", type=int, default=1,
                     help="time the plain FP64 solve of the workload beside the mixed form (1) or not (0)")
     ap.add_argument("--profile-solve", action="store_true",
@@ -479,6 +481,8 @@ def secondary(name, rtol, precision, args, stream, flush):
                         max_cycles=256)
         if P.dim == 3 and SWEEP3D >= 0:
             S.set_sweep3d(SWEEP3D)
+        if P.dim == 3 and BOUNDARY3D >= 0:
+            S.set_boundary3d(BOUNDARY3D)
         for l in range(S.nlev):
             S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
         G = S.ghosts(0)
@@ -533,6 +537,7 @@ def secondary(name, rtol, precision, args, stream, flush):
 
 
 SWEEP3D = -1   # --sweep3d
+BOUNDARY3D = -1   # --boundary3d
 
 
 def sweep3d_kernel(precision):
@@ -557,6 +562,8 @@ def make_solver(P, n, nc, stream, precision, gamma, rtol, **kw):
                     max_cycles=256, **kw)
     if P.dim == 3 and SWEEP3D >= 0:
         S.set_sweep3d(SWEEP3D)
+    if P.dim == 3 and BOUNDARY3D >= 0:
+        S.set_boundary3d(BOUNDARY3D)
     for l in range(S.nlev):
         S.set_bc_types(l, P.bc_types(S.ghosts(l)["B"]))
     G = S.ghosts(0)
@@ -864,9 +871,9 @@ def run_gcmg(args):
 
 
 def main():
-    global SWEEP3D
+    global SWEEP3D, BOUNDARY3D
     args = parse()
-    SWEEP3D = args.sweep3d
+    SWEEP3D, BOUNDARY3D = args.sweep3d, args.boundary3d
     if args.write_traffic:
         write_traffic(*args.write_traffic)
         return

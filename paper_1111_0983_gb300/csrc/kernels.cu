@@ -609,6 +609,38 @@ __global__ void __launch_bounds__(256) k_rb_rows(LevelView<T> v, const int2 *__r
     }
 }
 
+// The defect f + Lap_h u (TGCS step 3) at every inside node of a 3D level
+// into r, over the row segments of the one-colour sweep: a warp takes G
+// segments at once, lane l the nodes k0 + l and k0 + l + 32 of each, all
+// loads issued before the first store.  The expression of defect_node.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, const int2 *__restrict__ segs, int nseg) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int n = v.n;
+    pdl_wait();
+    for (int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; q < nseg; q += nw * G) {
+        T d[2 * G];
+        int64_t p[2 * G];
+        bool on[2 * G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            const int2 sg = q + g < nseg ? segs[q + g] : make_int2(0, 0x0000ffff);
+            const int k0 = sg.y & 0xffff, k1 = (int)((unsigned)sg.y >> 16);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int k = k0 + lane + 32 * h;
+                on[2 * g + h] = k <= k1;
+                p[2 * g + h] = (int64_t)sg.x * n + k;
+                if (on[2 * g + h]) d[2 * g + h] = inside_defect<T, 3>(v, p[2 * g + h]);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 2 * G; e++)
+            if (on[e]) v.r[p[e]] = d[e];
+    }
+}
+
 // ------------------------------------------- 3D boundary phase in one launch
 // Grid-wide barrier for k_boundary3d, whose CTAs are all resident at once
 // (the grid is sized by the kernel's occupancy and the launch does not
@@ -849,11 +881,13 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
     // dependents are large FP64 launches whose early CTAs measured slower)
     if (sizeof(T) == 4) pdl_trigger();
     if (D == 3) {
-        // 3D: the coarse nodes only, a thread each (the coarse ghost rows are
-        // summed by k_ghost_rows)
-        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        // 3D: the coarse nodes of the coarse level's active chunks, a thread
+        // each (every unknown is in one; the other nodes keep u = 0 and an f
+        // that nothing reads); the coarse ghost rows are summed by k_ghost_rows
+        int64_t i;
+        const bool has = level_node(C, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, i);
         pdl_wait();
-        if (i < C.nn) descend_node<T, D, FROM_R>(F, C, fc, uc, i);
+        if (has) descend_node<T, D, FROM_R>(F, C, fc, uc, i);
         return;
     }
     if (sizeof(T) == 8) {
@@ -1295,7 +1329,42 @@ template <typename T>
 void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
                     T *uc, cudaStream_t s) {
     const bool warp_rows = sizeof(T) == 4 && gf.dim == 2;   // 2D FP32: a warp per coarse ghost row
-    const int64_t n = gf.dim == 3 ? C.nn : warp_rows ? C.nn + 32 * (int64_t)C.ng : std::max<int64_t>(C.nn, C.ng);
+    const int64_t n = gf.dim == 3 ? level_threads(C, true) : warp_rows ? C.nn + 32 * (int64_t)C.ng
+                                                                      : std::max<int64_t>(C.nn, C.ng);
+    if (gf.dim == 3 && gf.nspl > 0) {
+        // 3D with row segments: one defect pass first (inside nodes over the
+        // segments, then the ghosts), so that each fine defect is computed
+        // once rather than once per coarse node whose 27-node neighbourhood
+        // holds it (27/8 times on average); the same values as on the spot
+        constexpr int G = 4;
+        static int resident = 0;
+        if (resident == 0) {
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_defect_rows<T, G>, 256, 0);
+            resident = std::max(1, sms * std::max(per, 1));
+        }
+        const unsigned blocks =
+            (unsigned)std::min<int64_t>(((int64_t)(gf.nspl + G - 1) / G * 32 + 255) / 256, resident);
+        g_launches++;
+        pdl_launch(k_defect_rows<T, G>, dim3(blocks), dim3(256), 0, s, F, reinterpret_cast<const int2 *>(gf.sp_list),
+                   gf.nspl);
+        if (F.ng > 0) {
+            g_launches++;
+            pdl_launch(k_defect_ghost<T, 27>, dim3(blocks_for(F.ng)), dim3(kThreads), 0, s, F,
+                       (unsigned long long *)nullptr);
+        }
+        if (C.ng > 0) {
+            g_launches++;
+            pdl_launch(k_ghost_rows<T, true>, dim3(blocks_for(32 * (int64_t)C.ng)), dim3(kThreads), 0, s,
+                       (const T *)F.r, F.gnode, gc, gf.gt_ptr, gf.gt_col, gt_val, C.ng);
+        }
+        g_launches++;
+        pdl_launch(k_descend<T, 3, true>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr,
+                   gf.gt_col, gt_val);
+        return;
+    }
     constexpr bool from_r = sizeof(T) == 8;   // FP64: one defect pass first (see descend_item)
     if (from_r) launch_defect<T>(F, gf.dim, false, nullptr, s);
     if (gf.dim == 3 && C.ng > 0) {
