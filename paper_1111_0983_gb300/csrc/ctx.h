@@ -118,6 +118,8 @@ LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
     v.chunks = g.chunks;
     v.clen = g.chunk_len;
     v.nchunks = g.nchunks;
+    v.segs = reinterpret_cast<const int2 *>(g.sp_list);
+    v.nsegs = g.nspl;
     return v;
 }
 

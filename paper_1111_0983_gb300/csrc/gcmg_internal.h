@@ -283,6 +283,9 @@ struct LevelView {
     const int32_t *chunks = nullptr;
     const uint8_t *clen = nullptr;
     int64_t nchunks = 0;
+    // 3D: segments of up to 64 consecutive inside nodes of a row (DevGeom::sp_list)
+    const int2 *segs = nullptr;
+    int nsegs = 0;
 };
 
 // One 3D boundary relaxation as a single launch (k_boundary3d): the Jacobi

@@ -552,6 +552,12 @@ __global__ void __launch_bounds__(SP_NW * 32, 1)
     }
 }
 
+// |v| for a max-norm that keeps NaN visible (as +Inf; fmax would drop it)
+__device__ __forceinline__ double abs_keep_nan(double v) {
+    const double a = fabs(v);
+    return a != a ? __longlong_as_double(0x7ff0000000000000ll) : a;
+}
+
 // -------------------------------- 3D one-colour sweep over rows, in place
 // One colour of the red-black interior sweep (Eq. jac2d, Sec. 2.4) over the
 // rows that hold inside nodes, in place (the neighbours of a node are of the
@@ -610,15 +616,21 @@ __global__ void __launch_bounds__(256) k_rb_rows(LevelView<T> v, const int2 *__r
 }
 
 // The defect f + Lap_h u (TGCS step 3) at every inside node of a 3D level
-// into r, over the row segments of the one-colour sweep: a warp takes G
-// segments at once, lane l the nodes k0 + l and k0 + l + 32 of each, all
-// loads issued before the first store.  The expression of defect_node.
-template <typename T, int G>
-__global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, const int2 *__restrict__ segs, int nseg) {
+// into r, over the row segments: a warp takes G segments at once, lane l the
+// nodes k0 + l and k0 + l + 32 of each, all loads issued before the first
+// store; with norm, its max-norm.  MIXED (the FP64 finest level of the mixed
+// form): also f32 = the defect rounded to FP32 and e32 = 0 at those nodes.
+// The expression of defect_node.
+template <typename T, int G, bool MIXED>
+__global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, unsigned long long *norm, float *__restrict__ f32,
+                                                    float *__restrict__ e32) {
+    if (MIXED) pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-    const int n = v.n;
+    const int n = v.n, nseg = v.nsegs;
+    const int2 *__restrict__ segs = v.segs;
     pdl_wait();
+    double m = 0.0;
     for (int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; q < nseg; q += nw * G) {
         T d[2 * G];
         int64_t p[2 * G];
@@ -637,8 +649,73 @@ __global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, const int2 
         }
 #pragma unroll
         for (int e = 0; e < 2 * G; e++)
-            if (on[e]) v.r[p[e]] = d[e];
+            if (on[e]) {
+                v.r[p[e]] = d[e];
+                if (MIXED) {
+                    f32[p[e]] = (float)d[e];
+                    e32[p[e]] = 0.0f;
+                }
+                m = fmax(m, abs_keep_nan((double)d[e]));
+            }
     }
+    reduce_norm(norm, m);
+}
+
+// u64 += e32 at the inside nodes over the row segments (G at once) and, past
+// them, at the ghosts
+template <int G>
+__global__ void __launch_bounds__(256) k_add_rows(LevelView<double> v, double *__restrict__ u64,
+                                                  const float *__restrict__ e32) {
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int n = v.n, nseg = v.nsegs;
+    const int2 *__restrict__ segs = v.segs;
+    pdl_wait();
+    for (int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; q < nseg; q += nw * G) {
+        double a[2 * G];
+        float b[2 * G];
+        int64_t p[2 * G];
+        bool on[2 * G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            const int2 sg = q + g < nseg ? segs[q + g] : make_int2(0, 0x0000ffff);
+            const int k0 = sg.y & 0xffff, k1 = (int)((unsigned)sg.y >> 16);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int k = k0 + lane + 32 * h;
+                on[2 * g + h] = k <= k1;
+                p[2 * g + h] = (int64_t)sg.x * n + k;
+                if (on[2 * g + h]) {
+                    a[2 * g + h] = u64[p[2 * g + h]];
+                    b[2 * g + h] = e32[p[2 * g + h]];
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 2 * G; e++)
+            if (on[e]) u64[p[e]] = a[e] + (double)b[e];
+    }
+    for (int q = (int)(blockIdx.x * blockDim.x + threadIdx.x); q < v.ng; q += (int)(gridDim.x * blockDim.x)) {
+        const int64_t g = v.gnode[q];
+        u64[g] += (double)e32[g];
+    }
+}
+
+template <typename K>
+static unsigned resident_blocks(K kernel) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0);
+    return (unsigned)std::max(1, sms * std::max(per, 1));
+}
+
+// a persistent grid over a level's row segments, G a warp at once
+template <typename K>
+static unsigned segment_blocks(K kernel, int nseg, int G, unsigned &resident) {
+    if (resident == 0) resident = resident_blocks(kernel);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)(nseg + G - 1) / G * 32 + 255) / 256, resident));
 }
 
 // ------------------------------------------- 3D boundary phase in one launch
@@ -822,12 +899,6 @@ __global__ void __launch_bounds__(LOCAL_THREADS, sizeof(T) == 4 && D == 2 ? 2 : 
 }
 
 // ------------------------------------------------------------------ defect
-// |v| for a max-norm that keeps NaN visible (as +Inf; fmax would drop it)
-__device__ __forceinline__ double abs_keep_nan(double v) {
-    const double a = fabs(v);
-    return a != a ? __longlong_as_double(0x7ff0000000000000ll) : a;
-}
-
 // grid-stride over the level's nodes: a capped grid keeps the number of
 // atomic updates of the norm word small
 template <typename T, int D>
@@ -994,8 +1065,10 @@ __global__ void k_defect_interior_mixed(LevelView<double> v, unsigned long long 
 }
 
 // ... and its ghost rows: the ghost defects rounded to FP32
+// (e32: when not null, also e32 = 0 at the ghosts)
 template <int K>
-__global__ void k_defect_ghost_mixed(LevelView<double> v, unsigned long long *norm, float *__restrict__ g32) {
+__global__ void k_defect_ghost_mixed(LevelView<double> v, unsigned long long *norm, float *__restrict__ g32,
+                                     float *__restrict__ e32) {
     pdl_trigger();
     pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1003,6 +1076,7 @@ __global__ void k_defect_ghost_mixed(LevelView<double> v, unsigned long long *no
     if (q < v.ng) {
         val = defect_ghost_item<double, K>(v, q);
         g32[q] = (float)val;
+        if (e32) e32[v.gnode[q]] = 0.0f;
     }
     reduce_norm(norm, val);
 }
@@ -1289,7 +1363,12 @@ template <typename T>
 void launch_defect(const LevelView<T> &v, int dim, bool zero_rest, unsigned long long *norm, cudaStream_t s) {
     g_launches += v.ng > 0 ? 2 : 1;
     const unsigned nb = std::min(blocks_for(level_threads(v, !zero_rest)), kNormBlocks);
-    if (dim == 2) pdl_launch(k_defect_interior<T, 2>, dim3(nb), dim3(kThreads), 0, s, v, zero_rest, norm);
+    if (dim == 3 && !zero_rest && v.nsegs > 0) {   // inside nodes over the row segments
+        constexpr int G = 4;
+        static unsigned resident = 0;
+        pdl_launch(k_defect_rows<T, G, false>, dim3(segment_blocks(k_defect_rows<T, G, false>, v.nsegs, G, resident)),
+                   dim3(256), 0, s, v, norm, (float *)nullptr, (float *)nullptr);
+    } else if (dim == 2) pdl_launch(k_defect_interior<T, 2>, dim3(nb), dim3(kThreads), 0, s, v, zero_rest, norm);
     else pdl_launch(k_defect_interior<T, 3>, dim3(nb), dim3(kThreads), 0, s, v, zero_rest, norm);
     if (v.ng > 0) {
         if (dim == 2) pdl_launch(k_defect_ghost<T, 9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm);
@@ -1331,25 +1410,17 @@ void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom 
     const bool warp_rows = sizeof(T) == 4 && gf.dim == 2;   // 2D FP32: a warp per coarse ghost row
     const int64_t n = gf.dim == 3 ? level_threads(C, true) : warp_rows ? C.nn + 32 * (int64_t)C.ng
                                                                       : std::max<int64_t>(C.nn, C.ng);
-    if (gf.dim == 3 && gf.nspl > 0) {
+    if (gf.dim == 3 && F.nsegs > 0) {
         // 3D with row segments: one defect pass first (inside nodes over the
         // segments, then the ghosts), so that each fine defect is computed
         // once rather than once per coarse node whose 27-node neighbourhood
         // holds it (27/8 times on average); the same values as on the spot
         constexpr int G = 4;
-        static int resident = 0;
-        if (resident == 0) {
-            int dev = 0, sms = 0, per = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_defect_rows<T, G>, 256, 0);
-            resident = std::max(1, sms * std::max(per, 1));
-        }
-        const unsigned blocks =
-            (unsigned)std::min<int64_t>(((int64_t)(gf.nspl + G - 1) / G * 32 + 255) / 256, resident);
+        static unsigned resident = 0;
+        const unsigned blocks = segment_blocks(k_defect_rows<T, G, false>, F.nsegs, G, resident);
         g_launches++;
-        pdl_launch(k_defect_rows<T, G>, dim3(blocks), dim3(256), 0, s, F, reinterpret_cast<const int2 *>(gf.sp_list),
-                   gf.nspl);
+        pdl_launch(k_defect_rows<T, G, false>, dim3(blocks), dim3(256), 0, s, F, (unsigned long long *)nullptr,
+                   (float *)nullptr, (float *)nullptr);
         if (F.ng > 0) {
             g_launches++;
             pdl_launch(k_defect_ghost<T, 27>, dim3(blocks_for(F.ng)), dim3(kThreads), 0, s, F,
@@ -1560,22 +1631,45 @@ void launch_defect_mixed(const LevelView<double> &v, int dim, unsigned long long
                          float *e32, cudaStream_t s) {
     g_launches += v.ng > 0 ? 2 : 1;
     const unsigned nb = std::min(blocks_for(level_threads(v, true)), kNormBlocks);
-    if (dim == 2) pdl_launch(k_defect_interior_mixed<2>, dim3(nb), dim3(kThreads), 0, s, v, norm, f32, e32);
+    // 3D with row segments: the inside nodes over the segments, e32 = 0 at
+    // the ghosts by the ghost launch; the other nodes of f32 and e32 are 0
+    // from the start and nothing writes them
+    const bool rows = dim == 3 && v.nsegs > 0;
+    if (rows) {
+        constexpr int G = 2;
+        static unsigned resident = 0;
+        pdl_launch(k_defect_rows<double, G, true>,
+                   dim3(segment_blocks(k_defect_rows<double, G, true>, v.nsegs, G, resident)), dim3(256), 0, s, v,
+                   norm, f32, e32);
+    } else if (dim == 2) pdl_launch(k_defect_interior_mixed<2>, dim3(nb), dim3(kThreads), 0, s, v, norm, f32, e32);
     else pdl_launch(k_defect_interior_mixed<3>, dim3(nb), dim3(kThreads), 0, s, v, norm, f32, e32);
+    float *ge = rows ? e32 : nullptr;
     if (v.ng > 0) {
-        if (dim == 2) pdl_launch(k_defect_ghost_mixed<9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32);
-        else pdl_launch(k_defect_ghost_mixed<27>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32);
+        if (dim == 2) pdl_launch(k_defect_ghost_mixed<9>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32, ge);
+        else pdl_launch(k_defect_ghost_mixed<27>, dim3(blocks_for(v.ng)), dim3(kThreads), 0, s, v, norm, g32, ge);
     }
 }
 
 void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cudaStream_t s) {
     g_launches++;
     LevelView<double> v{};
+    v.n = g.n;
     v.nn = g.nn;
     v.type = g.type;
     v.chunks = g.chunks;
     v.clen = g.chunk_len;
     v.nchunks = g.nchunks;
+    if (g.dim == 3 && g.nspl > 0) {   // inside nodes over the row segments, then the ghosts
+        constexpr int G = 4;
+        static unsigned resident = 0;
+        v.segs = reinterpret_cast<const int2 *>(g.sp_list);
+        v.nsegs = g.nspl;
+        v.ng = g.ng;
+        v.gnode = g.gnode;
+        pdl_launch(k_add_rows<G>, dim3(segment_blocks(k_add_rows<G>, v.nsegs, G, resident)), dim3(256), 0, s, v, u64,
+                   e32);
+        return;
+    }
     pdl_launch(k_add_correction, dim3(blocks_for(level_threads(v, true))), dim3(kThreads), 0, s, v, u64, e32);
 }
 

@@ -617,7 +617,8 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
     const int cube = D == 2 ? 9 : 27;
     const unsigned full = (1u << cube) - 1u;
     unsigned member = 0;
-    for (int c = 0; c < cube; c++) {
+#pragma unroll
+    for (int c = 0; c < cube; c++) {   // the 3^D types are loaded together
         int rem = c;
         int64_t q = p;
         for (int a = D - 1; a >= 0; a--) {
@@ -643,7 +644,36 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
         }
     }
     if (wait) pdl_wait();
-    if (member != full && count == 0) return (T)0;   // no box inside the set
+    if (member == full) {
+        // full weighting: every value loaded before the first product (one
+        // round trip, not 3^D), then the same sum in the same order as below
+        T val[cube];
+#pragma unroll
+        for (int c = 0; c < cube; c++) {
+            int rem = c;
+            int64_t q = p;
+            for (int a = D - 1; a >= 0; a--) {
+                q += (rem % 3 - 1) * (a == D - 1 ? (int64_t)1 : (a == 0 ? F.s0 : F.s1));
+                rem /= 3;
+            }
+            val[c] = value(q);
+        }
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < cube; c++) {
+            int rem = c;
+            T w = 1;
+            int o[3] = {0, 0, 0};
+            for (int a = D - 1; a >= 0; a--) {
+                o[a] = rem % 3 - 1;
+                rem /= 3;
+            }
+            for (int a = 0; a < D; a++) w *= w1d<T>(0, o[a]);
+            acc += w * val[c];
+        }
+        return acc;
+    }
+    if (count == 0) return (T)0;   // no box inside the set
     // weights and sum in T: the weights are dyadic or 1/count, an FP32 cycle
     // keeps its arithmetic on the FP32 pipe
     T acc = 0;
@@ -657,20 +687,15 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
             rem /= 3;
             q += o[a] * (a == D - 1 ? (int64_t)1 : (a == 0 ? F.s0 : F.s1));
         }
+        // the largest boxes in increasing order (as a scan of all boxes would)
         T w = 0;
-        if (member == full) {
-            w = 1;
-            for (int a = 0; a < D; a++) w *= w1d<T>(0, o[a]);
-        } else {
-            // the largest boxes in increasing order (as a scan of all boxes would)
-            for (unsigned long long bs = bestset; bs; bs &= bs - 1) {
-                const int b = __ffsll((long long)bs) - 1;
-                T wb = 1;
-                for (int a = 0; a < D; a++) wb *= w1d<T>((b >> (2 * a)) & 3, o[a]);
-                w += wb;
-            }
-            w /= (T)count;
+        for (unsigned long long bs = bestset; bs; bs &= bs - 1) {
+            const int b = __ffsll((long long)bs) - 1;
+            T wb = 1;
+            for (int a = 0; a < D; a++) wb *= w1d<T>((b >> (2 * a)) & 3, o[a]);
+            w += wb;
         }
+        w /= (T)count;
         if (w != (T)0) acc += w * value(q);
     }
     return acc;
@@ -913,29 +938,36 @@ __device__ __forceinline__ void prolong_node_early(const LevelView<T> &F, const 
         j[2] = (int)(rem - (int64_t)j[1] * F.s1);
     }
     const int n1 = (j[0] & 1) ? 2 : 1, n2 = (j[1] & 1) ? 2 : 1, n3 = (D == 3 && (j[2] & 1)) ? 2 : 1;
-    int64_t X[8];
-    unsigned use = 0;   // parents in Omega_2h u Gamma_2h, in (a, b, c) order
-    int np = 0;
-    if (on)
-        for (int a = 0; a < n1; a++)
-            for (int b = 0; b < n2; b++)
-                for (int c = 0; c < n3; c++) {
-                    const int64_t x = (int64_t)(j[0] / 2 + a) * C.s0 +
-                                      (D == 2 ? (int64_t)(j[1] / 2 + b) : (int64_t)(j[1] / 2 + b) * C.s1 + (j[2] / 2 + c));
-                    const uint8_t kc = C.type[x] & NODE_KIND;
-                    if (kc == NODE_IN || kc == NODE_GHOST) use |= 1u << np;
-                    X[np++] = x;
-                }
+    // up to 2^D parents in fixed slots (a, b, c), every load of a phase issued
+    // before the first use
+    constexpr int NS = D == 3 ? 8 : 4;
+    int64_t X[NS];
+    bool use[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const int a = D == 3 ? s >> 2 : s >> 1, b = D == 3 ? (s >> 1) & 1 : s & 1, c = D == 3 ? s & 1 : 0;
+        X[s] = (int64_t)(j[0] / 2 + a) * C.s0 +
+               (D == 2 ? (int64_t)(j[1] / 2 + b) : (int64_t)(j[1] / 2 + b) * C.s1 + (j[2] / 2 + c));
+        use[s] = false;
+        if (on && a < n1 && b < n2 && c < n3) {
+            const uint8_t kc = C.type[X[s]] & NODE_KIND;
+            use[s] = kc == NODE_IN || kc == NODE_GHOST;   // parents in Omega_2h u Gamma_2h
+        }
+    }
     pdl_wait();
     if (!on) {
         if (!add) out[p] = 0;
         return;
     }
+    T ev[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) ev[s] = use[s] ? e[X[s]] : (T)0;
     T num = 0, den = 0;
     const T w = (T)1 / (T)(n1 * n2 * n3);   // a power of two: exact
-    for (int i = 0; i < np; i++)
-        if ((use >> i) & 1u) {
-            num += w * e[X[i]];
+#pragma unroll
+    for (int s = 0; s < NS; s++)   // (a, b, c) order, as prolong_node
+        if (use[s]) {
+            num += w * ev[s];
             den += w;
         }
     const T val = den > (T)0 ? num / den : (T)0;
