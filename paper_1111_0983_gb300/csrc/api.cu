@@ -148,6 +148,7 @@ void upload_geometry(gcmg_ctx *c, int l) {
     std::vector<int32_t> stn = slot_major<int32_t, int32_t>(L.stn, g.ng, KMAX, kslots(L.dim));
     g.gstn = upload<int32_t>(c, stn.data(), stn.size());
     g.red = upload<int32_t>(c, L.band_red.data(), L.band_red.size());
+    if (!L.band_red_src.empty()) g.red_src = upload<int32_t>(c, L.band_red_src.data(), L.band_red_src.size());
     g.ntiles = (int)L.tiles.size();
     g.tiles = upload<int32_t>(c, L.tiles.data(), L.tiles.size());
     if (L.dim == 2) {
@@ -216,7 +217,7 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     int32_t **arrs[] = {&z.node_off, &z.wb_cnt, &z.lnode, &z.int_off, &z.red_cnt, &z.int_glob,
                         &z.int_me, &z.int_nb, &z.gh_off, &z.gh_me, &z.gh_q, &z.gh_stn,
                         &z.zred, &z.zblack, &z.zghost, &z.wb_list, &z.node_base,
-                        &z.pre_off, &z.pre_red_cnt, &z.pre_me, &z.pre_nb, &z.pre_glob};
+                        &z.pre_off, &z.pre_red_cnt, &z.pre_me, &z.pre_nb, &z.pre_glob, &z.zred_src};
     for (int32_t **a : arrs) { free_tracked(c, *a); *a = nullptr; }
     z.ncomp = J.ncomp();
     z.max_nodes = J.max_nodes;
@@ -253,6 +254,7 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     z.zred = upload<int32_t>(c, J.zred.data(), J.zred.size());
     z.zblack = upload<int32_t>(c, J.zblack.data(), J.zblack.size());
     z.zghost = upload<int32_t>(c, J.zghost.data(), J.zghost.size());
+    z.zred_src = J.zred_src.empty() ? nullptr : upload<int32_t>(c, J.zred_src.data(), J.zred_src.size());
     std::vector<int32_t> wb;
     for (int k = 0; k < z.ncomp; k++)
         wb.insert(wb.end(), J.lnode.begin() + J.node_off[k], J.lnode.begin() + J.node_off[k] + J.wb_cnt[k]);
@@ -439,7 +441,34 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
             }
             if (done) timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         }
-        if (!done) {
+        // mode 0 in 3D: the store of each Jacobi ghost sweep (its new values
+        // wait in gtmp) is merged into the launch of the next red sweep,
+        // whose updates read the ghosts' new values from gtmp (red_sources):
+        // three launches a band or junction sweep instead of four
+        const bool merged = !done && dim == 3 && extra && c->p.smoother == 0 && g.ng > 0 && g.red_src &&
+                            !c->coop3d && !c->cluster3d;
+        if (merged) {
+            const bool zmerge = !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 &&
+                                !g.jz.in_smem && g.jz.zred_src;
+            launch_ghost_new<T>(v, nullptr, g.ng, c->stream);
+            for (int k = 0; k < c->p.lambda; k++) {
+                launch_rb_list_store<T>(v, g.red, g.red_src, g.nred, nullptr, g.ng, c->stream);
+                launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
+                launch_ghost_new<T>(v, nullptr, g.ng, c->stream);
+            }
+            timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
+            if (zmerge) {   // the first red zone sweep stores every ghost, later ones the zone's
+                for (int k = 0; k < c->p.junction_sweeps; k++) {
+                    launch_rb_list_store<T>(v, g.jz.zred, g.jz.zred_src, g.jz.nzred, k == 0 ? nullptr : g.jz.zghost,
+                                            k == 0 ? g.ng : g.jz.nzghost, c->stream);
+                    launch_rb_list<T>(v, dim, g.jz.zblack, g.jz.nzblack, c->stream);
+                    launch_ghost_new<T>(v, g.jz.zghost, g.jz.nzghost, c->stream);
+                }
+                launch_ghost_store<T>(v, g.jz.zghost, g.jz.nzghost, c->stream);
+                return v.u;
+            }
+            launch_ghost_store<T>(v, nullptr, g.ng, c->stream);
+        } else if (!done) {
             launch_ghost_relax<T>(v, dim, c->stream);
             if (extra)
                 for (int k = 0; k < c->p.lambda; k++) {

@@ -62,6 +62,7 @@ struct LocalProgram {
     // slots, global node for f)
     std::vector<int32_t> pre_off{0}, pre_red_cnt, pre_me, pre_nb, pre_glob;
     std::vector<int32_t> zred, zblack, zghost;   // union over components (global fallback)
+    std::vector<int32_t> zred_src;   // 3D: red_sources of zred
     int max_nodes = 0, max_int = 0, max_gh = 0, max_pre = 0;
     int ncomp() const { return (int)wb_cnt.size(); }
 };
@@ -85,6 +86,7 @@ struct HostLevel {
     std::vector<uint8_t> bc;            // 0 Dirichlet, 1 Neumann
     // inside nodes of the extra-sweep band, split by colour
     std::vector<int32_t> band_red, band_black;
+    std::vector<int32_t> band_red_src;   // 3D: red_sources of band_red
     // 2D tiles (TILE_R x TILE_C) holding inside nodes, packed (tile row << 16 | tile column)
     std::vector<int32_t> tiles;
     // 3D active chunks: runs of CHUNK nodes along the contiguous axis (start
@@ -143,6 +145,13 @@ struct HostLevel {
     int64_t ng() const { return (int64_t)ghost_node.size(); }
 };
 
+// The sources of the six axis neighbours of each 3D inside node of `list`,
+// in the order of neighbour_sum (axis 2 -, +; axis 0 -, +; axis 1 -, +),
+// slot major (6 x list size): the node, or -1 - q where the neighbour is
+// ghost q, so that a red sweep can read the ghosts' new values from the
+// Jacobi buffer while the same launch stores them.
+std::vector<int32_t> red_sources(const HostLevel &L, const std::vector<int32_t> &list);
+
 // Rebuilds a 3D level's row-span sweep items for C columns a lane and items
 // of at most seg planes (C = 0: the cheapest C by the work model; seg = 0:
 // SP_SEG).  Returns false (and leaves the level without items) when a row's
@@ -191,6 +200,7 @@ struct LocalDev {
     int32_t *gh_off = nullptr, *gh_me = nullptr, *gh_q = nullptr, *gh_stn = nullptr;
     int nzred = 0, nzblack = 0, nzghost = 0;
     int32_t *zred = nullptr, *zblack = nullptr, *zghost = nullptr;
+    int32_t *zred_src = nullptr;   // 3D: LocalProgram::zred_src
     int nwb = 0;
     int32_t *wb_list = nullptr;   // every component's write-back nodes, one flat list
     bool in_smem = true;       // false: relaxed by per-sweep launches over the union lists
@@ -205,6 +215,7 @@ struct DevGeom {
     int32_t *gnode = nullptr;    // ng
     int32_t *gstn = nullptr;     // KMAX * ng, slot major
     int32_t *red = nullptr, *black = nullptr;
+    int32_t *red_src = nullptr;  // 3D: HostLevel::band_red_src
     int ntiles = 0;
     int32_t *tiles = nullptr;    // active 2D interior tiles
     int nstrips = 0, strip_rows = 0;

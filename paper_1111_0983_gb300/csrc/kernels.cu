@@ -846,6 +846,36 @@ __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int 
     v.u[p] = s * (T)(1.0 / (2 * D));
 }
 
+// The red half of a 3D band or junction-zone sweep merged with the store of
+// the ghosts' new values: threads below cnt update the list's red nodes,
+// reading each axis neighbour from src (slot major: the node, or -1 - q for
+// ghost q, whose new value is still in gtmp), threads past cnt store gtmp
+// into u for the ghosts of glist (null: every ghost).  Nothing the updates
+// read is written in the launch (their neighbours are black nodes and
+// ghosts).  The sum of k_rb_list in the same order.
+template <typename T>
+__global__ void k_rb_list_store(LevelView<T> v, const int32_t *__restrict__ list, const int32_t *__restrict__ src,
+                                int cnt, const int32_t *__restrict__ glist, int gcnt) {
+    pdl_wait();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) {
+        const int64_t p = list[i];
+        T x[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const int sk = src[(int64_t)k * cnt + i];
+            x[k] = sk >= 0 ? v.u[sk] : v.gtmp[-1 - sk];
+        }
+        T nb = x[0] + x[1] + x[2] + x[3];
+        nb += x[4] + x[5];
+        const T s = mul_rn(v.h2, v.f[p]) + nb;   // h^2 f rounded on its own
+        v.u[p] = s * (T)(1.0 / 6.0);
+    } else if (i - cnt < gcnt) {
+        const int q = glist ? glist[i - cnt] : i - cnt;
+        v.u[v.gnode[q]] = v.gtmp[q];
+    }
+}
+
 // Ghost relaxation, Eqs. (dir2d)/(neu2d): new value from the current values.
 template <typename T, int K>
 __global__ void k_ghost_new(LevelView<T> v) {
@@ -1351,6 +1381,33 @@ void launch_ghost_relax(const LevelView<T> &v, int dim, cudaStream_t s) {
 }
 
 template <typename T>
+void launch_rb_list_store(const LevelView<T> &v, const int32_t *list, const int32_t *src, int cnt,
+                          const int32_t *glist, int gcnt, cudaStream_t s) {
+    if (cnt + gcnt <= 0) return;
+    g_launches++;
+    pdl_launch(k_rb_list_store<T>, dim3(blocks_for((int64_t)cnt + gcnt)), dim3(kThreads), 0, s, v, list, src, cnt,
+               glist, gcnt);
+}
+
+// the two halves of a Jacobi ghost sweep as separate launches (3D: the store
+// merged into the next red sweep, see k_rb_list_store)
+template <typename T>
+void launch_ghost_new(const LevelView<T> &v, const int32_t *list, int cnt, cudaStream_t s) {
+    if (cnt <= 0) return;
+    g_launches++;
+    if (list) pdl_launch(k_ghost_new_list<T, 27>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+    else pdl_launch(k_ghost_new<T, 27>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v);
+}
+
+template <typename T>
+void launch_ghost_store(const LevelView<T> &v, const int32_t *list, int cnt, cudaStream_t s) {
+    if (cnt <= 0) return;
+    g_launches++;
+    if (list) pdl_launch(k_ghost_store_list<T>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+    else pdl_launch(k_ghost_store<T>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v);
+}
+
+template <typename T>
 void launch_ghost_relax_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s) {
     if (cnt <= 0) return;
     g_launches += 2;
@@ -1680,6 +1737,10 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_rb_strip<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);           \
     template void launch_ghost_relax<T>(const LevelView<T> &, int, cudaStream_t);                         \
     template void launch_ghost_relax_list<T>(const LevelView<T> &, int, const int32_t *, int, cudaStream_t); \
+    template void launch_rb_list_store<T>(const LevelView<T> &, const int32_t *, const int32_t *, int,      \
+                                          const int32_t *, int, cudaStream_t);                               \
+    template void launch_ghost_new<T>(const LevelView<T> &, const int32_t *, int, cudaStream_t);          \
+    template void launch_ghost_store<T>(const LevelView<T> &, const int32_t *, int, cudaStream_t);        \
     template void launch_defect<T>(const LevelView<T> &, int, bool, unsigned long long *, cudaStream_t); \
     template void launch_extend<T>(T *, const DevGeom &, const T *, cudaStream_t);                        \
     template void launch_restrict<T>(const LevelView<T> &, const LevelView<T> &, int, T *, T *, cudaStream_t); \

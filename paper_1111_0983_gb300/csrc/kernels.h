@@ -33,6 +33,16 @@ template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s);
 template <typename T>
 void launch_ghost_relax(const LevelView<T> &v, int dim, cudaStream_t s);
+// 3D: the red half of a band / junction-zone sweep (sources: red_sources)
+// merged with the store of the ghosts' new values (glist null: all ghosts)
+template <typename T>
+void launch_rb_list_store(const LevelView<T> &v, const int32_t *list, const int32_t *src, int cnt,
+                          const int32_t *glist, int gcnt, cudaStream_t s);
+// the halves of a 3D Jacobi ghost sweep (list null: all ghosts)
+template <typename T>
+void launch_ghost_new(const LevelView<T> &v, const int32_t *list, int cnt, cudaStream_t s);
+template <typename T>
+void launch_ghost_store(const LevelView<T> &v, const int32_t *list, int cnt, cudaStream_t s);
 template <typename T>
 void launch_ghost_relax_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s);
 template <typename T>

@@ -669,6 +669,7 @@ void build_junction(HostLevel &L, double radius) {
     }
     for (const auto &cz : comps) PB.add(cz, cz);
     PB.finish(zn);
+    if (L.dim == 3) prog.zred_src = red_sources(L, prog.zred);
     L.junction = std::move(prog);
 }
 
@@ -902,6 +903,23 @@ static void build_zmarch_items(HostLevel &L) {
     }
 }
 
+std::vector<int32_t> red_sources(const HostLevel &L, const std::vector<int32_t> &list) {
+    const size_t m = list.size();
+    std::vector<int32_t> src(6 * m);
+    const int64_t off[6] = {-1, 1, -L.stride[0], L.stride[0], -L.stride[1], L.stride[1]};
+    for (size_t i = 0; i < m; i++)
+        for (int k = 0; k < 6; k++) {
+            const int64_t q = (int64_t)list[i] + off[k];
+            int32_t v = (int32_t)q;
+            if ((L.type[q] & NODE_KIND) == NODE_GHOST) {
+                const auto it = std::lower_bound(L.ghost_node.begin(), L.ghost_node.end(), (int32_t)q);
+                v = -1 - (int32_t)(it - L.ghost_node.begin());
+            }
+            src[(size_t)k * m + i] = v;
+        }
+    return src;
+}
+
 // Row-span sweep items.  A row block is SP_J consecutive rows (axis 1); per
 // plane its span is the union of its rows' unknown spans.  The planes where
 // that span is not empty form runs (gaps of up to 2 idle planes merged), cut
@@ -1081,6 +1099,7 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
         L.bc.assign(ng, 0);
         for (int64_t q = 0; q < ng; q++) ghost_equation(L, q);
         mark_band(L, delta_over_h * L.h);
+        if (dim == 3) L.band_red_src = red_sources(L, L.band_red);
         if (dim == 2) {
             const int tr = (L.n + TILE_R - 1) / TILE_R, tc = (L.n + TILE_C - 1) / TILE_C;
             std::vector<uint8_t> active((size_t)tr * tc, 0);
