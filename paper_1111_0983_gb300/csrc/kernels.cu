@@ -630,7 +630,9 @@ __global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, unsigned lo
     const int n = v.n, nseg = v.nsegs;
     const int2 *__restrict__ segs = v.segs;
     pdl_wait();
-    double m = 0.0;
+    // the max-norm on the bit patterns of |d| (integer compares; the order of
+    // non-negative doubles, NaN above +Inf, which reduce_norm maps to +Inf)
+    unsigned long long mb = 0;
     for (int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; q < nseg; q += nw * G) {
         T d[2 * G];
         int64_t p[2 * G];
@@ -655,10 +657,11 @@ __global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, unsigned lo
                     f32[p[e]] = (float)d[e];
                     e32[p[e]] = 0.0f;
                 }
-                m = fmax(m, abs_keep_nan((double)d[e]));
+                const unsigned long long b = (unsigned long long)__double_as_longlong((double)d[e]) & 0x7fffffffffffffffull;
+                mb = b > mb ? b : mb;
             }
     }
-    reduce_norm(norm, m);
+    reduce_norm(norm, __longlong_as_double((long long)mb));
 }
 
 // u64 += e32 at the inside nodes over the row segments (G at once) and, past

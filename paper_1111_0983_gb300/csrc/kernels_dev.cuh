@@ -674,18 +674,29 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
         return acc;
     }
     if (count == 0) return (T)0;   // no box inside the set
-    // weights and sum in T: the weights are dyadic or 1/count, an FP32 cycle
-    // keeps its arithmetic on the FP32 pipe
+    // the members' values loaded together first, then weights and sum in T:
+    // the weights are dyadic or 1/count, an FP32 cycle keeps its arithmetic
+    // on the FP32 pipe
+    T val[cube];
+#pragma unroll
+    for (int c = 0; c < cube; c++) {
+        int rem = c;
+        int64_t q = p;
+        for (int a = D - 1; a >= 0; a--) {
+            q += (rem % 3 - 1) * (a == D - 1 ? (int64_t)1 : (a == 0 ? F.s0 : F.s1));
+            rem /= 3;
+        }
+        val[c] = ((member >> c) & 1u) ? value(q) : (T)0;
+    }
     T acc = 0;
+#pragma unroll
     for (int c = 0; c < cube; c++) {
         if (!((member >> c) & 1u)) continue;
         int rem = c;
-        int64_t q = p;
         int o[3] = {0, 0, 0};
         for (int a = D - 1; a >= 0; a--) {
             o[a] = rem % 3 - 1;
             rem /= 3;
-            q += o[a] * (a == D - 1 ? (int64_t)1 : (a == 0 ? F.s0 : F.s1));
         }
         // the largest boxes in increasing order (as a scan of all boxes would)
         T w = 0;
@@ -696,7 +707,7 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
             w += wb;
         }
         w /= (T)count;
-        if (w != (T)0) acc += w * value(q);
+        if (w != (T)0) acc += w * val[c];
     }
     return acc;
 }
