@@ -19,6 +19,7 @@ namespace {
 
 using namespace dev;
 constexpr int kThreads = 256;
+constexpr int LIST_M = 4;   // entries a thread of the band and junction-zone list sweeps
 constexpr unsigned kNormBlocks = 2048;   // grid cap of the kernels that reduce a max-norm
 
 // Launches with programmatic stream serialization: the kernel may be set up
@@ -841,12 +842,20 @@ __global__ void __launch_bounds__(BC_THREADS) k_boundary3d_cluster(LevelView<T> 
 // Same update over a compact list of band nodes of one colour (Sec. 3.2).
 template <typename T, int D>
 __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
+    // entries i0 + m * (threads of the launch), m < LIST_M: the loads of all
+    // of a thread's entries are issued before its first update
     pdl_wait();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int64_t p = list[i];
-    const T s = mul_rn(v.h2, v.f[p]) + neighbour_sum<T, D>(v.u, p, v.s0, v.s1);   // h^2 f rounded on its own
-    v.u[p] = s * (T)(1.0 / (2 * D));
+    const int nt = (int)(gridDim.x * blockDim.x), i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    int64_t p[LIST_M];
+    T sum[LIST_M];
+#pragma unroll
+    for (int m = 0; m < LIST_M; m++) p[m] = i0 + m * nt < cnt ? list[i0 + m * nt] : -1;
+#pragma unroll
+    for (int m = 0; m < LIST_M; m++)
+        if (p[m] >= 0) sum[m] = mul_rn(v.h2, v.f[p[m]]) + neighbour_sum<T, D>(v.u, p[m], v.s0, v.s1);   // h^2 f rounded on its own
+#pragma unroll
+    for (int m = 0; m < LIST_M; m++)
+        if (p[m] >= 0) v.u[p[m]] = sum[m] * (T)(1.0 / (2 * D));
 }
 
 // The red half of a 3D band or junction-zone sweep merged with the store of
@@ -859,23 +868,40 @@ __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int 
 template <typename T>
 __global__ void k_rb_list_store(LevelView<T> v, const int32_t *__restrict__ list, const int32_t *__restrict__ src,
                                 int cnt, const int32_t *__restrict__ glist, int gcnt) {
+    // items i0 + m * (threads of the launch), m < LIST_M, loads first (as k_rb_list)
     pdl_wait();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < cnt) {
-        const int64_t p = list[i];
-        T x[6];
+    const int nt = (int)(gridDim.x * blockDim.x), i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    T x[LIST_M][6], fv[LIST_M], gv[LIST_M];
+    int64_t p[LIST_M];
+    int kind[LIST_M];   // 0 none, 1 red entry, 2 ghost store
 #pragma unroll
-        for (int k = 0; k < 6; k++) {
-            const int sk = src[(int64_t)k * cnt + i];
-            x[k] = sk >= 0 ? v.u[sk] : v.gtmp[-1 - sk];
+    for (int m = 0; m < LIST_M; m++) {
+        const int i = i0 + m * nt;
+        kind[m] = i < cnt ? 1 : i - cnt < gcnt ? 2 : 0;
+        if (kind[m] == 1) {
+            p[m] = list[i];
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                const int sk = src[(int64_t)k * cnt + i];
+                x[m][k] = sk >= 0 ? v.u[sk] : v.gtmp[-1 - sk];
+            }
+            fv[m] = v.f[p[m]];
+        } else if (kind[m] == 2) {
+            const int q = glist ? glist[i - cnt] : i - cnt;
+            p[m] = v.gnode[q];
+            gv[m] = v.gtmp[q];
         }
-        T nb = x[0] + x[1] + x[2] + x[3];
-        nb += x[4] + x[5];
-        const T s = mul_rn(v.h2, v.f[p]) + nb;   // h^2 f rounded on its own
-        v.u[p] = s * (T)(1.0 / 6.0);
-    } else if (i - cnt < gcnt) {
-        const int q = glist ? glist[i - cnt] : i - cnt;
-        v.u[v.gnode[q]] = v.gtmp[q];
+    }
+#pragma unroll
+    for (int m = 0; m < LIST_M; m++) {
+        if (kind[m] == 1) {
+            T nb = x[m][0] + x[m][1] + x[m][2] + x[m][3];
+            nb += x[m][4] + x[m][5];
+            const T s = mul_rn(v.h2, fv[m]) + nb;   // h^2 f rounded on its own
+            v.u[p[m]] = s * (T)(1.0 / 6.0);
+        } else if (kind[m] == 2) {
+            v.u[p[m]] = gv[m];
+        }
     }
 }
 
@@ -1370,8 +1396,9 @@ template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s) {
     if (cnt <= 0) return;
     g_launches++;
-    if (dim == 2) pdl_launch(k_rb_list<T, 2>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
-    else pdl_launch(k_rb_list<T, 3>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+    const unsigned nb = blocks_for(((int64_t)cnt + LIST_M - 1) / LIST_M);
+    if (dim == 2) pdl_launch(k_rb_list<T, 2>, dim3(nb), dim3(kThreads), 0, s, v, list, cnt);
+    else pdl_launch(k_rb_list<T, 3>, dim3(nb), dim3(kThreads), 0, s, v, list, cnt);
 }
 
 template <typename T>
@@ -1388,8 +1415,8 @@ void launch_rb_list_store(const LevelView<T> &v, const int32_t *list, const int3
                           const int32_t *glist, int gcnt, cudaStream_t s) {
     if (cnt + gcnt <= 0) return;
     g_launches++;
-    pdl_launch(k_rb_list_store<T>, dim3(blocks_for((int64_t)cnt + gcnt)), dim3(kThreads), 0, s, v, list, src, cnt,
-               glist, gcnt);
+    pdl_launch(k_rb_list_store<T>, dim3(blocks_for(((int64_t)cnt + gcnt + LIST_M - 1) / LIST_M)), dim3(kThreads), 0,
+               s, v, list, src, cnt, glist, gcnt);
 }
 
 // the two halves of a Jacobi ghost sweep as separate launches (3D: the store
