@@ -19,7 +19,10 @@ namespace {
 
 using namespace dev;
 constexpr int kThreads = 256;
-constexpr int LIST_M = 4;   // entries a thread of the band and junction-zone list sweeps
+// lists of at least this many entries (the finest band) take four entries a
+// thread in the band and junction-zone sweeps, smaller ones one (measured at
+// 513^3: four a thread on every list made a cycle 12 % slower)
+constexpr int kListBig = 300000;
 constexpr unsigned kNormBlocks = 2048;   // grid cap of the kernels that reduce a max-norm
 
 // Launches with programmatic stream serialization: the kernel may be set up
@@ -840,7 +843,7 @@ __global__ void __launch_bounds__(BC_THREADS) k_boundary3d_cluster(LevelView<T> 
 }
 
 // Same update over a compact list of band nodes of one colour (Sec. 3.2).
-template <typename T, int D>
+template <typename T, int D, int LIST_M>
 __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
     // entries i0 + m * (threads of the launch), m < LIST_M: the loads of all
     // of a thread's entries are issued before its first update
@@ -865,7 +868,7 @@ __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int 
 // into u for the ghosts of glist (null: every ghost).  Nothing the updates
 // read is written in the launch (their neighbours are black nodes and
 // ghosts).  The sum of k_rb_list in the same order.
-template <typename T>
+template <typename T, int LIST_M>
 __global__ void k_rb_list_store(LevelView<T> v, const int32_t *__restrict__ list, const int32_t *__restrict__ src,
                                 int cnt, const int32_t *__restrict__ glist, int gcnt) {
     // items i0 + m * (threads of the launch), m < LIST_M, loads first (as k_rb_list)
@@ -1396,9 +1399,14 @@ template <typename T>
 void launch_rb_list(const LevelView<T> &v, int dim, const int32_t *list, int cnt, cudaStream_t s) {
     if (cnt <= 0) return;
     g_launches++;
-    const unsigned nb = blocks_for(((int64_t)cnt + LIST_M - 1) / LIST_M);
-    if (dim == 2) pdl_launch(k_rb_list<T, 2>, dim3(nb), dim3(kThreads), 0, s, v, list, cnt);
-    else pdl_launch(k_rb_list<T, 3>, dim3(nb), dim3(kThreads), 0, s, v, list, cnt);
+    if (cnt >= kListBig) {
+        const unsigned nb = blocks_for(((int64_t)cnt + 3) / 4);
+        if (dim == 2) pdl_launch(k_rb_list<T, 2, 4>, dim3(nb), dim3(kThreads), 0, s, v, list, cnt);
+        else pdl_launch(k_rb_list<T, 3, 4>, dim3(nb), dim3(kThreads), 0, s, v, list, cnt);
+    } else {
+        if (dim == 2) pdl_launch(k_rb_list<T, 2, 1>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+        else pdl_launch(k_rb_list<T, 3, 1>, dim3(blocks_for(cnt)), dim3(kThreads), 0, s, v, list, cnt);
+    }
 }
 
 template <typename T>
@@ -1415,8 +1423,12 @@ void launch_rb_list_store(const LevelView<T> &v, const int32_t *list, const int3
                           const int32_t *glist, int gcnt, cudaStream_t s) {
     if (cnt + gcnt <= 0) return;
     g_launches++;
-    pdl_launch(k_rb_list_store<T>, dim3(blocks_for(((int64_t)cnt + gcnt + LIST_M - 1) / LIST_M)), dim3(kThreads), 0,
-               s, v, list, src, cnt, glist, gcnt);
+    if ((int64_t)cnt + gcnt >= kListBig)
+        pdl_launch(k_rb_list_store<T, 4>, dim3(blocks_for(((int64_t)cnt + gcnt + 3) / 4)), dim3(kThreads), 0, s, v,
+                   list, src, cnt, glist, gcnt);
+    else
+        pdl_launch(k_rb_list_store<T, 1>, dim3(blocks_for((int64_t)cnt + gcnt)), dim3(kThreads), 0, s, v, list, src,
+                   cnt, glist, gcnt);
 }
 
 // the two halves of a Jacobi ghost sweep as separate launches (3D: the store
