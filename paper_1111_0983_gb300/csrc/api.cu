@@ -192,6 +192,10 @@ void upload_geometry(gcmg_ctx *c, int l) {
     g.esrc = upload<int32_t>(c, es.data(), es.size());
     g.wave = L.ext_wave;
     g.gt_ptr = upload<int32_t>(c, L.gt_ptr.data(), L.gt_ptr.size());
+    if (!L.partial_coarse.empty()) {
+        g.npartial = (int)L.partial_coarse.size();
+        g.partial_coarse = upload<int32_t>(c, L.partial_coarse.data(), L.partial_coarse.size());
+    }
     g.gt_col = upload<int32_t>(c, L.gt_col.data(), L.gt_col.size());
     if (l + 1 == (int)c->H.size()) {
         g.nunk = (int)L.unk_node.size();

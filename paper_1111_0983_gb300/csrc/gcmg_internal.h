@@ -126,6 +126,11 @@ struct HostLevel {
     // data (CSR over coarse ghosts; columns are this level's ghost numbers)
     std::vector<int32_t> gt_ptr, gt_col;
     std::vector<double> gt_val;
+    // 3D: the inside nodes of the next coarser level whose fine image's 3^3
+    // neighbourhood on this level is not all inside (the restriction's
+    // partial transfer there searches its boxes; the others take full
+    // weighting), in increasing order
+    std::vector<int32_t> partial_coarse;
     // shared-memory relaxation programs: the junction zone (depends on bc)
     // and, in 2D, the boundary blocks of the lambda extra sweeps
     LocalProgram junction, boundary;
@@ -238,6 +243,8 @@ struct DevGeom {
     uint8_t *ecnt = nullptr;     // ne
     int32_t *esrc = nullptr;     // EMAX * ne, slot major
     int32_t *gt_ptr = nullptr, *gt_col = nullptr;   // ghost transfer to the next level
+    int npartial = 0;
+    int32_t *partial_coarse = nullptr;                 // HostLevel::partial_coarse
     int32_t *unk_node = nullptr, *unk_ghost = nullptr;
     std::vector<int> wave;       // host copy of the wavefront offsets
     LocalDev jz, bz;             // junction zone / boundary blocks

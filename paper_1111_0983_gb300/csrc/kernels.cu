@@ -1009,7 +1009,7 @@ __global__ void k_restrict_interior(LevelView<T> F, LevelView<T> C, T *__restric
 template <typename T, int D, bool FROM_R>
 __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T *__restrict__ gc,
                           T *__restrict__ uc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                          const T *__restrict__ val) {
+                          const T *__restrict__ val, bool split) {
     // FP32 instances let their dependents start now; FP64 ones do not (their
     // dependents are large FP64 launches whose early CTAs measured slower)
     if (sizeof(T) == 4) pdl_trigger();
@@ -1017,10 +1017,12 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
         // 3D: the coarse nodes of the coarse level's active chunks, a thread
         // each (every unknown is in one; the other nodes keep u = 0 and an f
         // that nothing reads); the coarse ghost rows are summed by k_ghost_rows
+        // (split: the coarse nodes whose neighbourhood is partly outside are
+        // left to k_descend_partial)
         int64_t i;
         const bool has = level_node(C, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, i);
         pdl_wait();
-        if (has) descend_node<T, D, FROM_R>(F, C, fc, uc, i);
+        if (has) descend_node<T, D, FROM_R>(F, C, fc, uc, i, split);
         return;
     }
     if (sizeof(T) == 8) {
@@ -1035,6 +1037,21 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nw = 32 * (int64_t)C.ng;
     if (t < nw) descend_ghost_row_warp_early<T, D, FROM_R>(F, gc, ptr, col, val, (int)(t >> 5));   // uniform over the warp
     else if (t - nw < C.nn) descend_node_early<T, D, FROM_R>(F, C, fc, uc, t - nw);
+}
+
+// 3D descent at the coarse inside nodes whose fine neighbourhood is partly
+// outside Omega_h (the box search of the partial transfer), a thread each:
+// kept out of k_descend so that its warps all take full weighting
+template <typename T>
+__global__ void k_descend_partial(LevelView<T> F, LevelView<T> C, T *__restrict__ fc,
+                                  const int32_t *__restrict__ list, int cnt) {
+    if (sizeof(T) == 4) pdl_trigger();
+    pdl_wait();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int64_t i = list[t];
+    fc[i] = partial_transfer_of<T, 3>(F, fine_image<3>(i, C.s0, C.s1, F.s0, F.s1), true,
+                                      [&](int64_t q) { return F.r[q]; });
 }
 
 // 3D descent, coarse ghost rows (extension + partial transfer at coarse ghost
@@ -1530,9 +1547,16 @@ void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom 
             pdl_launch(k_ghost_rows<T, true>, dim3(blocks_for(32 * (int64_t)C.ng)), dim3(kThreads), 0, s,
                        (const T *)F.r, F.gnode, gc, gf.gt_ptr, gf.gt_col, gt_val, C.ng);
         }
+        // the coarse nodes of full weighting first, then those whose fine
+        // neighbourhood is partly outside
         g_launches++;
         pdl_launch(k_descend<T, 3, true>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr,
-                   gf.gt_col, gt_val);
+                   gf.gt_col, gt_val, gf.npartial > 0);
+        if (gf.npartial > 0) {
+            g_launches++;
+            pdl_launch(k_descend_partial<T>, dim3(blocks_for(gf.npartial)), dim3(kThreads), 0, s, F, C, fc,
+                       (const int32_t *)gf.partial_coarse, gf.npartial);
+        }
         return;
     }
     constexpr bool from_r = sizeof(T) == 8;   // FP64: one defect pass first (see descend_item)
@@ -1550,9 +1574,11 @@ void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom 
     }
     g_launches++;
     if (gf.dim == 2)
-        pdl_launch(k_descend<T, 2, from_r>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
+        pdl_launch(k_descend<T, 2, from_r>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val,
+                   false);
     else
-        pdl_launch(k_descend<T, 3, from_r>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val);
+        pdl_launch(k_descend<T, 3, from_r>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr, gf.gt_col, gt_val,
+                   false);
 }
 
 template <typename T>

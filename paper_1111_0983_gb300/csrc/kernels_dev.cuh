@@ -612,8 +612,12 @@ __device__ __forceinline__ int64_t fine_image(int64_t X, int64_t cs0, int64_t cs
 
 // wait: call pdl_wait once the node types are read, before any value (the
 // types are fixed while a solve runs; the values come from earlier launches)
+// skipped: when not null, a neighbourhood that is not all members is not
+// searched: *skipped is set and 0 returned (the caller handles those nodes
+// in another launch)
 template <typename T, int D, typename Get>
-__device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior, Get value, bool wait = false) {
+__device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior, Get value, bool wait = false,
+                                 bool *skipped = nullptr) {
     const int cube = D == 2 ? 9 : 27;
     const unsigned full = (1u << cube) - 1u;
     unsigned member = 0;
@@ -634,6 +638,10 @@ __device__ T partial_transfer_of(const LevelView<T> &F, int64_t p, bool interior
     unsigned long long bestset = 0;   // the boxes of the largest size inside the set
     if (member == full) {
         best = 1;  // full weighting fast path
+    } else if (skipped) {
+        *skipped = true;
+        if (wait) pdl_wait();
+        return (T)0;
     } else {
         for (int b = 0; b < nbox; b++) {
             const unsigned m = box_mask<D>(b);
@@ -745,14 +753,21 @@ __device__ __forceinline__ T ghost_defect(const LevelView<T> &v, int q) {
 // the bound (FP64), each fine defect is then computed once instead of once
 // per coarse node whose 3^d neighbourhood holds it (9/4 times on average in
 // 2D).
+// full_only: nodes whose neighbourhood is not all inside are left to another
+// launch (their fc is not written)
 template <typename T, int D, bool FROM_R>
 __device__ __forceinline__ void descend_node(const LevelView<T> &F, const LevelView<T> &C, T *__restrict__ fc,
-                                             T *__restrict__ uc, int64_t i) {
+                                             T *__restrict__ uc, int64_t i, bool full_only = false) {
     uc[i] = 0;
-    fc[i] = (C.type[i] & NODE_KIND) == NODE_IN
-                ? partial_transfer_of<T, D>(F, fine_image<D>(i, C.s0, C.s1, F.s0, F.s1), true,
-                                            [&](int64_t q) { return FROM_R ? F.r[q] : inside_defect<T, D>(F, q); })
-                : (T)0;
+    if ((C.type[i] & NODE_KIND) != NODE_IN) {
+        fc[i] = (T)0;
+        return;
+    }
+    bool skipped = false;
+    const T v = partial_transfer_of<T, D>(F, fine_image<D>(i, C.s0, C.s1, F.s0, F.s1), true,
+                                          [&](int64_t q) { return FROM_R ? F.r[q] : inside_defect<T, D>(F, q); },
+                                          false, full_only ? &skipped : nullptr);
+    if (!skipped) fc[i] = v;
 }
 
 // the fine ghost defect that entry col of a ghost-transfer row weighs

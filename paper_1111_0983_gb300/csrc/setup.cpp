@@ -1136,6 +1136,22 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
     for (int l = 0; l + 1 < nl; l++) {
         build_extension(levels[l], levels[l + 1]);
         build_ghost_transfer(levels[l], levels[l + 1]);
+        if (dim == 3) {
+            HostLevel &F = levels[l];
+            const HostLevel &C = levels[l + 1];
+            F.partial_coarse.clear();
+            for (int64_t i = 0; i < C.nn; i++) {
+                if ((C.type[i] & NODE_KIND) != NODE_IN) continue;
+                const int64_t ci = i / C.stride[0], cj = (i / C.stride[1]) % C.n, ck = i % C.n;
+                const int64_t p = 2 * ci * F.stride[0] + 2 * cj * F.stride[1] + 2 * ck;
+                bool full = true;
+                for (int a = -1; a <= 1 && full; a++)
+                    for (int b = -1; b <= 1 && full; b++)
+                        for (int c2 = -1; c2 <= 1 && full; c2++)
+                            if ((F.type[p + a * F.stride[0] + b * F.stride[1] + c2] & NODE_KIND) != NODE_IN) full = false;
+                if (!full) F.partial_coarse.push_back((int32_t)i);
+            }
+        }
     }
     number_coarse_unknowns(levels.back());   // the inverse is built before the first solve
 }
