@@ -120,6 +120,10 @@ void alloc_data(gcmg_ctx *c, int l, DevData<T> &D, bool grids) {
     D.ew = upload<T>(c, ew.data(), ew.size());
     std::vector<T> gtv(L.gt_val.begin(), L.gt_val.end());
     D.gt_val = upload<T>(c, gtv.data(), gtv.size());
+    if (!L.partial_coarse.empty()) {
+        if constexpr (std::is_same<T, float>::value) D.pt_w = upload<T>(c, L.partial_wf.data(), L.partial_wf.size());
+        else D.pt_w = upload<T>(c, L.partial_wd.data(), L.partial_wd.size());
+    }
     ck(cudaStreamSynchronize(c->stream), "sync");
     if (grids) {
         D.u = dalloc<T>(c, L.nn);
@@ -553,7 +557,7 @@ T *cycle(gcmg_ctx *c, int l, T *u) {
     // extension at the coarse ghosts (Sec. 2.6), and e_2h = 0: one launch
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
     launch_descend<T>(at(l, u), at(l + 1, D[l + 1].u), c->G[l], D[l].gt_val, D[l + 1].f, D[l + 1].gg, D[l + 1].u,
-                      c->stream);
+                      c->stream, D[l].pt_w);
     timer_mark(c, GCMG_KERNEL_RESTRICT, l);
     const int gam = (l + 1 == last) ? 1 : c->p.gamma;
     T *uc = D[l + 1].u;

@@ -131,6 +131,11 @@ struct HostLevel {
     // partial transfer there searches its boxes; the others take full
     // weighting), in increasing order
     std::vector<int32_t> partial_coarse;
+    // their 27 partial-transfer weights over this level's inside set, slot
+    // major (27 x list size), computed in FP32 and in FP64 with the
+    // operations of the device's partial transfer in the same order
+    std::vector<float> partial_wf;
+    std::vector<double> partial_wd;
     // shared-memory relaxation programs: the junction zone (depends on bc)
     // and, in 2D, the boundary blocks of the lambda extra sweeps
     LocalProgram junction, boundary;
@@ -273,6 +278,7 @@ struct DevData {
     T *gtmp = nullptr;   // ng new ghost values of a Jacobi sweep
     T *ew = nullptr;     // EMAX * ne extension weights, slot major
     T *gt_val = nullptr; // ghost transfer weights to the next level
+    T *pt_w = nullptr;   // HostLevel::partial_wf / partial_wd
     T *Ainv = nullptr;   // nunk * nunk (coarsest level)
     T *js_inv = nullptr; // inverses of the junction-solve components
     T *js_r = nullptr;   // defects of the junction-solve equations (padded layout, zero pads)

@@ -1042,16 +1042,32 @@ __global__ void k_descend(LevelView<T> F, LevelView<T> C, T *__restrict__ fc, T 
 // 3D descent at the coarse inside nodes whose fine neighbourhood is partly
 // outside Omega_h (the box search of the partial transfer), a thread each:
 // kept out of k_descend so that its warps all take full weighting
+// The weights (w, 27 per node, slot major) come from the host, computed with
+// the device's operations in its order; the sum is that of partial_transfer_of.
 template <typename T>
 __global__ void k_descend_partial(LevelView<T> F, LevelView<T> C, T *__restrict__ fc,
-                                  const int32_t *__restrict__ list, int cnt) {
+                                  const int32_t *__restrict__ list, const T *__restrict__ w, int cnt) {
     if (sizeof(T) == 4) pdl_trigger();
-    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = 0, p = 0;
+    T wc[27];
+    if (t < cnt) {   // set up once: read before the wait
+        i = list[t];
+        p = fine_image<3>(i, C.s0, C.s1, F.s0, F.s1);
+#pragma unroll
+        for (int c = 0; c < 27; c++) wc[c] = w[(int64_t)c * cnt + t];
+    }
+    pdl_wait();
     if (t >= cnt) return;
-    const int64_t i = list[t];
-    fc[i] = partial_transfer_of<T, 3>(F, fine_image<3>(i, C.s0, C.s1, F.s0, F.s1), true,
-                                      [&](int64_t q) { return F.r[q]; });
+    T val[27];
+#pragma unroll
+    for (int c = 0; c < 27; c++)
+        val[c] = wc[c] != (T)0 ? F.r[p + (c / 9 - 1) * F.s0 + ((c / 3) % 3 - 1) * F.s1 + (c % 3 - 1)] : (T)0;
+    T acc = 0;
+#pragma unroll
+    for (int c = 0; c < 27; c++)
+        if (wc[c] != (T)0) acc += wc[c] * val[c];
+    fc[i] = acc;
 }
 
 // 3D descent, coarse ghost rows (extension + partial transfer at coarse ghost
@@ -1522,7 +1538,7 @@ void launch_restrict(const LevelView<T> &F, const LevelView<T> &C, int dim, T *f
 
 template <typename T>
 void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
-                    T *uc, cudaStream_t s) {
+                    T *uc, cudaStream_t s, const T *pt_w) {
     const bool warp_rows = sizeof(T) == 4 && gf.dim == 2;   // 2D FP32: a warp per coarse ghost row
     const int64_t n = gf.dim == 3 ? level_threads(C, true) : warp_rows ? C.nn + 32 * (int64_t)C.ng
                                                                       : std::max<int64_t>(C.nn, C.ng);
@@ -1551,11 +1567,11 @@ void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom 
         // neighbourhood is partly outside
         g_launches++;
         pdl_launch(k_descend<T, 3, true>, dim3(blocks_for(n)), dim3(kThreads), 0, s, F, C, fc, gc, uc, gf.gt_ptr,
-                   gf.gt_col, gt_val, gf.npartial > 0);
-        if (gf.npartial > 0) {
+                   gf.gt_col, gt_val, gf.npartial > 0 && pt_w != nullptr);
+        if (gf.npartial > 0 && pt_w) {
             g_launches++;
             pdl_launch(k_descend_partial<T>, dim3(blocks_for(gf.npartial)), dim3(kThreads), 0, s, F, C, fc,
-                       (const int32_t *)gf.partial_coarse, gf.npartial);
+                       (const int32_t *)gf.partial_coarse, pt_w, gf.npartial);
         }
         return;
     }
@@ -1821,7 +1837,7 @@ void launch_add_correction(const DevGeom &g, double *u64, const float *e32, cuda
     template void launch_junction_solve<T>(const LevelView<T> &, const DevGeom &, const T *, T *, cudaStream_t, \
                                            const LocalView<T> *);                                                \
     template void launch_descend<T>(const LevelView<T> &, const LevelView<T> &, const DevGeom &, const T *, T *, T *, \
-                                    T *, cudaStream_t);                                                            \
+                                    T *, cudaStream_t, const T *);                                                 \
     template void launch_mask_unknowns<T>(const uint8_t *, T *, int64_t, cudaStream_t);            \
     template void launch_rb_zmarch<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);    \
     template void launch_rb_stream3d<T>(const LevelView<T> &, T *, const DevGeom &, cudaStream_t);  \

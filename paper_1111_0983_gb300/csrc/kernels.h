@@ -57,7 +57,7 @@ void launch_restrict_interior(const LevelView<T> &F, const LevelView<T> &C, int 
 // spot), coarse ghost data = transferred fine ghost defects, coarse u = 0
 template <typename T>
 void launch_descend(const LevelView<T> &F, const LevelView<T> &C, const DevGeom &gf, const T *gt_val, T *fc, T *gc,
-                    T *uc, cudaStream_t s);
+                    T *uc, cudaStream_t s, const T *pt_w = nullptr);
 template <typename T>
 void launch_ghost_transfer(const T *rf, const int32_t *fgnode, const int32_t *ptr, const int32_t *col, const T *val,
                            T *gc, int ngc, cudaStream_t s);

@@ -1062,6 +1062,67 @@ bool build_span_items(HostLevel &L, int C, int seg) {
     return true;
 }
 
+// The partial transfer's weights at fine image p over the inside set, in T,
+// with the device's operations in its order: the 3^3 members, the largest
+// boxes inside them (codes per axis 0 [-1,1], 1 [-1,0], 2 [0,1], 3 [0,0]; box
+// b has code (b >> 2 a) & 3 on axis a), then per member the sum over those
+// boxes, in increasing b, of the product over the axes of the 1D weights,
+// divided by their number.  Zero for non-members and when no box fits.
+template <typename T>
+static void partial_weights_t(const HostLevel &F, int64_t p, T *w) {
+    static const int LO[4] = {-1, -1, 0, 0}, HI[4] = {1, 0, 1, 0};
+    auto w1d = [](int iv, int o) -> T {
+        switch (iv) {
+            case 0: return o == 0 ? (T)0.5 : (T)0.25;
+            case 1: return o == 1 ? (T)0 : (T)0.5;
+            case 2: return o == -1 ? (T)0 : (T)0.5;
+            default: return o == 0 ? (T)1 : (T)0;
+        }
+    };
+    unsigned member = 0;
+    int off[27][3];
+    for (int c = 0; c < 27; c++) {
+        int rem = c;
+        int64_t q = p;
+        for (int a = 2; a >= 0; a--) {
+            off[c][a] = rem % 3 - 1;
+            rem /= 3;
+            q += off[c][a] * F.stride[a];
+        }
+        if ((F.type[q] & NODE_KIND) == NODE_IN) member |= 1u << c;
+    }
+    int best = 0, count = 0;
+    uint64_t bestset = 0;
+    for (int b = 0; b < 64; b++) {
+        unsigned m = 0;
+        for (int c = 0; c < 27; c++) {
+            bool in = true;
+            for (int a = 0; a < 3; a++) {
+                const int iv = (b >> (2 * a)) & 3;
+                if (off[c][a] < LO[iv] || off[c][a] > HI[iv]) in = false;
+            }
+            if (in) m |= 1u << c;
+        }
+        if (m & ~member) continue;
+        const int sz = __builtin_popcount(m);
+        if (sz > best) { best = sz; count = 1; bestset = (uint64_t)1 << b; }
+        else if (sz == best) { count++; bestset |= (uint64_t)1 << b; }
+    }
+    for (int c = 0; c < 27; c++) {
+        w[c] = (T)0;
+        if (count == 0 || !((member >> c) & 1u)) continue;
+        T wc = 0;
+        for (int b = 0; b < 64; b++) {
+            if (!((bestset >> b) & 1)) continue;
+            T wb = 1;
+            for (int a = 0; a < 3; a++) wb *= w1d((b >> (2 * a)) & 3, off[c][a]);
+            wc += wb;
+        }
+        wc /= (T)count;
+        w[c] = wc;
+    }
+}
+
 void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double delta_over_h,
                      std::vector<HostLevel> &levels, double h0, const double *origin) {
     if (!(h0 > 0.0)) h0 = 2.0 / (n - 1);
@@ -1150,6 +1211,22 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
                         for (int c2 = -1; c2 <= 1 && full; c2++)
                             if ((F.type[p + a * F.stride[0] + b * F.stride[1] + c2] & NODE_KIND) != NODE_IN) full = false;
                 if (!full) F.partial_coarse.push_back((int32_t)i);
+            }
+            const size_t m = F.partial_coarse.size();
+            F.partial_wf.assign(27 * m, 0.0f);
+            F.partial_wd.assign(27 * m, 0.0);
+            for (size_t t = 0; t < m; t++) {
+                const int64_t i = F.partial_coarse[t];
+                const int64_t ci = i / C.stride[0], cj = (i / C.stride[1]) % C.n, ck = i % C.n;
+                const int64_t p = 2 * ci * F.stride[0] + 2 * cj * F.stride[1] + 2 * ck;
+                float wf[27];
+                double wd[27];
+                partial_weights_t<float>(F, p, wf);
+                partial_weights_t<double>(F, p, wd);
+                for (int c = 0; c < 27; c++) {
+                    F.partial_wf[(size_t)c * m + t] = wf[c];
+                    F.partial_wd[(size_t)c * m + t] = wd[c];
+                }
             }
         }
     }
