@@ -668,6 +668,70 @@ __global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, unsigned lo
     reduce_norm(norm, __longlong_as_double((long long)mb));
 }
 
+// The interpolation of the coarse correction added at every unknown of a 3D
+// level (Sec. 2.6; the sums of prolong_node_early): the inside nodes over
+// the row segments, G at once, lane l the nodes k0 + l and k0 + l + 32 of
+// each, every parent's type and value loaded before the first sum; past
+// them the ghosts, a thread each.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_prolong_rows(LevelView<T> F, LevelView<T> C, const T *__restrict__ e,
+                                                      T *__restrict__ out) {
+    if (sizeof(T) == 4) pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int n = F.n, nseg = F.nsegs;
+    pdl_wait();
+    for (int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G; q < nseg; q += nw * G) {
+        T ev[2 * G][8], old[2 * G];
+        bool use[2 * G][8], on[2 * G];
+        int64_t pp[2 * G];
+        int cnt[2 * G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            const int2 sg = q + g < nseg ? F.segs[q + g] : make_int2(0, 0x0000ffff);
+            const int i = sg.x / n, j = sg.x - (sg.x / n) * n;
+            const int k0 = sg.y & 0xffff, k1 = (int)((unsigned)sg.y >> 16);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int e_ = 2 * g + h, k = k0 + lane + 32 * h;
+                on[e_] = k <= k1;
+                pp[e_] = (int64_t)sg.x * n + k;
+                const int n1 = (i & 1) ? 2 : 1, n2 = (j & 1) ? 2 : 1, n3 = (k & 1) ? 2 : 1;
+                cnt[e_] = n1 * n2 * n3;
+                const int64_t X0 = (int64_t)(i / 2) * C.s0 + (int64_t)(j / 2) * C.s1 + k / 2;
+#pragma unroll
+                for (int s8 = 0; s8 < 8; s8++) {
+                    const int a = s8 >> 2, b = (s8 >> 1) & 1, c = s8 & 1;
+                    const int64_t X = X0 + a * C.s0 + b * C.s1 + c;
+                    use[e_][s8] = false;
+                    if (on[e_] && a < n1 && b < n2 && c < n3) {
+                        const uint8_t kc = C.type[X] & NODE_KIND;
+                        use[e_][s8] = kc == NODE_IN || kc == NODE_GHOST;   // parents in Omega_2h u Gamma_2h
+                    }
+                    ev[e_][s8] = use[e_][s8] ? e[X] : (T)0;
+                }
+                old[e_] = on[e_] ? out[pp[e_]] : (T)0;
+            }
+        }
+#pragma unroll
+        for (int e_ = 0; e_ < 2 * G; e_++) {
+            if (!on[e_]) continue;
+            T num = 0, den = 0;
+            const T w = (T)1 / (T)cnt[e_];   // a power of two: exact
+#pragma unroll
+            for (int s8 = 0; s8 < 8; s8++)
+                if (use[e_][s8]) {
+                    num += w * ev[e_][s8];
+                    den += w;
+                }
+            const T val = den > (T)0 ? num / den : (T)0;
+            out[pp[e_]] = old[e_] + val;
+        }
+    }
+    for (int qg = (int)(blockIdx.x * blockDim.x + threadIdx.x); qg < F.ng; qg += (int)(gridDim.x * blockDim.x))
+        prolong_node<T, 3>(F, C, e, out, true, F.gnode[qg]);
+}
+
 // u64 += e32 at the inside nodes over the row segments (G at once) and, past
 // them, at the ghosts
 template <int G>
@@ -1609,6 +1673,13 @@ template <typename T>
 void launch_prolong(const LevelView<T> &F, const LevelView<T> &C, int dim, const T *e, T *out, bool add,
                     cudaStream_t s) {
     g_launches++;
+    if (dim == 3 && add && F.nsegs > 0) {   // inside nodes over the row segments, then the ghosts
+        constexpr int G = 1;
+        static unsigned resident = 0;
+        pdl_launch(k_prolong_rows<T, G>, dim3(segment_blocks(k_prolong_rows<T, G>, F.nsegs, G, resident)), dim3(256),
+                   0, s, F, C, e, out);
+        return;
+    }
     const int64_t nt = level_threads(F, add);
     if (dim == 2) pdl_launch(k_prolong<T, 2>, dim3(blocks_for(nt)), dim3(kThreads), 0, s, F, C, e, out, add);
     else pdl_launch(k_prolong<T, 3>, dim3(blocks_for(nt)), dim3(kThreads), 0, s, F, C, e, out, add);
