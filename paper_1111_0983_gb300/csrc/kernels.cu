@@ -910,13 +910,14 @@ __global__ void __launch_bounds__(BC_THREADS) k_boundary3d_cluster(LevelView<T> 
 template <typename T, int D, int LIST_M>
 __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
     // entries i0 + m * (threads of the launch), m < LIST_M: the loads of all
-    // of a thread's entries are issued before its first update
-    pdl_wait();
+    // of a thread's entries are issued before its first update; the list is
+    // fixed and read before the wait for the previous launch
     const int nt = (int)(gridDim.x * blockDim.x), i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     int64_t p[LIST_M];
     T sum[LIST_M];
 #pragma unroll
     for (int m = 0; m < LIST_M; m++) p[m] = i0 + m * nt < cnt ? list[i0 + m * nt] : -1;
+    pdl_wait();
 #pragma unroll
     for (int m = 0; m < LIST_M; m++)
         if (p[m] >= 0) sum[m] = mul_rn(v.h2, v.f[p[m]]) + neighbour_sum<T, D>(v.u, p[m], v.s0, v.s1);   // h^2 f rounded on its own
@@ -935,28 +936,38 @@ __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int 
 template <typename T, int LIST_M>
 __global__ void k_rb_list_store(LevelView<T> v, const int32_t *__restrict__ list, const int32_t *__restrict__ src,
                                 int cnt, const int32_t *__restrict__ glist, int gcnt) {
-    // items i0 + m * (threads of the launch), m < LIST_M, loads first (as k_rb_list)
-    pdl_wait();
+    // items i0 + m * (threads of the launch), m < LIST_M, loads first (as
+    // k_rb_list); the lists, sources and ghost nodes are fixed and read
+    // before the wait for the previous launch
     const int nt = (int)(gridDim.x * blockDim.x), i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     T x[LIST_M][6], fv[LIST_M], gv[LIST_M];
     int64_t p[LIST_M];
     int kind[LIST_M];   // 0 none, 1 red entry, 2 ghost store
+    int sk[LIST_M][6], gq[LIST_M];
 #pragma unroll
     for (int m = 0; m < LIST_M; m++) {
         const int i = i0 + m * nt;
         kind[m] = i < cnt ? 1 : i - cnt < gcnt ? 2 : 0;
+        p[m] = 0;
+        gq[m] = 0;
         if (kind[m] == 1) {
             p[m] = list[i];
 #pragma unroll
-            for (int k = 0; k < 6; k++) {
-                const int sk = src[(int64_t)k * cnt + i];
-                x[m][k] = sk >= 0 ? v.u[sk] : v.gtmp[-1 - sk];
-            }
+            for (int k = 0; k < 6; k++) sk[m][k] = src[(int64_t)k * cnt + i];
+        } else if (kind[m] == 2) {
+            gq[m] = glist ? glist[i - cnt] : i - cnt;
+            p[m] = v.gnode[gq[m]];
+        }
+    }
+    pdl_wait();
+#pragma unroll
+    for (int m = 0; m < LIST_M; m++) {
+        if (kind[m] == 1) {
+#pragma unroll
+            for (int k = 0; k < 6; k++) x[m][k] = sk[m][k] >= 0 ? v.u[sk[m][k]] : v.gtmp[-1 - sk[m][k]];
             fv[m] = v.f[p[m]];
         } else if (kind[m] == 2) {
-            const int q = glist ? glist[i - cnt] : i - cnt;
-            p[m] = v.gnode[q];
-            gv[m] = v.gtmp[q];
+            gv[m] = v.gtmp[gq[m]];
         }
     }
 #pragma unroll
@@ -973,45 +984,64 @@ __global__ void k_rb_list_store(LevelView<T> v, const int32_t *__restrict__ list
 }
 
 // Ghost relaxation, Eqs. (dir2d)/(neu2d): new value from the current values.
+// The ghost's stencil, weights, coefficient and node are fixed while a
+// solve runs: they are read before the wait for the previous launch, the
+// values of u and g after it (one round trip instead of three).
 template <typename T, int K>
-__global__ void k_ghost_new(LevelView<T> v) {
+__device__ __forceinline__ void ghost_new_early(const LevelView<T> &v, int q, bool on) {
+    int32_t st[K], gn = 0;
+    T w[K], gc = 0;
+    if (on) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            st[k] = v.gstn[(int64_t)k * v.ng + q];
+            w[k] = v.gw[(int64_t)k * v.ng + q];
+        }
+        gc = v.gc[q];
+        gn = v.gnode[q];
+    }
     pdl_wait();
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= v.ng) return;
+    if (!on) return;
     T s = 0;
 #pragma unroll
-    for (int k = 0; k < K; k++) s += v.gw[(int64_t)k * v.ng + q] * v.u[v.gstn[(int64_t)k * v.ng + q]];
-    v.gtmp[q] = v.u[v.gnode[q]] + v.gc[q] * (v.gg[q] - s);
+    for (int k = 0; k < K; k++) s += w[k] * v.u[st[k]];
+    v.gtmp[q] = v.u[gn] + gc * (v.gg[q] - s);
+}
+
+template <typename T, int K>
+__global__ void k_ghost_new(LevelView<T> v) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    ghost_new_early<T, K>(v, q, q < v.ng);
 }
 
 // same update restricted to a list of ghost numbers
 template <typename T, int K>
 __global__ void k_ghost_new_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
-    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int q = list[i];
-    T s = 0;
-#pragma unroll
-    for (int k = 0; k < K; k++) s += v.gw[(int64_t)k * v.ng + q] * v.u[v.gstn[(int64_t)k * v.ng + q]];
-    v.gtmp[q] = v.u[v.gnode[q]] + v.gc[q] * (v.gg[q] - s);
+    ghost_new_early<T, K>(v, i < cnt ? list[i] : 0, i < cnt);
 }
 
 template <typename T>
 __global__ void k_ghost_store_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
-    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int q = 0;
+    int32_t gn = 0;
+    if (i < cnt) {   // fixed: read before the wait
+        q = list[i];
+        gn = v.gnode[q];
+    }
+    pdl_wait();
     if (i >= cnt) return;
-    const int q = list[i];
-    v.u[v.gnode[q]] = v.gtmp[q];
+    v.u[gn] = v.gtmp[q];
 }
 
 template <typename T>
 __global__ void k_ghost_store(LevelView<T> v) {
-    pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t gn = q < v.ng ? v.gnode[q] : 0;   // fixed: read before the wait
+    pdl_wait();
     if (q >= v.ng) return;
-    v.u[v.gnode[q]] = v.gtmp[q];
+    v.u[gn] = v.gtmp[q];
 }
 
 // shared-memory programs (junction zones, 2D boundary blocks), one CTA per
