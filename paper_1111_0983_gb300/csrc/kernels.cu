@@ -911,7 +911,9 @@ template <typename T, int D, int LIST_M>
 __global__ void k_rb_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
     // entries i0 + m * (threads of the launch), m < LIST_M: the loads of all
     // of a thread's entries are issued before its first update; the list is
-    // fixed and read before the wait for the previous launch
+    // fixed and read before the wait for the previous launch, and the next
+    // launch may start reading its own fixed data meanwhile
+    pdl_trigger();
     const int nt = (int)(gridDim.x * blockDim.x), i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     int64_t p[LIST_M];
     T sum[LIST_M];
@@ -939,6 +941,7 @@ __global__ void k_rb_list_store(LevelView<T> v, const int32_t *__restrict__ list
     // items i0 + m * (threads of the launch), m < LIST_M, loads first (as
     // k_rb_list); the lists, sources and ghost nodes are fixed and read
     // before the wait for the previous launch
+    pdl_trigger();
     const int nt = (int)(gridDim.x * blockDim.x), i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     T x[LIST_M][6], fv[LIST_M], gv[LIST_M];
     int64_t p[LIST_M];
@@ -1010,6 +1013,7 @@ __device__ __forceinline__ void ghost_new_early(const LevelView<T> &v, int q, bo
 
 template <typename T, int K>
 __global__ void k_ghost_new(LevelView<T> v) {
+    pdl_trigger();   // the next launch reads its fixed data while this one runs
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     ghost_new_early<T, K>(v, q, q < v.ng);
 }
@@ -1017,12 +1021,14 @@ __global__ void k_ghost_new(LevelView<T> v) {
 // same update restricted to a list of ghost numbers
 template <typename T, int K>
 __global__ void k_ghost_new_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     ghost_new_early<T, K>(v, i < cnt ? list[i] : 0, i < cnt);
 }
 
 template <typename T>
 __global__ void k_ghost_store_list(LevelView<T> v, const int32_t *__restrict__ list, int cnt) {
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int q = 0;
     int32_t gn = 0;
@@ -1037,6 +1043,7 @@ __global__ void k_ghost_store_list(LevelView<T> v, const int32_t *__restrict__ l
 
 template <typename T>
 __global__ void k_ghost_store(LevelView<T> v) {
+    pdl_trigger();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t gn = q < v.ng ? v.gnode[q] : 0;   // fixed: read before the wait
     pdl_wait();
