@@ -576,7 +576,6 @@ __device__ __forceinline__ double abs_keep_nan(double v) {
 // u and f there.  The same sums in the same order as the fused sweeps.
 template <typename T, int G>
 __global__ void __launch_bounds__(256) k_rb_rows(LevelView<T> v, const int2 *__restrict__ segs, int nseg, int colour) {
-    if (sizeof(T) == 4) pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
     int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
@@ -629,7 +628,7 @@ __global__ void __launch_bounds__(256) k_rb_rows(LevelView<T> v, const int2 *__r
 template <typename T, int G, bool MIXED>
 __global__ void __launch_bounds__(256) k_defect_rows(LevelView<T> v, unsigned long long *norm, float *__restrict__ f32,
                                                     float *__restrict__ e32) {
-    if (MIXED || sizeof(T) == 4) pdl_trigger();
+    if (MIXED) pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
     const int n = v.n, nseg = v.nsegs;
@@ -1058,7 +1057,6 @@ __global__ void k_ghost_store(LevelView<T> v) {
 template <typename T, int D>
 __global__ void __launch_bounds__(LOCAL_THREADS, sizeof(T) == 4 && D == 2 ? 2 : 1)
     k_local(LocalView<T> J, int lead_ghost, int reps) {
-    if (sizeof(T) == 4 && D == 3) pdl_trigger();   // (3D FP32: the next launch may start at once)
     pdl_wait();
     local_body<T, D>(J, J.u, J.wb ? J.wb : J.u, blockIdx.x, lead_ghost, reps);
 }
@@ -1081,7 +1079,6 @@ __global__ void k_defect_interior(LevelView<T> v, bool zero_rest, unsigned long 
 
 template <typename T, int K>
 __global__ void k_defect_ghost(LevelView<T> v, unsigned long long *norm) {
-    if (sizeof(T) == 4) pdl_trigger();
     pdl_wait();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const double val = q < v.ng ? defect_ghost_item<T, K>(v, q) : 0.0;
