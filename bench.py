@@ -100,6 +100,9 @@ def parse():
                          "kernels matching KERNEL_REGEX in an ncu CSV (dram__bytes_read.sum, "
                          "dram__bytes_write.sum) and exit; a regex ending in '@largest' keeps only the "
                          "launches with the largest grid (the fine level)")
+    ap.add_argument("--traffic-group", type=int, default=1,
+                    help="with --write-traffic: bytes of a unit of this many consecutive launches (2 for the 3D "
+                         "interior sweep, whose red and black half-sweeps are two launches)")
     return ap.parse_args()
 
 
@@ -200,9 +203,10 @@ def traffic_for(kernel_key):
     return rec.get("dram_bytes_per_launch") if rec.get("kernels_sha") == kernels_sha() else None
 
 
-def write_traffic(csv_path, kernel_regex, key):
+def write_traffic(csv_path, kernel_regex, key, group=1):
     """Mean dram__bytes_read.sum + dram__bytes_write.sum per launch of the
-    matching kernels in an ncu --csv log, into profiles/traffic.json."""
+    matching kernels in an ncu --csv log (times `group`: the bytes of a unit
+    of that many launches), into profiles/traffic.json."""
     import csv
     import re
     per, grid = {}, {}
@@ -232,8 +236,8 @@ def write_traffic(csv_path, kernel_regex, key):
             data = json.load(fh)
     except (OSError, ValueError):
         data = {}
-    data[key] = {"dram_bytes_per_launch": sum(per.values()) / len(per), "launches": len(per),
-                 "kernel_regex": kernel_regex, "kernels_sha": kernels_sha()}
+    data[key] = {"dram_bytes_per_launch": group * sum(per.values()) / len(per), "launches": len(per),
+                 "launches_per_unit": group, "kernel_regex": kernel_regex, "kernels_sha": kernels_sha()}
     with open(path, "w") as fh:
         json.dump(data, fh, indent=1, sort_keys=True)
         fh.write("\n")
@@ -765,7 +769,12 @@ def run_gcmg(args):
              "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
              "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic_for(kname),
              "alg_bytes_per_launch": alg_bytes, "alg_bytes_note": f"{3 * elt} B x {n_in} inside nodes"
-             if P.dim == 3 else None, "avg_launch_ms": avg_ms, "launches_timed": k_launches}
+             if P.dim == 3 else None, "avg_launch_ms": avg_ms, "launches_timed": k_launches,
+             "share_of_solve": (k_ms / ms) if ms > 0 else None}
+    if P.dim == 3 and kern == "rows":
+        sweep["launch_note"] = ("a unit is one sweep: the red and the black launch, timed together; the kernels "
+                                "that take most of the solve's time are the boundary phases' short list launches "
+                                "(latency bound), see the launch list under profiles/")
     roofline = sweep
     if b_launches:
         bname = f"{'relax2d' if merged else 'local_bz'}_{'f64' if precision == 0 else 'f32'}_{args.config}"
@@ -875,7 +884,7 @@ def main():
     args = parse()
     SWEEP3D, BOUNDARY3D = args.sweep3d, args.boundary3d
     if args.write_traffic:
-        write_traffic(*args.write_traffic)
+        write_traffic(*args.write_traffic, group=args.traffic_group)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -407,12 +407,12 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         if (bzv.wb) pending = &bzv;
     } else {
-        // 3D: one launch a phase (default); gcmg_set_boundary3d 1: the ghost
-        // sweep, the band sweeps and (on global lists) the junction sweeps of
-        // small levels as one thread-block cluster with hardware barriers
-        // between the phases, on large levels the junction sweeps alone as
-        // one cluster; 2: all phases as one grid with software barriers
-        bool done = false, zdone = false, zcluster = false;
+        // 3D: one launch a phase (default); gcmg_set_boundary3d 1: on levels
+        // whose lists hold at most kClusterWork entries the ghost sweep, the
+        // band sweeps and (on global lists) the junction sweeps as one
+        // thread-block cluster with hardware barriers between the phases;
+        // 2: all phases as one grid with software barriers
+        bool done = false, zdone = false;
         BoundaryProgram3 P;
         if (dim == 3 && c->p.smoother == 0 && g.ng > 0) {
             P.red = g.red;
@@ -439,12 +439,11 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
                 done = launch_boundary3d<T>(v, P, c->bar_phantom, c->stream);
                 zdone = done && jglob;
             } else if (c->cluster3d) {
-                const int64_t big = std::max<int64_t>({(int64_t)g.ng, g.nred, g.nblack});
+                const int64_t big = std::max<int64_t>({(int64_t)g.ng, g.nred, g.nblack, (int64_t)P.nzred,
+                                                       (int64_t)P.nzblack, (int64_t)P.nzghost});
                 if (big <= kClusterWork) {
                     done = launch_boundary3d_cluster<T>(v, P, c->stream);
                     zdone = done && jglob;
-                } else {
-                    zcluster = jglob;
                 }
             }
             if (done) timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
@@ -454,7 +453,7 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         // whose updates read the ghosts' new values from gtmp (red_sources):
         // three launches a band or junction sweep instead of four
         const bool merged = !done && dim == 3 && extra && c->p.smoother == 0 && g.ng > 0 && g.red_src &&
-                            !c->coop3d && !c->cluster3d;
+                            !c->coop3d;
         if (merged) {
             const bool zmerge = !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 &&
                                 !g.jz.in_smem && g.jz.zred_src;
@@ -484,12 +483,6 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
                     launch_rb_list<T>(v, dim, g.black, g.nblack, c->stream);
                     launch_ghost_relax<T>(v, dim, c->stream);
                 }
-            if (zcluster) {   // the junction-zone sweeps alone, as one cluster
-                BoundaryProgram3 Z = P;
-                Z.lead = 0;
-                Z.lambda = 0;
-                zdone = launch_boundary3d_cluster<T>(v, Z, c->stream);
-            }
             if (dim == 3 && c->p.smoother == 0 && g.ng > 0) timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
         }
         if (!extra || zdone) return v.u;
