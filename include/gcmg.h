@@ -319,13 +319,14 @@ gcmg_status gcmg_kernel_timing_ex(gcmg_ctx *ctx, int64_t *launches, double *tota
 
 /* How the 3D boundary relaxation (the ghost sweep, the lambda band sweeps
  * of Sec. 3.2 and the junction sweeps) is launched; every mode gives the same
- * results bitwise.  mode 0 (default): one launch per phase; 1: on levels
- * whose ghost and band lists hold at most 65,536 entries all phases as one
- * thread-block cluster of 16 CTAs with hardware barriers between them, on
- * larger levels one launch per phase with the junction sweeps as one
- * cluster; 2: all phases as one grid with software barriers.  Modes 1 and 2
- * measured slower on GB300 (the per-phase launches overlap inside the solve's
- * graph and spread each phase's gathers over every SM).  Not in the paper. */
+ * results bitwise.  mode 0 (default): one launch per phase, the store of
+ * each Jacobi ghost sweep merged into the launch of the next red band or
+ * junction-zone sweep; 1: on levels whose ghost, band and junction lists
+ * hold at most 65,536 entries all phases as one thread-block cluster of 16
+ * CTAs with hardware barriers between them, mode 0 on the other levels; 2:
+ * all phases as one grid with software barriers.  Modes 1 and 2 measured
+ * slower on GB300 (the per-phase launches overlap inside the solve's graph
+ * and spread each phase's gathers over every SM).  Not in the paper. */
 gcmg_status gcmg_set_boundary3d(gcmg_ctx *ctx, int mode);
 
 /* Mode 2 of gcmg_set_boundary3d with test controls: every software barrier
