@@ -356,6 +356,20 @@ gcmg_status gcmg_set_sweep3d(gcmg_ctx *ctx, int variant);
  * GCMG_E_ARG for values out of range.  Not in the paper. */
 gcmg_status gcmg_set_span3d(gcmg_ctx *ctx, int columns, int planes);
 
+/* 3D junction zone (the mu junction sweeps; not in the paper): enable = 1
+ * (default) splits a zone component of more than 1,500 nodes into blocks of
+ * 8^3 nodes relaxed in shared memory, each updating the zone within 4 mu
+ * nodes of its block and writing back only its own nodes (two launches a
+ * relaxation instead of three a sweep; the same results bitwise); 0 keeps
+ * whole components (a large one then runs on global lists).  Rebuilds the
+ * junction programs of every level; GCMG_E_ARG for a null context. */
+gcmg_status gcmg_set_junction_blocks(gcmg_ctx *ctx, int enable);
+
+/* How level l's junction sweeps run: 0 on global lists (or no junction
+ * zone), 1 whole components in shared memory, 2 blocks in shared memory;
+ * -1 for a bad context or level.  Not in the paper. */
+int gcmg_junction_mode(const gcmg_ctx *ctx, int l);
+
 /* Sweep 2's work on level l: number of items (0: the level uses sweep 1)
  * and nodes a lane holds.  Not in the paper. */
 gcmg_status gcmg_span3d_info(const gcmg_ctx *ctx, int l, int *items, int *columns);

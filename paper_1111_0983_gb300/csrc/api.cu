@@ -263,6 +263,7 @@ void upload_program(gcmg_ctx *c, const LocalProgram &J, LocalDev &z) {
     z.zblack = upload<int32_t>(c, J.zblack.data(), J.zblack.size());
     z.zghost = upload<int32_t>(c, J.zghost.data(), J.zghost.size());
     z.zred_src = J.zred_src.empty() ? nullptr : upload<int32_t>(c, J.zred_src.data(), J.zred_src.size());
+    z.blocked = J.blocked;
     std::vector<int32_t> wb;
     for (int k = 0; k < z.ncomp; k++)
         wb.insert(wb.end(), J.lnode.begin() + J.node_off[k], J.lnode.begin() + J.node_off[k] + J.wb_cnt[k]);
@@ -494,7 +495,11 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
     }
     if (pending) launch_local_copyback<T>(*pending, c->stream);
     if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
-        if (g.jz.in_smem) {
+        if (g.jz.in_smem && g.jz.blocked) {   // overlapping blocks: write back through wb, then copy
+            const LocalView<T> J = lview<T>(g.jz, v, wb);
+            launch_local<T>(J, dim, 0, c->p.junction_sweeps, c->stream);
+            launch_local_copyback<T>(J, c->stream);
+        } else if (g.jz.in_smem) {
             launch_local<T>(lview<T>(g.jz, v), dim, 0, c->p.junction_sweeps, c->stream);
         } else {
             for (int k = 0; k < c->p.junction_sweeps; k++) {
@@ -1137,7 +1142,7 @@ gcmg_status gcmg_set_bc_types(gcmg_ctx *c, int l, const uint8_t *types) {
         if (c->p.junction_solve) {
             L.js_dirty = true;                                  // rebuilt before the next solve
         } else {
-            build_junction(L, c->p.junction_radius);
+            build_junction(L, c->p.junction_radius, c->junction_blocks ? c->p.junction_sweeps : 0);
             upload_program(c, L.junction, c->G[l].jz);
             check_program_fits(c, c->G[l].jz);
         }
@@ -1196,6 +1201,31 @@ gcmg_status gcmg_set_span3d(gcmg_ctx *c, int columns, int planes) {
         ck(cudaStreamSynchronize(c->stream), "sync");
     })
     return GCMG_OK;
+}
+
+gcmg_status gcmg_set_junction_blocks(gcmg_ctx *c, int enable) {
+    if (!c) return GCMG_E_ARG;
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        destroy_graph(c);
+        c->junction_blocks = enable ? 1 : 0;
+        if (!c->p.junction_solve)
+            for (size_t l = 0; l < c->H.size(); l++) {
+                HostLevel &L = c->H[l];
+                if (L.ng() == 0) continue;
+                build_junction(L, c->p.junction_radius, c->junction_blocks ? c->p.junction_sweeps : 0);
+                upload_program(c, L.junction, c->G[l].jz);
+                check_program_fits(c, c->G[l].jz);
+            }
+        return GCMG_OK;
+    })
+}
+
+int gcmg_junction_mode(const gcmg_ctx *c, int l) {
+    if (!valid_level(c, l)) return -1;
+    const LocalDev &z = c->G[l].jz;
+    if (z.ncomp == 0 || !z.in_smem) return 0;
+    return z.blocked ? 2 : 1;
 }
 
 gcmg_status gcmg_span3d_info(const gcmg_ctx *c, int l, int *items, int *columns) {

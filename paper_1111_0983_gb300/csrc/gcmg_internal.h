@@ -63,6 +63,9 @@ struct LocalProgram {
     std::vector<int32_t> pre_off{0}, pre_red_cnt, pre_me, pre_nb, pre_glob;
     std::vector<int32_t> zred, zblack, zghost;   // union over components (global fallback)
     std::vector<int32_t> zred_src;   // 3D: red_sources of zred
+    // components are overlapping blocks (3D junction zone): each writes back
+    // through a separate grid, copied into u after the launch
+    bool blocked = false;
     int max_nodes = 0, max_int = 0, max_gh = 0, max_pre = 0;
     int ncomp() const { return (int)wb_cnt.size(); }
 };
@@ -181,7 +184,7 @@ void number_coarse_unknowns(HostLevel &L);
 // Dense inverse of the coarsest system with the level's current bc (throws GeomError).
 void build_coarse_inverse(HostLevel &L);
 // Junction zone of the level's current bc (radius in h).
-void build_junction(HostLevel &L, double radius);
+void build_junction(HostLevel &L, double radius, int mu = 0);
 // The zone's unknowns as a mask (1 / 0, nn bytes).
 std::vector<uint8_t> junction_zone_mask(const HostLevel &L, double radius);
 // 2D sweep strips of `rows` x STRIP_W owned nodes holding inside nodes or
@@ -211,6 +214,7 @@ struct LocalDev {
     int nzred = 0, nzblack = 0, nzghost = 0;
     int32_t *zred = nullptr, *zblack = nullptr, *zghost = nullptr;
     int32_t *zred_src = nullptr;   // 3D: LocalProgram::zred_src
+    bool blocked = false;          // LocalProgram::blocked
     int nwb = 0;
     int32_t *wb_list = nullptr;   // every component's write-back nodes, one flat list
     bool in_smem = true;       // false: relaxed by per-sweep launches over the union lists

@@ -635,7 +635,15 @@ std::vector<uint8_t> junction_zone_mask(const HostLevel &L, double radius) {
     return junction_marks(L, radius, ghost_of);
 }
 
-void build_junction(HostLevel &L, double radius) {
+// 3D, mu > 0 and a component of more than kJunctionBlockMin nodes: the zone
+// is split instead into blocks of kJunctionBlock^3 nodes, each a component
+// that updates every zone node within Chebyshev distance 4 mu of its block
+// (the reach of mu sweeps: red 1, black 1, the ghosts' stencils 2) and writes
+// back only the block's own zone nodes, so the result equals the global
+// sweeps; the blocks overlap, so they write back through a separate grid.
+constexpr int kJunctionBlock = 8, kJunctionBlockMin = 1500;
+
+void build_junction(HostLevel &L, double radius, int mu) {
     LocalProgram prog;
     ProgramBuilder PB(L, prog);
     const std::vector<uint8_t> zone = junction_marks(L, radius, PB.ghost_of);
@@ -667,7 +675,36 @@ void build_junction(HostLevel &L, double radius) {
         if (comp_of_root[r] < 0) { comp_of_root[r] = (int32_t)comps.size(); comps.emplace_back(); }
         comps[comp_of_root[r]].push_back(zn[i]);
     }
-    for (const auto &cz : comps) PB.add(cz, cz);
+    size_t largest = 0;
+    for (const auto &cz : comps) largest = std::max(largest, cz.size());
+    if (L.dim == 3 && mu > 0 && largest > (size_t)kJunctionBlockMin) {
+        const int n = L.n, B = kJunctionBlock, H = 4 * mu, nb = (n + B - 1) / B;
+        std::vector<int> ci(zn.size()), cj(zn.size()), ck(zn.size());
+        std::vector<std::vector<int64_t>> own((size_t)nb * nb * nb);
+        std::vector<size_t> tiles;
+        for (size_t z = 0; z < zn.size(); z++) {
+            ci[z] = (int)(zn[z] / L.stride[0]);
+            cj[z] = (int)((zn[z] / L.stride[1]) % n);
+            ck[z] = (int)(zn[z] % n);
+            const size_t t = ((size_t)(ci[z] / B) * nb + cj[z] / B) * nb + ck[z] / B;
+            if (own[t].empty()) tiles.push_back(t);
+            own[t].push_back(zn[z]);
+        }
+        std::sort(tiles.begin(), tiles.end());
+        std::vector<int64_t> upd;
+        for (size_t t : tiles) {
+            const int t0 = (int)(t / ((size_t)nb * nb)) * B, t1 = (int)((t / nb) % nb) * B, t2 = (int)(t % nb) * B;
+            upd.clear();
+            for (size_t z = 0; z < zn.size(); z++)
+                if (ci[z] >= t0 - H && ci[z] < t0 + B + H && cj[z] >= t1 - H && cj[z] < t1 + B + H &&
+                    ck[z] >= t2 - H && ck[z] < t2 + B + H)
+                    upd.push_back(zn[z]);
+            PB.add(upd, own[t]);
+        }
+        prog.blocked = true;
+    } else {
+        for (const auto &cz : comps) PB.add(cz, cz);
+    }
     PB.finish(zn);
     if (L.dim == 3) prog.zred_src = red_sources(L, prog.zred);
     L.junction = std::move(prog);

@@ -71,6 +71,8 @@ def lib():
             "gcmg_debug_barrier": (st, [vp, i32, i32, C.c_uint]),
             "gcmg_set_sweep3d": (st, [vp, i32]),
             "gcmg_set_span3d": (st, [vp, i32, i32]),
+            "gcmg_set_junction_blocks": (st, [vp, i32]),
+            "gcmg_junction_mode": (i32, [vp, i32]),
             "gcmg_span3d_info": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
             "gcmg_set_boundary3d": (st, [vp, i32]),
             "gcmg_residual": (st, [vp, vp, vp, C.POINTER(dbl)]),
@@ -268,6 +270,16 @@ class Solver:
         """Rebuild the row-span sweep's items: columns a lane (2..5, 0 auto),
         planes an item (1..32, 0 = 32)."""
         self._check(lib().gcmg_set_span3d(self._h, int(columns), int(planes)))
+
+    def set_junction_blocks(self, enable=True):
+        """3D junction zone in overlapping shared-memory blocks (default) or
+        as whole components."""
+        self._check(lib().gcmg_set_junction_blocks(self._h, int(bool(enable))))
+
+    def junction_mode(self, l):
+        """Level l's junction sweeps: 0 global lists, 1 whole components in
+        shared memory, 2 blocks in shared memory."""
+        return int(lib().gcmg_junction_mode(self._h, int(l)))
 
     def span3d_info(self, l):
         """(items, columns) of the row-span sweep on level l."""

@@ -109,3 +109,22 @@ def test_sweep_kernels_agree_bitwise(precision, n):
         assert st2["converged"], (kind, arg)
         assert torch.equal(u1, u2), (kind, arg)
         np.testing.assert_array_equal(st1["rel"], st2["rel"])
+
+
+@pytest.mark.parametrize("precision,n", [(0, 129), (1, 257)])
+def test_junction_blocks_equal_global_junction_sweeps(precision, n):
+    """The junction zone relaxed in overlapping shared-memory blocks (each
+    updating the zone within 4 mu nodes of its block, writing back its own
+    nodes) gives bitwise the solve of the global junction sweeps."""
+    S = _solver(precision, n)
+    modes = [S.junction_mode(l) for l in range(S.nlev)]
+    assert 2 in modes, modes
+    u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
+    st1 = S.solve(u1)
+    S.set_junction_blocks(False)
+    assert 2 not in [S.junction_mode(l) for l in range(S.nlev)]
+    u2 = torch.zeros_like(u1)
+    st2 = S.solve(u2)
+    assert st1["converged"] and st2["converged"]
+    assert torch.equal(u1, u2)
+    np.testing.assert_array_equal(st1["rel"], st2["rel"])
