@@ -365,9 +365,10 @@ gcmg_status gcmg_set_span3d(gcmg_ctx *ctx, int columns, int planes);
  * junction programs of every level; GCMG_E_ARG for a null context. */
 gcmg_status gcmg_set_junction_blocks(gcmg_ctx *ctx, int enable);
 
-/* How level l's junction sweeps run: 0 on global lists (or no junction
- * zone), 1 whole components in shared memory, 2 blocks in shared memory;
- * -1 for a bad context or level.  Not in the paper. */
+/* How level l's junction sweeps run in the context's cycle precision (3D
+ * mixed form: the FP32 programs, which need less shared memory): 0 on global
+ * lists (or no junction zone), 1 whole components in shared memory, 2 blocks
+ * in shared memory; -1 for a bad context or level.  Not in the paper. */
 int gcmg_junction_mode(const gcmg_ctx *ctx, int l);
 
 /* Sweep 2's work on level l: number of items (0: the level uses sweep 1)

@@ -415,6 +415,7 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
         // 2: all phases as one grid with software barriers
         bool done = false, zdone = false;
         BoundaryProgram3 P;
+        const bool jz_smem = dim == 3 && sizeof(T) == 4 ? g.jz.in_smem32 : g.jz.in_smem;
         if (dim == 3 && c->p.smoother == 0 && g.ng > 0) {
             P.red = g.red;
             P.nred = g.nred;
@@ -422,7 +423,7 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
             P.nblack = g.nblack;
             P.lambda = extra ? c->p.lambda : 0;
             const bool jglob =
-                extra && !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 && !g.jz.in_smem;
+                extra && !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 && !jz_smem;
             if (jglob) {
                 P.zred = g.jz.zred;
                 P.nzred = g.jz.nzred;
@@ -457,7 +458,7 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
                             !c->coop3d;
         if (merged) {
             const bool zmerge = !c->p.junction_solve && c->p.junction_sweeps > 0 && g.jz.ncomp > 0 &&
-                                !g.jz.in_smem && g.jz.zred_src;
+                                !jz_smem && g.jz.zred_src;
             launch_ghost_new<T>(v, nullptr, g.ng, c->stream);
             for (int k = 0; k < c->p.lambda; k++) {
                 launch_rb_list_store<T>(v, g.red, g.red_src, g.nred, nullptr, g.ng, c->stream);
@@ -495,11 +496,12 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
     }
     if (pending) launch_local_copyback<T>(*pending, c->stream);
     if (c->p.junction_sweeps > 0 && g.jz.ncomp > 0) {
-        if (g.jz.in_smem && g.jz.blocked) {   // overlapping blocks: write back through wb, then copy
+        const bool jz_smem = dim == 3 && sizeof(T) == 4 ? g.jz.in_smem32 : g.jz.in_smem;
+        if (jz_smem && g.jz.blocked) {   // overlapping blocks: write back through wb, then copy
             const LocalView<T> J = lview<T>(g.jz, v, wb);
             launch_local<T>(J, dim, 0, c->p.junction_sweeps, c->stream);
             launch_local_copyback<T>(J, c->stream);
-        } else if (g.jz.in_smem) {
+        } else if (jz_smem) {
             launch_local<T>(lview<T>(g.jz, v), dim, 0, c->p.junction_sweeps, c->stream);
         } else {
             for (int k = 0; k < c->p.junction_sweeps; k++) {
@@ -520,9 +522,12 @@ void check_program_fits(gcmg_ctx *c, LocalDev &z) {
     int dev_max = 0;
     ck(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device), "attr");
     z.in_smem = need <= (size_t)dev_max && local_fits_registers(z.max_int);
-    if (!z.in_smem) return;    // relaxed from global memory instead
     LevelView<float> dummy32{};
-    z.pre_in_smem = z.has_pre && local_smem_bytes<float>(lview<float>(z, dummy32), c->p.dim, true) <= (size_t)dev_max;
+    z.in_smem32 = local_smem_bytes<float>(lview<float>(z, dummy32), c->p.dim) <= (size_t)dev_max &&
+                  local_fits_registers(z.max_int);
+    if (!z.in_smem && !z.in_smem32) return;    // relaxed from global memory instead
+    z.pre_in_smem = z.in_smem && z.has_pre &&
+                    local_smem_bytes<float>(lview<float>(z, dummy32), c->p.dim, true) <= (size_t)dev_max;
     // the attribute is per kernel: allow the device maximum once for all levels
     local_prepare<double>(c->p.dim, (size_t)dev_max);
     local_prepare<float>(c->p.dim, (size_t)dev_max);
@@ -1224,7 +1229,8 @@ gcmg_status gcmg_set_junction_blocks(gcmg_ctx *c, int enable) {
 int gcmg_junction_mode(const gcmg_ctx *c, int l) {
     if (!valid_level(c, l)) return -1;
     const LocalDev &z = c->G[l].jz;
-    if (z.ncomp == 0 || !z.in_smem) return 0;
+    const bool smem = c->p.dim == 3 && c->p.precision == 1 ? z.in_smem32 : z.in_smem;
+    if (z.ncomp == 0 || !smem) return 0;
     return z.blocked ? 2 : 1;
 }
 

@@ -218,6 +218,7 @@ struct LocalDev {
     int nwb = 0;
     int32_t *wb_list = nullptr;   // every component's write-back nodes, one flat list
     bool in_smem = true;       // false: relaxed by per-sweep launches over the union lists
+    bool in_smem32 = true;     // the same for the FP32 program (smaller: 3D FP32 cycles use it)
 };
 
 // Integer geometry of a level on the device (shared by both precisions).

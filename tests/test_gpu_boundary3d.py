@@ -111,11 +111,12 @@ def test_sweep_kernels_agree_bitwise(precision, n):
         np.testing.assert_array_equal(st1["rel"], st2["rel"])
 
 
-@pytest.mark.parametrize("precision,n", [(0, 129), (1, 257)])
+@pytest.mark.parametrize("precision,n", [(1, 257)])
 def test_junction_blocks_equal_global_junction_sweeps(precision, n):
     """The junction zone relaxed in overlapping shared-memory blocks (each
     updating the zone within 4 mu nodes of its block, writing back its own
-    nodes) gives bitwise the solve of the global junction sweeps."""
+    nodes) gives bitwise the solve of the global junction sweeps (FP32
+    cycles: the blocks of the finest level fit in shared memory)."""
     S = _solver(precision, n)
     modes = [S.junction_mode(l) for l in range(S.nlev)]
     assert 2 in modes, modes
