@@ -461,9 +461,23 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
 #pragma unroll
     for (int e = 0; e < EPT; e++) {
         const int ir = tid + e * nt, ib = nred + tid + e * nt;
-        if (ir < nred) rf[e] = J.h2 * sf[ir];
-        if (ib < ni) bf[e] = J.h2 * sf[ib];
+        if (ir < nred) rf[e] = D == 3 ? mul_rn(J.h2, sf[ir]) : J.h2 * sf[ir];
+        if (ib < ni) bf[e] = D == 3 ? mul_rn(J.h2, sf[ib]) : J.h2 * sf[ib];
     }
+    // 3D: the sum of the global list sweeps (neighbour_sum: axis 2, axis 0,
+    // then axis 1; the slots are ordered axis 0, 1, 2), so that a program
+    // gives bitwise the values of the launches over the union lists
+    auto inside_sum = [&](T h2f, const int *nb) -> T {
+        if (D == 3) {
+            T s = val[nb[4]] + val[nb[5]] + val[nb[0]] + val[nb[1]];
+            s += val[nb[2]] + val[nb[3]];
+            return h2f + s;
+        }
+        T s = h2f;
+#pragma unroll
+        for (int a = 0; a < 2 * D; a++) s += val[nb[a]];
+        return s;
+    };
     const T inv = (T)(1.0 / (2 * D));
     if (pre) {
         const int npr = J.pre_red_cnt[c];
@@ -493,21 +507,11 @@ __device__ __forceinline__ void local_body(const LocalView<T> &J, const T *src, 
     for (int it = 0; it < reps; it++) {
 #pragma unroll
         for (int e = 0; e < EPT; e++)
-            if (rme[e] >= 0) {
-                T s = rf[e];
-#pragma unroll
-                for (int a = 0; a < 2 * D; a++) s += val[rnb[e][a]];
-                val[rme[e]] = s * inv;
-            }
+            if (rme[e] >= 0) val[rme[e]] = inside_sum(rf[e], rnb[e]) * inv;
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < EPT; e++)
-            if (bme[e] >= 0) {
-                T s = bf[e];
-#pragma unroll
-                for (int a = 0; a < 2 * D; a++) s += val[bnb[e][a]];
-                val[bme[e]] = s * inv;
-            }
+            if (bme[e] >= 0) val[bme[e]] = inside_sum(bf[e], bnb[e]) * inv;
         __syncthreads();
         ghost_sweep();
     }
