@@ -357,11 +357,12 @@ gcmg_status gcmg_set_sweep3d(gcmg_ctx *ctx, int variant);
 gcmg_status gcmg_set_span3d(gcmg_ctx *ctx, int columns, int planes);
 
 /* 3D junction zone (the mu junction sweeps; not in the paper): enable = 1
- * (default) splits a zone component of more than 1,500 nodes into blocks of
- * 8^3 nodes relaxed in shared memory, each updating the zone within 4 mu
- * nodes of its block and writing back only its own nodes (two launches a
- * relaxation instead of three a sweep; the same results bitwise); 0 keeps
- * whole components (a large one then runs on global lists).  Rebuilds the
+ * splits a zone component of more than 1,500 nodes into blocks of 8^3 nodes
+ * relaxed in shared memory, each updating the zone within 4 mu nodes of its
+ * block and writing back only its own nodes (two launches a relaxation
+ * instead of three a sweep; the same results bitwise); 0 (default) keeps
+ * whole components (a large one then runs on global lists; measured faster
+ * on GB300: the blocks redo about ten times the zone's work).  Rebuilds the
  * junction programs of every level; GCMG_E_ARG for a null context. */
 gcmg_status gcmg_set_junction_blocks(gcmg_ctx *ctx, int enable);
 

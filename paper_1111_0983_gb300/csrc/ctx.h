@@ -54,7 +54,8 @@ struct gcmg_ctx {
     unsigned *d_bar = nullptr;
     int *d_err = nullptr;
     int coop3d = 0, bar_phantom = 0;
-    int junction_blocks = 1;   // 3D junction zone in overlapping shared-memory blocks (gcmg_set_junction_blocks)
+    int junction_blocks = 0;   // 3D junction zone in overlapping shared-memory blocks (gcmg_set_junction_blocks;
+                               // measured slower at 513^3: 3.28 against 3.11 ms a cycle)
     int sweep3d = 3;   // 3D interior sweep: 0 k_rb_zmarch (shared-memory planes), 1 k_rb_stream3d (registers),
                        // 2 k_rb_span3d (row spans; FP32, else 1), 3 k_rb_rows (two in-place colour launches)
     int cluster3d = 0; // 1: 3D boundary phases of small levels (and junction sweeps) as one thread-block

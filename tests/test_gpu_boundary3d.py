@@ -118,6 +118,7 @@ def test_junction_blocks_equal_global_junction_sweeps(precision, n):
     nodes) gives bitwise the solve of the global junction sweeps (FP32
     cycles: the blocks of the finest level fit in shared memory)."""
     S = _solver(precision, n)
+    S.set_junction_blocks(True)
     modes = [S.junction_mode(l) for l in range(S.nlev)]
     assert 2 in modes, modes
     u1 = torch.zeros((n,) * 3, dtype=torch.float64, device="cuda")
