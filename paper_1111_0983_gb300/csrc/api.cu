@@ -152,6 +152,10 @@ void upload_geometry(gcmg_ctx *c, int l) {
     std::vector<int32_t> stn = slot_major<int32_t, int32_t>(L.stn, g.ng, KMAX, kslots(L.dim));
     g.gstn = upload<int32_t>(c, stn.data(), stn.size());
     g.red = upload<int32_t>(c, L.band_red.data(), L.band_red.size());
+    if (!L.gcode.empty()) {
+        g.gcode = upload<uint8_t>(c, L.gcode.data(), L.gcode.size());
+        g.gbase = upload<int32_t>(c, L.gbase.data(), L.gbase.size());
+    }
     if (!L.band_red_src.empty()) g.red_src = upload<int32_t>(c, L.band_red_src.data(), L.band_red_src.size());
     g.ntiles = (int)L.tiles.size();
     g.tiles = upload<int32_t>(c, L.tiles.data(), L.tiles.size());

@@ -122,6 +122,8 @@ LevelView<T> view(const gcmg_ctx *c, int l, const DevData<T> &D) {
     v.nchunks = g.nchunks;
     v.segs = reinterpret_cast<const int2 *>(g.sp_list);
     v.nsegs = g.nspl;
+    v.gcode = g.gcode;
+    v.gbase = g.gbase;
     return v;
 }
 

@@ -87,6 +87,12 @@ struct HostLevel {
     std::vector<int32_t> stn;           // ng * KMAX, per ghost
     std::vector<double> wD, wN;         // ng * KMAX
     std::vector<uint8_t> bc;            // 0 Dirichlet, 1 Neumann
+    // 3D: the stencil of ghost q as a box when it is one (tensor-product
+    // stencils): code m | 4 (axis 0 descending) | 8 (axis 1) | 16 (axis 2), m
+    // = 3 (27 slots) or 2 (8 slots, the other 19 are the ghost itself), and
+    // the node of slot 0; code 0: use the 27 stored nodes
+    std::vector<uint8_t> gcode;
+    std::vector<int32_t> gbase;
     // inside nodes of the extra-sweep band, split by colour
     std::vector<int32_t> band_red, band_black;
     std::vector<int32_t> band_red_src;   // 3D: red_sources of band_red
@@ -229,6 +235,8 @@ struct DevGeom {
     uint8_t *type = nullptr;
     int32_t *gnode = nullptr;    // ng
     int32_t *gstn = nullptr;     // KMAX * ng, slot major
+    uint8_t *gcode = nullptr;    // HostLevel::gcode, gbase (3D)
+    int32_t *gbase = nullptr;
     int32_t *red = nullptr, *black = nullptr;
     int32_t *red_src = nullptr;  // 3D: HostLevel::band_red_src
     int ntiles = 0;
@@ -315,6 +323,9 @@ struct LevelView {
     // 3D: segments of up to 64 consecutive inside nodes of a row (DevGeom::sp_list)
     const int2 *segs = nullptr;
     int nsegs = 0;
+    // 3D: ghost stencils as boxes (DevGeom::gcode, gbase; null: gstn only)
+    const uint8_t *gcode = nullptr;
+    const int32_t *gbase = nullptr;
 };
 
 // One 3D boundary relaxation as a single launch (k_boundary3d): the Jacobi

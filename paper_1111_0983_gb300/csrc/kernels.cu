@@ -995,13 +995,28 @@ __device__ __forceinline__ void ghost_new_early(const LevelView<T> &v, int q, bo
     int32_t st[K], gn = 0;
     T w[K], gc = 0;
     if (on) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            st[k] = v.gstn[(int64_t)k * v.ng + q];
-            w[k] = v.gw[(int64_t)k * v.ng + q];
-        }
         gc = v.gc[q];
         gn = v.gnode[q];
+        const unsigned code = K == 27 && v.gcode ? v.gcode[q] : 0u;
+        if (code) {
+            // a box stencil: the nodes from slot 0 and the axis directions;
+            // an 8-slot box pads with the ghost itself and zero weights
+            const int m = (int)(code & 3u);
+            const int64_t b0 = v.gbase[q], D0 = (code & 4u) ? -v.s0 : v.s0, D1 = (code & 8u) ? -v.s1 : v.s1;
+            const int64_t D2 = (code & 16u) ? -1 : 1;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if (m == 3) st[k] = (int32_t)(b0 + (k / 9) * D0 + ((k / 3) % 3) * D1 + (k % 3) * D2);
+                else st[k] = k < 8 ? (int32_t)(b0 + (k / 4) * D0 + ((k / 2) % 2) * D1 + (k % 2) * D2) : gn;
+                w[k] = (m == 2 && k >= 8) ? (T)0 : v.gw[(int64_t)k * v.ng + q];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                st[k] = v.gstn[(int64_t)k * v.ng + q];
+                w[k] = v.gw[(int64_t)k * v.ng + q];
+            }
+        }
     }
     pdl_wait();
     if (!on) return;

@@ -1197,7 +1197,33 @@ void build_hierarchy(int dim, int n, int n_coarse, const double *phi, double del
         L.bc.assign(ng, 0);
         for (int64_t q = 0; q < ng; q++) ghost_equation(L, q);
         mark_band(L, delta_over_h * L.h);
-        if (dim == 3) L.band_red_src = red_sources(L, L.band_red);
+        if (dim == 3) {
+            L.band_red_src = red_sources(L, L.band_red);
+            // ghost stencils that are boxes: slot s = (k0 m + k1) m + k2 at
+            // node 0 + k0 D0 + k1 D1 + k2 D2, D_a = +-stride_a (checked slot
+            // by slot; the 8-slot boxes pad with the ghost itself)
+            L.gcode.assign(ng, 0);
+            L.gbase.assign(ng, 0);
+            for (int64_t q = 0; q < ng; q++) {
+                const int32_t *st = &L.stn[q * KMAX];
+                for (int m = 3; m >= 2; m--) {
+                    const int64_t D2 = (int64_t)st[1] - st[0], D1 = (int64_t)st[m] - st[0],
+                                  D0 = (int64_t)st[m * m] - st[0];
+                    if (std::llabs(D2) != 1 || std::llabs(D1) != L.stride[1] || std::llabs(D0) != L.stride[0])
+                        continue;
+                    bool ok = true;
+                    for (int sl = 0; sl < KMAX && ok; sl++) {
+                        int64_t want = L.ghost_node[q];
+                        if (sl < m * m * m) want = st[0] + (sl / (m * m)) * D0 + ((sl / m) % m) * D1 + (sl % m) * D2;
+                        if (st[sl] != want) ok = false;
+                    }
+                    if (!ok) continue;
+                    L.gcode[q] = (uint8_t)(m | (D0 < 0 ? 4 : 0) | (D1 < 0 ? 8 : 0) | (D2 < 0 ? 16 : 0));
+                    L.gbase[q] = st[0];
+                    break;
+                }
+            }
+        }
         if (dim == 2) {
             const int tr = (L.n + TILE_R - 1) / TILE_R, tc = (L.n + TILE_C - 1) / TILE_C;
             std::vector<uint8_t> active((size_t)tr * tc, 0);
