@@ -350,7 +350,17 @@ T *relax(gcmg_ctx *c, LevelView<T> v, T *out, T *wb, int l, bool extra) {
                                      : 0.0;
             timer_mark(c, GCMG_KERNEL_SMOOTH, l, bytes);
             timer_mark(c, GCMG_KERNEL_BOUNDARY, l, bytes);
-            launch_relax2d(v, out, g, lview<T>(g.bz, v), c->p.lambda, c->stream);
+            if (c->split2d_strips > 0 && g.nstrips >= c->split2d_strips) {
+                if (!c->sstream) {
+                    ck(cudaStreamCreateWithFlags(&c->sstream, cudaStreamNonBlocking), "cudaStreamCreate");
+                    ck(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+                    ck(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+                }
+                launch_relax2d_split(v, out, g, lview<T>(g.bz, v), c->p.lambda, c->stream, c->sstream, c->ev_fork,
+                                     c->ev_join);
+            } else {
+                launch_relax2d(v, out, g, lview<T>(g.bz, v), c->p.lambda, c->stream);
+            }
             timer_mark(c, GCMG_KERNEL_BOUNDARY, l);
             timer_mark(c, GCMG_KERNEL_SMOOTH, l);
             v.u = out;
@@ -1080,6 +1090,9 @@ void gcmg_destroy(gcmg_ctx *c) {
     cudaStreamSynchronize(c->stream);
     destroy_graph(c);
     if (c->gstream) { cudaStreamSynchronize(c->gstream); cudaStreamDestroy(c->gstream); }
+    if (c->sstream) { cudaStreamSynchronize(c->sstream); cudaStreamDestroy(c->sstream); }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -1228,6 +1241,13 @@ gcmg_status gcmg_set_junction_blocks(gcmg_ctx *c, int enable) {
             }
         return GCMG_OK;
     })
+}
+
+gcmg_status gcmg_set_split2d(gcmg_ctx *c, int min_strips) {
+    if (!c || min_strips < 0) return fail(c, GCMG_E_ARG, "bad argument");
+    destroy_graph(c);
+    c->split2d_strips = min_strips;
+    return GCMG_OK;
 }
 
 int gcmg_junction_mode(const gcmg_ctx *c, int l) {

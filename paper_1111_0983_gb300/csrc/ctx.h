@@ -43,6 +43,11 @@ struct gcmg_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // large 2D levels: the merged FP32 relaxation as two launches side by
+    // side (strips on the stream, boundary blocks on sstream)
+    cudaStream_t sstream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int split2d_strips = 16384;   // levels with at least this many strips split (0: never)
     double *d_rel = nullptr;                // rel[0..256]
     double *d_r0 = nullptr;
     int *d_m = nullptr;

@@ -1379,12 +1379,45 @@ void launch_relax2d(const LevelView<float> &v, float *out, const DevGeom &g, con
 }
 
 // both colours in one pass over the active 2D strips: 4 warps a CTA, one strip a warp
-template <typename T, int SR>
+// (INTERIOR_ONLY: the boundary blocks, launched beside, store the band and ghosts)
+template <typename T, int SR, bool INTERIOR_ONLY = false>
 __global__ void __launch_bounds__(128) k_rb_strip(LevelView<T> v, T *__restrict__ out,
                                                   const int32_t *__restrict__ strips, int ns) {
     pdl_wait();
     const int s = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (s < ns) rb_strip<T, SR>(v, out, strips[s]);   // uniform over the warp
+    if (s < ns) rb_strip<T, SR, INTERIOR_ONLY>(v, out, strips[s]);   // uniform over the warp
+}
+
+template <int SR>
+static void launch_strips_interior(const LevelView<float> &v, float *out, const DevGeom &g, cudaStream_t s) {
+    pdl_launch(k_rb_strip<float, SR, true>, dim3((unsigned)((g.nstrips + 3) / 4)), dim3(128), 0, s, v, out, g.strips,
+               g.nstrips);
+}
+
+void launch_relax2d_split(const LevelView<float> &v, float *out, const DevGeom &g, const LocalView<float> &J,
+                          int lambda, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+    // the boundary blocks (k_relax2d without strips) on the side stream, the
+    // strips (interior nodes off the band) on the main one: both read v.u and
+    // store disjoint nodes of out, as the merged launch does
+    g_launches += 2;
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(side, fork, 0);
+    const size_t smem = local_smem_bytes(J, 2, true);
+    const dim3 grid((unsigned)J.ncomp);
+    if (J.max_colour <= LOCAL_THREADS) {
+        if (g.strip_rows == 32) launch_relax2d_as<32, 1>(grid, smem, side, v, out, g, 0, J, lambda);
+        else if (g.strip_rows == 16) launch_relax2d_as<16, 1>(grid, smem, side, v, out, g, 0, J, lambda);
+        else launch_relax2d_as<8, 1>(grid, smem, side, v, out, g, 0, J, lambda);
+    } else {
+        if (g.strip_rows == 32) launch_relax2d_as<32, LOCAL_EPT>(grid, smem, side, v, out, g, 0, J, lambda);
+        else if (g.strip_rows == 16) launch_relax2d_as<16, LOCAL_EPT>(grid, smem, side, v, out, g, 0, J, lambda);
+        else launch_relax2d_as<8, LOCAL_EPT>(grid, smem, side, v, out, g, 0, J, lambda);
+    }
+    if (g.strip_rows == 32) launch_strips_interior<32>(v, out, g, s);
+    else if (g.strip_rows == 16) launch_strips_interior<16>(v, out, g, s);
+    else launch_strips_interior<8>(v, out, g, s);
+    cudaEventRecord(join, side);
+    cudaStreamWaitEvent(s, join, 0);
 }
 
 template <typename T>

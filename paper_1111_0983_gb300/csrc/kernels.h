@@ -20,6 +20,10 @@ template <typename T>
 void launch_rb(const LevelView<T> &v, int dim, int color, cudaStream_t s);
 // one FP32 2D relaxation (interior sweep, ghost sweep, band sweeps) in one
 // launch: strips and boundary blocks both read v.u and write out
+// the same as two launches side by side: the boundary blocks on `side`, the
+// strips' interior nodes on `s` (fork and join through the two events)
+void launch_relax2d_split(const LevelView<float> &v, float *out, const DevGeom &g, const LocalView<float> &J,
+                          int lambda, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 void launch_relax2d(const LevelView<float> &v, float *out, const DevGeom &g, const LocalView<float> &J, int lambda,
                     cudaStream_t s);
 // both colours of a 2D sweep over the active strips (one warp a strip, rows

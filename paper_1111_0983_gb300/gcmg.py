@@ -73,6 +73,7 @@ def lib():
             "gcmg_set_span3d": (st, [vp, i32, i32]),
             "gcmg_set_junction_blocks": (st, [vp, i32]),
             "gcmg_junction_mode": (i32, [vp, i32]),
+            "gcmg_set_split2d": (st, [vp, i32]),
             "gcmg_span3d_info": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
             "gcmg_set_boundary3d": (st, [vp, i32]),
             "gcmg_residual": (st, [vp, vp, vp, C.POINTER(dbl)]),
@@ -275,6 +276,11 @@ class Solver:
         """3D junction zone in overlapping shared-memory blocks (default) or
         as whole components."""
         self._check(lib().gcmg_set_junction_blocks(self._h, int(bool(enable))))
+
+    def set_split2d(self, min_strips):
+        """2D FP32 levels with at least min_strips strips relax as two launches
+        side by side (0: always one merged launch)."""
+        self._check(lib().gcmg_set_split2d(self._h, int(min_strips)))
 
     def junction_mode(self, l):
         """Level l's junction sweeps: 0 global lists, 1 whole components in

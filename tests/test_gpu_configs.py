@@ -154,3 +154,17 @@ def test_batch_of_513_and_1025_domains_matches_oracle():
         uo, _, _ = O.solve(rtol=1e-13, max_cycles=40)
         T = O.types(0)
         assert rel_maxdiff(u.cpu().numpy(), uo, T > 0) < PARITY, k
+
+
+def test_flower4097_split_relaxation_is_bitwise_the_merged_one():
+    """The finest 4097^2 level relaxes as two launches side by side (the
+    boundary blocks and the strips' interior nodes); one merged launch
+    computes the same values."""
+    P, n, nc = inputs.flower(), 4097, 33
+    S, u1, st1 = solve_gpu(P, n, nc, precision=1, rtol=1e-9)
+    S.set_split2d(0)
+    u2 = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st2 = S.solve(u2)
+    assert st1["converged"] and st2["converged"]
+    assert np.array_equal(u1, u2.cpu().numpy())
+    np.testing.assert_array_equal(st1["rel"], st2["rel"])
