@@ -47,7 +47,7 @@ struct gcmg_ctx {
     // side (strips on the stream, boundary blocks on sstream)
     cudaStream_t sstream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    int split2d_strips = 16384;   // levels with at least this many strips split (0: never)
+    int split2d_strips = 0;       // levels with at least this many strips split (0: never; measured no faster)
     double *d_rel = nullptr;                // rel[0..256]
     double *d_r0 = nullptr;
     int *d_m = nullptr;

@@ -157,12 +157,12 @@ def test_batch_of_513_and_1025_domains_matches_oracle():
 
 
 def test_flower4097_split_relaxation_is_bitwise_the_merged_one():
-    """The finest 4097^2 level relaxes as two launches side by side (the
-    boundary blocks and the strips' interior nodes); one merged launch
-    computes the same values."""
+    """The finest 4097^2 level relaxed as two launches side by side (the
+    boundary blocks and the strips' interior nodes) computes the values of
+    the one merged launch."""
     P, n, nc = inputs.flower(), 4097, 33
-    S, u1, st1 = solve_gpu(P, n, nc, precision=1, rtol=1e-9)
-    S.set_split2d(0)
+    S, u1, st1 = solve_gpu(P, n, nc, precision=1, rtol=1e-9)   # merged (the default)
+    S.set_split2d(4096)   # the finest level (about 7,000 strips) split
     u2 = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
     st2 = S.solve(u2)
     assert st1["converged"] and st2["converged"]
