@@ -230,6 +230,13 @@ gcmg_status gcmg_set_rhs(gcmg_ctx *ctx, const double *f_dev, const double *g_dev
  * GCMG_E_NOCONV if not converged.  stats may be NULL. */
 gcmg_status gcmg_solve(gcmg_ctx *ctx, double *u_dev, gcmg_stats *stats);
 
+/* Replaces the cycle limit of the next solves (params.max_cycles, 1..256; the
+ * paper runs a fixed number of cycles or stops on the defect, Sec. 3).  The
+ * limit lives in device memory, so a captured solve graph is kept (e.g. one
+ * cycle from a given start, to see the defect it leaves, then the rest of the
+ * solve from its result).  GCMG_E_ARG outside [1, 256]. */
+gcmg_status gcmg_set_max_cycles(gcmg_ctx *ctx, int max_cycles);
+
 /* FP64 defect of a fine-grid function (TGCS step 3, Eq. discr): r_dev
  * (device, n^d doubles) = f + Lap_h u on Omega_h, g - L_h u on Gamma_h (stored
  * at the ghost node), 0 elsewhere, with the f and g of gcmg_set_rhs; u_dev

@@ -658,9 +658,11 @@ bool barrier_timed_out(gcmg_ctx *c) {
 
 // end of one loop iteration: records rel[m] and sets the while condition;
 // r0[1] holds the previous relative residual, m[1] the number of consecutive
-// cycles whose defect grew (the loop stops once it reaches `diverge` > 0)
+// cycles whose defect grew (the loop stops once it reaches `diverge` > 0),
+// m[2] the cycle limit (device-resident, so gcmg_set_max_cycles needs no new graph)
 __global__ void k_loop_check(cudaGraphConditionalHandle h, const unsigned long long *bits, double *r0,
-                             double *rel, int *m, double rtol, int max_cycles, int diverge) {
+                             double *rel, int *m, double rtol, int diverge) {
+    const int max_cycles = m[2];
     const double nr = __longlong_as_double((long long)*bits);
     const int k = m[0] + 1;
     m[0] = k;
@@ -788,7 +790,7 @@ void build_graph(gcmg_ctx *c) {
     const long long before = g_launches.load();
     try {
         loop_body(c);
-        k_loop_check<<<1, 1, 0, c->gstream>>>(h, c->d_norm, c->d_r0, c->d_rel, c->d_m, c->p.rtol, c->p.max_cycles,
+        k_loop_check<<<1, 1, 0, c->gstream>>>(h, c->d_norm, c->d_r0, c->d_rel, c->d_m, c->p.rtol,
                                               c->p.diverge_cycles);
         g_launches++;
         c->graph_kernels = g_launches.load() - before;
@@ -891,9 +893,11 @@ gcmg_status create_from_levels(const gcmg_params &q, std::vector<HostLevel> &&H,
         c->d_norm = dalloc<unsigned long long>(c, 2);
         c->d_rel = dalloc<double>(c, 257);
         c->d_r0 = dalloc<double>(c, 2);   // r0, the last relative residual
-        c->d_m = dalloc<int>(c, 2);       // cycles, consecutive growing cycles
+        c->d_m = dalloc<int>(c, 3);       // cycles, consecutive growing cycles, cycle limit
         c->d_bar = dalloc<unsigned>(c, 2);
         c->d_err = dalloc<int>(c, 1);
+        const int maxc = p->max_cycles;
+        ck(cudaMemcpyAsync(c->d_m + 2, &maxc, sizeof(int), cudaMemcpyHostToDevice, c->stream), "max cycles");
         ck(cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream), "memset");
         ck(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
         ck(cudaMallocHost((void **)&c->h_norm, 2 * sizeof(unsigned long long)), "cudaMallocHost");
@@ -1239,6 +1243,18 @@ gcmg_status gcmg_set_junction_blocks(gcmg_ctx *c, int enable) {
                 upload_program(c, L.junction, c->G[l].jz);
                 check_program_fits(c, c->G[l].jz);
             }
+        return GCMG_OK;
+    })
+}
+
+gcmg_status gcmg_set_max_cycles(gcmg_ctx *c, int max_cycles) {
+    if (!c || max_cycles < 1 || max_cycles > 256) return fail(c, GCMG_E_ARG, "max_cycles outside [1, 256]");
+    GCMG_GUARD(c, {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        c->p.max_cycles = max_cycles;
+        // ordered before the next solve's graph launch, which waits on this stream
+        ck(cudaMemcpyAsync(c->d_m + 2, &max_cycles, sizeof(int), cudaMemcpyHostToDevice, c->stream), "max cycles");
+        ck(cudaStreamSynchronize(c->stream), "sync");
         return GCMG_OK;
     })
 }

@@ -74,6 +74,7 @@ def lib():
             "gcmg_set_junction_blocks": (st, [vp, i32]),
             "gcmg_junction_mode": (i32, [vp, i32]),
             "gcmg_set_split2d": (st, [vp, i32]),
+            "gcmg_set_max_cycles": (st, [vp, i32]),
             "gcmg_span3d_info": (st, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
             "gcmg_set_boundary3d": (st, [vp, i32]),
             "gcmg_residual": (st, [vp, vp, vp, C.POINTER(dbl)]),
@@ -276,6 +277,10 @@ class Solver:
         """3D junction zone in overlapping shared-memory blocks (default) or
         as whole components."""
         self._check(lib().gcmg_set_junction_blocks(self._h, int(bool(enable))))
+
+    def set_max_cycles(self, k):
+        """Cycle limit of the next solves (1..256), without a new solve graph."""
+        self._check(lib().gcmg_set_max_cycles(self._h, int(k)))
 
     def set_split2d(self, min_strips):
         """2D FP32 levels with at least min_strips strips relax as two launches

@@ -243,6 +243,28 @@ def test_graph_solve_start(precision):
     assert not torch.any(u4)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_max_cycles_split_solve(precision):
+    """gcmg_set_max_cycles changes the limit of a captured graph solve: one
+    cycle, then a solve from its result, gives the cycles and the solution of
+    one uninterrupted solve (a solve's state between cycles is u alone)."""
+    P, n, nc = inputs.flower(), 129, 33
+    S = solver_for(P, n, nc, precision=precision, rtol=1e-10, max_cycles=100)
+    set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    S.set_max_cycles(1)
+    u1 = torch.zeros_like(u)
+    st1 = S.solve(u1)
+    assert st1["cycles"] == 1 and not st1["converged"] and st1["rel"][1] == st["rel"][1]
+    S.set_max_cycles(100)
+    st2 = S.solve(u1)
+    assert st2["converged"] and st1["cycles"] + st2["cycles"] == st["cycles"]
+    assert rel_maxdiff(host(u1), host(u), np.ones(u.shape, bool)) < 1e-14
+    with pytest.raises(_gcmg().GcmgError):
+        S.set_max_cycles(0)
+
+
 def test_solve_host_equals_device():
     P, n, nc = inputs.flower(), 257, 33
     S = solver_for(P, n, nc)
