@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include "exact_lap.h"
 #include "gcmg_internal.h"
 
 namespace gcmg {
@@ -531,14 +532,38 @@ __device__ __forceinline__ void local_copyback(const LocalView<T> &J, T *u, int 
 // ------------------------------------------------------------------ defect
 // r = f + Lap_h u at inside node p (TGCS step 3), as a sum of differences so
 // that the O(u / h^2) terms do not cancel; with zero_rest, 0 at outside nodes.
+// The numerator sum_k u_k - 2d u_p of the 5/7-point Laplacian at inside node
+// p (neighbours in the order x-1, x+1, then the two slower axes).  FP32: the
+// sum of differences.  FP64: the exact integer sum of exact_lap.h rounded
+// once (no FP64-pipe work but the conversion), the sum of differences only
+// for non-finite or tiny values.
+template <typename T, int D>
+__device__ __forceinline__ T lap_numerator(const LevelView<T> &v, int64_t p, T up) {
+    T nb[2 * D];
+    nb[0] = v.u[p - 1];
+    nb[1] = v.u[p + 1];
+    nb[2] = v.u[p - v.s0];
+    nb[3] = v.u[p + v.s0];
+    if (D == 3) {
+        nb[2 * D - 2] = v.u[p - v.s1];
+        nb[2 * D - 1] = v.u[p + v.s1];
+    }
+    if constexpr (sizeof(T) == 8) {
+        double s;
+        if (exl::lap_sum_exact<2 * D>(up, nb, &s)) return s;
+    }
+    T lap = (nb[0] - up) + (nb[1] - up) + (nb[2] - up) + (nb[3] - up);
+    if (D == 3) lap += (nb[2 * D - 2] - up) + (nb[2 * D - 1] - up);
+    return lap;
+}
+
 // Returns the defect (0 off Omega_h) for the norm.
 template <typename T, int D>
 __device__ __forceinline__ double defect_node(const LevelView<T> &v, int64_t p, bool zero_rest) {
     const uint8_t k = v.type[p] & NODE_KIND;
     if (k == NODE_IN) {
         const T up = v.u[p];
-        T lap = (v.u[p - 1] - up) + (v.u[p + 1] - up) + (v.u[p - v.s0] - up) + (v.u[p + v.s0] - up);
-        if (D == 3) lap += (v.u[p - v.s1] - up) + (v.u[p + v.s1] - up);
+        const T lap = lap_numerator<T, D>(v, p, up);
         const T r = v.f[p] + lap * v.inv_h2;
         v.r[p] = r;
         return (double)r;
@@ -733,9 +758,7 @@ __device__ T partial_transfer(const LevelView<T> &F, int64_t p, bool interior) {
 template <typename T, int D>
 __device__ __forceinline__ T inside_defect(const LevelView<T> &v, int64_t p) {
     const T up = v.u[p];
-    T lap = (v.u[p - 1] - up) + (v.u[p + 1] - up) + (v.u[p - v.s0] - up) + (v.u[p + v.s0] - up);
-    if (D == 3) lap += (v.u[p - v.s1] - up) + (v.u[p + v.s1] - up);
-    return v.f[p] + lap * v.inv_h2;
+    return v.f[p] + lap_numerator<T, D>(v, p, up) * v.inv_h2;
 }
 
 // the defect g - L_G u at ghost q (the expression of defect_ghost_item)
