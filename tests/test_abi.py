@@ -96,3 +96,8 @@ def test_create_grid_rejects_bad_grids_without_gpu(lib):
     assert not h.value
     assert lib.gcmg_set_bc_types_from_mask(None, None) == gcmg.GCMG_E_ARG
     assert lib.gcmg_residual(None, None, None, None) == gcmg.GCMG_E_ARG
+
+
+def test_set_max_cycles_rejects_bad_arguments_without_gpu(lib):
+    from paper_1111_0983_gb300 import gcmg
+    assert lib.gcmg_set_max_cycles(None, 5) == gcmg.GCMG_E_ARG
