@@ -801,8 +801,12 @@ def run_gcmg(args):
                            "parallelism": f"replicas x{world}", "setup_s": setup_s},
                 "rho": [float(x) for x in (rel_hist[1:] / rel_hist[:-1])],
                 "roofline": roofline, "sweep_roofline": sweep, "clocks": clk, "gpu_launches": launches,
-                "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": int(f_h.nbytes + g_h.nbytes),
-                        "d2h_bytes_per_step": int(u_pin.nbytes)},
+                "e2e": {"value": e2e_value, "unit": "unknowns/s",
+                        # f is page-locked: the device reads it at the inside nodes only
+                        "h2d_bytes_per_step": int(8 * n_in + g_h.nbytes),
+                        "d2h_bytes_per_step": int(u_pin.nbytes),
+                        "note": "gcmg_solve_host with page-locked buffers: the device reads f at the "
+                                "inside nodes from host memory, g is copied, u (n^d) is copied back"},
                 "wall_s": wall}
         S.close()
         del S

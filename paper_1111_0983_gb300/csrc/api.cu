@@ -1513,13 +1513,47 @@ gcmg_status gcmg_solve(gcmg_ctx *c, double *u_dev, gcmg_stats *stats) {
     })
 }
 
+// f at the inside nodes of the finest level, read by the device straight from
+// a host buffer it can address (page-locked memory): the solver reads f only
+// on Omega_h, so the other n^d - |Omega_h| values need not cross the link.
+// Nodes visited as in k_rhs_norm (the active chunks in 3D, else every node).
+__global__ void k_gather_inside(LevelView<double> lv, const double *__restrict__ src, double *__restrict__ dst) {
+    const uint8_t *type = lv.type;
+    const int64_t nt = lv.chunks ? lv.nchunks * CHUNK : lv.nn;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = i;
+        if (lv.chunks) {
+            if ((int)(i % CHUNK) >= (lv.clen[i / CHUNK] & 63)) continue;
+            p = (int64_t)lv.chunks[i / CHUNK] + i % CHUNK;
+        }
+        if ((type[p] & NODE_KIND) == NODE_IN) dst[p] = src[p];
+    }
+}
+
 gcmg_status gcmg_solve_host(gcmg_ctx *c, const double *f_host, const double *g_host, double *u_host,
                             gcmg_stats *stats) {
     if (!c || !f_host || !u_host) return fail(c, GCMG_E_ARG, "null pointer");
     GCMG_GUARD(c, {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         const HostLevel &L = c->H[0];
-        ck(cudaMemcpyAsync(c->D64[0].f, f_host, L.nn * sizeof(double), cudaMemcpyHostToDevice, c->stream), "f");
+        // page-locked f: the device reads the inside nodes' values itself;
+        // any other host memory: one copy of all n^d values
+        cudaPointerAttributes pa;
+        std::memset(&pa, 0, sizeof(pa));
+        const bool mapped = cudaPointerGetAttributes(&pa, f_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                            pa.devicePointer != nullptr;
+        cudaGetLastError();   // an unregistered pointer may leave an error behind
+        if (mapped) {
+            const LevelView<double> lv = view<double>(c, 0, c->D64[0]);
+            const int64_t cnt = lv.chunks ? lv.nchunks * CHUNK : L.nn;
+            const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 8192);
+            k_gather_inside<<<nb, 256, 0, c->stream>>>(lv, static_cast<const double *>(pa.devicePointer),
+                                                       c->D64[0].f);
+            g_launches++;
+            check_launch();
+        } else {
+            ck(cudaMemcpyAsync(c->D64[0].f, f_host, L.nn * sizeof(double), cudaMemcpyHostToDevice, c->stream), "f");
+        }
         if (L.ng() > 0)
             ck(cudaMemcpyAsync(c->D64[0].gg, g_host, L.ng() * sizeof(double), cudaMemcpyHostToDevice, c->stream),
                "g");

@@ -276,6 +276,31 @@ def test_solve_host_equals_device():
     assert sth["cycles"] == st["cycles"]
 
 
+@pytest.mark.parametrize("P,n,nc", [(inputs.flower(), 257, 33), (inputs.torus(), 65, 17)])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_uses_f_on_the_inside_nodes_only(P, n, nc, pinned):
+    """gcmg_solve_host with f NaN off Omega_h and stale device values from an
+    earlier right-hand side: page-locked f is read by the device at the
+    inside nodes only, other host memory is copied whole; either way the
+    solution is bitwise the device solve's."""
+    S = solver_for(P, n, nc)
+    f, g = set_problem_rhs(S, P, n)
+    u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
+    st = S.solve(u)
+    T = S.node_types(0) & 3
+    f_nan = np.where(T == 1, f, np.nan)
+    S.set_rhs(dev(np.full_like(f, 7.0)), dev(g))
+    if pinned:
+        fh = torch.from_numpy(f_nan).pin_memory().numpy()
+        gh = torch.from_numpy(np.ascontiguousarray(g)).pin_memory().numpy()
+        uh = torch.empty(S.shape(0), dtype=torch.float64).pin_memory().numpy()
+    else:
+        fh, gh, uh = f_nan, np.ascontiguousarray(g), np.empty(S.shape(0))
+    out, sth = S.solve_host(fh, gh, uh)
+    assert sth["converged"] and sth["cycles"] == st["cycles"]
+    assert np.array_equal(out, host(u))
+
+
 def test_boundary_block_timing():
     """Timing the boundary blocks (every level) leaves the result bit for bit
     unchanged, times every launch of every relaxation, and reports bytes."""
