@@ -806,7 +806,8 @@ def run_gcmg(args):
                         "h2d_bytes_per_step": int(8 * n_in + g_h.nbytes),
                         "d2h_bytes_per_step": int(u_pin.nbytes),
                         "note": "gcmg_solve_host with page-locked buffers: the device reads f at the "
-                                "inside nodes from host memory, g is copied, u (n^d) is copied back"},
+                                "inside nodes from host memory, g is copied, the device stores u (n^d) "
+                                "into host memory"},
                 "wall_s": wall}
         S.close()
         del S

@@ -248,9 +248,9 @@ gcmg_status gcmg_residual(gcmg_ctx *ctx, const double *u_dev, double *r_dev, dou
 /* Same solve with host buffers: f_host (n^d) and g_host (fine ghosts) to the
  * device, a solve from u = 0, the solution copied to u_host (n^d).  When
  * f_host is page-locked (device-addressable host memory) the device reads it
- * at the inside nodes only, the only nodes where the solver uses f; other
- * host memory is copied whole.  The buffers are read and written before the
- * call returns. */
+ * at the inside nodes only, the only nodes where the solver uses f, and a
+ * page-locked u_host is stored by the device; other host memory is copied
+ * whole.  The buffers are read and written before the call returns. */
 gcmg_status gcmg_solve_host(gcmg_ctx *ctx, const double *f_host, const double *g_host, double *u_host,
                             gcmg_stats *stats);
 

@@ -1530,6 +1530,30 @@ __global__ void k_gather_inside(LevelView<double> lv, const double *__restrict__
     }
 }
 
+// u (all nn values) stored by the device straight into a host buffer it can
+// address: 16-byte stores where both buffers allow them
+__global__ void k_store_host(const double *__restrict__ src, double *__restrict__ dst, int64_t nn) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+        const double2 *s2 = reinterpret_cast<const double2 *>(src);
+        double2 *d2 = reinterpret_cast<double2 *>(dst);
+        for (int64_t i = t0; i < nn / 2; i += stride) d2[i] = s2[i];
+        if (t0 == 0 && (nn & 1)) dst[nn - 1] = src[nn - 1];
+    } else {
+        for (int64_t i = t0; i < nn; i += stride) dst[i] = src[i];
+    }
+}
+
+// the device address of a page-locked host buffer, or null for other memory
+const void *mapped_host(const void *p) {
+    cudaPointerAttributes pa;
+    std::memset(&pa, 0, sizeof(pa));
+    const bool ok = cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();   // an unregistered pointer may leave an error behind
+    return ok ? pa.devicePointer : nullptr;
+}
+
 gcmg_status gcmg_solve_host(gcmg_ctx *c, const double *f_host, const double *g_host, double *u_host,
                             gcmg_stats *stats) {
     if (!c || !f_host || !u_host) return fail(c, GCMG_E_ARG, "null pointer");
@@ -1538,17 +1562,12 @@ gcmg_status gcmg_solve_host(gcmg_ctx *c, const double *f_host, const double *g_h
         const HostLevel &L = c->H[0];
         // page-locked f: the device reads the inside nodes' values itself;
         // any other host memory: one copy of all n^d values
-        cudaPointerAttributes pa;
-        std::memset(&pa, 0, sizeof(pa));
-        const bool mapped = cudaPointerGetAttributes(&pa, f_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-                            pa.devicePointer != nullptr;
-        cudaGetLastError();   // an unregistered pointer may leave an error behind
-        if (mapped) {
+        const void *f_mapped = mapped_host(f_host);
+        if (f_mapped) {
             const LevelView<double> lv = view<double>(c, 0, c->D64[0]);
             const int64_t cnt = lv.chunks ? lv.nchunks * CHUNK : L.nn;
             const unsigned nb = (unsigned)std::min<int64_t>((cnt + 255) / 256, 8192);
-            k_gather_inside<<<nb, 256, 0, c->stream>>>(lv, static_cast<const double *>(pa.devicePointer),
-                                                       c->D64[0].f);
+            k_gather_inside<<<nb, 256, 0, c->stream>>>(lv, static_cast<const double *>(f_mapped), c->D64[0].f);
             g_launches++;
             check_launch();
         } else {
@@ -1561,7 +1580,16 @@ gcmg_status gcmg_solve_host(gcmg_ctx *c, const double *f_host, const double *g_h
         double *u = c->D64[0].u;
         ck(cudaMemsetAsync(u, 0, L.nn * sizeof(double), c->stream), "memset");
         gcmg_status s = gcmg_solve(c, u, stats);
-        ck(cudaMemcpyAsync(u_host, u, L.nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "u");
+        // page-locked u: the device stores it; other host memory: one copy
+        void *u_mapped = const_cast<void *>(mapped_host(u_host));
+        if (u_mapped) {
+            const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((L.nn / 2 + 255) / 256, 152 * 16));
+            k_store_host<<<nb, 256, 0, c->stream>>>(u, static_cast<double *>(u_mapped), L.nn);
+            g_launches++;
+            check_launch();
+        } else {
+            ck(cudaMemcpyAsync(u_host, u, L.nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "u");
+        }
         ck(cudaStreamSynchronize(c->stream), "sync");
         return s;
     })

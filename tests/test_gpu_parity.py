@@ -281,8 +281,9 @@ def test_solve_host_equals_device():
 def test_solve_host_uses_f_on_the_inside_nodes_only(P, n, nc, pinned):
     """gcmg_solve_host with f NaN off Omega_h and stale device values from an
     earlier right-hand side: page-locked f is read by the device at the
-    inside nodes only, other host memory is copied whole; either way the
-    solution is bitwise the device solve's."""
+    inside nodes only and page-locked u stored by the device, other host
+    memory is copied whole; either way the solution is bitwise the device
+    solve's."""
     S = solver_for(P, n, nc)
     f, g = set_problem_rhs(S, P, n)
     u = torch.zeros(S.shape(0), dtype=torch.float64, device="cuda")
